@@ -1,0 +1,843 @@
+/*
+ * mars_oracle.c -- plain, slow, single-threaded CPU oracle for MARS
+ * (Meyer, Rath, Yazici, Slusallek, SIGGRAPH Asia 2024).
+ *
+ * TEST INFRASTRUCTURE ONLY: it checks the CUDA path and is loaded by the
+ * tests, the smoke check and the benchmark's CPU-baseline leg, nothing else.
+ * It shares no code with the CUDA path.  Build: gcc -O2 -ffp-contract=off.
+ *
+ * The renderer is a depth-first recursion that evaluates the paper's
+ * estimators literally:
+ *   - multi-sample MIS estimator with real-valued budgets (Eq. 1, Sec. 3),
+ *   - per-vertex secondary estimator of reflected radiance (Sec. 3.1,
+ *     "Secondary estimator"), primary estimator per technique ("Primary
+ *     estimator"), random walk from the camera ("Random walks"),
+ *   - budget-aware balance heuristic (Sec. 3 "Proxy model"; App. A.1 gives the
+ *     budget-unaware form),
+ *   - low-discrepancy stochastic rounding (Alg. 1, App. B.1),
+ *   - spatially varying count update with throughput T(x)/I_px (Sec. 3.1
+ *     "Optimization"), local estimates per cache cell (Sec. 4.1 "Local
+ *     estimates"), image variance and cost (Sec. 4.1 "Image estimates"),
+ *     outlier and count clamping (Sec. 4.1 "Outlier clamping"), channel
+ *     handling ("Handling colors").
+ * Readings of passages the paper leaves open are stated where they are used.
+ */
+#include "mars_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define PI 3.14159265358979323846
+
+/* ------------------------------------------------------------------ vectors */
+typedef struct { double x, y, z; } v3;
+static v3 mk(double x, double y, double z) { v3 r = {x, y, z}; return r; }
+static v3 add(v3 a, v3 b) { return mk(a.x + b.x, a.y + b.y, a.z + b.z); }
+static v3 sub(v3 a, v3 b) { return mk(a.x - b.x, a.y - b.y, a.z - b.z); }
+static v3 scl(v3 a, double s) { return mk(a.x * s, a.y * s, a.z * s); }
+static double dot(v3 a, v3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+static v3 cross(v3 a, v3 b) {
+  return mk(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+static double len(v3 a) { return sqrt(dot(a, a)); }
+static v3 nrm(v3 a) { return scl(a, 1.0 / len(a)); }
+static v3 ld3(const double* p) { return mk(p[0], p[1], p[2]); }
+
+/* ------------------------------------------------------------ Philox4x32-10
+ * Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3"
+ * (SC 2011): ten rounds of two 32x32->64 multiplications with round keys
+ * k + r * (0x9E3779B9, 0xBB67AE85). */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int r = 0; r < 10; ++r) {
+    uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n1 = lo1;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    uint32_t n3 = lo0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* RNG keying (a reading; the paper uses an unspecified sampler):
+ * key = (seed, job); counter = (pixel, iteration << 16 | dimension,
+ * lineage low word, lineage high word).  Dimension: technique slot * 32 +
+ * sample index for technique samples, 96 for the Alg. 1 draw, 97 for the
+ * camera jitter.  Each uniform takes the top 24 bits of one output word. */
+enum { DIM_ROUND = 96, DIM_CAMERA = 97 };
+static void rng4(const orc_params* P, uint32_t px, uint32_t dim, uint64_t lin, double u[4]) {
+  uint32_t ctr[4] = {px, (P->iteration << 16) | dim, (uint32_t)lin, (uint32_t)(lin >> 32)};
+  uint32_t key[2] = {P->seed, P->job};
+  uint32_t o[4];
+  orc_philox4x32_10(ctr, key, o);
+  for (int i = 0; i < 4; ++i) u[i] = (double)(o[i] >> 8) * (1.0 / 16777216.0);
+}
+
+/* ------------------------------------------------------------------- scene */
+typedef struct {
+  const orc_scene_desc* d;
+  double lo[3], ext[3];
+  double eps;
+  int n_lights;
+  int* light_quad;     /* quad index of light l */
+  double* light_pmf;   /* selection probability of light l */
+  float* light_cdf;    /* inclusive CDF, rounded to float */
+  double tanh, aspect;
+  v3 cam_o, cam_f, cam_r, cam_u;
+  int bits;            /* lineage bits per level */
+} ctx_t;
+
+static const double* mat_of(const orc_scene_desc* d, int m) { return d->materials + 8 * m; }
+static double mean3(const double* c) { return (c[0] + c[1] + c[2]) / 3.0; }
+
+static void bbox_add(double lo[3], double hi[3], v3 p) {
+  double a[3] = {p.x, p.y, p.z};
+  for (int i = 0; i < 3; ++i) {
+    if (a[i] < lo[i]) lo[i] = a[i];
+    if (a[i] > hi[i]) hi[i] = a[i];
+  }
+}
+
+static int ctx_init(ctx_t* C, const orc_scene_desc* d, const orc_params* P) {
+  memset(C, 0, sizeof(*C));
+  C->d = d;
+  if (d->width <= 0 || d->height <= 0) return -1;
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int i = 0; i < d->n_quads; ++i) {
+    const double* q = d->quads + 9 * i;
+    v3 p0 = ld3(q), e1 = ld3(q + 3), e2 = ld3(q + 6);
+    bbox_add(lo, hi, p0); bbox_add(lo, hi, add(p0, e1));
+    bbox_add(lo, hi, add(p0, e2)); bbox_add(lo, hi, add(add(p0, e1), e2));
+  }
+  for (int i = 0; i < d->n_spheres; ++i) {
+    const double* s = d->spheres + 4 * i;
+    bbox_add(lo, hi, mk(s[0] - s[3], s[1] - s[3], s[2] - s[3]));
+    bbox_add(lo, hi, mk(s[0] + s[3], s[1] + s[3], s[2] + s[3]));
+  }
+  for (int i = 0; i < d->n_tris; ++i)
+    for (int k = 0; k < 3; ++k) bbox_add(lo, hi, ld3(d->tris + 9 * i + 3 * k));
+  if (d->n_quads + d->n_spheres + d->n_tris == 0) return -1;
+  double emax = 0.0;
+  for (int i = 0; i < 3; ++i) {
+    C->lo[i] = lo[i];
+    C->ext[i] = hi[i] - lo[i] > 0.0 ? hi[i] - lo[i] : 1.0;
+    if (hi[i] - lo[i] > emax) emax = hi[i] - lo[i];
+  }
+  /* ray offset: 1e-4 x the largest scene extent along the shading normal */
+  C->eps = 1e-4 * (emax > 0.0 ? emax : 1.0);
+
+  /* emitters: only quads may emit; one-sided along normalize(e1 x e2) */
+  for (int i = 0; i < d->n_spheres; ++i)
+    if (mean3(mat_of(d, d->sphere_mat[i]) + 5) > 0.0) return -1;
+  for (int i = 0; i < d->n_tris; ++i)
+    if (mean3(mat_of(d, d->tri_mat[i]) + 5) > 0.0) return -1;
+  C->light_quad = (int*)malloc(sizeof(int) * (d->n_quads + 1));
+  C->light_pmf = (double*)malloc(sizeof(double) * (d->n_quads + 1));
+  C->light_cdf = (float*)malloc(sizeof(float) * (d->n_quads + 1));
+  double tot = 0.0;
+  for (int i = 0; i < d->n_quads; ++i) {
+    const double* m = mat_of(d, d->quad_mat[i]);
+    double p = mean3(m + 5);
+    if (p > 0.0) {
+      const double* q = d->quads + 9 * i;
+      double area = len(cross(ld3(q + 3), ld3(q + 6)));
+      C->light_quad[C->n_lights] = i;
+      C->light_pmf[C->n_lights] = area * p; /* selection proportional to area x radiance */
+      tot += area * p;
+      C->n_lights++;
+    }
+  }
+  double run = 0.0;
+  for (int l = 0; l < C->n_lights; ++l) {
+    run += C->light_pmf[l];
+    C->light_pmf[l] /= tot;
+    C->light_cdf[l] = (float)(run / tot);
+  }
+  if ((P->techniques & 2) && C->n_lights == 0) return -1;
+
+  /* pinhole camera: right = normalize(up x forward), true up = forward x right */
+  v3 o = ld3(d->camera), at = ld3(d->camera + 3), up = ld3(d->camera + 6);
+  C->cam_o = o;
+  C->cam_f = nrm(sub(at, o));
+  C->cam_r = nrm(cross(up, C->cam_f));
+  C->cam_u = cross(C->cam_f, C->cam_r);
+  C->tanh = tan(0.5 * d->camera[9] * PI / 180.0);
+  C->aspect = (double)d->width / (double)d->height;
+  C->bits = (P->techniques & 4) ? 6 : 5;
+  return 0;
+}
+
+static void ctx_free(ctx_t* C) {
+  free(C->light_quad);
+  free(C->light_pmf);
+  free(C->light_cdf);
+}
+
+/* -------------------------------------------------------------- intersection */
+typedef struct {
+  double t;
+  int prim;    /* global index: quads, then spheres, then triangles */
+  v3 p, ng;    /* position, unit geometric normal */
+  int mat;
+} hit_t;
+
+static int isect_quad(const double* q, v3 o, v3 d, double tmax, double* t_out) {
+  v3 p0 = ld3(q), e1 = ld3(q + 3), e2 = ld3(q + 6);
+  v3 n = cross(e1, e2);
+  double den = dot(d, n);
+  if (den == 0.0) return 0;
+  double t = dot(sub(p0, o), n) / den;
+  if (!(t > 0.0 && t < tmax)) return 0;
+  v3 w = sub(add(o, scl(d, t)), p0);
+  double nn = dot(n, n);
+  double a = dot(cross(w, e2), n) / nn;
+  double b = dot(cross(e1, w), n) / nn;
+  if (a < 0.0 || a > 1.0 || b < 0.0 || b > 1.0) return 0;
+  *t_out = t;
+  return 1;
+}
+
+static int isect_sphere(const double* s, v3 o, v3 d, double tmax, double* t_out) {
+  v3 oc = sub(o, ld3(s));
+  double b = dot(oc, d);
+  double c = dot(oc, oc) - s[3] * s[3];
+  double disc = b * b - c;
+  if (disc < 0.0) return 0;
+  double sq = sqrt(disc);
+  double t = -b - sq;
+  if (!(t > 0.0)) t = -b + sq;
+  if (!(t > 0.0 && t < tmax)) return 0;
+  *t_out = t;
+  return 1;
+}
+
+static int isect_tri(const double* v, v3 o, v3 d, double tmax, double* t_out) {
+  v3 v0 = ld3(v), e1 = sub(ld3(v + 3), v0), e2 = sub(ld3(v + 6), v0);
+  v3 p = cross(d, e2);
+  double det = dot(e1, p);
+  if (det == 0.0) return 0;
+  double inv = 1.0 / det;
+  v3 s = sub(o, v0);
+  double a = dot(s, p) * inv;
+  if (a < 0.0 || a > 1.0) return 0;
+  v3 q = cross(s, e1);
+  double b = dot(d, q) * inv;
+  if (b < 0.0 || a + b > 1.0) return 0;
+  double t = dot(e2, q) * inv;
+  if (!(t > 0.0 && t < tmax)) return 0;
+  *t_out = t;
+  return 1;
+}
+
+/* brute force over all primitives; the lowest index wins a tie in t */
+static int closest_hit(const ctx_t* C, v3 o, v3 d, hit_t* h) {
+  const orc_scene_desc* S = C->d;
+  double best = INFINITY, t;
+  int bi = -1;
+  for (int i = 0; i < S->n_quads; ++i)
+    if (isect_quad(S->quads + 9 * i, o, d, best, &t)) { best = t; bi = i; }
+  for (int i = 0; i < S->n_spheres; ++i)
+    if (isect_sphere(S->spheres + 4 * i, o, d, best, &t)) { best = t; bi = S->n_quads + i; }
+  for (int i = 0; i < S->n_tris; ++i)
+    if (isect_tri(S->tris + 9 * i, o, d, best, &t)) { best = t; bi = S->n_quads + S->n_spheres + i; }
+  if (bi < 0) return 0;
+  h->t = best;
+  h->prim = bi;
+  h->p = add(o, scl(d, best));
+  if (bi < S->n_quads) {
+    const double* q = S->quads + 9 * bi;
+    h->ng = nrm(cross(ld3(q + 3), ld3(q + 6)));
+    h->mat = S->quad_mat[bi];
+  } else if (bi < S->n_quads + S->n_spheres) {
+    int k = bi - S->n_quads;
+    const double* s = S->spheres + 4 * k;
+    h->ng = scl(sub(h->p, ld3(s)), 1.0 / s[3]);
+    h->mat = S->sphere_mat[k];
+  } else {
+    int k = bi - S->n_quads - S->n_spheres;
+    const double* v = S->tris + 9 * k;
+    h->ng = nrm(cross(sub(ld3(v + 3), ld3(v)), sub(ld3(v + 6), ld3(v))));
+    h->mat = S->tri_mat[k];
+  }
+  return 1;
+}
+
+static int occluded(const ctx_t* C, v3 o, v3 d, double tmax) {
+  const orc_scene_desc* S = C->d;
+  double t;
+  for (int i = 0; i < S->n_quads; ++i)
+    if (isect_quad(S->quads + 9 * i, o, d, tmax, &t)) return 1;
+  for (int i = 0; i < S->n_spheres; ++i)
+    if (isect_sphere(S->spheres + 4 * i, o, d, tmax, &t)) return 1;
+  for (int i = 0; i < S->n_tris; ++i)
+    if (isect_tri(S->tris + 9 * i, o, d, tmax, &t)) return 1;
+  return 0;
+}
+
+/* ------------------------------------------------------------------- frames */
+/* orthonormal basis around n (Duff et al., "Building an Orthonormal Basis,
+ * Revisited", JCGT 2017) */
+static void onb(v3 n, v3* b1, v3* b2) {
+  double sign = copysign(1.0, n.z);
+  double a = -1.0 / (sign + n.z);
+  double b = n.x * n.y * a;
+  *b1 = mk(1.0 + sign * n.x * n.x * a, sign * b, -sign * n.x);
+  *b2 = mk(b, sign + n.y * n.y * a, -n.y);
+}
+static v3 to_world(v3 l, v3 b1, v3 b2, v3 n) {
+  return add(add(scl(b1, l.x), scl(b2, l.y)), scl(n, l.z));
+}
+static v3 to_local(v3 w, v3 b1, v3 b2, v3 n) { return mk(dot(w, b1), dot(w, b2), dot(w, n)); }
+
+/* ---------------------------------------------------------------------- BSDF
+ * Lambert: f = albedo / pi, cosine-weighted sampling.
+ * GGX (Walter et al. 2007): D(h) with roughness alpha, height-correlated Smith
+ * masking-shadowing, Schlick Fresnel with F0 = material colour; sampling of
+ * D(h) cos(theta_h) and reflection about h. */
+static double ggx_D(double a2, double cz) {
+  double k = cz * cz * (a2 - 1.0) + 1.0;
+  return a2 / (PI * k * k);
+}
+static double ggx_Lambda(double a2, double cz) {
+  double c2 = cz * cz;
+  double t2 = (1.0 - c2) / c2;
+  return 0.5 * (-1.0 + sqrt(1.0 + a2 * t2));
+}
+
+/* f(wo, wi) |cos theta_i| and the BSDF-sampling pdf of wi (local frame, n=+z) */
+static void bsdf_eval(const double* m, v3 wo, v3 wi, double fcos[3], double* pdf) {
+  fcos[0] = fcos[1] = fcos[2] = 0.0;
+  *pdf = 0.0;
+  if (wo.z <= 0.0 || wi.z <= 0.0) return;
+  if ((int)m[0] == 0) {
+    for (int c = 0; c < 3; ++c) fcos[c] = m[1 + c] / PI * wi.z;
+    *pdf = wi.z / PI;
+    return;
+  }
+  double a2 = m[4] * m[4];
+  v3 h = nrm(add(wo, wi));
+  double woh = dot(wo, h);
+  if (woh <= 0.0) return;
+  double D = ggx_D(a2, h.z);
+  double G = 1.0 / (1.0 + ggx_Lambda(a2, wo.z) + ggx_Lambda(a2, wi.z));
+  double s = 1.0 - woh;
+  double s5 = s * s * s * s * s;
+  for (int c = 0; c < 3; ++c) {
+    double F = m[1 + c] + (1.0 - m[1 + c]) * s5;
+    fcos[c] = D * G * F / (4.0 * wo.z);
+  }
+  *pdf = D * h.z / (4.0 * woh);
+}
+
+/* returns 1 and a direction with wi.z > 0 on success, 0 for an invalid sample */
+static int bsdf_sample(const double* m, v3 wo, double u0, double u1, v3* wi) {
+  if ((int)m[0] == 0) {
+    double r = sqrt(u0), phi = 2.0 * PI * u1;
+    double z = 1.0 - u0;
+    *wi = mk(r * cos(phi), r * sin(phi), sqrt(z > 0.0 ? z : 0.0));
+    return wi->z > 0.0;
+  }
+  double a2 = m[4] * m[4];
+  double t2 = a2 * u0 / (1.0 - u0);
+  double ct = 1.0 / sqrt(1.0 + t2);
+  double st = sqrt(t2) * ct;
+  double phi = 2.0 * PI * u1;
+  v3 h = mk(st * cos(phi), st * sin(phi), ct);
+  double woh = dot(wo, h);
+  if (woh <= 0.0) return 0;
+  *wi = sub(scl(h, 2.0 * woh), wo);
+  return wi->z > 0.0;
+}
+
+void orc_bsdf_eval_local(const orc_scene_desc* scene, int m, const double* wo, const double* wi,
+                         double* fcos_rgb, double* pdf) {
+  bsdf_eval(mat_of(scene, m), ld3(wo), ld3(wi), fcos_rgb, pdf);
+}
+
+int orc_bsdf_sample_local(const orc_scene_desc* scene, int m, const double* wo, double u0,
+                          double u1, double* wi, double* pdf) {
+  v3 w;
+  const double* mm = mat_of(scene, m);
+  if (!bsdf_sample(mm, ld3(wo), u0, u1, &w)) { *pdf = 0.0; return 0; }
+  double f[3];
+  bsdf_eval(mm, ld3(wo), w, f, pdf);
+  wi[0] = w.x; wi[1] = w.y; wi[2] = w.z;
+  return 1;
+}
+
+/* ------------------------------------------------------------------- guide
+ * Per-cell directional histogram on the cylinder (z = cos theta, phi), 16 x 16
+ * equal-area bins; the bin index of a direction is decided in float32. */
+static int guide_bin(v3 w) {
+  float zf = (float)w.z;
+  int iz = (int)floorf((zf + 1.0f) * 8.0f);
+  if (iz < 0) iz = 0;
+  if (iz > 15) iz = 15;
+  float ph = atan2f((float)w.y, (float)w.x);
+  if (ph < 0.0f) ph += 6.28318530717958647692f;
+  int ip = (int)floorf(ph * (float)(16.0 / (2.0 * PI)));
+  if (ip < 0) ip = 0;
+  if (ip > 15) ip = 15;
+  return iz * 16 + ip;
+}
+static double bin_prob(const float* cdf, int b) {
+  float pb = cdf[b] - (b > 0 ? cdf[b - 1] : 0.0f); /* float subtraction on purpose */
+  return (double)pb;
+}
+double orc_guide_pdf(const float* cdf, const double* w) {
+  return bin_prob(cdf, guide_bin(ld3(w))) * (ORC_GUIDE_BINS / (4.0 * PI));
+}
+static int guide_pick(const float* cdf, float u0) {
+  for (int b = 0; b < ORC_GUIDE_BINS; ++b)
+    if (u0 < cdf[b]) return b;
+  return ORC_GUIDE_BINS - 1;
+}
+static v3 guide_dir(int b, double u1, double u2) {
+  int iz = b / 16, ip = b % 16;
+  double z = -1.0 + 2.0 * ((double)iz + u1) / 16.0;
+  double phi = 2.0 * PI * ((double)ip + u2) / 16.0;
+  double s = 1.0 - z * z;
+  s = sqrt(s > 0.0 ? s : 0.0);
+  return mk(s * cos(phi), s * sin(phi), z);
+}
+void orc_guide_sample(const float* cdf, double u0, double u1, double u2, double* w, double* pdf) {
+  int b = guide_pick(cdf, (float)u0);
+  v3 d = guide_dir(b, u1, u2);
+  w[0] = d.x; w[1] = d.y; w[2] = d.z;
+  *pdf = bin_prob(cdf, b) * (ORC_GUIDE_BINS / (4.0 * PI));
+}
+
+/* --------------------------------------------------------- MIS and rounding */
+/* Balance heuristic over the techniques that participate in a subintegrand
+ * (App. A.1); budget-aware weights multiply each density by its real-valued
+ * budget beta (reading of Sec. 3 "Proxy model": weights "containing the
+ * techniques' budgets"). */
+double orc_balance_weight(int n, const double* beta, const double* pdf, const int* participates,
+                          int t, int aware) {
+  double den = 0.0;
+  for (int k = 0; k < n; ++k)
+    if (participates[k]) den += (aware ? beta[k] : 1.0) * pdf[k];
+  if (!participates[t] || den <= 0.0) return 0.0;
+  return (aware ? beta[t] : 1.0) * pdf[t] / den;
+}
+
+/* Alg. 1: one uniform r decides the rounding of all techniques in order. */
+void orc_stochastic_round(int n, const float* beta, float r, int32_t* gamma) {
+  for (int t = 0; t < n; ++t) {
+    float s = beta[t] + r;
+    int32_t g = (int32_t)floorf(s);
+    gamma[t] = g;
+    r = s - (float)g;
+  }
+}
+
+/* Spatial count (Sec. 3.1 "Optimization"; colour per "Handling colors"):
+ * per channel beta_ch = T_ch / I_ch * q_ch for the RR and S factors, combined
+ * by the root mean square over channels, then the three cases of the update
+ * (RR if below 1, else S if above 1, else 1), then the clamp (Sec. 4.1). */
+double orc_vertex_count(const float* q_rr, const float* q_s, const double* T, const float* I,
+                        double lo, double hi) {
+  double brr = 0.0, bs = 0.0;
+  for (int c = 0; c < 3; ++c) {
+    double f = T[c] / (double)I[c];
+    double a = f * (double)q_rr[c], b = f * (double)q_s[c];
+    brr += a * a;
+    bs += b * b;
+  }
+  brr = sqrt(brr / 3.0);
+  bs = sqrt(bs / 3.0);
+  double beta = brr < 1.0 ? brr : (bs > 1.0 ? bs : 1.0);
+  if (beta < lo) beta = lo;
+  if (beta > hi) beta = hi;
+  return beta;
+}
+
+/* ----------------------------------------------------------------- renderer */
+typedef struct {
+  const ctx_t* C;
+  const orc_params* P;
+  orc_state* st;
+  int px;
+  int on[ORC_NT];  /* technique enabled */
+} rnd_t;
+
+static int cell_of(const ctx_t* C, int N, v3 p) {
+  /* the cell index is decided in float32 */
+  float pf[3] = {(float)p.x, (float)p.y, (float)p.z};
+  int idx[3];
+  for (int a = 0; a < 3; ++a) {
+    float f = (pf[a] - (float)C->lo[a]) / (float)C->ext[a] * (float)N;
+    int i = (int)floorf(f);
+    if (i < 0) i = 0;
+    if (i > N - 1) i = N - 1;
+    idx[a] = i;
+  }
+  return (idx[2] * N + idx[1]) * N + idx[0];
+}
+
+static double lum(const double* c) { return 0.2126 * c[0] + 0.7152 * c[1] + 0.0722 * c[2]; }
+
+typedef struct {
+  v3 p, ng, ns, wo;
+  int mat, cell;
+  v3 b1, b2;
+} vtx_t;
+
+static void secondary_estimator(rnd_t* R, const vtx_t* x, int depth, uint64_t lin, const double T[3],
+                                double Lr[3], double* cost);
+
+/* pdf of the NEE technique for a direction that reaches point y on light quad q */
+static double nee_pdf_at(const ctx_t* C, int quad, v3 x, v3 y, v3 wi) {
+  for (int l = 0; l < C->n_lights; ++l) {
+    if (C->light_quad[l] != quad) continue;
+    const double* q = C->d->quads + 9 * quad;
+    v3 n = cross(ld3(q + 3), ld3(q + 6));
+    double area = len(n);
+    n = scl(n, 1.0 / area);
+    double cosl = -dot(n, wi);
+    if (cosl <= 0.0) return 0.0;
+    v3 dv = sub(y, x);
+    return C->light_pmf[l] * dot(dv, dv) / (area * cosl);
+  }
+  return 0.0;
+}
+
+/* Trace a ray drawn at the parent (or the camera) and return its sample value
+ * fcp * (Le * w_dir + w_ind * <L_r(child)>), its cost in rays, and the
+ * luminance of the incident radiance estimate (for guide learning). */
+typedef struct {
+  double fcp[3];     /* f |cos| / p_t at the parent (1 for the camera) */
+  double A;          /* MIS numerator of the drawing technique */
+  double S_ind;      /* MIS denominator over the indirect techniques */
+  double betaN_pN0;  /* beta_NEE (aware) or 1 (unaware) if NEE competes, else 0 */
+  int camera;        /* camera ray: no MIS */
+  double T_child[3]; /* prefix throughput at the hit */
+} ray_info;
+
+static void trace_sample(rnd_t* R, v3 o, v3 d, int depth, uint64_t lin, const ray_info* ri,
+                         double v_out[3], double* cost_out, double* Li_lum) {
+  const ctx_t* C = R->C;
+  const orc_params* P = R->P;
+  hit_t h;
+  double E[3] = {0, 0, 0}, Le_raw[3] = {0, 0, 0}, Lchild[3] = {0, 0, 0};
+  double ccost = 0.0;
+  double w_ind = ri->camera ? 1.0 : (ri->S_ind > 0.0 ? ri->A / ri->S_ind : 0.0);
+  R->st->counters[1] += 1.0; /* one traced path vertex */
+  if (closest_hit(C, o, d, &h)) {
+    v3 wo = scl(d, -1.0);
+    const double* m = mat_of(C->d, h.mat);
+    double cosg = dot(h.ng, wo);
+    if (cosg > 0.0 && mean3(m + 5) > 0.0) {
+      /* emission reached by a technique sample: weight against NEE's density */
+      double w_dir = 1.0;
+      if (!ri->camera) {
+        double pn = 0.0;
+        if (ri->betaN_pN0 > 0.0 && h.prim < C->d->n_quads)
+          pn = nee_pdf_at(C, h.prim, o, h.p, d);
+        double den = ri->S_ind + ri->betaN_pN0 * pn;
+        w_dir = den > 0.0 ? ri->A / den : 0.0;
+      }
+      for (int c = 0; c < 3; ++c) {
+        Le_raw[c] = m[5 + c];
+        E[c] = m[5 + c] * w_dir;
+      }
+    }
+    int reflective = (m[1] > 0.0 || m[2] > 0.0 || m[3] > 0.0);
+    if (depth <= P->max_depth - 1 && reflective) {
+      vtx_t x;
+      x.p = h.p;
+      x.ng = h.ng;
+      x.wo = wo;
+      x.ns = cosg >= 0.0 ? h.ng : scl(h.ng, -1.0);
+      x.mat = h.mat;
+      x.cell = cell_of(C, P->grid_n, h.p);
+      onb(x.ns, &x.b1, &x.b2);
+      secondary_estimator(R, &x, depth, lin, ri->T_child, Lchild, &ccost);
+    }
+  }
+  for (int c = 0; c < 3; ++c) v_out[c] = ri->fcp[c] * (E[c] + w_ind * Lchild[c]);
+  *cost_out = 1.0 + ccost;
+  if (Li_lum) {
+    double Li[3] = {Le_raw[0] + Lchild[0], Le_raw[1] + Lchild[1], Le_raw[2] + Lchild[2]};
+    *Li_lum = lum(Li);
+  }
+}
+
+static void stat_add(rnd_t* R, int cell, int t, const double v[3], double cost, const double T[3]) {
+  if (!R->P->collect) return;
+  double* s = R->st->stats + ((size_t)cell * ORC_NT + t) * ORC_NSTAT;
+  s[0] += 1.0;
+  for (int c = 0; c < 3; ++c) {
+    double x = v[c];
+    /* local outlier clamp (Sec. 4.1): the sample's image contribution is kept
+     * below outlier x pixel estimate, i.e. v <= outlier * I_px / T */
+    if (R->P->has_estimate && T[c] > 0.0) {
+      double lim = R->P->outlier * (double)R->st->est[3 * R->px + c] / T[c];
+      if (x > lim) x = lim;
+    }
+    s[1 + c] += x;
+    s[4 + c] += x * x;
+  }
+  s[7] += cost;
+}
+
+/* Secondary estimator at vertex x (Sec. 3.1): sum over techniques t of
+ * 1/beta_t times the sum of gamma_t primary estimates, gamma from Alg. 1. */
+static void secondary_estimator(rnd_t* R, const vtx_t* x, int depth, uint64_t lin, const double T[3],
+                                double Lr[3], double* cost) {
+  const ctx_t* C = R->C;
+  const orc_params* P = R->P;
+  orc_state* st = R->st;
+  const double* m = mat_of(C->d, x->mat);
+  Lr[0] = Lr[1] = Lr[2] = 0.0;
+  *cost = 0.0;
+  st->counters[2] += 1.0;
+
+  /* budgets beta_t(x) */
+  float betaf[ORC_NT] = {0, 0, 0};
+  double beta[ORC_NT] = {0, 0, 0};
+  for (int t = 0; t < ORC_NT; ++t) {
+    if (!R->on[t]) continue;
+    double b = 1.0;
+    if (P->mode == ORC_MODE_MARS && st->valid[x->cell * ORC_NT + t]) {
+      size_t o = ((size_t)x->cell * ORC_NT + t) * 3;
+      b = orc_vertex_count(st->q_rr + o, st->q_s + o, T, st->est + 3 * R->px, P->clamp_lo, P->clamp_hi);
+    }
+    betaf[t] = (float)b;       /* the budget is carried in float32 */
+    beta[t] = (double)betaf[t];
+    st->counters[3 + t] += beta[t];
+  }
+
+  /* Alg. 1 */
+  double u[4];
+  rng4(P, (uint32_t)R->px, DIM_ROUND, lin, u);
+  float rb[ORC_NT];
+  int32_t gam[ORC_NT];
+  int n_on = 0, idx[ORC_NT];
+  for (int t = 0; t < ORC_NT; ++t)
+    if (R->on[t]) { rb[n_on] = betaf[t]; idx[n_on++] = t; }
+  int32_t gtmp[ORC_NT];
+  orc_stochastic_round(n_on, rb, (float)u[0], gtmp);
+  for (int t = 0; t < ORC_NT; ++t) gam[t] = 0;
+  for (int k = 0; k < n_on; ++k) gam[idx[k]] = gtmp[k];
+
+  /* MIS participation: direct light {BSDF, NEE, guided}, indirect {BSDF, guided} */
+  int aware = P->weights == ORC_WEIGHTS_AWARE;
+  double bw[ORC_NT];
+  for (int t = 0; t < ORC_NT; ++t) bw[t] = R->on[t] ? (aware ? beta[t] : 1.0) : 0.0;
+  const float* cdf = (R->on[ORC_T_GUIDED]) ? st->guide_cdf + (size_t)x->cell * ORC_GUIDE_BINS : NULL;
+
+  for (int t = 0; t < ORC_NT; ++t) {
+    for (int s = 0; s < gam[t]; ++s) {
+      double v[3] = {0, 0, 0}, c_s = 1.0;
+      rng4(P, (uint32_t)R->px, (uint32_t)(t * 32 + s), lin, u);
+      if (t == ORC_T_NEE) {
+        /* primary estimator of NEE: light by area x radiance, uniform point */
+        int l = C->n_lights - 1;
+        for (int k = 0; k < C->n_lights; ++k)
+          if ((float)u[0] < C->light_cdf[k]) { l = k; break; }
+        int qi = C->light_quad[l];
+        const double* q = C->d->quads + 9 * qi;
+        v3 y = add(ld3(q), add(scl(ld3(q + 3), u[1]), scl(ld3(q + 6), u[2])));
+        v3 xo = add(x->p, scl(x->ns, C->eps));
+        v3 dv = sub(y, xo);
+        double dist = len(dv);
+        v3 wi = scl(dv, 1.0 / dist);
+        double pn = nee_pdf_at(C, qi, xo, y, wi);
+        double ci = dot(x->ns, wi);
+        if (pn > 0.0 && ci > 0.0) {
+          double fc[3], pb, pg = 0.0;
+          bsdf_eval(m, to_local(x->wo, x->b1, x->b2, x->ns), to_local(wi, x->b1, x->b2, x->ns), fc, &pb);
+          if (cdf) pg = orc_guide_pdf(cdf, (double[]){wi.x, wi.y, wi.z});
+          if ((fc[0] > 0.0 || fc[1] > 0.0 || fc[2] > 0.0) && !occluded(C, xo, wi, dist - C->eps)) {
+            double den = bw[ORC_T_BSDF] * pb + bw[ORC_T_GUIDED] * pg + bw[ORC_T_NEE] * pn;
+            double w = bw[ORC_T_NEE] * pn / den;
+            const double* Le = mat_of(C->d, C->d->quad_mat[qi]) + 5;
+            for (int c = 0; c < 3; ++c) v[c] = fc[c] * Le[c] / pn * w;
+          }
+        }
+      } else {
+        /* primary estimator of BSDF or guided sampling: extend the path */
+        v3 wi;
+        int ok;
+        double pt = 0.0;
+        if (t == ORC_T_BSDF) {
+          v3 wl;
+          ok = bsdf_sample(m, to_local(x->wo, x->b1, x->b2, x->ns), u[0], u[1], &wl);
+          if (ok) wi = to_world(wl, x->b1, x->b2, x->ns);
+        } else {
+          int b = guide_pick(cdf, (float)u[0]);
+          wi = guide_dir(b, u[1], u[2]);
+          pt = bin_prob(cdf, b) * (ORC_GUIDE_BINS / (4.0 * PI));
+          ok = dot(wi, x->ns) > 0.0;
+        }
+        if (ok) {
+          double fc[3], pb, pg = 0.0;
+          bsdf_eval(m, to_local(x->wo, x->b1, x->b2, x->ns), to_local(wi, x->b1, x->b2, x->ns), fc, &pb);
+          if (cdf) pg = orc_guide_pdf(cdf, (double[]){wi.x, wi.y, wi.z});
+          if (t == ORC_T_BSDF) pt = pb;
+          if (pt > 0.0 && (fc[0] > 0.0 || fc[1] > 0.0 || fc[2] > 0.0)) {
+            ray_info ri;
+            ri.camera = 0;
+            for (int c = 0; c < 3; ++c) ri.fcp[c] = fc[c] / pt;
+            ri.A = bw[t] * pt;
+            ri.S_ind = bw[ORC_T_BSDF] * pb + bw[ORC_T_GUIDED] * pg;
+            ri.betaN_pN0 = bw[ORC_T_NEE];
+            double w_ind = ri.A / ri.S_ind;
+            for (int c = 0; c < 3; ++c) ri.T_child[c] = T[c] * ri.fcp[c] * w_ind / beta[t];
+            uint64_t digit = (uint64_t)(t == ORC_T_BSDF ? s + 1 : 32 + s + 1);
+            uint64_t clin = (lin << C->bits) | digit;
+            double li_lum = 0.0;
+            trace_sample(R, add(x->p, scl(x->ns, C->eps)), wi, depth + 1, clin, &ri, v, &c_s, &li_lum);
+            if (cdf && P->collect) {
+              /* guide learning: incident radiance / multi-sample density of the
+               * indirect techniques, binned by direction */
+              double dens = beta[ORC_T_BSDF] * pb + beta[ORC_T_GUIDED] * pg;
+              if (dens > 0.0 && li_lum > 0.0)
+                st->hist[(size_t)x->cell * ORC_GUIDE_BINS + guide_bin(wi)] += li_lum / dens;
+            }
+          }
+        }
+      }
+      for (int c = 0; c < 3; ++c) Lr[c] += v[c] / beta[t];
+      *cost += c_s;
+      stat_add(R, x->cell, t, v, c_s, T);
+    }
+  }
+}
+
+int orc_render(const orc_scene_desc* scene, const orc_params* P, orc_state* st, int px_begin,
+               int px_end) {
+  if (!scene || !P || !st) return -1;
+  if (!(P->techniques & 1)) return -1;
+  if (P->max_depth < 1 || P->grid_n < 1) return -1;
+  if (P->clamp_hi > 30.0 || P->clamp_lo < 0.0) return -1;
+  if (P->mode == ORC_MODE_MARS && !P->has_estimate) return -2;
+  if ((P->techniques & 4) && !st->guide_cdf) return -1;
+  ctx_t C;
+  if (ctx_init(&C, scene, P) != 0) { ctx_free(&C); return -3; }
+  if ((P->max_depth - 1) * C.bits > 64) { ctx_free(&C); return -1; }
+  int npx = scene->width * scene->height;
+  if (px_begin < 0 || px_end > npx || px_begin > px_end) { ctx_free(&C); return -1; }
+  rnd_t R;
+  R.C = &C;
+  R.P = P;
+  R.st = st;
+  for (int t = 0; t < ORC_NT; ++t) R.on[t] = (P->techniques >> t) & 1;
+  for (int px = px_begin; px < px_end; ++px) {
+    R.px = px;
+    double u[4];
+    rng4(P, (uint32_t)px, DIM_CAMERA, 0, u);
+    int ix = px % scene->width, iy = px / scene->width;
+    double sx = (2.0 * ((double)ix + u[0]) / scene->width - 1.0) * C.tanh * C.aspect;
+    double sy = (1.0 - 2.0 * ((double)iy + u[1]) / scene->height) * C.tanh;
+    v3 d = nrm(add(C.cam_f, add(scl(C.cam_r, sx), scl(C.cam_u, sy))));
+    /* random walk (Sec. 3.1): W/p = 1 for the pinhole with box filter */
+    ray_info ri;
+    memset(&ri, 0, sizeof(ri));
+    ri.camera = 1;
+    ri.A = ri.S_ind = 1.0;
+    for (int c = 0; c < 3; ++c) { ri.fcp[c] = 1.0; ri.T_child[c] = 1.0; }
+    double v[3], cost;
+    trace_sample(&R, C.cam_o, d, 1, 0, &ri, v, &cost, NULL);
+    for (int c = 0; c < 3; ++c) st->image[3 * px + c] = v[c];
+    st->counters[0] += cost;
+  }
+  ctx_free(&C);
+  return 0;
+}
+
+/* ------------------------------------------------------------ image / update */
+double orc_image_stats(int W, int H, const double* img, double* run_sum, int n_prev,
+                       double outlier, double* est_out) {
+  int n = W * H;
+  double inv = 1.0 / (double)(n_prev + 1);
+  double chmean[3] = {0, 0, 0};
+  for (int p = 0; p < n; ++p)
+    for (int c = 0; c < 3; ++c) {
+      run_sum[3 * p + c] += img[3 * p + c];
+      chmean[c] += run_sum[3 * p + c] * inv;
+    }
+  for (int c = 0; c < 3; ++c) chmean[c] /= (double)n;
+  /* pixel estimate (reading; the paper denoises with OIDN, Sec. 4.1): 3x3 box
+   * filter of the running mean over the in-image neighbours, floored */
+  for (int y = 0; y < H; ++y)
+    for (int x = 0; x < W; ++x)
+      for (int c = 0; c < 3; ++c) {
+        double s = 0.0;
+        int k = 0;
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx) {
+            int xx = x + dx, yy = y + dy;
+            if (xx < 0 || yy < 0 || xx >= W || yy >= H) continue;
+            s += run_sum[3 * (yy * W + xx) + c] * inv;
+            k++;
+          }
+        double e = s / (double)k;
+        double fl = 1e-3 * chmean[c];
+        if (e < fl) e = fl;
+        if (e < 1e-8) e = 1e-8;
+        est_out[3 * (y * W + x) + c] = e;
+      }
+  /* image relative variance (Sec. 4.1 "Image estimates") with the sample
+   * clamped at outlier x estimate ("Outlier clamping"); one sample per pixel */
+  double vi = 0.0;
+  for (int p = 0; p < n; ++p)
+    for (int c = 0; c < 3; ++c) {
+      double e = est_out[3 * p + c];
+      double I = img[3 * p + c];
+      if (I > outlier * e) I = outlier * e;
+      double r = (I - e) / e;
+      vi += r * r;
+    }
+  return vi / (3.0 * (double)n);
+}
+
+/* Fixed-point step (Eq. optimalBeta in its spatial form, Sec. 3.1): the cache
+ * stores per channel q^RR = sqrt(C_I / C_t * E[<L_r,t>^2] / V_I) and
+ * q^S = sqrt(C_I / C_t * V[<L_r,t>] / V_I); the vertex multiplies by T / I_px.
+ * Moments are the per-sample (primary) moments of Sec. 4.1 "Local estimates". */
+void orc_update_counts(int n_cells, int techniques, const double* stats, double VI, double CI,
+                       float* q_rr, float* q_s, uint8_t* valid) {
+  if (!(VI > 1e-12)) return;
+  for (int c = 0; c < n_cells; ++c)
+    for (int t = 0; t < ORC_NT; ++t) {
+      if (!((techniques >> t) & 1)) continue;
+      const double* s = stats + ((size_t)c * ORC_NT + t) * ORC_NSTAT;
+      double n = s[0];
+      if (n < 2.0 || !(s[7] > 0.0)) continue;
+      double Ct = s[7] / n;
+      for (int ch = 0; ch < 3; ++ch) {
+        double m1 = s[1 + ch] / n;
+        double m2 = s[4 + ch] / n;
+        double var = m2 - m1 * m1;
+        if (var < 0.0) var = 0.0;
+        q_rr[((size_t)c * ORC_NT + t) * 3 + ch] = (float)sqrt(CI / Ct * m2 / VI);
+        q_s[((size_t)c * ORC_NT + t) * 3 + ch] = (float)sqrt(CI / Ct * var / VI);
+      }
+      valid[(size_t)c * ORC_NT + t] = 1;
+    }
+}
+
+void orc_guide_update(int n_cells, const double* hist, float* cdf) {
+  for (int c = 0; c < n_cells; ++c) {
+    const double* h = hist + (size_t)c * ORC_GUIDE_BINS;
+    double H = 0.0;
+    for (int b = 0; b < ORC_GUIDE_BINS; ++b) H += h[b];
+    double run = 0.0;
+    for (int b = 0; b < ORC_GUIDE_BINS; ++b) {
+      double p = H > 0.0 ? 0.9 * h[b] / H + 0.1 / ORC_GUIDE_BINS : 1.0 / ORC_GUIDE_BINS;
+      run += p;
+      cdf[(size_t)c * ORC_GUIDE_BINS + b] = (float)run;
+    }
+    cdf[(size_t)c * ORC_GUIDE_BINS + ORC_GUIDE_BINS - 1] = 1.0f;
+  }
+}

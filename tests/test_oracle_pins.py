@@ -1,0 +1,484 @@
+"""Pins of the CPU oracle against facts fixed by the paper or by mathematics.
+
+Each test checks the oracle against something other than itself: closed forms
+(furnace, polygonal-light irradiance, the budget-unaware optimum of App. A.3),
+invariants (sum of MIS weights, unbiasedness under any count field, Alg. 1
+marginals), the paper's own derived formulas (rounding variance rho of App. A.2)
+and brute force over small grids.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import mars_workloads as W
+
+
+# --------------------------------------------------------------------- Philox
+def test_philox_uniform_and_avalanche(orc):
+    rng = np.random.default_rng(1)
+    key = np.array([12345, 678], np.uint32)
+    outs = []
+    for i in range(20000):
+        outs.append(orc.philox(np.array([i, 7, 3, 0], np.uint32), key))
+    o = np.array(outs, dtype=np.uint64)
+    u = (o >> np.uint64(8)).astype(np.float64) / 2 ** 24
+    assert abs(u.mean() - 0.5) < 4 * math.sqrt(1 / 12 / u.size)
+    hist = np.histogram(u, bins=64, range=(0, 1))[0]
+    exp = u.size / 64
+    chi2 = ((hist - exp) ** 2 / exp).sum()
+    assert chi2 < 63 + 5 * math.sqrt(2 * 63)
+    bits = np.unpackbits(o.astype(np.uint32).view(np.uint8))
+    assert abs(bits.mean() - 0.5) < 0.005
+    # avalanche: one flipped counter bit flips about half of the 128 output bits
+    flips = []
+    for _ in range(300):
+        c = rng.integers(0, 2 ** 32, size=4, dtype=np.uint64).astype(np.uint32)
+        k = rng.integers(0, 2 ** 32, size=2, dtype=np.uint64).astype(np.uint32)
+        b = int(rng.integers(0, 128))
+        c2 = c.copy()
+        c2[b // 32] ^= np.uint32(1 << (b % 32))
+        a1, a2 = orc.philox(c, k), orc.philox(c2, k)
+        flips.append(sum(bin(int(x) ^ int(y)).count("1") for x, y in zip(a1, a2)))
+    assert abs(np.mean(flips) - 64) < 2.0
+    # a bijection of the counter for a fixed key: no collisions
+    seen = {tuple(x) for x in o.tolist()}
+    assert len(seen) == len(o)
+
+
+# ---------------------------------------------------------------------- Alg. 1
+@pytest.mark.parametrize("betas", [[0.3, 0.45], [1.7, 0.05, 2.25], [0.999, 19.5, 3.0], [4.0, 0.5, 0.5]])
+def test_alg1_marginals_and_total(orc, betas):
+    """Alg. 1 (App. B.1): with one uniform r, E[gamma_t] = beta_t for every t and
+    the total is floor or ceil of sum(beta)."""
+    n = 1 << 14
+    g = np.array([orc.stochastic_round(betas, (k + 0.5) / n) for k in range(n)])
+    b = np.array(betas, np.float32).astype(np.float64)
+    assert np.all(np.abs(g.mean(0) - b) <= len(betas) / n + 1e-6)
+    tot = g.sum(1)
+    assert set(np.unique(tot)) <= {math.floor(b.sum()), math.ceil(b.sum())}
+    # every technique's count is floor or ceil of its own budget
+    for t in range(len(betas)):
+        assert set(np.unique(g[:, t])) <= {math.floor(b[t]), math.ceil(b[t])}
+
+
+@pytest.mark.parametrize("beta", [0.3, 1.0, 1.4, 2.5, 7.75])
+@pytest.mark.parametrize("E,V", [(1.0, 0.5), (2.0, 10.0)])
+def test_stochastic_rounding_variance_matches_rho(orc, beta, E, V):
+    """App. A.2: V[<I; beta>] = V/beta + rho(beta) E^2 with
+    rho = (beta - floor)(ceil - beta) / beta^2, for rounding that divides by the
+    real-valued beta.  gamma comes from the oracle's Alg. 1 with one technique;
+    E[(sum_{s<=gamma} X)^2 | gamma] = gamma V + gamma^2 E^2."""
+    n = 1 << 14
+    gam = np.array([orc.stochastic_round([beta], (k + 0.5) / n)[0] for k in range(n)], np.float64)
+    b = float(np.float32(beta))
+    second = ((gam * V + gam ** 2 * E ** 2) / b ** 2).mean()
+    mean = (gam * E / b).mean()
+    var = second - mean ** 2
+    rho = (b - math.floor(b)) * (math.ceil(b) - b) / b ** 2
+    assert mean == pytest.approx(E, rel=1e-3)
+    assert var == pytest.approx(V / b + rho * E ** 2, rel=2e-3, abs=1e-6)
+
+
+# ------------------------------------------------------------------------- MIS
+def test_balance_weights_sum_to_one(orc):
+    """App. A.1: for every subintegrand the weights of the participating
+    techniques sum to one (budget-aware and budget-unaware)."""
+    rng = np.random.default_rng(3)
+    for _ in range(200):
+        beta = rng.uniform(0.05, 20, 3)
+        pdf = rng.exponential(1.0, 3)
+        part = rng.integers(0, 2, 3)
+        part[rng.integers(0, 3)] = 1
+        for aware in (True, False):
+            ws = [orc.balance_weight(beta, pdf, part, t, aware) for t in range(3)]
+            assert sum(ws) == pytest.approx(1.0, rel=1e-12)
+            for t in range(3):
+                if not part[t]:
+                    assert ws[t] == 0.0
+    # budget-aware weight of a technique grows with its own budget
+    w1 = orc.balance_weight([1.0, 1.0, 0], [1.0, 1.0, 0], [1, 1, 0], 0, True)
+    w2 = orc.balance_weight([3.0, 1.0, 0], [1.0, 1.0, 0], [1, 1, 0], 0, True)
+    assert w1 == pytest.approx(0.5) and w2 == pytest.approx(0.75)
+
+
+# ----------------------------------------------------------- count rule (Eq. 2)
+def test_vertex_count_three_cases_and_clamp(orc):
+    """Sec. 3.1 'Optimization': beta = beta_RR if beta_RR < 1, else beta_S if
+    beta_S > 1, else 1; clamped to [0.05, 20] (Sec. 4.1).  Grey inputs reduce to
+    the scalar formula T / I * q."""
+    one = np.ones(3)
+    I = np.ones(3, np.float32)
+    g = lambda x: np.full(3, x, np.float32)
+    # RR regime
+    assert orc.vertex_count(g(0.5), g(0.2), one, I) == pytest.approx(0.5, rel=1e-7)
+    # splitting regime
+    assert orc.vertex_count(g(4.0), g(3.0), one, I) == pytest.approx(3.0, rel=1e-7)
+    # disagreement: RR says >= 1, S says <= 1 -> one sample
+    assert orc.vertex_count(g(1.5), g(0.5), one, I) == 1.0
+    # throughput and pixel estimate scale the factors
+    assert orc.vertex_count(g(0.5), g(0.1), 0.5 * one, g(2.0)) == pytest.approx(0.125, rel=1e-7)
+    # clamp
+    assert orc.vertex_count(g(1e-4), g(0.0), one, I) == pytest.approx(0.05)
+    assert orc.vertex_count(g(100.0), g(90.0), one, I) == pytest.approx(20.0)
+    # colour: root mean square over channels of the per-channel counts
+    q = np.array([0.3, 0.6, 0.9], np.float32)
+    rms = math.sqrt((0.3 ** 2 + 0.6 ** 2 + 0.9 ** 2) / 3)
+    assert orc.vertex_count(q, q * 0.5, one, I) == pytest.approx(rms, rel=1e-6)
+
+
+# --------------------------------------------------------- fixed point (App. A)
+def _scalar_moments(beta, E, V, C, VD, CD):
+    """Proxy model (Sec. 3 'Optimization', EARS simplification): technique
+    variance M2/beta - E^2 for beta < 1, V/beta otherwise."""
+    var = 0.0
+    for b, e, v in zip(beta, E, V):
+        m2 = v + e * e
+        var += (m2 / b - e * e) if b < 1 else v / b
+    return var + VD, float(np.dot(beta, C)) + CD
+
+
+def _stats_for(E, V, C, n=1e6):
+    """Per-cell statistics whose moments are exactly (E, E^2 + V, C)."""
+    st = np.zeros((1, 3, 8))
+    for t in range(len(E)):
+        st[0, t, 0] = n
+        st[0, t, 1:4] = n * E[t]
+        st[0, t, 4:7] = n * (V[t] + E[t] ** 2)
+        st[0, t, 7] = n * C[t]
+    return st
+
+
+def _fixed_point(orc, E, V, C, VD, CD, beta0, steps):
+    tech = (1 << len(E)) - 1
+    beta = np.array(beta0, float)
+    q_rr = np.zeros((1, 3, 3), np.float32)
+    q_s = np.zeros((1, 3, 3), np.float32)
+    valid = np.zeros((1, 3), np.uint8)
+    hist = [beta.copy()]
+    for _ in range(steps):
+        VI, CI = _scalar_moments(beta, E, V, C, VD, CD)
+        q_rr, q_s, valid = orc.update_counts(_stats_for(E, V, C), VI, CI, tech, q_rr, q_s, valid)
+        beta = np.array([orc.vertex_count(q_rr[0, t], q_s[0, t], np.ones(3), np.ones(3, np.float32))
+                         for t in range(len(E))])
+        hist.append(beta.copy())
+    return beta, hist
+
+
+def test_fixed_point_reaches_budget_unaware_optimum(orc):
+    """App. A.3: for budget-unaware weights the optimum is
+    beta_t* = sqrt(C_D V_t / (V_D C_t)) (the lambda-line argument with
+    lambda = sqrt(C_D / V_D)); the update of Eq. 2 converges to it, and is close
+    to optimal efficiency within about five steps (Fig. 1DConvergence)."""
+    E, V, C = [1.0, 1.0], [40.0, 12.0], [1.0, 30.0]
+    VD, CD = 1.0, 4.0
+    star = np.sqrt(CD * np.array(V) / (VD * np.array(C)))
+    assert np.all(star > 1)  # splitting regime, where the closed form holds
+    beta, hist = _fixed_point(orc, E, V, C, VD, CD, [1.0, 1.0], 300)
+    assert beta == pytest.approx(star, rel=1e-5)
+    ieff = lambda b: np.prod(_scalar_moments(b, E, V, C, VD, CD))
+    opt = ieff(star)
+    assert ieff(hist[5]) <= opt * 1.05
+
+
+def test_fixed_point_matches_grid_search_mixed_regime(orc):
+    """A case where one technique ends in Russian roulette and one splits:
+    an exhaustive grid over [0.05, 20]^2 of the proxy's inverse efficiency has its
+    minimum where the fixed point lands (to grid resolution)."""
+    E, V, C = [0.05, 2.0], [0.2, 30.0], [6.0, 1.0]
+    VD, CD = 0.5, 3.0
+    beta, _ = _fixed_point(orc, E, V, C, VD, CD, [1.0, 1.0], 200)
+    grid = np.exp(np.linspace(np.log(0.05), np.log(20.0), 400))
+    best, arg = np.inf, None
+    for b0 in grid:
+        for b1 in grid:
+            v = np.prod(_scalar_moments([b0, b1], E, V, C, VD, CD))
+            if v < best:
+                best, arg = v, (b0, b1)
+    step = grid[1] / grid[0]
+    assert beta[0] < 1 and beta[1] > 1
+    assert arg[0] / step <= beta[0] <= arg[0] * step
+    assert arg[1] / step <= beta[1] <= arg[1] * step
+
+
+def test_update_fallbacks(orc):
+    """Readings: cells with fewer than two samples or zero cost keep their
+    previous factors; V_I <= 1e-12 keeps everything."""
+    st = np.zeros((3, 3, 8))
+    st[0, 0] = [1, 1, 1, 1, 1, 1, 1, 1]                  # n < 2
+    st[1, 0] = [4, 4, 4, 4, 8, 8, 8, 0]                  # cost 0
+    st[2, 0] = [4, 4, 4, 4, 8, 8, 8, 8]                  # valid
+    q_rr = np.full((3, 3, 3), 7.0, np.float32)
+    q_s = np.full((3, 3, 3), 5.0, np.float32)
+    valid = np.zeros((3, 3), np.uint8)
+    a, b, v = orc.update_counts(st, 0.5, 2.0, 1, q_rr, q_s, valid)
+    assert np.all(a[:2] == 7.0) and np.all(v[:2] == 0)
+    # cell 2: m1 = 1, m2 = 2, var = 1, C_t = 2 -> q_rr = sqrt(2/2 * 2/0.5) = 2, q_s = sqrt(1/0.5)
+    assert a[2, 0] == pytest.approx([2.0] * 3) and b[2, 0] == pytest.approx([math.sqrt(2.0)] * 3)
+    assert v[2, 0] == 1 and v[2, 1] == 0
+    a, b, v = orc.update_counts(st, 1e-13, 2.0, 1, q_rr, q_s, valid)
+    assert np.all(a == 7.0) and np.all(v == 0)
+
+
+# ----------------------------------------------------------------------- BSDFs
+def _sphere_grid(n):
+    """Midpoint quadrature over the sphere (z, phi) -> directions, weights."""
+    z = -1 + 2 * (np.arange(n) + 0.5) / n
+    ph = 2 * np.pi * (np.arange(2 * n) + 0.5) / (2 * n)
+    Z, P = np.meshgrid(z, ph, indexing="ij")
+    s = np.sqrt(1 - Z ** 2)
+    d = np.stack([s * np.cos(P), s * np.sin(P), Z], -1).reshape(-1, 3)
+    w = (2.0 / n) * (2 * np.pi / (2 * n))
+    return d, w
+
+
+def _mat_scene(mat_rows):
+    sc = W.box_scene(2, 2)
+    sc.materials = np.asarray(mat_rows, np.float64).reshape(-1, 8)
+    return sc
+
+
+@pytest.mark.parametrize("mat", [[0, 0.8, 0.5, 0.2, 0, 0, 0, 0],
+                                 [1, 0.9, 0.6, 0.3, 0.3, 0, 0, 0],
+                                 [1, 1.0, 1.0, 1.0, 0.1, 0, 0, 0]])
+def test_bsdf_sampling_density_consistency(orc, mat):
+    """The sampling routine and the pdf agree: the probability that a sample is
+    valid equals the integral of the pdf over the upper hemisphere, and a
+    chi-square test over direction bins accepts the sample histogram.  Lambert
+    sampling is cosine-weighted (f cos / p = albedo)."""
+    sc = _mat_scene([mat])
+    th = 0.6
+    wo = np.array([math.sin(th), 0.0, math.cos(th)])
+    dirs, w = _sphere_grid(200)
+    pdf = np.array([orc.bsdf_eval_local(sc, 0, wo, d)[1] for d in dirs[dirs[:, 2] > 0]])
+    integral = pdf.sum() * w
+    n = 96
+    u = (np.arange(n) + 0.5) / n
+    ok = []
+    samples = []
+    for a in u:
+        for b in u:
+            good, wi, p = orc.bsdf_sample_local(sc, 0, wo, a, b)
+            ok.append(good)
+            if good:
+                samples.append(wi)
+                f, p2 = orc.bsdf_eval_local(sc, 0, wo, wi)
+                assert p == pytest.approx(p2, rel=1e-9)
+                if mat[0] == 0:
+                    assert f / p == pytest.approx(mat[1:4], rel=1e-9)
+    assert integral == pytest.approx(np.mean(ok), abs=4e-3)
+    # chi-square over 8 x 8 (cos theta, phi) bins of the upper hemisphere
+    s = np.array(samples)
+    zb = np.minimum((s[:, 2] * 8).astype(int), 7)
+    pb = np.minimum(((np.arctan2(s[:, 1], s[:, 0]) % (2 * np.pi)) / (2 * np.pi) * 8).astype(int), 7)
+    counts = np.bincount(zb * 8 + pb, minlength=64)
+    up = dirs[:, 2] > 0
+    du = dirs[up]
+    zb2 = np.minimum((du[:, 2] * 8).astype(int), 7)
+    pb2 = np.minimum(((np.arctan2(du[:, 1], du[:, 0]) % (2 * np.pi)) / (2 * np.pi) * 8).astype(int), 7)
+    exp_p = np.bincount(zb2 * 8 + pb2, weights=pdf * w, minlength=64)
+    expected = exp_p * n * n
+    m = expected > 5
+    chi2 = ((counts[m] - expected[m]) ** 2 / expected[m]).sum()
+    dof = m.sum() - 1
+    assert chi2 < dof + 6 * math.sqrt(2 * dof)
+
+
+def test_ggx_reciprocity_and_energy(orc):
+    """f(wo, wi) = f(wi, wo); with F0 = 1 the directional albedo is at most 1
+    and approaches 1 for a smooth surface at normal incidence (single
+    scattering with height-correlated masking)."""
+    sc = _mat_scene([[1, 1.0, 1.0, 1.0, 0.2, 0, 0, 0], [1, 1.0, 1.0, 1.0, 0.02, 0, 0, 0]])
+    rng = np.random.default_rng(5)
+    for _ in range(50):
+        a = rng.normal(size=3); a[2] = abs(a[2]); a /= np.linalg.norm(a)
+        b = rng.normal(size=3); b[2] = abs(b[2]); b /= np.linalg.norm(b)
+        fa, _ = orc.bsdf_eval_local(sc, 0, a, b)
+        fb, _ = orc.bsdf_eval_local(sc, 0, b, a)
+        assert fa[0] / b[2] == pytest.approx(fb[0] / a[2], rel=1e-9)
+    for mat, lo in ((0, 0.9), (1, 0.995)):
+        wo = np.array([0.0, 0.0, 1.0])
+        n = 128
+        acc = 0.0
+        for x in (np.arange(n) + 0.5) / n:
+            for y in (np.arange(n) + 0.5) / n:
+                good, wi, p = orc.bsdf_sample_local(sc, mat, wo, x, y)
+                if good:
+                    f, _ = orc.bsdf_eval_local(sc, mat, wo, wi)
+                    acc += f[0] / p
+        alb = acc / (n * n)
+        assert lo <= alb <= 1.0 + 1e-3
+
+
+def test_guide_pdf_and_sampling(orc):
+    """The guide's pdf integrates to one over the sphere and samples land in bin
+    b with probability P_b (the CDF difference)."""
+    cdf = W.random_guide_cdf(1, seed=9)[0]
+    dirs, w = _sphere_grid(256)
+    integral = sum(orc.guide_pdf(cdf, d) for d in dirs) * w
+    assert integral == pytest.approx(1.0, abs=2e-3)
+    P = np.diff(np.concatenate([[0.0], cdf.astype(np.float64)]))
+    n = 4096
+    counts = np.zeros(256)
+    for k in range(n):
+        wv, p = orc.guide_sample(cdf, (k + 0.5) / n, 0.37, 0.61)
+        z = wv[2]
+        ph = math.atan2(wv[1], wv[0]) % (2 * math.pi)
+        b = min(int((z + 1) * 8), 15) * 16 + min(int(ph / (2 * math.pi) * 16), 15)
+        counts[b] += 1
+        assert p == pytest.approx(P[b] * 256 / (4 * math.pi), rel=1e-6)
+    assert np.abs(counts / n - P).max() < 2.0 / n + 1e-6
+
+
+def test_guide_update(orc):
+    h = np.zeros((2, 256))
+    h[1, 17] = 5.0
+    cdf = orc.guide_update(h)
+    P = np.diff(np.concatenate([np.zeros((2, 1)), cdf.astype(np.float64)], axis=1), axis=1)
+    assert P[0] == pytest.approx(np.full(256, 1 / 256), abs=1e-6)
+    assert P[1, 17] == pytest.approx(0.9 + 0.1 / 256, abs=1e-6)
+    assert P[1, 3] == pytest.approx(0.1 / 256, abs=1e-6)
+    assert cdf[:, -1].tolist() == [1.0, 1.0]
+
+
+# ----------------------------------------------------------------- image stats
+def test_image_stats_small_case(orc):
+    """3 x 2 image worked by hand: box filter over in-image neighbours, V_I as the
+    mean squared relative deviation with the sample clamped at 50 x estimate."""
+    img = np.array([[1, 1, 1], [2, 2, 2], [3, 3, 3], [4, 4, 4], [5, 5, 5], [600, 600, 600]], float)
+    vi, rs, est = orc.image_stats(3, 2, img, np.zeros_like(img), 0)
+    # pixel (0,0): neighbours (0,0),(1,0),(0,1),(1,1) -> (1 + 2 + 4 + 5) / 4 = 3
+    assert est[0, 0] == pytest.approx(3.0)
+    # pixel (1,0): all six pixels -> 615 / 6
+    assert est[1, 0] == pytest.approx(615 / 6)
+    # pixel (2,1): (2,3,5,600)/4
+    assert est[5, 0] == pytest.approx(610 / 4)
+    manual = 0.0
+    for p in range(6):
+        e = est[p, 0]
+        i = min(img[p, 0], 50 * e)
+        manual += ((i - e) / e) ** 2
+    assert vi == pytest.approx(manual / 6)
+    # a constant image is its own estimate: zero variance
+    c = np.full((12, 3), 0.7)
+    vi2, _, est2 = orc.image_stats(4, 3, c, np.zeros_like(c), 0)
+    assert vi2 == pytest.approx(0.0, abs=1e-20) and est2 == pytest.approx(0.7)
+    # running mean over iterations and the floor at 1e-3 x channel mean
+    z = np.zeros((4, 3)); z[0] = 8.0
+    vi3, rs3, est3 = orc.image_stats(4, 1, z, np.full((4, 3), 8.0), 1)
+    assert rs3[0, 0] == 16.0 and rs3[3, 0] == 8.0
+    assert est3[3, 0] == pytest.approx(4.0)   # mean of (4, 4) from pixels 2 and 3
+
+
+# --------------------------------------------------------- whole-render pins
+def _mean_and_sem(vals):
+    v = np.asarray(vals)
+    return v.mean(), v.std(ddof=1) / math.sqrt(len(v))
+
+
+@pytest.mark.parametrize("albedo,D", [(0.5, 3), (0.8, 4)])
+@pytest.mark.parametrize("counts", ["beta1", "random"])
+def test_furnace_closed_form(orc, albedo, D, counts):
+    """Closed furnace: every pixel's expectation is Le (1 - a^D) / (1 - a),
+    independent of the count field (Sec. 3 'Continuous sample counts': dividing
+    by the real-valued beta keeps the estimator unbiased)."""
+    sc = W.furnace_scene(albedo=albedo, radiance=1.5, width=12, height=12)
+    cells = 4 ** 3
+    q_rr, q_s, valid = W.random_count_fields(cells, seed=11, lo=0.1, hi=3.0)
+    est = W.random_pixel_estimate(sc.n_pixels, seed=12, lo=0.5, hi=4.0)
+    vals = []
+    for it in range(60):
+        kw = dict(grid_n=4, techniques=W.TECH_BSDF | W.TECH_NEE, max_depth=D, iteration=it)
+        if counts == "random":
+            kw.update(mode=orc.MODE_MARS, q_rr=q_rr, q_s=q_s, valid=valid, est=est)
+        vals.append(orc.render(sc, **kw).image.mean())
+    m, se = _mean_and_sem(vals)
+    expected = 1.5 * (1 - albedo ** D) / (1 - albedo)
+    assert abs(m - expected) < 3.5 * se + 1e-9
+
+
+@pytest.mark.parametrize("weights", [0, 1])
+@pytest.mark.parametrize("counts", ["beta1", "random"])
+def test_polygon_light_irradiance_closed_form(orc, weights, counts):
+    """Floor under a square Lambertian emitter, two segments: the pixel value
+    is albedo / pi x irradiance, and the irradiance of a rectangle seen from a
+    point on its axis is the classical corner form factor sum (Lambert).  This
+    pins the NEE density (light pmf, area and cosine Jacobian), the BSDF density
+    and their multi-sample MIS combination."""
+    sc = W.area_light_plane_scene(width=6, height=6, albedo=0.5, radiance=2.0)
+    eps = 1e-4 * 2.0        # ray offset = 1e-4 x largest scene extent (the floor is 2 wide)
+    c = 1.0 - eps
+    X = 0.5 / c
+
+    def corner(x, y):
+        return (x / math.sqrt(1 + x * x) * math.atan(y / math.sqrt(1 + x * x))
+                + y / math.sqrt(1 + y * y) * math.atan(x / math.sqrt(1 + y * y))) / (2 * math.pi)
+
+    expected = 0.5 / math.pi * (math.pi * 2.0 * 4 * corner(X, X))
+    q_rr, q_s, valid = W.random_count_fields(8, seed=21, lo=0.2, hi=6.0, p_valid=1.0)
+    est = np.full((sc.n_pixels, 3), 0.25, np.float32)
+    vals = []
+    for it in range(150):
+        kw = dict(grid_n=2, techniques=W.TECH_BSDF | W.TECH_NEE, max_depth=2, iteration=it, weights=weights)
+        if counts == "random":
+            kw.update(mode=orc.MODE_MARS, q_rr=q_rr, q_s=q_s, valid=valid, est=est)
+        vals.append(orc.render(sc, **kw).image.mean())
+    m, se = _mean_and_sem(vals)
+    assert abs(m - expected) < 3.5 * se
+
+
+def test_unbiased_under_random_counts_box(orc):
+    """Box scene: the image mean under a random count field equals the image
+    mean with beta = 1 within the combined 3.5 sigma (App. A.1 'Unbiasedness')."""
+    cfg = W.config_box(16, 16)
+    cells = cfg.n_cells
+    q_rr, q_s, valid = W.random_count_fields(cells, seed=31, lo=0.05, hi=3.0)
+    est = W.random_pixel_estimate(cfg.scene.n_pixels, seed=32, lo=0.05, hi=1.0)
+    a, b = [], []
+    for it in range(150):
+        kw = dict(grid_n=cfg.grid_n, techniques=cfg.techniques, max_depth=cfg.max_depth, iteration=it)
+        a.append(orc.render(cfg.scene, **kw).image.mean(0))
+        b.append(orc.render(cfg.scene, mode=orc.MODE_MARS, q_rr=q_rr, q_s=q_s, valid=valid, est=est,
+                            seed=7, **kw).image.mean(0))
+    a, b = np.array(a), np.array(b)
+    for ch in range(3):
+        ma, sa = _mean_and_sem(a[:, ch])
+        mb, sb = _mean_and_sem(b[:, ch])
+        assert abs(ma - mb) < 3.5 * math.hypot(sa, sb)
+
+
+def test_guided_technique_unbiased(orc):
+    """Three techniques (BSDF, NEE, guided) on a small crop of the guided room:
+    with a random guide distribution and random counts the image mean matches
+    BSDF+NEE alone (the guided technique only redistributes samples)."""
+    sc = W.guided_room_scene(seed=0, width=8, height=8, n_spheres=16)
+    cells = 4 ** 3
+    cdf = W.random_guide_cdf(cells, seed=41, sparsity=0.5)
+    q_rr, q_s, valid = W.random_count_fields(cells, seed=42, lo=0.1, hi=2.0)
+    est = W.random_pixel_estimate(sc.n_pixels, seed=43, lo=0.2, hi=2.0)
+    a, b = [], []
+    for it in range(120):
+        kw = dict(grid_n=4, max_depth=4, iteration=it)
+        a.append(orc.render(sc, techniques=3, **kw).image.mean())
+        b.append(orc.render(sc, techniques=7, mode=orc.MODE_MARS, q_rr=q_rr, q_s=q_s, valid=valid, est=est,
+                            guide_cdf=cdf, seed=5, **kw).image.mean())
+    ma, sa = _mean_and_sem(a)
+    mb, sb = _mean_and_sem(b)
+    assert abs(ma - mb) < 3.5 * math.hypot(sa, sb)
+
+
+def test_statistics_bookkeeping(orc):
+    """With beta = 1 every estimator vertex draws one sample per technique, so
+    n per technique equals the number of estimator vertices; rays (the cost
+    unit) are the camera rays plus every drawn sample; a technique's summed
+    cost is at least its sample count."""
+    cfg = W.config_box(16, 16)
+    r = orc.render(cfg.scene, grid_n=cfg.grid_n, techniques=cfg.techniques, max_depth=cfg.max_depth)
+    nv = r.counters[2]
+    n = r.stats[:, :, 0].sum(0)
+    assert n[0] == nv and n[1] == nv and n[2] == 0
+    assert r.rays == cfg.scene.n_pixels + n.sum()
+    assert np.all(r.stats[:, 1, 7] == r.stats[:, 1, 0])      # NEE: one ray per sample
+    assert np.all(r.stats[:, 0, 7] >= r.stats[:, 0, 0])
+    # estimator vertices never exceed the traced vertices
+    assert r.counters[2] <= r.counters[1]
