@@ -601,12 +601,18 @@ static void secondary_estimator(rnd_t* R, const vtx_t* x, int depth, uint64_t li
   *cost = 0.0;
   st->counters[2] += 1.0;
 
-  /* budgets beta_t(x) */
+  /* budgets beta_t(x).  Without learned counts (warm-up, fixed-count mode,
+   * cells without statistics) every vertex draws one NEE sample and one
+   * continuation sample split evenly over the continuation techniques (BSDF,
+   * guided): Sec. 4.1 "Fixed-point iteration" warms up without splitting; with
+   * two continuation techniques beta = 1 each would double every path at every
+   * bounce.  Alg. 1 turns beta = (1/2, 1/2) into exactly one continuation. */
   float betaf[ORC_NT] = {0, 0, 0};
   double beta[ORC_NT] = {0, 0, 0};
+  const double base_cont = 1.0 / (double)(R->on[ORC_T_BSDF] + R->on[ORC_T_GUIDED]);
   for (int t = 0; t < ORC_NT; ++t) {
     if (!R->on[t]) continue;
-    double b = 1.0;
+    double b = t == ORC_T_NEE ? 1.0 : base_cont;
     if (P->mode == ORC_MODE_MARS && st->valid[x->cell * ORC_NT + t]) {
       size_t o = ((size_t)x->cell * ORC_NT + t) * 3;
       b = orc_vertex_count(st->q_rr + o, st->q_s + o, T, st->est + 3 * R->px, P->clamp_lo, P->clamp_hi);
