@@ -1,0 +1,397 @@
+"""Benchmark of the MARS path tracer on one GB300 (or N replicas).
+
+Workload: the guided-room scene at 512 x 512 (64 seeded spheres, 70 % GGX,
+four small ceiling lights), max depth 10, techniques BSDF + NEE + guided,
+32^3 statistics grid.  A step is one fixed-point iteration: one sample per
+pixel rendered with the MARS counts, the image statistics, and the count /
+guide update.  The first W steps are the warm-up iterations (beta = 1).
+
+Printed (one JSON line, rank 0):
+  value      path vertices per second (closest-hit queries) over the K timed
+             steps, device time from CUDA events on the rendering stream
+  e2e        the same metric through the C ABI with the image returned to pinned
+             host memory every step (host copies inside the timed region)
+  roofline   the dominant kernel's algorithmic bytes per launch / its average
+             launch time, against the measured HBM copy bandwidth
+  efficiency equal-time efficiency 1 / (relMSE x seconds) of MARS (counts frozen
+             after the timed steps) and of fixed-count MIS (beta = 1) on the
+             same GPU, against a long fixed-count reference render
+  cpu_baseline  the CPU oracle on a bounded pixel sample of the same workload
+
+--impl reference runs the CPU oracle instead (the only reference arm: the paper
+ships no GPU code) on a bounded sample per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import mars_workloads as W  # noqa: E402
+
+METRIC = "efficiency 1/(relMSE·s) MARS vs fixed-count MIS; Mvertices/s; p50/p99 latency"
+UNIT = "Mvertices/s"
+
+# algorithmic bytes of the arena records (see the layout in csrc/internal.h)
+RAY_BYTES = 80          # five float4 per ray
+VERT_BASE_BYTES = 32    # V0, V1 for every slot
+VERT_EST_BYTES = 64     # V2..V5 for a vertex that runs the estimator
+VERT_GUIDE_BYTES = 16   # V6 for a traced ray when the guided technique learns
+SAMPLE_BYTES = 16       # S: one float4 per slot
+EST_READ_BYTES = 16     # pixel estimate read per estimator vertex
+
+
+def workload(args):
+    cfg = W.config_guided(args.width, args.height, seed=0)
+    return cfg
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    def __init__(self, gpu_index: int, out_path: str):
+        self.proc = None
+        self.path = out_path
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(out_path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[5 + k].lower() in ("active", "1", "yes"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def rel_mse(img, ref):
+    """relMSE: mean over pixels and channels of (I - R)^2 / (R^2 + 1e-2), after
+    dropping the 0.01 % largest per-pixel terms."""
+    t = ((img - ref) ** 2 / (ref ** 2 + 1e-2)).reshape(-1, 3).mean(axis=1)
+    k = int(math.ceil(1e-4 * t.size))
+    if k > 0:
+        t = np.sort(t)[:-k]
+    return float(t.mean())
+
+
+def run_mars(args):
+    import torch
+    import paper_2410_20429_gb300 as M
+    from paper_2410_20429_gb300 import build as B
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0 or world == 1:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    B.build()
+    cfg = workload(args)
+    sc = cfg.scene
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        scene = M.Scene(sc, stream=stream)
+        cache = M.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, stream=stream)
+    npx = sc.n_pixels
+    img = torch.zeros(npx * 3, dtype=torch.float32, device="cuda")
+    seed = 1000 + rank  # weak-scaling replicas: every rank renders its own job
+    it = 0
+
+    def step(i, mode, profile=False, image=img, collect=True):
+        st = cache.render_iteration(image, seed=seed, iteration=i, mode=mode, collect=collect,
+                                    update_estimate=True, profile=profile, stream=stream)
+        cache.update_counts(stream=stream)
+        return st
+
+    for _ in range(args.warmup):
+        step(it, M.MARS_MODE_WARMUP)
+        it += 1
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local, os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
+                          if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/mars_clocks_{rank}.csv")
+    time.sleep(0.3)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    sts = []
+    torch.cuda.synchronize()
+    evs[0].record(stream)
+    for k in range(args.steps):
+        sts.append(step(it, M.MARS_MODE_MARS, profile=True))
+        it += 1
+        evs[k + 1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    per_step = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
+    total_ms = sum(per_step)
+    verts = sum(s["vertices"] for s in sts)
+    t_max = total_ms
+    verts_all = verts
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        v = torch.tensor([float(verts)], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(v)
+        t_max, verts_all = float(t.item()), float(v.item())
+    value = verts_all / (t_max * 1e-3) / 1e6
+
+    # ---- dominant kernel roofline (live CUDA-event stage times)
+    shade_ms = sum(s["shade_ms"] for s in sts)
+    rev_ms = sum(s["reverse_ms"] for s in sts)
+    shade_l = sum(s["shade_launches"] for s in sts)
+    entries = sum(s["wave_entries"] for s in sts)
+    est_v = sum(s["estimator_vertices"] for s in sts)
+    traced = verts
+    pixels_total = npx * args.steps
+    children = entries - pixels_total
+    guided = bool(cfg.techniques & W.TECH_GUIDED)
+    shade_bytes = (RAY_BYTES * children * 2 + VERT_BASE_BYTES * entries + (VERT_EST_BYTES + EST_READ_BYTES) * est_v
+                   + (VERT_GUIDE_BYTES * (traced - pixels_total) if guided else 0))
+    rev_bytes = (VERT_BASE_BYTES * entries + VERT_EST_BYTES * est_v + SAMPLE_BYTES * (entries + children)
+                 + (VERT_GUIDE_BYTES * (traced - pixels_total) if guided else 0))
+    hbm, peak_kind = peaks()
+    dom = "k_shade" if shade_ms >= rev_ms else "k_reverse"
+    dom_ms, dom_bytes = (shade_ms, shade_bytes) if dom == "k_shade" else (rev_ms, rev_bytes)
+    per_launch_ms = dom_ms / max(shade_l, 1)
+    achieved = dom_bytes / max(shade_l, 1) / (per_launch_ms * 1e-3) / 1e9
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved / hbm, 4), "traffic": None, "peak_kind": peak_kind,
+                "bytes_per_launch": int(dom_bytes / max(shade_l, 1)), "launch_ms": round(per_launch_ms, 4),
+                "stage_ms_per_step": {"shade": round(shade_ms / args.steps, 4),
+                                      "reverse": round(rev_ms / args.steps, 4),
+                                      "image": round(sum(s["image_ms"] for s in sts) / args.steps, 4)}}
+
+    # ---- end to end through the C ABI with a pinned host image every step
+    host_img = torch.empty(npx * 3, dtype=torch.float32, pin_memory=True).numpy()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_verts = 0
+    for k in range(args.steps):
+        st = cache.render_iteration(host_img, seed=seed, iteration=it, mode=M.MARS_MODE_MARS, update_estimate=True,
+                                    stream=stream)
+        cache.update_counts(stream=stream)
+        e2e_verts += st["vertices"]
+        it += 1
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": round(e2e_verts / e2e_s / 1e6, 3), "unit": UNIT, "h2d_bytes_per_step": 48,
+           "d2h_bytes_per_step": npx * 3 * 4 + 512}
+
+    launches = sum(s["launches"] for s in sts) + args.steps * (2 if guided else 1)
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": cfg.name, "pixels": npx, "max_depth": cfg.max_depth, "grid": cfg.grid_n,
+                   "techniques": "bsdf+nee+guided", "statistics_dtype": "f64",
+                   "l2": "working set > L2: queue arena %.0f MB per step" % (
+                       entries / args.steps * (RAY_BYTES + 7 * 16 + SAMPLE_BYTES) / 1e6),
+                   "parallelism": f"replicas x{world}"},
+        "latency_ms": {"p50": round(float(np.percentile(per_step, 50)), 4),
+                       "p99": round(float(np.percentile(per_step, 99)), 4)},
+        "per_step": {"vertices": verts / args.steps, "rays": sum(s["rays"] for s in sts) / args.steps,
+                     "mean_beta": [round(sum(s["mean_beta"][t] for s in sts) / args.steps, 4) for t in range(3)],
+                     "tiles": sum(s["tiles"] for s in sts) / args.steps},
+        "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+    }
+
+    if rank == 0 and not args.no_efficiency:
+        line["efficiency"] = efficiency(args, M, cfg, scene, cache, seed, it, stream)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cfg, args.cpu_seconds)
+    if world > 1:
+        dist.barrier()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def efficiency(args, M, cfg, scene, cache, seed, it0, stream):
+    """Equal-time efficiency 1/(relMSE * s): MARS with the counts learned so far
+    (frozen: no statistics, no update) vs fixed-count MIS (beta = 1), both
+    timed with CUDA events, against a long fixed-count reference."""
+    import torch
+    npx = cfg.scene.n_pixels
+    img = torch.zeros(npx * 3, dtype=torch.float32, device="cuda")
+    ref_cache = M.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, stream=stream)
+    acc = torch.zeros(npx * 3, dtype=torch.float64, device="cuda")
+    for k in range(args.ref_spp):
+        ref_cache.render_iteration(img, seed=777, iteration=k, mode=M.MARS_MODE_FIXED, collect=False,
+                                   update_estimate=False, stream=stream)
+        acc += img.double()
+    ref = (acc / args.ref_spp).cpu().numpy().reshape(-1, 3)
+    del ref_cache
+
+    def timed(c, mode, n, it_base):
+        a = torch.zeros(npx * 3, dtype=torch.float64, device="cuda")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        rays = 0
+        for k in range(n):
+            st = c.render_iteration(img, seed=seed + 17, iteration=it_base + k, mode=mode, collect=False,
+                                    update_estimate=False, stream=stream)
+            rays += st["rays"]
+            a += img.double()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        s = e0.elapsed_time(e1) * 1e-3
+        mean = (a / n).cpu().numpy().reshape(-1, 3)
+        r = rel_mse(mean, ref)
+        return {"relmse": r, "seconds": s, "efficiency": 1.0 / (r * s), "rays_per_pixel": rays / n / npx,
+                "spp": n}
+
+    mars = timed(cache, M.MARS_MODE_MARS, args.eff_spp, 20000)
+    fixed_cache = M.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, stream=stream)
+    fixed = timed(fixed_cache, M.MARS_MODE_FIXED, args.eff_spp, 20000)
+    return {"mars": mars, "fixed_count_mis": fixed, "ratio": mars["efficiency"] / fixed["efficiency"],
+            "reference_spp": args.ref_spp,
+            "protocol": "counts learned over warm-up + timed steps, then frozen; both estimators render "
+                        f"{args.eff_spp} fresh iterations; reference = fixed-count MIS, {args.ref_spp} spp, "
+                        "other random numbers"}
+
+
+def cpu_baseline(cfg, seconds, reference_arm=False):
+    """The CPU oracle (single thread, as it stands) on a bounded pixel sample of
+    the same workload: warm-up mode (beta = 1), pixels evenly strided over the
+    image, sized to roughly `seconds` of work."""
+    import oracle
+    sc = cfg.scene
+    oracle.build()
+
+    def run(npx_sample, it):
+        stride = max(1, sc.n_pixels // npx_sample)
+        t = 0.0
+        verts = 0.0
+        # render contiguous chunks at strided offsets to cover the image
+        chunk = 64
+        starts = list(range(0, sc.n_pixels, stride * chunk))[: max(1, npx_sample // chunk)]
+        for s0 in starts:
+            t0 = time.perf_counter()
+            r = oracle.render(sc, grid_n=cfg.grid_n, techniques=cfg.techniques, max_depth=cfg.max_depth,
+                              iteration=it, seed=3, px_begin=s0, px_end=min(sc.n_pixels, s0 + chunk))
+            t += time.perf_counter() - t0
+            verts += r.vertices
+        return verts, t, len(starts) * chunk
+
+    v, t, n = run(512, 0)
+    rate = v / max(t, 1e-9)
+    target = max(512, int(512 * seconds / max(t, 1e-3)))
+    v, t, n = run(min(target, sc.n_pixels), 1)
+    return {"value": round(v / t / 1e6, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} pixels of the {sc.width}x{sc.height} workload (64-pixel rows evenly spread), "
+                      f"one warm-up iteration (beta = 1), {int(v)} path vertices in {t:.1f} s"}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle as it stands on the host cores, rank 0 only."""
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    cfg = workload(args)
+    sc = cfg.scene
+    per_step = max(64, args.ref_pixels_per_step)
+    times, verts = [], []
+    for k in range(args.warmup + args.steps):
+        b = (k * 7919 * 64) % max(1, sc.n_pixels - per_step)
+        t0 = time.perf_counter()
+        r = oracle.render(sc, grid_n=cfg.grid_n, techniques=cfg.techniques, max_depth=cfg.max_depth, iteration=k,
+                          seed=3, px_begin=b, px_end=b + per_step)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+            verts.append(r.vertices)
+    value = sum(verts) / sum(times) / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * sum(times) / len(times), 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": cfg.name, "pixels": sc.n_pixels, "max_depth": cfg.max_depth,
+                       "grid": cfg.grid_n, "techniques": "bsdf+nee+guided"},
+            "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{per_step} contiguous pixels per step of the {sc.width}x{sc.height} "
+                                       "workload, warm-up mode (beta = 1)"},
+            "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=13)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mars", choices=["mars", "reference"])
+    ap.add_argument("--width", type=int, default=512)
+    ap.add_argument("--height", type=int, default=512)
+    ap.add_argument("--no-efficiency", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--ref-spp", type=int, default=256)
+    ap.add_argument("--eff-spp", type=int, default=32)
+    ap.add_argument("--ref-pixels-per-step", type=int, default=1024)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "mars":
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_mars(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,272 @@
+/*
+ * mars.h -- C ABI of the GB300 MARS path tracer.
+ *
+ * MARS (Meyer, Rath, Yazici, Slusallek, "MARS: Multi-sample Allocation through
+ * Russian roulette and Splitting", SIGGRAPH Asia 2024) renders an image by
+ * iterating a fixed-point scheme: every iteration traces paths in which each
+ * vertex draws a real-valued number of samples beta_t per technique t (BSDF
+ * sampling, next-event estimation, guided sampling), rounds them with
+ * low-discrepancy stochastic rounding (Alg. 1), combines the samples with the
+ * multi-sample balance heuristic (Sec. 3.1, "Secondary estimator") and records
+ * per-cell moment and cost estimates (Sec. 4.1, "Local estimates").  The update
+ * step turns those estimates, the image variance V_I and the image cost C_I
+ * into the next iteration's counts (Eq. "optimalBeta" in the spatial form of
+ * Sec. 3.1, "Optimization").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - All calls return a mars_status.  Nothing is thrown across the ABI.  The
+ *   message of the last failure on the calling thread is available through
+ *   mars_last_error_string().
+ * - "stream" is a cudaStream_t passed as void* (NULL = legacy default stream).
+ * - Descriptors and host arrays are owned by the caller and copied during the
+ *   call.  Objects (mars_scene, mars_cache, mars_server) are owned by the
+ *   library until the matching *_destroy.
+ * - Objects live on the CUDA device that was current when they were created;
+ *   every call switches to that device for its duration.
+ * - After MARS_ERR_CUDA an object is poisoned: every later call on it fails
+ *   with MARS_ERR_CUDA and only *_destroy is meaningful.
+ * - The library never falls back to the CPU.
+ */
+#ifndef MARS_H
+#define MARS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MARS_OK = 0,
+  MARS_ERR_INVALID_ARG = 1, /* a pointer, size or enum is out of range */
+  MARS_ERR_OOM = 2,         /* device memory, or a single pixel's path tree exceeds the queue arena */
+  MARS_ERR_CUDA = 3,        /* a CUDA runtime call failed; the object is poisoned */
+  MARS_ERR_TIMEOUT = 4,     /* a bounded wait ran out */
+  MARS_ERR_BUSY = 5,        /* the server has no free slot for the request right now */
+  MARS_ERR_NOT_FOUND = 6    /* unknown job id */
+} mars_status;
+
+typedef struct mars_scene mars_scene;
+typedef struct mars_cache mars_cache;
+typedef struct mars_server mars_server;
+
+/* technique bits and slots; slots are the order Alg. 1 rounds in */
+#define MARS_TECH_BSDF 1
+#define MARS_TECH_NEE 2
+#define MARS_TECH_GUIDED 4
+#define MARS_SLOT_BSDF 0
+#define MARS_SLOT_NEE 1
+#define MARS_SLOT_GUIDED 2
+#define MARS_NUM_SLOTS 3
+#define MARS_NUM_STATS 8      /* n, sum v (rgb), sum v^2 (rgb), sum cost */
+#define MARS_GUIDE_BINS 256   /* 16 (cos theta) x 16 (phi) equal-area bins */
+#define MARS_MAX_DEPTH 16
+
+typedef enum { MARS_MODE_WARMUP = 0, MARS_MODE_MARS = 1, MARS_MODE_FIXED = 2 } mars_mode;
+typedef enum { MARS_WEIGHTS_AWARE = 0, MARS_WEIGHTS_UNAWARE = 1 } mars_weights;
+
+/* Scene description (host memory, copied by mars_scene_create).
+ * quads [n_quads][9]: corner p0, edge e1, edge e2; a quad whose material emits
+ *   is an area light, emitting on the side of normalize(e1 x e2).
+ * spheres [n_spheres][4]: centre, radius.   tris [n_tris][9]: v0, v1, v2.
+ * *_mat: material index per primitive.  Only quads may use emitting materials.
+ * materials [n_materials][8]: type (0 Lambert, 1 GGX), colour rgb (Lambertian
+ *   albedo, or GGX Fresnel F0), GGX roughness alpha, emitted radiance rgb.
+ * camera: pinhole origin, look-at point, up vector, vertical FOV in degrees;
+ *   width x height pixels, one box-filtered sample per pixel per iteration. */
+typedef struct {
+  int32_t n_quads, n_spheres, n_tris, n_materials;
+  const double* quads;
+  const int32_t* quad_mat;
+  const double* spheres;
+  const int32_t* sphere_mat;
+  const double* tris;
+  const int32_t* tri_mat;
+  const double* materials;
+  double camera[10];
+  int32_t width, height;
+} mars_scene_desc;
+
+/* Statistics cache and iteration state of one render job.
+ * grid_n: uniform N^3 grid over the scene bounds (Sec. 4.1 stores the local
+ *   estimates in a spatial data structure; a uniform grid stands in for it).
+ * techniques: MARS_TECH_* bits; BSDF is required.
+ * max_depth: maximum number of path segments D (1..MARS_MAX_DEPTH); vertices
+ *   x_1..x_{D-1} run the secondary estimator.
+ * arena_capacity: rays held by the per-iteration queue arena summed over all
+ *   depths (0 = 8 x pixels x max_depth, at least 2^20).  An iteration whose path
+ *   trees do not fit is rendered in pixel tiles (results do not depend on it). */
+typedef struct {
+  int32_t grid_n;
+  int32_t techniques;
+  int32_t max_depth;
+  int32_t reserved;
+  uint64_t arena_capacity;
+} mars_cache_desc;
+
+/* Per-iteration parameters.
+ * seed, job: Philox key.  iteration: fixed-point iteration index (< 65536);
+ *   it keys the random numbers, so re-rendering an iteration reproduces it.
+ * mode: WARMUP and FIXED draw one sample per technique (beta = 1); MARS reads
+ *   the counts from the cache (Sec. 3.1 "Optimization").
+ * weights: budget-aware (default) or budget-unaware balance heuristic.
+ * clamp_lo/hi: count clamp (0.05, 20 in Sec. 4.1); clamp_hi <= 30.
+ * outlier: multiple of the pixel estimate that bounds a sample's contribution
+ *   to the variance estimates (50 in Sec. 4.1), not to the image.
+ * collect: accumulate local statistics and guide deposits.
+ * image_on_host: image_rgb is host memory (the call copies the image back).
+ * update_estimate: after rendering, add the image to the running mean and
+ *   recompute the pixel estimate, V_I and C_I (needed before mars_update_counts).
+ * profile: time every kernel launch with CUDA events on `stream`; the device
+ *   time per stage is returned in mars_iter_stats. */
+typedef struct {
+  uint32_t seed, job, iteration;
+  int32_t mode;
+  int32_t weights;
+  float clamp_lo, clamp_hi, outlier;
+  int32_t collect;
+  int32_t image_on_host;
+  int32_t update_estimate;
+  int32_t profile;         /* record CUDA events around every kernel (stage times in mars_iter_stats) */
+} mars_iter_params;
+
+/* What one iteration did (host memory, filled by mars_render_iteration). */
+typedef struct {
+  double VI;                  /* image relative variance (Sec. 4.1, "Image estimates") */
+  double CI;                  /* rays per pixel (cost units, Sec. 4.1) */
+  uint64_t rays;              /* camera rays + every drawn technique sample */
+  uint64_t vertices;          /* closest-hit queries (camera and extension rays traced) */
+  uint64_t estimator_vertices;/* vertices that ran the secondary estimator */
+  double mean_beta[3];        /* mean beta per technique slot over estimator vertices */
+  uint32_t tiles;             /* pixel tiles used (1 unless the arena overflowed) */
+  uint32_t retries;           /* tiles re-rendered after an overflow */
+  uint64_t arena_demand;      /* rays the largest tile needed */
+  uint32_t launches;          /* kernels this call launched */
+  uint32_t shade_launches;    /* of which wavefront shade kernels */
+  double shade_ms, reverse_ms, image_ms;  /* device time per stage (profile = 1) */
+  uint64_t wave_entries;      /* rays held in the depth waves (traced or not), all tiles */
+} mars_iter_stats;
+
+/* Host copy of a cache's state (checkpoint / teacher forcing).  Any pointer
+ * may be NULL to skip that field.  Layouts:
+ * q_rr, q_s [cells][3][3]: count factors per (cell, technique slot, channel):
+ *   q = sqrt(C_I / C_t * M_t / V_I) with M_t the second moment (RR) or the
+ *   variance (S) of the technique's samples in the cell.
+ * valid [cells][3]: 0 -> the vertex uses beta = 1 for that technique.
+ * stats [cells][3][8]: n, sum v (rgb), sum v^2 (rgb), sum cost (float64).
+ * guide_hist [cells][256]: accumulated guide deposits.
+ * guide_cdf [cells][256]: inclusive CDF of the guided technique per cell.
+ * pixel_estimate [pixels][3], run_sum [pixels][3]: float32. */
+typedef struct {
+  float* q_rr;
+  float* q_s;
+  uint8_t* valid;
+  double* stats;
+  float* guide_hist;
+  float* guide_cdf;
+  float* pixel_estimate;
+  float* run_sum;
+  int32_t n_iterations;   /* iterations summed in run_sum */
+  int32_t has_estimate;   /* pixel_estimate is meaningful */
+  double VI, CI;          /* inputs of the next mars_update_counts */
+} mars_cache_state;
+
+typedef struct {
+  int64_t n_cells, n_pixels;
+  int32_t grid_n, techniques, max_depth, n_prims;
+  uint64_t arena_capacity;
+  uint64_t device_bytes;
+  int32_t device;
+  int32_t n_lights;
+} mars_cache_info;
+
+/* ---- scene ------------------------------------------------------------
+ * Copies the description to the device, builds a linear BVH (Morton codes,
+ * radix sort, Karras hierarchy, bottom-up bounds) and the light-selection
+ * table (probability proportional to area x mean radiance).  Synchronises
+ * `stream` before returning.  Errors: INVALID_ARG (no primitives, bad sizes,
+ * material index out of range, emitting sphere/triangle), OOM, CUDA. */
+mars_status mars_scene_create(const mars_scene_desc* desc, void* stream, mars_scene** out);
+mars_status mars_scene_destroy(mars_scene* scene);
+
+/* ---- cache --------------------------------------------------------------
+ * Allocates the statistics cache, count fields (all invalid: beta = 1), guide
+ * (uniform), image accumulators and the queue arena for `scene`, which must
+ * outlive the cache.  Synchronises `stream`.  Errors: INVALID_ARG, OOM, CUDA. */
+mars_status mars_cache_create(const mars_scene* scene, const mars_cache_desc* desc, void* stream,
+                              mars_cache** out);
+mars_status mars_cache_destroy(mars_cache* cache);
+mars_status mars_cache_info_get(const mars_cache* cache, mars_cache_info* info);
+
+/* ---- one fixed-point iteration (Sec. 4.1, "Fixed-point iteration") ---------
+ * Renders one sample per pixel with the wavefront MARS path tracer: camera
+ * rays, then per depth wave closest hit, count lookup (T(x)/I_px x q, three
+ * cases, clamp), Alg. 1, NEE shadow rays, BSDF/guided child rays compacted
+ * into the next wave; then a deepest-first pass that forms every sample's value
+ * and cost and scatters the local statistics.  image_rgb [height][width][3]
+ * float32 receives the iteration's one-sample image (device memory unless
+ * params->image_on_host).  stats_host may be NULL.  Statistics accumulate
+ * until mars_update_counts.  The call synchronises `stream` once at the end
+ * (twice if the arena overflowed and tiles were re-rendered).
+ * Errors: INVALID_ARG (MARS mode without a pixel estimate, clamp_hi > 30,
+ * iteration >= 65536), OOM (a single pixel's path tree exceeds the arena), CUDA. */
+mars_status mars_render_iteration(mars_cache* cache, const mars_iter_params* params, float* image_rgb,
+                                  mars_iter_stats* stats_host, void* stream);
+
+/* ---- fixed-point update (Sec. 3.1 "Optimization"; App. A.3) -----------------
+ * One step per (cell, technique): q^RR and q^S per channel from the collected
+ * statistics and the V_I, C_I of the last mars_render_iteration with
+ * update_estimate; keeps the previous factors where n < 2 or the cost is 0, and
+ * everything when V_I <= 1e-12.  Rebuilds the guided technique's per-cell CDF
+ * from the accumulated deposits (P_b = 0.9 h_b / H + 0.1 / 256).  Zeroes the
+ * statistics.  Asynchronous on `stream`.  Errors: CUDA. */
+mars_status mars_update_counts(mars_cache* cache, void* stream);
+
+/* ---- state transfer (checkpoint / resume, teacher-forced checks) ----------
+ * Synchronous copies of the fields whose pointers are non-NULL. */
+mars_status mars_cache_get_state(mars_cache* cache, mars_cache_state* state, void* stream);
+mars_status mars_cache_set_state(mars_cache* cache, const mars_cache_state* state, void* stream);
+
+/* ---- serving ----------------------------------------------------------------
+ * A server owns a host scheduler thread that admits render jobs while their
+ * estimated device footprint fits `memory_budget_bytes` and fewer than
+ * `max_slots` jobs are resident, and runs every admitted job's iterations on
+ * its own stream so that jobs overlap on the device. */
+typedef struct {
+  const mars_scene_desc* scene;
+  mars_cache_desc cache;
+  uint32_t seed;
+  int32_t iterations;      /* fixed-point iterations of the job */
+  int32_t warmup;          /* leading iterations with beta = 1 */
+  int32_t reserved;
+} mars_job_desc;
+
+typedef enum { MARS_JOB_QUEUED = 0, MARS_JOB_RUNNING = 1, MARS_JOB_DONE = 2, MARS_JOB_FAILED = 3 } mars_job_state;
+
+typedef struct {
+  int32_t state;           /* mars_job_state */
+  int32_t iterations_done;
+  int32_t error;           /* mars_status of a failed job */
+  int32_t reserved;
+  double submit_s, start_s, end_s;   /* wall-clock seconds since server creation */
+  double iter_ms_p50, iter_ms_p99;   /* per-iteration latency */
+} mars_job_status;
+
+mars_status mars_server_create(uint64_t memory_budget_bytes, int32_t max_slots, mars_server** out);
+mars_status mars_server_destroy(mars_server* server);
+/* Queues a job (the scene description is copied).  Never blocks on the GPU. */
+mars_status mars_submit(mars_server* server, const mars_job_desc* job, uint64_t* job_id);
+/* Status of a job; when done, image_rgb (host, width*height*3 float32, may be
+ * NULL) receives the mean image over its iterations after warm-up. */
+mars_status mars_poll(mars_server* server, uint64_t job_id, mars_job_status* out, float* image_rgb);
+
+/* ---- diagnostics ------------------------------------------------------------ */
+const char* mars_last_error_string(void);
+const char* mars_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,20 @@
+"""GB300 (sm_103a) implementation of the MARS path tracer (Meyer et al.,
+SIGGRAPH Asia 2024): a wavefront path tracer with per-technique Russian
+roulette and splitting counts learned by a fixed-point scheme.
+
+The compute lives in ``libmars.so`` (hand-written CUDA, C ABI in
+``include/mars.h``); this package only marshals arguments.  Loading fails
+loudly when the library has not been built."""
+from ._abi import (  # noqa: F401
+    MARS_MODE_FIXED,
+    MARS_MODE_MARS,
+    MARS_MODE_WARMUP,
+    MARS_TECH_BSDF,
+    MARS_TECH_GUIDED,
+    MARS_TECH_NEE,
+    MARS_WEIGHTS_AWARE,
+    MARS_WEIGHTS_UNAWARE,
+    MarsError,
+    load,
+)
+from .renderer import Cache, Scene, Server, scene_desc  # noqa: F401

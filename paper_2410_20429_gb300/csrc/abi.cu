@@ -1,0 +1,810 @@
+// abi.cu -- the C ABI of libmars: scene and cache objects, the per-iteration
+// orchestration (pixel tiles over one queue arena), state transfer and the
+// error convention (status codes plus a thread-local message).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "abi_internal.h"
+
+namespace mars {
+
+thread_local std::string g_last_error;
+
+mars_status set_error(mars_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return s;
+}
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+double dlen(const double* v) { return std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]); }
+void dcross(const double* a, const double* b, double* r) {
+  r[0] = a[1] * b[2] - a[2] * b[1];
+  r[1] = a[2] * b[0] - a[0] * b[2];
+  r[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+float host_i2f(int v) {
+  float f;
+  std::memcpy(&f, &v, sizeof(f));
+  return f;
+}
+
+int num_sms_of(int dev) {
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 132;
+  return n;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ scene
+mars_status scene_create_impl(const mars_scene_desc* d, cudaStream_t st, mars_scene** out) {
+  if (!d || !out) return set_error(MARS_ERR_INVALID_ARG, "null descriptor or output");
+  *out = nullptr;
+  if (d->n_quads < 0 || d->n_spheres < 0 || d->n_tris < 0 || d->n_materials <= 0)
+    return set_error(MARS_ERR_INVALID_ARG, "negative primitive count or no materials");
+  const int n = d->n_quads + d->n_spheres + d->n_tris;
+  if (n <= 0) return set_error(MARS_ERR_INVALID_ARG, "scene has no primitives");
+  if (d->width <= 0 || d->height <= 0 || (int64_t)d->width * d->height > (1ll << 31))
+    return set_error(MARS_ERR_INVALID_ARG, "bad resolution %d x %d", d->width, d->height);
+  if ((d->n_quads && (!d->quads || !d->quad_mat)) || (d->n_spheres && (!d->spheres || !d->sphere_mat)) ||
+      (d->n_tris && (!d->tris || !d->tri_mat)) || !d->materials)
+    return set_error(MARS_ERR_INVALID_ARG, "null primitive array");
+  auto mat_ok = [&](int m) { return m >= 0 && m < d->n_materials; };
+  auto emits = [&](int m) {
+    const double* r = d->materials + 8 * m;
+    return (r[5] + r[6] + r[7]) / 3.0 > 0.0;
+  };
+  for (int i = 0; i < d->n_materials; ++i) {
+    const double* r = d->materials + 8 * i;
+    if (!(r[0] == 0.0 || r[0] == 1.0)) return set_error(MARS_ERR_INVALID_ARG, "material %d: bad type", i);
+    if (r[0] == 1.0 && !(r[4] > 0.0)) return set_error(MARS_ERR_INVALID_ARG, "material %d: alpha <= 0", i);
+  }
+  for (int i = 0; i < d->n_quads; ++i)
+    if (!mat_ok(d->quad_mat[i])) return set_error(MARS_ERR_INVALID_ARG, "quad %d: material out of range", i);
+  for (int i = 0; i < d->n_spheres; ++i) {
+    if (!mat_ok(d->sphere_mat[i])) return set_error(MARS_ERR_INVALID_ARG, "sphere %d: material out of range", i);
+    if (emits(d->sphere_mat[i])) return set_error(MARS_ERR_INVALID_ARG, "sphere %d: only quads may emit", i);
+    if (!(d->spheres[4 * i + 3] > 0.0)) return set_error(MARS_ERR_INVALID_ARG, "sphere %d: radius <= 0", i);
+  }
+  for (int i = 0; i < d->n_tris; ++i) {
+    if (!mat_ok(d->tri_mat[i])) return set_error(MARS_ERR_INVALID_ARG, "triangle %d: material out of range", i);
+    if (emits(d->tri_mat[i])) return set_error(MARS_ERR_INVALID_ARG, "triangle %d: only quads may emit", i);
+  }
+
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return set_error(MARS_ERR_CUDA, "no CUDA device");
+  mars_scene* s = new mars_scene();
+  s->device = dev;
+  s->num_sms = num_sms_of(dev);
+  s->width = d->width;
+  s->height = d->height;
+  s->n_prims = n;
+  s->desc_copy.assign(d);
+
+  // bounds in float64 (primitive corners, sphere boxes, triangle vertices)
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  auto grow = [&](double x, double y, double z) {
+    const double p[3] = {x, y, z};
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = std::min(lo[a], p[a]);
+      hi[a] = std::max(hi[a], p[a]);
+    }
+  };
+  std::vector<float4> prims(4 * (size_t)n), boxes(2 * (size_t)n);
+  std::vector<double> blo(3 * (size_t)n), bhi(3 * (size_t)n);
+  for (int i = 0; i < d->n_quads; ++i) {
+    const double* q = d->quads + 9 * i;
+    double mn[3], mx[3];
+    for (int a = 0; a < 3; ++a) {
+      const double c0 = q[a], c1 = q[a] + q[3 + a], c2 = q[a] + q[6 + a], c3 = q[a] + q[3 + a] + q[6 + a];
+      mn[a] = std::min(std::min(c0, c1), std::min(c2, c3));
+      mx[a] = std::max(std::max(c0, c1), std::max(c2, c3));
+    }
+    grow(q[0], q[1], q[2]);
+    grow(q[0] + q[3], q[1] + q[4], q[2] + q[5]);
+    grow(q[0] + q[6], q[1] + q[7], q[2] + q[8]);
+    grow(q[0] + q[3] + q[6], q[1] + q[4] + q[7], q[2] + q[5] + q[8]);
+    for (int a = 0; a < 3; ++a) { blo[3 * i + a] = mn[a]; bhi[3 * i + a] = mx[a]; }
+  }
+  for (int k = 0; k < d->n_spheres; ++k) {
+    const double* sp = d->spheres + 4 * k;
+    const int i = d->n_quads + k;
+    grow(sp[0] - sp[3], sp[1] - sp[3], sp[2] - sp[3]);
+    grow(sp[0] + sp[3], sp[1] + sp[3], sp[2] + sp[3]);
+    for (int a = 0; a < 3; ++a) { blo[3 * i + a] = sp[a] - sp[3]; bhi[3 * i + a] = sp[a] + sp[3]; }
+  }
+  for (int k = 0; k < d->n_tris; ++k) {
+    const double* v = d->tris + 9 * k;
+    const int i = d->n_quads + d->n_spheres + k;
+    for (int a = 0; a < 3; ++a) {
+      blo[3 * i + a] = std::min(std::min(v[a], v[3 + a]), v[6 + a]);
+      bhi[3 * i + a] = std::max(std::max(v[a], v[3 + a]), v[6 + a]);
+    }
+    for (int c = 0; c < 3; ++c) grow(v[3 * c], v[3 * c + 1], v[3 * c + 2]);
+  }
+  double emax = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    s->ds.lo[a] = (float)lo[a];
+    const double e = hi[a] - lo[a];
+    s->ds.ext[a] = (float)(e > 0.0 ? e : 1.0);
+    emax = std::max(emax, e);
+  }
+  // ray offset: 1e-4 x the largest scene extent
+  s->ds.eps = (float)(1e-4 * (emax > 0.0 ? emax : 1.0));
+  const double pad = 1e-6 * (emax > 0.0 ? emax : 1.0);
+  for (int i = 0; i < n; ++i) {
+    boxes[2 * i] = make_float4((float)(blo[3 * i] - pad), (float)(blo[3 * i + 1] - pad), (float)(blo[3 * i + 2] - pad), 0.f);
+    boxes[2 * i + 1] = make_float4((float)(bhi[3 * i] + pad), (float)(bhi[3 * i + 1] + pad), (float)(bhi[3 * i + 2] + pad), 0.f);
+  }
+
+  // lights: emitting quads, picked with probability ~ area x mean radiance
+  std::vector<int> light_of_quad(d->n_quads, -1);
+  std::vector<double> lw;
+  std::vector<int> lq;
+  double tot = 0.0;
+  for (int i = 0; i < d->n_quads; ++i) {
+    const int m = d->quad_mat[i];
+    const double* r = d->materials + 8 * m;
+    const double p = (r[5] + r[6] + r[7]) / 3.0;
+    if (p > 0.0) {
+      const double* q = d->quads + 9 * i;
+      double nrm[3];
+      dcross(q + 3, q + 6, nrm);
+      light_of_quad[i] = (int)lq.size();
+      lq.push_back(i);
+      lw.push_back(dlen(nrm) * p);
+      tot += dlen(nrm) * p;
+    }
+  }
+  s->n_lights = (int)lq.size();
+  std::vector<float4> lights(5 * std::max<size_t>(1, lq.size()));
+  double run = 0.0;
+  for (size_t l = 0; l < lq.size(); ++l) {
+    const double* q = d->quads + 9 * lq[l];
+    const double* r = d->materials + 8 * d->quad_mat[lq[l]];
+    double nrm[3];
+    dcross(q + 3, q + 6, nrm);
+    const double area = dlen(nrm);
+    run += lw[l];
+    lights[5 * l + 0] = make_float4((float)q[0], (float)q[1], (float)q[2], (float)(run / tot));
+    lights[5 * l + 1] = make_float4((float)q[3], (float)q[4], (float)q[5], (float)(lw[l] / tot));
+    lights[5 * l + 2] = make_float4((float)q[6], (float)q[7], (float)q[8], (float)area);
+    lights[5 * l + 3] = make_float4((float)(nrm[0] / area), (float)(nrm[1] / area), (float)(nrm[2] / area),
+                                    host_i2f(lq[l]));
+    lights[5 * l + 4] = make_float4((float)r[5], (float)r[6], (float)r[7], 0.f);
+  }
+
+  for (int i = 0; i < d->n_quads; ++i) {
+    const double* q = d->quads + 9 * i;
+    double nrm[3];
+    dcross(q + 3, q + 6, nrm);
+    const double L = dlen(nrm);
+    const int bits = (d->quad_mat[i] << 2) | PRIM_QUAD;
+    prims[4 * i + 0] = make_float4((float)q[0], (float)q[1], (float)q[2], host_i2f(bits));
+    prims[4 * i + 1] = make_float4((float)q[3], (float)q[4], (float)q[5], 0.f);
+    prims[4 * i + 2] = make_float4((float)q[6], (float)q[7], (float)q[8], 0.f);
+    prims[4 * i + 3] = make_float4((float)(nrm[0] / L), (float)(nrm[1] / L), (float)(nrm[2] / L),
+                                   host_i2f(light_of_quad[i]));
+  }
+  for (int k = 0; k < d->n_spheres; ++k) {
+    const double* sp = d->spheres + 4 * k;
+    const int i = d->n_quads + k;
+    const int bits = (d->sphere_mat[k] << 2) | PRIM_SPHERE;
+    prims[4 * i + 0] = make_float4((float)sp[0], (float)sp[1], (float)sp[2], host_i2f(bits));
+    prims[4 * i + 1] = make_float4((float)sp[3], (float)(1.0 / sp[3]), 0.f, 0.f);
+    prims[4 * i + 2] = make_float4(0.f, 0.f, 0.f, 0.f);
+    prims[4 * i + 3] = make_float4(0.f, 0.f, 0.f, host_i2f(-1));
+  }
+  for (int k = 0; k < d->n_tris; ++k) {
+    const double* v = d->tris + 9 * k;
+    const int i = d->n_quads + d->n_spheres + k;
+    const double e1[3] = {v[3] - v[0], v[4] - v[1], v[5] - v[2]};
+    const double e2[3] = {v[6] - v[0], v[7] - v[1], v[8] - v[2]};
+    double nrm[3];
+    dcross(e1, e2, nrm);
+    const double L = dlen(nrm);
+    const int bits = (d->tri_mat[k] << 2) | PRIM_TRI;
+    prims[4 * i + 0] = make_float4((float)v[0], (float)v[1], (float)v[2], host_i2f(bits));
+    prims[4 * i + 1] = make_float4((float)e1[0], (float)e1[1], (float)e1[2], 0.f);
+    prims[4 * i + 2] = make_float4((float)e2[0], (float)e2[1], (float)e2[2], 0.f);
+    prims[4 * i + 3] = make_float4((float)(nrm[0] / L), (float)(nrm[1] / L), (float)(nrm[2] / L), host_i2f(-1));
+  }
+  std::vector<float4> mats(3 * (size_t)d->n_materials);
+  for (int m = 0; m < d->n_materials; ++m) {
+    const double* r = d->materials + 8 * m;
+    const bool refl = r[1] > 0.0 || r[2] > 0.0 || r[3] > 0.0;
+    mats[3 * m + 0] = make_float4((float)r[0], (float)r[4], refl ? 1.f : 0.f, emits(m) ? 1.f : 0.f);
+    mats[3 * m + 1] = make_float4((float)r[1], (float)r[2], (float)r[3], 0.f);
+    mats[3 * m + 2] = make_float4((float)r[5], (float)r[6], (float)r[7], 0.f);
+  }
+  // pinhole camera: right = normalize(up x forward), true up = forward x right
+  {
+    const double* c = d->camera;
+    double f[3] = {c[3] - c[0], c[4] - c[1], c[5] - c[2]};
+    const double fl = dlen(f);
+    for (double& x : f) x /= fl;
+    double r[3];
+    dcross(c + 6, f, r);
+    const double rl = dlen(r);
+    for (double& x : r) x /= rl;
+    double u[3];
+    dcross(f, r, u);
+    for (int a = 0; a < 3; ++a) {
+      s->ds.cam_o[a] = (float)c[a];
+      s->ds.cam_f[a] = (float)f[a];
+      s->ds.cam_r[a] = (float)r[a];
+      s->ds.cam_u[a] = (float)u[a];
+    }
+    s->ds.tanh_half = (float)std::tan(0.5 * c[9] * 3.14159265358979323846 / 180.0);
+    s->ds.aspect = (float)((double)d->width / (double)d->height);
+  }
+  s->ds.n_prims = n;
+  s->ds.n_quads = d->n_quads;
+  s->ds.n_lights = s->n_lights;
+  s->ds.n_mats = d->n_materials;
+  s->ds.width = d->width;
+  s->ds.height = d->height;
+
+  auto cleanup = [&](cudaError_t e, const char* what) {
+    set_error(e == cudaErrorMemoryAllocation ? MARS_ERR_OOM : MARS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    scene_destroy_impl(s);
+    return e == cudaErrorMemoryAllocation ? MARS_ERR_OOM : MARS_ERR_CUDA;
+  };
+  cudaError_t e;
+  if ((e = cudaMalloc(&s->d_prims, sizeof(float4) * prims.size())) != cudaSuccess) return cleanup(e, "scene alloc");
+  if ((e = cudaMalloc(&s->d_boxes, sizeof(float4) * boxes.size())) != cudaSuccess) return cleanup(e, "scene alloc");
+  if ((e = cudaMalloc(&s->d_nodes, sizeof(BvhNode) * std::max(1, n - 1))) != cudaSuccess) return cleanup(e, "scene alloc");
+  if ((e = cudaMalloc(&s->d_mats, sizeof(float4) * mats.size())) != cudaSuccess) return cleanup(e, "scene alloc");
+  if ((e = cudaMalloc(&s->d_lights, sizeof(float4) * lights.size())) != cudaSuccess) return cleanup(e, "scene alloc");
+  if ((e = cudaMemcpyAsync(s->d_prims, prims.data(), sizeof(float4) * prims.size(), cudaMemcpyHostToDevice, st)) ||
+      (e = cudaMemcpyAsync(s->d_boxes, boxes.data(), sizeof(float4) * boxes.size(), cudaMemcpyHostToDevice, st)) ||
+      (e = cudaMemcpyAsync(s->d_mats, mats.data(), sizeof(float4) * mats.size(), cudaMemcpyHostToDevice, st)) ||
+      (e = cudaMemcpyAsync(s->d_lights, lights.data(), sizeof(float4) * lights.size(), cudaMemcpyHostToDevice, st)))
+    return cleanup(e, "scene upload");
+  std::string berr;
+  if ((e = build_bvh(s->d_boxes, n, s->ds.lo, s->ds.ext, s->d_nodes, st, &berr)) != cudaSuccess)
+    return cleanup(e, berr.c_str());
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cleanup(e, "scene create");
+  if (n >= 2) {
+    // check the hierarchy before any kernel traverses it: every internal node
+    // reached once from the root, every primitive once, all indices in range
+    std::vector<BvhNode> nodes(n - 1);
+    if ((e = cudaMemcpy(nodes.data(), s->d_nodes, sizeof(BvhNode) * (n - 1), cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return cleanup(e, "BVH readback");
+    std::vector<uint8_t> seen_node(n - 1, 0), seen_leaf(n, 0);
+    std::vector<int> stack{0};
+    bool okb = true;
+    while (!stack.empty() && okb) {
+      const int k = stack.back();
+      stack.pop_back();
+      if (k < 0 || k >= n - 1 || seen_node[k]) { okb = false; break; }
+      seen_node[k] = 1;
+      int ch[2];
+      std::memcpy(&ch[0], &nodes[k].a.w, sizeof(int));
+      std::memcpy(&ch[1], &nodes[k].b.w, sizeof(int));
+      for (int c : ch) {
+        if (c < 0) {
+          const int leaf = ~c;
+          if (leaf >= n || seen_leaf[leaf]) { okb = false; break; }
+          seen_leaf[leaf] = 1;
+        } else {
+          stack.push_back(c);
+        }
+      }
+    }
+    for (int k = 0; okb && k < n - 1; ++k) okb = seen_node[k];
+    for (int k = 0; okb && k < n; ++k) okb = seen_leaf[k];
+    if (!okb) {
+      set_error(MARS_ERR_CUDA, "BVH build produced an invalid hierarchy");
+      scene_destroy_impl(s);
+      return MARS_ERR_CUDA;
+    }
+  }
+  s->ds.prims = s->d_prims;
+  s->ds.nodes = s->d_nodes;
+  s->ds.mats = s->d_mats;
+  s->ds.lights = s->d_lights;
+  s->device_bytes = sizeof(float4) * (prims.size() + boxes.size() + mats.size() + lights.size()) +
+                    sizeof(BvhNode) * std::max(1, n - 1);
+  *out = s;
+  return MARS_OK;
+}
+
+void scene_destroy_impl(mars_scene* s) {
+  if (!s) return;
+  DeviceGuard g(s->device);
+  if (s->d_prims) cudaFree(s->d_prims);
+  if (s->d_boxes) cudaFree(s->d_boxes);
+  if (s->d_nodes) cudaFree(s->d_nodes);
+  if (s->d_mats) cudaFree(s->d_mats);
+  if (s->d_lights) cudaFree(s->d_lights);
+  delete s;
+}
+
+// ------------------------------------------------------------------ cache
+uint64_t cache_footprint(int64_t cells, int64_t pixels, int max_depth, int techniques, uint64_t cap) {
+  (void)max_depth;
+  uint64_t b = (uint64_t)cap * (NR + NV + 1) * sizeof(float4);
+  b += (uint64_t)cells * NT * (2 * sizeof(float4) + NSTAT * sizeof(double));
+  if (techniques & MARS_TECH_GUIDED) b += (uint64_t)cells * GUIDE_BINS * 2 * sizeof(float);
+  b += (uint64_t)pixels * 3 * sizeof(float4);
+  return b + sizeof(DevCounters) + 4096;
+}
+
+uint64_t default_capacity(int64_t pixels, int max_depth) {
+  uint64_t cap = (uint64_t)pixels * (uint64_t)max_depth * 8ull;
+  if (cap < (1ull << 20)) cap = 1ull << 20;
+  return cap;
+}
+
+mars_status cache_create_impl(const mars_scene* s, const mars_cache_desc* d, cudaStream_t st, mars_cache** out) {
+  if (!s || !d || !out) return set_error(MARS_ERR_INVALID_ARG, "null scene, descriptor or output");
+  *out = nullptr;
+  if (d->grid_n < 1 || d->grid_n > 256) return set_error(MARS_ERR_INVALID_ARG, "grid_n %d out of [1, 256]", d->grid_n);
+  if (!(d->techniques & MARS_TECH_BSDF) || (d->techniques & ~7))
+    return set_error(MARS_ERR_INVALID_ARG, "techniques must include BSDF and only use bits 0..2");
+  if (d->max_depth < 1 || d->max_depth > MAXD)
+    return set_error(MARS_ERR_INVALID_ARG, "max_depth %d out of [1, %d]", d->max_depth, MAXD);
+  if ((d->techniques & MARS_TECH_NEE) && s->n_lights == 0)
+    return set_error(MARS_ERR_INVALID_ARG, "NEE requested but the scene has no emitting quad");
+  const int bits = (d->techniques & MARS_TECH_GUIDED) ? 6 : 5;
+  if ((d->max_depth - 1) * bits > 64)
+    return set_error(MARS_ERR_INVALID_ARG, "max_depth %d too deep for %d lineage bits per level", d->max_depth, bits);
+  const int64_t cells = (int64_t)d->grid_n * d->grid_n * d->grid_n;
+  const int64_t pixels = (int64_t)s->width * s->height;
+  uint64_t cap = d->arena_capacity ? d->arena_capacity : default_capacity(pixels, d->max_depth);
+  if (cap < 64) cap = 64;
+  if (cap > 0xFFFFFFF0ull) return set_error(MARS_ERR_INVALID_ARG, "arena_capacity above 2^32 - 16");
+
+  DeviceGuard g(s->device);
+  mars_cache* c = new mars_cache();
+  c->scene = s;
+  c->device = s->device;
+  c->grid_n = d->grid_n;
+  c->techniques = d->techniques;
+  c->max_depth = d->max_depth;
+  c->cells = cells;
+  c->pixels = pixels;
+  c->arena.cap = cap;
+  c->max_tiles = 4096;
+  auto cleanup = [&](cudaError_t e, const char* what) {
+    const mars_status ms = e == cudaErrorMemoryAllocation ? MARS_ERR_OOM : MARS_ERR_CUDA;
+    set_error(ms, "%s: %s", what, cudaGetErrorString(e));
+    cache_destroy_impl(c);
+    return ms;
+  };
+  cudaError_t e;
+  for (int k = 0; k < NR; ++k)
+    if ((e = cudaMalloc(&c->arena.R[k], sizeof(float4) * cap)) != cudaSuccess) return cleanup(e, "arena alloc");
+  for (int k = 0; k < NV; ++k)
+    if ((e = cudaMalloc(&c->arena.V[k], sizeof(float4) * cap)) != cudaSuccess) return cleanup(e, "arena alloc");
+  if ((e = cudaMalloc(&c->arena.S, sizeof(float4) * cap)) != cudaSuccess) return cleanup(e, "arena alloc");
+  if ((e = cudaMalloc(&c->d_cnt, sizeof(float4) * 2 * NT * cells)) != cudaSuccess) return cleanup(e, "cache alloc");
+  if ((e = cudaMalloc(&c->d_stats, sizeof(double) * NSTAT * NT * cells)) != cudaSuccess) return cleanup(e, "cache alloc");
+  const int64_t gcells = (d->techniques & MARS_TECH_GUIDED) ? cells : 1;
+  if ((e = cudaMalloc(&c->d_hist, sizeof(float) * GUIDE_BINS * gcells)) != cudaSuccess) return cleanup(e, "cache alloc");
+  if ((e = cudaMalloc(&c->d_cdf, sizeof(float) * GUIDE_BINS * gcells)) != cudaSuccess) return cleanup(e, "cache alloc");
+  if ((e = cudaMalloc(&c->d_est, sizeof(float4) * pixels)) != cudaSuccess) return cleanup(e, "image alloc");
+  if ((e = cudaMalloc(&c->d_run, sizeof(float4) * pixels)) != cudaSuccess) return cleanup(e, "image alloc");
+  if ((e = cudaMalloc(&c->d_img, sizeof(float4) * pixels)) != cudaSuccess) return cleanup(e, "image alloc");
+  if ((e = cudaMalloc(&c->d_ctr, sizeof(DevCounters))) != cudaSuccess) return cleanup(e, "counter alloc");
+  if ((e = cudaMalloc(&c->d_tile_status, sizeof(unsigned int) * c->max_tiles)) != cudaSuccess)
+    return cleanup(e, "counter alloc");
+  if ((e = cudaMallocHost(&c->h_ctr, sizeof(DevCounters))) != cudaSuccess) return cleanup(e, "pinned alloc");
+  if ((e = cudaMallocHost(&c->h_tile_status, sizeof(unsigned int) * c->max_tiles)) != cudaSuccess)
+    return cleanup(e, "pinned alloc");
+  cudaMemsetAsync(c->d_cnt, 0, sizeof(float4) * 2 * NT * cells, st);
+  cudaMemsetAsync(c->d_stats, 0, sizeof(double) * NSTAT * NT * cells, st);
+  cudaMemsetAsync(c->d_hist, 0, sizeof(float) * GUIDE_BINS * gcells, st);
+  cudaMemsetAsync(c->d_run, 0, sizeof(float4) * pixels, st);
+  cudaMemsetAsync(c->d_img, 0, sizeof(float4) * pixels, st);
+  cudaMemsetAsync(c->d_ctr, 0, sizeof(DevCounters), st);
+  cudaMemsetAsync(c->d_tile_status, 0, sizeof(unsigned int) * c->max_tiles, st);
+  {
+    std::vector<float> cdf((size_t)GUIDE_BINS * gcells);
+    for (int64_t k = 0; k < gcells; ++k)
+      for (int b = 0; b < GUIDE_BINS; ++b) cdf[k * GUIDE_BINS + b] = (float)((double)(b + 1) / GUIDE_BINS);
+    std::vector<float4> one((size_t)pixels, make_float4(1.f, 1.f, 1.f, 0.f));
+    if ((e = cudaMemcpyAsync(c->d_cdf, cdf.data(), sizeof(float) * cdf.size(), cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemcpyAsync(c->d_est, one.data(), sizeof(float4) * one.size(), cudaMemcpyHostToDevice, st)))
+      return cleanup(e, "cache init");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cleanup(e, "cache init");
+  }
+  c->dc.grid_n = d->grid_n;
+  c->dc.n_cells = (int)cells;
+  c->dc.techniques = d->techniques;
+  c->dc.max_depth = d->max_depth;
+  c->dc.bits = bits;
+  c->dc.n_pixels = (int)pixels;
+  c->dc.cnt = c->d_cnt;
+  c->dc.stats = c->d_stats;
+  c->dc.guide_hist = c->d_hist;
+  c->dc.guide_cdf = c->d_cdf;
+  c->dc.est = c->d_est;
+  c->dc.run_sum = c->d_run;
+  c->dc.img = c->d_img;
+  c->dc.ctr = c->d_ctr;
+  c->dc.tile_status = c->d_tile_status;
+  c->device_bytes = cache_footprint(cells, pixels, d->max_depth, d->techniques, cap);
+  *out = c;
+  return MARS_OK;
+}
+
+void cache_destroy_impl(mars_cache* c) {
+  if (!c) return;
+  DeviceGuard g(c->device);
+  for (auto* p : c->arena.R) if (p) cudaFree(p);
+  for (auto* p : c->arena.V) if (p) cudaFree(p);
+  if (c->arena.S) cudaFree(c->arena.S);
+  void* ptrs[] = {c->d_cnt, c->d_stats, c->d_hist, c->d_cdf, c->d_est, c->d_run, c->d_img, c->d_ctr, c->d_tile_status};
+  for (void* p : ptrs) if (p) cudaFree(p);
+  if (c->h_ctr) cudaFreeHost(c->h_ctr);
+  if (c->h_tile_status) cudaFreeHost(c->h_tile_status);
+  for (cudaEvent_t ev : c->events) cudaEventDestroy(ev);
+  delete c;
+}
+
+// ------------------------------------------------------------ iteration
+static mars_status poison(mars_cache* c, cudaError_t e, const char* what) {
+  c->poisoned = true;
+  return set_error(MARS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, float* image, mars_iter_stats* out,
+                                  cudaStream_t st) {
+  if (!c || !p) return set_error(MARS_ERR_INVALID_ARG, "null cache or params");
+  if (c->poisoned) return set_error(MARS_ERR_CUDA, "cache is poisoned by an earlier CUDA error");
+  if (p->iteration >= 65536u) return set_error(MARS_ERR_INVALID_ARG, "iteration %u >= 65536", p->iteration);
+  if (p->mode < 0 || p->mode > 2) return set_error(MARS_ERR_INVALID_ARG, "bad mode %d", p->mode);
+  if (p->mode == MARS_MODE_MARS && !c->has_estimate)
+    return set_error(MARS_ERR_INVALID_ARG, "MARS mode needs a pixel estimate (run an iteration with update_estimate)");
+  if (!(p->clamp_lo >= 0.0f) || !(p->clamp_hi <= 30.0f) || !(p->clamp_lo <= p->clamp_hi))
+    return set_error(MARS_ERR_INVALID_ARG, "clamp range [%g, %g] outside [0, 30]", p->clamp_lo, p->clamp_hi);
+  if (!(p->outlier > 0.0f)) return set_error(MARS_ERR_INVALID_ARG, "outlier multiple must be positive");
+  if (p->image_on_host && !image) return set_error(MARS_ERR_INVALID_ARG, "image_on_host without an image");
+  DeviceGuard g(c->device);
+  if (!g.ok) return set_error(MARS_ERR_CUDA, "cannot select device %d", c->device);
+  const mars_scene* s = c->scene;
+  const int num_sms = s->num_sms;
+
+  IterArgs it{};
+  it.seed = p->seed;
+  it.job = p->job;
+  it.iteration = p->iteration;
+  it.mode = p->mode;
+  it.aware = p->weights == MARS_WEIGHTS_AWARE;
+  it.collect = p->collect != 0;
+  it.has_estimate = c->has_estimate ? 1 : 0;
+  it.clamp_lo = p->clamp_lo;
+  it.clamp_hi = p->clamp_hi;
+  it.outlier = p->outlier;
+
+  // reset the iteration counters (rays, vertices, beta sums, image sums)
+  cudaError_t e = cudaMemsetAsync(c->d_ctr, 0, sizeof(DevCounters), st);
+  if (e != cudaSuccess) return poison(c, e, "counter reset");
+
+  const int64_t npx = c->pixels;
+  int ntiles = c->next_tiles > 0 ? c->next_tiles : 1;
+  if (ntiles > c->max_tiles) ntiles = c->max_tiles;
+  std::vector<std::pair<int64_t, int64_t>> tiles;
+  for (int t = 0; t < ntiles; ++t) {
+    const int64_t a = npx * t / ntiles, b = npx * (t + 1) / ntiles;
+    if (b > a) tiles.emplace_back(a, b);
+  }
+  uint32_t retries = 0, used = 0, launches = 0, shade_launches = 0;
+  uint64_t demand = 0;
+  double shade_ms = 0.0, reverse_ms = 0.0, image_ms = 0.0;
+  const int D = c->max_depth;
+  const int per_tile = 2 * D + 1;
+  float* dev_out = p->image_on_host ? nullptr : image;
+  while (true) {
+    if (p->profile) {
+      const size_t need = tiles.size() * per_tile + 2;
+      while (c->events.size() < need) {
+        cudaEvent_t ev;
+        if ((e = cudaEventCreate(&ev)) != cudaSuccess) return poison(c, e, "event create");
+        c->events.push_back(ev);
+      }
+    }
+    for (size_t t = 0; t < tiles.size(); ++t) {
+      it.tile_begin = (int)tiles[t].first;
+      it.tile_end = (int)tiles[t].second;
+      it.tile_slot = (int)t;
+      cudaEvent_t* ev = p->profile ? c->events.data() + t * per_tile : nullptr;
+      if ((e = launch_tile(s->ds, c->dc, c->arena, it, num_sms, st, ev)) != cudaSuccess)
+        return poison(c, e, "render launch");
+      launches += 2 * D + TILE_LAUNCHES_FIXED;
+      shade_launches += D;
+    }
+    used += (uint32_t)tiles.size();
+    cudaEvent_t* iev = p->profile ? c->events.data() + tiles.size() * per_tile : nullptr;
+    if (iev) cudaEventRecord(iev[0], st);
+    if (p->update_estimate) {
+      if ((e = launch_image_stats(c->dc, s->width, s->height, c->n_iterations, p->outlier, dev_out, st)) !=
+          cudaSuccess)
+        return poison(c, e, "image stats launch");
+      launches += 3;
+    } else if (dev_out) {
+      if ((e = launch_image_copy(c->dc, (int)npx, dev_out, st)) != cudaSuccess) return poison(c, e, "image copy");
+      launches += 1;
+    }
+    if (iev) cudaEventRecord(iev[1], st);
+    if ((e = cudaMemcpyAsync(c->h_tile_status, c->d_tile_status, sizeof(unsigned int) * tiles.size(),
+                             cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+      return poison(c, e, "status copy");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return poison(c, e, "render");
+    if (p->profile) {
+      for (size_t t = 0; t < tiles.size(); ++t) {
+        cudaEvent_t* ev = c->events.data() + t * per_tile;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[0], ev[D]);
+        shade_ms += ms;
+        cudaEventElapsedTime(&ms, ev[D], ev[2 * D]);
+        reverse_ms += ms;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, iev[0], iev[1]);
+      image_ms += ms;
+    }
+    demand = std::max<uint64_t>(demand, c->h_ctr->demand);
+    std::vector<std::pair<int64_t, int64_t>> again;
+    for (size_t t = 0; t < tiles.size(); ++t) {
+      if (!c->h_tile_status[t]) continue;
+      const int64_t a = tiles[t].first, b = tiles[t].second;
+      if (b - a <= 1)
+        return set_error(MARS_ERR_OOM, "one pixel's path tree needs more than the arena's %llu rays",
+                         (unsigned long long)c->arena.cap);
+      const int64_t m = (a + b) / 2;
+      again.emplace_back(a, m);
+      again.emplace_back(m, b);
+    }
+    if (again.empty()) break;
+    if ((int)again.size() > c->max_tiles) return set_error(MARS_ERR_OOM, "too many tiles after arena overflow");
+    retries += (uint32_t)again.size();
+    tiles.swap(again);
+    // the committed tiles stay; clear the overflow marker so the image pass runs
+    if ((e = cudaMemsetAsync(&c->d_ctr->any_overflow, 0, sizeof(unsigned int), st)) != cudaSuccess)
+      return poison(c, e, "overflow reset");
+  }
+  // plan the next iteration's tiles: every failure split one tile in two; when
+  // the largest tile used less than half the arena, try fewer tiles again
+  {
+    const int final_tiles = ntiles + (int)(retries / 2);
+    if (retries > 0)
+      c->next_tiles = std::min(c->max_tiles, (final_tiles * 5 + 3) / 4);
+    else if (c->next_tiles > 1 && demand < c->arena.cap / 2)
+      c->next_tiles = std::max(1, c->next_tiles / 2);
+  }
+  if (p->update_estimate) {
+    c->n_iterations += 1;
+    c->has_estimate = true;
+  }
+  if (p->image_on_host) {
+    // gather the float4 image into the caller's packed rgb buffer
+    if ((e = cudaMemcpy2DAsync(image, 3 * sizeof(float), c->d_img, sizeof(float4), 3 * sizeof(float), (size_t)npx,
+                               cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+      return poison(c, e, "image copy");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return poison(c, e, "image copy");
+  }
+  if (out) {
+    const DevCounters& h = *c->h_ctr;
+    out->VI = h.VI;
+    out->CI = h.CI;
+    out->rays = h.rays;
+    out->vertices = h.vertices;
+    out->estimator_vertices = h.est_vertices;
+    for (int t = 0; t < NT; ++t) out->mean_beta[t] = h.est_vertices ? h.sum_beta[t] / (double)h.est_vertices : 0.0;
+    out->tiles = used;
+    out->retries = retries;
+    out->arena_demand = demand;
+    out->launches = launches;
+    out->shade_launches = shade_launches;
+    out->shade_ms = shade_ms;
+    out->reverse_ms = reverse_ms;
+    out->image_ms = image_ms;
+    out->wave_entries = h.entries;
+  }
+  c->last_VI = c->h_ctr->VI;
+  c->last_CI = c->h_ctr->CI;
+  return MARS_OK;
+}
+
+mars_status update_counts_impl(mars_cache* c, cudaStream_t st) {
+  if (!c) return set_error(MARS_ERR_INVALID_ARG, "null cache");
+  if (c->poisoned) return set_error(MARS_ERR_CUDA, "cache is poisoned by an earlier CUDA error");
+  DeviceGuard g(c->device);
+  cudaError_t e = launch_update(c->dc, c->scene->num_sms, st);
+  if (e != cudaSuccess) return poison(c, e, "update launch");
+  return MARS_OK;
+}
+
+mars_status get_state_impl(mars_cache* c, mars_cache_state* s, cudaStream_t st) {
+  if (!c || !s) return set_error(MARS_ERR_INVALID_ARG, "null cache or state");
+  if (c->poisoned) return set_error(MARS_ERR_CUDA, "cache is poisoned by an earlier CUDA error");
+  DeviceGuard g(c->device);
+  const int64_t cells = c->cells, px = c->pixels;
+  const bool guided = c->techniques & MARS_TECH_GUIDED;
+  cudaError_t e = cudaSuccess;
+  std::vector<float4> cnt;
+  std::vector<float4> img4;
+  if (s->q_rr || s->q_s || s->valid) {
+    cnt.resize(2 * NT * cells);
+    e = cudaMemcpyAsync(cnt.data(), c->d_cnt, sizeof(float4) * cnt.size(), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return poison(c, e, "state copy");
+  }
+  if (s->stats && (e = cudaMemcpyAsync(s->stats, c->d_stats, sizeof(double) * NSTAT * NT * cells,
+                                       cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return poison(c, e, "state copy");
+  if (s->guide_hist && guided &&
+      (e = cudaMemcpyAsync(s->guide_hist, c->d_hist, sizeof(float) * GUIDE_BINS * cells, cudaMemcpyDeviceToHost,
+                           st)) != cudaSuccess)
+    return poison(c, e, "state copy");
+  if (s->guide_cdf && guided &&
+      (e = cudaMemcpyAsync(s->guide_cdf, c->d_cdf, sizeof(float) * GUIDE_BINS * cells, cudaMemcpyDeviceToHost, st)) !=
+          cudaSuccess)
+    return poison(c, e, "state copy");
+  if (s->pixel_estimate &&
+      (e = cudaMemcpy2DAsync(s->pixel_estimate, 3 * sizeof(float), c->d_est, sizeof(float4), 3 * sizeof(float),
+                             (size_t)px, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return poison(c, e, "state copy");
+  if (s->run_sum &&
+      (e = cudaMemcpy2DAsync(s->run_sum, 3 * sizeof(float), c->d_run, sizeof(float4), 3 * sizeof(float), (size_t)px,
+                             cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return poison(c, e, "state copy");
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return poison(c, e, "state copy");
+  for (int64_t k = 0; k < cells * NT && !cnt.empty(); ++k) {
+    const float4 r = cnt[2 * k], q = cnt[2 * k + 1];
+    if (s->q_rr) { s->q_rr[3 * k] = r.x; s->q_rr[3 * k + 1] = r.y; s->q_rr[3 * k + 2] = r.z; }
+    if (s->q_s) { s->q_s[3 * k] = q.x; s->q_s[3 * k + 1] = q.y; s->q_s[3 * k + 2] = q.z; }
+    if (s->valid) s->valid[k] = r.w > 0.0f ? 1 : 0;
+  }
+  s->n_iterations = c->n_iterations;
+  s->has_estimate = c->has_estimate ? 1 : 0;
+  s->VI = c->last_VI;
+  s->CI = c->last_CI;
+  return MARS_OK;
+}
+
+mars_status set_state_impl(mars_cache* c, const mars_cache_state* s, cudaStream_t st) {
+  if (!c || !s) return set_error(MARS_ERR_INVALID_ARG, "null cache or state");
+  if (c->poisoned) return set_error(MARS_ERR_CUDA, "cache is poisoned by an earlier CUDA error");
+  if (s->n_iterations < 0) return set_error(MARS_ERR_INVALID_ARG, "negative n_iterations");
+  DeviceGuard g(c->device);
+  const int64_t cells = c->cells, px = c->pixels;
+  const bool guided = c->techniques & MARS_TECH_GUIDED;
+  cudaError_t e = cudaSuccess;
+  if (s->q_rr || s->q_s || s->valid) {
+    std::vector<float4> cnt(2 * NT * cells);
+    if ((e = cudaMemcpy(cnt.data(), c->d_cnt, sizeof(float4) * cnt.size(), cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return poison(c, e, "state copy");
+    for (int64_t k = 0; k < cells * NT; ++k) {
+      float4& r = cnt[2 * k];
+      float4& q = cnt[2 * k + 1];
+      if (s->q_rr) { r.x = s->q_rr[3 * k]; r.y = s->q_rr[3 * k + 1]; r.z = s->q_rr[3 * k + 2]; }
+      if (s->q_s) { q.x = s->q_s[3 * k]; q.y = s->q_s[3 * k + 1]; q.z = s->q_s[3 * k + 2]; }
+      if (s->valid) r.w = s->valid[k] ? 1.0f : 0.0f;
+    }
+    if ((e = cudaMemcpyAsync(c->d_cnt, cnt.data(), sizeof(float4) * cnt.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+      return poison(c, e, "state copy");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return poison(c, e, "state copy");
+  }
+  if (s->stats && (e = cudaMemcpyAsync(c->d_stats, s->stats, sizeof(double) * NSTAT * NT * cells,
+                                       cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return poison(c, e, "state copy");
+  if (s->guide_hist && guided &&
+      (e = cudaMemcpyAsync(c->d_hist, s->guide_hist, sizeof(float) * GUIDE_BINS * cells, cudaMemcpyHostToDevice,
+                           st)) != cudaSuccess)
+    return poison(c, e, "state copy");
+  if (s->guide_cdf && guided &&
+      (e = cudaMemcpyAsync(c->d_cdf, s->guide_cdf, sizeof(float) * GUIDE_BINS * cells, cudaMemcpyHostToDevice, st)) !=
+          cudaSuccess)
+    return poison(c, e, "state copy");
+  if (s->pixel_estimate &&
+      (e = cudaMemcpy2DAsync(c->d_est, sizeof(float4), s->pixel_estimate, 3 * sizeof(float), 3 * sizeof(float),
+                             (size_t)px, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return poison(c, e, "state copy");
+  if (s->run_sum &&
+      (e = cudaMemcpy2DAsync(c->d_run, sizeof(float4), s->run_sum, 3 * sizeof(float), 3 * sizeof(float), (size_t)px,
+                             cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return poison(c, e, "state copy");
+  // V_I and C_I feed the next update
+  if ((e = cudaMemcpyAsync(&c->d_ctr->VI, &s->VI, sizeof(double), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(&c->d_ctr->CI, &s->CI, sizeof(double), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return poison(c, e, "state copy");
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return poison(c, e, "state copy");
+  c->n_iterations = s->n_iterations;
+  c->has_estimate = s->has_estimate != 0;
+  c->last_VI = s->VI;
+  c->last_CI = s->CI;
+  return MARS_OK;
+}
+
+}  // namespace mars
+
+// ======================================================================= C ABI
+using namespace mars;
+
+extern "C" {
+
+mars_status mars_scene_create(const mars_scene_desc* desc, void* stream, mars_scene** out) {
+  return scene_create_impl(desc, (cudaStream_t)stream, out);
+}
+
+mars_status mars_scene_destroy(mars_scene* scene) {
+  scene_destroy_impl(scene);
+  return MARS_OK;
+}
+
+mars_status mars_cache_create(const mars_scene* scene, const mars_cache_desc* desc, void* stream, mars_cache** out) {
+  return cache_create_impl(scene, desc, (cudaStream_t)stream, out);
+}
+
+mars_status mars_cache_destroy(mars_cache* cache) {
+  cache_destroy_impl(cache);
+  return MARS_OK;
+}
+
+mars_status mars_cache_info_get(const mars_cache* c, mars_cache_info* info) {
+  if (!c || !info) return set_error(MARS_ERR_INVALID_ARG, "null cache or info");
+  info->n_cells = c->cells;
+  info->n_pixels = c->pixels;
+  info->grid_n = c->grid_n;
+  info->techniques = c->techniques;
+  info->max_depth = c->max_depth;
+  info->n_prims = c->scene->n_prims;
+  info->arena_capacity = c->arena.cap;
+  info->device_bytes = c->device_bytes + c->scene->device_bytes;
+  info->device = c->device;
+  info->n_lights = c->scene->n_lights;
+  return MARS_OK;
+}
+
+mars_status mars_render_iteration(mars_cache* cache, const mars_iter_params* params, float* image_rgb,
+                                  mars_iter_stats* stats_host, void* stream) {
+  return render_iteration_impl(cache, params, image_rgb, stats_host, (cudaStream_t)stream);
+}
+
+mars_status mars_update_counts(mars_cache* cache, void* stream) {
+  return update_counts_impl(cache, (cudaStream_t)stream);
+}
+
+mars_status mars_cache_get_state(mars_cache* cache, mars_cache_state* state, void* stream) {
+  return get_state_impl(cache, state, (cudaStream_t)stream);
+}
+
+mars_status mars_cache_set_state(mars_cache* cache, const mars_cache_state* state, void* stream) {
+  return set_state_impl(cache, state, (cudaStream_t)stream);
+}
+
+const char* mars_last_error_string(void) { return g_last_error.c_str(); }
+
+const char* mars_version(void) { return "mars-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,99 @@
+// abi_internal.h -- host-side object layouts behind the opaque ABI handles.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <condition_variable>
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "internal.h"
+
+namespace mars {
+
+// Owned deep copy of a mars_scene_desc (the server keeps one per job).
+struct SceneDescCopy {
+  std::vector<double> quads, spheres, tris, materials;
+  std::vector<int32_t> quad_mat, sphere_mat, tri_mat;
+  mars_scene_desc desc{};
+  void assign(const mars_scene_desc* d) {
+    quads.assign(d->quads, d->quads + 9 * (size_t)d->n_quads);
+    spheres.assign(d->spheres, d->spheres + 4 * (size_t)d->n_spheres);
+    tris.assign(d->tris, d->tris + 9 * (size_t)d->n_tris);
+    materials.assign(d->materials, d->materials + 8 * (size_t)d->n_materials);
+    quad_mat.assign(d->quad_mat, d->quad_mat + d->n_quads);
+    sphere_mat.assign(d->sphere_mat, d->sphere_mat + d->n_spheres);
+    tri_mat.assign(d->tri_mat, d->tri_mat + d->n_tris);
+    desc = *d;
+    desc.quads = quads.data();
+    desc.spheres = spheres.data();
+    desc.tris = tris.data();
+    desc.materials = materials.data();
+    desc.quad_mat = quad_mat.data();
+    desc.sphere_mat = sphere_mat.data();
+    desc.tri_mat = tri_mat.data();
+  }
+};
+
+mars_status set_error(mars_status s, const char* fmt, ...);
+
+}  // namespace mars
+
+struct mars_scene {
+  int device = 0;
+  int num_sms = 0;
+  int width = 0, height = 0, n_prims = 0, n_lights = 0;
+  mars::DevScene ds{};
+  float4* d_prims = nullptr;
+  float4* d_boxes = nullptr;
+  mars::BvhNode* d_nodes = nullptr;
+  float4* d_mats = nullptr;
+  float4* d_lights = nullptr;
+  uint64_t device_bytes = 0;
+  mars::SceneDescCopy desc_copy;
+};
+
+struct mars_cache {
+  const mars_scene* scene = nullptr;
+  int device = 0;
+  int grid_n = 0, techniques = 0, max_depth = 0;
+  int64_t cells = 0, pixels = 0;
+  mars::Arena arena{};
+  mars::DevCache dc{};
+  float4* d_cnt = nullptr;
+  double* d_stats = nullptr;
+  float* d_hist = nullptr;
+  float* d_cdf = nullptr;
+  float4* d_est = nullptr;
+  float4* d_run = nullptr;
+  float4* d_img = nullptr;
+  mars::DevCounters* d_ctr = nullptr;
+  unsigned int* d_tile_status = nullptr;
+  mars::DevCounters* h_ctr = nullptr;
+  unsigned int* h_tile_status = nullptr;
+  int max_tiles = 0;
+  int next_tiles = 1;
+  int n_iterations = 0;
+  bool has_estimate = false;
+  bool poisoned = false;
+  double last_VI = 0.0, last_CI = 0.0;
+  uint64_t device_bytes = 0;
+  std::vector<cudaEvent_t> events;  // profiling events, grown on demand
+};
+
+namespace mars {
+mars_status scene_create_impl(const mars_scene_desc* d, cudaStream_t st, mars_scene** out);
+void scene_destroy_impl(mars_scene* s);
+mars_status cache_create_impl(const mars_scene* s, const mars_cache_desc* d, cudaStream_t st, mars_cache** out);
+void cache_destroy_impl(mars_cache* c);
+mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, float* image, mars_iter_stats* out,
+                                  cudaStream_t st);
+mars_status update_counts_impl(mars_cache* c, cudaStream_t st);
+uint64_t cache_footprint(int64_t cells, int64_t pixels, int max_depth, int techniques, uint64_t cap);
+uint64_t default_capacity(int64_t pixels, int max_depth);
+}  // namespace mars

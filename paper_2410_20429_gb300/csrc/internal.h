@@ -1,0 +1,128 @@
+// internal.h -- device data layout and launch wrappers shared by the CUDA
+// translation units of libmars (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "mars.h"
+
+namespace mars {
+
+constexpr int NT = MARS_NUM_SLOTS;
+constexpr int NSTAT = MARS_NUM_STATS;
+constexpr int GUIDE_BINS = MARS_GUIDE_BINS;
+constexpr int MAXD = MARS_MAX_DEPTH;
+constexpr uint32_t DIM_ROUND = 96;   // Philox dimension of the Alg. 1 draw
+constexpr uint32_t DIM_CAMERA = 97;  // Philox dimension of the pixel jitter
+
+// ---------------------------------------------------------------- scene
+// Primitive record: four float4 per primitive.
+//   w-bits of p[0]: (material << 2) | type   (type 0 quad, 1 sphere, 2 triangle)
+//   quad:     p0 | e1 | e2 | unit normal, w = light index (int bits, -1 if none)
+//   sphere:   centre | (r, 1/r, 0, 0) | - | -
+//   triangle: v0 | e1 = v1 - v0 | e2 = v2 - v0 | unit normal
+enum { PRIM_QUAD = 0, PRIM_SPHERE = 1, PRIM_TRI = 2 };
+
+// BVH node (Karras 2012 binary LBVH): the bounds of both children live in the
+// parent so one 64-byte fetch tests two boxes.
+//   a = (left lo xyz,  left child)   b = (left hi xyz,  right child)
+//   c = (right lo xyz, 0)            d = (right hi xyz, 0)
+// child >= 0: internal node index; child < 0: leaf holding primitive ~child.
+struct BvhNode {
+  float4 a, b, c, d;
+};
+
+// Material: m0 = (type, alpha, reflective, emissive), m1 = (colour rgb, 0),
+// m2 = (emitted radiance rgb, 0).
+// Light: l0 = (p0 xyz, cdf), l1 = (e1 xyz, pmf), l2 = (e2 xyz, area),
+//        l3 = (unit normal xyz, primitive index bits), l4 = (radiance rgb, 0).
+struct DevScene {
+  const float4* prims;
+  const BvhNode* nodes;
+  const float4* mats;
+  const float4* lights;
+  int n_prims, n_quads, n_lights, n_mats;
+  float lo[3], ext[3];
+  float eps;
+  float cam_o[3], cam_f[3], cam_r[3], cam_u[3];
+  float tanh_half, aspect;
+  int width, height;
+};
+
+// ---------------------------------------------------------------- arena
+// One arena for all depth waves of a tile; wave d occupies
+// [base[d], base[d] + count[d]).  Structure of arrays, one float4 per field
+// group so every load/store is a coalesced 16-byte access.
+//   R0 = (origin xyz, pixel)            R1 = (direction xyz, A = beta_t p_t)
+//   R2 = (T at the hit xyz, S_ind)      R3 = (f|cos|/p xyz, NEE weight factor)
+//   R4 = (lineage lo, lineage hi, parent cell, 1 / sum beta_k p_k)
+//   V0 = (E xyz, flags)                 V1 = (G xyz, first child)
+//   V2 = (NEE sum xyz, cell)            V3 = (NEE clamped sum xyz, beta_BSDF)
+//   V4 = (NEE clamped squares xyz, beta_NEE)
+//   V5 = (clamp limit xyz, beta_guided) V6 = (Le luminance, 1/S_beta, parent cell, bin)
+//   S  = (sample value xyz, cost)
+constexpr int NR = 5, NV = 7;
+struct Arena {
+  float4* R[NR];
+  float4* V[NV];
+  float4* S;
+  uint64_t cap;
+};
+
+// V0.w flag bits
+constexpr uint32_t F_TRACED = 1u << 24;
+constexpr uint32_t F_EST = 1u << 25;
+
+// Device-resident per-iteration counters.
+struct DevCounters {
+  unsigned long long base[MAXD + 2];
+  unsigned long long count[MAXD + 2];
+  unsigned int overflow;       // this tile overflowed the arena
+  unsigned int any_overflow;   // some tile of this iteration overflowed
+  unsigned long long demand;   // rays the tile needed (may exceed the arena)
+  unsigned long long rays, vertices, est_vertices;
+  unsigned long long entries;  // arena slots processed by committed tiles (all waves)
+  double sum_beta[NT];
+  double chsum[3];             // sum over pixels of the running mean (image stats)
+  double vi_sum;
+  double VI, CI;               // results of the last image-stats pass
+};
+
+struct DevCache {
+  int grid_n, n_cells, techniques, max_depth, bits;
+  int n_pixels;
+  float4* cnt;          // [cells][3][2]: (q_rr xyz, valid), (q_s xyz, 0)
+  double* stats;        // [cells][3][8]
+  float* guide_hist;    // [cells][256]
+  float* guide_cdf;     // [cells][256]
+  float4* est;          // [pixels] pixel estimate
+  float4* run_sum;      // [pixels]
+  float4* img;          // [pixels] this iteration's image
+  DevCounters* ctr;
+  unsigned int* tile_status;  // [max tiles] overflow per tile of the current attempt
+};
+
+struct IterArgs {
+  uint32_t seed, job, iteration;
+  int mode, aware, collect, has_estimate;
+  float clamp_lo, clamp_hi, outlier;
+  int tile_begin, tile_end, tile_slot;
+};
+
+// launch wrappers (render.cu)
+cudaError_t launch_tile(const DevScene& s, const DevCache& c, const Arena& a, const IterArgs& it,
+                        int num_sms, cudaStream_t st, cudaEvent_t* ev);
+constexpr int TILE_LAUNCHES_FIXED = 2;  // tile init + tile finish, besides 2 D wave kernels
+// image statistics (stats.cu)
+cudaError_t launch_image_stats(const DevCache& c, int width, int height, int n_prev, float outlier,
+                               float* image_out_dev, cudaStream_t st);
+cudaError_t launch_image_copy(const DevCache& c, int npix, float* out, cudaStream_t st);
+cudaError_t launch_update(const DevCache& c, int num_sms, cudaStream_t st);
+// scene build (scene.cu)
+cudaError_t build_bvh(const float4* d_prims, int n, const float lo[3], const float ext[3], BvhNode* d_nodes,
+                      cudaStream_t st, std::string* err);
+
+}  // namespace mars

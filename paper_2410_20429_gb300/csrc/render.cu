@@ -1,0 +1,510 @@
+// render.cu -- wavefront MARS path tracer: one shade kernel per depth wave and
+// one deepest-first reverse kernel per depth.
+//
+// Shade (wave d): trace the wave's rays (camera rays for d = 1), weight any
+// emission reached against NEE (multi-sample balance heuristic, Sec. 3.1), and
+// at each vertex x_d with d <= D-1 run the secondary estimator's sampling half:
+// counts beta_t from the cache (T(x)/I_px x q, three cases, clamp; Sec. 3.1
+// "Optimization", Sec. 4.1 "Outlier clamping" / "Handling colors"), Alg. 1,
+// NEE samples with their shadow rays, and BSDF / guided children appended to
+// wave d+1 with a warp-aggregated allocation.
+//
+// Reverse (wave d, deepest first): every ray's sample value
+//   <L_r,t> = f|cos|/p_t * (Le w_dir + w_ind <L_r(child vertex)>)
+// and cost (rays in its subtree, counting itself), the vertex's
+// <L_r> = sum_t 1/beta_t sum_s <L_r,t> (Sec. 3.1 "Secondary estimator"), and the
+// local statistics of Sec. 4.1 "Local estimates" (per cell and technique: n,
+// sum v, sum v^2, sum cost), pre-reduced over runs of equal cells in a warp
+// before float64 atomics.  A tile whose arena overflowed commits nothing.
+#include "device.cuh"
+
+namespace mars {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int SHADE_THREADS = 128;
+constexpr int REVERSE_THREADS = 128;
+
+__device__ __forceinline__ float4 f4(f3 a, float w) { return make_float4(a.x, a.y, a.z, w); }
+__device__ __forceinline__ f3 fmin3(f3 a, f3 b) { return mk3(fminf(a.x, b.x), fminf(a.y, b.y), fminf(a.z, b.z)); }
+
+// NEE density (solid angle at x) of reaching point y on light l along wi
+__device__ __forceinline__ float nee_pdf(const DevScene& s, int l, f3 x, f3 y, f3 wi) {
+  const float4 l1 = __ldg(s.lights + 5 * l + 1), l2 = __ldg(s.lights + 5 * l + 2), l3 = __ldg(s.lights + 5 * l + 3);
+  const float cosl = -dot(xyz(l3), wi);
+  if (cosl <= 0.0f) return 0.0f;
+  const f3 dv = y - x;
+  return l1.w * dot(dv, dv) / (l2.w * cosl);
+}
+
+__global__ void k_tile_init(DevCounters* ctr, unsigned long long n0) {
+  const int t = threadIdx.x;
+  if (t < MAXD + 2) {
+    ctr->base[t] = 0;
+    ctr->count[t] = (t == 1) ? n0 : 0ull;
+  }
+  if (t == 0) {
+    ctr->overflow = 0;
+    ctr->demand = n0;
+  }
+}
+
+__global__ void k_tile_finish(DevCounters* ctr, unsigned int* tile_status, int slot, int D) {
+  if (threadIdx.x != 0) return;
+  unsigned long long dem = 0;
+  for (int d = 1; d <= D; ++d) {
+    const unsigned long long e = ctr->base[d] + ctr->count[d];
+    dem = e > dem ? e : dem;
+  }
+  ctr->demand = dem;
+  if (!ctr->overflow) {
+    unsigned long long tot = 0;
+    for (int d = 1; d <= D; ++d) tot += ctr->count[d];
+    ctr->entries += tot;
+  }
+  tile_status[slot] = ctr->overflow;
+  if (ctr->overflow) ctr->any_overflow = 1;
+}
+
+__global__ void __launch_bounds__(SHADE_THREADS) k_shade(const DevScene s, const DevCache c, const Arena a,
+                                                         const IterArgs it, const int d) {
+  DevCounters* ctr = c.ctr;
+  // after an overflow some slots of this wave were never written: stop here,
+  // the tile is re-rendered in smaller pieces
+  if (ctr->overflow) return;
+  const unsigned long long base = ctr->base[d];
+  const unsigned long long cnt = ctr->count[d];
+  const unsigned long long n = cnt < a.cap - base ? cnt : a.cap - base;
+  const unsigned long long base_next = base + cnt < a.cap ? base + cnt : a.cap;
+  if (blockIdx.x == 0 && threadIdx.x == 0) ctr->base[d + 1] = base_next;
+
+  const int lane = threadIdx.x & 31;
+  const unsigned long long gw = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
+  const unsigned long long nw = (gridDim.x * (unsigned long long)blockDim.x) >> 5;
+  const int D = c.max_depth;
+  const bool est_depth = d <= D - 1;
+  const bool camera = d == 1;
+  const bool on_b = c.techniques & MARS_TECH_BSDF, on_n = c.techniques & MARS_TECH_NEE,
+             on_g = c.techniques & MARS_TECH_GUIDED;
+  const Rng rng{it.seed, it.job, it.iteration};
+  const float inf = __int_as_float(0x7f800000);
+
+  for (unsigned long long c0 = gw * 32; c0 < n; c0 += nw * 32) {
+    const unsigned long long li = c0 + lane;
+    const bool active = li < n;
+    const unsigned long long i = base + li;
+
+    // ---- the ray of this slot
+    f3 o = mk3(0.f, 0.f, 0.f), dir = mk3(0.f, 0.f, 1.f), T = mk3(1.f, 1.f, 1.f), fcp = mk3(1.f, 1.f, 1.f);
+    float A = 1.0f, S_ind = 1.0f, bwN = 0.0f, invSb = 0.0f;
+    uint64_t lin = 0;
+    uint32_t px = 0, parent_cell = 0;
+    if (active) {
+      if (camera) {
+        px = (uint32_t)(it.tile_begin + li);
+        const float4 u = rng.u4(px, DIM_CAMERA, 0);
+        const int ix = (int)(px % (uint32_t)s.width), iy = (int)(px / (uint32_t)s.width);
+        const float sx = (2.0f * ((float)ix + u.x) / (float)s.width - 1.0f) * s.tanh_half * s.aspect;
+        const float sy = (1.0f - 2.0f * ((float)iy + u.y) / (float)s.height) * s.tanh_half;
+        const f3 cf = mk3(s.cam_f[0], s.cam_f[1], s.cam_f[2]);
+        const f3 cr = mk3(s.cam_r[0], s.cam_r[1], s.cam_r[2]);
+        const f3 cu = mk3(s.cam_u[0], s.cam_u[1], s.cam_u[2]);
+        dir = normalize(cf + (cr * sx + cu * sy));
+        o = mk3(s.cam_o[0], s.cam_o[1], s.cam_o[2]);
+      } else {
+        const float4 r0 = a.R[0][i], r1 = a.R[1][i], r2 = a.R[2][i], r3 = a.R[3][i], r4 = a.R[4][i];
+        o = xyz(r0);
+        px = __float_as_uint(r0.w);
+        dir = xyz(r1);
+        A = r1.w;
+        T = xyz(r2);
+        S_ind = r2.w;
+        fcp = xyz(r3);
+        bwN = r3.w;
+        lin = (uint64_t)__float_as_uint(r4.x) | ((uint64_t)__float_as_uint(r4.y) << 32);
+        parent_cell = __float_as_uint(r4.z);
+        invSb = r4.w;
+      }
+    }
+    const bool alive = active && (camera || A > 0.0f);
+
+    // ---- closest hit and emission
+    f3 E = mk3(0.f, 0.f, 0.f);
+    float Le_lum = 0.0f;
+    const f3 G = camera ? mk3(1.f, 1.f, 1.f) : (S_ind > 0.0f ? fcp * (A / S_ind) : mk3(0.f, 0.f, 0.f));
+    uint32_t flags = 0;
+    int n_ext = 0;
+    int gam[NT] = {0, 0, 0};
+    float beta[NT] = {0.f, 0.f, 0.f};
+    int cell = 0;
+    f3 p, ns, wo, nsum = mk3(0.f, 0.f, 0.f), nm1 = mk3(0.f, 0.f, 0.f), nm2 = mk3(0.f, 0.f, 0.f);
+    f3 climit = mk3(inf, inf, inf);
+    Frame fr;
+    Mat mat;
+    const float* cdf = nullptr;
+    if (alive) {
+      flags |= F_TRACED;
+      float th;
+      const int prim = trace_closest(s, o, dir, th);
+      if (prim >= 0) {
+        p = o + dir * th;
+        const f3 ng = prim_normal(s.prims, prim, p);
+        wo = dir * -1.0f;
+        const int m = prim_material(s.prims, prim);
+        const float4 m0 = __ldg(s.mats + 3 * m), m1 = __ldg(s.mats + 3 * m + 1), m2 = __ldg(s.mats + 3 * m + 2);
+        const float cosg = dot(ng, wo);
+        if (cosg > 0.0f && m0.w > 0.0f) {
+          float w_dir = 1.0f;
+          if (!camera) {
+            float pn = 0.0f;
+            if (bwN > 0.0f && prim < s.n_quads) {
+              const int l = __float_as_int(__ldg(&s.prims[4 * prim + 3].w));
+              if (l >= 0) pn = nee_pdf(s, l, o, p, dir);
+            }
+            const float den = S_ind + bwN * pn;
+            w_dir = den > 0.0f ? A / den : 0.0f;
+          }
+          const f3 Le = xyz(m2);
+          E = mul(fcp, Le * w_dir);
+          Le_lum = lum(Le);
+        }
+        if (est_depth && m0.z > 0.0f) {
+          // ---- secondary estimator at x_d: budgets, Alg. 1, NEE, children
+          flags |= F_EST;
+          ns = cosg >= 0.0f ? ng : ng * -1.0f;
+          fr = make_frame(ns);
+          cell = cell_of(s, c.grid_n, p);
+          mat.type = (int)m0.x;
+          mat.alpha = m0.y;
+          mat.col = xyz(m1);
+          const float4 est = it.has_estimate ? c.est[px] : make_float4(1.f, 1.f, 1.f, 0.f);
+          if (it.collect && it.has_estimate) {
+            climit.x = T.x > 0.0f ? it.outlier * est.x / T.x : inf;
+            climit.y = T.y > 0.0f ? it.outlier * est.y / T.y : inf;
+            climit.z = T.z > 0.0f ? it.outlier * est.z / T.z : inf;
+          }
+          // counts without learned statistics: one NEE sample and one
+          // continuation sample split evenly over BSDF and guided sampling
+          const float base_cont = (on_b && on_g) ? 0.5f : 1.0f;
+#pragma unroll
+          for (int t = 0; t < NT; ++t) {
+            const bool on = (c.techniques >> t) & 1;
+            float b = on ? (t == 1 ? 1.0f : base_cont) : 0.0f;
+            if (on && it.mode == MARS_MODE_MARS) {
+              const float4 qr = __ldg(c.cnt + (2 * (NT * cell + t)));
+              if (qr.w > 0.0f) {
+                const float4 qs = __ldg(c.cnt + (2 * (NT * cell + t) + 1));
+                const f3 f = mk3(T.x / est.x, T.y / est.y, T.z / est.z);
+                const f3 ar = mul(f, xyz(qr)), as = mul(f, xyz(qs));
+                const float brr = sqrtf(dot(ar, ar) / 3.0f), bs = sqrtf(dot(as, as) / 3.0f);
+                b = brr < 1.0f ? brr : (bs > 1.0f ? bs : 1.0f);
+                b = fminf(fmaxf(b, it.clamp_lo), it.clamp_hi);
+              }
+            }
+            beta[t] = b;
+          }
+          // Alg. 1: one uniform decides the rounding of every technique
+          float r = rng.u4(px, DIM_ROUND, lin).x;
+#pragma unroll
+          for (int t = 0; t < NT; ++t) {
+            if (!((c.techniques >> t) & 1)) continue;
+            const float sm = beta[t] + r;
+            const int g = (int)floorf(sm);
+            gam[t] = g;
+            r = sm - (float)g;
+          }
+          const float bwB = on_b ? (it.aware ? beta[0] : 1.0f) : 0.0f;
+          const float bwNv = on_n ? (it.aware ? beta[1] : 1.0f) : 0.0f;
+          const float bwG = on_g ? (it.aware ? beta[2] : 1.0f) : 0.0f;
+          if (on_g) cdf = c.guide_cdf + (size_t)cell * GUIDE_BINS;
+          const f3 wol = fr.to_local(wo);
+          const f3 xo = p + ns * s.eps;
+          // NEE samples (primary estimator of NEE), traced here
+          for (int sidx = 0; sidx < gam[1]; ++sidx) {
+            const float4 u = rng.u4(px, 32u + (uint32_t)sidx, lin);
+            int l = s.n_lights - 1;
+            for (int k = 0; k < s.n_lights; ++k)
+              if (u.x < __ldg(&s.lights[5 * k].w)) { l = k; break; }
+            const float4 l0 = __ldg(s.lights + 5 * l), l1 = __ldg(s.lights + 5 * l + 1),
+                         l2 = __ldg(s.lights + 5 * l + 2), l4 = __ldg(s.lights + 5 * l + 4);
+            const f3 y = xyz(l0) + (xyz(l1) * u.y + xyz(l2) * u.z);
+            const f3 dv = y - xo;
+            const float dist = sqrtf(dot(dv, dv));
+            const f3 wi = dv * (1.0f / dist);
+            const float pn = nee_pdf(s, l, xo, y, wi);
+            const float ci = dot(ns, wi);
+            f3 v = mk3(0.f, 0.f, 0.f);
+            if (pn > 0.0f && ci > 0.0f) {
+              float pb;
+              const f3 fc = bsdf_eval(mat, wol, fr.to_local(wi), pb);
+              const float pg = on_g ? guide_pdf(cdf, wi) : 0.0f;
+              if (nonzero(fc) && !trace_any(s, xo, wi, dist - s.eps)) {
+                const float den = bwB * pb + bwG * pg + bwNv * pn;
+                const float w = bwNv * pn / den;
+                v = mk3(fc.x * l4.x / pn * w, fc.y * l4.y / pn * w, fc.z * l4.z / pn * w);
+              }
+            }
+            nsum = nsum + v;
+            const f3 vc = fmin3(v, climit);
+            nm1 = nm1 + vc;
+            nm2 = nm2 + mul(vc, vc);
+          }
+          n_ext = gam[0] + gam[2];
+        }
+      }
+    }
+
+    // ---- warp-aggregated allocation of the children in wave d+1
+    int incl = n_ext;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int y = __shfl_up_sync(FULL, incl, off);
+      if (lane >= off) incl += y;
+    }
+    const int total = __shfl_sync(FULL, incl, 31);
+    unsigned long long wbase = 0;
+    if (total > 0) {
+      if (lane == 31) wbase = atomicAdd(&ctr->count[d + 1], (unsigned long long)total);
+      wbase = __shfl_sync(FULL, wbase, 31);
+    }
+    const unsigned long long first = base_next + wbase + (unsigned long long)(incl - n_ext);
+    const bool fits = first + (unsigned long long)n_ext <= a.cap;
+    if (n_ext > 0 && !fits) atomicOr(&ctr->overflow, 1u);
+
+    if (n_ext > 0 && fits) {
+      const float bwB = on_b ? (it.aware ? beta[0] : 1.0f) : 0.0f;
+      const float bwNv = on_n ? (it.aware ? beta[1] : 1.0f) : 0.0f;
+      const float bwG = on_g ? (it.aware ? beta[2] : 1.0f) : 0.0f;
+      const f3 wol = fr.to_local(wo);
+      const f3 xo = p + ns * s.eps;
+      for (int k = 0; k < n_ext; ++k) {
+        const int t = k < gam[0] ? 0 : 2;
+        const int sidx = t == 0 ? k : k - gam[0];
+        const float4 u = rng.u4(px, (uint32_t)(t * 32 + sidx), lin);
+        f3 wi = mk3(0.f, 0.f, 1.f);
+        bool ok;
+        float pt = 0.0f;
+        if (t == 0) {
+          f3 wl;
+          ok = bsdf_sample(mat, wol, u.x, u.y, wl);
+          if (ok) wi = fr.to_world(wl);
+        } else {
+          const int b = guide_pick(cdf, u.x);
+          wi = guide_dir(b, u.y, u.z);
+          pt = guide_bin_prob(cdf, b) * (GUIDE_BINS / (4.0f * PI_F));
+          ok = dot(wi, ns) > 0.0f;
+        }
+        float cA = 0.0f, cS = 0.0f, cinvSb = 0.0f;
+        f3 cf = mk3(0.f, 0.f, 0.f), cT = mk3(0.f, 0.f, 0.f);
+        if (ok) {
+          float pb;
+          const f3 fc = bsdf_eval(mat, wol, fr.to_local(wi), pb);
+          const float pg = on_g ? guide_pdf(cdf, wi) : 0.0f;
+          if (t == 0) pt = pb;
+          if (pt > 0.0f && nonzero(fc)) {
+            cf = mk3(fc.x / pt, fc.y / pt, fc.z / pt);
+            cA = (t == 0 ? bwB : bwG) * pt;
+            cS = bwB * pb + bwG * pg;
+            const float w_ind = cA / cS;
+            cT = mk3(T.x * cf.x * w_ind / beta[t], T.y * cf.y * w_ind / beta[t], T.z * cf.z * w_ind / beta[t]);
+            const float sb = beta[0] * pb + (on_g ? beta[2] * pg : 0.0f);
+            cinvSb = sb > 0.0f ? 1.0f / sb : 0.0f;
+          }
+        }
+        const uint64_t digit = (uint64_t)(t == 0 ? sidx + 1 : 32 + sidx + 1);
+        const uint64_t clin = (lin << c.bits) | digit;
+        const unsigned long long j = first + k;
+        a.R[0][j] = f4(xo, __uint_as_float(px));
+        a.R[1][j] = f4(wi, cA);
+        a.R[2][j] = f4(cT, cS);
+        a.R[3][j] = f4(cf, bwNv);
+        a.R[4][j] = make_float4(__uint_as_float((uint32_t)clin), __uint_as_float((uint32_t)(clin >> 32)),
+                                __uint_as_float((uint32_t)cell), cinvSb);
+      }
+    }
+
+    // ---- vertex record of this slot
+    if (active) {
+      flags |= (uint32_t)gam[0] | ((uint32_t)gam[1] << 8) | ((uint32_t)gam[2] << 16);
+      a.V[0][i] = f4(E, __uint_as_float(flags));
+      a.V[1][i] = f4(G, __uint_as_float((uint32_t)(fits ? first : 0ull)));
+      if (flags & F_EST) {
+        a.V[2][i] = f4(nsum, __uint_as_float((uint32_t)cell));
+        a.V[3][i] = f4(nm1, beta[0]);
+        a.V[4][i] = f4(nm2, beta[1]);
+        a.V[5][i] = f4(climit, beta[2]);
+      }
+      if (on_g && it.collect && !camera && (flags & F_TRACED))
+        a.V[6][i] = make_float4(Le_lum, invSb, __uint_as_float(parent_cell), __int_as_float(guide_bin(dir)));
+    }
+  }
+}
+
+// inclusive scan restricted to runs of equal keys (start = first lane of the run)
+__device__ __forceinline__ float seg_scan(float v, int lane, int start) {
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const float u = __shfl_up_sync(FULL, v, off);
+    if (lane - off >= start) v += u;
+  }
+  return v;
+}
+
+__global__ void __launch_bounds__(REVERSE_THREADS) k_reverse(const DevScene s, const DevCache c, const Arena a,
+                                                             const IterArgs it, const int d) {
+  DevCounters* ctr = c.ctr;
+  if (ctr->overflow) return;  // the tile is re-rendered; commit nothing
+  const unsigned long long base = ctr->base[d];
+  const unsigned long long cnt = ctr->count[d];
+  const unsigned long long n = cnt < a.cap - base ? cnt : a.cap - base;
+  const int lane = threadIdx.x & 31;
+  const unsigned long long gw = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
+  const unsigned long long nw = (gridDim.x * (unsigned long long)blockDim.x) >> 5;
+  const bool on_n = c.techniques & MARS_TECH_NEE, on_g = c.techniques & MARS_TECH_GUIDED;
+  const bool collect = it.collect != 0;
+
+  for (unsigned long long c0 = gw * 32; c0 < n; c0 += nw * 32) {
+    const unsigned long long li = c0 + lane;
+    const bool active = li < n;
+    const unsigned long long i = base + li;
+    uint32_t flags = 0;
+    f3 E = mk3(0.f, 0.f, 0.f), Lr = mk3(0.f, 0.f, 0.f);
+    uint32_t csub = 0;
+    uint32_t key = 0xffffffffu;
+    float st[NT][NSTAT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t)
+#pragma unroll
+      for (int k = 0; k < NSTAT; ++k) st[t][k] = 0.0f;
+    float bt[NT] = {0.f, 0.f, 0.f};
+    if (active) {
+      const float4 v0 = a.V[0][i];
+      E = xyz(v0);
+      flags = __float_as_uint(v0.w);
+      if (flags & F_EST) {
+        const float4 v1 = a.V[1][i], v3 = a.V[3][i], v4 = a.V[4][i], v5 = a.V[5][i];
+        const int gB = flags & 0xff, gN = (flags >> 8) & 0xff, gG = (flags >> 16) & 0xff;
+        bt[0] = v3.w; bt[1] = v4.w; bt[2] = v5.w;
+        const f3 climit = xyz(v5);
+        const unsigned long long first = __float_as_uint(v1.w);
+        const float4 v2 = a.V[2][i];
+        key = __float_as_uint(v2.w);
+        if (gN > 0) {
+          Lr = mk3(v2.x / bt[1], v2.y / bt[1], v2.z / bt[1]);
+          csub += (uint32_t)gN;
+          st[1][0] = (float)gN;
+          st[1][1] = v3.x; st[1][2] = v3.y; st[1][3] = v3.z;
+          st[1][4] = v4.x; st[1][5] = v4.y; st[1][6] = v4.z;
+          st[1][7] = (float)gN;
+        }
+        const int ne = gB + gG;
+        for (int k = 0; k < ne; ++k) {
+          const float4 sv = a.S[first + k];
+          const int t = k < gB ? 0 : 2;
+          const float b = bt[t];
+          Lr = Lr + mk3(sv.x / b, sv.y / b, sv.z / b);
+          const uint32_t cc = __float_as_uint(sv.w);
+          csub += cc;
+          const f3 vc = fmin3(xyz(sv), climit);
+          if (t == 0) {
+            st[0][0] += 1.0f; st[0][1] += vc.x; st[0][2] += vc.y; st[0][3] += vc.z;
+            st[0][4] += vc.x * vc.x; st[0][5] += vc.y * vc.y; st[0][6] += vc.z * vc.z; st[0][7] += (float)cc;
+          } else {
+            st[2][0] += 1.0f; st[2][1] += vc.x; st[2][2] += vc.y; st[2][3] += vc.z;
+            st[2][4] += vc.x * vc.x; st[2][5] += vc.y * vc.y; st[2][6] += vc.z * vc.z; st[2][7] += (float)cc;
+          }
+        }
+        const f3 G = xyz(v1);
+        E = E + mul(G, Lr);
+      }
+      const uint32_t cost = 1u + csub;
+      a.S[i] = f4(E, __uint_as_float(cost));
+      if (d == 1) c.img[it.tile_begin + li] = f4(E, 0.0f);
+      if (on_g && collect && d >= 2 && (flags & F_TRACED)) {
+        const float4 v6 = a.V[6][i];
+        const float w = (v6.x + lum(Lr)) * v6.y;
+        if (w > 0.0f)
+          atomicAdd(c.guide_hist + (size_t)__float_as_uint(v6.z) * GUIDE_BINS + __float_as_int(v6.w), w);
+      }
+    }
+
+    // ---- iteration counters (one atomic per warp)
+    {
+      const unsigned traced = __ballot_sync(FULL, active && (flags & F_TRACED));
+      const unsigned estv = __ballot_sync(FULL, active && (flags & F_EST));
+      double rays = (active && d == 1) ? (double)(1u + csub) : 0.0;
+      float sb0 = bt[0], sb1 = bt[1], sb2 = bt[2];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        if (d == 1) rays += __shfl_xor_sync(FULL, rays, off);
+        sb0 += __shfl_xor_sync(FULL, sb0, off);
+        sb1 += __shfl_xor_sync(FULL, sb1, off);
+        sb2 += __shfl_xor_sync(FULL, sb2, off);
+      }
+      if (lane == 0) {
+        if (traced) atomicAdd(&ctr->vertices, (unsigned long long)__popc(traced));
+        if (estv) {
+          atomicAdd(&ctr->est_vertices, (unsigned long long)__popc(estv));
+          atomicAdd(&ctr->sum_beta[0], (double)sb0);
+          if (on_n) atomicAdd(&ctr->sum_beta[1], (double)sb1);
+          if (on_g) atomicAdd(&ctr->sum_beta[2], (double)sb2);
+        }
+        if (rays > 0.0) atomicAdd(&ctr->rays, (unsigned long long)rays);
+      }
+    }
+
+    // ---- local statistics: reduce runs of equal cells, then float64 atomics
+    if (collect) {
+      const unsigned any = __ballot_sync(FULL, key != 0xffffffffu);
+      if (any) {
+        const uint32_t prev = __shfl_up_sync(FULL, key, 1);
+        const bool head = lane == 0 || prev != key;
+        const unsigned heads = __ballot_sync(FULL, head);
+        const unsigned below = lane == 31 ? FULL : ((2u << lane) - 1u);
+        const int start = 31 - __clz(heads & below);
+        const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+          if (!((c.techniques >> t) & 1)) continue;
+#pragma unroll
+          for (int k = 0; k < NSTAT; ++k) st[t][k] = seg_scan(st[t][k], lane, start);
+        }
+        if (tail && key != 0xffffffffu) {
+          double* dst = c.stats + (size_t)key * NT * NSTAT;
+#pragma unroll
+          for (int t = 0; t < NT; ++t) {
+            if (!((c.techniques >> t) & 1) || st[t][0] <= 0.0f) continue;
+#pragma unroll
+            for (int k = 0; k < NSTAT; ++k) atomicAdd(dst + t * NSTAT + k, (double)st[t][k]);
+          }
+        }
+      }
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_tile(const DevScene& s, const DevCache& c, const Arena& a, const IterArgs& it, int num_sms,
+                        cudaStream_t st, cudaEvent_t* ev) {
+  const unsigned long long n0 = (unsigned long long)(it.tile_end - it.tile_begin);
+  k_tile_init<<<1, 32, 0, st>>>(c.ctr, n0);
+  const int D = c.max_depth;
+  const int gshade = num_sms * 8, grev = num_sms * 8;
+  // ev (optional): ev[0] before the first shade kernel, ev[d] after shade d,
+  // ev[D + k] after the k-th reverse kernel
+  if (ev) cudaEventRecord(ev[0], st);
+  for (int d = 1; d <= D; ++d) {
+    k_shade<<<gshade, SHADE_THREADS, 0, st>>>(s, c, a, it, d);
+    if (ev) cudaEventRecord(ev[d], st);
+  }
+  for (int d = D; d >= 1; --d) {
+    k_reverse<<<grev, REVERSE_THREADS, 0, st>>>(s, c, a, it, d);
+    if (ev) cudaEventRecord(ev[D + (D - d + 1)], st);
+  }
+  k_tile_finish<<<1, 32, 0, st>>>(c.ctr, c.tile_status, it.tile_slot, D);
+  return cudaGetLastError();
+}
+
+}  // namespace mars

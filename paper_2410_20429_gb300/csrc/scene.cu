@@ -1,0 +1,181 @@
+// scene.cu -- linear BVH construction on the device (Karras, "Maximizing
+// Parallelism in the Construction of BVHs, Octrees, and k-d Trees", HPG 2012):
+// 30-bit Morton codes of the primitive centroids with the primitive index as a
+// tie-breaking low word, a bitonic sort, one thread per internal node to find
+// its key range and split, and a bottom-up pass that fills the child bounds
+// (the second thread to reach a node computes it).
+#include <string>
+
+#include "internal.h"
+
+namespace mars {
+
+namespace {
+
+__device__ __forceinline__ uint32_t spread10(uint32_t v) {
+  v = (v * 0x00010001u) & 0xFF0000FFu;
+  v = (v * 0x00000101u) & 0x0F00F00Fu;
+  v = (v * 0x00000011u) & 0xC30C30C3u;
+  v = (v * 0x00000005u) & 0x49249249u;
+  return v;
+}
+
+// keys[i] = morton(centroid) << 32 | i ; padding keys are all ones
+__global__ void k_morton(const float4* __restrict__ box, int n, int npow, float lo0, float lo1, float lo2,
+                         float ie0, float ie1, float ie2, unsigned long long* keys) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npow) return;
+  if (i >= n) {
+    keys[i] = ~0ull;
+    return;
+  }
+  const float4 blo = box[2 * i], bhi = box[2 * i + 1];
+  const float c[3] = {0.5f * (blo.x + bhi.x), 0.5f * (blo.y + bhi.y), 0.5f * (blo.z + bhi.z)};
+  const float lo[3] = {lo0, lo1, lo2}, ie[3] = {ie0, ie1, ie2};
+  uint32_t q[3];
+  for (int a = 0; a < 3; ++a) {
+    float f = (c[a] - lo[a]) * ie[a] * 1024.0f;
+    f = fminf(fmaxf(f, 0.0f), 1023.0f);
+    q[a] = (uint32_t)f;
+  }
+  const uint32_t m = (spread10(q[0]) << 2) | (spread10(q[1]) << 1) | spread10(q[2]);
+  keys[i] = ((unsigned long long)m << 32) | (unsigned long long)i;
+}
+
+__global__ void k_bitonic(unsigned long long* keys, int npow, int j, int k) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npow) return;
+  const int l = i ^ j;
+  if (l <= i) return;
+  const unsigned long long a = keys[i], b = keys[l];
+  const bool up = (i & k) == 0;
+  if ((up && a > b) || (!up && a < b)) {
+    keys[i] = b;
+    keys[l] = a;
+  }
+}
+
+__device__ __forceinline__ int delta(const unsigned long long* k, int n, int i, int j) {
+  if (j < 0 || j >= n) return -1;
+  return __clzll(k[i] ^ k[j]);
+}
+
+// internal node i of n-1: children encoded as internal index (>= 0) or ~leaf slot
+__global__ void k_hierarchy(const unsigned long long* __restrict__ keys, int n, int2* child, int* parent_int,
+                            int* parent_leaf) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n - 1) return;
+  const int dsign = (delta(keys, n, i, i + 1) - delta(keys, n, i, i - 1)) >= 0 ? 1 : -1;
+  const int dmin = delta(keys, n, i, i - dsign);
+  int lmax = 2;
+  while (delta(keys, n, i, i + lmax * dsign) > dmin) lmax <<= 1;
+  int l = 0;
+  for (int t = lmax >> 1; t >= 1; t >>= 1)
+    if (delta(keys, n, i, i + (l + t) * dsign) > dmin) l += t;
+  const int j = i + l * dsign;
+  const int dnode = delta(keys, n, i, j);
+  int s = 0;
+  int t = l;
+  do {
+    t = (t + 1) >> 1;
+    if (delta(keys, n, i, i + (s + t) * dsign) > dnode) s += t;
+  } while (t > 1);
+  const int gamma = i + s * dsign + (dsign < 0 ? -1 : 0);
+  const int lo = i < j ? i : j, hi = i < j ? j : i;
+  const int left = (lo == gamma) ? ~gamma : gamma;
+  const int right = (hi == gamma + 1) ? ~(gamma + 1) : gamma + 1;
+  child[i] = make_int2(left, right);
+  if (left < 0) parent_leaf[~left] = i; else parent_int[left] = i;
+  if (right < 0) parent_leaf[~right] = i; else parent_int[right] = i;
+  if (i == 0) parent_int[0] = -1;
+}
+
+__device__ __forceinline__ void get_box(int c, const float4* __restrict__ leaf_box,
+                                        const unsigned long long* __restrict__ keys, const float4* ibox,
+                                        float4& lo, float4& hi) {
+  if (c < 0) {
+    const int prim = (int)(keys[~c] & 0xffffffffull);
+    lo = leaf_box[2 * prim];
+    hi = leaf_box[2 * prim + 1];
+  } else {
+    lo = __ldcg(ibox + 2 * c);  // L2-coherent: written by another thread of this kernel
+    hi = __ldcg(ibox + 2 * c + 1);
+  }
+}
+
+__global__ void k_refit(const float4* __restrict__ leaf_box, const unsigned long long* __restrict__ keys, int n,
+                        const int2* __restrict__ child, const int* __restrict__ parent_int,
+                        const int* __restrict__ parent_leaf, unsigned int* flags, float4* ibox, BvhNode* nodes) {
+  const int leaf = blockIdx.x * blockDim.x + threadIdx.x;
+  if (leaf >= n) return;
+  int node = parent_leaf[leaf];
+  // a tree over unique 62-bit keys is at most 63 levels deep; the bound keeps
+  // a malformed hierarchy from looping
+  for (int guard = 0; node >= 0 && guard < 128; ++guard) {
+    __threadfence();
+    if (atomicAdd(&flags[node], 1u) == 0) return;  // the sibling's thread finishes this node
+    __threadfence();
+    const int2 ch = child[node];
+    float4 llo, lhi, rlo, rhi;
+    get_box(ch.x, leaf_box, keys, ibox, llo, lhi);
+    get_box(ch.y, leaf_box, keys, ibox, rlo, rhi);
+    const int lc = ch.x < 0 ? ~(int)(keys[~ch.x] & 0xffffffffull) : ch.x;
+    const int rc = ch.y < 0 ? ~(int)(keys[~ch.y] & 0xffffffffull) : ch.y;
+    BvhNode nd;
+    nd.a = make_float4(llo.x, llo.y, llo.z, __int_as_float(lc));
+    nd.b = make_float4(lhi.x, lhi.y, lhi.z, __int_as_float(rc));
+    nd.c = make_float4(rlo.x, rlo.y, rlo.z, 0.0f);
+    nd.d = make_float4(rhi.x, rhi.y, rhi.z, 0.0f);
+    nodes[node] = nd;
+    __stcg(ibox + 2 * node, make_float4(fminf(llo.x, rlo.x), fminf(llo.y, rlo.y), fminf(llo.z, rlo.z), 0.0f));
+    __stcg(ibox + 2 * node + 1, make_float4(fmaxf(lhi.x, rhi.x), fmaxf(lhi.y, rhi.y), fmaxf(lhi.z, rhi.z), 0.0f));
+    node = parent_int[node];
+  }
+}
+
+}  // namespace
+
+// d_box: [n][2] float4 (lo, hi) per primitive, already padded.
+cudaError_t build_bvh(const float4* d_box, int n, const float lo[3], const float ext[3], BvhNode* d_nodes,
+                      cudaStream_t st, std::string* err) {
+  if (n < 2) return cudaSuccess;
+  int npow = 1;
+  while (npow < n) npow <<= 1;
+  unsigned long long* keys = nullptr;
+  int2* child = nullptr;
+  int *pint = nullptr, *pleaf = nullptr;
+  unsigned int* flags = nullptr;
+  float4* ibox = nullptr;
+  cudaError_t e = cudaSuccess;
+  auto fail = [&](const char* what) {
+    if (err) *err = std::string("BVH build: ") + what + ": " + cudaGetErrorString(e);
+  };
+  do {
+    if ((e = cudaMallocAsync(&keys, sizeof(unsigned long long) * npow, st)) != cudaSuccess) { fail("alloc"); break; }
+    if ((e = cudaMallocAsync(&child, sizeof(int2) * (n - 1), st)) != cudaSuccess) { fail("alloc"); break; }
+    if ((e = cudaMallocAsync(&pint, sizeof(int) * (n - 1), st)) != cudaSuccess) { fail("alloc"); break; }
+    if ((e = cudaMallocAsync(&pleaf, sizeof(int) * n, st)) != cudaSuccess) { fail("alloc"); break; }
+    if ((e = cudaMallocAsync(&flags, sizeof(unsigned int) * (n - 1), st)) != cudaSuccess) { fail("alloc"); break; }
+    if ((e = cudaMallocAsync(&ibox, sizeof(float4) * 2 * (n - 1), st)) != cudaSuccess) { fail("alloc"); break; }
+    cudaMemsetAsync(flags, 0, sizeof(unsigned int) * (n - 1), st);
+    const int TB = 256;
+    const float ie[3] = {1.0f / ext[0], 1.0f / ext[1], 1.0f / ext[2]};
+    k_morton<<<(npow + TB - 1) / TB, TB, 0, st>>>(d_box, n, npow, lo[0], lo[1], lo[2], ie[0], ie[1], ie[2], keys);
+    for (int k = 2; k <= npow; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1) k_bitonic<<<(npow + TB - 1) / TB, TB, 0, st>>>(keys, npow, j, k);
+    k_hierarchy<<<(n - 1 + TB - 1) / TB, TB, 0, st>>>(keys, n, child, pint, pleaf);
+    k_refit<<<(n + TB - 1) / TB, TB, 0, st>>>(d_box, keys, n, child, pint, pleaf, flags, ibox, d_nodes);
+    if ((e = cudaGetLastError()) != cudaSuccess) { fail("launch"); break; }
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) { fail("run"); break; }
+  } while (false);
+  if (keys) cudaFreeAsync(keys, st);
+  if (child) cudaFreeAsync(child, st);
+  if (pint) cudaFreeAsync(pint, st);
+  if (pleaf) cudaFreeAsync(pleaf, st);
+  if (flags) cudaFreeAsync(flags, st);
+  if (ibox) cudaFreeAsync(ibox, st);
+  cudaStreamSynchronize(st);
+  return e;
+}
+
+}  // namespace mars

@@ -1,0 +1,232 @@
+// server.cu -- continuous-batching render server behind mars_submit / mars_poll.
+//
+// A scheduler thread admits queued jobs in arrival order while the sum of the
+// resident jobs' device footprints stays within the memory budget and a slot
+// is free.  Every admitted job gets a worker thread with its own CUDA stream,
+// so the iterations of resident jobs overlap on the device; a job's scene,
+// cache, queues and image stay resident on the device across its fixed-point
+// iterations and are freed when it finishes, which admits the next job.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <deque>
+
+#include "abi_internal.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Job {
+  uint64_t id = 0;
+  mars::SceneDescCopy scene;
+  mars_cache_desc cache{};
+  uint32_t seed = 0;
+  int iterations = 0, warmup = 0;
+  uint64_t footprint = 0;
+  mars_job_state state = MARS_JOB_QUEUED;
+  int done_iters = 0;
+  mars_status error = MARS_OK;
+  std::string message;
+  double submit_s = 0, start_s = 0, end_s = 0;
+  std::vector<double> iter_ms;
+  std::vector<float> image;  // mean over post-warm-up iterations
+  std::thread worker;
+};
+
+}  // namespace
+
+struct mars_server {
+  uint64_t budget = 0;
+  int max_slots = 1;
+  int device = 0;
+  Clock::time_point t0;
+  std::mutex mu;
+  std::condition_variable cv;
+  bool stop = false;
+  uint64_t next_id = 1;
+  uint64_t in_use = 0;
+  int resident = 0;
+  std::deque<uint64_t> queue;
+  std::map<uint64_t, std::unique_ptr<Job>> jobs;
+  std::thread scheduler;
+
+  double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
+
+  void run_job(Job* j) {
+    cudaSetDevice(device);
+    cudaStream_t st = nullptr;
+    mars_scene* sc = nullptr;
+    mars_cache* ca = nullptr;
+    mars_status rc = MARS_OK;
+    std::string msg;
+    const int64_t npx = (int64_t)j->scene.desc.width * j->scene.desc.height;
+    std::vector<float> img(3 * (size_t)npx), acc(3 * (size_t)npx, 0.0f);
+    int kept = 0;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      rc = MARS_ERR_CUDA;
+      msg = "stream create failed";
+    }
+    if (rc == MARS_OK) rc = mars::scene_create_impl(&j->scene.desc, st, &sc);
+    if (rc == MARS_OK) rc = mars::cache_create_impl(sc, &j->cache, st, &ca);
+    for (int it = 0; rc == MARS_OK && it < j->iterations; ++it) {
+      mars_iter_params p{};
+      p.seed = j->seed;
+      p.job = (uint32_t)j->id;
+      p.iteration = (uint32_t)it;
+      p.mode = it < j->warmup ? MARS_MODE_WARMUP : MARS_MODE_MARS;
+      p.weights = MARS_WEIGHTS_AWARE;
+      p.clamp_lo = 0.05f;
+      p.clamp_hi = 20.0f;
+      p.outlier = 50.0f;
+      p.collect = 1;
+      p.image_on_host = 1;
+      p.update_estimate = 1;
+      const auto a = Clock::now();
+      rc = mars::render_iteration_impl(ca, &p, img.data(), nullptr, st);
+      if (rc == MARS_OK) rc = mars::update_counts_impl(ca, st);
+      if (rc == MARS_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = MARS_ERR_CUDA;
+      const double ms = std::chrono::duration<double, std::milli>(Clock::now() - a).count();
+      if (rc != MARS_OK) break;
+      if (it >= j->warmup) {
+        for (size_t k = 0; k < acc.size(); ++k) acc[k] += img[k];
+        ++kept;
+      }
+      std::lock_guard<std::mutex> lk(mu);
+      j->iter_ms.push_back(ms);
+      j->done_iters = it + 1;
+    }
+    if (rc != MARS_OK) msg = mars_last_error_string();
+    if (ca) mars::cache_destroy_impl(ca);
+    if (sc) mars::scene_destroy_impl(sc);
+    if (st) cudaStreamDestroy(st);
+    if (kept > 0)
+      for (float& v : acc) v /= (float)kept;
+    std::lock_guard<std::mutex> lk(mu);
+    j->image.swap(acc);
+    j->error = rc;
+    j->message = msg;
+    j->state = rc == MARS_OK ? MARS_JOB_DONE : MARS_JOB_FAILED;
+    j->end_s = now();
+    in_use -= j->footprint;
+    resident -= 1;
+    cv.notify_all();
+  }
+
+  void schedule() {
+    std::unique_lock<std::mutex> lk(mu);
+    while (true) {
+      cv.wait(lk, [&] {
+        if (stop) return true;
+        if (queue.empty() || resident >= max_slots) return false;
+        const Job* j = jobs[queue.front()].get();
+        return in_use + j->footprint <= budget || resident == 0;
+      });
+      if (stop) return;
+      Job* j = jobs[queue.front()].get();
+      queue.pop_front();
+      in_use += j->footprint;
+      resident += 1;
+      j->state = MARS_JOB_RUNNING;
+      j->start_s = now();
+      j->worker = std::thread([this, j] { run_job(j); });
+    }
+  }
+};
+
+extern "C" {
+
+mars_status mars_server_create(uint64_t memory_budget_bytes, int32_t max_slots, mars_server** out) {
+  if (!out || max_slots < 1 || memory_budget_bytes == 0)
+    return mars::set_error(MARS_ERR_INVALID_ARG, "server needs an output, max_slots >= 1 and a budget");
+  mars_server* s = new mars_server();
+  s->budget = memory_budget_bytes;
+  s->max_slots = max_slots;
+  if (cudaGetDevice(&s->device) != cudaSuccess) {
+    delete s;
+    return mars::set_error(MARS_ERR_CUDA, "no CUDA device");
+  }
+  s->t0 = Clock::now();
+  s->scheduler = std::thread([s] { s->schedule(); });
+  *out = s;
+  return MARS_OK;
+}
+
+mars_status mars_server_destroy(mars_server* s) {
+  if (!s) return MARS_OK;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+    s->cv.notify_all();
+  }
+  s->scheduler.join();
+  for (auto& kv : s->jobs)
+    if (kv.second->worker.joinable()) kv.second->worker.join();
+  delete s;
+  return MARS_OK;
+}
+
+mars_status mars_submit(mars_server* s, const mars_job_desc* jd, uint64_t* job_id) {
+  if (!s || !jd || !jd->scene || !job_id) return mars::set_error(MARS_ERR_INVALID_ARG, "null server, job or id");
+  if (jd->iterations < 1 || jd->warmup < 0 || jd->warmup > jd->iterations)
+    return mars::set_error(MARS_ERR_INVALID_ARG, "bad iteration counts");
+  const mars_scene_desc* d = jd->scene;
+  if (d->width <= 0 || d->height <= 0) return mars::set_error(MARS_ERR_INVALID_ARG, "bad resolution");
+  auto j = std::make_unique<Job>();
+  j->scene.assign(d);
+  j->cache = jd->cache;
+  j->seed = jd->seed;
+  j->iterations = jd->iterations;
+  j->warmup = jd->warmup;
+  const int64_t npx = (int64_t)d->width * d->height;
+  const int64_t cells = (int64_t)jd->cache.grid_n * jd->cache.grid_n * jd->cache.grid_n;
+  const uint64_t cap = jd->cache.arena_capacity ? jd->cache.arena_capacity
+                                                 : mars::default_capacity(npx, jd->cache.max_depth);
+  const int nprim = d->n_quads + d->n_spheres + d->n_tris;
+  j->footprint = mars::cache_footprint(cells, npx, jd->cache.max_depth, jd->cache.techniques, cap) +
+                 (uint64_t)nprim * 256 + (64ull << 20);
+  if (j->footprint > s->budget)
+    return mars::set_error(MARS_ERR_OOM, "job needs %llu bytes, more than the budget",
+                           (unsigned long long)j->footprint);
+  std::lock_guard<std::mutex> lk(s->mu);
+  j->id = s->next_id++;
+  j->submit_s = s->now();
+  *job_id = j->id;
+  s->queue.push_back(j->id);
+  s->jobs[j->id] = std::move(j);
+  s->cv.notify_all();
+  return MARS_OK;
+}
+
+mars_status mars_poll(mars_server* s, uint64_t job_id, mars_job_status* out, float* image_rgb) {
+  if (!s || !out) return mars::set_error(MARS_ERR_INVALID_ARG, "null server or output");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->jobs.find(job_id);
+  if (it == s->jobs.end()) return mars::set_error(MARS_ERR_NOT_FOUND, "unknown job %llu", (unsigned long long)job_id);
+  Job* j = it->second.get();
+  out->state = j->state;
+  out->iterations_done = j->done_iters;
+  out->error = j->error;
+  out->reserved = 0;
+  out->submit_s = j->submit_s;
+  out->start_s = j->start_s;
+  out->end_s = j->end_s;
+  std::vector<double> ms = j->iter_ms;
+  std::sort(ms.begin(), ms.end());
+  auto q = [&](double f) {
+    if (ms.empty()) return 0.0;
+    const size_t k = std::min(ms.size() - 1, (size_t)std::ceil(f * (double)ms.size()) - (f > 0 ? 1 : 0));
+    return ms[k];
+  };
+  out->iter_ms_p50 = q(0.5);
+  out->iter_ms_p99 = q(0.99);
+  if (j->state == MARS_JOB_FAILED) mars::set_error(j->error, "job %llu failed: %s", (unsigned long long)job_id,
+                                                   j->message.c_str());
+  if (image_rgb && j->state == MARS_JOB_DONE && !j->image.empty())
+    std::copy(j->image.begin(), j->image.end(), image_rgb);
+  return MARS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,203 @@
+// stats.cu -- image statistics and the fixed-point count update.
+//
+// Image statistics (Sec. 4.1, "Image estimates"): the iteration's one-sample
+// image is added to the running sum; the pixel estimate is a 3x3 box filter of
+// the running mean over in-image neighbours, floored at 1e-3 x the channel mean
+// (the paper denoises with OIDN instead); V_I is the mean over pixels and
+// channels of ((min(I, outlier x est) - est) / est)^2 ("Outlier clamping");
+// C_I is rays per pixel.
+//
+// Update (Eq. "optimalBeta", spatial form of Sec. 3.1 "Optimization"): per
+// cell, technique and channel, in float64,
+//   q^RR = sqrt(C_I / C_t * m2 / V_I),   q^S = sqrt(C_I / C_t * var / V_I),
+// with m2, var the per-sample moments of Sec. 4.1 "Local estimates" and C_t the
+// mean cost; cells with n < 2 or no cost keep their factors; statistics reset.
+// The guided technique's per-cell CDF is rebuilt from the accumulated deposits.
+#include "device.cuh"
+
+namespace mars {
+
+namespace {
+
+constexpr int IMG_THREADS = 256;
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) r += sh[k];
+  return r;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(IMG_THREADS) k_img_accum(DevCache c, int npix, int n_prev, float* out) {
+  __shared__ double sh[IMG_THREADS / 32];
+  if (c.ctr->any_overflow) return;
+  const float inv = 1.0f / (float)(n_prev + 1);
+  double m0 = 0.0, m1 = 0.0, m2 = 0.0;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) {
+    const float4 I = c.img[p];
+    float4 rs = c.run_sum[p];
+    rs.x += I.x; rs.y += I.y; rs.z += I.z;
+    c.run_sum[p] = rs;
+    if (out) {
+      out[3 * p] = I.x;
+      out[3 * p + 1] = I.y;
+      out[3 * p + 2] = I.z;
+    }
+    m0 += (double)(rs.x * inv);
+    m1 += (double)(rs.y * inv);
+    m2 += (double)(rs.z * inv);
+  }
+  m0 = block_sum(m0, sh);
+  m1 = block_sum(m1, sh);
+  m2 = block_sum(m2, sh);
+  if (threadIdx.x == 0) {
+    atomicAdd(&c.ctr->chsum[0], m0);
+    atomicAdd(&c.ctr->chsum[1], m1);
+    atomicAdd(&c.ctr->chsum[2], m2);
+  }
+}
+
+__global__ void __launch_bounds__(IMG_THREADS) k_img_est(DevCache c, int W, int H, int n_prev, float outlier) {
+  __shared__ double sh[IMG_THREADS / 32];
+  if (c.ctr->any_overflow) return;
+  const int npix = W * H;
+  const float inv = 1.0f / (float)(n_prev + 1);
+  const float fl0 = 1e-3f * (float)(c.ctr->chsum[0] / npix), fl1 = 1e-3f * (float)(c.ctr->chsum[1] / npix),
+              fl2 = 1e-3f * (float)(c.ctr->chsum[2] / npix);
+  double vi = 0.0;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) {
+    const int x = p % W, y = p / W;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+    int k = 0;
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int xx = x + dx, yy = y + dy;
+        if (xx < 0 || yy < 0 || xx >= W || yy >= H) continue;
+        const float4 r = c.run_sum[yy * W + xx];
+        s0 += r.x * inv;
+        s1 += r.y * inv;
+        s2 += r.z * inv;
+        ++k;
+      }
+    float e0 = fmaxf(fmaxf(s0 / (float)k, fl0), 1e-8f);
+    float e1 = fmaxf(fmaxf(s1 / (float)k, fl1), 1e-8f);
+    float e2 = fmaxf(fmaxf(s2 / (float)k, fl2), 1e-8f);
+    c.est[p] = make_float4(e0, e1, e2, 0.0f);
+    const float4 I = c.img[p];
+    const float r0 = (fminf(I.x, outlier * e0) - e0) / e0;
+    const float r1 = (fminf(I.y, outlier * e1) - e1) / e1;
+    const float r2 = (fminf(I.z, outlier * e2) - e2) / e2;
+    vi += (double)(r0 * r0) + (double)(r1 * r1) + (double)(r2 * r2);
+  }
+  vi = block_sum(vi, sh);
+  if (threadIdx.x == 0) atomicAdd(&c.ctr->vi_sum, vi);
+}
+
+__global__ void __launch_bounds__(IMG_THREADS) k_img_copy(DevCache c, int npix, float* out) {
+  if (c.ctr->any_overflow) return;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) {
+    const float4 I = c.img[p];
+    out[3 * p] = I.x;
+    out[3 * p + 1] = I.y;
+    out[3 * p + 2] = I.z;
+  }
+}
+
+__global__ void k_img_final(DevCache c, int npix) {
+  if (threadIdx.x != 0 || c.ctr->any_overflow) return;
+  c.ctr->VI = c.ctr->vi_sum / (3.0 * (double)npix);
+  c.ctr->CI = (double)c.ctr->rays / (double)npix;
+}
+
+__global__ void k_update_counts(DevCache c) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= c.n_cells * NT) return;
+  const int t = idx % NT;
+  double* s = c.stats + (size_t)idx * NSTAT;
+  const double VI = c.ctr->VI, CI = c.ctr->CI;
+  if (((c.techniques >> t) & 1) && VI > 1e-12) {
+    const double n = s[0];
+    if (n >= 2.0 && s[7] > 0.0) {
+      const double Ct = s[7] / n;
+      float qr[3], qs[3];
+      for (int ch = 0; ch < 3; ++ch) {
+        const double m1 = s[1 + ch] / n, m2 = s[4 + ch] / n;
+        double var = m2 - m1 * m1;
+        if (var < 0.0) var = 0.0;
+        qr[ch] = (float)sqrt(CI / Ct * m2 / VI);
+        qs[ch] = (float)sqrt(CI / Ct * var / VI);
+      }
+      c.cnt[2 * idx] = make_float4(qr[0], qr[1], qr[2], 1.0f);
+      c.cnt[2 * idx + 1] = make_float4(qs[0], qs[1], qs[2], 0.0f);
+    }
+  }
+  for (int k = 0; k < NSTAT; ++k) s[k] = 0.0;
+}
+
+// one warp per cell: P_b = 0.9 h_b / H + 0.1 / 256 (uniform when H = 0), then an
+// inclusive prefix sum in float64
+__global__ void k_guide_update(DevCache c) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= c.n_cells) return;
+  const float* h = c.guide_hist + (size_t)warp * GUIDE_BINS;
+  float* cdf = c.guide_cdf + (size_t)warp * GUIDE_BINS;
+  double v[8];
+  double loc = 0.0;
+  for (int k = 0; k < 8; ++k) {
+    v[k] = (double)h[lane * 8 + k];
+    loc += v[k];
+  }
+  double H = loc;
+  for (int off = 16; off > 0; off >>= 1) H += __shfl_xor_sync(0xffffffffu, H, off);
+  double run = 0.0;
+  for (int k = 0; k < 8; ++k) {
+    v[k] = H > 0.0 ? 0.9 * v[k] / H + 0.1 / GUIDE_BINS : 1.0 / GUIDE_BINS;
+    run += v[k];
+  }
+  double incl = run;
+  for (int off = 1; off < 32; off <<= 1) {
+    const double y = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += y;
+  }
+  double acc = incl - run;
+  for (int k = 0; k < 8; ++k) {
+    acc += v[k];
+    cdf[lane * 8 + k] = (lane == 31 && k == 7) ? 1.0f : (float)acc;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_image_stats(const DevCache& c, int width, int height, int n_prev, float outlier,
+                               float* image_out_dev, cudaStream_t st) {
+  const int npix = width * height;
+  int blocks = (npix + IMG_THREADS - 1) / IMG_THREADS;
+  if (blocks > 4096) blocks = 4096;
+  k_img_accum<<<blocks, IMG_THREADS, 0, st>>>(c, npix, n_prev, image_out_dev);
+  k_img_est<<<blocks, IMG_THREADS, 0, st>>>(c, width, height, n_prev, outlier);
+  k_img_final<<<1, 32, 0, st>>>(c, npix);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_image_copy(const DevCache& c, int npix, float* out, cudaStream_t st) {
+  int blocks = (npix + IMG_THREADS - 1) / IMG_THREADS;
+  if (blocks > 4096) blocks = 4096;
+  k_img_copy<<<blocks, IMG_THREADS, 0, st>>>(c, npix, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update(const DevCache& c, int num_sms, cudaStream_t st) {
+  (void)num_sms;
+  const int n = c.n_cells * NT;
+  k_update_counts<<<(n + 255) / 256, 256, 0, st>>>(c);
+  if (c.techniques & MARS_TECH_GUIDED) k_guide_update<<<(c.n_cells * 32 + 255) / 256, 256, 0, st>>>(c);
+  return cudaGetLastError();
+}
+
+}  // namespace mars

@@ -1,0 +1,265 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the
+same seeded inputs and the same Philox streams.
+
+Bars (floating point; the oracle is float64, the CUDA path float32):
+* images: at least 99.9 % of pixels agree within 1e-4 relative in every channel
+  (a rare pixel may take a different discrete branch -- a rounding decision of
+  Alg. 1 or a grazing hit -- because float32 and float64 differ in the last bits);
+* per-cell statistics: 99 % of (cell, technique) entries within 1e-3 relative,
+  and the sums over all cells within 1e-3 relative;
+* integer counters (rays, traced vertices) within 0.1 %.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import mars_workloads as W
+
+pytestmark = pytest.mark.gpu
+
+PIX_TOL = 1e-4
+STAT_TOL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def mars():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2410_20429_gb300 import build as B
+    B.build()
+    import paper_2410_20429_gb300 as M
+    return M
+
+
+def _gpu_iteration(M, cache, *, iteration=0, seed=0, mode=0, weights=0, update_estimate=False, collect=True):
+    import torch
+    img = torch.zeros(cache.n_pixels * 3, dtype=torch.float32, device="cuda")
+    st = cache.render_iteration(img, seed=seed, iteration=iteration, mode=mode, weights=weights, collect=collect,
+                                update_estimate=update_estimate)
+    torch.cuda.synchronize()
+    return img.cpu().numpy().reshape(-1, 3).astype(np.float64), st
+
+
+def _pixel_agreement(g, o):
+    ok = np.abs(g - o) <= PIX_TOL * np.abs(o) + 1e-7
+    return ok.all(axis=1).mean()
+
+
+def _stat_agreement(gs, os_):
+    """fraction of populated (cell, technique) entries whose 8 statistics agree"""
+    n_g, n_o = gs[..., 0], os_[..., 0]
+    pop = (n_g > 0) | (n_o > 0)
+    close = np.abs(gs - os_) <= STAT_TOL * np.abs(os_) + 1e-9
+    agree = close.all(axis=-1) & pop
+    return agree.sum() / max(pop.sum(), 1)
+
+
+def _check(g_img, o_img, g_state, o_res, g_st, what):
+    frac = _pixel_agreement(g_img, o_img)
+    assert frac >= 0.999, f"{what}: only {frac:.5f} of pixels agree"
+    sa = _stat_agreement(g_state["stats"], o_res.stats)
+    assert sa >= 0.99, f"{what}: only {sa:.4f} of cell statistics agree"
+    tot_g = g_state["stats"].sum(axis=0)
+    tot_o = o_res.stats.sum(axis=0)
+    assert np.allclose(tot_g, tot_o, rtol=STAT_TOL, atol=1e-6), f"{what}: total statistics differ"
+    assert abs(g_st["rays"] - o_res.rays) <= 1e-3 * o_res.rays + 1
+    assert abs(g_st["vertices"] - o_res.vertices) <= 1e-3 * o_res.vertices + 1
+
+
+def _make(M, cfg, **kw):
+    scene = M.Scene(cfg.scene)
+    cache = M.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, **kw)
+    return scene, cache
+
+
+def test_box_warmup_iteration_parity(mars, orc):
+    cfg = W.config_box(64, 64)
+    scene, cache = _make(mars, cfg)
+    g_img, g_st = _gpu_iteration(mars, cache, iteration=0, seed=0, mode=0)
+    g_state = cache.get_state()
+    o = orc.render(cfg.scene, grid_n=cfg.grid_n, techniques=cfg.techniques, max_depth=cfg.max_depth, iteration=0)
+    _check(g_img, o.image, g_state, o, g_st, "box warm-up")
+    assert g_st["estimator_vertices"] == pytest.approx(o.counters[2], rel=1e-3)
+
+
+@pytest.mark.parametrize("weights", [0, 1])
+def test_box_mars_iteration_parity(mars, orc, weights):
+    """Teacher-forced MARS iteration: random count fields and pixel estimate set
+    on both sides; splitting and Russian roulette both occur."""
+    cfg = W.config_box(64, 64)
+    scene, cache = _make(mars, cfg)
+    q_rr, q_s, valid = W.random_count_fields(cfg.n_cells, seed=101, lo=0.05, hi=4.0)
+    est = W.random_pixel_estimate(cfg.scene.n_pixels, seed=102, lo=0.05, hi=1.0)
+    cache.set_state(q_rr=q_rr, q_s=q_s, valid=valid, pixel_estimate=est, has_estimate=True, n_iterations=1)
+    g_img, g_st = _gpu_iteration(mars, cache, iteration=3, seed=5, mode=1, weights=weights)
+    g_state = cache.get_state()
+    o = orc.render(cfg.scene, grid_n=cfg.grid_n, techniques=cfg.techniques, max_depth=cfg.max_depth, iteration=3,
+                   seed=5, mode=orc.MODE_MARS, weights=weights, q_rr=q_rr, q_s=q_s, valid=valid, est=est)
+    _check(g_img, o.image, g_state, o, g_st, "box MARS")
+    # splitting and roulette really happened
+    assert o.counters[3] / o.counters[2] != pytest.approx(1.0, abs=0.05)
+    for t in range(2):
+        assert g_st["mean_beta"][t] == pytest.approx(o.counters[3 + t] / o.counters[2], rel=1e-3)
+
+
+def test_guided_room_crop_parity(mars, orc):
+    """Three techniques (BSDF, NEE, guided) on a 64 x 64 render of the guided room
+    with 16 spheres, GGX and Lambert, random guide CDFs and random counts."""
+    sc = W.guided_room_scene(seed=0, width=64, height=64, n_spheres=16)
+    cfg = W.WorkloadConfig(sc, max_depth=6, grid_n=8, techniques=7, iterations=1, warmup=0, name="guided crop")
+    scene, cache = _make(mars, cfg)
+    q_rr, q_s, valid = W.random_count_fields(cfg.n_cells, seed=201, lo=0.1, hi=3.0)
+    est = W.random_pixel_estimate(sc.n_pixels, seed=202, lo=0.05, hi=2.0)
+    cdf = W.random_guide_cdf(cfg.n_cells, seed=203)
+    cache.set_state(q_rr=q_rr, q_s=q_s, valid=valid, pixel_estimate=est, guide_cdf=cdf, has_estimate=True,
+                    n_iterations=2)
+    g_img, g_st = _gpu_iteration(mars, cache, iteration=2, seed=9, mode=1)
+    g_state = cache.get_state()
+    o = orc.render(sc, grid_n=cfg.grid_n, techniques=7, max_depth=cfg.max_depth, iteration=2, seed=9,
+                   mode=orc.MODE_MARS, q_rr=q_rr, q_s=q_s, valid=valid, est=est, guide_cdf=cdf)
+    _check(g_img, o.image, g_state, o, g_st, "guided room")
+    gh, oh = g_state["guide_hist"].astype(np.float64), o.hist
+    pop = (gh > 0) | (oh > 0)
+    close = np.abs(gh - oh) <= STAT_TOL * np.abs(oh) + 1e-9
+    assert (close & pop).sum() >= 0.99 * pop.sum()
+    assert gh.sum() == pytest.approx(oh.sum(), rel=STAT_TOL)
+
+
+def test_update_and_guide_parity(mars, orc):
+    """Fixed-point update and guide CDF from the same synthetic statistics."""
+    cfg = W.config_guided(16, 16)
+    scene, cache = _make(mars, cfg)
+    rng = np.random.default_rng(301)
+    cells = cfg.n_cells
+    stats = np.zeros((cells, 3, 8))
+    n = rng.integers(0, 40, size=(cells, 3)).astype(float)
+    stats[..., 0] = n
+    m1 = rng.exponential(0.5, size=(cells, 3, 3))
+    stats[..., 1:4] = n[..., None] * m1
+    stats[..., 4:7] = n[..., None] * (m1 ** 2 + rng.exponential(0.3, size=(cells, 3, 3)))
+    stats[..., 7] = n * rng.uniform(1.0, 6.0, size=(cells, 3))
+    stats[rng.uniform(size=(cells, 3)) < 0.05, 7] = 0.0
+    hist = rng.exponential(1.0, size=(cells, 256)).astype(np.float32)
+    hist[rng.uniform(size=hist.shape) < 0.6] = 0.0
+    hist[:7] = 0.0
+    q_rr0, q_s0, valid0 = W.random_count_fields(cells, seed=302)
+    VI, CI = 0.37, 4.25
+    cache.set_state(q_rr=q_rr0, q_s=q_s0, valid=valid0, stats=stats, guide_hist=hist, VI=VI, CI=CI,
+                    has_estimate=True, n_iterations=3)
+    cache.update_counts()
+    g = cache.get_state()
+    q_rr, q_s, valid = orc.update_counts(stats, VI, CI, cfg.techniques, q_rr0, q_s0, valid0)
+    assert np.array_equal(g["valid"], valid)
+    np.testing.assert_allclose(g["q_rr"], q_rr, rtol=1e-6)
+    np.testing.assert_allclose(g["q_s"], q_s, rtol=1e-6, atol=1e-30)
+    assert np.all(g["stats"] == 0.0)
+    cdf = orc.guide_update(hist.astype(np.float64))
+    np.testing.assert_allclose(g["guide_cdf"], cdf, atol=2e-7)
+
+
+def test_image_statistics_parity(mars, orc):
+    """Running mean, pixel estimate and V_I after one rendered iteration, from a
+    seeded running sum; the oracle uses its own image of the same iteration."""
+    cfg = W.config_box(48, 40)
+    scene, cache = _make(mars, cfg)
+    rs = W.random_pixel_estimate(cfg.scene.n_pixels, seed=401, lo=0.1, hi=3.0) * 2.0
+    cache.set_state(run_sum=rs, n_iterations=2, has_estimate=True,
+                    pixel_estimate=np.ones((cfg.scene.n_pixels, 3), np.float32))
+    g_img, g_st = _gpu_iteration(mars, cache, iteration=2, seed=3, mode=0, update_estimate=True)
+    g = cache.get_state()
+    o = orc.render(cfg.scene, grid_n=cfg.grid_n, techniques=cfg.techniques, max_depth=cfg.max_depth, iteration=2,
+                   seed=3, est=np.ones((cfg.scene.n_pixels, 3), np.float32))
+    vi, o_rs, o_est = orc.image_stats(48, 40, o.image, rs.astype(np.float64), 2)
+    assert _pixel_agreement(g["run_sum"].astype(np.float64), o_rs) >= 0.999
+    est_ok = np.abs(g["pixel_estimate"] - o_est) <= 1e-4 * np.abs(o_est) + 1e-7
+    assert est_ok.all(axis=1).mean() >= 0.99
+    assert g_st["VI"] == pytest.approx(vi, rel=1e-2)
+    assert g_st["CI"] == pytest.approx(o.rays / cfg.scene.n_pixels, rel=1e-3)
+    assert g["n_iterations"] == 3
+
+
+def test_arena_overflow_tiles_reproduce_the_image(mars):
+    """A small queue arena forces pixel tiles; the image is bitwise identical and
+    the statistics equal up to summation order (runs of equal cells are summed
+    in float32 within a warp before the float64 atomics, and tiling changes
+    which vertices share a warp)."""
+    cfg = W.config_box(32, 32)
+    q_rr, q_s, valid = W.random_count_fields(cfg.n_cells, seed=501, lo=0.5, hi=6.0)
+    est = W.random_pixel_estimate(cfg.scene.n_pixels, seed=502, lo=0.05, hi=0.5)
+    res = []
+    for cap in (0, 6000):
+        scene, cache = _make(mars, cfg, arena_capacity=cap)
+        cache.set_state(q_rr=q_rr, q_s=q_s, valid=valid, pixel_estimate=est, has_estimate=True, n_iterations=1)
+        img, st = _gpu_iteration(mars, cache, iteration=1, seed=2, mode=1)
+        res.append((img, st, cache.get_state()["stats"]))
+    (a, sa, ta), (b, sb, tb) = res
+    assert sa["retries"] == 0 and sb["retries"] > 0 and sb["tiles"] > 1
+    assert np.array_equal(a, b)
+    np.testing.assert_allclose(ta, tb, rtol=1e-6, atol=1e-9)
+    assert sa["rays"] == sb["rays"] and sa["vertices"] == sb["vertices"]
+
+
+@pytest.mark.parametrize("albedo,D", [(0.5, 3), (0.8, 5)])
+def test_gpu_furnace_closed_form(mars, albedo, D):
+    """The CUDA path alone against the closed furnace Le (1 - a^D) / (1 - a)
+    under a random count field (unbiasedness, App. A.1)."""
+    sc = W.furnace_scene(albedo=albedo, radiance=1.5, width=64, height=64)
+    cfg = W.WorkloadConfig(sc, max_depth=D, grid_n=4, techniques=3, iterations=1, warmup=0, name="furnace")
+    scene, cache = _make(mars, cfg)
+    q_rr, q_s, valid = W.random_count_fields(cfg.n_cells, seed=601, lo=0.1, hi=3.0)
+    est = W.random_pixel_estimate(sc.n_pixels, seed=602, lo=0.5, hi=4.0)
+    cache.set_state(q_rr=q_rr, q_s=q_s, valid=valid, pixel_estimate=est, has_estimate=True, n_iterations=1)
+    means = []
+    for it in range(40):
+        img, _ = _gpu_iteration(mars, cache, iteration=it, seed=1, mode=1, collect=False)
+        means.append(img.mean())
+    m, se = np.mean(means), np.std(means, ddof=1) / math.sqrt(len(means))
+    expected = 1.5 * (1 - albedo ** D) / (1 - albedo)
+    assert abs(m - expected) < 3.5 * se
+
+
+def test_state_roundtrip(mars):
+    cfg = W.config_guided(8, 8)
+    scene, cache = _make(mars, cfg)
+    rng = np.random.default_rng(701)
+    q_rr, q_s, valid = W.random_count_fields(cfg.n_cells, seed=702)
+    stats = rng.normal(size=(cfg.n_cells, 3, 8))
+    hist = rng.exponential(size=(cfg.n_cells, 256)).astype(np.float32)
+    cdf = W.random_guide_cdf(cfg.n_cells, seed=703)
+    est = W.random_pixel_estimate(64, seed=704)
+    rs = W.random_pixel_estimate(64, seed=705)
+    cache.set_state(q_rr=q_rr, q_s=q_s, valid=valid, stats=stats, guide_hist=hist, guide_cdf=cdf,
+                    pixel_estimate=est, run_sum=rs, n_iterations=5, has_estimate=True, VI=0.5, CI=3.0)
+    g = cache.get_state()
+    for k, v in dict(q_rr=q_rr, q_s=q_s, valid=valid, stats=stats, guide_hist=hist, guide_cdf=cdf,
+                     pixel_estimate=est, run_sum=rs).items():
+        assert np.array_equal(g[k], v), k
+    assert g["n_iterations"] == 5 and g["has_estimate"] and g["VI"] == 0.5 and g["CI"] == 3.0
+
+
+def test_invalid_arguments_are_reported(mars):
+    from paper_2410_20429_gb300 import _abi as A
+    cfg = W.config_box(8, 8)
+    scene = mars.Scene(cfg.scene)
+    with pytest.raises(mars.MarsError) as e:
+        mars.Cache(scene, 0, 3, 5)
+    assert e.value.status == A.MARS_ERR_INVALID_ARG
+    with pytest.raises(mars.MarsError):
+        mars.Cache(scene, 4, 2, 5)        # BSDF missing
+    cache = mars.Cache(scene, 4, 3, 5)
+    import torch
+    img = torch.zeros(8 * 8 * 3, device="cuda")
+    with pytest.raises(mars.MarsError) as e:
+        cache.render_iteration(img, mode=A.MARS_MODE_MARS)   # no pixel estimate yet
+    assert "pixel estimate" in str(e.value)
+    with pytest.raises(mars.MarsError):
+        cache.render_iteration(img, clamp_hi=40.0)
+    bad = W.box_scene(4, 4)
+    bad.quad_mat = bad.quad_mat.copy()
+    bad.quad_mat[0] = 99
+    with pytest.raises(mars.MarsError):
+        mars.Scene(bad)
+    # the cache still works after rejected calls
+    cache.render_iteration(img)
