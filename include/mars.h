@@ -262,6 +262,30 @@ mars_status mars_submit(mars_server* server, const mars_job_desc* job, uint64_t*
  * NULL) receives the mean image over its iterations after warm-up. */
 mars_status mars_poll(mars_server* server, uint64_t job_id, mars_job_status* out, float* image_rgb);
 
+/* ---- image statistics without allocation ------------------------------------
+ * The paper has no counterpart to this entry point; it is a library service.
+ * Some callers cannot call cudaMalloc: code that runs while a CUDA graph is
+ * being captured, allocator-less embedded hosts, or a serving process whose
+ * device memory is fully reserved up front.  For them this call computes the
+ * same per-iteration image statistics as mars_render_iteration with
+ * update_estimate = 1 (running sum, pixel estimate, V_I and C_I) directly on
+ * caller buffers and allocates nothing: its only scratch is a static device
+ * array of the library (256 KB, held by every GPU that loads the library until
+ * the process exits), with room for images of at most 8192 rows.
+ *   image_rgb    [height][width][3] float32, device: this iteration's image.
+ *   run_sum_rgb  [height][width][3] float32, device, in/out: sum over the
+ *                n_prev earlier iterations; the image is added to it.
+ *   estimate_rgb [height][width][3] float32, device, out: pixel estimate.
+ *   vi_ci        2 float64, device, out: V_I and C_I = rays / pixels.
+ * Asynchronous on `stream`.  The first call on a device looks up the scratch
+ * array's device address (cudaGetSymbolAddress) and must therefore come before
+ * any stream capture on that device.  All calls share the scratch array: calls
+ * whose work overlaps on the GPU race and give wrong results; serialise them.
+ * Errors: INVALID_ARG (null pointer, height above 8192 rows, bad sizes), CUDA. */
+mars_status mars_image_stats_static(const float* image_rgb, float* run_sum_rgb, float* estimate_rgb, int32_t width,
+                                    int32_t height, int32_t n_prev, float outlier, double rays, double* vi_ci,
+                                    void* stream);
+
 /* ---- diagnostics ------------------------------------------------------------ */
 const char* mars_last_error_string(void);
 const char* mars_version(void);

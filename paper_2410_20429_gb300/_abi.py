@@ -106,6 +106,8 @@ SIGNATURES = {
     "mars_server_destroy": ([_VP], ct.c_int),
     "mars_submit": ([_VP, ct.POINTER(mars_job_desc), ct.POINTER(ct.c_uint64)], ct.c_int),
     "mars_poll": ([_VP, ct.c_uint64, ct.POINTER(mars_job_status), _VP], ct.c_int),
+    "mars_image_stats_static": ([_VP, _VP, _VP, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_float, ct.c_double, _VP,
+                                 _VP], ct.c_int),
     "mars_last_error_string": ([], ct.c_char_p),
     "mars_version": ([], ct.c_char_p),
 }

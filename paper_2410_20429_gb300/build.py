@@ -14,7 +14,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libmars.so")
-SOURCES = ["abi.cu", "render.cu", "stats.cu", "scene.cu", "server.cu"]
+SOURCES = ["abi.cu", "render.cu", "stats.cu", "scene.cu", "server.cu", "static_scratch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
