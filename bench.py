@@ -42,12 +42,32 @@ METRIC = "efficiency 1/(relMSE·s) MARS vs fixed-count MIS; Mvertices/s; p50/p99
 UNIT = "Mvertices/s"
 
 # algorithmic bytes of the arena records (see the layout in csrc/internal.h)
-RAY_BYTES = 80          # five float4 per ray
-VERT_BASE_BYTES = 32    # V0, V1 for every slot
-VERT_EST_BYTES = 64     # V2..V5 for a vertex that runs the estimator
-VERT_GUIDE_BYTES = 16   # V6 for a traced ray when the guided technique learns
+RAY_BYTES = 80          # R0..R4: five float4 per ray
+RAY_TRACE_BYTES = 32    # R0, R1: origin and direction
+HIT_BYTES = 8           # H: (t, primitive)
+V0_BYTES = 16           # V0 for every slot
+VERT_EST_BYTES = 48     # V1..V3 for a vertex that runs the estimator
+VERT_GUIDE_BYTES = 16   # V4 for a traced ray when the guided technique learns
 SAMPLE_BYTES = 16       # S: one float4 per slot
 EST_READ_BYTES = 16     # pixel estimate read per estimator vertex
+SHADOW_BYTES = 48       # SH0..SH2 per NEE shadow ray
+SLOT_BYTES = RAY_BYTES + HIT_BYTES + V0_BYTES + VERT_EST_BYTES + VERT_GUIDE_BYTES + SAMPLE_BYTES
+
+
+def kernel_bytes(entries, pixels, est_v, traced, shadows, guided):
+    """Minimum HBM bytes each wave kernel must move for one step (its inputs
+    read once, its outputs written once)."""
+    children = entries - pixels
+    guide = VERT_GUIDE_BYTES * (traced - pixels) if guided else 0
+    return {
+        "k_trace": RAY_TRACE_BYTES * children + HIT_BYTES * entries,
+        "k_shade": (RAY_BYTES * children + HIT_BYTES * entries + V0_BYTES * entries
+                    + (VERT_EST_BYTES + EST_READ_BYTES) * est_v + RAY_BYTES * children + SHADOW_BYTES * shadows
+                    + guide),
+        "k_shadow": 32 * shadows,
+        "k_reverse": (V0_BYTES * entries + SAMPLE_BYTES * entries + VERT_EST_BYTES * est_v
+                      + SAMPLE_BYTES * children + 16 * shadows + guide),
+    }
 
 
 def workload(args):
@@ -186,31 +206,25 @@ def run_mars(args):
         t_max, verts_all = float(t.item()), float(v.item())
     value = verts_all / (t_max * 1e-3) / 1e6
 
-    # ---- dominant kernel roofline (live CUDA-event stage times)
-    shade_ms = sum(s["shade_ms"] for s in sts)
-    rev_ms = sum(s["reverse_ms"] for s in sts)
-    shade_l = sum(s["shade_launches"] for s in sts)
-    entries = sum(s["wave_entries"] for s in sts)
-    est_v = sum(s["estimator_vertices"] for s in sts)
-    traced = verts
-    pixels_total = npx * args.steps
-    children = entries - pixels_total
+    # ---- dominant kernel roofline (live CUDA-event times of every launch)
     guided = bool(cfg.techniques & W.TECH_GUIDED)
-    shade_bytes = (RAY_BYTES * children * 2 + VERT_BASE_BYTES * entries + (VERT_EST_BYTES + EST_READ_BYTES) * est_v
-                   + (VERT_GUIDE_BYTES * (traced - pixels_total) if guided else 0))
-    rev_bytes = (VERT_BASE_BYTES * entries + VERT_EST_BYTES * est_v + SAMPLE_BYTES * (entries + children)
-                 + (VERT_GUIDE_BYTES * (traced - pixels_total) if guided else 0))
+    kb = kernel_bytes(sum(s["wave_entries"] for s in sts), npx * args.steps,
+                      sum(s["estimator_vertices"] for s in sts), verts, sum(s["shadow_entries"] for s in sts),
+                      guided)
+    kms = {k: sum(s[k[2:] + "_ms"] for s in sts) for k in kb}
+    launches_per_kernel = sum(s["wave_launches"] for s in sts)
     hbm, peak_kind = peaks()
-    dom = "k_shade" if shade_ms >= rev_ms else "k_reverse"
-    dom_ms, dom_bytes = (shade_ms, shade_bytes) if dom == "k_shade" else (rev_ms, rev_bytes)
-    per_launch_ms = dom_ms / max(shade_l, 1)
-    achieved = dom_bytes / max(shade_l, 1) / (per_launch_ms * 1e-3) / 1e9
+    dom = max(kms, key=kms.get)
+    per_launch_ms = kms[dom] / max(launches_per_kernel, 1)
+    bytes_per_launch = kb[dom] / max(launches_per_kernel, 1)
+    achieved = bytes_per_launch / (per_launch_ms * 1e-3) / 1e9
     roofline = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(achieved / hbm, 4), "traffic": None, "peak_kind": peak_kind,
-                "bytes_per_launch": int(dom_bytes / max(shade_l, 1)), "launch_ms": round(per_launch_ms, 4),
-                "stage_ms_per_step": {"shade": round(shade_ms / args.steps, 4),
-                                      "reverse": round(rev_ms / args.steps, 4),
-                                      "image": round(sum(s["image_ms"] for s in sts) / args.steps, 4)}}
+                "bytes_per_launch": int(bytes_per_launch), "launch_ms": round(per_launch_ms, 4),
+                "kernel_ms_per_step": {k: round(v / args.steps, 4) for k, v in kms.items()},
+                "kernel_gbs": {k: round(kb[k] / max(kms[k], 1e-9) / 1e6, 1) for k in kb}}
+    roofline["kernel_ms_per_step"]["image"] = round(sum(s["image_ms"] for s in sts) / args.steps, 4)
+    entries = sum(s["wave_entries"] for s in sts)
 
     # ---- end to end through the C ABI with a pinned host image every step
     host_img = torch.empty(npx * 3, dtype=torch.float32, pin_memory=True).numpy()
@@ -236,7 +250,7 @@ def run_mars(args):
         "config": {"workload": cfg.name, "pixels": npx, "max_depth": cfg.max_depth, "grid": cfg.grid_n,
                    "techniques": "bsdf+nee+guided", "statistics_dtype": "f64",
                    "l2": "working set > L2: queue arena %.0f MB per step" % (
-                       entries / args.steps * (RAY_BYTES + 7 * 16 + SAMPLE_BYTES) / 1e6),
+                       entries / args.steps * SLOT_BYTES / 1e6),
                    "parallelism": f"replicas x{world}"},
         "latency_ms": {"p50": round(float(np.percentile(per_step, 50)), 4),
                        "p99": round(float(np.percentile(per_step, 99)), 4)},

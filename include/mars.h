@@ -144,9 +144,11 @@ typedef struct {
   uint32_t retries;           /* tiles re-rendered after an overflow */
   uint64_t arena_demand;      /* rays the largest tile needed */
   uint32_t launches;          /* kernels this call launched */
-  uint32_t shade_launches;    /* of which wavefront shade kernels */
-  double shade_ms, reverse_ms, image_ms;  /* device time per stage (profile = 1) */
+  uint32_t wave_launches;     /* launches of each per-wave kernel (depth waves x tiles) */
+  /* device time per kernel kind, summed over waves and tiles (profile = 1) */
+  double trace_ms, shade_ms, shadow_ms, reverse_ms, image_ms;
   uint64_t wave_entries;      /* rays held in the depth waves (traced or not), all tiles */
+  uint64_t shadow_entries;    /* NEE shadow-ray slots, all tiles */
 } mars_iter_stats;
 
 /* Host copy of a cache's state (checkpoint / teacher forcing).  Any pointer

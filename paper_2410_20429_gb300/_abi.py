@@ -56,8 +56,9 @@ class mars_iter_stats(ct.Structure):
         ("VI", ct.c_double), ("CI", ct.c_double), ("rays", ct.c_uint64), ("vertices", ct.c_uint64),
         ("estimator_vertices", ct.c_uint64), ("mean_beta", ct.c_double * 3), ("tiles", ct.c_uint32),
         ("retries", ct.c_uint32), ("arena_demand", ct.c_uint64), ("launches", ct.c_uint32),
-        ("shade_launches", ct.c_uint32), ("shade_ms", ct.c_double), ("reverse_ms", ct.c_double),
-        ("image_ms", ct.c_double), ("wave_entries", ct.c_uint64),
+        ("wave_launches", ct.c_uint32), ("trace_ms", ct.c_double), ("shade_ms", ct.c_double),
+        ("shadow_ms", ct.c_double), ("reverse_ms", ct.c_double), ("image_ms", ct.c_double),
+        ("wave_entries", ct.c_uint64), ("shadow_entries", ct.c_uint64),
     ]
 
 

@@ -350,7 +350,7 @@ void scene_destroy_impl(mars_scene* s) {
 // ------------------------------------------------------------------ cache
 uint64_t cache_footprint(int64_t cells, int64_t pixels, int max_depth, int techniques, uint64_t cap) {
   (void)max_depth;
-  uint64_t b = (uint64_t)cap * (NR + NV + 1) * sizeof(float4);
+  uint64_t b = (uint64_t)cap * (SLOT_BYTES + SHADOW_BYTES);
   b += (uint64_t)cells * NT * (2 * sizeof(float4) + NSTAT * sizeof(double));
   if (techniques & MARS_TECH_GUIDED) b += (uint64_t)cells * GUIDE_BINS * 2 * sizeof(float);
   b += (uint64_t)pixels * 3 * sizeof(float4);
@@ -392,6 +392,7 @@ mars_status cache_create_impl(const mars_scene* s, const mars_cache_desc* d, cud
   c->cells = cells;
   c->pixels = pixels;
   c->arena.cap = cap;
+  c->arena.scap = cap;  // NEE shadow rays: as many slots as rays
   c->max_tiles = 4096;
   auto cleanup = [&](cudaError_t e, const char* what) {
     const mars_status ms = e == cudaErrorMemoryAllocation ? MARS_ERR_OOM : MARS_ERR_CUDA;
@@ -405,6 +406,10 @@ mars_status cache_create_impl(const mars_scene* s, const mars_cache_desc* d, cud
   for (int k = 0; k < NV; ++k)
     if ((e = cudaMalloc(&c->arena.V[k], sizeof(float4) * cap)) != cudaSuccess) return cleanup(e, "arena alloc");
   if ((e = cudaMalloc(&c->arena.S, sizeof(float4) * cap)) != cudaSuccess) return cleanup(e, "arena alloc");
+  if ((e = cudaMalloc(&c->arena.H, sizeof(float2) * cap)) != cudaSuccess) return cleanup(e, "arena alloc");
+  for (int k = 0; k < NSH; ++k)
+    if ((e = cudaMalloc(&c->arena.SH[k], sizeof(float4) * c->arena.scap)) != cudaSuccess)
+      return cleanup(e, "arena alloc");
   if ((e = cudaMalloc(&c->d_cnt, sizeof(float4) * 2 * NT * cells)) != cudaSuccess) return cleanup(e, "cache alloc");
   if ((e = cudaMalloc(&c->d_stats, sizeof(double) * NSTAT * NT * cells)) != cudaSuccess) return cleanup(e, "cache alloc");
   const int64_t gcells = (d->techniques & MARS_TECH_GUIDED) ? cells : 1;
@@ -462,6 +467,8 @@ void cache_destroy_impl(mars_cache* c) {
   for (auto* p : c->arena.R) if (p) cudaFree(p);
   for (auto* p : c->arena.V) if (p) cudaFree(p);
   if (c->arena.S) cudaFree(c->arena.S);
+  if (c->arena.H) cudaFree(c->arena.H);
+  for (auto* p : c->arena.SH) if (p) cudaFree(p);
   void* ptrs[] = {c->d_cnt, c->d_stats, c->d_hist, c->d_cdf, c->d_est, c->d_run, c->d_img, c->d_ctr, c->d_tile_status};
   for (void* p : ptrs) if (p) cudaFree(p);
   if (c->h_ctr) cudaFreeHost(c->h_ctr);
@@ -517,11 +524,11 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
     const int64_t a = npx * t / ntiles, b = npx * (t + 1) / ntiles;
     if (b > a) tiles.emplace_back(a, b);
   }
-  uint32_t retries = 0, used = 0, launches = 0, shade_launches = 0;
+  uint32_t retries = 0, used = 0, launches = 0, wave_launches = 0;
   uint64_t demand = 0;
-  double shade_ms = 0.0, reverse_ms = 0.0, image_ms = 0.0;
+  double trace_ms = 0.0, shade_ms = 0.0, shadow_ms = 0.0, reverse_ms = 0.0, image_ms = 0.0;
   const int D = c->max_depth;
-  const int per_tile = 2 * D + 1;
+  const int per_tile = 4 * D + 1;
   float* dev_out = p->image_on_host ? nullptr : image;
   while (true) {
     if (p->profile) {
@@ -539,8 +546,8 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
       cudaEvent_t* ev = p->profile ? c->events.data() + t * per_tile : nullptr;
       if ((e = launch_tile(s->ds, c->dc, c->arena, it, num_sms, st, ev)) != cudaSuccess)
         return poison(c, e, "render launch");
-      launches += 2 * D + TILE_LAUNCHES_FIXED;
-      shade_launches += D;
+      launches += (uint32_t)tile_launches(D, c->techniques);
+      wave_launches += (uint32_t)D;
     }
     used += (uint32_t)tiles.size();
     cudaEvent_t* iev = p->profile ? c->events.data() + tiles.size() * per_tile : nullptr;
@@ -564,9 +571,15 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
       for (size_t t = 0; t < tiles.size(); ++t) {
         cudaEvent_t* ev = c->events.data() + t * per_tile;
         float ms = 0.f;
-        cudaEventElapsedTime(&ms, ev[0], ev[D]);
-        shade_ms += ms;
-        cudaEventElapsedTime(&ms, ev[D], ev[2 * D]);
+        for (int d = 1; d <= D; ++d) {
+          cudaEventElapsedTime(&ms, ev[3 * (d - 1)], ev[3 * (d - 1) + 1]);
+          trace_ms += ms;
+          cudaEventElapsedTime(&ms, ev[3 * (d - 1) + 1], ev[3 * (d - 1) + 2]);
+          shade_ms += ms;
+          cudaEventElapsedTime(&ms, ev[3 * (d - 1) + 2], ev[3 * (d - 1) + 3]);
+          shadow_ms += ms;
+        }
+        cudaEventElapsedTime(&ms, ev[3 * D], ev[4 * D]);
         reverse_ms += ms;
       }
       float ms = 0.f;
@@ -625,11 +638,14 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
     out->retries = retries;
     out->arena_demand = demand;
     out->launches = launches;
-    out->shade_launches = shade_launches;
+    out->wave_launches = wave_launches;
+    out->trace_ms = trace_ms;
     out->shade_ms = shade_ms;
+    out->shadow_ms = shadow_ms;
     out->reverse_ms = reverse_ms;
     out->image_ms = image_ms;
     out->wave_entries = h.entries;
+    out->shadow_entries = h.shadow_entries;
   }
   c->last_VI = c->h_ctr->VI;
   c->last_CI = c->h_ctr->CI;

@@ -54,22 +54,30 @@ struct DevScene {
 
 // ---------------------------------------------------------------- arena
 // One arena for all depth waves of a tile; wave d occupies
-// [base[d], base[d] + count[d]).  Structure of arrays, one float4 per field
-// group so every load/store is a coalesced 16-byte access.
+// [base[d], base[d] + count[d]).  Structure of arrays, one float4 (or float2)
+// per field group so every load/store is a coalesced 8- or 16-byte access.
 //   R0 = (origin xyz, pixel)            R1 = (direction xyz, A = beta_t p_t)
 //   R2 = (T at the hit xyz, S_ind)      R3 = (f|cos|/p xyz, NEE weight factor)
 //   R4 = (lineage lo, lineage hi, parent cell, 1 / sum beta_k p_k)
+//   H  = (t, primitive: -1 missed, -2 not traced)
 //   V0 = (E xyz, flags)                 V1 = (G xyz, first child)
-//   V2 = (NEE sum xyz, cell)            V3 = (NEE clamped sum xyz, beta_BSDF)
-//   V4 = (NEE clamped squares xyz, beta_NEE)
-//   V5 = (clamp limit xyz, beta_guided) V6 = (Le luminance, 1/S_beta, parent cell, bin)
+//   V2 = (clamp limit xyz, cell)        V3 = (beta BSDF, NEE, guided, first shadow ray)
+//   V4 = (Le luminance, 1/S_beta, parent cell, bin)
 //   S  = (sample value xyz, cost)
-constexpr int NR = 5, NV = 7;
+// NEE shadow rays of wave d occupy [sbase[d], sbase[d] + scount[d]) of a second
+// arena: SH0 = (origin xyz, tmax; < 0: nothing to trace), SH1 = (direction, -),
+// SH2 = (sample value if visible, -), zeroed by the shadow kernel when occluded.
+constexpr int NR = 5, NV = 5, NSH = 3;
+constexpr int SLOT_BYTES = (NR + NV + 1) * 16 + 8;  // per ray slot
+constexpr int SHADOW_BYTES = NSH * 16;              // per shadow-ray slot
 struct Arena {
   float4* R[NR];
+  float2* H;
   float4* V[NV];
   float4* S;
-  uint64_t cap;
+  float4* SH[NSH];
+  uint64_t cap;   // ray slots
+  uint64_t scap;  // shadow-ray slots
 };
 
 // V0.w flag bits
@@ -80,6 +88,9 @@ constexpr uint32_t F_EST = 1u << 25;
 struct DevCounters {
   unsigned long long base[MAXD + 2];
   unsigned long long count[MAXD + 2];
+  unsigned long long sbase[MAXD + 2];   // shadow rays of wave d
+  unsigned long long scount[MAXD + 2];
+  unsigned long long shadow_entries;     // shadow rays of committed tiles
   unsigned int overflow;       // this tile overflowed the arena
   unsigned int any_overflow;   // some tile of this iteration overflowed
   unsigned long long demand;   // rays the tile needed (may exceed the arena)
@@ -115,7 +126,7 @@ struct IterArgs {
 // launch wrappers (render.cu)
 cudaError_t launch_tile(const DevScene& s, const DevCache& c, const Arena& a, const IterArgs& it,
                         int num_sms, cudaStream_t st, cudaEvent_t* ev);
-constexpr int TILE_LAUNCHES_FIXED = 2;  // tile init + tile finish, besides 2 D wave kernels
+int tile_launches(int max_depth, int techniques);  // kernels launch_tile issues
 // image statistics (stats.cu)
 cudaError_t launch_image_stats(const DevCache& c, int width, int height, int n_prev, float outlier,
                                float* image_out_dev, cudaStream_t st);

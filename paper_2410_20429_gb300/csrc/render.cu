@@ -1,21 +1,29 @@
-// render.cu -- wavefront MARS path tracer: one shade kernel per depth wave and
-// one deepest-first reverse kernel per depth.
+// render.cu -- wavefront MARS path tracer.  Per depth wave d (rays in
+// [base[d], base[d] + count[d]) of the tile's arena):
 //
-// Shade (wave d): trace the wave's rays (camera rays for d = 1), weight any
-// emission reached against NEE (multi-sample balance heuristic, Sec. 3.1), and
-// at each vertex x_d with d <= D-1 run the secondary estimator's sampling half:
-// counts beta_t from the cache (T(x)/I_px x q, three cases, clamp; Sec. 3.1
-// "Optimization", Sec. 4.1 "Outlier clamping" / "Handling colors"), Alg. 1,
-// NEE samples with their shadow rays, and BSDF / guided children appended to
-// wave d+1 with a warp-aggregated allocation.
+//   k_trace  (wave d)  closest hit of every ray (camera rays for d = 1)
+//   k_shade  (wave d)  emission reached by the ray, weighted against NEE
+//                      (multi-sample balance heuristic, Sec. 3.1); at a vertex
+//                      x_d with d <= D-1 the sampling half of the secondary
+//                      estimator: counts beta_t from the cache (T(x)/I_px x q,
+//                      three cases, clamp; Sec. 3.1 "Optimization", Sec. 4.1),
+//                      Alg. 1, NEE samples written as shadow rays, BSDF / guided
+//                      children appended to wave d+1 (warp-aggregated
+//                      allocation)
+//   k_shadow (wave d)  one thread per NEE shadow ray: any hit zeroes the sample
 //
-// Reverse (wave d, deepest first): every ray's sample value
-//   <L_r,t> = f|cos|/p_t * (Le w_dir + w_ind <L_r(child vertex)>)
-// and cost (rays in its subtree, counting itself), the vertex's
-// <L_r> = sum_t 1/beta_t sum_s <L_r,t> (Sec. 3.1 "Secondary estimator"), and the
-// local statistics of Sec. 4.1 "Local estimates" (per cell and technique: n,
-// sum v, sum v^2, sum cost), pre-reduced over runs of equal cells in a warp
-// before float64 atomics.  A tile whose arena overflowed commits nothing.
+// then deepest first
+//
+//   k_reverse (wave d) every ray's sample value
+//                        <L_r,t> = f|cos|/p_t (Le w_dir + w_ind <L_r(child vertex)>)
+//                      and cost (rays in its subtree, counting itself), the
+//                      vertex's <L_r> = sum_t 1/beta_t sum_s <L_r,t> (Sec. 3.1
+//                      "Secondary estimator"), and the local statistics of
+//                      Sec. 4.1 "Local estimates" (per cell and technique: n,
+//                      sum v, sum v^2, sum cost), pre-reduced over runs of equal
+//                      cells in a warp before float64 atomics.
+//
+// A tile whose arena overflowed commits nothing.
 #include "device.cuh"
 
 namespace mars {
@@ -23,7 +31,9 @@ namespace mars {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
+constexpr int TRACE_THREADS = 128;
 constexpr int SHADE_THREADS = 128;
+constexpr int SHADOW_THREADS = 128;
 constexpr int REVERSE_THREADS = 128;
 
 __device__ __forceinline__ float4 f4(f3 a, float w) { return make_float4(a.x, a.y, a.z, w); }
@@ -38,11 +48,53 @@ __device__ __forceinline__ float nee_pdf(const DevScene& s, int l, f3 x, f3 y, f
   return l1.w * dot(dv, dv) / (l2.w * cosl);
 }
 
+// pinhole camera ray of pixel px with box-filter jitter (W/p = 1)
+__device__ __forceinline__ void camera_ray(const DevScene& s, const Rng& rng, uint32_t px, f3& o, f3& dir) {
+  const float4 u = rng.u4(px, DIM_CAMERA, 0);
+  const int ix = (int)(px % (uint32_t)s.width), iy = (int)(px / (uint32_t)s.width);
+  const float sx = (2.0f * ((float)ix + u.x) / (float)s.width - 1.0f) * s.tanh_half * s.aspect;
+  const float sy = (1.0f - 2.0f * ((float)iy + u.y) / (float)s.height) * s.tanh_half;
+  const f3 cf = mk3(s.cam_f[0], s.cam_f[1], s.cam_f[2]);
+  const f3 cr = mk3(s.cam_r[0], s.cam_r[1], s.cam_r[2]);
+  const f3 cu = mk3(s.cam_u[0], s.cam_u[1], s.cam_u[2]);
+  dir = normalize(cf + (cr * sx + cu * sy));
+  o = mk3(s.cam_o[0], s.cam_o[1], s.cam_o[2]);
+}
+
+// slots [base, base + n) of wave d, clamped to the arena
+struct Wave {
+  unsigned long long base, n;
+};
+__device__ __forceinline__ Wave wave_of(const DevCounters* ctr, const Arena& a, int d) {
+  const unsigned long long base = ctr->base[d], cnt = ctr->count[d];
+  return {base, cnt < a.cap - base ? cnt : a.cap - base};
+}
+
+// inclusive warp scan of a per-lane count, one atomicAdd per warp on *counter;
+// returns the lane's first slot relative to the counter's old value
+__device__ __forceinline__ unsigned long long warp_alloc(int n, int lane, unsigned long long* counter) {
+  int incl = n;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int y = __shfl_up_sync(FULL, incl, off);
+    if (lane >= off) incl += y;
+  }
+  const int total = __shfl_sync(FULL, incl, 31);
+  unsigned long long wbase = 0;
+  if (total > 0) {
+    if (lane == 31) wbase = atomicAdd(counter, (unsigned long long)total);
+    wbase = __shfl_sync(FULL, wbase, 31);
+  }
+  return wbase + (unsigned long long)(incl - n);
+}
+
 __global__ void k_tile_init(DevCounters* ctr, unsigned long long n0) {
   const int t = threadIdx.x;
   if (t < MAXD + 2) {
     ctr->base[t] = 0;
     ctr->count[t] = (t == 1) ? n0 : 0ull;
+    ctr->sbase[t] = 0;
+    ctr->scount[t] = 0;
   }
   if (t == 0) {
     ctr->overflow = 0;
@@ -59,25 +111,60 @@ __global__ void k_tile_finish(DevCounters* ctr, unsigned int* tile_status, int s
   }
   ctr->demand = dem;
   if (!ctr->overflow) {
-    unsigned long long tot = 0;
-    for (int d = 1; d <= D; ++d) tot += ctr->count[d];
+    unsigned long long tot = 0, sh = 0;
+    for (int d = 1; d <= D; ++d) {
+      tot += ctr->count[d];
+      sh += ctr->scount[d];
+    }
     ctr->entries += tot;
+    ctr->shadow_entries += sh;
   }
   tile_status[slot] = ctr->overflow;
   if (ctr->overflow) ctr->any_overflow = 1;
 }
 
+// ------------------------------------------------------------------ trace
+__global__ void __launch_bounds__(TRACE_THREADS) k_trace(const DevScene s, const DevCache c, const Arena a,
+                                                         const IterArgs it, const int d) {
+  const DevCounters* ctr = c.ctr;
+  // after an overflow some slots of this wave were never written: stop, the
+  // tile is re-rendered in smaller pieces
+  if (ctr->overflow) return;
+  const Wave w = wave_of(ctr, a, d);
+  const Rng rng{it.seed, it.job, it.iteration};
+  for (unsigned long long li = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; li < w.n;
+       li += gridDim.x * (unsigned long long)blockDim.x) {
+    const unsigned long long i = w.base + li;
+    f3 o, dir;
+    bool alive = true;
+    if (d == 1) {
+      camera_ray(s, rng, (uint32_t)(it.tile_begin + li), o, dir);
+    } else {
+      const float4 r0 = a.R[0][i], r1 = a.R[1][i];
+      o = xyz(r0);
+      dir = xyz(r1);
+      alive = r1.w > 0.0f;  // A = beta_t p_t is 0 for a drawn sample that is not traced
+    }
+    float t = 0.0f;
+    int prim = -2;  // -2: not traced, -1: traced and missed
+    if (alive) prim = trace_closest(s, o, dir, t);
+    a.H[i] = make_float2(t, __int_as_float(prim));
+  }
+}
+
+// ------------------------------------------------------------------ shade
 __global__ void __launch_bounds__(SHADE_THREADS) k_shade(const DevScene s, const DevCache c, const Arena a,
                                                          const IterArgs it, const int d) {
   DevCounters* ctr = c.ctr;
-  // after an overflow some slots of this wave were never written: stop here,
-  // the tile is re-rendered in smaller pieces
   if (ctr->overflow) return;
-  const unsigned long long base = ctr->base[d];
+  const Wave w = wave_of(ctr, a, d);
   const unsigned long long cnt = ctr->count[d];
-  const unsigned long long n = cnt < a.cap - base ? cnt : a.cap - base;
-  const unsigned long long base_next = base + cnt < a.cap ? base + cnt : a.cap;
-  if (blockIdx.x == 0 && threadIdx.x == 0) ctr->base[d + 1] = base_next;
+  const unsigned long long base_next = w.base + cnt < a.cap ? w.base + cnt : a.cap;
+  const unsigned long long sbase = d == 1 ? 0ull : ctr->sbase[d - 1] + ctr->scount[d - 1];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctr->base[d + 1] = base_next;
+    ctr->sbase[d] = sbase;
+  }
 
   const int lane = threadIdx.x & 31;
   const unsigned long long gw = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
@@ -90,28 +177,22 @@ __global__ void __launch_bounds__(SHADE_THREADS) k_shade(const DevScene s, const
   const Rng rng{it.seed, it.job, it.iteration};
   const float inf = __int_as_float(0x7f800000);
 
-  for (unsigned long long c0 = gw * 32; c0 < n; c0 += nw * 32) {
+  for (unsigned long long c0 = gw * 32; c0 < w.n; c0 += nw * 32) {
     const unsigned long long li = c0 + lane;
-    const bool active = li < n;
-    const unsigned long long i = base + li;
+    const bool active = li < w.n;
+    const unsigned long long i = w.base + li;
 
-    // ---- the ray of this slot
+    // ---- the ray of this slot and its hit
     f3 o = mk3(0.f, 0.f, 0.f), dir = mk3(0.f, 0.f, 1.f), T = mk3(1.f, 1.f, 1.f), fcp = mk3(1.f, 1.f, 1.f);
     float A = 1.0f, S_ind = 1.0f, bwN = 0.0f, invSb = 0.0f;
     uint64_t lin = 0;
     uint32_t px = 0, parent_cell = 0;
+    float th = 0.0f;
+    int prim = -2;
     if (active) {
       if (camera) {
         px = (uint32_t)(it.tile_begin + li);
-        const float4 u = rng.u4(px, DIM_CAMERA, 0);
-        const int ix = (int)(px % (uint32_t)s.width), iy = (int)(px / (uint32_t)s.width);
-        const float sx = (2.0f * ((float)ix + u.x) / (float)s.width - 1.0f) * s.tanh_half * s.aspect;
-        const float sy = (1.0f - 2.0f * ((float)iy + u.y) / (float)s.height) * s.tanh_half;
-        const f3 cf = mk3(s.cam_f[0], s.cam_f[1], s.cam_f[2]);
-        const f3 cr = mk3(s.cam_r[0], s.cam_r[1], s.cam_r[2]);
-        const f3 cu = mk3(s.cam_u[0], s.cam_u[1], s.cam_u[2]);
-        dir = normalize(cf + (cr * sx + cu * sy));
-        o = mk3(s.cam_o[0], s.cam_o[1], s.cam_o[2]);
+        camera_ray(s, rng, px, o, dir);
       } else {
         const float4 r0 = a.R[0][i], r1 = a.R[1][i], r2 = a.R[2][i], r3 = a.R[3][i], r4 = a.R[4][i];
         o = xyz(r0);
@@ -126,158 +207,140 @@ __global__ void __launch_bounds__(SHADE_THREADS) k_shade(const DevScene s, const
         parent_cell = __float_as_uint(r4.z);
         invSb = r4.w;
       }
+      const float2 h = a.H[i];
+      th = h.x;
+      prim = __float_as_int(h.y);
     }
-    const bool alive = active && (camera || A > 0.0f);
 
-    // ---- closest hit and emission
     f3 E = mk3(0.f, 0.f, 0.f);
     float Le_lum = 0.0f;
     const f3 G = camera ? mk3(1.f, 1.f, 1.f) : (S_ind > 0.0f ? fcp * (A / S_ind) : mk3(0.f, 0.f, 0.f));
-    uint32_t flags = 0;
-    int n_ext = 0;
+    uint32_t flags = prim >= -1 ? F_TRACED : 0u;
     int gam[NT] = {0, 0, 0};
     float beta[NT] = {0.f, 0.f, 0.f};
     int cell = 0;
-    f3 p, ns, wo, nsum = mk3(0.f, 0.f, 0.f), nm1 = mk3(0.f, 0.f, 0.f), nm2 = mk3(0.f, 0.f, 0.f);
+    f3 p = mk3(0.f, 0.f, 0.f), ns = mk3(0.f, 0.f, 1.f), wo = mk3(0.f, 0.f, 1.f);
     f3 climit = mk3(inf, inf, inf);
-    Frame fr;
     Mat mat;
-    const float* cdf = nullptr;
-    if (alive) {
-      flags |= F_TRACED;
-      float th;
-      const int prim = trace_closest(s, o, dir, th);
-      if (prim >= 0) {
-        p = o + dir * th;
-        const f3 ng = prim_normal(s.prims, prim, p);
-        wo = dir * -1.0f;
-        const int m = prim_material(s.prims, prim);
-        const float4 m0 = __ldg(s.mats + 3 * m), m1 = __ldg(s.mats + 3 * m + 1), m2 = __ldg(s.mats + 3 * m + 2);
-        const float cosg = dot(ng, wo);
-        if (cosg > 0.0f && m0.w > 0.0f) {
-          float w_dir = 1.0f;
-          if (!camera) {
-            float pn = 0.0f;
-            if (bwN > 0.0f && prim < s.n_quads) {
-              const int l = __float_as_int(__ldg(&s.prims[4 * prim + 3].w));
-              if (l >= 0) pn = nee_pdf(s, l, o, p, dir);
-            }
-            const float den = S_ind + bwN * pn;
-            w_dir = den > 0.0f ? A / den : 0.0f;
+    mat.type = 0;
+    mat.alpha = 1.0f;
+    mat.col = mk3(0.f, 0.f, 0.f);
+    if (prim >= 0) {
+      p = o + dir * th;
+      const f3 ng = prim_normal(s.prims, prim, p);
+      wo = dir * -1.0f;
+      const int m = prim_material(s.prims, prim);
+      const float4 m0 = __ldg(s.mats + 3 * m), m1 = __ldg(s.mats + 3 * m + 1), m2 = __ldg(s.mats + 3 * m + 2);
+      const float cosg = dot(ng, wo);
+      if (cosg > 0.0f && m0.w > 0.0f) {
+        float w_dir = 1.0f;
+        if (!camera) {
+          float pn = 0.0f;
+          if (bwN > 0.0f && prim < s.n_quads) {
+            const int l = __float_as_int(__ldg(&s.prims[4 * prim + 3].w));
+            if (l >= 0) pn = nee_pdf(s, l, o, p, dir);
           }
-          const f3 Le = xyz(m2);
-          E = mul(fcp, Le * w_dir);
-          Le_lum = lum(Le);
+          const float den = S_ind + bwN * pn;
+          w_dir = den > 0.0f ? A / den : 0.0f;
         }
-        if (est_depth && m0.z > 0.0f) {
-          // ---- secondary estimator at x_d: budgets, Alg. 1, NEE, children
-          flags |= F_EST;
-          ns = cosg >= 0.0f ? ng : ng * -1.0f;
-          fr = make_frame(ns);
-          cell = cell_of(s, c.grid_n, p);
-          mat.type = (int)m0.x;
-          mat.alpha = m0.y;
-          mat.col = xyz(m1);
-          const float4 est = it.has_estimate ? c.est[px] : make_float4(1.f, 1.f, 1.f, 0.f);
-          if (it.collect && it.has_estimate) {
-            climit.x = T.x > 0.0f ? it.outlier * est.x / T.x : inf;
-            climit.y = T.y > 0.0f ? it.outlier * est.y / T.y : inf;
-            climit.z = T.z > 0.0f ? it.outlier * est.z / T.z : inf;
-          }
-          // counts without learned statistics: one NEE sample and one
-          // continuation sample split evenly over BSDF and guided sampling
-          const float base_cont = (on_b && on_g) ? 0.5f : 1.0f;
+        const f3 Le = xyz(m2);
+        E = mul(fcp, Le * w_dir);
+        Le_lum = lum(Le);
+      }
+      if (est_depth && m0.z > 0.0f) {
+        // ---- budgets and Alg. 1 at vertex x_d
+        flags |= F_EST;
+        ns = cosg >= 0.0f ? ng : ng * -1.0f;
+        cell = cell_of(s, c.grid_n, p);
+        mat.type = (int)m0.x;
+        mat.alpha = m0.y;
+        mat.col = xyz(m1);
+        const float4 est = it.has_estimate ? c.est[px] : make_float4(1.f, 1.f, 1.f, 0.f);
+        if (it.collect && it.has_estimate) {
+          climit.x = T.x > 0.0f ? it.outlier * est.x / T.x : inf;
+          climit.y = T.y > 0.0f ? it.outlier * est.y / T.y : inf;
+          climit.z = T.z > 0.0f ? it.outlier * est.z / T.z : inf;
+        }
+        // counts without learned statistics: one NEE sample and one
+        // continuation sample split evenly over BSDF and guided sampling
+        const float base_cont = (on_b && on_g) ? 0.5f : 1.0f;
 #pragma unroll
-          for (int t = 0; t < NT; ++t) {
-            const bool on = (c.techniques >> t) & 1;
-            float b = on ? (t == 1 ? 1.0f : base_cont) : 0.0f;
-            if (on && it.mode == MARS_MODE_MARS) {
-              const float4 qr = __ldg(c.cnt + (2 * (NT * cell + t)));
-              if (qr.w > 0.0f) {
-                const float4 qs = __ldg(c.cnt + (2 * (NT * cell + t) + 1));
-                const f3 f = mk3(T.x / est.x, T.y / est.y, T.z / est.z);
-                const f3 ar = mul(f, xyz(qr)), as = mul(f, xyz(qs));
-                const float brr = sqrtf(dot(ar, ar) / 3.0f), bs = sqrtf(dot(as, as) / 3.0f);
-                b = brr < 1.0f ? brr : (bs > 1.0f ? bs : 1.0f);
-                b = fminf(fmaxf(b, it.clamp_lo), it.clamp_hi);
-              }
+        for (int t = 0; t < NT; ++t) {
+          const bool on = (c.techniques >> t) & 1;
+          float b = on ? (t == 1 ? 1.0f : base_cont) : 0.0f;
+          if (on && it.mode == MARS_MODE_MARS) {
+            const float4 qr = __ldg(c.cnt + (2 * (NT * cell + t)));
+            if (qr.w > 0.0f) {
+              const float4 qs = __ldg(c.cnt + (2 * (NT * cell + t) + 1));
+              const f3 f = mk3(T.x / est.x, T.y / est.y, T.z / est.z);
+              const f3 ar = mul(f, xyz(qr)), as = mul(f, xyz(qs));
+              const float brr = sqrtf(dot(ar, ar) / 3.0f), bs = sqrtf(dot(as, as) / 3.0f);
+              b = brr < 1.0f ? brr : (bs > 1.0f ? bs : 1.0f);
+              b = fminf(fmaxf(b, it.clamp_lo), it.clamp_hi);
             }
-            beta[t] = b;
           }
-          // Alg. 1: one uniform decides the rounding of every technique
-          float r = rng.u4(px, DIM_ROUND, lin).x;
+          beta[t] = b;
+        }
+        // Alg. 1: one uniform decides the rounding of every technique
+        float r = rng.u4(px, DIM_ROUND, lin).x;
 #pragma unroll
-          for (int t = 0; t < NT; ++t) {
-            if (!((c.techniques >> t) & 1)) continue;
-            const float sm = beta[t] + r;
-            const int g = (int)floorf(sm);
-            gam[t] = g;
-            r = sm - (float)g;
-          }
-          const float bwB = on_b ? (it.aware ? beta[0] : 1.0f) : 0.0f;
-          const float bwNv = on_n ? (it.aware ? beta[1] : 1.0f) : 0.0f;
-          const float bwG = on_g ? (it.aware ? beta[2] : 1.0f) : 0.0f;
-          if (on_g) cdf = c.guide_cdf + (size_t)cell * GUIDE_BINS;
-          const f3 wol = fr.to_local(wo);
-          const f3 xo = p + ns * s.eps;
-          // NEE samples (primary estimator of NEE), traced here
-          for (int sidx = 0; sidx < gam[1]; ++sidx) {
-            const float4 u = rng.u4(px, 32u + (uint32_t)sidx, lin);
-            int l = s.n_lights - 1;
-            for (int k = 0; k < s.n_lights; ++k)
-              if (u.x < __ldg(&s.lights[5 * k].w)) { l = k; break; }
-            const float4 l0 = __ldg(s.lights + 5 * l), l1 = __ldg(s.lights + 5 * l + 1),
-                         l2 = __ldg(s.lights + 5 * l + 2), l4 = __ldg(s.lights + 5 * l + 4);
-            const f3 y = xyz(l0) + (xyz(l1) * u.y + xyz(l2) * u.z);
-            const f3 dv = y - xo;
-            const float dist = sqrtf(dot(dv, dv));
-            const f3 wi = dv * (1.0f / dist);
-            const float pn = nee_pdf(s, l, xo, y, wi);
-            const float ci = dot(ns, wi);
-            f3 v = mk3(0.f, 0.f, 0.f);
-            if (pn > 0.0f && ci > 0.0f) {
-              float pb;
-              const f3 fc = bsdf_eval(mat, wol, fr.to_local(wi), pb);
-              const float pg = on_g ? guide_pdf(cdf, wi) : 0.0f;
-              if (nonzero(fc) && !trace_any(s, xo, wi, dist - s.eps)) {
-                const float den = bwB * pb + bwG * pg + bwNv * pn;
-                const float w = bwNv * pn / den;
-                v = mk3(fc.x * l4.x / pn * w, fc.y * l4.y / pn * w, fc.z * l4.z / pn * w);
-              }
-            }
-            nsum = nsum + v;
-            const f3 vc = fmin3(v, climit);
-            nm1 = nm1 + vc;
-            nm2 = nm2 + mul(vc, vc);
-          }
-          n_ext = gam[0] + gam[2];
+        for (int t = 0; t < NT; ++t) {
+          if (!((c.techniques >> t) & 1)) continue;
+          const float sm = beta[t] + r;
+          const int g = (int)floorf(sm);
+          gam[t] = g;
+          r = sm - (float)g;
         }
       }
     }
 
-    // ---- warp-aggregated allocation of the children in wave d+1
-    int incl = n_ext;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const int y = __shfl_up_sync(FULL, incl, off);
-      if (lane >= off) incl += y;
-    }
-    const int total = __shfl_sync(FULL, incl, 31);
-    unsigned long long wbase = 0;
-    if (total > 0) {
-      if (lane == 31) wbase = atomicAdd(&ctr->count[d + 1], (unsigned long long)total);
-      wbase = __shfl_sync(FULL, wbase, 31);
-    }
-    const unsigned long long first = base_next + wbase + (unsigned long long)(incl - n_ext);
-    const bool fits = first + (unsigned long long)n_ext <= a.cap;
-    if (n_ext > 0 && !fits) atomicOr(&ctr->overflow, 1u);
+    // ---- slots for the children (wave d+1) and the NEE shadow rays
+    const int n_ext = gam[0] + gam[2], n_sh = gam[1];
+    const unsigned long long first = base_next + warp_alloc(n_ext, lane, &ctr->count[d + 1]);
+    const unsigned long long sfirst = sbase + warp_alloc(n_sh, lane, &ctr->scount[d]);
+    const bool fits = first + (unsigned long long)n_ext <= a.cap && sfirst + (unsigned long long)n_sh <= a.scap;
+    if ((n_ext > 0 || n_sh > 0) && !fits) atomicOr(&ctr->overflow, 1u);
 
-    if (n_ext > 0 && fits) {
+    if ((flags & F_EST) && fits) {
+      const Frame fr = make_frame(ns);
+      const f3 wol = fr.to_local(wo);
+      const f3 xo = p + ns * s.eps;
       const float bwB = on_b ? (it.aware ? beta[0] : 1.0f) : 0.0f;
       const float bwNv = on_n ? (it.aware ? beta[1] : 1.0f) : 0.0f;
       const float bwG = on_g ? (it.aware ? beta[2] : 1.0f) : 0.0f;
-      const f3 wol = fr.to_local(wo);
-      const f3 xo = p + ns * s.eps;
+      const float* cdf = on_g ? c.guide_cdf + (size_t)cell * GUIDE_BINS : nullptr;
+      // NEE samples (primary estimator of NEE), value assuming the light is visible
+      for (int sidx = 0; sidx < n_sh; ++sidx) {
+        const float4 u = rng.u4(px, 32u + (uint32_t)sidx, lin);
+        int l = s.n_lights - 1;
+        for (int k = 0; k < s.n_lights; ++k)
+          if (u.x < __ldg(&s.lights[5 * k].w)) { l = k; break; }
+        const float4 l0 = __ldg(s.lights + 5 * l), l1 = __ldg(s.lights + 5 * l + 1),
+                     l2 = __ldg(s.lights + 5 * l + 2), l4 = __ldg(s.lights + 5 * l + 4);
+        const f3 y = xyz(l0) + (xyz(l1) * u.y + xyz(l2) * u.z);
+        const f3 dv = y - xo;
+        const float dist = sqrtf(dot(dv, dv));
+        const f3 wi = dv * (1.0f / dist);
+        const float pn = nee_pdf(s, l, xo, y, wi);
+        const float ci = dot(ns, wi);
+        f3 v = mk3(0.f, 0.f, 0.f);
+        if (pn > 0.0f && ci > 0.0f) {
+          float pb;
+          const f3 fc = bsdf_eval(mat, wol, fr.to_local(wi), pb);
+          const float pg = on_g ? guide_pdf(cdf, wi) : 0.0f;
+          if (nonzero(fc)) {
+            const float den = bwB * pb + bwG * pg + bwNv * pn;
+            const float wgt = bwNv * pn / den;
+            v = mk3(fc.x * l4.x / pn * wgt, fc.y * l4.y / pn * wgt, fc.z * l4.z / pn * wgt);
+          }
+        }
+        const unsigned long long j = sfirst + sidx;
+        // tmax < 0 marks a sample that needs no shadow ray (its value is 0)
+        a.SH[0][j] = f4(xo, nonzero(v) ? dist - s.eps : -1.0f);
+        a.SH[1][j] = f4(wi, 0.0f);
+        a.SH[2][j] = f4(v, 0.0f);
+      }
+      // BSDF and guided children (primary estimators that continue the path)
       for (int k = 0; k < n_ext; ++k) {
         const int t = k < gam[0] ? 0 : 2;
         const int sidx = t == 0 ? k : k - gam[0];
@@ -328,19 +391,35 @@ __global__ void __launch_bounds__(SHADE_THREADS) k_shade(const DevScene s, const
     if (active) {
       flags |= (uint32_t)gam[0] | ((uint32_t)gam[1] << 8) | ((uint32_t)gam[2] << 16);
       a.V[0][i] = f4(E, __uint_as_float(flags));
-      a.V[1][i] = f4(G, __uint_as_float((uint32_t)(fits ? first : 0ull)));
       if (flags & F_EST) {
-        a.V[2][i] = f4(nsum, __uint_as_float((uint32_t)cell));
-        a.V[3][i] = f4(nm1, beta[0]);
-        a.V[4][i] = f4(nm2, beta[1]);
-        a.V[5][i] = f4(climit, beta[2]);
+        a.V[1][i] = f4(G, __uint_as_float((uint32_t)(fits ? first : 0ull)));
+        a.V[2][i] = f4(climit, __uint_as_float((uint32_t)cell));
+        a.V[3][i] = make_float4(beta[0], beta[1], beta[2], __uint_as_float((uint32_t)(fits ? sfirst : 0ull)));
       }
       if (on_g && it.collect && !camera && (flags & F_TRACED))
-        a.V[6][i] = make_float4(Le_lum, invSb, __uint_as_float(parent_cell), __int_as_float(guide_bin(dir)));
+        a.V[4][i] = make_float4(Le_lum, invSb, __uint_as_float(parent_cell), __int_as_float(guide_bin(dir)));
     }
   }
 }
 
+// ----------------------------------------------------------------- shadow
+__global__ void __launch_bounds__(SHADOW_THREADS) k_shadow(const DevScene s, const DevCache c, const Arena a,
+                                                           const int d) {
+  const DevCounters* ctr = c.ctr;
+  if (ctr->overflow) return;
+  const unsigned long long sb = ctr->sbase[d], sc = ctr->scount[d];
+  const unsigned long long n = sc < a.scap - sb ? sc : a.scap - sb;
+  for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < n;
+       k += gridDim.x * (unsigned long long)blockDim.x) {
+    const unsigned long long j = sb + k;
+    const float4 s0 = a.SH[0][j];
+    if (!(s0.w > 0.0f)) continue;
+    const float4 s1 = a.SH[1][j];
+    if (trace_any(s, xyz(s0), xyz(s1), s0.w)) a.SH[2][j] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+// ---------------------------------------------------------------- reverse
 // inclusive scan restricted to runs of equal keys (start = first lane of the run)
 __device__ __forceinline__ float seg_scan(float v, int lane, int start) {
 #pragma unroll
@@ -355,19 +434,17 @@ __global__ void __launch_bounds__(REVERSE_THREADS) k_reverse(const DevScene s, c
                                                              const IterArgs it, const int d) {
   DevCounters* ctr = c.ctr;
   if (ctr->overflow) return;  // the tile is re-rendered; commit nothing
-  const unsigned long long base = ctr->base[d];
-  const unsigned long long cnt = ctr->count[d];
-  const unsigned long long n = cnt < a.cap - base ? cnt : a.cap - base;
+  const Wave w = wave_of(ctr, a, d);
   const int lane = threadIdx.x & 31;
   const unsigned long long gw = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
   const unsigned long long nw = (gridDim.x * (unsigned long long)blockDim.x) >> 5;
   const bool on_n = c.techniques & MARS_TECH_NEE, on_g = c.techniques & MARS_TECH_GUIDED;
   const bool collect = it.collect != 0;
 
-  for (unsigned long long c0 = gw * 32; c0 < n; c0 += nw * 32) {
+  for (unsigned long long c0 = gw * 32; c0 < w.n; c0 += nw * 32) {
     const unsigned long long li = c0 + lane;
-    const bool active = li < n;
-    const unsigned long long i = base + li;
+    const bool active = li < w.n;
+    const unsigned long long i = w.base + li;
     uint32_t flags = 0;
     f3 E = mk3(0.f, 0.f, 0.f), Lr = mk3(0.f, 0.f, 0.f);
     uint32_t csub = 0;
@@ -383,21 +460,27 @@ __global__ void __launch_bounds__(REVERSE_THREADS) k_reverse(const DevScene s, c
       E = xyz(v0);
       flags = __float_as_uint(v0.w);
       if (flags & F_EST) {
-        const float4 v1 = a.V[1][i], v3 = a.V[3][i], v4 = a.V[4][i], v5 = a.V[5][i];
+        const float4 v1 = a.V[1][i], v2 = a.V[2][i], v3 = a.V[3][i];
         const int gB = flags & 0xff, gN = (flags >> 8) & 0xff, gG = (flags >> 16) & 0xff;
-        bt[0] = v3.w; bt[1] = v4.w; bt[2] = v5.w;
-        const f3 climit = xyz(v5);
-        const unsigned long long first = __float_as_uint(v1.w);
-        const float4 v2 = a.V[2][i];
+        bt[0] = v3.x; bt[1] = v3.y; bt[2] = v3.z;
+        const f3 climit = xyz(v2);
         key = __float_as_uint(v2.w);
         if (gN > 0) {
-          Lr = mk3(v2.x / bt[1], v2.y / bt[1], v2.z / bt[1]);
+          const unsigned long long sf = __float_as_uint(v3.w);
+          f3 sum = mk3(0.f, 0.f, 0.f);
+          for (int k = 0; k < gN; ++k) {
+            const f3 v = xyz(a.SH[2][sf + k]);
+            sum = sum + v;
+            const f3 vc = fmin3(v, climit);
+            st[1][1] += vc.x; st[1][2] += vc.y; st[1][3] += vc.z;
+            st[1][4] += vc.x * vc.x; st[1][5] += vc.y * vc.y; st[1][6] += vc.z * vc.z;
+          }
+          Lr = mk3(sum.x / bt[1], sum.y / bt[1], sum.z / bt[1]);
           csub += (uint32_t)gN;
           st[1][0] = (float)gN;
-          st[1][1] = v3.x; st[1][2] = v3.y; st[1][3] = v3.z;
-          st[1][4] = v4.x; st[1][5] = v4.y; st[1][6] = v4.z;
           st[1][7] = (float)gN;
         }
+        const unsigned long long first = __float_as_uint(v1.w);
         const int ne = gB + gG;
         for (int k = 0; k < ne; ++k) {
           const float4 sv = a.S[first + k];
@@ -422,10 +505,10 @@ __global__ void __launch_bounds__(REVERSE_THREADS) k_reverse(const DevScene s, c
       a.S[i] = f4(E, __uint_as_float(cost));
       if (d == 1) c.img[it.tile_begin + li] = f4(E, 0.0f);
       if (on_g && collect && d >= 2 && (flags & F_TRACED)) {
-        const float4 v6 = a.V[6][i];
-        const float w = (v6.x + lum(Lr)) * v6.y;
-        if (w > 0.0f)
-          atomicAdd(c.guide_hist + (size_t)__float_as_uint(v6.z) * GUIDE_BINS + __float_as_int(v6.w), w);
+        const float4 v4 = a.V[4][i];
+        const float wdep = (v4.x + lum(Lr)) * v4.y;
+        if (wdep > 0.0f)
+          atomicAdd(c.guide_hist + (size_t)__float_as_uint(v4.z) * GUIDE_BINS + __float_as_int(v4.w), wdep);
       }
     }
 
@@ -491,20 +574,28 @@ cudaError_t launch_tile(const DevScene& s, const DevCache& c, const Arena& a, co
   const unsigned long long n0 = (unsigned long long)(it.tile_end - it.tile_begin);
   k_tile_init<<<1, 32, 0, st>>>(c.ctr, n0);
   const int D = c.max_depth;
-  const int gshade = num_sms * 8, grev = num_sms * 8;
-  // ev (optional): ev[0] before the first shade kernel, ev[d] after shade d,
-  // ev[D + k] after the k-th reverse kernel
+  const int g = num_sms * 8;
+  // ev (optional, 4 D + 1 events): ev[0] first; after wave d's trace, shade and
+  // shadow kernels ev[3(d-1) + 1..3]; after the k-th reverse kernel ev[3 D + k]
   if (ev) cudaEventRecord(ev[0], st);
   for (int d = 1; d <= D; ++d) {
-    k_shade<<<gshade, SHADE_THREADS, 0, st>>>(s, c, a, it, d);
-    if (ev) cudaEventRecord(ev[d], st);
+    k_trace<<<g, TRACE_THREADS, 0, st>>>(s, c, a, it, d);
+    if (ev) cudaEventRecord(ev[3 * (d - 1) + 1], st);
+    k_shade<<<g, SHADE_THREADS, 0, st>>>(s, c, a, it, d);
+    if (ev) cudaEventRecord(ev[3 * (d - 1) + 2], st);
+    if (d <= D - 1 && (c.techniques & MARS_TECH_NEE)) k_shadow<<<g, SHADOW_THREADS, 0, st>>>(s, c, a, d);
+    if (ev) cudaEventRecord(ev[3 * (d - 1) + 3], st);
   }
   for (int d = D; d >= 1; --d) {
-    k_reverse<<<grev, REVERSE_THREADS, 0, st>>>(s, c, a, it, d);
-    if (ev) cudaEventRecord(ev[D + (D - d + 1)], st);
+    k_reverse<<<g, REVERSE_THREADS, 0, st>>>(s, c, a, it, d);
+    if (ev) cudaEventRecord(ev[3 * D + (D - d + 1)], st);
   }
   k_tile_finish<<<1, 32, 0, st>>>(c.ctr, c.tile_status, it.tile_slot, D);
   return cudaGetLastError();
+}
+
+int tile_launches(int max_depth, int techniques) {
+  return 2 + 2 * max_depth + max_depth + ((techniques & MARS_TECH_NEE) ? max_depth - 1 : 0);
 }
 
 }  // namespace mars

@@ -122,8 +122,9 @@ class Cache:
         return {"VI": st.VI, "CI": st.CI, "rays": st.rays, "vertices": st.vertices,
                 "estimator_vertices": st.estimator_vertices, "mean_beta": list(st.mean_beta),
                 "tiles": st.tiles, "retries": st.retries, "arena_demand": st.arena_demand,
-                "launches": st.launches, "shade_launches": st.shade_launches, "shade_ms": st.shade_ms,
-                "reverse_ms": st.reverse_ms, "image_ms": st.image_ms, "wave_entries": st.wave_entries}
+                "launches": st.launches, "wave_launches": st.wave_launches, "trace_ms": st.trace_ms,
+                "shade_ms": st.shade_ms, "shadow_ms": st.shadow_ms, "reverse_ms": st.reverse_ms,
+                "image_ms": st.image_ms, "wave_entries": st.wave_entries, "shadow_entries": st.shadow_entries}
 
     def update_counts(self, stream=None) -> None:
         A.check(self._lib.mars_update_counts(self.handle, _stream_handle(stream)), "mars_update_counts")
