@@ -177,6 +177,10 @@ def run_mars(args):
     for _ in range(args.warmup):
         step(it, M.MARS_MODE_WARMUP)
         it += 1
+    # launch shape of the wave kernels picked by the library's autotuner on a
+    # MARS iteration with the counts learned so far (no state change)
+    launch = cache.autotune(iteration=it, seed=seed, mode=M.MARS_MODE_MARS, repeats=2, stream=stream) \
+        if not args.no_autotune else cache.get_launch()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -258,6 +262,8 @@ def run_mars(args):
                      "mean_beta": [round(sum(s["mean_beta"][t] for s in sts) / args.steps, 4) for t in range(3)],
                      "tiles": sum(s["tiles"] for s in sts) / args.steps},
         "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+        "launch": {"kernels": ["trace", "shade", "shadow", "reverse"], **launch,
+                   "autotuned": not args.no_autotune},
     }
 
     if rank == 0 and not args.no_efficiency:
@@ -398,6 +404,7 @@ def main():
     ap.add_argument("--ref-spp", type=int, default=256)
     ap.add_argument("--eff-spp", type=int, default=32)
     ap.add_argument("--ref-pixels-per-step", type=int, default=1024)
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "mars":
         ap.error("--warmup must be at least 3")

@@ -231,6 +231,32 @@ mars_status mars_update_counts(mars_cache* cache, void* stream);
 mars_status mars_cache_get_state(mars_cache* cache, mars_cache_state* state, void* stream);
 mars_status mars_cache_set_state(mars_cache* cache, const mars_cache_state* state, void* stream);
 
+/* ---- launch shape and autotuning ---------------------------------------------
+ * The four per-wave kernels (closest hit, shading and sampling, NEE shadow
+ * rays, deepest-first reverse pass) each run a persistent grid of
+ * SMs x blocks_per_sm blocks that strides over its wave in chunks of 32 slots;
+ * the launch shape changes their speed, never their results.
+ * threads[k]: threads per block of kernel k (0 trace, 1 shade, 2 shadow,
+ *   3 reverse), a multiple of 32 in 32..256.
+ * blocks_per_sm[k]: 1..64, or 0 = as many blocks as fit on an SM at once
+ *   (mars_cache_get_launch reports the resolved count).  Default: 128 threads,
+ *   the occupancy maximum.  Errors: INVALID_ARG, CUDA. */
+typedef struct {
+  int32_t threads[4];
+  int32_t blocks_per_sm[4];
+} mars_launch_config;
+mars_status mars_cache_get_launch(const mars_cache* cache, mars_launch_config* out);
+mars_status mars_cache_set_launch(mars_cache* cache, const mars_launch_config* config);
+/* Picks each wave kernel's launch shape in turn (threads per block in
+ * {64, 128, 256} x blocks per SM in {half, full, twice} the occupancy maximum)
+ * by the kernel's device time over `repeats` (1..100) renders of `params`'s
+ * iteration, rendered without statistics, guide deposits or image statistics
+ * so that the cache's learned state is unchanged; keeps the fastest shape and
+ * writes it to `chosen` (may be NULL).  Synchronises `stream` after every
+ * render.  Errors: INVALID_ARG, and those of mars_render_iteration. */
+mars_status mars_cache_autotune(mars_cache* cache, const mars_iter_params* params, int32_t repeats,
+                                mars_launch_config* chosen, void* stream);
+
 /* ---- serving ----------------------------------------------------------------
  * A server owns a host scheduler thread that admits render jobs while their
  * estimated device footprint fits `memory_budget_bytes` and fewer than
@@ -239,10 +265,11 @@ mars_status mars_cache_set_state(mars_cache* cache, const mars_cache_state* stat
 typedef struct {
   const mars_scene_desc* scene;
   mars_cache_desc cache;
-  uint32_t seed;
+  uint32_t seed;           /* Philox key of the job: (seed, key) */
   int32_t iterations;      /* fixed-point iterations of the job */
   int32_t warmup;          /* leading iterations with beta = 1 */
-  int32_t reserved;
+  uint32_t key;            /* second Philox key word; a job's random numbers depend
+                              on (seed, key) only, never on the server's job id */
 } mars_job_desc;
 
 typedef enum { MARS_JOB_QUEUED = 0, MARS_JOB_RUNNING = 1, MARS_JOB_DONE = 2, MARS_JOB_FAILED = 3 } mars_job_state;
@@ -254,6 +281,7 @@ typedef struct {
   int32_t reserved;
   double submit_s, start_s, end_s;   /* wall-clock seconds since server creation */
   double iter_ms_p50, iter_ms_p99;   /* per-iteration latency */
+  uint64_t device_bytes;             /* device memory the job was admitted with */
 } mars_job_status;
 
 mars_status mars_server_create(uint64_t memory_budget_bytes, int32_t max_slots, mars_server** out);

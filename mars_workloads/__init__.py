@@ -16,6 +16,7 @@ from .scenes import (  # noqa: F401
     random_count_fields,
     random_guide_cdf,
     random_pixel_estimate,
+    serving_requests,
     TECH_BSDF,
     TECH_NEE,
     TECH_GUIDED,

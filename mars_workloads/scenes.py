@@ -263,16 +263,42 @@ def random_count_fields(n_cells: int, seed: int, lo: float = 0.05, hi: float = 4
 
 
 def random_guide_cdf(n_cells: int, seed: int, sparsity: float = 0.7) -> np.ndarray:
-    """Seeded per-cell inclusive CDFs over the 256 directional bins, in float32,
-    mixing a sparse random histogram with 10 % uniform so every bin is positive."""
+    """Seeded per-cell inclusive CDFs over the 256 directional bins, in float32:
+    a sparse random histogram plus a small positive floor, normalised, so that
+    every bin has a positive probability and some bins dominate."""
     rng = np.random.default_rng(seed)
     h = rng.exponential(1.0, size=(n_cells, GUIDE_BINS))
     h[rng.uniform(size=h.shape) < sparsity] = 0.0
-    tot = h.sum(axis=1, keepdims=True)
-    p = np.where(tot > 0, 0.9 * h / np.where(tot > 0, tot, 1.0) + 0.1 / GUIDE_BINS, 1.0 / GUIDE_BINS)
-    cdf = np.cumsum(p, axis=1)
+    h += rng.uniform(0.005, 0.05, size=(n_cells, 1))
+    cdf = np.cumsum(h / h.sum(axis=1, keepdims=True), axis=1)
     cdf[:, -1] = 1.0
     return cdf.astype(np.float32)
+
+
+def serving_requests(n: int = 256, rate: float = 20.0, seed: int = 0,
+                     resolutions=(64, 128, 256, 512), spheres=(16, 4096), iterations=(4, 16),
+                     warmup: int = 3):
+    """A seeded stream of render requests: Poisson arrivals at ``rate`` per
+    second (exponential gaps), a square resolution drawn uniformly from
+    ``resolutions`` (log-uniform over 64^2 .. 512^2), a room with a log-uniform
+    number of spheres in ``spheres`` and 4 ceiling lights, and a uniform number
+    of fixed-point iterations in ``iterations`` (at least warmup + 1).  Every
+    request carries its own scene seed and Philox key."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for k in range(n):
+        t += rng.exponential(1.0 / rate)
+        res = int(resolutions[rng.integers(len(resolutions))])
+        ns = int(round(math.exp(rng.uniform(math.log(spheres[0]), math.log(spheres[1])))))
+        iters = int(rng.integers(iterations[0], iterations[1] + 1))
+        scene_seed = int(rng.integers(1, 2 ** 31))
+        sc = guided_room_scene(scene_seed, res, res, n_spheres=ns)
+        sc.name = f"room{ns}_{res}x{res}"
+        out.append({"arrival_s": t, "scene": sc, "iterations": max(iters, warmup + 1), "warmup": warmup,
+                    "seed": scene_seed & 0xFFFFFFFF, "key": k + 1, "grid_n": 32, "max_depth": 10,
+                    "techniques": TECH_BSDF | TECH_NEE | TECH_GUIDED})
+    return out
 
 
 def random_pixel_estimate(n_pixels: int, seed: int, lo: float = 0.05, hi: float = 2.0) -> np.ndarray:

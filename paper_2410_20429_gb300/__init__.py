@@ -6,6 +6,16 @@ The compute lives in ``libmars.so`` (hand-written CUDA, C ABI in
 ``include/mars.h``); this package only marshals arguments.  Loading fails
 loudly when the library has not been built."""
 from ._abi import (  # noqa: F401
+    MARS_ERR_BUSY,
+    MARS_ERR_CUDA,
+    MARS_ERR_INVALID_ARG,
+    MARS_ERR_NOT_FOUND,
+    MARS_ERR_OOM,
+    MARS_ERR_TIMEOUT,
+    MARS_JOB_DONE,
+    MARS_JOB_FAILED,
+    MARS_JOB_QUEUED,
+    MARS_JOB_RUNNING,
     MARS_MODE_FIXED,
     MARS_MODE_MARS,
     MARS_MODE_WARMUP,

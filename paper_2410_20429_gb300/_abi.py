@@ -80,15 +80,20 @@ class mars_cache_info(ct.Structure):
     ]
 
 
+class mars_launch_config(ct.Structure):
+    _fields_ = [("threads", ct.c_int32 * 4), ("blocks_per_sm", ct.c_int32 * 4)]
+
+
 class mars_job_desc(ct.Structure):
     _fields_ = [("scene", ct.POINTER(mars_scene_desc)), ("cache", mars_cache_desc), ("seed", ct.c_uint32),
-                ("iterations", ct.c_int32), ("warmup", ct.c_int32), ("reserved", ct.c_int32)]
+                ("iterations", ct.c_int32), ("warmup", ct.c_int32), ("key", ct.c_uint32)]
 
 
 class mars_job_status(ct.Structure):
     _fields_ = [("state", ct.c_int32), ("iterations_done", ct.c_int32), ("error", ct.c_int32),
                 ("reserved", ct.c_int32), ("submit_s", ct.c_double), ("start_s", ct.c_double),
-                ("end_s", ct.c_double), ("iter_ms_p50", ct.c_double), ("iter_ms_p99", ct.c_double)]
+                ("end_s", ct.c_double), ("iter_ms_p50", ct.c_double), ("iter_ms_p99", ct.c_double),
+                ("device_bytes", ct.c_uint64)]
 
 
 _VP = ct.c_void_p
@@ -103,6 +108,10 @@ SIGNATURES = {
     "mars_update_counts": ([_VP, _VP], ct.c_int),
     "mars_cache_get_state": ([_VP, ct.POINTER(mars_cache_state), _VP], ct.c_int),
     "mars_cache_set_state": ([_VP, ct.POINTER(mars_cache_state), _VP], ct.c_int),
+    "mars_cache_get_launch": ([_VP, ct.POINTER(mars_launch_config)], ct.c_int),
+    "mars_cache_set_launch": ([_VP, ct.POINTER(mars_launch_config)], ct.c_int),
+    "mars_cache_autotune": ([_VP, ct.POINTER(mars_iter_params), ct.c_int32, ct.POINTER(mars_launch_config), _VP],
+                            ct.c_int),
     "mars_server_create": ([ct.c_uint64, ct.c_int32, ct.POINTER(_VP)], ct.c_int),
     "mars_server_destroy": ([_VP], ct.c_int),
     "mars_submit": ([_VP, ct.POINTER(mars_job_desc), ct.POINTER(ct.c_uint64)], ct.c_int),

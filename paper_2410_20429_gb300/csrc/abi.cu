@@ -457,7 +457,39 @@ mars_status cache_create_impl(const mars_scene* s, const mars_cache_desc* d, cud
   c->dc.ctr = c->d_ctr;
   c->dc.tile_status = c->d_tile_status;
   c->device_bytes = cache_footprint(cells, pixels, d->max_depth, d->techniques, cap);
+  {
+    const int threads[WAVE_KERNELS] = {128, 128, 128, 128};
+    const int bps[WAVE_KERNELS] = {0, 0, 0, 0};
+    const mars_status ls = apply_launch(c, threads, bps);
+    if (ls != MARS_OK) {
+      cache_destroy_impl(c);
+      return ls;
+    }
+  }
   *out = c;
+  return MARS_OK;
+}
+
+// Grid of each wave kernel = SMs x resident blocks per SM (the occupancy
+// maximum unless a positive count is given): a persistent grid that strides
+// over the wave.
+mars_status apply_launch(mars_cache* c, const int threads[WAVE_KERNELS], const int blocks_per_sm[WAVE_KERNELS]) {
+  for (int k = 0; k < WAVE_KERNELS; ++k) {
+    if (!wave_threads_ok(threads[k]))
+      return set_error(MARS_ERR_INVALID_ARG, "wave kernel %d: %d threads per block (need a multiple of 32 in 32..256)",
+                       k, threads[k]);
+    if (blocks_per_sm[k] < 0 || blocks_per_sm[k] > 64)
+      return set_error(MARS_ERR_INVALID_ARG, "wave kernel %d: blocks per SM %d outside 0..64", k, blocks_per_sm[k]);
+  }
+  int occ[WAVE_KERNELS];
+  const cudaError_t e = wave_occupancy(threads, occ);
+  if (e != cudaSuccess) return set_error(MARS_ERR_CUDA, "occupancy query: %s", cudaGetErrorString(e));
+  for (int k = 0; k < WAVE_KERNELS; ++k) {
+    const int b = blocks_per_sm[k] > 0 ? blocks_per_sm[k] : std::max(1, occ[k]);
+    c->launch.threads[k] = threads[k];
+    c->launch.grid[k] = c->scene->num_sms * b;
+    c->blocks_per_sm[k] = b;
+  }
   return MARS_OK;
 }
 
@@ -498,7 +530,6 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
   DeviceGuard g(c->device);
   if (!g.ok) return set_error(MARS_ERR_CUDA, "cannot select device %d", c->device);
   const mars_scene* s = c->scene;
-  const int num_sms = s->num_sms;
 
   IterArgs it{};
   it.seed = p->seed;
@@ -544,7 +575,7 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
       it.tile_end = (int)tiles[t].second;
       it.tile_slot = (int)t;
       cudaEvent_t* ev = p->profile ? c->events.data() + t * per_tile : nullptr;
-      if ((e = launch_tile(s->ds, c->dc, c->arena, it, num_sms, st, ev)) != cudaSuccess)
+      if ((e = launch_tile(s->ds, c->dc, c->arena, it, c->launch, st, ev)) != cudaSuccess)
         return poison(c, e, "render launch");
       launches += (uint32_t)tile_launches(D, c->techniques);
       wave_launches += (uint32_t)D;
@@ -817,6 +848,90 @@ mars_status mars_cache_get_state(mars_cache* cache, mars_cache_state* state, voi
 
 mars_status mars_cache_set_state(mars_cache* cache, const mars_cache_state* state, void* stream) {
   return set_state_impl(cache, state, (cudaStream_t)stream);
+}
+
+mars_status mars_cache_get_launch(const mars_cache* c, mars_launch_config* out) {
+  if (!c || !out) return set_error(MARS_ERR_INVALID_ARG, "null cache or output");
+  for (int k = 0; k < WAVE_KERNELS; ++k) {
+    out->threads[k] = c->launch.threads[k];
+    out->blocks_per_sm[k] = c->blocks_per_sm[k];
+  }
+  return MARS_OK;
+}
+
+mars_status mars_cache_set_launch(mars_cache* c, const mars_launch_config* cfg) {
+  if (!c || !cfg) return set_error(MARS_ERR_INVALID_ARG, "null cache or config");
+  DeviceGuard g(c->device);
+  return apply_launch(c, cfg->threads, cfg->blocks_per_sm);
+}
+
+// Coordinate search over the launch shape of each wave kernel in turn (threads
+// per block x blocks per SM), timing the kernel's own CUDA events over
+// `repeats` renders of the given iteration without statistics, image
+// statistics or guide deposits, so the cache's state is left as it was.
+mars_status mars_cache_autotune(mars_cache* c, const mars_iter_params* params, int32_t repeats,
+                                mars_launch_config* chosen, void* stream) {
+  if (!c || !params) return set_error(MARS_ERR_INVALID_ARG, "null cache or params");
+  if (repeats < 1 || repeats > 100) return set_error(MARS_ERR_INVALID_ARG, "repeats %d outside 1..100", repeats);
+  if (c->poisoned) return set_error(MARS_ERR_CUDA, "cache is poisoned by an earlier CUDA error");
+  DeviceGuard g(c->device);
+  mars_iter_params p = *params;
+  p.collect = 0;
+  p.update_estimate = 0;
+  p.image_on_host = 0;
+  p.profile = 1;
+  int threads[WAVE_KERNELS], bps[WAVE_KERNELS];
+  for (int k = 0; k < WAVE_KERNELS; ++k) {
+    threads[k] = c->launch.threads[k];
+    bps[k] = c->blocks_per_sm[k];
+  }
+  auto time_of = [&](int k, double* ms) -> mars_status {
+    mars_status rc = apply_launch(c, threads, bps);
+    if (rc != MARS_OK) return rc;
+    double tot = 0.0;
+    for (int r = 0; r <= repeats; ++r) {  // the first render warms up
+      mars_iter_stats st{};
+      rc = render_iteration_impl(c, &p, nullptr, &st, (cudaStream_t)stream);
+      if (rc != MARS_OK) return rc;
+      const double v[WAVE_KERNELS] = {st.trace_ms, st.shade_ms, st.shadow_ms, st.reverse_ms};
+      if (r > 0) tot += v[k];
+    }
+    *ms = tot / repeats;
+    return MARS_OK;
+  };
+  const int cand_threads[3] = {64, 128, 256};
+  for (int k = 0; k < WAVE_KERNELS; ++k) {
+    if (k == WK_SHADOW && !(c->techniques & MARS_TECH_NEE)) continue;
+    int best_t = threads[k], best_b = bps[k];
+    double best = 1e300;
+    for (int ti = 0; ti < 3; ++ti) {
+      int occ[WAVE_KERNELS];
+      int tt[WAVE_KERNELS] = {threads[0], threads[1], threads[2], threads[3]};
+      tt[k] = cand_threads[ti];
+      if (wave_occupancy(tt, occ) != cudaSuccess) return set_error(MARS_ERR_CUDA, "occupancy query failed");
+      const int o = std::max(1, occ[k]);
+      const int cand_b[3] = {std::max(1, o / 2), o, 2 * o};
+      for (int bi = 0; bi < 3; ++bi) {
+        if (bi == 0 && cand_b[0] == o) continue;
+        threads[k] = cand_threads[ti];
+        bps[k] = std::min(64, cand_b[bi]);
+        double ms = 0.0;
+        const mars_status rc = time_of(k, &ms);
+        if (rc != MARS_OK) return rc;
+        if (ms < best) {
+          best = ms;
+          best_t = threads[k];
+          best_b = bps[k];
+        }
+      }
+    }
+    threads[k] = best_t;
+    bps[k] = best_b;
+  }
+  const mars_status rc = apply_launch(c, threads, bps);
+  if (rc != MARS_OK) return rc;
+  if (chosen) return mars_cache_get_launch(c, chosen);
+  return MARS_OK;
 }
 
 const char* mars_last_error_string(void) { return g_last_error.c_str(); }

@@ -84,6 +84,8 @@ struct mars_cache {
   double last_VI = 0.0, last_CI = 0.0;
   uint64_t device_bytes = 0;
   std::vector<cudaEvent_t> events;  // profiling events, grown on demand
+  mars::WaveLaunch launch{};        // launch shape of the per-wave kernels
+  int blocks_per_sm[mars::WAVE_KERNELS] = {0, 0, 0, 0};  // 0: occupancy maximum
 };
 
 namespace mars {
@@ -96,4 +98,5 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
 mars_status update_counts_impl(mars_cache* c, cudaStream_t st);
 uint64_t cache_footprint(int64_t cells, int64_t pixels, int max_depth, int techniques, uint64_t cap);
 uint64_t default_capacity(int64_t pixels, int max_depth);
+mars_status apply_launch(mars_cache* c, const int threads[WAVE_KERNELS], const int blocks_per_sm[WAVE_KERNELS]);
 }  // namespace mars

@@ -123,9 +123,21 @@ struct IterArgs {
   int tile_begin, tile_end, tile_slot;
 };
 
+// Launch shape of the four per-wave kernels: threads per block (a multiple of
+// 32, at most 256) and grid size in blocks.  Every kernel strides over its
+// wave in chunks of 32 slots, so results do not depend on the shape.
+enum { WK_TRACE = 0, WK_SHADE = 1, WK_SHADOW = 2, WK_REVERSE = 3, WAVE_KERNELS = 4 };
+struct WaveLaunch {
+  int threads[WAVE_KERNELS];
+  int grid[WAVE_KERNELS];
+};
+
 // launch wrappers (render.cu)
 cudaError_t launch_tile(const DevScene& s, const DevCache& c, const Arena& a, const IterArgs& it,
-                        int num_sms, cudaStream_t st, cudaEvent_t* ev);
+                        const WaveLaunch& L, cudaStream_t st, cudaEvent_t* ev);
+// resident blocks per SM of each wave kernel at the given block sizes
+cudaError_t wave_occupancy(const int threads[WAVE_KERNELS], int blocks_per_sm[WAVE_KERNELS]);
+bool wave_threads_ok(int threads);
 int tile_launches(int max_depth, int techniques);  // kernels launch_tile issues
 // image statistics (stats.cu)
 cudaError_t launch_image_stats(const DevCache& c, int width, int height, int n_prev, float outlier,

@@ -31,10 +31,9 @@ namespace mars {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int TRACE_THREADS = 128;
-constexpr int SHADE_THREADS = 128;
-constexpr int SHADOW_THREADS = 128;
-constexpr int REVERSE_THREADS = 128;
+// every wave kernel accepts blocks of up to MAX_WAVE_THREADS threads; the launch
+// shape (threads per block, grid) is a per-cache setting (WaveLaunch)
+constexpr int MAX_WAVE_THREADS = 256;
 
 __device__ __forceinline__ float4 f4(f3 a, float w) { return make_float4(a.x, a.y, a.z, w); }
 __device__ __forceinline__ f3 fmin3(f3 a, f3 b) { return mk3(fminf(a.x, b.x), fminf(a.y, b.y), fminf(a.z, b.z)); }
@@ -70,9 +69,15 @@ __device__ __forceinline__ Wave wave_of(const DevCounters* ctr, const Arena& a, 
   return {base, cnt < a.cap - base ? cnt : a.cap - base};
 }
 
-// inclusive warp scan of a per-lane count, one atomicAdd per warp on *counter;
-// returns the lane's first slot relative to the counter's old value
-__device__ __forceinline__ unsigned long long warp_alloc(int n, int lane, unsigned long long* counter) {
+// Warp-aggregated allocation: inclusive warp scan of a per-lane count and one
+// atomicAdd per warp on *counter.  The warp's slots are contiguous, in lane
+// order: lane l owns [base + incl - n, base + incl).
+struct WarpAlloc {
+  unsigned long long base;  // first slot of the warp (relative to the counter's origin)
+  int incl;                 // inclusive prefix of the counts up to this lane
+  int total;                // slots of the whole warp
+};
+__device__ __forceinline__ WarpAlloc warp_alloc(int n, int lane, unsigned long long* counter) {
   int incl = n;
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1) {
@@ -85,7 +90,18 @@ __device__ __forceinline__ unsigned long long warp_alloc(int n, int lane, unsign
     if (lane == 31) wbase = atomicAdd(counter, (unsigned long long)total);
     wbase = __shfl_sync(FULL, wbase, 31);
   }
-  return wbase + (unsigned long long)(incl - n);
+  return {wbase, incl, total};
+}
+
+// lane owning item k of a warp block: the smallest l with incl[l] > k
+__device__ __forceinline__ int owner_lane(const int* incl, int k) {
+  int lo = 0, hi = 31;
+#pragma unroll
+  for (int it = 0; it < 5; ++it) {
+    const int mid = (lo + hi) >> 1;
+    if (incl[mid] > k) hi = mid; else lo = mid + 1;
+  }
+  return lo;
 }
 
 __global__ void k_tile_init(DevCounters* ctr, unsigned long long n0) {
@@ -124,7 +140,7 @@ __global__ void k_tile_finish(DevCounters* ctr, unsigned int* tile_status, int s
 }
 
 // ------------------------------------------------------------------ trace
-__global__ void __launch_bounds__(TRACE_THREADS) k_trace(const DevScene s, const DevCache c, const Arena a,
+__global__ void __launch_bounds__(MAX_WAVE_THREADS) k_trace(const DevScene s, const DevCache c, const Arena a,
                                                          const IterArgs it, const int d) {
   const DevCounters* ctr = c.ctr;
   // after an overflow some slots of this wave were never written: stop, the
@@ -153,7 +169,19 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_trace(const DevScene s, const
 }
 
 // ------------------------------------------------------------------ shade
-__global__ void __launch_bounds__(SHADE_THREADS) k_shade(const DevScene s, const DevCache c, const Arena a,
+// Per-warp staging area of k_shade: the context of the 32 vertices of a chunk,
+// structure of arrays [field][lane], read by the lanes that draw their samples.
+enum {
+  C_XO = 0, C_NS = 3, C_WO = 6, C_MTYPE = 9, C_ALPHA = 10, C_COL = 11, C_CELL = 14, C_PX = 15, C_LIN = 16,
+  C_T = 18, C_B0 = 21, C_B1 = 22, C_B2 = 23, C_G0 = 24, C_FIELDS = 25
+};
+struct ShadeWarpCtx {
+  float f[C_FIELDS][32];
+  int incl_ext[32];
+  int incl_sh[32];
+};
+
+__global__ void __launch_bounds__(MAX_WAVE_THREADS) k_shade(const DevScene s, const DevCache c, const Arena a,
                                                          const IterArgs it, const int d) {
   DevCounters* ctr = c.ctr;
   if (ctr->overflow) return;
@@ -176,6 +204,8 @@ __global__ void __launch_bounds__(SHADE_THREADS) k_shade(const DevScene s, const
              on_g = c.techniques & MARS_TECH_GUIDED;
   const Rng rng{it.seed, it.job, it.iteration};
   const float inf = __int_as_float(0x7f800000);
+  extern __shared__ ShadeWarpCtx shade_ctx[];
+  ShadeWarpCtx* ctx = shade_ctx + (threadIdx.x >> 5);
 
   for (unsigned long long c0 = gw * 32; c0 < w.n; c0 += nw * 32) {
     const unsigned long long li = c0 + lane;
@@ -296,96 +326,12 @@ __global__ void __launch_bounds__(SHADE_THREADS) k_shade(const DevScene s, const
 
     // ---- slots for the children (wave d+1) and the NEE shadow rays
     const int n_ext = gam[0] + gam[2], n_sh = gam[1];
-    const unsigned long long first = base_next + warp_alloc(n_ext, lane, &ctr->count[d + 1]);
-    const unsigned long long sfirst = sbase + warp_alloc(n_sh, lane, &ctr->scount[d]);
+    const WarpAlloc ae = warp_alloc(n_ext, lane, &ctr->count[d + 1]);
+    const WarpAlloc as = warp_alloc(n_sh, lane, &ctr->scount[d]);
+    const unsigned long long first = base_next + ae.base + (unsigned long long)(ae.incl - n_ext);
+    const unsigned long long sfirst = sbase + as.base + (unsigned long long)(as.incl - n_sh);
     const bool fits = first + (unsigned long long)n_ext <= a.cap && sfirst + (unsigned long long)n_sh <= a.scap;
     if ((n_ext > 0 || n_sh > 0) && !fits) atomicOr(&ctr->overflow, 1u);
-
-    if ((flags & F_EST) && fits) {
-      const Frame fr = make_frame(ns);
-      const f3 wol = fr.to_local(wo);
-      const f3 xo = p + ns * s.eps;
-      const float bwB = on_b ? (it.aware ? beta[0] : 1.0f) : 0.0f;
-      const float bwNv = on_n ? (it.aware ? beta[1] : 1.0f) : 0.0f;
-      const float bwG = on_g ? (it.aware ? beta[2] : 1.0f) : 0.0f;
-      const float* cdf = on_g ? c.guide_cdf + (size_t)cell * GUIDE_BINS : nullptr;
-      // NEE samples (primary estimator of NEE), value assuming the light is visible
-      for (int sidx = 0; sidx < n_sh; ++sidx) {
-        const float4 u = rng.u4(px, 32u + (uint32_t)sidx, lin);
-        int l = s.n_lights - 1;
-        for (int k = 0; k < s.n_lights; ++k)
-          if (u.x < __ldg(&s.lights[5 * k].w)) { l = k; break; }
-        const float4 l0 = __ldg(s.lights + 5 * l), l1 = __ldg(s.lights + 5 * l + 1),
-                     l2 = __ldg(s.lights + 5 * l + 2), l4 = __ldg(s.lights + 5 * l + 4);
-        const f3 y = xyz(l0) + (xyz(l1) * u.y + xyz(l2) * u.z);
-        const f3 dv = y - xo;
-        const float dist = sqrtf(dot(dv, dv));
-        const f3 wi = dv * (1.0f / dist);
-        const float pn = nee_pdf(s, l, xo, y, wi);
-        const float ci = dot(ns, wi);
-        f3 v = mk3(0.f, 0.f, 0.f);
-        if (pn > 0.0f && ci > 0.0f) {
-          float pb;
-          const f3 fc = bsdf_eval(mat, wol, fr.to_local(wi), pb);
-          const float pg = on_g ? guide_pdf(cdf, wi) : 0.0f;
-          if (nonzero(fc)) {
-            const float den = bwB * pb + bwG * pg + bwNv * pn;
-            const float wgt = bwNv * pn / den;
-            v = mk3(fc.x * l4.x / pn * wgt, fc.y * l4.y / pn * wgt, fc.z * l4.z / pn * wgt);
-          }
-        }
-        const unsigned long long j = sfirst + sidx;
-        // tmax < 0 marks a sample that needs no shadow ray (its value is 0)
-        a.SH[0][j] = f4(xo, nonzero(v) ? dist - s.eps : -1.0f);
-        a.SH[1][j] = f4(wi, 0.0f);
-        a.SH[2][j] = f4(v, 0.0f);
-      }
-      // BSDF and guided children (primary estimators that continue the path)
-      for (int k = 0; k < n_ext; ++k) {
-        const int t = k < gam[0] ? 0 : 2;
-        const int sidx = t == 0 ? k : k - gam[0];
-        const float4 u = rng.u4(px, (uint32_t)(t * 32 + sidx), lin);
-        f3 wi = mk3(0.f, 0.f, 1.f);
-        bool ok;
-        float pt = 0.0f;
-        if (t == 0) {
-          f3 wl;
-          ok = bsdf_sample(mat, wol, u.x, u.y, wl);
-          if (ok) wi = fr.to_world(wl);
-        } else {
-          const int b = guide_pick(cdf, u.x);
-          wi = guide_dir(b, u.y, u.z);
-          pt = guide_bin_prob(cdf, b) * (GUIDE_BINS / (4.0f * PI_F));
-          ok = dot(wi, ns) > 0.0f;
-        }
-        float cA = 0.0f, cS = 0.0f, cinvSb = 0.0f;
-        f3 cf = mk3(0.f, 0.f, 0.f), cT = mk3(0.f, 0.f, 0.f);
-        if (ok) {
-          float pb;
-          const f3 fc = bsdf_eval(mat, wol, fr.to_local(wi), pb);
-          const float pg = on_g ? guide_pdf(cdf, wi) : 0.0f;
-          if (t == 0) pt = pb;
-          if (pt > 0.0f && nonzero(fc)) {
-            cf = mk3(fc.x / pt, fc.y / pt, fc.z / pt);
-            cA = (t == 0 ? bwB : bwG) * pt;
-            cS = bwB * pb + bwG * pg;
-            const float w_ind = cA / cS;
-            cT = mk3(T.x * cf.x * w_ind / beta[t], T.y * cf.y * w_ind / beta[t], T.z * cf.z * w_ind / beta[t]);
-            const float sb = beta[0] * pb + (on_g ? beta[2] * pg : 0.0f);
-            cinvSb = sb > 0.0f ? 1.0f / sb : 0.0f;
-          }
-        }
-        const uint64_t digit = (uint64_t)(t == 0 ? sidx + 1 : 32 + sidx + 1);
-        const uint64_t clin = (lin << c.bits) | digit;
-        const unsigned long long j = first + k;
-        a.R[0][j] = f4(xo, __uint_as_float(px));
-        a.R[1][j] = f4(wi, cA);
-        a.R[2][j] = f4(cT, cS);
-        a.R[3][j] = f4(cf, bwNv);
-        a.R[4][j] = make_float4(__uint_as_float((uint32_t)clin), __uint_as_float((uint32_t)(clin >> 32)),
-                                __uint_as_float((uint32_t)cell), cinvSb);
-      }
-    }
 
     // ---- vertex record of this slot
     if (active) {
@@ -399,11 +345,166 @@ __global__ void __launch_bounds__(SHADE_THREADS) k_shade(const DevScene s, const
       if (on_g && it.collect && !camera && (flags & F_TRACED))
         a.V[4][i] = make_float4(Le_lum, invSb, __uint_as_float(parent_cell), __int_as_float(guide_bin(dir)));
     }
+    if (ae.total == 0 && as.total == 0) continue;  // warp-uniform
+
+    // ---- stage the vertex context of every lane for the cooperative loops
+    {
+      const Frame fr = make_frame(ns);
+      const f3 wol = fr.to_local(wo);
+      const f3 xo = p + ns * s.eps;
+      float* cx = ctx->f[0];
+      cx[C_XO * 32 + lane] = xo.x; cx[(C_XO + 1) * 32 + lane] = xo.y; cx[(C_XO + 2) * 32 + lane] = xo.z;
+      cx[C_NS * 32 + lane] = ns.x; cx[(C_NS + 1) * 32 + lane] = ns.y; cx[(C_NS + 2) * 32 + lane] = ns.z;
+      cx[C_WO * 32 + lane] = wol.x; cx[(C_WO + 1) * 32 + lane] = wol.y; cx[(C_WO + 2) * 32 + lane] = wol.z;
+      cx[C_MTYPE * 32 + lane] = __int_as_float(mat.type);
+      cx[C_ALPHA * 32 + lane] = mat.alpha;
+      cx[C_COL * 32 + lane] = mat.col.x; cx[(C_COL + 1) * 32 + lane] = mat.col.y; cx[(C_COL + 2) * 32 + lane] = mat.col.z;
+      cx[C_CELL * 32 + lane] = __int_as_float(cell);
+      cx[C_PX * 32 + lane] = __uint_as_float(px);
+      cx[C_LIN * 32 + lane] = __uint_as_float((uint32_t)lin);
+      cx[(C_LIN + 1) * 32 + lane] = __uint_as_float((uint32_t)(lin >> 32));
+      cx[C_T * 32 + lane] = T.x; cx[(C_T + 1) * 32 + lane] = T.y; cx[(C_T + 2) * 32 + lane] = T.z;
+      cx[C_B0 * 32 + lane] = beta[0];
+      cx[C_B1 * 32 + lane] = beta[1];
+      cx[C_B2 * 32 + lane] = beta[2];
+      cx[C_G0 * 32 + lane] = __int_as_float(gam[0]);
+      ctx->incl_ext[lane] = ae.incl;
+      ctx->incl_sh[lane] = as.incl;
+    }
+    __syncwarp();
+    const float* cx = ctx->f[0];
+
+    // NEE samples (primary estimators of NEE), one per lane and pass; the value
+    // assumes the light is visible (the shadow kernel zeroes it otherwise)
+    for (int k0 = 0; k0 < as.total; k0 += 32) {
+      const int k = k0 + lane;
+      const unsigned long long j = sbase + as.base + (unsigned long long)k;
+      if (k < as.total && j < a.scap) {
+        const int L = owner_lane(ctx->incl_sh, k);
+        const int sidx = k - (L > 0 ? ctx->incl_sh[L - 1] : 0);
+        const f3 xo = mk3(cx[C_XO * 32 + L], cx[(C_XO + 1) * 32 + L], cx[(C_XO + 2) * 32 + L]);
+        const f3 vns = mk3(cx[C_NS * 32 + L], cx[(C_NS + 1) * 32 + L], cx[(C_NS + 2) * 32 + L]);
+        const f3 wol = mk3(cx[C_WO * 32 + L], cx[(C_WO + 1) * 32 + L], cx[(C_WO + 2) * 32 + L]);
+        Mat m;
+        m.type = __float_as_int(cx[C_MTYPE * 32 + L]);
+        m.alpha = cx[C_ALPHA * 32 + L];
+        m.col = mk3(cx[C_COL * 32 + L], cx[(C_COL + 1) * 32 + L], cx[(C_COL + 2) * 32 + L]);
+        const uint32_t vpx = __float_as_uint(cx[C_PX * 32 + L]);
+        const uint64_t vlin = (uint64_t)__float_as_uint(cx[C_LIN * 32 + L]) |
+                              ((uint64_t)__float_as_uint(cx[(C_LIN + 1) * 32 + L]) << 32);
+        const float bB = cx[C_B0 * 32 + L], bN = cx[C_B1 * 32 + L], bG = cx[C_B2 * 32 + L];
+        const float bwB = on_b ? (it.aware ? bB : 1.0f) : 0.0f;
+        const float bwNv = on_n ? (it.aware ? bN : 1.0f) : 0.0f;
+        const float bwG = on_g ? (it.aware ? bG : 1.0f) : 0.0f;
+        const float4 u = rng.u4(vpx, 32u + (uint32_t)sidx, vlin);
+        int l = s.n_lights - 1;
+        for (int q = 0; q < s.n_lights; ++q)
+          if (u.x < __ldg(&s.lights[5 * q].w)) { l = q; break; }
+        const float4 l0 = __ldg(s.lights + 5 * l), l1 = __ldg(s.lights + 5 * l + 1),
+                     l2 = __ldg(s.lights + 5 * l + 2), l4 = __ldg(s.lights + 5 * l + 4);
+        const f3 y = xyz(l0) + (xyz(l1) * u.y + xyz(l2) * u.z);
+        const f3 dv = y - xo;
+        const float dist = sqrtf(dot(dv, dv));
+        const f3 wi = dv * (1.0f / dist);
+        const float pn = nee_pdf(s, l, xo, y, wi);
+        const float ci = dot(vns, wi);
+        f3 v = mk3(0.f, 0.f, 0.f);
+        if (pn > 0.0f && ci > 0.0f) {
+          const Frame fr = make_frame(vns);
+          float pb;
+          const f3 fc = bsdf_eval(m, wol, fr.to_local(wi), pb);
+          const float pg = on_g ? guide_pdf(c.guide_cdf + (size_t)__float_as_int(cx[C_CELL * 32 + L]) * GUIDE_BINS, wi)
+                                : 0.0f;
+          if (nonzero(fc)) {
+            const float den = bwB * pb + bwG * pg + bwNv * pn;
+            const float wgt = bwNv * pn / den;
+            v = mk3(fc.x * l4.x / pn * wgt, fc.y * l4.y / pn * wgt, fc.z * l4.z / pn * wgt);
+          }
+        }
+        // tmax < 0 marks a sample that needs no shadow ray (its value is 0)
+        a.SH[0][j] = f4(xo, nonzero(v) ? dist - s.eps : -1.0f);
+        a.SH[1][j] = f4(wi, 0.0f);
+        a.SH[2][j] = f4(v, 0.0f);
+      }
+    }
+
+    // BSDF and guided children (primary estimators that continue the path);
+    // a vertex's BSDF children come first, then its guided children
+    for (int k0 = 0; k0 < ae.total; k0 += 32) {
+      const int k = k0 + lane;
+      const unsigned long long j = base_next + ae.base + (unsigned long long)k;
+      if (k < ae.total && j < a.cap) {
+        const int L = owner_lane(ctx->incl_ext, k);
+        const int kk = k - (L > 0 ? ctx->incl_ext[L - 1] : 0);
+        const int g0 = __float_as_int(cx[C_G0 * 32 + L]);
+        const int t = kk < g0 ? 0 : 2;
+        const int sidx = t == 0 ? kk : kk - g0;
+        const f3 xo = mk3(cx[C_XO * 32 + L], cx[(C_XO + 1) * 32 + L], cx[(C_XO + 2) * 32 + L]);
+        const f3 vns = mk3(cx[C_NS * 32 + L], cx[(C_NS + 1) * 32 + L], cx[(C_NS + 2) * 32 + L]);
+        const f3 wol = mk3(cx[C_WO * 32 + L], cx[(C_WO + 1) * 32 + L], cx[(C_WO + 2) * 32 + L]);
+        Mat m;
+        m.type = __float_as_int(cx[C_MTYPE * 32 + L]);
+        m.alpha = cx[C_ALPHA * 32 + L];
+        m.col = mk3(cx[C_COL * 32 + L], cx[(C_COL + 1) * 32 + L], cx[(C_COL + 2) * 32 + L]);
+        const int vcell = __float_as_int(cx[C_CELL * 32 + L]);
+        const uint32_t vpx = __float_as_uint(cx[C_PX * 32 + L]);
+        const uint64_t vlin = (uint64_t)__float_as_uint(cx[C_LIN * 32 + L]) |
+                              ((uint64_t)__float_as_uint(cx[(C_LIN + 1) * 32 + L]) << 32);
+        const f3 vT = mk3(cx[C_T * 32 + L], cx[(C_T + 1) * 32 + L], cx[(C_T + 2) * 32 + L]);
+        const float bB = cx[C_B0 * 32 + L], bN = cx[C_B1 * 32 + L], bG = cx[C_B2 * 32 + L];
+        const float bwB = on_b ? (it.aware ? bB : 1.0f) : 0.0f;
+        const float bwNv = on_n ? (it.aware ? bN : 1.0f) : 0.0f;
+        const float bwG = on_g ? (it.aware ? bG : 1.0f) : 0.0f;
+        const float bt = t == 0 ? bB : bG;
+        const float* cdf = on_g ? c.guide_cdf + (size_t)vcell * GUIDE_BINS : nullptr;
+        const Frame fr = make_frame(vns);
+        const float4 u = rng.u4(vpx, (uint32_t)(t * 32 + sidx), vlin);
+        f3 wi = mk3(0.f, 0.f, 1.f);
+        bool ok;
+        float pt = 0.0f;
+        if (t == 0) {
+          f3 wl;
+          ok = bsdf_sample(m, wol, u.x, u.y, wl);
+          if (ok) wi = fr.to_world(wl);
+        } else {
+          const int b = guide_pick(cdf, u.x);
+          wi = guide_dir(b, u.y, u.z);
+          pt = guide_bin_prob(cdf, b) * (GUIDE_BINS / (4.0f * PI_F));
+          ok = dot(wi, vns) > 0.0f;
+        }
+        float cA = 0.0f, cS = 0.0f, cinvSb = 0.0f;
+        f3 cf = mk3(0.f, 0.f, 0.f), cT = mk3(0.f, 0.f, 0.f);
+        if (ok) {
+          float pb;
+          const f3 fc = bsdf_eval(m, wol, fr.to_local(wi), pb);
+          const float pg = on_g ? guide_pdf(cdf, wi) : 0.0f;
+          if (t == 0) pt = pb;
+          if (pt > 0.0f && nonzero(fc)) {
+            cf = mk3(fc.x / pt, fc.y / pt, fc.z / pt);
+            cA = (t == 0 ? bwB : bwG) * pt;
+            cS = bwB * pb + bwG * pg;
+            const float w_ind = cA / cS;
+            cT = mk3(vT.x * cf.x * w_ind / bt, vT.y * cf.y * w_ind / bt, vT.z * cf.z * w_ind / bt);
+            const float sb = bB * pb + (on_g ? bG * pg : 0.0f);
+            cinvSb = sb > 0.0f ? 1.0f / sb : 0.0f;
+          }
+        }
+        const uint64_t digit = (uint64_t)(t == 0 ? sidx + 1 : 32 + sidx + 1);
+        const uint64_t clin = (vlin << c.bits) | digit;
+        a.R[0][j] = f4(xo, __uint_as_float(vpx));
+        a.R[1][j] = f4(wi, cA);
+        a.R[2][j] = f4(cT, cS);
+        a.R[3][j] = f4(cf, bwNv);
+        a.R[4][j] = make_float4(__uint_as_float((uint32_t)clin), __uint_as_float((uint32_t)(clin >> 32)),
+                                __uint_as_float((uint32_t)vcell), cinvSb);
+      }
+    }
+    __syncwarp();  // the context is overwritten by the next chunk
   }
 }
 
 // ----------------------------------------------------------------- shadow
-__global__ void __launch_bounds__(SHADOW_THREADS) k_shadow(const DevScene s, const DevCache c, const Arena a,
+__global__ void __launch_bounds__(MAX_WAVE_THREADS) k_shadow(const DevScene s, const DevCache c, const Arena a,
                                                            const int d) {
   const DevCounters* ctr = c.ctr;
   if (ctr->overflow) return;
@@ -430,7 +531,7 @@ __device__ __forceinline__ float seg_scan(float v, int lane, int start) {
   return v;
 }
 
-__global__ void __launch_bounds__(REVERSE_THREADS) k_reverse(const DevScene s, const DevCache c, const Arena a,
+__global__ void __launch_bounds__(MAX_WAVE_THREADS) k_reverse(const DevScene s, const DevCache c, const Arena a,
                                                              const IterArgs it, const int d) {
   DevCounters* ctr = c.ctr;
   if (ctr->overflow) return;  // the tile is re-rendered; commit nothing
@@ -468,12 +569,19 @@ __global__ void __launch_bounds__(REVERSE_THREADS) k_reverse(const DevScene s, c
         if (gN > 0) {
           const unsigned long long sf = __float_as_uint(v3.w);
           f3 sum = mk3(0.f, 0.f, 0.f);
-          for (int k = 0; k < gN; ++k) {
-            const f3 v = xyz(a.SH[2][sf + k]);
-            sum = sum + v;
-            const f3 vc = fmin3(v, climit);
-            st[1][1] += vc.x; st[1][2] += vc.y; st[1][3] += vc.z;
-            st[1][4] += vc.x * vc.x; st[1][5] += vc.y * vc.y; st[1][6] += vc.z * vc.z;
+          for (int k = 0; k < gN; k += 4) {
+            float4 vv[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) vv[q] = k + q < gN ? a.SH[2][sf + k + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              if (k + q >= gN) break;
+              const f3 v = xyz(vv[q]);
+              sum = sum + v;
+              const f3 vc = fmin3(v, climit);
+              st[1][1] += vc.x; st[1][2] += vc.y; st[1][3] += vc.z;
+              st[1][4] += vc.x * vc.x; st[1][5] += vc.y * vc.y; st[1][6] += vc.z * vc.z;
+            }
           }
           Lr = mk3(sum.x / bt[1], sum.y / bt[1], sum.z / bt[1]);
           csub += (uint32_t)gN;
@@ -482,20 +590,27 @@ __global__ void __launch_bounds__(REVERSE_THREADS) k_reverse(const DevScene s, c
         }
         const unsigned long long first = __float_as_uint(v1.w);
         const int ne = gB + gG;
-        for (int k = 0; k < ne; ++k) {
-          const float4 sv = a.S[first + k];
-          const int t = k < gB ? 0 : 2;
-          const float b = bt[t];
-          Lr = Lr + mk3(sv.x / b, sv.y / b, sv.z / b);
-          const uint32_t cc = __float_as_uint(sv.w);
-          csub += cc;
-          const f3 vc = fmin3(xyz(sv), climit);
-          if (t == 0) {
-            st[0][0] += 1.0f; st[0][1] += vc.x; st[0][2] += vc.y; st[0][3] += vc.z;
-            st[0][4] += vc.x * vc.x; st[0][5] += vc.y * vc.y; st[0][6] += vc.z * vc.z; st[0][7] += (float)cc;
-          } else {
-            st[2][0] += 1.0f; st[2][1] += vc.x; st[2][2] += vc.y; st[2][3] += vc.z;
-            st[2][4] += vc.x * vc.x; st[2][5] += vc.y * vc.y; st[2][6] += vc.z * vc.z; st[2][7] += (float)cc;
+        for (int k = 0; k < ne; k += 4) {
+          float4 sv4[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) sv4[q] = k + q < ne ? a.S[first + k + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (k + q >= ne) break;
+            const float4 sv = sv4[q];
+            const int t = k + q < gB ? 0 : 2;
+            const float b = bt[t];
+            Lr = Lr + mk3(sv.x / b, sv.y / b, sv.z / b);
+            const uint32_t cc = __float_as_uint(sv.w);
+            csub += cc;
+            const f3 vc = fmin3(xyz(sv), climit);
+            if (t == 0) {
+              st[0][0] += 1.0f; st[0][1] += vc.x; st[0][2] += vc.y; st[0][3] += vc.z;
+              st[0][4] += vc.x * vc.x; st[0][5] += vc.y * vc.y; st[0][6] += vc.z * vc.z; st[0][7] += (float)cc;
+            } else {
+              st[2][0] += 1.0f; st[2][1] += vc.x; st[2][2] += vc.y; st[2][3] += vc.z;
+              st[2][4] += vc.x * vc.x; st[2][5] += vc.y * vc.y; st[2][6] += vc.z * vc.z; st[2][7] += (float)cc;
+            }
           }
         }
         const f3 G = xyz(v1);
@@ -550,16 +665,16 @@ __global__ void __launch_bounds__(REVERSE_THREADS) k_reverse(const DevScene s, c
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
           if (!((c.techniques >> t) & 1)) continue;
+          // skip a technique no lane drew, and the scan when every run is one lane
+          if (!__any_sync(FULL, st[t][0] > 0.0f)) continue;
+          if (heads != FULL) {
 #pragma unroll
-          for (int k = 0; k < NSTAT; ++k) st[t][k] = seg_scan(st[t][k], lane, start);
-        }
-        if (tail && key != 0xffffffffu) {
-          double* dst = c.stats + (size_t)key * NT * NSTAT;
+            for (int k = 0; k < NSTAT; ++k) st[t][k] = seg_scan(st[t][k], lane, start);
+          }
+          if (tail && key != 0xffffffffu && st[t][0] > 0.0f) {
+            double* dst = c.stats + ((size_t)key * NT + t) * NSTAT;
 #pragma unroll
-          for (int t = 0; t < NT; ++t) {
-            if (!((c.techniques >> t) & 1) || st[t][0] <= 0.0f) continue;
-#pragma unroll
-            for (int k = 0; k < NSTAT; ++k) atomicAdd(dst + t * NSTAT + k, (double)st[t][k]);
+            for (int k = 0; k < NSTAT; ++k) atomicAdd(dst + k, (double)st[t][k]);
           }
         }
       }
@@ -569,25 +684,45 @@ __global__ void __launch_bounds__(REVERSE_THREADS) k_reverse(const DevScene s, c
 
 }  // namespace
 
-cudaError_t launch_tile(const DevScene& s, const DevCache& c, const Arena& a, const IterArgs& it, int num_sms,
+size_t shade_smem(int threads) { return (size_t)(threads / 32) * sizeof(ShadeWarpCtx); }
+
+cudaError_t wave_occupancy(const int threads[WAVE_KERNELS], int blocks_per_sm[WAVE_KERNELS]) {
+  cudaError_t e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[WK_TRACE], k_trace, threads[WK_TRACE], 0)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[WK_SHADE], k_shade, threads[WK_SHADE],
+                                                         shade_smem(threads[WK_SHADE]))) != cudaSuccess)
+    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[WK_SHADOW], k_shadow, threads[WK_SHADOW],
+                                                         0)) != cudaSuccess)
+    return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[WK_REVERSE], k_reverse, threads[WK_REVERSE], 0);
+}
+
+bool wave_threads_ok(int threads) { return threads >= 32 && threads <= MAX_WAVE_THREADS && threads % 32 == 0; }
+
+cudaError_t launch_tile(const DevScene& s, const DevCache& c, const Arena& a, const IterArgs& it, const WaveLaunch& L,
                         cudaStream_t st, cudaEvent_t* ev) {
   const unsigned long long n0 = (unsigned long long)(it.tile_end - it.tile_begin);
   k_tile_init<<<1, 32, 0, st>>>(c.ctr, n0);
   const int D = c.max_depth;
-  const int g = num_sms * 8;
+  const int tT = L.threads[WK_TRACE], tS = L.threads[WK_SHADE], tH = L.threads[WK_SHADOW], tR = L.threads[WK_REVERSE];
+  const int gT = L.grid[WK_TRACE], gS = L.grid[WK_SHADE], gH = L.grid[WK_SHADOW], gR = L.grid[WK_REVERSE];
+  const size_t smS = shade_smem(tS);
   // ev (optional, 4 D + 1 events): ev[0] first; after wave d's trace, shade and
   // shadow kernels ev[3(d-1) + 1..3]; after the k-th reverse kernel ev[3 D + k]
   if (ev) cudaEventRecord(ev[0], st);
   for (int d = 1; d <= D; ++d) {
-    k_trace<<<g, TRACE_THREADS, 0, st>>>(s, c, a, it, d);
+    k_trace<<<gT, tT, 0, st>>>(s, c, a, it, d);
     if (ev) cudaEventRecord(ev[3 * (d - 1) + 1], st);
-    k_shade<<<g, SHADE_THREADS, 0, st>>>(s, c, a, it, d);
+    k_shade<<<gS, tS, smS, st>>>(s, c, a, it, d);
     if (ev) cudaEventRecord(ev[3 * (d - 1) + 2], st);
-    if (d <= D - 1 && (c.techniques & MARS_TECH_NEE)) k_shadow<<<g, SHADOW_THREADS, 0, st>>>(s, c, a, d);
+    if (d <= D - 1 && (c.techniques & MARS_TECH_NEE)) k_shadow<<<gH, tH, 0, st>>>(s, c, a, d);
     if (ev) cudaEventRecord(ev[3 * (d - 1) + 3], st);
   }
   for (int d = D; d >= 1; --d) {
-    k_reverse<<<g, REVERSE_THREADS, 0, st>>>(s, c, a, it, d);
+    k_reverse<<<gR, tR, 0, st>>>(s, c, a, it, d);
     if (ev) cudaEventRecord(ev[3 * D + (D - d + 1)], st);
   }
   k_tile_finish<<<1, 32, 0, st>>>(c.ctr, c.tile_status, it.tile_slot, D);

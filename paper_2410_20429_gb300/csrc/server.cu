@@ -23,7 +23,7 @@ struct Job {
   uint64_t id = 0;
   mars::SceneDescCopy scene;
   mars_cache_desc cache{};
-  uint32_t seed = 0;
+  uint32_t seed = 0, key = 0;
   int iterations = 0, warmup = 0;
   uint64_t footprint = 0;
   mars_job_state state = MARS_JOB_QUEUED;
@@ -74,7 +74,7 @@ struct mars_server {
     for (int it = 0; rc == MARS_OK && it < j->iterations; ++it) {
       mars_iter_params p{};
       p.seed = j->seed;
-      p.job = (uint32_t)j->id;
+      p.job = j->key;
       p.iteration = (uint32_t)it;
       p.mode = it < j->warmup ? MARS_MODE_WARMUP : MARS_MODE_MARS;
       p.weights = MARS_WEIGHTS_AWARE;
@@ -178,6 +178,7 @@ mars_status mars_submit(mars_server* s, const mars_job_desc* jd, uint64_t* job_i
   j->scene.assign(d);
   j->cache = jd->cache;
   j->seed = jd->seed;
+  j->key = jd->key;
   j->iterations = jd->iterations;
   j->warmup = jd->warmup;
   const int64_t npx = (int64_t)d->width * d->height;
@@ -222,6 +223,7 @@ mars_status mars_poll(mars_server* s, uint64_t job_id, mars_job_status* out, flo
   };
   out->iter_ms_p50 = q(0.5);
   out->iter_ms_p99 = q(0.99);
+  out->device_bytes = j->footprint;
   if (j->state == MARS_JOB_FAILED) mars::set_error(j->error, "job %llu failed: %s", (unsigned long long)job_id,
                                                    j->message.c_str());
   if (image_rgb && j->state == MARS_JOB_DONE && !j->image.empty())

@@ -118,46 +118,59 @@ __global__ void k_update_counts(DevCache c) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= c.n_cells * NT) return;
   const int t = idx % NT;
-  double* s = c.stats + (size_t)idx * NSTAT;
+  double2* s2 = reinterpret_cast<double2*>(c.stats + (size_t)idx * NSTAT);
+  const double2 a = s2[0];
+  // no sample landed in this (cell, technique): every sum is already zero
+  if (a.x == 0.0) return;
+  const double2 b = s2[1], cc = s2[2], e = s2[3];
   const double VI = c.ctr->VI, CI = c.ctr->CI;
-  if (((c.techniques >> t) & 1) && VI > 1e-12) {
-    const double n = s[0];
-    if (n >= 2.0 && s[7] > 0.0) {
-      const double Ct = s[7] / n;
-      float qr[3], qs[3];
-      for (int ch = 0; ch < 3; ++ch) {
-        const double m1 = s[1 + ch] / n, m2 = s[4 + ch] / n;
-        double var = m2 - m1 * m1;
-        if (var < 0.0) var = 0.0;
-        qr[ch] = (float)sqrt(CI / Ct * m2 / VI);
-        qs[ch] = (float)sqrt(CI / Ct * var / VI);
-      }
-      c.cnt[2 * idx] = make_float4(qr[0], qr[1], qr[2], 1.0f);
-      c.cnt[2 * idx + 1] = make_float4(qs[0], qs[1], qs[2], 0.0f);
+  const double n = a.x, cost = e.y;
+  if (((c.techniques >> t) & 1) && VI > 1e-12 && n >= 2.0 && cost > 0.0) {
+    // C_I / C_t / V_I with C_t = cost / n, and 1 / n, formed once in float64
+    const double inv_n = 1.0 / n;
+    const double r = CI * n / (cost * VI);
+    const double s1[3] = {a.y, b.x, b.y}, s2v[3] = {cc.x, cc.y, e.x};
+    float qr[3], qs[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      const double m1 = s1[ch] * inv_n, m2 = s2v[ch] * inv_n;
+      double var = m2 - m1 * m1;
+      if (var < 0.0) var = 0.0;
+      qr[ch] = (float)sqrt(r * m2);
+      qs[ch] = (float)sqrt(r * var);
     }
+    c.cnt[2 * idx] = make_float4(qr[0], qr[1], qr[2], 1.0f);
+    c.cnt[2 * idx + 1] = make_float4(qs[0], qs[1], qs[2], 0.0f);
   }
-  for (int k = 0; k < NSTAT; ++k) s[k] = 0.0;
+  const double2 z = make_double2(0.0, 0.0);
+  s2[0] = z;
+  s2[1] = z;
+  s2[2] = z;
+  s2[3] = z;
 }
 
 // one warp per cell: P_b = 0.9 h_b / H + 0.1 / 256 (uniform when H = 0), then an
-// inclusive prefix sum in float64
+// inclusive prefix sum in float64.  Lane l holds bins 8 l .. 8 l + 7 (two float4
+// loads and stores); one float64 reciprocal per cell.
 __global__ void k_guide_update(DevCache c) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= c.n_cells) return;
-  const float* h = c.guide_hist + (size_t)warp * GUIDE_BINS;
-  float* cdf = c.guide_cdf + (size_t)warp * GUIDE_BINS;
-  double v[8];
+  const float4* h = reinterpret_cast<const float4*>(c.guide_hist + (size_t)warp * GUIDE_BINS) + 2 * lane;
+  float4* cdf = reinterpret_cast<float4*>(c.guide_cdf + (size_t)warp * GUIDE_BINS) + 2 * lane;
+  const float4 h0 = h[0], h1 = h[1];
+  double v[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
   double loc = 0.0;
-  for (int k = 0; k < 8; ++k) {
-    v[k] = (double)h[lane * 8 + k];
-    loc += v[k];
-  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) loc += v[k];
   double H = loc;
   for (int off = 16; off > 0; off >>= 1) H += __shfl_xor_sync(0xffffffffu, H, off);
+  const double sc = H > 0.0 ? 0.9 / H : 0.0;
+  const double base = H > 0.0 ? 0.1 / GUIDE_BINS : 1.0 / GUIDE_BINS;
   double run = 0.0;
+#pragma unroll
   for (int k = 0; k < 8; ++k) {
-    v[k] = H > 0.0 ? 0.9 * v[k] / H + 0.1 / GUIDE_BINS : 1.0 / GUIDE_BINS;
+    v[k] = v[k] * sc + base;
     run += v[k];
   }
   double incl = run;
@@ -166,10 +179,15 @@ __global__ void k_guide_update(DevCache c) {
     if (lane >= off) incl += y;
   }
   double acc = incl - run;
+  float o[8];
+#pragma unroll
   for (int k = 0; k < 8; ++k) {
     acc += v[k];
-    cdf[lane * 8 + k] = (lane == 31 && k == 7) ? 1.0f : (float)acc;
+    o[k] = (float)acc;
   }
+  if (lane == 31) o[7] = 1.0f;
+  cdf[0] = make_float4(o[0], o[1], o[2], o[3]);
+  cdf[1] = make_float4(o[4], o[5], o[6], o[7]);
 }
 
 }  // namespace

@@ -126,6 +126,30 @@ class Cache:
                 "shade_ms": st.shade_ms, "shadow_ms": st.shadow_ms, "reverse_ms": st.reverse_ms,
                 "image_ms": st.image_ms, "wave_entries": st.wave_entries, "shadow_entries": st.shadow_entries}
 
+    def get_launch(self) -> dict:
+        """Launch shape of the wave kernels (trace, shade, shadow, reverse)."""
+        cfg = A.mars_launch_config()
+        A.check(self._lib.mars_cache_get_launch(self.handle, ct.byref(cfg)), "mars_cache_get_launch")
+        return {"threads": list(cfg.threads), "blocks_per_sm": list(cfg.blocks_per_sm)}
+
+    def set_launch(self, threads, blocks_per_sm) -> None:
+        cfg = A.mars_launch_config()
+        for k in range(4):
+            cfg.threads[k] = int(threads[k])
+            cfg.blocks_per_sm[k] = int(blocks_per_sm[k])
+        A.check(self._lib.mars_cache_set_launch(self.handle, ct.byref(cfg)), "mars_cache_set_launch")
+
+    def autotune(self, *, seed=0, job=0, iteration=0, mode=A.MARS_MODE_WARMUP, weights=A.MARS_WEIGHTS_AWARE,
+                 clamp_lo=0.05, clamp_hi=20.0, outlier=50.0, repeats=2, stream=None) -> dict:
+        """Pick the fastest launch shape of every wave kernel on this iteration
+        (rendered without statistics, so the learned state is unchanged)."""
+        p = A.mars_iter_params(int(seed), int(job), int(iteration), int(mode), int(weights), float(clamp_lo),
+                               float(clamp_hi), float(outlier), 0, 0, 0, 1)
+        cfg = A.mars_launch_config()
+        A.check(self._lib.mars_cache_autotune(self.handle, ct.byref(p), int(repeats), ct.byref(cfg),
+                                              _stream_handle(stream)), "mars_cache_autotune")
+        return {"threads": list(cfg.threads), "blocks_per_sm": list(cfg.blocks_per_sm)}
+
     def update_counts(self, stream=None) -> None:
         A.check(self._lib.mars_update_counts(self.handle, _stream_handle(stream)), "mars_update_counts")
 
@@ -201,12 +225,13 @@ class Server:
         self.handle = h
         self._descs = {}
 
-    def submit(self, desc, *, grid_n, techniques, max_depth, iterations, warmup, seed=0, arena_capacity=0) -> int:
+    def submit(self, desc, *, grid_n, techniques, max_depth, iterations, warmup, seed=0, key=0,
+               arena_capacity=0) -> int:
         d, keep = scene_desc(desc)
         j = A.mars_job_desc()
         j.scene = ct.pointer(d)
         j.cache = A.mars_cache_desc(int(grid_n), int(techniques), int(max_depth), 0, int(arena_capacity))
-        j.seed, j.iterations, j.warmup = int(seed), int(iterations), int(warmup)
+        j.seed, j.iterations, j.warmup, j.key = int(seed), int(iterations), int(warmup), int(key)
         jid = ct.c_uint64()
         A.check(self._lib.mars_submit(self.handle, ct.byref(j), ct.byref(jid)), "mars_submit")
         self._descs[jid.value] = (desc.width, desc.height)

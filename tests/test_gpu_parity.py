@@ -201,6 +201,40 @@ def test_arena_overflow_tiles_reproduce_the_image(mars):
     assert sa["rays"] == sb["rays"] and sa["vertices"] == sb["vertices"]
 
 
+def test_launch_shape_does_not_change_results(mars):
+    """Every wave kernel strides over its wave in chunks of 32 slots, so threads
+    per block and grid size change the speed only: the image is bitwise equal
+    and the statistics equal up to the order of the float64 atomics.  The
+    autotuner leaves the learned state untouched."""
+    cfg = W.config_guided(48, 40)
+    q_rr, q_s, valid = W.random_count_fields(cfg.n_cells, seed=601, lo=0.3, hi=4.0)
+    est = W.random_pixel_estimate(cfg.scene.n_pixels, seed=602, lo=0.05, hi=0.5)
+    scene, cache = _make(mars, cfg)
+    base = cache.get_launch()
+    assert base["threads"] == [128, 128, 128, 128] and min(base["blocks_per_sm"]) >= 1
+    res = []
+    for threads, bps in (([128] * 4, [0] * 4), ([64, 256, 32, 256], [3, 1, 7, 2]), ([256, 64, 256, 64], [9, 5, 1, 4])):
+        cache.set_launch(threads, bps)
+        cache.set_state(q_rr=q_rr, q_s=q_s, valid=valid, pixel_estimate=est, has_estimate=True, n_iterations=1,
+                        stats=np.zeros((cfg.n_cells, 3, 8)))
+        img, st = _gpu_iteration(mars, cache, iteration=1, seed=4, mode=1)
+        res.append((img, st, cache.get_state()["stats"]))
+    for img, st, stats in res[1:]:
+        assert np.array_equal(img, res[0][0])
+        assert st["rays"] == res[0][1]["rays"] and st["vertices"] == res[0][1]["vertices"]
+        np.testing.assert_allclose(stats, res[0][2], rtol=1e-6, atol=1e-9)
+    before = cache.get_state()
+    chosen = cache.autotune(iteration=1, seed=4, mode=1, repeats=1)
+    assert all(t in (64, 128, 256) for t in chosen["threads"]) and min(chosen["blocks_per_sm"]) >= 1
+    after = cache.get_state()
+    for k in ("q_rr", "q_s", "valid", "stats", "run_sum", "pixel_estimate", "guide_cdf", "guide_hist"):
+        assert np.array_equal(before[k], after[k]), k
+    img, st = _gpu_iteration(mars, cache, iteration=1, seed=4, mode=1)
+    assert np.array_equal(img, res[0][0])
+    with pytest.raises(mars.MarsError):
+        cache.set_launch([100, 128, 128, 128], [0] * 4)
+
+
 @pytest.mark.parametrize("albedo,D", [(0.5, 3), (0.8, 5)])
 def test_gpu_furnace_closed_form(mars, albedo, D):
     """The CUDA path alone against the closed furnace Le (1 - a^D) / (1 - a)
