@@ -44,17 +44,18 @@ UNIT = "Mvertices/s"
 # algorithmic bytes of the arena records (see the layout in csrc/internal.h)
 RAY_BYTES = 80          # R0..R4: five float4 per ray
 RAY_TRACE_BYTES = 32    # R0, R1: origin and direction
-HIT_BYTES = 8           # H: (t, primitive)
+HIT_BYTES = 8           # H: (t, primitive), then (first child, first shadow ray)
 V0_BYTES = 16           # V0 for every slot
 VERT_EST_BYTES = 48     # V1..V3 for a vertex that runs the estimator
 VERT_GUIDE_BYTES = 16   # V4 for a traced ray when the guided technique learns
 SAMPLE_BYTES = 16       # S: one float4 per slot
 EST_READ_BYTES = 16     # pixel estimate read per estimator vertex
-SHADOW_BYTES = 48       # SH0..SH2 per NEE shadow ray
+SHADOW_VALUE_BYTES = 16  # SH2 per NEE sample
+SHADOW_RAY_BYTES = 36   # SH0, SH1 and the work-list entry per traced shadow ray
 SLOT_BYTES = RAY_BYTES + HIT_BYTES + V0_BYTES + VERT_EST_BYTES + VERT_GUIDE_BYTES + SAMPLE_BYTES
 
 
-def kernel_bytes(entries, pixels, est_v, traced, shadows, guided):
+def kernel_bytes(entries, pixels, est_v, traced, shadows, shadow_traced, guided):
     """Minimum HBM bytes each wave kernel must move for one step (its inputs
     read once, its outputs written once)."""
     children = entries - pixels
@@ -62,11 +63,11 @@ def kernel_bytes(entries, pixels, est_v, traced, shadows, guided):
     return {
         "k_trace": RAY_TRACE_BYTES * children + HIT_BYTES * entries,
         "k_shade": (RAY_BYTES * children + HIT_BYTES * entries + V0_BYTES * entries
-                    + (VERT_EST_BYTES + EST_READ_BYTES) * est_v + RAY_BYTES * children + SHADOW_BYTES * shadows
-                    + guide),
-        "k_shadow": 32 * shadows,
-        "k_reverse": (V0_BYTES * entries + SAMPLE_BYTES * entries + VERT_EST_BYTES * est_v
-                      + SAMPLE_BYTES * children + 16 * shadows + guide),
+                    + (VERT_EST_BYTES + EST_READ_BYTES + HIT_BYTES) * est_v + RAY_BYTES * children
+                    + SHADOW_VALUE_BYTES * shadows + SHADOW_RAY_BYTES * shadow_traced + guide),
+        "k_shadow": SHADOW_RAY_BYTES * shadow_traced,
+        "k_reverse": (V0_BYTES * entries + SAMPLE_BYTES * entries + (VERT_EST_BYTES + HIT_BYTES) * est_v
+                      + SAMPLE_BYTES * children + SHADOW_VALUE_BYTES * shadows + guide),
     }
 
 
@@ -140,6 +141,20 @@ def rel_mse(img, ref):
     return float(t.mean())
 
 
+def reduce_over_ranks(total_ms, units, world, device):
+    """Whole-job aggregation across ranks: the slowest rank's time (MAX) and the
+    units all ranks processed (SUM).  One rank: the inputs unchanged."""
+    if world <= 1:
+        return float(total_ms), float(units)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(total_ms)], device=device, dtype=torch.float64)
+    v = torch.tensor([float(units)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(v)
+    return float(t.item()), float(v.item())
+
+
 def run_mars(args):
     import torch
     import paper_2410_20429_gb300 as M
@@ -162,7 +177,12 @@ def run_mars(args):
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         scene = M.Scene(sc, stream=stream)
-        cache = M.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, stream=stream)
+        cache = M.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, arena_capacity=args.arena_capacity,
+                        stream=stream)
+    if args.launch:
+        parts = args.launch.split(":")
+        regs = [int(x) for x in parts[2].split(",")] if len(parts) > 2 else [0, 0, 0, 0]
+        cache.set_launch([int(x) for x in parts[0].split(",")], [int(x) for x in parts[1].split(",")], regs)
     npx = sc.n_pixels
     img = torch.zeros(npx * 3, dtype=torch.float32, device="cuda")
     seed = 1000 + rank  # weak-scaling replicas: every rank renders its own job
@@ -180,7 +200,7 @@ def run_mars(args):
     # launch shape of the wave kernels picked by the library's autotuner on a
     # MARS iteration with the counts learned so far (no state change)
     launch = cache.autotune(iteration=it, seed=seed, mode=M.MARS_MODE_MARS, repeats=2, stream=stream) \
-        if not args.no_autotune else cache.get_launch()
+        if not (args.no_autotune or args.launch) else cache.get_launch()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -200,21 +220,14 @@ def run_mars(args):
     per_step = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
     total_ms = sum(per_step)
     verts = sum(s["vertices"] for s in sts)
-    t_max = total_ms
-    verts_all = verts
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        v = torch.tensor([float(verts)], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(v)
-        t_max, verts_all = float(t.item()), float(v.item())
+    t_max, verts_all = reduce_over_ranks(total_ms, verts, world, "cuda")
     value = verts_all / (t_max * 1e-3) / 1e6
 
     # ---- dominant kernel roofline (live CUDA-event times of every launch)
     guided = bool(cfg.techniques & W.TECH_GUIDED)
     kb = kernel_bytes(sum(s["wave_entries"] for s in sts), npx * args.steps,
                       sum(s["estimator_vertices"] for s in sts), verts, sum(s["shadow_entries"] for s in sts),
-                      guided)
+                      sum(s["shadow_traced"] for s in sts), guided)
     kms = {k: sum(s[k[2:] + "_ms"] for s in sts) for k in kb}
     launches_per_kernel = sum(s["wave_launches"] for s in sts)
     hbm, peak_kind = peaks()
@@ -228,6 +241,9 @@ def run_mars(args):
                 "kernel_ms_per_step": {k: round(v / args.steps, 4) for k, v in kms.items()},
                 "kernel_gbs": {k: round(kb[k] / max(kms[k], 1e-9) / 1e6, 1) for k in kb}}
     roofline["kernel_ms_per_step"]["image"] = round(sum(s["image_ms"] for s in sts) / args.steps, 4)
+    roofline["wave_ms_per_step"] = {k: [round(sum(s["wave_ms"][ki][d] for s in sts) / args.steps, 4)
+                                        for d in range(cfg.max_depth)]
+                                    for ki, k in enumerate(["k_trace", "k_shade", "k_shadow", "k_reverse"])}
     entries = sum(s["wave_entries"] for s in sts)
 
     # ---- end to end through the C ABI with a pinned host image every step
@@ -263,9 +279,11 @@ def run_mars(args):
                      "tiles": sum(s["tiles"] for s in sts) / args.steps},
         "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
         "launch": {"kernels": ["trace", "shade", "shadow", "reverse"], **launch,
-                   "autotuned": not args.no_autotune},
+                   "autotuned": not (args.no_autotune or args.launch)},
     }
 
+    if rank == 0 and not args.no_precision:
+        line["precision"] = precision_study(cfg, cache, seed, it, stream)
     if rank == 0 and not args.no_efficiency:
         line["efficiency"] = efficiency(args, M, cfg, scene, cache, seed, it, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -276,6 +294,23 @@ def run_mars(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def precision_study(cfg, cache, seed, it, stream):
+    """Float32 versus float64 statistics on the full workload: the next MARS
+    iteration rendered from the bench cache's learned state on one cache of
+    each precision; relative error of every statistic of the float32 run
+    (max and median over the (cell, technique) entries with >= 2 samples)."""
+    from paper_2410_20429_gb300 import precision
+    g = cache.get_state(stream=stream)
+    rep = precision.compare(cfg.scene, cfg.grid_n, cfg.techniques, cfg.max_depth, g["q_rr"], g["q_s"], g["valid"],
+                            g["pixel_estimate"], g["run_sum"], g["n_iterations"], iteration=it, seed=seed,
+                            stream=stream)
+    out = {k: [float("%.3g" % rep[k]["max"]), float("%.3g" % rep[k]["median"])] for k in precision.STATISTICS}
+    out["fields"] = "relative error of float32 vs float64 statistics: [max, median]"
+    out["images_equal"] = rep["images_equal"]
+    out["entries"] = rep["cells_compared"]
+    return out
 
 
 def efficiency(args, M, cfg, scene, cache, seed, it0, stream):
@@ -405,6 +440,10 @@ def main():
     ap.add_argument("--eff-spp", type=int, default=32)
     ap.add_argument("--ref-pixels-per-step", type=int, default=1024)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--launch", default="", help="fixed wave-kernel launch shape 't,t,t,t:b,b,b,b[:r,r,r,r]' (threads per "
+                    "block, blocks per SM and register cap of trace, shade, shadow, reverse); skips the autotuner")
+    ap.add_argument("--arena-capacity", type=int, default=0, help="queue arena slots (0 = library default)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "mars":
         ap.error("--warmup must be at least 3")

@@ -95,14 +95,18 @@ typedef struct {
  * techniques: MARS_TECH_* bits; BSDF is required.
  * max_depth: maximum number of path segments D (1..MARS_MAX_DEPTH); vertices
  *   x_1..x_{D-1} run the secondary estimator.
+ * flags: 0, or MARS_CACHE_FP32_STATISTICS: accumulate the local statistics,
+ *   run the count update and reduce V_I and C_I in float32 instead of float64
+ *   (the float32-only variant of the precision study; default float64).
  * arena_capacity: rays held by the per-iteration queue arena summed over all
  *   depths (0 = 8 x pixels x max_depth, at least 2^20).  An iteration whose path
  *   trees do not fit is rendered in pixel tiles (results do not depend on it). */
+#define MARS_CACHE_FP32_STATISTICS 1
 typedef struct {
   int32_t grid_n;
   int32_t techniques;
   int32_t max_depth;
-  int32_t reserved;
+  int32_t flags;
   uint64_t arena_capacity;
 } mars_cache_desc;
 
@@ -149,6 +153,8 @@ typedef struct {
   double trace_ms, shade_ms, shadow_ms, reverse_ms, image_ms;
   uint64_t wave_entries;      /* rays held in the depth waves (traced or not), all tiles */
   uint64_t shadow_entries;    /* NEE shadow-ray slots, all tiles */
+  uint64_t shadow_traced;     /* NEE shadow rays traced (samples of nonzero value), all tiles */
+  float wave_ms[4][16];       /* profile = 1: device ms of trace, shade, shadow, reverse per depth wave d (index d - 1) */
 } mars_iter_stats;
 
 /* Host copy of a cache's state (checkpoint / teacher forcing).  Any pointer
@@ -239,16 +245,23 @@ mars_status mars_cache_set_state(mars_cache* cache, const mars_cache_state* stat
  * threads[k]: threads per block of kernel k (0 trace, 1 shade, 2 shadow,
  *   3 reverse), a multiple of 32 in 32..256.
  * blocks_per_sm[k]: 1..64, or 0 = as many blocks as fit on an SM at once
- *   (mars_cache_get_launch reports the resolved count).  Default: 128 threads,
- *   the occupancy maximum.  Errors: INVALID_ARG, CUDA. */
+ *   (mars_cache_get_launch reports the resolved count).
+ * max_registers[k]: selects a compiled variant of the kernel whose registers
+ *   per thread are capped (more resident blocks, possibly some spilling).
+ * Default: 128 threads, no cap, the occupancy maximum.  Each depth wave's grid
+ * is further sized from the previous iteration's wave size (at least one block
+ * per SM, at most the grid above).  Errors: INVALID_ARG, CUDA. */
 typedef struct {
   int32_t threads[4];
   int32_t blocks_per_sm[4];
+  int32_t max_registers[4];  /* register cap of the compiled variant: 0 = the compiler's
+                                choice; shade and reverse also 80 or 64, trace and shadow 40 */
 } mars_launch_config;
 mars_status mars_cache_get_launch(const mars_cache* cache, mars_launch_config* out);
 mars_status mars_cache_set_launch(mars_cache* cache, const mars_launch_config* config);
-/* Picks each wave kernel's launch shape in turn (threads per block in
- * {64, 128, 256} x blocks per SM in {half, full, twice} the occupancy maximum)
+/* Picks each wave kernel's launch shape in turn (register-cap variant x threads
+ * per block in {64, 128, 256} x blocks per SM in {half, full, twice} the
+ * occupancy maximum)
  * by the kernel's device time over `repeats` (1..100) renders of `params`'s
  * iteration, rendered without statistics, guide deposits or image statistics
  * so that the cache's learned state is unchanged; keeps the fastest shape and

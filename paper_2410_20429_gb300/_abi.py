@@ -15,6 +15,7 @@ MARS_TECH_BSDF, MARS_TECH_NEE, MARS_TECH_GUIDED = 1, 2, 4
 MARS_MODE_WARMUP, MARS_MODE_MARS, MARS_MODE_FIXED = 0, 1, 2
 MARS_WEIGHTS_AWARE, MARS_WEIGHTS_UNAWARE = 0, 1
 MARS_JOB_QUEUED, MARS_JOB_RUNNING, MARS_JOB_DONE, MARS_JOB_FAILED = range(4)
+MARS_CACHE_FP32_STATISTICS = 1
 NUM_SLOTS, NUM_STATS, GUIDE_BINS, MAX_DEPTH = 3, 8, 256, 16
 
 
@@ -38,7 +39,7 @@ class mars_scene_desc(ct.Structure):
 
 class mars_cache_desc(ct.Structure):
     _fields_ = [("grid_n", ct.c_int32), ("techniques", ct.c_int32), ("max_depth", ct.c_int32),
-                ("reserved", ct.c_int32), ("arena_capacity", ct.c_uint64)]
+                ("flags", ct.c_int32), ("arena_capacity", ct.c_uint64)]
 
 
 class mars_iter_params(ct.Structure):
@@ -58,7 +59,8 @@ class mars_iter_stats(ct.Structure):
         ("retries", ct.c_uint32), ("arena_demand", ct.c_uint64), ("launches", ct.c_uint32),
         ("wave_launches", ct.c_uint32), ("trace_ms", ct.c_double), ("shade_ms", ct.c_double),
         ("shadow_ms", ct.c_double), ("reverse_ms", ct.c_double), ("image_ms", ct.c_double),
-        ("wave_entries", ct.c_uint64), ("shadow_entries", ct.c_uint64),
+        ("wave_entries", ct.c_uint64), ("shadow_entries", ct.c_uint64), ("shadow_traced", ct.c_uint64),
+        ("wave_ms", (ct.c_float * 16) * 4),
     ]
 
 
@@ -81,7 +83,7 @@ class mars_cache_info(ct.Structure):
 
 
 class mars_launch_config(ct.Structure):
-    _fields_ = [("threads", ct.c_int32 * 4), ("blocks_per_sm", ct.c_int32 * 4)]
+    _fields_ = [("threads", ct.c_int32 * 4), ("blocks_per_sm", ct.c_int32 * 4), ("max_registers", ct.c_int32 * 4)]
 
 
 class mars_job_desc(ct.Structure):

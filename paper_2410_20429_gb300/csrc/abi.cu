@@ -373,6 +373,8 @@ mars_status cache_create_impl(const mars_scene* s, const mars_cache_desc* d, cud
     return set_error(MARS_ERR_INVALID_ARG, "max_depth %d out of [1, %d]", d->max_depth, MAXD);
   if ((d->techniques & MARS_TECH_NEE) && s->n_lights == 0)
     return set_error(MARS_ERR_INVALID_ARG, "NEE requested but the scene has no emitting quad");
+  if (d->flags & ~MARS_CACHE_FP32_STATISTICS) return set_error(MARS_ERR_INVALID_ARG, "unknown cache flags %d", d->flags);
+  const bool fp32 = (d->flags & MARS_CACHE_FP32_STATISTICS) != 0;
   const int bits = (d->techniques & MARS_TECH_GUIDED) ? 6 : 5;
   if ((d->max_depth - 1) * bits > 64)
     return set_error(MARS_ERR_INVALID_ARG, "max_depth %d too deep for %d lineage bits per level", d->max_depth, bits);
@@ -410,11 +412,20 @@ mars_status cache_create_impl(const mars_scene* s, const mars_cache_desc* d, cud
   for (int k = 0; k < NSH; ++k)
     if ((e = cudaMalloc(&c->arena.SH[k], sizeof(float4) * c->arena.scap)) != cudaSuccess)
       return cleanup(e, "arena alloc");
+  if ((e = cudaMalloc(&c->arena.SL, sizeof(unsigned int) * c->arena.scap)) != cudaSuccess)
+    return cleanup(e, "arena alloc");
   if ((e = cudaMalloc(&c->d_cnt, sizeof(float4) * 2 * NT * cells)) != cudaSuccess) return cleanup(e, "cache alloc");
-  if ((e = cudaMalloc(&c->d_stats, sizeof(double) * NSTAT * NT * cells)) != cudaSuccess) return cleanup(e, "cache alloc");
+  c->fp32_stats = fp32;
+  if (fp32) {
+    if ((e = cudaMalloc(&c->d_stats32, sizeof(float) * NSTAT * NT * cells)) != cudaSuccess)
+      return cleanup(e, "cache alloc");
+  } else if ((e = cudaMalloc(&c->d_stats, sizeof(double) * NSTAT * NT * cells)) != cudaSuccess) {
+    return cleanup(e, "cache alloc");
+  }
   const int64_t gcells = (d->techniques & MARS_TECH_GUIDED) ? cells : 1;
   if ((e = cudaMalloc(&c->d_hist, sizeof(float) * GUIDE_BINS * gcells)) != cudaSuccess) return cleanup(e, "cache alloc");
   if ((e = cudaMalloc(&c->d_cdf, sizeof(float) * GUIDE_BINS * gcells)) != cudaSuccess) return cleanup(e, "cache alloc");
+  if ((e = cudaMalloc(&c->d_guide_dirty, (size_t)gcells)) != cudaSuccess) return cleanup(e, "cache alloc");
   if ((e = cudaMalloc(&c->d_est, sizeof(float4) * pixels)) != cudaSuccess) return cleanup(e, "image alloc");
   if ((e = cudaMalloc(&c->d_run, sizeof(float4) * pixels)) != cudaSuccess) return cleanup(e, "image alloc");
   if ((e = cudaMalloc(&c->d_img, sizeof(float4) * pixels)) != cudaSuccess) return cleanup(e, "image alloc");
@@ -425,8 +436,10 @@ mars_status cache_create_impl(const mars_scene* s, const mars_cache_desc* d, cud
   if ((e = cudaMallocHost(&c->h_tile_status, sizeof(unsigned int) * c->max_tiles)) != cudaSuccess)
     return cleanup(e, "pinned alloc");
   cudaMemsetAsync(c->d_cnt, 0, sizeof(float4) * 2 * NT * cells, st);
-  cudaMemsetAsync(c->d_stats, 0, sizeof(double) * NSTAT * NT * cells, st);
+  if (c->d_stats) cudaMemsetAsync(c->d_stats, 0, sizeof(double) * NSTAT * NT * cells, st);
+  if (c->d_stats32) cudaMemsetAsync(c->d_stats32, 0, sizeof(float) * NSTAT * NT * cells, st);
   cudaMemsetAsync(c->d_hist, 0, sizeof(float) * GUIDE_BINS * gcells, st);
+  cudaMemsetAsync(c->d_guide_dirty, 0, (size_t)gcells, st);
   cudaMemsetAsync(c->d_run, 0, sizeof(float4) * pixels, st);
   cudaMemsetAsync(c->d_img, 0, sizeof(float4) * pixels, st);
   cudaMemsetAsync(c->d_ctr, 0, sizeof(DevCounters), st);
@@ -449,8 +462,10 @@ mars_status cache_create_impl(const mars_scene* s, const mars_cache_desc* d, cud
   c->dc.n_pixels = (int)pixels;
   c->dc.cnt = c->d_cnt;
   c->dc.stats = c->d_stats;
+  c->dc.stats32 = c->d_stats32;
   c->dc.guide_hist = c->d_hist;
   c->dc.guide_cdf = c->d_cdf;
+  c->dc.guide_dirty = c->d_guide_dirty;
   c->dc.est = c->d_est;
   c->dc.run_sum = c->d_run;
   c->dc.img = c->d_img;
@@ -460,7 +475,8 @@ mars_status cache_create_impl(const mars_scene* s, const mars_cache_desc* d, cud
   {
     const int threads[WAVE_KERNELS] = {128, 128, 128, 128};
     const int bps[WAVE_KERNELS] = {0, 0, 0, 0};
-    const mars_status ls = apply_launch(c, threads, bps);
+    const int var[WAVE_KERNELS] = {0, 0, 0, 0};
+    const mars_status ls = apply_launch(c, threads, bps, var);
     if (ls != MARS_OK) {
       cache_destroy_impl(c);
       return ls;
@@ -473,8 +489,11 @@ mars_status cache_create_impl(const mars_scene* s, const mars_cache_desc* d, cud
 // Grid of each wave kernel = SMs x resident blocks per SM (the occupancy
 // maximum unless a positive count is given): a persistent grid that strides
 // over the wave.
-mars_status apply_launch(mars_cache* c, const int threads[WAVE_KERNELS], const int blocks_per_sm[WAVE_KERNELS]) {
+mars_status apply_launch(mars_cache* c, const int threads[WAVE_KERNELS], const int blocks_per_sm[WAVE_KERNELS],
+                         const int variant[WAVE_KERNELS]) {
   for (int k = 0; k < WAVE_KERNELS; ++k) {
+    if (variant[k] < 0 || variant[k] >= wave_variants(k))
+      return set_error(MARS_ERR_INVALID_ARG, "wave kernel %d: no register-cap variant %d", k, variant[k]);
     if (!wave_threads_ok(threads[k]))
       return set_error(MARS_ERR_INVALID_ARG, "wave kernel %d: %d threads per block (need a multiple of 32 in 32..256)",
                        k, threads[k]);
@@ -482,11 +501,12 @@ mars_status apply_launch(mars_cache* c, const int threads[WAVE_KERNELS], const i
       return set_error(MARS_ERR_INVALID_ARG, "wave kernel %d: blocks per SM %d outside 0..64", k, blocks_per_sm[k]);
   }
   int occ[WAVE_KERNELS];
-  const cudaError_t e = wave_occupancy(threads, occ);
+  const cudaError_t e = wave_occupancy(threads, variant, occ);
   if (e != cudaSuccess) return set_error(MARS_ERR_CUDA, "occupancy query: %s", cudaGetErrorString(e));
   for (int k = 0; k < WAVE_KERNELS; ++k) {
     const int b = blocks_per_sm[k] > 0 ? blocks_per_sm[k] : std::max(1, occ[k]);
     c->launch.threads[k] = threads[k];
+    c->launch.variant[k] = variant[k];
     c->launch.grid[k] = c->scene->num_sms * b;
     c->blocks_per_sm[k] = b;
   }
@@ -501,7 +521,8 @@ void cache_destroy_impl(mars_cache* c) {
   if (c->arena.S) cudaFree(c->arena.S);
   if (c->arena.H) cudaFree(c->arena.H);
   for (auto* p : c->arena.SH) if (p) cudaFree(p);
-  void* ptrs[] = {c->d_cnt, c->d_stats, c->d_hist, c->d_cdf, c->d_est, c->d_run, c->d_img, c->d_ctr, c->d_tile_status};
+  if (c->arena.SL) cudaFree(c->arena.SL);
+  void* ptrs[] = {c->d_cnt, c->d_stats, c->d_stats32, c->d_hist, c->d_cdf, c->d_guide_dirty, c->d_est, c->d_run, c->d_img, c->d_ctr, c->d_tile_status};
   for (void* p : ptrs) if (p) cudaFree(p);
   if (c->h_ctr) cudaFreeHost(c->h_ctr);
   if (c->h_tile_status) cudaFreeHost(c->h_tile_status);
@@ -510,6 +531,32 @@ void cache_destroy_impl(mars_cache* c) {
 }
 
 // ------------------------------------------------------------ iteration
+// Grid of every depth wave: the wave sizes of the last single-tile iteration,
+// scaled to this tile's pixels with 50 % headroom, in blocks, between one block
+// per SM and the persistent grid.  Only the speed depends on it: every kernel
+// strides over whatever its wave holds.
+static WaveLaunch wave_grids(const mars_cache* c, int64_t tile_pixels) {
+  WaveLaunch L = c->launch;
+  const int sms = c->scene->num_sms;
+  for (int k = 0; k < WAVE_KERNELS; ++k)
+    for (int d = 0; d < MAXD + 2; ++d) L.wave_grid[k][d] = 0;
+  if (c->last_pixels <= 0) return L;
+  const double scale = (double)tile_pixels / (double)c->last_pixels;
+  auto blocks = [&](int k, double items) {
+    const double est = items * scale * 1.5 + 2048.0;
+    int b = (int)std::ceil(est / L.threads[k]);
+    return std::max(std::min(b, L.grid[k]), std::min(sms, L.grid[k]));
+  };
+  for (int d = 1; d <= c->max_depth; ++d) {
+    const double n = d == 1 ? (double)c->last_pixels : (double)c->last_count[d];
+    L.wave_grid[WK_TRACE][d] = blocks(WK_TRACE, n);
+    L.wave_grid[WK_SHADE][d] = blocks(WK_SHADE, n);
+    L.wave_grid[WK_REVERSE][d] = blocks(WK_REVERSE, n);
+    L.wave_grid[WK_SHADOW][d] = blocks(WK_SHADOW, (double)c->last_slcount[d]);
+  }
+  return L;
+}
+
 static mars_status poison(mars_cache* c, cudaError_t e, const char* what) {
   c->poisoned = true;
   return set_error(MARS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
@@ -558,6 +605,7 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
   uint32_t retries = 0, used = 0, launches = 0, wave_launches = 0;
   uint64_t demand = 0;
   double trace_ms = 0.0, shade_ms = 0.0, shadow_ms = 0.0, reverse_ms = 0.0, image_ms = 0.0;
+  float wave_ms[WAVE_KERNELS][MAXD] = {};
   const int D = c->max_depth;
   const int per_tile = 4 * D + 1;
   float* dev_out = p->image_on_host ? nullptr : image;
@@ -575,7 +623,8 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
       it.tile_end = (int)tiles[t].second;
       it.tile_slot = (int)t;
       cudaEvent_t* ev = p->profile ? c->events.data() + t * per_tile : nullptr;
-      if ((e = launch_tile(s->ds, c->dc, c->arena, it, c->launch, st, ev)) != cudaSuccess)
+      const WaveLaunch L = wave_grids(c, it.tile_end - it.tile_begin);
+      if ((e = launch_tile(s->ds, c->dc, c->arena, it, L, st, ev)) != cudaSuccess)
         return poison(c, e, "render launch");
       launches += (uint32_t)tile_launches(D, c->techniques);
       wave_launches += (uint32_t)D;
@@ -605,13 +654,20 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
         for (int d = 1; d <= D; ++d) {
           cudaEventElapsedTime(&ms, ev[3 * (d - 1)], ev[3 * (d - 1) + 1]);
           trace_ms += ms;
+          wave_ms[WK_TRACE][d - 1] += ms;
           cudaEventElapsedTime(&ms, ev[3 * (d - 1) + 1], ev[3 * (d - 1) + 2]);
           shade_ms += ms;
+          wave_ms[WK_SHADE][d - 1] += ms;
           cudaEventElapsedTime(&ms, ev[3 * (d - 1) + 2], ev[3 * (d - 1) + 3]);
           shadow_ms += ms;
+          wave_ms[WK_SHADOW][d - 1] += ms;
         }
-        cudaEventElapsedTime(&ms, ev[3 * D], ev[4 * D]);
-        reverse_ms += ms;
+        // the k-th reverse launch (k = 1..D) handles wave D - k + 1
+        for (int k = 1; k <= D; ++k) {
+          cudaEventElapsedTime(&ms, ev[3 * D + k - 1], ev[3 * D + k]);
+          reverse_ms += ms;
+          wave_ms[WK_REVERSE][D - k] += ms;
+        }
       }
       float ms = 0.f;
       cudaEventElapsedTime(&ms, iev[0], iev[1]);
@@ -677,9 +733,19 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
     out->image_ms = image_ms;
     out->wave_entries = h.entries;
     out->shadow_entries = h.shadow_entries;
+    out->shadow_traced = h.shadow_traced;
+    for (int k = 0; k < WAVE_KERNELS; ++k)
+      for (int d = 0; d < MAXD; ++d) out->wave_ms[k][d] = wave_ms[k][d];
   }
   c->last_VI = c->h_ctr->VI;
   c->last_CI = c->h_ctr->CI;
+  if (used == 1 && retries == 0) {
+    for (int d = 0; d < MAXD + 2; ++d) {
+      c->last_count[d] = c->h_ctr->count[d];
+      c->last_slcount[d] = c->h_ctr->slcount[d];
+    }
+    c->last_pixels = npx;
+  }
   return MARS_OK;
 }
 
@@ -706,9 +772,16 @@ mars_status get_state_impl(mars_cache* c, mars_cache_state* s, cudaStream_t st) 
     e = cudaMemcpyAsync(cnt.data(), c->d_cnt, sizeof(float4) * cnt.size(), cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return poison(c, e, "state copy");
   }
-  if (s->stats && (e = cudaMemcpyAsync(s->stats, c->d_stats, sizeof(double) * NSTAT * NT * cells,
-                                       cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+  std::vector<float> s32;
+  if (s->stats && c->fp32_stats) {
+    s32.resize((size_t)NSTAT * NT * cells);
+    if ((e = cudaMemcpyAsync(s32.data(), c->d_stats32, sizeof(float) * s32.size(), cudaMemcpyDeviceToHost, st)) !=
+        cudaSuccess)
+      return poison(c, e, "state copy");
+  } else if (s->stats && (e = cudaMemcpyAsync(s->stats, c->d_stats, sizeof(double) * NSTAT * NT * cells,
+                                              cudaMemcpyDeviceToHost, st)) != cudaSuccess) {
     return poison(c, e, "state copy");
+  }
   if (s->guide_hist && guided &&
       (e = cudaMemcpyAsync(s->guide_hist, c->d_hist, sizeof(float) * GUIDE_BINS * cells, cudaMemcpyDeviceToHost,
                            st)) != cudaSuccess)
@@ -726,6 +799,7 @@ mars_status get_state_impl(mars_cache* c, mars_cache_state* s, cudaStream_t st) 
                              cudaMemcpyDeviceToHost, st)) != cudaSuccess)
     return poison(c, e, "state copy");
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return poison(c, e, "state copy");
+  for (size_t k = 0; k < s32.size(); ++k) s->stats[k] = (double)s32[k];
   for (int64_t k = 0; k < cells * NT && !cnt.empty(); ++k) {
     const float4 r = cnt[2 * k], q = cnt[2 * k + 1];
     if (s->q_rr) { s->q_rr[3 * k] = r.x; s->q_rr[3 * k + 1] = r.y; s->q_rr[3 * k + 2] = r.z; }
@@ -762,9 +836,17 @@ mars_status set_state_impl(mars_cache* c, const mars_cache_state* s, cudaStream_
       return poison(c, e, "state copy");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return poison(c, e, "state copy");
   }
-  if (s->stats && (e = cudaMemcpyAsync(c->d_stats, s->stats, sizeof(double) * NSTAT * NT * cells,
-                                       cudaMemcpyHostToDevice, st)) != cudaSuccess)
+  std::vector<float> s32;
+  if (s->stats && c->fp32_stats) {
+    s32.resize((size_t)NSTAT * NT * cells);
+    for (size_t k = 0; k < s32.size(); ++k) s32[k] = (float)s->stats[k];
+    if ((e = cudaMemcpyAsync(c->d_stats32, s32.data(), sizeof(float) * s32.size(), cudaMemcpyHostToDevice, st)) !=
+        cudaSuccess)
+      return poison(c, e, "state copy");
+  } else if (s->stats && (e = cudaMemcpyAsync(c->d_stats, s->stats, sizeof(double) * NSTAT * NT * cells,
+                                              cudaMemcpyHostToDevice, st)) != cudaSuccess) {
     return poison(c, e, "state copy");
+  }
   if (s->guide_hist && guided &&
       (e = cudaMemcpyAsync(c->d_hist, s->guide_hist, sizeof(float) * GUIDE_BINS * cells, cudaMemcpyHostToDevice,
                            st)) != cudaSuccess)
@@ -772,6 +854,10 @@ mars_status set_state_impl(mars_cache* c, const mars_cache_state* s, cudaStream_
   if (s->guide_cdf && guided &&
       (e = cudaMemcpyAsync(c->d_cdf, s->guide_cdf, sizeof(float) * GUIDE_BINS * cells, cudaMemcpyHostToDevice, st)) !=
           cudaSuccess)
+    return poison(c, e, "state copy");
+  // a histogram or CDF from outside: the next update rebuilds every cell's CDF
+  if ((s->guide_hist || s->guide_cdf) && guided &&
+      (e = cudaMemsetAsync(c->d_guide_dirty, 1, (size_t)cells, st)) != cudaSuccess)
     return poison(c, e, "state copy");
   if (s->pixel_estimate &&
       (e = cudaMemcpy2DAsync(c->d_est, sizeof(float4), s->pixel_estimate, 3 * sizeof(float), 3 * sizeof(float),
@@ -855,20 +941,36 @@ mars_status mars_cache_get_launch(const mars_cache* c, mars_launch_config* out) 
   for (int k = 0; k < WAVE_KERNELS; ++k) {
     out->threads[k] = c->launch.threads[k];
     out->blocks_per_sm[k] = c->blocks_per_sm[k];
+    out->max_registers[k] = wave_variant_registers(k, c->launch.variant[k]);
   }
   return MARS_OK;
 }
 
-mars_status mars_cache_set_launch(mars_cache* c, const mars_launch_config* cfg) {
-  if (!c || !cfg) return set_error(MARS_ERR_INVALID_ARG, "null cache or config");
-  DeviceGuard g(c->device);
-  return apply_launch(c, cfg->threads, cfg->blocks_per_sm);
+static bool variant_of(int kernel, int regs, int* v) {
+  for (int k = 0; k < wave_variants(kernel); ++k)
+    if (wave_variant_registers(kernel, k) == regs) {
+      *v = k;
+      return true;
+    }
+  return false;
 }
 
-// Coordinate search over the launch shape of each wave kernel in turn (threads
-// per block x blocks per SM), timing the kernel's own CUDA events over
-// `repeats` renders of the given iteration without statistics, image
-// statistics or guide deposits, so the cache's state is left as it was.
+mars_status mars_cache_set_launch(mars_cache* c, const mars_launch_config* cfg) {
+  if (!c || !cfg) return set_error(MARS_ERR_INVALID_ARG, "null cache or config");
+  int var[WAVE_KERNELS];
+  for (int k = 0; k < WAVE_KERNELS; ++k)
+    if (!variant_of(k, cfg->max_registers[k], &var[k]))
+      return set_error(MARS_ERR_INVALID_ARG, "wave kernel %d: no variant capped at %d registers", k,
+                       cfg->max_registers[k]);
+  DeviceGuard g(c->device);
+  return apply_launch(c, cfg->threads, cfg->blocks_per_sm, var);
+}
+
+// Coordinate search over the launch shape of each wave kernel in turn (register
+// cap variant x threads per block x blocks per SM), timing the kernel's own
+// CUDA events over `repeats` renders of the given iteration without
+// statistics, image statistics or guide deposits, so the cache's state is left
+// as it was.
 mars_status mars_cache_autotune(mars_cache* c, const mars_iter_params* params, int32_t repeats,
                                 mars_launch_config* chosen, void* stream) {
   if (!c || !params) return set_error(MARS_ERR_INVALID_ARG, "null cache or params");
@@ -880,13 +982,14 @@ mars_status mars_cache_autotune(mars_cache* c, const mars_iter_params* params, i
   p.update_estimate = 0;
   p.image_on_host = 0;
   p.profile = 1;
-  int threads[WAVE_KERNELS], bps[WAVE_KERNELS];
+  int threads[WAVE_KERNELS], bps[WAVE_KERNELS], var[WAVE_KERNELS];
   for (int k = 0; k < WAVE_KERNELS; ++k) {
     threads[k] = c->launch.threads[k];
     bps[k] = c->blocks_per_sm[k];
+    var[k] = c->launch.variant[k];
   }
   auto time_of = [&](int k, double* ms) -> mars_status {
-    mars_status rc = apply_launch(c, threads, bps);
+    mars_status rc = apply_launch(c, threads, bps, var);
     if (rc != MARS_OK) return rc;
     double tot = 0.0;
     for (int r = 0; r <= repeats; ++r) {  // the first render warms up
@@ -902,33 +1005,40 @@ mars_status mars_cache_autotune(mars_cache* c, const mars_iter_params* params, i
   const int cand_threads[3] = {64, 128, 256};
   for (int k = 0; k < WAVE_KERNELS; ++k) {
     if (k == WK_SHADOW && !(c->techniques & MARS_TECH_NEE)) continue;
-    int best_t = threads[k], best_b = bps[k];
+    int best_t = threads[k], best_b = bps[k], best_v = var[k];
     double best = 1e300;
-    for (int ti = 0; ti < 3; ++ti) {
-      int occ[WAVE_KERNELS];
-      int tt[WAVE_KERNELS] = {threads[0], threads[1], threads[2], threads[3]};
-      tt[k] = cand_threads[ti];
-      if (wave_occupancy(tt, occ) != cudaSuccess) return set_error(MARS_ERR_CUDA, "occupancy query failed");
-      const int o = std::max(1, occ[k]);
-      const int cand_b[3] = {std::max(1, o / 2), o, 2 * o};
-      for (int bi = 0; bi < 3; ++bi) {
-        if (bi == 0 && cand_b[0] == o) continue;
-        threads[k] = cand_threads[ti];
-        bps[k] = std::min(64, cand_b[bi]);
-        double ms = 0.0;
-        const mars_status rc = time_of(k, &ms);
-        if (rc != MARS_OK) return rc;
-        if (ms < best) {
-          best = ms;
-          best_t = threads[k];
-          best_b = bps[k];
+    for (int v = 0; v < wave_variants(k); ++v) {
+      for (int ti = 0; ti < 3; ++ti) {
+        int occ[WAVE_KERNELS];
+        int tt[WAVE_KERNELS] = {threads[0], threads[1], threads[2], threads[3]};
+        int vv[WAVE_KERNELS] = {var[0], var[1], var[2], var[3]};
+        tt[k] = cand_threads[ti];
+        vv[k] = v;
+        if (wave_occupancy(tt, vv, occ) != cudaSuccess) return set_error(MARS_ERR_CUDA, "occupancy query failed");
+        const int o = std::max(1, occ[k]);
+        const int cand_b[3] = {std::max(1, o / 2), o, 2 * o};
+        for (int bi = 0; bi < 3; ++bi) {
+          if (bi == 0 && cand_b[0] == o) continue;
+          threads[k] = cand_threads[ti];
+          var[k] = v;
+          bps[k] = std::min(64, cand_b[bi]);
+          double ms = 0.0;
+          const mars_status rc = time_of(k, &ms);
+          if (rc != MARS_OK) return rc;
+          if (ms < best) {
+            best = ms;
+            best_t = threads[k];
+            best_b = bps[k];
+            best_v = var[k];
+          }
         }
       }
     }
     threads[k] = best_t;
     bps[k] = best_b;
+    var[k] = best_v;
   }
-  const mars_status rc = apply_launch(c, threads, bps);
+  const mars_status rc = apply_launch(c, threads, bps, var);
   if (rc != MARS_OK) return rc;
   if (chosen) return mars_cache_get_launch(c, chosen);
   return MARS_OK;

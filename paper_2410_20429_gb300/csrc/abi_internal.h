@@ -67,8 +67,11 @@ struct mars_cache {
   mars::DevCache dc{};
   float4* d_cnt = nullptr;
   double* d_stats = nullptr;
+  float* d_stats32 = nullptr;  // float32 statistics variant (then d_stats is null)
+  bool fp32_stats = false;
   float* d_hist = nullptr;
   float* d_cdf = nullptr;
+  uint8_t* d_guide_dirty = nullptr;
   float4* d_est = nullptr;
   float4* d_run = nullptr;
   float4* d_img = nullptr;
@@ -86,6 +89,12 @@ struct mars_cache {
   std::vector<cudaEvent_t> events;  // profiling events, grown on demand
   mars::WaveLaunch launch{};        // launch shape of the per-wave kernels
   int blocks_per_sm[mars::WAVE_KERNELS] = {0, 0, 0, 0};  // 0: occupancy maximum
+  // wave sizes of the last single-tile iteration (rays per depth wave, NEE
+  // shadow rays to trace per wave) and its pixel count: the next iteration sizes the
+  // grid of each small wave from them
+  uint64_t last_count[mars::MAXD + 2] = {};
+  uint64_t last_slcount[mars::MAXD + 2] = {};
+  int64_t last_pixels = 0;
 };
 
 namespace mars {
@@ -98,5 +107,6 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
 mars_status update_counts_impl(mars_cache* c, cudaStream_t st);
 uint64_t cache_footprint(int64_t cells, int64_t pixels, int max_depth, int techniques, uint64_t cap);
 uint64_t default_capacity(int64_t pixels, int max_depth);
-mars_status apply_launch(mars_cache* c, const int threads[WAVE_KERNELS], const int blocks_per_sm[WAVE_KERNELS]);
+mars_status apply_launch(mars_cache* c, const int threads[WAVE_KERNELS], const int blocks_per_sm[WAVE_KERNELS],
+                         const int variant[WAVE_KERNELS]);
 }  // namespace mars

@@ -59,23 +59,29 @@ struct DevScene {
 //   R0 = (origin xyz, pixel)            R1 = (direction xyz, A = beta_t p_t)
 //   R2 = (T at the hit xyz, S_ind)      R3 = (f|cos|/p xyz, NEE weight factor)
 //   R4 = (lineage lo, lineage hi, parent cell, 1 / sum beta_k p_k)
-//   H  = (t, primitive: -1 missed, -2 not traced)
-//   V0 = (E xyz, flags)                 V1 = (G xyz, first child)
-//   V2 = (clamp limit xyz, cell)        V3 = (beta BSDF, NEE, guided, first shadow ray)
+//   H  = (t, primitive: -1 missed, -2 not traced) from the trace kernel; the
+//        shade kernel then overwrites it with (first child, first shadow ray)
+//        as slot indices, the first two addresses the reverse pass needs
+//   V0 = (E xyz, flags)                 V1 = (G xyz, -)
+//   V2 = (clamp limit xyz, cell)        V3 = (beta BSDF, NEE, guided, -)
 //   V4 = (Le luminance, 1/S_beta, parent cell, bin)
 //   S  = (sample value xyz, cost)
 // NEE shadow rays of wave d occupy [sbase[d], sbase[d] + scount[d]) of a second
 // arena: SH0 = (origin xyz, tmax; < 0: nothing to trace), SH1 = (direction, -),
 // SH2 = (sample value if visible, -), zeroed by the shadow kernel when occluded.
+// Only samples with a nonzero value need a ray: their slots are listed in
+// SL[sbase[d], sbase[d] + slcount[d]) (a compacted work list), and SH0/SH1 are
+// written for them alone.
 constexpr int NR = 5, NV = 5, NSH = 3;
 constexpr int SLOT_BYTES = (NR + NV + 1) * 16 + 8;  // per ray slot
-constexpr int SHADOW_BYTES = NSH * 16;              // per shadow-ray slot
+constexpr int SHADOW_BYTES = NSH * 16 + 4;          // per shadow-ray slot
 struct Arena {
   float4* R[NR];
   float2* H;
   float4* V[NV];
   float4* S;
   float4* SH[NSH];
+  unsigned int* SL;
   uint64_t cap;   // ray slots
   uint64_t scap;  // shadow-ray slots
 };
@@ -90,7 +96,9 @@ struct DevCounters {
   unsigned long long count[MAXD + 2];
   unsigned long long sbase[MAXD + 2];   // shadow rays of wave d
   unsigned long long scount[MAXD + 2];
+  unsigned long long slcount[MAXD + 2];  // shadow rays of wave d that need tracing
   unsigned long long shadow_entries;     // shadow rays of committed tiles
+  unsigned long long shadow_traced;      // listed (traced) shadow rays of committed tiles
   unsigned int overflow;       // this tile overflowed the arena
   unsigned int any_overflow;   // some tile of this iteration overflowed
   unsigned long long demand;   // rays the tile needed (may exceed the arena)
@@ -99,6 +107,7 @@ struct DevCounters {
   double sum_beta[NT];
   double chsum[3];             // sum over pixels of the running mean (image stats)
   double vi_sum;
+  float chsum32[3], vi_sum32;  // the same sums in float32 (float32 statistics)
   double VI, CI;               // results of the last image-stats pass
 };
 
@@ -106,9 +115,11 @@ struct DevCache {
   int grid_n, n_cells, techniques, max_depth, bits;
   int n_pixels;
   float4* cnt;          // [cells][3][2]: (q_rr xyz, valid), (q_s xyz, 0)
-  double* stats;        // [cells][3][8]
+  double* stats;        // [cells][3][8] (float64 statistics)
+  float* stats32;       // [cells][3][8] (float32 statistics; then stats is null)
   float* guide_hist;    // [cells][256]
   float* guide_cdf;     // [cells][256]
+  uint8_t* guide_dirty; // [cells] 1: deposits since the last CDF rebuild
   float4* est;          // [pixels] pixel estimate
   float4* run_sum;      // [pixels]
   float4* img;          // [pixels] this iteration's image
@@ -129,14 +140,19 @@ struct IterArgs {
 enum { WK_TRACE = 0, WK_SHADE = 1, WK_SHADOW = 2, WK_REVERSE = 3, WAVE_KERNELS = 4 };
 struct WaveLaunch {
   int threads[WAVE_KERNELS];
-  int grid[WAVE_KERNELS];
+  int variant[WAVE_KERNELS];               // register-cap variant (wave_variant_registers)
+  int grid[WAVE_KERNELS];                  // persistent grid: SMs x resident blocks
+  int wave_grid[WAVE_KERNELS][MAXD + 2];   // grid of wave d (<= grid; 0 = grid)
 };
 
 // launch wrappers (render.cu)
 cudaError_t launch_tile(const DevScene& s, const DevCache& c, const Arena& a, const IterArgs& it,
                         const WaveLaunch& L, cudaStream_t st, cudaEvent_t* ev);
-// resident blocks per SM of each wave kernel at the given block sizes
-cudaError_t wave_occupancy(const int threads[WAVE_KERNELS], int blocks_per_sm[WAVE_KERNELS]);
+// resident blocks per SM of each wave kernel at the given block sizes and variants
+cudaError_t wave_occupancy(const int threads[WAVE_KERNELS], const int variant[WAVE_KERNELS],
+                           int blocks_per_sm[WAVE_KERNELS]);
+int wave_variants(int kernel);                    // compiled register-cap variants of a wave kernel
+int wave_variant_registers(int kernel, int v);    // its register cap (0: the compiler's choice)
 bool wave_threads_ok(int threads);
 int tile_launches(int max_depth, int techniques);  // kernels launch_tile issues
 // image statistics (stats.cu)

@@ -111,6 +111,7 @@ __global__ void k_tile_init(DevCounters* ctr, unsigned long long n0) {
     ctr->count[t] = (t == 1) ? n0 : 0ull;
     ctr->sbase[t] = 0;
     ctr->scount[t] = 0;
+    ctr->slcount[t] = 0;
   }
   if (t == 0) {
     ctr->overflow = 0;
@@ -127,20 +128,23 @@ __global__ void k_tile_finish(DevCounters* ctr, unsigned int* tile_status, int s
   }
   ctr->demand = dem;
   if (!ctr->overflow) {
-    unsigned long long tot = 0, sh = 0;
+    unsigned long long tot = 0, sh = 0, sl = 0;
     for (int d = 1; d <= D; ++d) {
       tot += ctr->count[d];
       sh += ctr->scount[d];
+      sl += ctr->slcount[d];
     }
     ctr->entries += tot;
     ctr->shadow_entries += sh;
+    ctr->shadow_traced += sl;
   }
   tile_status[slot] = ctr->overflow;
   if (ctr->overflow) ctr->any_overflow = 1;
 }
 
 // ------------------------------------------------------------------ trace
-__global__ void __launch_bounds__(MAX_WAVE_THREADS) k_trace(const DevScene s, const DevCache c, const Arena a,
+template <int MINB>
+__global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_trace(const DevScene s, const DevCache c, const Arena a,
                                                          const IterArgs it, const int d) {
   const DevCounters* ctr = c.ctr;
   // after an overflow some slots of this wave were never written: stop, the
@@ -181,7 +185,8 @@ struct ShadeWarpCtx {
   int incl_sh[32];
 };
 
-__global__ void __launch_bounds__(MAX_WAVE_THREADS) k_shade(const DevScene s, const DevCache c, const Arena a,
+template <int MINB>
+__global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_shade(const DevScene s, const DevCache c, const Arena a,
                                                          const IterArgs it, const int d) {
   DevCounters* ctr = c.ctr;
   if (ctr->overflow) return;
@@ -338,9 +343,13 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS) k_shade(const DevScene s, co
       flags |= (uint32_t)gam[0] | ((uint32_t)gam[1] << 8) | ((uint32_t)gam[2] << 16);
       a.V[0][i] = f4(E, __uint_as_float(flags));
       if (flags & F_EST) {
-        a.V[1][i] = f4(G, __uint_as_float((uint32_t)(fits ? first : 0ull)));
+        a.V[1][i] = f4(G, 0.0f);
         a.V[2][i] = f4(climit, __uint_as_float((uint32_t)cell));
-        a.V[3][i] = make_float4(beta[0], beta[1], beta[2], __uint_as_float((uint32_t)(fits ? sfirst : 0ull)));
+        a.V[3][i] = make_float4(beta[0], beta[1], beta[2], 0.0f);
+        // the hit record is dead from here on: keep the first child and first
+        // shadow-ray slots in it for the reverse pass
+        a.H[i] = make_float2(__uint_as_float((uint32_t)(fits ? first : 0ull)),
+                             __uint_as_float((uint32_t)(fits ? sfirst : 0ull)));
       }
       if (on_g && it.collect && !camera && (flags & F_TRACED))
         a.V[4][i] = make_float4(Le_lum, invSb, __uint_as_float(parent_cell), __int_as_float(guide_bin(dir)));
@@ -379,10 +388,13 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS) k_shade(const DevScene s, co
     for (int k0 = 0; k0 < as.total; k0 += 32) {
       const int k = k0 + lane;
       const unsigned long long j = sbase + as.base + (unsigned long long)k;
+      bool trace = false;
+      f3 xo = mk3(0.f, 0.f, 0.f), wi = mk3(0.f, 0.f, 1.f);
+      float tmax = -1.0f;
       if (k < as.total && j < a.scap) {
         const int L = owner_lane(ctx->incl_sh, k);
         const int sidx = k - (L > 0 ? ctx->incl_sh[L - 1] : 0);
-        const f3 xo = mk3(cx[C_XO * 32 + L], cx[(C_XO + 1) * 32 + L], cx[(C_XO + 2) * 32 + L]);
+        xo = mk3(cx[C_XO * 32 + L], cx[(C_XO + 1) * 32 + L], cx[(C_XO + 2) * 32 + L]);
         const f3 vns = mk3(cx[C_NS * 32 + L], cx[(C_NS + 1) * 32 + L], cx[(C_NS + 2) * 32 + L]);
         const f3 wol = mk3(cx[C_WO * 32 + L], cx[(C_WO + 1) * 32 + L], cx[(C_WO + 2) * 32 + L]);
         Mat m;
@@ -405,7 +417,7 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS) k_shade(const DevScene s, co
         const f3 y = xyz(l0) + (xyz(l1) * u.y + xyz(l2) * u.z);
         const f3 dv = y - xo;
         const float dist = sqrtf(dot(dv, dv));
-        const f3 wi = dv * (1.0f / dist);
+        wi = dv * (1.0f / dist);
         const float pn = nee_pdf(s, l, xo, y, wi);
         const float ci = dot(vns, wi);
         f3 v = mk3(0.f, 0.f, 0.f);
@@ -421,10 +433,25 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS) k_shade(const DevScene s, co
             v = mk3(fc.x * l4.x / pn * wgt, fc.y * l4.y / pn * wgt, fc.z * l4.z / pn * wgt);
           }
         }
-        // tmax < 0 marks a sample that needs no shadow ray (its value is 0)
-        a.SH[0][j] = f4(xo, nonzero(v) ? dist - s.eps : -1.0f);
-        a.SH[1][j] = f4(wi, 0.0f);
         a.SH[2][j] = f4(v, 0.0f);
+        // a sample of value 0 needs no shadow ray
+        trace = nonzero(v);
+        tmax = dist - s.eps;
+      }
+      // compacted list of the shadow rays to trace: one atomic per warp
+      const unsigned need = __ballot_sync(FULL, trace);
+      if (need) {
+        unsigned long long lb = 0;
+        if (lane == 0) lb = atomicAdd(&ctr->slcount[d], (unsigned long long)__popc(need));
+        lb = __shfl_sync(FULL, lb, 0);
+        if (trace) {
+          const unsigned long long pos = sbase + lb + (unsigned long long)__popc(need & ((1u << lane) - 1u));
+          if (pos < a.scap) {
+            a.SL[pos] = (unsigned int)j;
+            a.SH[0][j] = f4(xo, tmax);
+            a.SH[1][j] = f4(wi, 0.0f);
+          }
+        }
       }
     }
 
@@ -504,15 +531,18 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS) k_shade(const DevScene s, co
 }
 
 // ----------------------------------------------------------------- shadow
-__global__ void __launch_bounds__(MAX_WAVE_THREADS) k_shadow(const DevScene s, const DevCache c, const Arena a,
+template <int MINB>
+__global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_shadow(const DevScene s, const DevCache c, const Arena a,
                                                            const int d) {
   const DevCounters* ctr = c.ctr;
   if (ctr->overflow) return;
-  const unsigned long long sb = ctr->sbase[d], sc = ctr->scount[d];
-  const unsigned long long n = sc < a.scap - sb ? sc : a.scap - sb;
+  // the listed shadow rays of wave d: SL[sbase, sbase + slcount), slot indices
+  // into the wave's shadow region (at most scount of them)
+  const unsigned long long sb = ctr->sbase[d], sl = ctr->slcount[d];
+  const unsigned long long n = sl < a.scap - sb ? sl : a.scap - sb;
   for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < n;
        k += gridDim.x * (unsigned long long)blockDim.x) {
-    const unsigned long long j = sb + k;
+    const unsigned long long j = a.SL[sb + k];
     const float4 s0 = a.SH[0][j];
     if (!(s0.w > 0.0f)) continue;
     const float4 s1 = a.SH[1][j];
@@ -531,7 +561,8 @@ __device__ __forceinline__ float seg_scan(float v, int lane, int start) {
   return v;
 }
 
-__global__ void __launch_bounds__(MAX_WAVE_THREADS) k_reverse(const DevScene s, const DevCache c, const Arena a,
+template <int MINB>
+__global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_reverse(const DevScene s, const DevCache c, const Arena a,
                                                              const IterArgs it, const int d) {
   DevCounters* ctr = c.ctr;
   if (ctr->overflow) return;  // the tile is re-rendered; commit nothing
@@ -557,26 +588,41 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS) k_reverse(const DevScene s, 
       for (int k = 0; k < NSTAT; ++k) st[t][k] = 0.0f;
     float bt[NT] = {0.f, 0.f, 0.f};
     if (active) {
+      // one round trip for the flags and the first child / shadow-ray slots,
+      // then every other load of the vertex is issued before any is used
       const float4 v0 = a.V[0][i];
+      const float2 fs = a.H[i];
       E = xyz(v0);
       flags = __float_as_uint(v0.w);
+      const bool guide_dep = on_g && collect && d >= 2 && (flags & F_TRACED);
+      float4 v4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (guide_dep) v4 = a.V[4][i];
       if (flags & F_EST) {
-        const float4 v1 = a.V[1][i], v2 = a.V[2][i], v3 = a.V[3][i];
         const int gB = flags & 0xff, gN = (flags >> 8) & 0xff, gG = (flags >> 16) & 0xff;
+        const int ne = gB + gG;
+        const unsigned long long first = __float_as_uint(fs.x), sf = __float_as_uint(fs.y);
+        const float4 v1 = a.V[1][i], v2 = a.V[2][i], v3 = a.V[3][i];
+        float4 pn[4], pe[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          pn[q] = q < gN ? a.SH[2][sf + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+          pe[q] = q < ne ? a.S[first + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         bt[0] = v3.x; bt[1] = v3.y; bt[2] = v3.z;
         const f3 climit = xyz(v2);
         key = __float_as_uint(v2.w);
         if (gN > 0) {
-          const unsigned long long sf = __float_as_uint(v3.w);
           f3 sum = mk3(0.f, 0.f, 0.f);
           for (int k = 0; k < gN; k += 4) {
-            float4 vv[4];
+            if (k > 0) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) vv[q] = k + q < gN ? a.SH[2][sf + k + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+              for (int q = 0; q < 4; ++q)
+                pn[q] = k + q < gN ? a.SH[2][sf + k + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
               if (k + q >= gN) break;
-              const f3 v = xyz(vv[q]);
+              const f3 v = xyz(pn[q]);
               sum = sum + v;
               const f3 vc = fmin3(v, climit);
               st[1][1] += vc.x; st[1][2] += vc.y; st[1][3] += vc.z;
@@ -588,16 +634,15 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS) k_reverse(const DevScene s, 
           st[1][0] = (float)gN;
           st[1][7] = (float)gN;
         }
-        const unsigned long long first = __float_as_uint(v1.w);
-        const int ne = gB + gG;
         for (int k = 0; k < ne; k += 4) {
-          float4 sv4[4];
+          if (k > 0) {
 #pragma unroll
-          for (int q = 0; q < 4; ++q) sv4[q] = k + q < ne ? a.S[first + k + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int q = 0; q < 4; ++q) pe[q] = k + q < ne ? a.S[first + k + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             if (k + q >= ne) break;
-            const float4 sv = sv4[q];
+            const float4 sv = pe[q];
             const int t = k + q < gB ? 0 : 2;
             const float b = bt[t];
             Lr = Lr + mk3(sv.x / b, sv.y / b, sv.z / b);
@@ -619,11 +664,13 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS) k_reverse(const DevScene s, 
       const uint32_t cost = 1u + csub;
       a.S[i] = f4(E, __uint_as_float(cost));
       if (d == 1) c.img[it.tile_begin + li] = f4(E, 0.0f);
-      if (on_g && collect && d >= 2 && (flags & F_TRACED)) {
-        const float4 v4 = a.V[4][i];
+      if (guide_dep) {
         const float wdep = (v4.x + lum(Lr)) * v4.y;
-        if (wdep > 0.0f)
-          atomicAdd(c.guide_hist + (size_t)__float_as_uint(v4.z) * GUIDE_BINS + __float_as_int(v4.w), wdep);
+        if (wdep > 0.0f) {
+          const uint32_t pc = __float_as_uint(v4.z);
+          atomicAdd(c.guide_hist + (size_t)pc * GUIDE_BINS + __float_as_int(v4.w), wdep);
+          c.guide_dirty[pc] = 1;
+        }
       }
     }
 
@@ -672,9 +719,15 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS) k_reverse(const DevScene s, 
             for (int k = 0; k < NSTAT; ++k) st[t][k] = seg_scan(st[t][k], lane, start);
           }
           if (tail && key != 0xffffffffu && st[t][0] > 0.0f) {
-            double* dst = c.stats + ((size_t)key * NT + t) * NSTAT;
+            if (c.stats32) {
+              float4* dst = reinterpret_cast<float4*>(c.stats32 + ((size_t)key * NT + t) * NSTAT);
+              atomicAdd(dst, make_float4(st[t][0], st[t][1], st[t][2], st[t][3]));
+              atomicAdd(dst + 1, make_float4(st[t][4], st[t][5], st[t][6], st[t][7]));
+            } else {
+              double* dst = c.stats + ((size_t)key * NT + t) * NSTAT;
 #pragma unroll
-            for (int k = 0; k < NSTAT; ++k) atomicAdd(dst + k, (double)st[t][k]);
+              for (int k = 0; k < NSTAT; ++k) atomicAdd(dst + k, (double)st[t][k]);
+            }
           }
         }
       }
@@ -682,22 +735,43 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS) k_reverse(const DevScene s, 
   }
 }
 
-}  // namespace
-
 size_t shade_smem(int threads) { return (size_t)(threads / 32) * sizeof(ShadeWarpCtx); }
 
-cudaError_t wave_occupancy(const int threads[WAVE_KERNELS], int blocks_per_sm[WAVE_KERNELS]) {
+// Register-cap variants of every wave kernel: variant v is compiled with
+// __launch_bounds__(256, MINB) for MINB = 1 (the compiler's choice), or a cap
+// that lets more blocks share an SM (shade and reverse: 80 and 64 registers;
+// trace and shadow: 40 registers), trading spills for occupancy.
+using TraceFn = void (*)(const DevScene, const DevCache, const Arena, const IterArgs, const int);
+using ShadowFn = void (*)(const DevScene, const DevCache, const Arena, const int);
+TraceFn trace_fn(int v) { return v == 1 ? k_trace<6> : k_trace<1>; }
+TraceFn shade_fn(int v) { return v == 2 ? k_shade<4> : (v == 1 ? k_shade<3> : k_shade<1>); }
+ShadowFn shadow_fn(int v) { return v == 1 ? k_shadow<6> : k_shadow<1>; }
+TraceFn reverse_fn(int v) { return v == 2 ? k_reverse<4> : (v == 1 ? k_reverse<3> : k_reverse<1>); }
+
+}  // namespace
+
+int wave_variants(int kernel) { return (kernel == WK_SHADE || kernel == WK_REVERSE) ? 3 : 2; }
+int wave_variant_registers(int kernel, int v) {
+  if (v == 0) return 0;
+  if (kernel == WK_SHADE || kernel == WK_REVERSE) return v == 1 ? 80 : 64;
+  return 40;
+}
+
+cudaError_t wave_occupancy(const int threads[WAVE_KERNELS], const int variant[WAVE_KERNELS],
+                           int blocks_per_sm[WAVE_KERNELS]) {
   cudaError_t e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[WK_TRACE], k_trace, threads[WK_TRACE], 0)) !=
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[WK_TRACE], trace_fn(variant[WK_TRACE]),
+                                                         threads[WK_TRACE], 0)) != cudaSuccess)
+    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[WK_SHADE], shade_fn(variant[WK_SHADE]),
+                                                         threads[WK_SHADE], shade_smem(threads[WK_SHADE]))) !=
       cudaSuccess)
     return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[WK_SHADE], k_shade, threads[WK_SHADE],
-                                                         shade_smem(threads[WK_SHADE]))) != cudaSuccess)
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[WK_SHADOW], shadow_fn(variant[WK_SHADOW]),
+                                                         threads[WK_SHADOW], 0)) != cudaSuccess)
     return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[WK_SHADOW], k_shadow, threads[WK_SHADOW],
-                                                         0)) != cudaSuccess)
-    return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[WK_REVERSE], k_reverse, threads[WK_REVERSE], 0);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[WK_REVERSE], reverse_fn(variant[WK_REVERSE]),
+                                                       threads[WK_REVERSE], 0);
 }
 
 bool wave_threads_ok(int threads) { return threads >= 32 && threads <= MAX_WAVE_THREADS && threads % 32 == 0; }
@@ -708,21 +782,21 @@ cudaError_t launch_tile(const DevScene& s, const DevCache& c, const Arena& a, co
   k_tile_init<<<1, 32, 0, st>>>(c.ctr, n0);
   const int D = c.max_depth;
   const int tT = L.threads[WK_TRACE], tS = L.threads[WK_SHADE], tH = L.threads[WK_SHADOW], tR = L.threads[WK_REVERSE];
-  const int gT = L.grid[WK_TRACE], gS = L.grid[WK_SHADE], gH = L.grid[WK_SHADOW], gR = L.grid[WK_REVERSE];
+  auto G = [&](int k, int d) { return L.wave_grid[k][d] > 0 ? L.wave_grid[k][d] : L.grid[k]; };
   const size_t smS = shade_smem(tS);
   // ev (optional, 4 D + 1 events): ev[0] first; after wave d's trace, shade and
   // shadow kernels ev[3(d-1) + 1..3]; after the k-th reverse kernel ev[3 D + k]
   if (ev) cudaEventRecord(ev[0], st);
   for (int d = 1; d <= D; ++d) {
-    k_trace<<<gT, tT, 0, st>>>(s, c, a, it, d);
+    trace_fn(L.variant[WK_TRACE])<<<G(WK_TRACE, d), tT, 0, st>>>(s, c, a, it, d);
     if (ev) cudaEventRecord(ev[3 * (d - 1) + 1], st);
-    k_shade<<<gS, tS, smS, st>>>(s, c, a, it, d);
+    shade_fn(L.variant[WK_SHADE])<<<G(WK_SHADE, d), tS, smS, st>>>(s, c, a, it, d);
     if (ev) cudaEventRecord(ev[3 * (d - 1) + 2], st);
-    if (d <= D - 1 && (c.techniques & MARS_TECH_NEE)) k_shadow<<<gH, tH, 0, st>>>(s, c, a, d);
+    if (d <= D - 1 && (c.techniques & MARS_TECH_NEE)) shadow_fn(L.variant[WK_SHADOW])<<<G(WK_SHADOW, d), tH, 0, st>>>(s, c, a, d);
     if (ev) cudaEventRecord(ev[3 * (d - 1) + 3], st);
   }
   for (int d = D; d >= 1; --d) {
-    k_reverse<<<gR, tR, 0, st>>>(s, c, a, it, d);
+    reverse_fn(L.variant[WK_REVERSE])<<<G(WK_REVERSE, d), tR, 0, st>>>(s, c, a, it, d);
     if (ev) cudaEventRecord(ev[3 * D + (D - d + 1)], st);
   }
   k_tile_finish<<<1, 32, 0, st>>>(c.ctr, c.tile_status, it.tile_slot, D);

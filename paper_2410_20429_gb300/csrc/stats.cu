@@ -21,23 +21,34 @@ namespace {
 
 constexpr int IMG_THREADS = 256;
 
-__device__ __forceinline__ double block_sum(double v, double* sh) {
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* sh) {
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   __syncthreads();
   if (l == 0) sh[w] = v;
   __syncthreads();
-  double r = 0.0;
+  T r = 0;
   if (threadIdx.x == 0)
     for (int k = 0; k < (int)(blockDim.x >> 5); ++k) r += sh[k];
   return r;  // valid in thread 0
 }
 
+// image sums in the statistics' precision: float64, or float32 for the
+// float32-statistics variant
+template <typename T>
+__device__ __forceinline__ void add_sum(double* d64, float* d32, T v);
+template <>
+__device__ __forceinline__ void add_sum<double>(double* d64, float*, double v) { atomicAdd(d64, v); }
+template <>
+__device__ __forceinline__ void add_sum<float>(double*, float* d32, float v) { atomicAdd(d32, v); }
+
+template <typename T>
 __global__ void __launch_bounds__(IMG_THREADS) k_img_accum(DevCache c, int npix, int n_prev, float* out) {
-  __shared__ double sh[IMG_THREADS / 32];
+  __shared__ T sh[IMG_THREADS / 32];
   if (c.ctr->any_overflow) return;
   const float inv = 1.0f / (float)(n_prev + 1);
-  double m0 = 0.0, m1 = 0.0, m2 = 0.0;
+  T m0 = 0, m1 = 0, m2 = 0;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) {
     const float4 I = c.img[p];
     float4 rs = c.run_sum[p];
@@ -48,28 +59,31 @@ __global__ void __launch_bounds__(IMG_THREADS) k_img_accum(DevCache c, int npix,
       out[3 * p + 1] = I.y;
       out[3 * p + 2] = I.z;
     }
-    m0 += (double)(rs.x * inv);
-    m1 += (double)(rs.y * inv);
-    m2 += (double)(rs.z * inv);
+    m0 += (T)(rs.x * inv);
+    m1 += (T)(rs.y * inv);
+    m2 += (T)(rs.z * inv);
   }
-  m0 = block_sum(m0, sh);
-  m1 = block_sum(m1, sh);
-  m2 = block_sum(m2, sh);
+  m0 = block_sum<T>(m0, sh);
+  m1 = block_sum<T>(m1, sh);
+  m2 = block_sum<T>(m2, sh);
   if (threadIdx.x == 0) {
-    atomicAdd(&c.ctr->chsum[0], m0);
-    atomicAdd(&c.ctr->chsum[1], m1);
-    atomicAdd(&c.ctr->chsum[2], m2);
+    add_sum<T>(&c.ctr->chsum[0], &c.ctr->chsum32[0], m0);
+    add_sum<T>(&c.ctr->chsum[1], &c.ctr->chsum32[1], m1);
+    add_sum<T>(&c.ctr->chsum[2], &c.ctr->chsum32[2], m2);
   }
 }
 
+template <typename T>
 __global__ void __launch_bounds__(IMG_THREADS) k_img_est(DevCache c, int W, int H, int n_prev, float outlier) {
-  __shared__ double sh[IMG_THREADS / 32];
+  __shared__ T sh[IMG_THREADS / 32];
   if (c.ctr->any_overflow) return;
   const int npix = W * H;
   const float inv = 1.0f / (float)(n_prev + 1);
-  const float fl0 = 1e-3f * (float)(c.ctr->chsum[0] / npix), fl1 = 1e-3f * (float)(c.ctr->chsum[1] / npix),
-              fl2 = 1e-3f * (float)(c.ctr->chsum[2] / npix);
-  double vi = 0.0;
+  const bool f32 = c.stats32 != nullptr;
+  const float fl0 = 1e-3f * (f32 ? c.ctr->chsum32[0] / (float)npix : (float)(c.ctr->chsum[0] / npix));
+  const float fl1 = 1e-3f * (f32 ? c.ctr->chsum32[1] / (float)npix : (float)(c.ctr->chsum[1] / npix));
+  const float fl2 = 1e-3f * (f32 ? c.ctr->chsum32[2] / (float)npix : (float)(c.ctr->chsum[2] / npix));
+  T vi = 0;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) {
     const int x = p % W, y = p / W;
     float s0 = 0.f, s1 = 0.f, s2 = 0.f;
@@ -92,10 +106,10 @@ __global__ void __launch_bounds__(IMG_THREADS) k_img_est(DevCache c, int W, int 
     const float r0 = (fminf(I.x, outlier * e0) - e0) / e0;
     const float r1 = (fminf(I.y, outlier * e1) - e1) / e1;
     const float r2 = (fminf(I.z, outlier * e2) - e2) / e2;
-    vi += (double)(r0 * r0) + (double)(r1 * r1) + (double)(r2 * r2);
+    vi += (T)(r0 * r0) + (T)(r1 * r1) + (T)(r2 * r2);
   }
-  vi = block_sum(vi, sh);
-  if (threadIdx.x == 0) atomicAdd(&c.ctr->vi_sum, vi);
+  vi = block_sum<T>(vi, sh);
+  if (threadIdx.x == 0) add_sum<T>(&c.ctr->vi_sum, &c.ctr->vi_sum32, vi);
 }
 
 __global__ void __launch_bounds__(IMG_THREADS) k_img_copy(DevCache c, int npix, float* out) {
@@ -110,8 +124,13 @@ __global__ void __launch_bounds__(IMG_THREADS) k_img_copy(DevCache c, int npix, 
 
 __global__ void k_img_final(DevCache c, int npix) {
   if (threadIdx.x != 0 || c.ctr->any_overflow) return;
-  c.ctr->VI = c.ctr->vi_sum / (3.0 * (double)npix);
-  c.ctr->CI = (double)c.ctr->rays / (double)npix;
+  if (c.stats32) {
+    c.ctr->VI = (double)(c.ctr->vi_sum32 / (3.0f * (float)npix));
+    c.ctr->CI = (double)((float)c.ctr->rays / (float)npix);
+  } else {
+    c.ctr->VI = c.ctr->vi_sum / (3.0 * (double)npix);
+    c.ctr->CI = (double)c.ctr->rays / (double)npix;
+  }
 }
 
 __global__ void k_update_counts(DevCache c) {
@@ -149,13 +168,48 @@ __global__ void k_update_counts(DevCache c) {
   s2[3] = z;
 }
 
+// the same update with float32 statistics and arithmetic (precision study)
+__global__ void k_update_counts32(DevCache c) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= c.n_cells * NT) return;
+  const int t = idx % NT;
+  float4* s4 = reinterpret_cast<float4*>(c.stats32 + (size_t)idx * NSTAT);
+  const float4 a = s4[0];
+  if (a.x == 0.0f) return;
+  const float4 b = s4[1];
+  const float VI = (float)c.ctr->VI, CI = (float)c.ctr->CI;
+  const float n = a.x, cost = b.w;
+  if (((c.techniques >> t) & 1) && VI > 1e-12f && n >= 2.0f && cost > 0.0f) {
+    const float inv_n = 1.0f / n;
+    const float r = CI * n / (cost * VI);
+    const float s1[3] = {a.y, a.z, a.w}, s2v[3] = {b.x, b.y, b.z};
+    float qr[3], qs[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      const float m1 = s1[ch] * inv_n, m2 = s2v[ch] * inv_n;
+      float var = m2 - m1 * m1;
+      if (var < 0.0f) var = 0.0f;
+      qr[ch] = sqrtf(r * m2);
+      qs[ch] = sqrtf(r * var);
+    }
+    c.cnt[2 * idx] = make_float4(qr[0], qr[1], qr[2], 1.0f);
+    c.cnt[2 * idx + 1] = make_float4(qs[0], qs[1], qs[2], 0.0f);
+  }
+  s4[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+  s4[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
 // one warp per cell: P_b = 0.9 h_b / H + 0.1 / 256 (uniform when H = 0), then an
 // inclusive prefix sum in float64.  Lane l holds bins 8 l .. 8 l + 7 (two float4
-// loads and stores); one float64 reciprocal per cell.
+// loads and stores); one float64 reciprocal per cell.  Only cells that received
+// deposits since their last rebuild are rebuilt: the others' CDF already is
+// the one their histogram gives.
 __global__ void k_guide_update(DevCache c) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (warp >= c.n_cells) return;
+  if (warp >= c.n_cells || !c.guide_dirty[warp]) return;
+  __syncwarp();
+  if (lane == 0) c.guide_dirty[warp] = 0;
   const float4* h = reinterpret_cast<const float4*>(c.guide_hist + (size_t)warp * GUIDE_BINS) + 2 * lane;
   float4* cdf = reinterpret_cast<float4*>(c.guide_cdf + (size_t)warp * GUIDE_BINS) + 2 * lane;
   const float4 h0 = h[0], h1 = h[1];
@@ -197,8 +251,13 @@ cudaError_t launch_image_stats(const DevCache& c, int width, int height, int n_p
   const int npix = width * height;
   int blocks = (npix + IMG_THREADS - 1) / IMG_THREADS;
   if (blocks > 4096) blocks = 4096;
-  k_img_accum<<<blocks, IMG_THREADS, 0, st>>>(c, npix, n_prev, image_out_dev);
-  k_img_est<<<blocks, IMG_THREADS, 0, st>>>(c, width, height, n_prev, outlier);
+  if (c.stats32) {
+    k_img_accum<float><<<blocks, IMG_THREADS, 0, st>>>(c, npix, n_prev, image_out_dev);
+    k_img_est<float><<<blocks, IMG_THREADS, 0, st>>>(c, width, height, n_prev, outlier);
+  } else {
+    k_img_accum<double><<<blocks, IMG_THREADS, 0, st>>>(c, npix, n_prev, image_out_dev);
+    k_img_est<double><<<blocks, IMG_THREADS, 0, st>>>(c, width, height, n_prev, outlier);
+  }
   k_img_final<<<1, 32, 0, st>>>(c, npix);
   return cudaGetLastError();
 }
@@ -213,7 +272,10 @@ cudaError_t launch_image_copy(const DevCache& c, int npix, float* out, cudaStrea
 cudaError_t launch_update(const DevCache& c, int num_sms, cudaStream_t st) {
   (void)num_sms;
   const int n = c.n_cells * NT;
-  k_update_counts<<<(n + 255) / 256, 256, 0, st>>>(c);
+  if (c.stats32)
+    k_update_counts32<<<(n + 255) / 256, 256, 0, st>>>(c);
+  else
+    k_update_counts<<<(n + 255) / 256, 256, 0, st>>>(c);
   if (c.techniques & MARS_TECH_GUIDED) k_guide_update<<<(c.n_cells * 32 + 255) / 256, 256, 0, st>>>(c);
   return cudaGetLastError();
 }

@@ -78,10 +78,11 @@ class Cache:
     """Statistics cache, count fields, guide and image accumulators of one job."""
 
     def __init__(self, scene: Scene, grid_n: int, techniques: int, max_depth: int, arena_capacity: int = 0,
-                 stream=None):
+                 fp32_statistics: bool = False, stream=None):
         self._lib = A.load()
         self.scene = scene
-        d = A.mars_cache_desc(int(grid_n), int(techniques), int(max_depth), 0, int(arena_capacity))
+        flags = A.MARS_CACHE_FP32_STATISTICS if fp32_statistics else 0
+        d = A.mars_cache_desc(int(grid_n), int(techniques), int(max_depth), flags, int(arena_capacity))
         h = ct.c_void_p()
         A.check(self._lib.mars_cache_create(scene.handle, ct.byref(d), _stream_handle(stream), ct.byref(h)),
                 "mars_cache_create")
@@ -124,19 +125,23 @@ class Cache:
                 "tiles": st.tiles, "retries": st.retries, "arena_demand": st.arena_demand,
                 "launches": st.launches, "wave_launches": st.wave_launches, "trace_ms": st.trace_ms,
                 "shade_ms": st.shade_ms, "shadow_ms": st.shadow_ms, "reverse_ms": st.reverse_ms,
-                "image_ms": st.image_ms, "wave_entries": st.wave_entries, "shadow_entries": st.shadow_entries}
+                "image_ms": st.image_ms, "wave_entries": st.wave_entries, "shadow_entries": st.shadow_entries,
+                "shadow_traced": st.shadow_traced,
+                "wave_ms": [[st.wave_ms[k][d] for d in range(self.max_depth)] for k in range(4)]}
 
     def get_launch(self) -> dict:
         """Launch shape of the wave kernels (trace, shade, shadow, reverse)."""
         cfg = A.mars_launch_config()
         A.check(self._lib.mars_cache_get_launch(self.handle, ct.byref(cfg)), "mars_cache_get_launch")
-        return {"threads": list(cfg.threads), "blocks_per_sm": list(cfg.blocks_per_sm)}
+        return {"threads": list(cfg.threads), "blocks_per_sm": list(cfg.blocks_per_sm),
+                "max_registers": list(cfg.max_registers)}
 
-    def set_launch(self, threads, blocks_per_sm) -> None:
+    def set_launch(self, threads, blocks_per_sm, max_registers=(0, 0, 0, 0)) -> None:
         cfg = A.mars_launch_config()
         for k in range(4):
             cfg.threads[k] = int(threads[k])
             cfg.blocks_per_sm[k] = int(blocks_per_sm[k])
+            cfg.max_registers[k] = int(max_registers[k])
         A.check(self._lib.mars_cache_set_launch(self.handle, ct.byref(cfg)), "mars_cache_set_launch")
 
     def autotune(self, *, seed=0, job=0, iteration=0, mode=A.MARS_MODE_WARMUP, weights=A.MARS_WEIGHTS_AWARE,
@@ -148,7 +153,8 @@ class Cache:
         cfg = A.mars_launch_config()
         A.check(self._lib.mars_cache_autotune(self.handle, ct.byref(p), int(repeats), ct.byref(cfg),
                                               _stream_handle(stream)), "mars_cache_autotune")
-        return {"threads": list(cfg.threads), "blocks_per_sm": list(cfg.blocks_per_sm)}
+        return {"threads": list(cfg.threads), "blocks_per_sm": list(cfg.blocks_per_sm),
+                "max_registers": list(cfg.max_registers)}
 
     def update_counts(self, stream=None) -> None:
         A.check(self._lib.mars_update_counts(self.handle, _stream_handle(stream)), "mars_update_counts")

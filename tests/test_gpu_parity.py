@@ -212,9 +212,11 @@ def test_launch_shape_does_not_change_results(mars):
     scene, cache = _make(mars, cfg)
     base = cache.get_launch()
     assert base["threads"] == [128, 128, 128, 128] and min(base["blocks_per_sm"]) >= 1
+    assert base["max_registers"] == [0, 0, 0, 0]
     res = []
-    for threads, bps in (([128] * 4, [0] * 4), ([64, 256, 32, 256], [3, 1, 7, 2]), ([256, 64, 256, 64], [9, 5, 1, 4])):
-        cache.set_launch(threads, bps)
+    for threads, bps, regs in (([128] * 4, [0] * 4, [0] * 4), ([64, 256, 32, 256], [3, 1, 7, 2], [40, 80, 0, 64]),
+                               ([256, 64, 256, 64], [9, 5, 1, 4], [0, 64, 40, 80])):
+        cache.set_launch(threads, bps, regs)
         cache.set_state(q_rr=q_rr, q_s=q_s, valid=valid, pixel_estimate=est, has_estimate=True, n_iterations=1,
                         stats=np.zeros((cfg.n_cells, 3, 8)))
         img, st = _gpu_iteration(mars, cache, iteration=1, seed=4, mode=1)
@@ -233,6 +235,8 @@ def test_launch_shape_does_not_change_results(mars):
     assert np.array_equal(img, res[0][0])
     with pytest.raises(mars.MarsError):
         cache.set_launch([100, 128, 128, 128], [0] * 4)
+    with pytest.raises(mars.MarsError):
+        cache.set_launch([128] * 4, [0] * 4, [0, 0, 0, 48])
 
 
 @pytest.mark.parametrize("albedo,D", [(0.5, 3), (0.8, 5)])
