@@ -241,6 +241,8 @@ def run_mars(args):
                 "kernel_ms_per_step": {k: round(v / args.steps, 4) for k, v in kms.items()},
                 "kernel_gbs": {k: round(kb[k] / max(kms[k], 1e-9) / 1e6, 1) for k in kb}}
     roofline["kernel_ms_per_step"]["image"] = round(sum(s["image_ms"] for s in sts) / args.steps, 4)
+    roofline["wave_rays_per_step"] = [int(sum(s["wave_rays"][d] for s in sts) / args.steps)
+                                      for d in range(cfg.max_depth)]
     roofline["wave_ms_per_step"] = {k: [round(sum(s["wave_ms"][ki][d] for s in sts) / args.steps, 4)
                                         for d in range(cfg.max_depth)]
                                     for ki, k in enumerate(["k_trace", "k_shade", "k_shadow", "k_reverse"])}
@@ -282,6 +284,8 @@ def run_mars(args):
                    "autotuned": not (args.no_autotune or args.launch)},
     }
 
+    if rank == 0 and args.serve_requests > 0:
+        line["serving"] = serving(args)
     if rank == 0 and not args.no_precision:
         line["precision"] = precision_study(cfg, cache, seed, it, stream)
     if rank == 0 and not args.no_efficiency:
@@ -294,6 +298,54 @@ def run_mars(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def serving(args):
+    """Serving stream: seeded render requests arriving Poisson at --serve-rate per
+    second (square resolutions 64..512, 16..4096 spheres in a room, 4..16
+    fixed-point iterations each) submitted to a continuous-batching server with a
+    40 GB device-memory budget; per-iteration latency p50 / p99 over all
+    iterations of all jobs, job latency (arrival to completion) and aggregate
+    vertex throughput over the stream."""
+    import paper_2410_20429_gb300 as M
+    reqs = W.serving_requests(args.serve_requests, rate=args.serve_rate, seed=11)
+    srv = M.Server(40 << 30, args.serve_slots)
+    t0 = time.perf_counter()
+    ids = []
+    for r in reqs:
+        wait = r["arrival_s"] - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        ids.append(srv.submit(r["scene"], grid_n=r["grid_n"], techniques=r["techniques"],
+                              max_depth=r["max_depth"], iterations=r["iterations"], warmup=r["warmup"],
+                              seed=r["seed"], key=r["key"]))
+    done = {}
+    while len(done) < len(ids):
+        for j in ids:
+            if j not in done:
+                st, _ = srv.poll(j)
+                if st["state"] in (M.MARS_JOB_DONE, M.MARS_JOB_FAILED):
+                    done[j] = st
+        time.sleep(0.005)
+    lat = np.concatenate([srv.latencies(j) for j in ids])
+    sts = [done[j] for j in ids]
+    job_s = np.array([s["end_s"] - s["submit_s"] for s in sts])
+    span = max(s["end_s"] for s in sts) - min(s["submit_s"] for s in sts)
+    verts = sum(s["vertices"] for s in sts)
+    starts = sorted((s["start_s"], 1) for s in sts) + sorted((s["end_s"], -1) for s in sts)
+    cur = peak = 0
+    for _, dlt in sorted(starts):
+        cur += dlt
+        peak = max(peak, cur)
+    srv.close()
+    return {"requests": len(ids), "rate_per_s": args.serve_rate, "slots": args.serve_slots,
+            "budget_gb": 40, "failed": sum(s["state"] != M.MARS_JOB_DONE for s in sts),
+            "iterations": int(lat.size), "iter_ms_p50": round(float(np.percentile(lat, 50)), 3),
+            "iter_ms_p99": round(float(np.percentile(lat, 99)), 3),
+            "job_s_p50": round(float(np.percentile(job_s, 50)), 3),
+            "job_s_p99": round(float(np.percentile(job_s, 99)), 3),
+            "throughput_mvertices_s": round(verts / span / 1e6, 2), "span_s": round(span, 2),
+            "max_resident": peak}
 
 
 def precision_study(cfg, cache, seed, it, stream):
@@ -441,6 +493,9 @@ def main():
     ap.add_argument("--ref-pixels-per-step", type=int, default=1024)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=256, help="serving-stream requests (0 = skip)")
+    ap.add_argument("--serve-rate", type=float, default=20.0)
+    ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--launch", default="", help="fixed wave-kernel launch shape 't,t,t,t:b,b,b,b[:r,r,r,r]' (threads per "
                     "block, blocks per SM and register cap of trace, shade, shadow, reverse); skips the autotuner")
     ap.add_argument("--arena-capacity", type=int, default=0, help="queue arena slots (0 = library default)")

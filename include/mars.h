@@ -155,6 +155,7 @@ typedef struct {
   uint64_t shadow_entries;    /* NEE shadow-ray slots, all tiles */
   uint64_t shadow_traced;     /* NEE shadow rays traced (samples of nonzero value), all tiles */
   float wave_ms[4][16];       /* profile = 1: device ms of trace, shade, shadow, reverse per depth wave d (index d - 1) */
+  uint64_t wave_rays[16];     /* rays held by depth wave d (index d - 1), all tiles */
 } mars_iter_stats;
 
 /* Host copy of a cache's state (checkpoint / teacher forcing).  Any pointer
@@ -295,6 +296,7 @@ typedef struct {
   double submit_s, start_s, end_s;   /* wall-clock seconds since server creation */
   double iter_ms_p50, iter_ms_p99;   /* per-iteration latency */
   uint64_t device_bytes;             /* device memory the job was admitted with */
+  uint64_t vertices;                 /* path vertices (closest-hit queries) over the done iterations */
 } mars_job_status;
 
 mars_status mars_server_create(uint64_t memory_budget_bytes, int32_t max_slots, mars_server** out);
@@ -305,6 +307,11 @@ mars_status mars_submit(mars_server* server, const mars_job_desc* job, uint64_t*
  * NULL) receives the mean image over its iterations after warm-up. */
 mars_status mars_poll(mars_server* server, uint64_t job_id, mars_job_status* out, float* image_rgb);
 
+/* Per-iteration latencies of a job in milliseconds (render + update, host wall
+ * clock around the job stream's synchronisation), in iteration order: writes
+ * min(capacity, done iterations) values to ms (host) and the number of done
+ * iterations to *count.  Errors: INVALID_ARG, NOT_FOUND. */
+mars_status mars_job_latencies(mars_server* server, uint64_t job_id, double* ms, int32_t capacity, int32_t* count);
 /* ---- image statistics without allocation ------------------------------------
  * The paper has no counterpart to this entry point; it is a library service.
  * Some callers cannot call cudaMalloc: code that runs while a CUDA graph is

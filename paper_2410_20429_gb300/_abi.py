@@ -60,7 +60,7 @@ class mars_iter_stats(ct.Structure):
         ("wave_launches", ct.c_uint32), ("trace_ms", ct.c_double), ("shade_ms", ct.c_double),
         ("shadow_ms", ct.c_double), ("reverse_ms", ct.c_double), ("image_ms", ct.c_double),
         ("wave_entries", ct.c_uint64), ("shadow_entries", ct.c_uint64), ("shadow_traced", ct.c_uint64),
-        ("wave_ms", (ct.c_float * 16) * 4),
+        ("wave_ms", (ct.c_float * 16) * 4), ("wave_rays", ct.c_uint64 * 16),
     ]
 
 
@@ -95,7 +95,7 @@ class mars_job_status(ct.Structure):
     _fields_ = [("state", ct.c_int32), ("iterations_done", ct.c_int32), ("error", ct.c_int32),
                 ("reserved", ct.c_int32), ("submit_s", ct.c_double), ("start_s", ct.c_double),
                 ("end_s", ct.c_double), ("iter_ms_p50", ct.c_double), ("iter_ms_p99", ct.c_double),
-                ("device_bytes", ct.c_uint64)]
+                ("device_bytes", ct.c_uint64), ("vertices", ct.c_uint64)]
 
 
 _VP = ct.c_void_p
@@ -118,6 +118,7 @@ SIGNATURES = {
     "mars_server_destroy": ([_VP], ct.c_int),
     "mars_submit": ([_VP, ct.POINTER(mars_job_desc), ct.POINTER(ct.c_uint64)], ct.c_int),
     "mars_poll": ([_VP, ct.c_uint64, ct.POINTER(mars_job_status), _VP], ct.c_int),
+    "mars_job_latencies": ([_VP, ct.c_uint64, _VP, ct.c_int32, ct.POINTER(ct.c_int32)], ct.c_int),
     "mars_image_stats_static": ([_VP, _VP, _VP, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_float, ct.c_double, _VP,
                                  _VP], ct.c_int),
     "mars_last_error_string": ([], ct.c_char_p),

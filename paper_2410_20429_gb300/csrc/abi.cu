@@ -736,6 +736,7 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
     out->shadow_traced = h.shadow_traced;
     for (int k = 0; k < WAVE_KERNELS; ++k)
       for (int d = 0; d < MAXD; ++d) out->wave_ms[k][d] = wave_ms[k][d];
+    for (int d = 0; d < MAXD; ++d) out->wave_rays[d] = h.wave_total[d + 1];
   }
   c->last_VI = c->h_ctr->VI;
   c->last_CI = c->h_ctr->CI;
@@ -773,14 +774,18 @@ mars_status get_state_impl(mars_cache* c, mars_cache_state* s, cudaStream_t st) 
     if (e != cudaSuccess) return poison(c, e, "state copy");
   }
   std::vector<float> s32;
+  std::vector<double> s64;
   if (s->stats && c->fp32_stats) {
     s32.resize((size_t)NSTAT * NT * cells);
     if ((e = cudaMemcpyAsync(s32.data(), c->d_stats32, sizeof(float) * s32.size(), cudaMemcpyDeviceToHost, st)) !=
         cudaSuccess)
       return poison(c, e, "state copy");
-  } else if (s->stats && (e = cudaMemcpyAsync(s->stats, c->d_stats, sizeof(double) * NSTAT * NT * cells,
-                                              cudaMemcpyDeviceToHost, st)) != cudaSuccess) {
-    return poison(c, e, "state copy");
+  } else if (s->stats) {
+    // device layout: structure of arrays [stat][cell][technique]
+    s64.resize((size_t)NSTAT * NT * cells);
+    if ((e = cudaMemcpyAsync(s64.data(), c->d_stats, sizeof(double) * s64.size(), cudaMemcpyDeviceToHost, st)) !=
+        cudaSuccess)
+      return poison(c, e, "state copy");
   }
   if (s->guide_hist && guided &&
       (e = cudaMemcpyAsync(s->guide_hist, c->d_hist, sizeof(float) * GUIDE_BINS * cells, cudaMemcpyDeviceToHost,
@@ -800,6 +805,11 @@ mars_status get_state_impl(mars_cache* c, mars_cache_state* s, cudaStream_t st) 
     return poison(c, e, "state copy");
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return poison(c, e, "state copy");
   for (size_t k = 0; k < s32.size(); ++k) s->stats[k] = (double)s32[k];
+  if (!s64.empty()) {
+    const size_t plane = (size_t)NT * cells;
+    for (size_t k = 0; k < plane; ++k)
+      for (int q = 0; q < NSTAT; ++q) s->stats[k * NSTAT + q] = s64[q * plane + k];
+  }
   for (int64_t k = 0; k < cells * NT && !cnt.empty(); ++k) {
     const float4 r = cnt[2 * k], q = cnt[2 * k + 1];
     if (s->q_rr) { s->q_rr[3 * k] = r.x; s->q_rr[3 * k + 1] = r.y; s->q_rr[3 * k + 2] = r.z; }
@@ -836,6 +846,7 @@ mars_status set_state_impl(mars_cache* c, const mars_cache_state* s, cudaStream_
       return poison(c, e, "state copy");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return poison(c, e, "state copy");
   }
+  std::vector<double> s64;
   std::vector<float> s32;
   if (s->stats && c->fp32_stats) {
     s32.resize((size_t)NSTAT * NT * cells);
@@ -843,9 +854,14 @@ mars_status set_state_impl(mars_cache* c, const mars_cache_state* s, cudaStream_
     if ((e = cudaMemcpyAsync(c->d_stats32, s32.data(), sizeof(float) * s32.size(), cudaMemcpyHostToDevice, st)) !=
         cudaSuccess)
       return poison(c, e, "state copy");
-  } else if (s->stats && (e = cudaMemcpyAsync(c->d_stats, s->stats, sizeof(double) * NSTAT * NT * cells,
-                                              cudaMemcpyHostToDevice, st)) != cudaSuccess) {
-    return poison(c, e, "state copy");
+  } else if (s->stats) {
+    const size_t plane = (size_t)NT * cells;
+    s64.resize((size_t)NSTAT * plane);
+    for (size_t k = 0; k < plane; ++k)
+      for (int q = 0; q < NSTAT; ++q) s64[q * plane + k] = s->stats[k * NSTAT + q];
+    if ((e = cudaMemcpyAsync(c->d_stats, s64.data(), sizeof(double) * s64.size(), cudaMemcpyHostToDevice, st)) !=
+        cudaSuccess)
+      return poison(c, e, "state copy");
   }
   if (s->guide_hist && guided &&
       (e = cudaMemcpyAsync(c->d_hist, s->guide_hist, sizeof(float) * GUIDE_BINS * cells, cudaMemcpyHostToDevice,

@@ -99,6 +99,7 @@ struct DevCounters {
   unsigned long long slcount[MAXD + 2];  // shadow rays of wave d that need tracing
   unsigned long long shadow_entries;     // shadow rays of committed tiles
   unsigned long long shadow_traced;      // listed (traced) shadow rays of committed tiles
+  unsigned long long wave_total[MAXD + 2];  // rays per depth wave of committed tiles
   unsigned int overflow;       // this tile overflowed the arena
   unsigned int any_overflow;   // some tile of this iteration overflowed
   unsigned long long demand;   // rays the tile needed (may exceed the arena)
@@ -115,7 +116,7 @@ struct DevCache {
   int grid_n, n_cells, techniques, max_depth, bits;
   int n_pixels;
   float4* cnt;          // [cells][3][2]: (q_rr xyz, valid), (q_s xyz, 0)
-  double* stats;        // [cells][3][8] (float64 statistics)
+  double* stats;        // [8][cells][3] (float64 statistics, structure of arrays)
   float* stats32;       // [cells][3][8] (float32 statistics; then stats is null)
   float* guide_hist;    // [cells][256]
   float* guide_cdf;     // [cells][256]

@@ -93,6 +93,17 @@ __device__ __forceinline__ WarpAlloc warp_alloc(int n, int lane, unsigned long l
   return {wbase, incl, total};
 }
 
+// inclusive warp scan of a per-lane count; returns (inclusive prefix, warp total)
+__device__ __forceinline__ int2 warp_scan(int n, int lane) {
+  int incl = n;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int y = __shfl_up_sync(FULL, incl, off);
+    if (lane >= off) incl += y;
+  }
+  return make_int2(incl, __shfl_sync(FULL, incl, 31));
+}
+
 // lane owning item k of a warp block: the smallest l with incl[l] > k
 __device__ __forceinline__ int owner_lane(const int* incl, int k) {
   int lo = 0, hi = 31;
@@ -133,6 +144,7 @@ __global__ void k_tile_finish(DevCounters* ctr, unsigned int* tile_status, int s
       tot += ctr->count[d];
       sh += ctr->scount[d];
       sl += ctr->slcount[d];
+      ctr->wave_total[d] += ctr->count[d];
     }
     ctr->entries += tot;
     ctr->shadow_entries += sh;
@@ -189,7 +201,14 @@ template <int MINB>
 __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_shade(const DevScene s, const DevCache c, const Arena a,
                                                          const IterArgs it, const int d) {
   DevCounters* ctr = c.ctr;
-  if (ctr->overflow) return;
+  // block-level allocation below synchronises the block: decide the early exit
+  // once per block (other blocks may raise the overflow flag meanwhile)
+  __shared__ unsigned int blk_exit;
+  __shared__ int blk_n[2][MAX_WAVE_THREADS / 32];
+  __shared__ unsigned long long blk_base[2][MAX_WAVE_THREADS / 32];
+  if (threadIdx.x == 0) blk_exit = ctr->overflow;
+  __syncthreads();
+  if (blk_exit) return;
   const Wave w = wave_of(ctr, a, d);
   const unsigned long long cnt = ctr->count[d];
   const unsigned long long base_next = w.base + cnt < a.cap ? w.base + cnt : a.cap;
@@ -199,9 +218,7 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_shade(const DevScene
     ctr->sbase[d] = sbase;
   }
 
-  const int lane = threadIdx.x & 31;
-  const unsigned long long gw = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
-  const unsigned long long nw = (gridDim.x * (unsigned long long)blockDim.x) >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int D = c.max_depth;
   const bool est_depth = d <= D - 1;
   const bool camera = d == 1;
@@ -212,8 +229,11 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_shade(const DevScene
   extern __shared__ ShadeWarpCtx shade_ctx[];
   ShadeWarpCtx* ctx = shade_ctx + (threadIdx.x >> 5);
 
-  for (unsigned long long c0 = gw * 32; c0 < w.n; c0 += nw * 32) {
-    const unsigned long long li = c0 + lane;
+  // block-sized chunks (uniform trip count over the block); warp k of the block
+  // takes the k-th 32 slots of the chunk
+  for (unsigned long long b0 = blockIdx.x * (unsigned long long)blockDim.x; b0 < w.n;
+       b0 += gridDim.x * (unsigned long long)blockDim.x) {
+    const unsigned long long li = b0 + threadIdx.x;
     const bool active = li < w.n;
     const unsigned long long i = w.base + li;
 
@@ -329,10 +349,35 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_shade(const DevScene
       }
     }
 
-    // ---- slots for the children (wave d+1) and the NEE shadow rays
+    // ---- slots for the children (wave d+1) and the NEE shadow rays: warp
+    // scans, then one atomic per counter and block (every block of the grid
+    // allocates from the same two counters)
     const int n_ext = gam[0] + gam[2], n_sh = gam[1];
-    const WarpAlloc ae = warp_alloc(n_ext, lane, &ctr->count[d + 1]);
-    const WarpAlloc as = warp_alloc(n_sh, lane, &ctr->scount[d]);
+    const int2 se = warp_scan(n_ext, lane), ss = warp_scan(n_sh, lane);
+    if (lane == 31) {
+      blk_n[0][warp] = se.y;
+      blk_n[1][warp] = ss.y;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int te = 0, ts = 0;
+      for (int k = 0; k < nwarps; ++k) {
+        const int e = blk_n[0][k], h = blk_n[1][k];
+        blk_n[0][k] = te;
+        blk_n[1][k] = ts;
+        te += e;
+        ts += h;
+      }
+      const unsigned long long be = te > 0 ? atomicAdd(&ctr->count[d + 1], (unsigned long long)te) : 0ull;
+      const unsigned long long bs = ts > 0 ? atomicAdd(&ctr->scount[d], (unsigned long long)ts) : 0ull;
+      for (int k = 0; k < nwarps; ++k) {
+        blk_base[0][k] = be + (unsigned long long)blk_n[0][k];
+        blk_base[1][k] = bs + (unsigned long long)blk_n[1][k];
+      }
+    }
+    __syncthreads();
+    const WarpAlloc ae{blk_base[0][warp], se.x, se.y};
+    const WarpAlloc as{blk_base[1][warp], ss.x, ss.y};
     const unsigned long long first = base_next + ae.base + (unsigned long long)(ae.incl - n_ext);
     const unsigned long long sfirst = sbase + as.base + (unsigned long long)(as.incl - n_sh);
     const bool fits = first + (unsigned long long)n_ext <= a.cap && sfirst + (unsigned long long)n_sh <= a.scap;
@@ -354,7 +399,7 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_shade(const DevScene
       if (on_g && it.collect && !camera && (flags & F_TRACED))
         a.V[4][i] = make_float4(Le_lum, invSb, __uint_as_float(parent_cell), __int_as_float(guide_bin(dir)));
     }
-    if (ae.total == 0 && as.total == 0) continue;  // warp-uniform
+    if (ae.total == 0 && as.total == 0) continue;  // warp-uniform; no block barrier follows
 
     // ---- stage the vertex context of every lane for the cooperative loops
     {
@@ -572,6 +617,11 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_reverse(const DevSce
   const unsigned long long nw = (gridDim.x * (unsigned long long)blockDim.x) >> 5;
   const bool on_n = c.techniques & MARS_TECH_NEE, on_g = c.techniques & MARS_TECH_GUIDED;
   const bool collect = it.collect != 0;
+  // iteration counters of this thread's slots: one warp reduction and one
+  // atomic per counter and warp at the end, not per chunk (every warp of the
+  // grid adds to the same few addresses)
+  unsigned long long n_traced = 0, n_est = 0, n_rays = 0;
+  double sb0 = 0.0, sb1 = 0.0, sb2 = 0.0;
 
   for (unsigned long long c0 = gw * 32; c0 < w.n; c0 += nw * 32) {
     const unsigned long long li = c0 + lane;
@@ -674,30 +724,15 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_reverse(const DevSce
       }
     }
 
-    // ---- iteration counters (one atomic per warp)
-    {
-      const unsigned traced = __ballot_sync(FULL, active && (flags & F_TRACED));
-      const unsigned estv = __ballot_sync(FULL, active && (flags & F_EST));
-      double rays = (active && d == 1) ? (double)(1u + csub) : 0.0;
-      float sb0 = bt[0], sb1 = bt[1], sb2 = bt[2];
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        if (d == 1) rays += __shfl_xor_sync(FULL, rays, off);
-        sb0 += __shfl_xor_sync(FULL, sb0, off);
-        sb1 += __shfl_xor_sync(FULL, sb1, off);
-        sb2 += __shfl_xor_sync(FULL, sb2, off);
-      }
-      if (lane == 0) {
-        if (traced) atomicAdd(&ctr->vertices, (unsigned long long)__popc(traced));
-        if (estv) {
-          atomicAdd(&ctr->est_vertices, (unsigned long long)__popc(estv));
-          atomicAdd(&ctr->sum_beta[0], (double)sb0);
-          if (on_n) atomicAdd(&ctr->sum_beta[1], (double)sb1);
-          if (on_g) atomicAdd(&ctr->sum_beta[2], (double)sb2);
-        }
-        if (rays > 0.0) atomicAdd(&ctr->rays, (unsigned long long)rays);
-      }
+    // ---- iteration counters, kept per thread over all chunks of the launch
+    if (active && (flags & F_TRACED)) ++n_traced;
+    if (active && (flags & F_EST)) {
+      ++n_est;
+      sb0 += bt[0];
+      sb1 += bt[1];
+      sb2 += bt[2];
     }
+    if (active && d == 1) n_rays += 1ull + csub;
 
     // ---- local statistics: reduce runs of equal cells, then float64 atomics
     if (collect) {
@@ -724,14 +759,38 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_reverse(const DevSce
               atomicAdd(dst, make_float4(st[t][0], st[t][1], st[t][2], st[t][3]));
               atomicAdd(dst + 1, make_float4(st[t][4], st[t][5], st[t][6], st[t][7]));
             } else {
-              double* dst = c.stats + ((size_t)key * NT + t) * NSTAT;
+              // structure of arrays: the 8 sums of a record sit in 8 different
+              // cache lines, so their atomics do not queue on one line
+              const size_t plane = (size_t)c.n_cells * NT;
+              double* dst = c.stats + (size_t)key * NT + t;
 #pragma unroll
-              for (int k = 0; k < NSTAT; ++k) atomicAdd(dst + k, (double)st[t][k]);
+              for (int k = 0; k < NSTAT; ++k) atomicAdd(dst + k * plane, (double)st[t][k]);
             }
           }
         }
       }
     }
+  }
+
+  // ---- flush the iteration counters: one atomic per counter and warp
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    n_traced += __shfl_xor_sync(FULL, n_traced, off);
+    n_est += __shfl_xor_sync(FULL, n_est, off);
+    n_rays += __shfl_xor_sync(FULL, n_rays, off);
+    sb0 += __shfl_xor_sync(FULL, sb0, off);
+    sb1 += __shfl_xor_sync(FULL, sb1, off);
+    sb2 += __shfl_xor_sync(FULL, sb2, off);
+  }
+  if (lane == 0) {
+    if (n_traced) atomicAdd(&ctr->vertices, n_traced);
+    if (n_est) {
+      atomicAdd(&ctr->est_vertices, n_est);
+      atomicAdd(&ctr->sum_beta[0], sb0);
+      if (on_n) atomicAdd(&ctr->sum_beta[1], sb1);
+      if (on_g) atomicAdd(&ctr->sum_beta[2], sb2);
+    }
+    if (n_rays) atomicAdd(&ctr->rays, n_rays);
   }
 }
 

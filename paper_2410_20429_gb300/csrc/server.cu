@@ -32,6 +32,7 @@ struct Job {
   std::string message;
   double submit_s = 0, start_s = 0, end_s = 0;
   std::vector<double> iter_ms;
+  uint64_t vertices = 0;
   std::vector<float> image;  // mean over post-warm-up iterations
   std::thread worker;
 };
@@ -85,7 +86,8 @@ struct mars_server {
       p.image_on_host = 1;
       p.update_estimate = 1;
       const auto a = Clock::now();
-      rc = mars::render_iteration_impl(ca, &p, img.data(), nullptr, st);
+      mars_iter_stats ist{};
+      rc = mars::render_iteration_impl(ca, &p, img.data(), &ist, st);
       if (rc == MARS_OK) rc = mars::update_counts_impl(ca, st);
       if (rc == MARS_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = MARS_ERR_CUDA;
       const double ms = std::chrono::duration<double, std::milli>(Clock::now() - a).count();
@@ -96,6 +98,7 @@ struct mars_server {
       }
       std::lock_guard<std::mutex> lk(mu);
       j->iter_ms.push_back(ms);
+      j->vertices += ist.vertices;
       j->done_iters = it + 1;
     }
     if (rc != MARS_OK) msg = mars_last_error_string();
@@ -224,10 +227,24 @@ mars_status mars_poll(mars_server* s, uint64_t job_id, mars_job_status* out, flo
   out->iter_ms_p50 = q(0.5);
   out->iter_ms_p99 = q(0.99);
   out->device_bytes = j->footprint;
+  out->vertices = j->vertices;
   if (j->state == MARS_JOB_FAILED) mars::set_error(j->error, "job %llu failed: %s", (unsigned long long)job_id,
                                                    j->message.c_str());
   if (image_rgb && j->state == MARS_JOB_DONE && !j->image.empty())
     std::copy(j->image.begin(), j->image.end(), image_rgb);
+  return MARS_OK;
+}
+
+mars_status mars_job_latencies(mars_server* s, uint64_t job_id, double* ms, int32_t capacity, int32_t* count) {
+  if (!s || !count || capacity < 0 || (capacity > 0 && !ms))
+    return mars::set_error(MARS_ERR_INVALID_ARG, "null server, count or buffer");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->jobs.find(job_id);
+  if (it == s->jobs.end()) return mars::set_error(MARS_ERR_NOT_FOUND, "unknown job %llu", (unsigned long long)job_id);
+  const std::vector<double>& v = it->second->iter_ms;
+  const size_t n = std::min(v.size(), (size_t)capacity);
+  std::copy(v.begin(), v.begin() + n, ms);
+  *count = (int32_t)v.size();
   return MARS_OK;
 }
 

@@ -137,18 +137,22 @@ __global__ void k_update_counts(DevCache c) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= c.n_cells * NT) return;
   const int t = idx % NT;
-  double2* s2 = reinterpret_cast<double2*>(c.stats + (size_t)idx * NSTAT);
-  const double2 a = s2[0];
+  // structure of arrays: statistic k of entry idx at stats[k * plane + idx]
+  const size_t plane = (size_t)c.n_cells * NT;
+  double* sp = c.stats + idx;
+  const double n = sp[0];
   // no sample landed in this (cell, technique): every sum is already zero
-  if (a.x == 0.0) return;
-  const double2 b = s2[1], cc = s2[2], e = s2[3];
+  if (n == 0.0) return;
+  double v[NSTAT];
+#pragma unroll
+  for (int k = 1; k < NSTAT; ++k) v[k] = sp[k * plane];
   const double VI = c.ctr->VI, CI = c.ctr->CI;
-  const double n = a.x, cost = e.y;
+  const double cost = v[7];
   if (((c.techniques >> t) & 1) && VI > 1e-12 && n >= 2.0 && cost > 0.0) {
     // C_I / C_t / V_I with C_t = cost / n, and 1 / n, formed once in float64
     const double inv_n = 1.0 / n;
     const double r = CI * n / (cost * VI);
-    const double s1[3] = {a.y, b.x, b.y}, s2v[3] = {cc.x, cc.y, e.x};
+    const double s1[3] = {v[1], v[2], v[3]}, s2v[3] = {v[4], v[5], v[6]};
     float qr[3], qs[3];
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
@@ -161,11 +165,8 @@ __global__ void k_update_counts(DevCache c) {
     c.cnt[2 * idx] = make_float4(qr[0], qr[1], qr[2], 1.0f);
     c.cnt[2 * idx + 1] = make_float4(qs[0], qs[1], qs[2], 0.0f);
   }
-  const double2 z = make_double2(0.0, 0.0);
-  s2[0] = z;
-  s2[1] = z;
-  s2[2] = z;
-  s2[3] = z;
+#pragma unroll
+  for (int k = 0; k < NSTAT; ++k) sp[k * plane] = 0.0;
 }
 
 // the same update with float32 statistics and arithmetic (precision study)

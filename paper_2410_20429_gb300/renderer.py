@@ -127,7 +127,8 @@ class Cache:
                 "shade_ms": st.shade_ms, "shadow_ms": st.shadow_ms, "reverse_ms": st.reverse_ms,
                 "image_ms": st.image_ms, "wave_entries": st.wave_entries, "shadow_entries": st.shadow_entries,
                 "shadow_traced": st.shadow_traced,
-                "wave_ms": [[st.wave_ms[k][d] for d in range(self.max_depth)] for k in range(4)]}
+                "wave_ms": [[st.wave_ms[k][d] for d in range(self.max_depth)] for k in range(4)],
+                "wave_rays": [st.wave_rays[d] for d in range(self.max_depth)]}
 
     def get_launch(self) -> dict:
         """Launch shape of the wave kernels (trace, shade, shadow, reverse)."""
@@ -254,6 +255,16 @@ class Server:
         A.check(self._lib.mars_poll(self.handle, ct.c_uint64(job_id), ct.byref(s), ptr), "mars_poll")
         st = {f: getattr(s, f) for f, _ in A.mars_job_status._fields_}
         return st, img
+
+    def latencies(self, job_id: int) -> np.ndarray:
+        """Per-iteration latencies (ms) of a job, in iteration order."""
+        n = ct.c_int32()
+        A.check(self._lib.mars_job_latencies(self.handle, ct.c_uint64(job_id), None, 0, ct.byref(n)),
+                "mars_job_latencies")
+        out = np.zeros(max(n.value, 1), np.float64)
+        A.check(self._lib.mars_job_latencies(self.handle, ct.c_uint64(job_id), out.ctypes.data, n.value,
+                                             ct.byref(n)), "mars_job_latencies")
+        return out[:n.value]
 
     def close(self):
         if getattr(self, "handle", None):

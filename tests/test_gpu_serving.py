@@ -57,6 +57,9 @@ def test_job_result_is_the_same_alone_and_in_the_mix(mars):
     ja = _submit(srv, A, seed=5, key=77)
     st, imgs = _wait(mars, srv, [ja])
     assert st[ja]["state"] == mars.MARS_JOB_DONE and st[ja]["iterations_done"] == 5
+    lat = srv.latencies(ja)
+    assert lat.shape == (5,) and (lat > 0).all() and st[ja]["vertices"] > 64 * 64 * 5
+    assert st[ja]["iter_ms_p50"] == pytest.approx(np.sort(lat)[2])
     alone = imgs[ja]
     srv.close()
 
