@@ -85,6 +85,32 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def sm_max_mhz():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return float(json.load(f).get("sm_max_mhz", 2070.0))
+    return 2070.0
+
+
+# Algorithmic float32 operations of one traversal step, counted from the
+# arithmetic of the intersection routines (every add, multiply, min, max,
+# divide and square root is one operation; a fused multiply-add counts two):
+# a BVH node visit tests two slab boxes (25 each); a quad test 67, a sphere
+# test 25, a triangle test 45.
+OPS_NODE, OPS_QUAD, OPS_SPHERE, OPS_TRI = 50, 67, 25, 45
+
+
+def trace_ops(work):
+    n, q, sp, t = work
+    return OPS_NODE * n + OPS_QUAD * q + OPS_SPHERE * sp + OPS_TRI * t
+
+
+def alu_peak_tflops(num_sms):
+    """Float32 peak: SMs x 128 FP32 lanes x 2 operations (FMA) x max SM clock."""
+    return num_sms * 128 * 2 * sm_max_mhz() * 1e6 / 1e12
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle samples during the timed region."""
 
@@ -229,17 +255,36 @@ def run_mars(args):
                       sum(s["estimator_vertices"] for s in sts), verts, sum(s["shadow_entries"] for s in sts),
                       sum(s["shadow_traced"] for s in sts), guided)
     kms = {k: sum(s[k[2:] + "_ms"] for s in sts) for k in kb}
-    launches_per_kernel = sum(s["wave_launches"] for s in sts)
+    nlaunch = {k: sum(s["wave_launches"] for s in sts) for k in kb}
+    nlaunch["k_shadow"] = sum(max(s["wave_launches"] - s["tiles"], 0) for s in sts)  # no shadow launch at d = D
     hbm, peak_kind = peaks()
+    alu = alu_peak_tflops(torch.cuda.get_device_properties(local).multi_processor_count)
+    # the traversal kernels are bound by float32 arithmetic and instruction issue,
+    # the queue kernels by memory: each gets its own roofline
+    ops = {"k_trace": sum(trace_ops(s["trace_work"][0]) for s in sts),
+           "k_shadow": sum(trace_ops(s["trace_work"][1]) for s in sts)}
+    per_kernel = {}
+    for k in kb:
+        ms_launch = kms[k] / max(nlaunch[k], 1)
+        if k in ops:
+            a = ops[k] / max(nlaunch[k], 1) / (ms_launch * 1e-3) / 1e12
+            per_kernel[k] = {"bound": "alu", "achieved": round(a, 3), "peak": round(alu, 1), "unit": "TFLOP/s",
+                             "frac": round(a / alu, 4), "per_launch": int(ops[k] / max(nlaunch[k], 1)),
+                             "launch_ms": round(ms_launch, 4)}
+        else:
+            a = kb[k] / max(nlaunch[k], 1) / (ms_launch * 1e-3) / 1e9
+            per_kernel[k] = {"bound": "hbm", "achieved": round(a, 1), "peak": hbm, "unit": "GB/s",
+                             "frac": round(a / hbm, 4), "per_launch": int(kb[k] / max(nlaunch[k], 1)),
+                             "launch_ms": round(ms_launch, 4)}
     dom = max(kms, key=kms.get)
-    per_launch_ms = kms[dom] / max(launches_per_kernel, 1)
-    bytes_per_launch = kb[dom] / max(launches_per_kernel, 1)
-    achieved = bytes_per_launch / (per_launch_ms * 1e-3) / 1e9
-    roofline = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(achieved / hbm, 4), "traffic": None, "peak_kind": peak_kind,
-                "bytes_per_launch": int(bytes_per_launch), "launch_ms": round(per_launch_ms, 4),
-                "kernel_ms_per_step": {k: round(v / args.steps, 4) for k, v in kms.items()},
-                "kernel_gbs": {k: round(kb[k] / max(kms[k], 1e-9) / 1e6, 1) for k in kb}}
+    d0 = per_kernel[dom]
+    roofline = {"kernel": dom, "bound": d0["bound"], "achieved": d0["achieved"], "peak": d0["peak"],
+                "unit": d0["unit"], "frac": d0["frac"], "traffic": None,
+                "peak_kind": peak_kind if d0["bound"] == "hbm" else
+                "derived: SMs x 128 FP32 lanes x 2 x max SM clock (measured)",
+                "per_launch": d0["per_launch"], "launch_ms": d0["launch_ms"],
+                "kernels": per_kernel,
+                "kernel_ms_per_step": {k: round(v / args.steps, 4) for k, v in kms.items()}}
     roofline["kernel_ms_per_step"]["image"] = round(sum(s["image_ms"] for s in sts) / args.steps, 4)
     roofline["wave_rays_per_step"] = [int(sum(s["wave_rays"][d] for s in sts) / args.steps)
                                       for d in range(cfg.max_depth)]
@@ -345,7 +390,8 @@ def serving(args):
             "job_s_p50": round(float(np.percentile(job_s, 50)), 3),
             "job_s_p99": round(float(np.percentile(job_s, 99)), 3),
             "throughput_mvertices_s": round(verts / span / 1e6, 2), "span_s": round(span, 2),
-            "max_resident": peak}
+            "max_resident": peak,
+            "failures": sorted(set(s.get("message", "")[:120] for s in sts if s["state"] != M.MARS_JOB_DONE))[:3]}
 
 
 def precision_study(cfg, cache, seed, it, stream):

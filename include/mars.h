@@ -99,7 +99,7 @@ typedef struct {
  *   run the count update and reduce V_I and C_I in float32 instead of float64
  *   (the float32-only variant of the precision study; default float64).
  * arena_capacity: rays held by the per-iteration queue arena summed over all
- *   depths (0 = 8 x pixels x max_depth, at least 2^20).  An iteration whose path
+ *   depths (0 = 3 x pixels x max_depth, at least 2^20).  An iteration whose path
  *   trees do not fit is rendered in pixel tiles (results do not depend on it). */
 #define MARS_CACHE_FP32_STATISTICS 1
 typedef struct {
@@ -134,6 +134,10 @@ typedef struct {
   int32_t image_on_host;
   int32_t update_estimate;
   int32_t profile;         /* record CUDA events around every kernel (stage times in mars_iter_stats) */
+  float max_multiplicity;  /* path multiplicity cap M (0 = none, the paper's rule): every budget is
+                              further limited to max(clamp_lo, M / P), P = the product of the budgets
+                              that drew the path so far, so one camera sample spawns at most M
+                              vertices per depth in expectation; any budget field stays unbiased */
 } mars_iter_params;
 
 /* What one iteration did (host memory, filled by mars_render_iteration). */
@@ -156,6 +160,8 @@ typedef struct {
   uint64_t shadow_traced;     /* NEE shadow rays traced (samples of nonzero value), all tiles */
   float wave_ms[4][16];       /* profile = 1: device ms of trace, shade, shadow, reverse per depth wave d (index d - 1) */
   uint64_t wave_rays[16];     /* rays held by depth wave d (index d - 1), all tiles */
+  uint64_t trace_work[2][4];  /* closest-hit [0] and shadow [1] traversal: BVH node visits
+                                 (two box tests each), quad, sphere and triangle tests */
 } mars_iter_stats;
 
 /* Host copy of a cache's state (checkpoint / teacher forcing).  Any pointer
@@ -203,7 +209,10 @@ mars_status mars_scene_destroy(mars_scene* scene);
 /* ---- cache --------------------------------------------------------------
  * Allocates the statistics cache, count fields (all invalid: beta = 1), guide
  * (uniform), image accumulators and the queue arena for `scene`, which must
- * outlive the cache.  Synchronises `stream`.  Errors: INVALID_ARG, OOM, CUDA. */
+ * outlive the cache.  Synchronises `stream`.  Errors: INVALID_ARG, OOM, CUDA.
+ * Scene and cache memory comes from the device's stream-ordered memory pool,
+ * which keeps released memory for the next object; *_destroy waits for the
+ * stream of the object's last call and releases the memory there. */
 mars_status mars_cache_create(const mars_scene* scene, const mars_cache_desc* desc, void* stream,
                               mars_cache** out);
 mars_status mars_cache_destroy(mars_cache* cache);
@@ -256,7 +265,7 @@ typedef struct {
   int32_t threads[4];
   int32_t blocks_per_sm[4];
   int32_t max_registers[4];  /* register cap of the compiled variant: 0 = the compiler's
-                                choice; shade and reverse also 80 or 64, trace and shadow 40 */
+                                choice; shade and reverse also 80 or 64, trace and shadow 64 or 40 */
 } mars_launch_config;
 mars_status mars_cache_get_launch(const mars_cache* cache, mars_launch_config* out);
 mars_status mars_cache_set_launch(mars_cache* cache, const mars_launch_config* config);

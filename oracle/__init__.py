@@ -62,7 +62,7 @@ class Params(ct.Structure):
         ("mode", ct.c_int), ("weights", ct.c_int),
         ("seed", ct.c_uint32), ("job", ct.c_uint32), ("iteration", ct.c_uint32),
         ("clamp_lo", ct.c_double), ("clamp_hi", ct.c_double), ("outlier", ct.c_double),
-        ("has_estimate", ct.c_int), ("collect", ct.c_int),
+        ("has_estimate", ct.c_int), ("collect", ct.c_int), ("max_mult", ct.c_float),
     ]
 
 
@@ -172,7 +172,7 @@ class RenderResult:
 def render(scene, *, grid_n, techniques, max_depth, mode=MODE_WARMUP, weights=WEIGHTS_AWARE,
            seed=0, job=0, iteration=0, clamp_lo=0.05, clamp_hi=20.0, outlier=50.0,
            q_rr=None, q_s=None, valid=None, guide_cdf=None, est=None, collect=True,
-           px_begin=0, px_end=None) -> RenderResult:
+           px_begin=0, px_end=None, max_mult=0.0) -> RenderResult:
     """One iteration of the MARS path tracer over pixels [px_begin, px_end)."""
     L = lib()
     cells = grid_n ** 3
@@ -203,7 +203,7 @@ def render(scene, *, grid_n, techniques, max_depth, mode=MODE_WARMUP, weights=WE
     counters = np.zeros(8, np.float64)
     sh = _SceneHolder(scene)
     P = Params(grid_n, techniques, max_depth, mode, weights, seed, job, iteration,
-               clamp_lo, clamp_hi, outlier, int(has_est), int(bool(collect)))
+               clamp_lo, clamp_hi, outlier, int(has_est), int(bool(collect)), float(max_mult))
     S = State(_p(q_rr, ct.c_float), _p(q_s, ct.c_float), _p(valid, ct.c_uint8),
               _p(guide_cdf, ct.c_float), _p(est, ct.c_float), _p(image, ct.c_double),
               _p(stats, ct.c_double), _p(hist, ct.c_double), _p(counters, ct.c_double))

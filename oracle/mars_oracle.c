@@ -492,7 +492,7 @@ typedef struct {
 } vtx_t;
 
 static void secondary_estimator(rnd_t* R, const vtx_t* x, int depth, uint64_t lin, const double T[3],
-                                double Lr[3], double* cost);
+                                float mult, double Lr[3], double* cost);
 
 /* pdf of the NEE technique for a direction that reaches point y on light quad q */
 static double nee_pdf_at(const ctx_t* C, int quad, v3 x, v3 y, v3 wi) {
@@ -520,6 +520,7 @@ typedef struct {
   double betaN_pN0;  /* beta_NEE (aware) or 1 (unaware) if NEE competes, else 0 */
   int camera;        /* camera ray: no MIS */
   double T_child[3]; /* prefix throughput at the hit */
+  float mult_child;  /* path multiplicity at the hit (product of the budgets that drew the path) */
 } ray_info;
 
 static void trace_sample(rnd_t* R, v3 o, v3 d, int depth, uint64_t lin, const ray_info* ri,
@@ -560,7 +561,7 @@ static void trace_sample(rnd_t* R, v3 o, v3 d, int depth, uint64_t lin, const ra
       x.mat = h.mat;
       x.cell = cell_of(C, P->grid_n, h.p);
       onb(x.ns, &x.b1, &x.b2);
-      secondary_estimator(R, &x, depth, lin, ri->T_child, Lchild, &ccost);
+      secondary_estimator(R, &x, depth, lin, ri->T_child, ri->mult_child, Lchild, &ccost);
     }
   }
   for (int c = 0; c < 3; ++c) v_out[c] = ri->fcp[c] * (E[c] + w_ind * Lchild[c]);
@@ -590,9 +591,14 @@ static void stat_add(rnd_t* R, int cell, int t, const double v[3], double cost, 
 }
 
 /* Secondary estimator at vertex x (Sec. 3.1): sum over techniques t of
- * 1/beta_t times the sum of gamma_t primary estimates, gamma from Alg. 1. */
+ * 1/beta_t times the sum of gamma_t primary estimates, gamma from Alg. 1.
+ * mult is the path multiplicity at x: the product of the budgets of the
+ * techniques that drew the path's earlier vertices (1 at the first vertex).
+ * With a cap M > 0 every budget is further limited to max(clamp_lo, M / mult)
+ * (in float32), which bounds the expected number of vertices per depth that one
+ * camera sample spawns by M; any budget field keeps the estimator unbiased. */
 static void secondary_estimator(rnd_t* R, const vtx_t* x, int depth, uint64_t lin, const double T[3],
-                                double Lr[3], double* cost) {
+                                float mult, double Lr[3], double* cost) {
   const ctx_t* C = R->C;
   const orc_params* P = R->P;
   orc_state* st = R->st;
@@ -618,6 +624,11 @@ static void secondary_estimator(rnd_t* R, const vtx_t* x, int depth, uint64_t li
       b = orc_vertex_count(st->q_rr + o, st->q_s + o, T, st->est + 3 * R->px, P->clamp_lo, P->clamp_hi);
     }
     betaf[t] = (float)b;       /* the budget is carried in float32 */
+    if (P->max_mult > 0.0f) {
+      float cap = P->max_mult / mult;
+      if (cap < (float)P->clamp_lo) cap = (float)P->clamp_lo;
+      if (betaf[t] > cap) betaf[t] = cap;
+    }
     beta[t] = (double)betaf[t];
     st->counters[3 + t] += beta[t];
   }
@@ -699,6 +710,7 @@ static void secondary_estimator(rnd_t* R, const vtx_t* x, int depth, uint64_t li
             ri.betaN_pN0 = bw[ORC_T_NEE];
             double w_ind = ri.A / ri.S_ind;
             for (int c = 0; c < 3; ++c) ri.T_child[c] = T[c] * ri.fcp[c] * w_ind / beta[t];
+            ri.mult_child = mult * betaf[t];
             uint64_t digit = (uint64_t)(t == ORC_T_BSDF ? s + 1 : 32 + s + 1);
             uint64_t clin = (lin << C->bits) | digit;
             double li_lum = 0.0;
@@ -750,6 +762,7 @@ int orc_render(const orc_scene_desc* scene, const orc_params* P, orc_state* st, 
     ray_info ri;
     memset(&ri, 0, sizeof(ri));
     ri.camera = 1;
+    ri.mult_child = 1.0f;
     ri.A = ri.S_ind = 1.0;
     for (int c = 0; c < 3; ++c) { ri.fcp[c] = 1.0; ri.T_child[c] = 1.0; }
     double v[3], cost;

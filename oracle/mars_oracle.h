@@ -59,6 +59,7 @@ typedef struct {
   double outlier;       /* outlier multiple of the pixel estimate (50) */
   int has_estimate;     /* 1 if est[] holds a pixel estimate */
   int collect;          /* 1: accumulate statistics and guide deposits */
+  float max_mult;       /* path multiplicity cap M (0: none), see orc_render */
 } orc_params;
 
 typedef struct {

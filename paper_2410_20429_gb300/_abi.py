@@ -48,7 +48,7 @@ class mars_iter_params(ct.Structure):
         ("mode", ct.c_int32), ("weights", ct.c_int32),
         ("clamp_lo", ct.c_float), ("clamp_hi", ct.c_float), ("outlier", ct.c_float),
         ("collect", ct.c_int32), ("image_on_host", ct.c_int32), ("update_estimate", ct.c_int32),
-        ("profile", ct.c_int32),
+        ("profile", ct.c_int32), ("max_multiplicity", ct.c_float),
     ]
 
 
@@ -61,6 +61,7 @@ class mars_iter_stats(ct.Structure):
         ("shadow_ms", ct.c_double), ("reverse_ms", ct.c_double), ("image_ms", ct.c_double),
         ("wave_entries", ct.c_uint64), ("shadow_entries", ct.c_uint64), ("shadow_traced", ct.c_uint64),
         ("wave_ms", (ct.c_float * 16) * 4), ("wave_rays", ct.c_uint64 * 16),
+        ("trace_work", (ct.c_uint64 * 4) * 2),
     ]
 
 

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -16,6 +18,53 @@
 namespace mars {
 
 thread_local std::string g_last_error;
+
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t st) {
+  static std::once_flag once[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64)
+    std::call_once(once[dev], [dev] {
+      // keep memory released to the pool instead of returning it to the driver
+      cudaMemPool_t pool;
+      if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+      }
+    });
+  *p = nullptr;
+  return cudaMallocAsync(p, bytes, st);
+}
+
+void dev_free(void* p, cudaStream_t st) {
+  if (p) cudaFreeAsync(p, st);
+}
+
+namespace {
+std::mutex g_pinned_mu;
+std::multimap<size_t, void*> g_pinned_free;
+}  // namespace
+
+void* pinned_acquire(size_t bytes) {
+  {
+    std::lock_guard<std::mutex> lk(g_pinned_mu);
+    auto it = g_pinned_free.lower_bound(bytes);
+    if (it != g_pinned_free.end() && it->first <= 2 * bytes) {
+      void* p = it->second;
+      g_pinned_free.erase(it);
+      return p;
+    }
+  }
+  void* p = nullptr;
+  if (cudaMallocHost(&p, bytes) != cudaSuccess) return nullptr;
+  return p;
+}
+
+void pinned_release(void* p, size_t bytes) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_pinned_mu);
+  g_pinned_free.emplace(bytes, p);
+}
 
 mars_status set_error(mars_status s, const char* fmt, ...) {
   char buf[512];
@@ -101,6 +150,7 @@ mars_status scene_create_impl(const mars_scene_desc* d, cudaStream_t st, mars_sc
   if (cudaGetDevice(&dev) != cudaSuccess) return set_error(MARS_ERR_CUDA, "no CUDA device");
   mars_scene* s = new mars_scene();
   s->device = dev;
+  s->stream = st;
   s->num_sms = num_sms_of(dev);
   s->width = d->width;
   s->height = d->height;
@@ -277,11 +327,11 @@ mars_status scene_create_impl(const mars_scene_desc* d, cudaStream_t st, mars_sc
     return e == cudaErrorMemoryAllocation ? MARS_ERR_OOM : MARS_ERR_CUDA;
   };
   cudaError_t e;
-  if ((e = cudaMalloc(&s->d_prims, sizeof(float4) * prims.size())) != cudaSuccess) return cleanup(e, "scene alloc");
-  if ((e = cudaMalloc(&s->d_boxes, sizeof(float4) * boxes.size())) != cudaSuccess) return cleanup(e, "scene alloc");
-  if ((e = cudaMalloc(&s->d_nodes, sizeof(BvhNode) * std::max(1, n - 1))) != cudaSuccess) return cleanup(e, "scene alloc");
-  if ((e = cudaMalloc(&s->d_mats, sizeof(float4) * mats.size())) != cudaSuccess) return cleanup(e, "scene alloc");
-  if ((e = cudaMalloc(&s->d_lights, sizeof(float4) * lights.size())) != cudaSuccess) return cleanup(e, "scene alloc");
+  if ((e = dev_alloc((void**)&s->d_prims, sizeof(float4) * prims.size(), st)) != cudaSuccess) return cleanup(e, "scene alloc");
+  if ((e = dev_alloc((void**)&s->d_boxes, sizeof(float4) * boxes.size(), st)) != cudaSuccess) return cleanup(e, "scene alloc");
+  if ((e = dev_alloc((void**)&s->d_nodes, sizeof(BvhNode) * std::max(1, n - 1), st)) != cudaSuccess) return cleanup(e, "scene alloc");
+  if ((e = dev_alloc((void**)&s->d_mats, sizeof(float4) * mats.size(), st)) != cudaSuccess) return cleanup(e, "scene alloc");
+  if ((e = dev_alloc((void**)&s->d_lights, sizeof(float4) * lights.size(), st)) != cudaSuccess) return cleanup(e, "scene alloc");
   if ((e = cudaMemcpyAsync(s->d_prims, prims.data(), sizeof(float4) * prims.size(), cudaMemcpyHostToDevice, st)) ||
       (e = cudaMemcpyAsync(s->d_boxes, boxes.data(), sizeof(float4) * boxes.size(), cudaMemcpyHostToDevice, st)) ||
       (e = cudaMemcpyAsync(s->d_mats, mats.data(), sizeof(float4) * mats.size(), cudaMemcpyHostToDevice, st)) ||
@@ -295,7 +345,9 @@ mars_status scene_create_impl(const mars_scene_desc* d, cudaStream_t st, mars_sc
     // check the hierarchy before any kernel traverses it: every internal node
     // reached once from the root, every primitive once, all indices in range
     std::vector<BvhNode> nodes(n - 1);
-    if ((e = cudaMemcpy(nodes.data(), s->d_nodes, sizeof(BvhNode) * (n - 1), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    if ((e = cudaMemcpyAsync(nodes.data(), s->d_nodes, sizeof(BvhNode) * (n - 1), cudaMemcpyDeviceToHost, st)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
       return cleanup(e, "BVH readback");
     std::vector<uint8_t> seen_node(n - 1, 0), seen_leaf(n, 0);
     std::vector<int> stack{0};
@@ -339,11 +391,15 @@ mars_status scene_create_impl(const mars_scene_desc* d, cudaStream_t st, mars_sc
 void scene_destroy_impl(mars_scene* s) {
   if (!s) return;
   DeviceGuard g(s->device);
-  if (s->d_prims) cudaFree(s->d_prims);
-  if (s->d_boxes) cudaFree(s->d_boxes);
-  if (s->d_nodes) cudaFree(s->d_nodes);
-  if (s->d_mats) cudaFree(s->d_mats);
-  if (s->d_lights) cudaFree(s->d_lights);
+  // the scene's last users are the caches' iterations, which end synchronised;
+  // release on its creation stream
+  cudaStream_t st = s->stream;
+  if (cudaStreamQuery(st) == cudaErrorInvalidResourceHandle) st = cudaStreamPerThread;
+  dev_free(s->d_prims, st);
+  dev_free(s->d_boxes, st);
+  dev_free(s->d_nodes, st);
+  dev_free(s->d_mats, st);
+  dev_free(s->d_lights, st);
   delete s;
 }
 
@@ -358,7 +414,9 @@ uint64_t cache_footprint(int64_t cells, int64_t pixels, int max_depth, int techn
 }
 
 uint64_t default_capacity(int64_t pixels, int max_depth) {
-  uint64_t cap = (uint64_t)pixels * (uint64_t)max_depth * 8ull;
+  // a MARS iteration of the guided room at 512^2 holds about 1.4 x pixels x D
+  // rays; heavier splitting that overflows this falls back to pixel tiles
+  uint64_t cap = (uint64_t)pixels * (uint64_t)max_depth * 3ull;
   if (cap < (1ull << 20)) cap = 1ull << 20;
   return cap;
 }
@@ -388,6 +446,7 @@ mars_status cache_create_impl(const mars_scene* s, const mars_cache_desc* d, cud
   mars_cache* c = new mars_cache();
   c->scene = s;
   c->device = s->device;
+  c->last_stream = st;
   c->grid_n = d->grid_n;
   c->techniques = d->techniques;
   c->max_depth = d->max_depth;
@@ -404,37 +463,39 @@ mars_status cache_create_impl(const mars_scene* s, const mars_cache_desc* d, cud
   };
   cudaError_t e;
   for (int k = 0; k < NR; ++k)
-    if ((e = cudaMalloc(&c->arena.R[k], sizeof(float4) * cap)) != cudaSuccess) return cleanup(e, "arena alloc");
+    if ((e = dev_alloc((void**)&c->arena.R[k], sizeof(float4) * cap, st)) != cudaSuccess) return cleanup(e, "arena alloc");
   for (int k = 0; k < NV; ++k)
-    if ((e = cudaMalloc(&c->arena.V[k], sizeof(float4) * cap)) != cudaSuccess) return cleanup(e, "arena alloc");
-  if ((e = cudaMalloc(&c->arena.S, sizeof(float4) * cap)) != cudaSuccess) return cleanup(e, "arena alloc");
-  if ((e = cudaMalloc(&c->arena.H, sizeof(float2) * cap)) != cudaSuccess) return cleanup(e, "arena alloc");
+    if ((e = dev_alloc((void**)&c->arena.V[k], sizeof(float4) * cap, st)) != cudaSuccess) return cleanup(e, "arena alloc");
+  if ((e = dev_alloc((void**)&c->arena.S, sizeof(float4) * cap, st)) != cudaSuccess) return cleanup(e, "arena alloc");
+  if ((e = dev_alloc((void**)&c->arena.M, sizeof(float) * cap, st)) != cudaSuccess) return cleanup(e, "arena alloc");
+  if ((e = dev_alloc((void**)&c->arena.H, sizeof(float2) * cap, st)) != cudaSuccess) return cleanup(e, "arena alloc");
   for (int k = 0; k < NSH; ++k)
-    if ((e = cudaMalloc(&c->arena.SH[k], sizeof(float4) * c->arena.scap)) != cudaSuccess)
+    if ((e = dev_alloc((void**)&c->arena.SH[k], sizeof(float4) * c->arena.scap, st)) != cudaSuccess)
       return cleanup(e, "arena alloc");
-  if ((e = cudaMalloc(&c->arena.SL, sizeof(unsigned int) * c->arena.scap)) != cudaSuccess)
+  if ((e = dev_alloc((void**)&c->arena.SL, sizeof(unsigned int) * c->arena.scap, st)) != cudaSuccess)
     return cleanup(e, "arena alloc");
-  if ((e = cudaMalloc(&c->d_cnt, sizeof(float4) * 2 * NT * cells)) != cudaSuccess) return cleanup(e, "cache alloc");
+  if ((e = dev_alloc((void**)&c->d_cnt, sizeof(float4) * 2 * NT * cells, st)) != cudaSuccess) return cleanup(e, "cache alloc");
   c->fp32_stats = fp32;
   if (fp32) {
-    if ((e = cudaMalloc(&c->d_stats32, sizeof(float) * NSTAT * NT * cells)) != cudaSuccess)
+    if ((e = dev_alloc((void**)&c->d_stats32, sizeof(float) * NSTAT * NT * cells, st)) != cudaSuccess)
       return cleanup(e, "cache alloc");
-  } else if ((e = cudaMalloc(&c->d_stats, sizeof(double) * NSTAT * NT * cells)) != cudaSuccess) {
+  } else if ((e = dev_alloc((void**)&c->d_stats, sizeof(double) * NSTAT * NT * cells, st)) != cudaSuccess) {
     return cleanup(e, "cache alloc");
   }
   const int64_t gcells = (d->techniques & MARS_TECH_GUIDED) ? cells : 1;
-  if ((e = cudaMalloc(&c->d_hist, sizeof(float) * GUIDE_BINS * gcells)) != cudaSuccess) return cleanup(e, "cache alloc");
-  if ((e = cudaMalloc(&c->d_cdf, sizeof(float) * GUIDE_BINS * gcells)) != cudaSuccess) return cleanup(e, "cache alloc");
-  if ((e = cudaMalloc(&c->d_guide_dirty, (size_t)gcells)) != cudaSuccess) return cleanup(e, "cache alloc");
-  if ((e = cudaMalloc(&c->d_est, sizeof(float4) * pixels)) != cudaSuccess) return cleanup(e, "image alloc");
-  if ((e = cudaMalloc(&c->d_run, sizeof(float4) * pixels)) != cudaSuccess) return cleanup(e, "image alloc");
-  if ((e = cudaMalloc(&c->d_img, sizeof(float4) * pixels)) != cudaSuccess) return cleanup(e, "image alloc");
-  if ((e = cudaMalloc(&c->d_ctr, sizeof(DevCounters))) != cudaSuccess) return cleanup(e, "counter alloc");
-  if ((e = cudaMalloc(&c->d_tile_status, sizeof(unsigned int) * c->max_tiles)) != cudaSuccess)
+  if ((e = dev_alloc((void**)&c->d_hist, sizeof(float) * GUIDE_BINS * gcells, st)) != cudaSuccess) return cleanup(e, "cache alloc");
+  if ((e = dev_alloc((void**)&c->d_cdf, sizeof(float) * GUIDE_BINS * gcells, st)) != cudaSuccess) return cleanup(e, "cache alloc");
+  if ((e = dev_alloc((void**)&c->d_guide_dirty, (size_t)gcells, st)) != cudaSuccess) return cleanup(e, "cache alloc");
+  if ((e = dev_alloc((void**)&c->d_est, sizeof(float4) * pixels, st)) != cudaSuccess) return cleanup(e, "image alloc");
+  if ((e = dev_alloc((void**)&c->d_run, sizeof(float4) * pixels, st)) != cudaSuccess) return cleanup(e, "image alloc");
+  if ((e = dev_alloc((void**)&c->d_img, sizeof(float4) * pixels, st)) != cudaSuccess) return cleanup(e, "image alloc");
+  if ((e = dev_alloc((void**)&c->d_ctr, sizeof(DevCounters), st)) != cudaSuccess) return cleanup(e, "counter alloc");
+  if ((e = dev_alloc((void**)&c->d_tile_status, sizeof(unsigned int) * c->max_tiles, st)) != cudaSuccess)
     return cleanup(e, "counter alloc");
-  if ((e = cudaMallocHost(&c->h_ctr, sizeof(DevCounters))) != cudaSuccess) return cleanup(e, "pinned alloc");
-  if ((e = cudaMallocHost(&c->h_tile_status, sizeof(unsigned int) * c->max_tiles)) != cudaSuccess)
-    return cleanup(e, "pinned alloc");
+  c->h_ctr = (DevCounters*)pinned_acquire(sizeof(DevCounters));
+  if (!c->h_ctr) return cleanup(cudaErrorMemoryAllocation, "pinned alloc");
+  c->h_tile_status = (unsigned int*)pinned_acquire(sizeof(unsigned int) * c->max_tiles);
+  if (!c->h_tile_status) return cleanup(cudaErrorMemoryAllocation, "pinned alloc");
   cudaMemsetAsync(c->d_cnt, 0, sizeof(float4) * 2 * NT * cells, st);
   if (c->d_stats) cudaMemsetAsync(c->d_stats, 0, sizeof(double) * NSTAT * NT * cells, st);
   if (c->d_stats32) cudaMemsetAsync(c->d_stats32, 0, sizeof(float) * NSTAT * NT * cells, st);
@@ -516,16 +577,25 @@ mars_status apply_launch(mars_cache* c, const int threads[WAVE_KERNELS], const i
 void cache_destroy_impl(mars_cache* c) {
   if (!c) return;
   DeviceGuard g(c->device);
-  for (auto* p : c->arena.R) if (p) cudaFree(p);
-  for (auto* p : c->arena.V) if (p) cudaFree(p);
-  if (c->arena.S) cudaFree(c->arena.S);
-  if (c->arena.H) cudaFree(c->arena.H);
-  for (auto* p : c->arena.SH) if (p) cudaFree(p);
-  if (c->arena.SL) cudaFree(c->arena.SL);
+  // work still queued for the cache (an update, a state copy) is on the stream
+  // of its last call: let it finish, then release the memory to the pool
+  cudaStream_t st = c->last_stream;
+  if (cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    cudaDeviceSynchronize();
+    st = cudaStreamPerThread;
+  }
+  for (auto* p : c->arena.R) dev_free(p, st);
+  for (auto* p : c->arena.V) dev_free(p, st);
+  dev_free(c->arena.S, st);
+  dev_free(c->arena.M, st);
+  dev_free(c->arena.H, st);
+  for (auto* p : c->arena.SH) dev_free(p, st);
+  dev_free(c->arena.SL, st);
   void* ptrs[] = {c->d_cnt, c->d_stats, c->d_stats32, c->d_hist, c->d_cdf, c->d_guide_dirty, c->d_est, c->d_run, c->d_img, c->d_ctr, c->d_tile_status};
-  for (void* p : ptrs) if (p) cudaFree(p);
-  if (c->h_ctr) cudaFreeHost(c->h_ctr);
-  if (c->h_tile_status) cudaFreeHost(c->h_tile_status);
+  for (void* p : ptrs) dev_free(p, st);
+  pinned_release(c->h_ctr, sizeof(DevCounters));
+  pinned_release(c->h_tile_status, sizeof(unsigned int) * c->max_tiles);
   for (cudaEvent_t ev : c->events) cudaEventDestroy(ev);
   delete c;
 }
@@ -573,9 +643,11 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
   if (!(p->clamp_lo >= 0.0f) || !(p->clamp_hi <= 30.0f) || !(p->clamp_lo <= p->clamp_hi))
     return set_error(MARS_ERR_INVALID_ARG, "clamp range [%g, %g] outside [0, 30]", p->clamp_lo, p->clamp_hi);
   if (!(p->outlier > 0.0f)) return set_error(MARS_ERR_INVALID_ARG, "outlier multiple must be positive");
+  if (!(p->max_multiplicity >= 0.0f)) return set_error(MARS_ERR_INVALID_ARG, "max_multiplicity must be >= 0");
   if (p->image_on_host && !image) return set_error(MARS_ERR_INVALID_ARG, "image_on_host without an image");
   DeviceGuard g(c->device);
   if (!g.ok) return set_error(MARS_ERR_CUDA, "cannot select device %d", c->device);
+  c->last_stream = st;
   const mars_scene* s = c->scene;
 
   IterArgs it{};
@@ -589,6 +661,7 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
   it.clamp_lo = p->clamp_lo;
   it.clamp_hi = p->clamp_hi;
   it.outlier = p->outlier;
+  it.max_mult = p->max_multiplicity;
 
   // reset the iteration counters (rays, vertices, beta sums, image sums)
   cudaError_t e = cudaMemsetAsync(c->d_ctr, 0, sizeof(DevCounters), st);
@@ -737,6 +810,8 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
     for (int k = 0; k < WAVE_KERNELS; ++k)
       for (int d = 0; d < MAXD; ++d) out->wave_ms[k][d] = wave_ms[k][d];
     for (int d = 0; d < MAXD; ++d) out->wave_rays[d] = h.wave_total[d + 1];
+    for (int k = 0; k < 2; ++k)
+      for (int q = 0; q < 4; ++q) out->trace_work[k][q] = h.trace_work[k][q];
   }
   c->last_VI = c->h_ctr->VI;
   c->last_CI = c->h_ctr->CI;
@@ -754,6 +829,7 @@ mars_status update_counts_impl(mars_cache* c, cudaStream_t st) {
   if (!c) return set_error(MARS_ERR_INVALID_ARG, "null cache");
   if (c->poisoned) return set_error(MARS_ERR_CUDA, "cache is poisoned by an earlier CUDA error");
   DeviceGuard g(c->device);
+  c->last_stream = st;
   cudaError_t e = launch_update(c->dc, c->scene->num_sms, st);
   if (e != cudaSuccess) return poison(c, e, "update launch");
   return MARS_OK;

@@ -42,6 +42,17 @@ struct SceneDescCopy {
 
 mars_status set_error(mars_status s, const char* fmt, ...);
 
+// Device memory of scenes and caches comes from the device's stream-ordered
+// memory pool (cudaMallocAsync / cudaFreeAsync), which keeps released memory
+// for reuse: creating and destroying objects while other streams render
+// neither maps nor unmaps memory nor synchronises the device.
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t st);
+void dev_free(void* p, cudaStream_t st);
+// Page-locked host buffers for the per-iteration status copies, kept in a
+// process-wide free list (cudaMallocHost / cudaFreeHost are slow and serialise).
+void* pinned_acquire(size_t bytes);
+void pinned_release(void* p, size_t bytes);
+
 }  // namespace mars
 
 struct mars_scene {
@@ -56,6 +67,7 @@ struct mars_scene {
   float4* d_lights = nullptr;
   uint64_t device_bytes = 0;
   mars::SceneDescCopy desc_copy;
+  cudaStream_t stream = nullptr;  // the stream it was created on (released there)
 };
 
 struct mars_cache {
@@ -87,6 +99,7 @@ struct mars_cache {
   double last_VI = 0.0, last_CI = 0.0;
   uint64_t device_bytes = 0;
   std::vector<cudaEvent_t> events;  // profiling events, grown on demand
+  cudaStream_t last_stream = nullptr;  // the stream of the last call that used the cache
   mars::WaveLaunch launch{};        // launch shape of the per-wave kernels
   int blocks_per_sm[mars::WAVE_KERNELS] = {0, 0, 0, 0};  // 0: occupancy maximum
   // wave sizes of the last single-tile iteration (rays per depth wave, NEE
@@ -105,6 +118,7 @@ void cache_destroy_impl(mars_cache* c);
 mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, float* image, mars_iter_stats* out,
                                   cudaStream_t st);
 mars_status update_counts_impl(mars_cache* c, cudaStream_t st);
+mars_status get_state_impl(mars_cache* c, mars_cache_state* s, cudaStream_t st);
 uint64_t cache_footprint(int64_t cells, int64_t pixels, int max_depth, int techniques, uint64_t cap);
 uint64_t default_capacity(int64_t pixels, int max_depth);
 mars_status apply_launch(mars_cache* c, const int threads[WAVE_KERNELS], const int blocks_per_sm[WAVE_KERNELS],

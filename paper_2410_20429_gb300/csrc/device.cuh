@@ -111,10 +111,19 @@ __device__ __forceinline__ bool hit_tri(const float4* q, f3 o, f3 d, float tmax,
   return true;
 }
 
+// Work counters of a traversal (for the arithmetic roofline): node visits
+// (two box tests each) and primitive tests by type.
+struct TraceWork {
+  unsigned int nodes = 0, quads = 0, spheres = 0, tris = 0;
+};
+
 __device__ __forceinline__ bool hit_prim(const float4* __restrict__ prims, int i, f3 o, f3 d, float tmax,
-                                         float& t) {
+                                         float& t, TraceWork& w) {
   const float4* q = prims + 4 * i;
   const int type = __float_as_int(q[0].w) & 3;
+  w.quads += type == PRIM_QUAD;
+  w.spheres += type == PRIM_SPHERE;
+  w.tris += type == PRIM_TRI;
   if (type == PRIM_QUAD) return hit_quad(q, o, d, tmax, t);
   if (type == PRIM_SPHERE) return hit_sphere(q, o, d, tmax, t);
   return hit_tri(q, o, d, tmax, t);
@@ -138,12 +147,12 @@ constexpr int STACK = 48;
 
 // Closest hit by stack traversal of the LBVH.  Ties in t go to the lower
 // primitive index, as in a brute-force scan in index order.
-__device__ __forceinline__ int trace_closest(const DevScene& s, f3 o, f3 d, float& t_best) {
+__device__ __forceinline__ int trace_closest(const DevScene& s, f3 o, f3 d, float& t_best, TraceWork& w) {
   t_best = __int_as_float(0x7f800000);
   int best = -1;
   if (s.n_prims == 1) {
     float t;
-    if (hit_prim(s.prims, 0, o, d, t_best, t)) { t_best = t; best = 0; }
+    if (hit_prim(s.prims, 0, o, d, t_best, t, w)) { t_best = t; best = 0; }
     return best;
   }
   const f3 inv = mk3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
@@ -153,6 +162,7 @@ __device__ __forceinline__ int trace_closest(const DevScene& s, f3 o, f3 d, floa
   // every internal node is visited at most once per ray
   for (int visits = 0; visits < s.n_prims; ++visits) {
     const BvhNode nd = s.nodes[node];
+    ++w.nodes;
     // admit boxes entered at t <= t_best (a tie may still win on index)
     const float tl = box_entry(nd.a, nd.b, o, inv, t_best);
     const float tr = box_entry(nd.c, nd.d, o, inv, t_best);
@@ -161,14 +171,14 @@ __device__ __forceinline__ int trace_closest(const DevScene& s, f3 o, f3 d, floa
     if (vl && cl < 0) {
       float t;
       const int p = ~cl;
-      if (hit_prim(s.prims, p, o, d, t_best * 1.0000002f + 1e-30f, t) &&
+      if (hit_prim(s.prims, p, o, d, t_best * 1.0000002f + 1e-30f, t, w) &&
           (t < t_best || (t == t_best && p < best))) { t_best = t; best = p; }
       vl = false;
     }
     if (vr && cr < 0) {
       float t;
       const int p = ~cr;
-      if (hit_prim(s.prims, p, o, d, t_best * 1.0000002f + 1e-30f, t) &&
+      if (hit_prim(s.prims, p, o, d, t_best * 1.0000002f + 1e-30f, t, w) &&
           (t < t_best || (t == t_best && p < best))) { t_best = t; best = p; }
       vr = false;
     }
@@ -190,25 +200,26 @@ __device__ __forceinline__ int trace_closest(const DevScene& s, f3 o, f3 d, floa
 }
 
 // Any hit with 0 < t < tmax.
-__device__ __forceinline__ bool trace_any(const DevScene& s, f3 o, f3 d, float tmax) {
+__device__ __forceinline__ bool trace_any(const DevScene& s, f3 o, f3 d, float tmax, TraceWork& w) {
   float t;
-  if (s.n_prims == 1) return hit_prim(s.prims, 0, o, d, tmax, t);
+  if (s.n_prims == 1) return hit_prim(s.prims, 0, o, d, tmax, t, w);
   const f3 inv = mk3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
   int stack[STACK];
   int sp = 0;
   int node = 0;
   for (int visits = 0; visits < s.n_prims; ++visits) {
     const BvhNode nd = s.nodes[node];
+    ++w.nodes;
     const float tl = box_entry(nd.a, nd.b, o, inv, tmax);
     const float tr = box_entry(nd.c, nd.d, o, inv, tmax);
     const int cl = __float_as_int(nd.a.w), cr = __float_as_int(nd.b.w);
     bool vl = tl <= tmax, vr = tr <= tmax;
     if (vl && cl < 0) {
-      if (hit_prim(s.prims, ~cl, o, d, tmax, t)) return true;
+      if (hit_prim(s.prims, ~cl, o, d, tmax, t, w)) return true;
       vl = false;
     }
     if (vr && cr < 0) {
-      if (hit_prim(s.prims, ~cr, o, d, tmax, t)) return true;
+      if (hit_prim(s.prims, ~cr, o, d, tmax, t, w)) return true;
       vr = false;
     }
     if (vl && vr) {
@@ -340,14 +351,25 @@ __device__ __forceinline__ float guide_bin_prob(const float* __restrict__ cdf, i
 __device__ __forceinline__ float guide_pdf(const float* __restrict__ cdf, f3 w) {
   return guide_bin_prob(cdf, guide_bin(w)) * (GUIDE_BINS / (4.0f * PI_F));
 }
-// first bin b with u < cdf[b] (the last bin if none)
+// First bin b with u < cdf[b] (the last bin if none).  The CDF is
+// non-decreasing, so that bin is the number of bins with cdf[b] <= u: count the
+// 16 row ends (16 independent loads), then the 16 bins of the row they select
+// (four float4 loads) -- two dependent memory round trips instead of the eight
+// of a binary search, with the same result.
 __device__ __forceinline__ int guide_pick(const float* __restrict__ cdf, float u) {
-  int lo = 0, hi = GUIDE_BINS - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (u < __ldg(cdf + mid)) hi = mid; else lo = mid + 1;
-  }
-  return lo;
+  float ends[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) ends[k] = __ldg(cdf + 16 * k + 15);
+  int row = 0;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) row += ends[k] <= u;
+  if (row >= 16) return GUIDE_BINS - 1;
+  const float4* r4 = reinterpret_cast<const float4*>(cdf + 16 * row);
+  const float4 a = __ldg(r4), b = __ldg(r4 + 1), c = __ldg(r4 + 2), d = __ldg(r4 + 3);
+  const int col = (a.x <= u) + (a.y <= u) + (a.z <= u) + (a.w <= u) + (b.x <= u) + (b.y <= u) + (b.z <= u) +
+                  (b.w <= u) + (c.x <= u) + (c.y <= u) + (c.z <= u) + (c.w <= u) + (d.x <= u) + (d.y <= u) +
+                  (d.z <= u) + (d.w <= u);
+  return 16 * row + (col < 16 ? col : 15);
 }
 __device__ __forceinline__ f3 guide_dir(int b, float u1, float u2) {
   const int iz = b >> 4, ip = b & 15;

@@ -73,13 +73,14 @@ struct DevScene {
 // SL[sbase[d], sbase[d] + slcount[d]) (a compacted work list), and SH0/SH1 are
 // written for them alone.
 constexpr int NR = 5, NV = 5, NSH = 3;
-constexpr int SLOT_BYTES = (NR + NV + 1) * 16 + 8;  // per ray slot
+constexpr int SLOT_BYTES = (NR + NV + 1) * 16 + 8 + 4;  // per ray slot
 constexpr int SHADOW_BYTES = NSH * 16 + 4;          // per shadow-ray slot
 struct Arena {
   float4* R[NR];
   float2* H;
   float4* V[NV];
   float4* S;
+  float* M;   // path multiplicity of the ray (product of the budgets that drew its path)
   float4* SH[NSH];
   unsigned int* SL;
   uint64_t cap;   // ray slots
@@ -100,6 +101,9 @@ struct DevCounters {
   unsigned long long shadow_entries;     // shadow rays of committed tiles
   unsigned long long shadow_traced;      // listed (traced) shadow rays of committed tiles
   unsigned long long wave_total[MAXD + 2];  // rays per depth wave of committed tiles
+  // traversal work of the closest-hit (0) and shadow (1) kernels: node visits,
+  // quad, sphere and triangle tests (every launch, committed or not)
+  unsigned long long trace_work[2][4];
   unsigned int overflow;       // this tile overflowed the arena
   unsigned int any_overflow;   // some tile of this iteration overflowed
   unsigned long long demand;   // rays the tile needed (may exceed the arena)
@@ -132,6 +136,7 @@ struct IterArgs {
   uint32_t seed, job, iteration;
   int mode, aware, collect, has_estimate;
   float clamp_lo, clamp_hi, outlier;
+  float max_mult;  // path multiplicity cap (0: none)
   int tile_begin, tile_end, tile_slot;
 };
 

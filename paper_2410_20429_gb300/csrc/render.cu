@@ -115,6 +115,21 @@ __device__ __forceinline__ int owner_lane(const int* incl, int k) {
   return lo;
 }
 
+// warp sum of a thread's traversal counters, one atomic per counter and warp
+__device__ __forceinline__ void flush_work(TraceWork w, unsigned long long* dst) {
+  unsigned long long v[4] = {w.nodes, w.quads, w.spheres, w.tris};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_xor_sync(FULL, v[k], off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (v[k]) atomicAdd(dst + k, v[k]);
+  }
+}
+
 __global__ void k_tile_init(DevCounters* ctr, unsigned long long n0) {
   const int t = threadIdx.x;
   if (t < MAXD + 2) {
@@ -164,6 +179,7 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_trace(const DevScene
   if (ctr->overflow) return;
   const Wave w = wave_of(ctr, a, d);
   const Rng rng{it.seed, it.job, it.iteration};
+  TraceWork tw;
   for (unsigned long long li = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; li < w.n;
        li += gridDim.x * (unsigned long long)blockDim.x) {
     const unsigned long long i = w.base + li;
@@ -179,9 +195,10 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_trace(const DevScene
     }
     float t = 0.0f;
     int prim = -2;  // -2: not traced, -1: traced and missed
-    if (alive) prim = trace_closest(s, o, dir, t);
+    if (alive) prim = trace_closest(s, o, dir, t, tw);
     a.H[i] = make_float2(t, __int_as_float(prim));
   }
+  flush_work(tw, c.ctr->trace_work[0]);
 }
 
 // ------------------------------------------------------------------ shade
@@ -189,7 +206,7 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_trace(const DevScene
 // structure of arrays [field][lane], read by the lanes that draw their samples.
 enum {
   C_XO = 0, C_NS = 3, C_WO = 6, C_MTYPE = 9, C_ALPHA = 10, C_COL = 11, C_CELL = 14, C_PX = 15, C_LIN = 16,
-  C_T = 18, C_B0 = 21, C_B1 = 22, C_B2 = 23, C_G0 = 24, C_FIELDS = 25
+  C_T = 18, C_B0 = 21, C_B1 = 22, C_B2 = 23, C_G0 = 24, C_MULT = 25, C_FIELDS = 26
 };
 struct ShadeWarpCtx {
   float f[C_FIELDS][32];
@@ -242,13 +259,14 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_shade(const DevScene
     float A = 1.0f, S_ind = 1.0f, bwN = 0.0f, invSb = 0.0f;
     uint64_t lin = 0;
     uint32_t px = 0, parent_cell = 0;
-    float th = 0.0f;
+    float th = 0.0f, mult = 1.0f;
     int prim = -2;
     if (active) {
       if (camera) {
         px = (uint32_t)(it.tile_begin + li);
         camera_ray(s, rng, px, o, dir);
       } else {
+        mult = a.M[i];
         const float4 r0 = a.R[0][i], r1 = a.R[1][i], r2 = a.R[2][i], r3 = a.R[3][i], r4 = a.R[4][i];
         o = xyz(r0);
         px = __float_as_uint(r0.w);
@@ -334,6 +352,8 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_shade(const DevScene
               b = fminf(fmaxf(b, it.clamp_lo), it.clamp_hi);
             }
           }
+          // path multiplicity cap: b <= max(clamp_lo, M / P)
+          if (on && it.max_mult > 0.0f) b = fminf(b, fmaxf(it.max_mult / mult, it.clamp_lo));
           beta[t] = b;
         }
         // Alg. 1: one uniform decides the rounding of every technique
@@ -422,6 +442,7 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_shade(const DevScene
       cx[C_B1 * 32 + lane] = beta[1];
       cx[C_B2 * 32 + lane] = beta[2];
       cx[C_G0 * 32 + lane] = __int_as_float(gam[0]);
+      cx[C_MULT * 32 + lane] = mult;
       ctx->incl_ext[lane] = ae.incl;
       ctx->incl_sh[lane] = as.incl;
     }
@@ -569,6 +590,7 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_shade(const DevScene
         a.R[3][j] = f4(cf, bwNv);
         a.R[4][j] = make_float4(__uint_as_float((uint32_t)clin), __uint_as_float((uint32_t)(clin >> 32)),
                                 __uint_as_float((uint32_t)vcell), cinvSb);
+        a.M[j] = cx[C_MULT * 32 + L] * bt;
       }
     }
     __syncwarp();  // the context is overwritten by the next chunk
@@ -585,14 +607,16 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_shadow(const DevScen
   // into the wave's shadow region (at most scount of them)
   const unsigned long long sb = ctr->sbase[d], sl = ctr->slcount[d];
   const unsigned long long n = sl < a.scap - sb ? sl : a.scap - sb;
+  TraceWork tw;
   for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < n;
        k += gridDim.x * (unsigned long long)blockDim.x) {
     const unsigned long long j = a.SL[sb + k];
     const float4 s0 = a.SH[0][j];
     if (!(s0.w > 0.0f)) continue;
     const float4 s1 = a.SH[1][j];
-    if (trace_any(s, xyz(s0), xyz(s1), s0.w)) a.SH[2][j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (trace_any(s, xyz(s0), xyz(s1), s0.w, tw)) a.SH[2][j] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
+  flush_work(tw, c.ctr->trace_work[1]);
 }
 
 // ---------------------------------------------------------------- reverse
@@ -799,21 +823,21 @@ size_t shade_smem(int threads) { return (size_t)(threads / 32) * sizeof(ShadeWar
 // Register-cap variants of every wave kernel: variant v is compiled with
 // __launch_bounds__(256, MINB) for MINB = 1 (the compiler's choice), or a cap
 // that lets more blocks share an SM (shade and reverse: 80 and 64 registers;
-// trace and shadow: 40 registers), trading spills for occupancy.
+// trace and shadow: 64 and 40 registers), trading spills for occupancy.
 using TraceFn = void (*)(const DevScene, const DevCache, const Arena, const IterArgs, const int);
 using ShadowFn = void (*)(const DevScene, const DevCache, const Arena, const int);
-TraceFn trace_fn(int v) { return v == 1 ? k_trace<6> : k_trace<1>; }
+TraceFn trace_fn(int v) { return v == 2 ? k_trace<6> : (v == 1 ? k_trace<4> : k_trace<1>); }
 TraceFn shade_fn(int v) { return v == 2 ? k_shade<4> : (v == 1 ? k_shade<3> : k_shade<1>); }
-ShadowFn shadow_fn(int v) { return v == 1 ? k_shadow<6> : k_shadow<1>; }
+ShadowFn shadow_fn(int v) { return v == 2 ? k_shadow<6> : (v == 1 ? k_shadow<4> : k_shadow<1>); }
 TraceFn reverse_fn(int v) { return v == 2 ? k_reverse<4> : (v == 1 ? k_reverse<3> : k_reverse<1>); }
 
 }  // namespace
 
-int wave_variants(int kernel) { return (kernel == WK_SHADE || kernel == WK_REVERSE) ? 3 : 2; }
+int wave_variants(int) { return 3; }
 int wave_variant_registers(int kernel, int v) {
   if (v == 0) return 0;
   if (kernel == WK_SHADE || kernel == WK_REVERSE) return v == 1 ? 80 : 64;
-  return 40;
+  return v == 1 ? 64 : 40;
 }
 
 cudaError_t wave_occupancy(const int threads[WAVE_KERNELS], const int variant[WAVE_KERNELS],

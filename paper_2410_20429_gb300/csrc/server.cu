@@ -19,6 +19,12 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+// Served jobs bound the splitting along a path (mars_iter_params.max_multiplicity):
+// a dark pixel in a job's first MARS iterations, whose estimate comes from a
+// few warm-up samples, could otherwise split at the clamp (20) at every bounce
+// and hold up the GPU for every other job.
+constexpr float kServeMultiplicity = 100.0f;
+
 struct Job {
   uint64_t id = 0;
   mars::SceneDescCopy scene;
@@ -64,8 +70,16 @@ struct mars_server {
     mars_status rc = MARS_OK;
     std::string msg;
     const int64_t npx = (int64_t)j->scene.desc.width * j->scene.desc.height;
-    std::vector<float> img(3 * (size_t)npx), acc(3 * (size_t)npx, 0.0f);
+    // the cache's running sum holds every iteration's image: the job's mean
+    // image over the iterations after warm-up is (sum at the end - sum after
+    // warm-up) / kept, read back twice per job instead of once per iteration
+    std::vector<float> warm(3 * (size_t)npx, 0.0f), acc(3 * (size_t)npx, 0.0f);
     int kept = 0;
+    auto read_sum = [&](std::vector<float>& dst) {
+      mars_cache_state cs{};
+      cs.run_sum = dst.data();
+      return mars::get_state_impl(ca, &cs, st);
+    };
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
       rc = MARS_ERR_CUDA;
       msg = "stream create failed";
@@ -83,30 +97,31 @@ struct mars_server {
       p.clamp_hi = 20.0f;
       p.outlier = 50.0f;
       p.collect = 1;
-      p.image_on_host = 1;
+      p.max_multiplicity = kServeMultiplicity;
+      p.image_on_host = 0;
       p.update_estimate = 1;
       const auto a = Clock::now();
       mars_iter_stats ist{};
-      rc = mars::render_iteration_impl(ca, &p, img.data(), &ist, st);
+      rc = mars::render_iteration_impl(ca, &p, nullptr, &ist, st);
       if (rc == MARS_OK) rc = mars::update_counts_impl(ca, st);
       if (rc == MARS_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = MARS_ERR_CUDA;
       const double ms = std::chrono::duration<double, std::milli>(Clock::now() - a).count();
       if (rc != MARS_OK) break;
-      if (it >= j->warmup) {
-        for (size_t k = 0; k < acc.size(); ++k) acc[k] += img[k];
-        ++kept;
-      }
+      if (it >= j->warmup) ++kept;
+      if (it + 1 == j->warmup && j->warmup < j->iterations) rc = read_sum(warm);
       std::lock_guard<std::mutex> lk(mu);
       j->iter_ms.push_back(ms);
       j->vertices += ist.vertices;
       j->done_iters = it + 1;
     }
+    if (rc == MARS_OK && kept > 0) {
+      rc = read_sum(acc);
+      for (size_t k = 0; k < acc.size(); ++k) acc[k] = (acc[k] - warm[k]) / (float)kept;
+    }
     if (rc != MARS_OK) msg = mars_last_error_string();
     if (ca) mars::cache_destroy_impl(ca);
     if (sc) mars::scene_destroy_impl(sc);
     if (st) cudaStreamDestroy(st);
-    if (kept > 0)
-      for (float& v : acc) v /= (float)kept;
     std::lock_guard<std::mutex> lk(mu);
     j->image.swap(acc);
     j->error = rc;

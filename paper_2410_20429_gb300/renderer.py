@@ -98,7 +98,7 @@ class Cache:
 
     def render_iteration(self, image, *, seed=0, job=0, iteration=0, mode=A.MARS_MODE_WARMUP,
                          weights=A.MARS_WEIGHTS_AWARE, clamp_lo=0.05, clamp_hi=20.0, outlier=50.0, collect=True,
-                         update_estimate=True, profile=False, stream=None) -> dict:
+                         update_estimate=True, profile=False, max_multiplicity=0.0, stream=None) -> dict:
         """Render one iteration into ``image``: a CUDA float32 tensor with
         height*width*3 elements, or a host numpy float32 array of that size (the
         library then copies the image back)."""
@@ -116,7 +116,7 @@ class Cache:
             ptr = image.data_ptr()
         p = A.mars_iter_params(int(seed), int(job), int(iteration), int(mode), int(weights), float(clamp_lo),
                                float(clamp_hi), float(outlier), int(bool(collect)), int(on_host),
-                               int(bool(update_estimate)), int(bool(profile)))
+                               int(bool(update_estimate)), int(bool(profile)), float(max_multiplicity))
         st = A.mars_iter_stats()
         A.check(self._lib.mars_render_iteration(self.handle, ct.byref(p), ptr, ct.byref(st), _stream_handle(stream)),
                 "mars_render_iteration")
@@ -128,7 +128,8 @@ class Cache:
                 "image_ms": st.image_ms, "wave_entries": st.wave_entries, "shadow_entries": st.shadow_entries,
                 "shadow_traced": st.shadow_traced,
                 "wave_ms": [[st.wave_ms[k][d] for d in range(self.max_depth)] for k in range(4)],
-                "wave_rays": [st.wave_rays[d] for d in range(self.max_depth)]}
+                "wave_rays": [st.wave_rays[d] for d in range(self.max_depth)],
+                "trace_work": [[st.trace_work[k][q] for q in range(4)] for k in range(2)]}
 
     def get_launch(self) -> dict:
         """Launch shape of the wave kernels (trace, shade, shadow, reverse)."""
@@ -146,11 +147,11 @@ class Cache:
         A.check(self._lib.mars_cache_set_launch(self.handle, ct.byref(cfg)), "mars_cache_set_launch")
 
     def autotune(self, *, seed=0, job=0, iteration=0, mode=A.MARS_MODE_WARMUP, weights=A.MARS_WEIGHTS_AWARE,
-                 clamp_lo=0.05, clamp_hi=20.0, outlier=50.0, repeats=2, stream=None) -> dict:
+                 clamp_lo=0.05, clamp_hi=20.0, outlier=50.0, repeats=2, max_multiplicity=0.0, stream=None) -> dict:
         """Pick the fastest launch shape of every wave kernel on this iteration
         (rendered without statistics, so the learned state is unchanged)."""
         p = A.mars_iter_params(int(seed), int(job), int(iteration), int(mode), int(weights), float(clamp_lo),
-                               float(clamp_hi), float(outlier), 0, 0, 0, 1)
+                               float(clamp_hi), float(outlier), 0, 0, 0, 1, float(max_multiplicity))
         cfg = A.mars_launch_config()
         A.check(self._lib.mars_cache_autotune(self.handle, ct.byref(p), int(repeats), ct.byref(cfg),
                                               _stream_handle(stream)), "mars_cache_autotune")
@@ -254,6 +255,9 @@ class Server:
             ptr = img.ctypes.data
         A.check(self._lib.mars_poll(self.handle, ct.c_uint64(job_id), ct.byref(s), ptr), "mars_poll")
         st = {f: getattr(s, f) for f, _ in A.mars_job_status._fields_}
+        if s.state == A.MARS_JOB_FAILED:
+            msg = self._lib.mars_last_error_string()
+            st["message"] = msg.decode() if msg else ""
         return st, img
 
     def latencies(self, job_id: int) -> np.ndarray:

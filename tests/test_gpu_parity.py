@@ -104,6 +104,29 @@ def test_box_mars_iteration_parity(mars, orc, weights):
         assert g_st["mean_beta"][t] == pytest.approx(o.counters[3 + t] / o.counters[2], rel=1e-3)
 
 
+def test_multiplicity_cap_parity(mars, orc):
+    """Teacher-forced MARS iteration with large count factors (splitting at the
+    clamp) and a path multiplicity cap that binds: the capped budgets, the
+    children's multiplicities and everything downstream agree with the oracle."""
+    cfg = W.config_box(48, 40)
+    scene, cache = _make(mars, cfg)
+    q_rr, q_s, valid = W.random_count_fields(cfg.n_cells, seed=111, lo=2.0, hi=30.0)
+    est = W.random_pixel_estimate(cfg.scene.n_pixels, seed=112, lo=0.02, hi=0.3)
+    cache.set_state(q_rr=q_rr, q_s=q_s, valid=valid, pixel_estimate=est, has_estimate=True, n_iterations=1)
+    import torch
+    img = torch.zeros(cache.n_pixels * 3, dtype=torch.float32, device="cuda")
+    g_st = cache.render_iteration(img, seed=6, iteration=2, mode=1, update_estimate=False, max_multiplicity=6.0)
+    torch.cuda.synchronize()
+    g_img = img.cpu().numpy().reshape(-1, 3).astype(np.float64)
+    g_state = cache.get_state()
+    o = orc.render(cfg.scene, grid_n=cfg.grid_n, techniques=cfg.techniques, max_depth=cfg.max_depth, iteration=2,
+                   seed=6, mode=orc.MODE_MARS, q_rr=q_rr, q_s=q_s, valid=valid, est=est, max_mult=6.0)
+    _check(g_img, o.image, g_state, o, g_st, "box MARS, multiplicity cap")
+    free = orc.render(cfg.scene, grid_n=cfg.grid_n, techniques=cfg.techniques, max_depth=cfg.max_depth,
+                      iteration=2, seed=6, mode=orc.MODE_MARS, q_rr=q_rr, q_s=q_s, valid=valid, est=est)
+    assert free.vertices > 2 * o.vertices   # the cap binds
+
+
 def test_guided_room_crop_parity(mars, orc):
     """Three techniques (BSDF, NEE, guided) on a 64 x 64 render of the guided room
     with 16 spheres, GGX and Lambert, random guide CDFs and random counts."""

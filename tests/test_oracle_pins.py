@@ -397,6 +397,36 @@ def test_furnace_closed_form(orc, albedo, D, counts):
     assert abs(m - expected) < 3.5 * se + 1e-9
 
 
+@pytest.mark.parametrize("M", [1.5, 4.0])
+def test_multiplicity_cap_keeps_the_furnace_and_bounds_the_tree(orc, M):
+    """Path multiplicity cap: budgets limited to max(clamp_lo, M / P).  The
+    furnace expectation is unchanged (it is one more count field), and the
+    traced vertices per pixel and depth stay near M even where the uncapped
+    field splits at every bounce."""
+    albedo, D = 0.8, 5
+    sc = W.furnace_scene(albedo=albedo, radiance=1.5, width=8, height=8)
+    cells = 4 ** 3
+    q_rr = np.full((cells, 3, 3), 40.0, np.float32)   # beta = 20 (the clamp) everywhere
+    q_s = np.full((cells, 3, 3), 40.0, np.float32)
+    valid = np.ones((cells, 3), np.uint8)
+    est = np.full((sc.n_pixels, 3), 0.1, np.float32)
+    kw = dict(grid_n=4, techniques=W.TECH_BSDF | W.TECH_NEE, max_depth=D, mode=orc.MODE_MARS, q_rr=q_rr,
+              q_s=q_s, valid=valid, est=est, max_mult=M)
+    vals, verts = [], []
+    for it in range(40):
+        r = orc.render(sc, iteration=it, **kw)
+        vals.append(r.image.mean())
+        verts.append(r.vertices / sc.n_pixels)
+    m, se = _mean_and_sem(vals)
+    expected = 1.5 * (1 - albedo ** D) / (1 - albedo)
+    assert abs(m - expected) < 3.5 * se + 1e-9
+    # expected traced vertices per pixel: at most 1 + M per later depth (and
+    # at least the camera ray)
+    assert np.mean(verts) <= 1 + (D - 1) * M * 1.1
+    uncapped = orc.render(sc, iteration=0, **dict(kw, max_mult=0.0))
+    assert uncapped.vertices / sc.n_pixels > 20 * np.mean(verts)
+
+
 @pytest.mark.parametrize("weights", [0, 1])
 @pytest.mark.parametrize("counts", ["beta1", "random"])
 def test_polygon_light_irradiance_closed_form(orc, weights, counts):
