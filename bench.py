@@ -276,6 +276,13 @@ def run_mars(args):
             per_kernel[k] = {"bound": "hbm", "achieved": round(a, 1), "peak": hbm, "unit": "GB/s",
                              "frac": round(a / hbm, 4), "per_launch": int(kb[k] / max(nlaunch[k], 1)),
                              "launch_ms": round(ms_launch, 4)}
+    tw = [[sum(s["trace_work"][k][q] for s in sts) for q in range(4)] for k in range(2)]
+    n_closest = max(sum(s["wave_entries"] for s in sts), 1)
+    n_shadow = max(sum(s["shadow_traced"] for s in sts), 1)
+    per_kernel["k_trace"]["per_ray"] = {"nodes": round(tw[0][0] / n_closest, 2),
+                                        "prim_tests": round(sum(tw[0][1:]) / n_closest, 2)}
+    per_kernel["k_shadow"]["per_ray"] = {"nodes": round(tw[1][0] / n_shadow, 2),
+                                         "prim_tests": round(sum(tw[1][1:]) / n_shadow, 2)}
     dom = max(kms, key=kms.get)
     d0 = per_kernel[dom]
     roofline = {"kernel": dom, "bound": d0["bound"], "achieved": d0["achieved"], "peak": d0["peak"],

@@ -1,7 +1,7 @@
 // scene.cu -- linear BVH construction on the device (Karras, "Maximizing
 // Parallelism in the Construction of BVHs, Octrees, and k-d Trees", HPG 2012):
-// 30-bit Morton codes of the primitive centroids with the primitive index as a
-// tie-breaking low word, a bitonic sort, one thread per internal node to find
+// 30-bit Morton codes of the primitive centroids (above a size-class bit) with
+// the primitive index as a tie-breaking low word, a bitonic sort, one thread per internal node to find
 // its key range and split, and a bottom-up pass that fills the child bounds
 // (the second thread to reach a node computes it).
 #include <string>
@@ -20,9 +20,13 @@ __device__ __forceinline__ uint32_t spread10(uint32_t v) {
   return v;
 }
 
-// keys[i] = morton(centroid) << 32 | i ; padding keys are all ones
+// keys[i] = large << 62 | morton(centroid) << 32 | i ; padding keys are all ones.
+// A primitive whose box spans at least half the scene's largest extent (a wall,
+// a floor) is "large": the flag bit makes the hierarchy's first split separate
+// the large primitives from the small ones, so no subtree of small primitives
+// carries a box inflated by a wall.
 __global__ void k_morton(const float4* __restrict__ box, int n, int npow, float lo0, float lo1, float lo2,
-                         float ie0, float ie1, float ie2, unsigned long long* keys) {
+                         float ie0, float ie1, float ie2, float large_extent, unsigned long long* keys) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= npow) return;
   if (i >= n) {
@@ -39,7 +43,9 @@ __global__ void k_morton(const float4* __restrict__ box, int n, int npow, float 
     q[a] = (uint32_t)f;
   }
   const uint32_t m = (spread10(q[0]) << 2) | (spread10(q[1]) << 1) | spread10(q[2]);
-  keys[i] = ((unsigned long long)m << 32) | (unsigned long long)i;
+  const float span = fmaxf(fmaxf(bhi.x - blo.x, bhi.y - blo.y), bhi.z - blo.z);
+  const unsigned long long large = span >= large_extent ? 1ull : 0ull;
+  keys[i] = (large << 62) | ((unsigned long long)m << 32) | (unsigned long long)i;
 }
 
 __global__ void k_bitonic(unsigned long long* keys, int npow, int j, int k) {
@@ -160,7 +166,9 @@ cudaError_t build_bvh(const float4* d_box, int n, const float lo[3], const float
     cudaMemsetAsync(flags, 0, sizeof(unsigned int) * (n - 1), st);
     const int TB = 256;
     const float ie[3] = {1.0f / ext[0], 1.0f / ext[1], 1.0f / ext[2]};
-    k_morton<<<(npow + TB - 1) / TB, TB, 0, st>>>(d_box, n, npow, lo[0], lo[1], lo[2], ie[0], ie[1], ie[2], keys);
+    const float emax = fmaxf(fmaxf(ext[0], ext[1]), ext[2]);
+    k_morton<<<(npow + TB - 1) / TB, TB, 0, st>>>(d_box, n, npow, lo[0], lo[1], lo[2], ie[0], ie[1], ie[2],
+                                                  0.5f * emax, keys);
     for (int k = 2; k <= npow; k <<= 1)
       for (int j = k >> 1; j > 0; j >>= 1) k_bitonic<<<(npow + TB - 1) / TB, TB, 0, st>>>(keys, npow, j, k);
     k_hierarchy<<<(n - 1 + TB - 1) / TB, TB, 0, st>>>(keys, n, child, pint, pleaf);
