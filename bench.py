@@ -342,6 +342,7 @@ def run_mars(args):
         line["precision"] = precision_study(cfg, cache, seed, it, stream)
     if rank == 0 and not args.no_efficiency:
         line["efficiency"] = efficiency(args, M, cfg, scene, cache, seed, it, stream)
+        line["efficiency_box"] = box_efficiency(args, M, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg, args.cpu_seconds)
     if world > 1:
@@ -379,7 +380,10 @@ def serving(args):
                 if st["state"] in (M.MARS_JOB_DONE, M.MARS_JOB_FAILED):
                     done[j] = st
         time.sleep(0.005)
-    lat = np.concatenate([srv.latencies(j) for j in ids])
+    lats = [srv.latencies(j) for j in ids]
+    lat = np.concatenate(lats)
+    slow = sorted(((float(l.max()), int(l.argmax()), r["scene"].width, len(r["scene"].spheres), r["iterations"])
+                   for l, r in zip(lats, reqs) if l.size), reverse=True)[:5]
     sts = [done[j] for j in ids]
     job_s = np.array([s["end_s"] - s["submit_s"] for s in sts])
     span = max(s["end_s"] for s in sts) - min(s["submit_s"] for s in sts)
@@ -398,6 +402,8 @@ def serving(args):
             "job_s_p99": round(float(np.percentile(job_s, 99)), 3),
             "throughput_mvertices_s": round(verts / span / 1e6, 2), "span_s": round(span, 2),
             "max_resident": peak,
+            "slowest_iterations": [{"ms": round(a, 1), "iteration": b, "resolution": c, "spheres": d2,
+                                    "iterations": e} for a, b, c, d2, e in slow],
             "failures": sorted(set(s.get("message", "")[:120] for s in sts if s["state"] != M.MARS_JOB_DONE))[:3]}
 
 
@@ -461,6 +467,42 @@ def efficiency(args, M, cfg, scene, cache, seed, it0, stream):
             "protocol": "counts learned over warm-up + timed steps, then frozen; both estimators render "
                         f"{args.eff_spp} fresh iterations; reference = fixed-count MIS, {args.ref_spp} spp, "
                         "other random numbers"}
+
+
+def box_efficiency(args, M, stream):
+    """The box workload (64 x 64, D = 5, BSDF + NEE, 8^3 grid; the paper's own
+    failure case, where MARS's overhead can dominate): 1 warm-up and 3 MARS
+    fixed-point iterations learn the counts, then the same equal-time comparison
+    with fixed-count MIS as for the main workload, plus the device time of one
+    MARS iteration (launch-bound at this size)."""
+    import torch
+    cfg = W.config_box(64, 64)
+    scene = M.Scene(cfg.scene, stream=stream)
+    cache = M.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, stream=stream)
+    img = torch.zeros(cfg.scene.n_pixels * 3, dtype=torch.float32, device="cuda")
+    it = 0
+    for k in range(cfg.iterations):
+        mode = M.MARS_MODE_WARMUP if k < cfg.warmup else M.MARS_MODE_MARS
+        cache.render_iteration(img, seed=2024, iteration=it, mode=mode, update_estimate=True, stream=stream)
+        cache.update_counts(stream=stream)
+        it += 1
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    n = 20
+    verts = 0
+    for k in range(n):
+        st = cache.render_iteration(img, seed=2024, iteration=100 + k, mode=M.MARS_MODE_MARS, collect=False,
+                                    update_estimate=False, stream=stream)
+        verts += st["vertices"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    eff = efficiency(args, M, cfg, scene, cache, 2024, it, stream)
+    eff["workload"] = cfg.name
+    eff["iteration_ms"] = round(ms, 4)
+    eff["mvertices_s"] = round(verts / n / (ms * 1e-3) / 1e6, 2)
+    return eff
 
 
 def cpu_baseline(cfg, seconds, reference_arm=False):

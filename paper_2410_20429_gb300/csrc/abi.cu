@@ -378,6 +378,89 @@ mars_status scene_create_impl(const mars_scene_desc* d, cudaStream_t st, mars_sc
       return MARS_ERR_CUDA;
     }
   }
+  if (n >= 2) {
+    // collapse the binary hierarchy into 4-wide nodes: a node's children are
+    // grown by replacing the internal child with the largest box surface by its
+    // two children until there are four or only leaves remain
+    std::vector<BvhNode> bin(n - 1);
+    if ((e = cudaMemcpyAsync(bin.data(), s->d_nodes, sizeof(BvhNode) * (n - 1), cudaMemcpyDeviceToHost, st)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+      return cleanup(e, "BVH readback");
+    struct Ch {
+      int id;              // >= 0 binary internal node, < 0 ~primitive
+      float lo[3], hi[3];
+    };
+    auto kids = [&](int k, Ch out[2]) {
+      const BvhNode& b = bin[k];
+      int l, r;
+      std::memcpy(&l, &b.a.w, sizeof(int));
+      std::memcpy(&r, &b.b.w, sizeof(int));
+      out[0] = {l, {b.a.x, b.a.y, b.a.z}, {b.b.x, b.b.y, b.b.z}};
+      out[1] = {r, {b.c.x, b.c.y, b.c.z}, {b.d.x, b.d.y, b.d.z}};
+    };
+    auto area = [](const Ch& c) {
+      const double dx = c.hi[0] - c.lo[0], dy = c.hi[1] - c.lo[1], dz = c.hi[2] - c.lo[2];
+      return dx * dy + dy * dz + dz * dx;
+    };
+    std::vector<Bvh4Node> n4;
+    n4.reserve(n);
+    std::vector<std::pair<int, int>> todo;  // (binary node, BVH4 slot)
+    n4.emplace_back();
+    todo.emplace_back(0, 0);
+    while (!todo.empty()) {
+      const auto [bk, slot] = todo.back();
+      todo.pop_back();
+      Ch set[4];
+      int m = 2;
+      kids(bk, set);
+      while (m < 4) {
+        int best = -1;
+        double ba = -1.0;
+        for (int k = 0; k < m; ++k)
+          if (set[k].id >= 0 && area(set[k]) > ba) { ba = area(set[k]); best = k; }
+        if (best < 0) break;
+        Ch two[2];
+        kids(set[best].id, two);
+        set[best] = two[0];
+        set[m++] = two[1];
+      }
+      float lo[3][4], hi[3][4];
+      int ch[4];
+      for (int k = 0; k < 4; ++k) {
+        for (int a = 0; a < 3; ++a) {
+          lo[a][k] = k < m ? set[k].lo[a] : 0.0f;   // empty slot (child BVH4_EMPTY): never visited
+          hi[a][k] = k < m ? set[k].hi[a] : 0.0f;
+        }
+        if (k >= m) {
+          ch[k] = BVH4_EMPTY;
+        } else if (set[k].id < 0) {
+          ch[k] = set[k].id;
+        } else {
+          ch[k] = (int)n4.size();
+          n4.emplace_back();
+          todo.emplace_back(set[k].id, ch[k]);
+        }
+      }
+      Bvh4Node& nd = n4[slot];
+      nd.lox = make_float4(lo[0][0], lo[0][1], lo[0][2], lo[0][3]);
+      nd.loy = make_float4(lo[1][0], lo[1][1], lo[1][2], lo[1][3]);
+      nd.loz = make_float4(lo[2][0], lo[2][1], lo[2][2], lo[2][3]);
+      nd.hix = make_float4(hi[0][0], hi[0][1], hi[0][2], hi[0][3]);
+      nd.hiy = make_float4(hi[1][0], hi[1][1], hi[1][2], hi[1][3]);
+      nd.hiz = make_float4(hi[2][0], hi[2][1], hi[2][2], hi[2][3]);
+      nd.child = make_int4(ch[0], ch[1], ch[2], ch[3]);
+      nd.pad = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if ((e = dev_alloc((void**)&s->d_nodes4, sizeof(Bvh4Node) * n4.size(), st)) != cudaSuccess)
+      return cleanup(e, "scene alloc");
+    if ((e = cudaMemcpyAsync(s->d_nodes4, n4.data(), sizeof(Bvh4Node) * n4.size(), cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+      return cleanup(e, "BVH4 upload");
+    s->ds.n_nodes4 = (int)n4.size();
+  }
+  s->ds.nodes4 = s->d_nodes4;
   s->ds.prims = s->d_prims;
   s->ds.nodes = s->d_nodes;
   s->ds.mats = s->d_mats;
@@ -398,6 +481,7 @@ void scene_destroy_impl(mars_scene* s) {
   dev_free(s->d_prims, st);
   dev_free(s->d_boxes, st);
   dev_free(s->d_nodes, st);
+  dev_free(s->d_nodes4, st);
   dev_free(s->d_mats, st);
   dev_free(s->d_lights, st);
   delete s;
@@ -533,6 +617,13 @@ mars_status cache_create_impl(const mars_scene* s, const mars_cache_desc* d, cud
   c->dc.ctr = c->d_ctr;
   c->dc.tile_status = c->d_tile_status;
   c->device_bytes = cache_footprint(cells, pixels, d->max_depth, d->techniques, cap);
+  if ((e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking)) != cudaSuccess)
+    return cleanup(e, "side stream");
+  for (int k = 0; k <= d->max_depth; ++k) {
+    cudaEvent_t ev;
+    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return cleanup(e, "event");
+    c->sync_events.push_back(ev);
+  }
   {
     const int threads[WAVE_KERNELS] = {128, 128, 128, 128};
     const int bps[WAVE_KERNELS] = {0, 0, 0, 0};
@@ -597,6 +688,11 @@ void cache_destroy_impl(mars_cache* c) {
   pinned_release(c->h_ctr, sizeof(DevCounters));
   pinned_release(c->h_tile_status, sizeof(unsigned int) * c->max_tiles);
   for (cudaEvent_t ev : c->events) cudaEventDestroy(ev);
+  for (cudaEvent_t ev : c->sync_events) cudaEventDestroy(ev);
+  if (c->side) {
+    cudaStreamSynchronize(c->side);
+    cudaStreamDestroy(c->side);
+  }
   delete c;
 }
 
@@ -680,7 +776,7 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
   double trace_ms = 0.0, shade_ms = 0.0, shadow_ms = 0.0, reverse_ms = 0.0, image_ms = 0.0;
   float wave_ms[WAVE_KERNELS][MAXD] = {};
   const int D = c->max_depth;
-  const int per_tile = 4 * D + 1;
+  const int per_tile = 5 * D + 2;
   float* dev_out = p->image_on_host ? nullptr : image;
   while (true) {
     if (p->profile) {
@@ -697,7 +793,7 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
       it.tile_slot = (int)t;
       cudaEvent_t* ev = p->profile ? c->events.data() + t * per_tile : nullptr;
       const WaveLaunch L = wave_grids(c, it.tile_end - it.tile_begin);
-      if ((e = launch_tile(s->ds, c->dc, c->arena, it, L, st, ev)) != cudaSuccess)
+      if ((e = launch_tile(s->ds, c->dc, c->arena, it, L, st, c->side, c->sync_events.data(), ev)) != cudaSuccess)
         return poison(c, e, "render launch");
       launches += (uint32_t)tile_launches(D, c->techniques);
       wave_launches += (uint32_t)D;
@@ -724,20 +820,23 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
       for (size_t t = 0; t < tiles.size(); ++t) {
         cudaEvent_t* ev = c->events.data() + t * per_tile;
         float ms = 0.f;
+        // event layout: see launch_tile
         for (int d = 1; d <= D; ++d) {
-          cudaEventElapsedTime(&ms, ev[3 * (d - 1)], ev[3 * (d - 1) + 1]);
+          cudaEventElapsedTime(&ms, ev[2 * (d - 1)], ev[2 * (d - 1) + 1]);
           trace_ms += ms;
           wave_ms[WK_TRACE][d - 1] += ms;
-          cudaEventElapsedTime(&ms, ev[3 * (d - 1) + 1], ev[3 * (d - 1) + 2]);
+          cudaEventElapsedTime(&ms, ev[2 * (d - 1) + 1], ev[2 * (d - 1) + 2]);
           shade_ms += ms;
           wave_ms[WK_SHADE][d - 1] += ms;
-          cudaEventElapsedTime(&ms, ev[3 * (d - 1) + 2], ev[3 * (d - 1) + 3]);
-          shadow_ms += ms;
-          wave_ms[WK_SHADOW][d - 1] += ms;
+          if (d <= D - 1 && (c->techniques & MARS_TECH_NEE)) {
+            cudaEventElapsedTime(&ms, ev[2 * D + 2 * (d - 1) + 1], ev[2 * D + 2 * (d - 1) + 2]);
+            shadow_ms += ms;
+            wave_ms[WK_SHADOW][d - 1] += ms;
+          }
         }
         // the k-th reverse launch (k = 1..D) handles wave D - k + 1
         for (int k = 1; k <= D; ++k) {
-          cudaEventElapsedTime(&ms, ev[3 * D + k - 1], ev[3 * D + k]);
+          cudaEventElapsedTime(&ms, k == 1 ? ev[5 * D + 1] : ev[4 * D + k - 1], ev[4 * D + k]);
           reverse_ms += ms;
           wave_ms[WK_REVERSE][D - k] += ms;
         }

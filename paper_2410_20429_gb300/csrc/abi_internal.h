@@ -63,6 +63,7 @@ struct mars_scene {
   float4* d_prims = nullptr;
   float4* d_boxes = nullptr;
   mars::BvhNode* d_nodes = nullptr;
+  mars::Bvh4Node* d_nodes4 = nullptr;
   float4* d_mats = nullptr;
   float4* d_lights = nullptr;
   uint64_t device_bytes = 0;
@@ -100,6 +101,8 @@ struct mars_cache {
   uint64_t device_bytes = 0;
   std::vector<cudaEvent_t> events;  // profiling events, grown on demand
   cudaStream_t last_stream = nullptr;  // the stream of the last call that used the cache
+  cudaStream_t side = nullptr;         // second stream: NEE shadow rays overlap the next waves
+  std::vector<cudaEvent_t> sync_events;  // D + 1 cross-stream events (no timing)
   mars::WaveLaunch launch{};        // launch shape of the per-wave kernels
   int blocks_per_sm[mars::WAVE_KERNELS] = {0, 0, 0, 0};  // 0: occupancy maximum
   // wave sizes of the last single-tile iteration (rays per depth wave, NEE

@@ -199,6 +199,121 @@ __device__ __forceinline__ int trace_closest(const DevScene& s, f3 o, f3 d, floa
   return best;
 }
 
+// Closest-hit traversal as a resumable state: one call of closest_step visits
+// one node, so a warp can refill lanes whose ray has finished with new rays
+// while the others keep traversing.  Same visiting rule, culling and tie-break
+// as trace_closest, hence the same result.
+struct ClosestState {
+  f3 o, d, inv;
+  float t_best;
+  int best, node, sp, visits;
+};
+
+__device__ __forceinline__ void closest_begin(ClosestState& q, f3 o, f3 d) {
+  q.o = o;
+  q.d = d;
+  q.inv = mk3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
+  q.t_best = __int_as_float(0x7f800000);
+  q.best = -1;
+  q.node = 0;
+  q.sp = 0;
+  q.visits = 0;
+}
+
+// returns false once the traversal has finished (result in t_best, best)
+__device__ __forceinline__ bool closest_step(const DevScene& s, ClosestState& q, int* stack, TraceWork& w) {
+  const BvhNode nd = s.nodes[q.node];
+  ++w.nodes;
+  const float tl = box_entry(nd.a, nd.b, q.o, q.inv, q.t_best);
+  const float tr = box_entry(nd.c, nd.d, q.o, q.inv, q.t_best);
+  const int cl = __float_as_int(nd.a.w), cr = __float_as_int(nd.b.w);
+  bool vl = tl <= q.t_best, vr = tr <= q.t_best;
+  if (vl && cl < 0) {
+    float t;
+    const int p = ~cl;
+    if (hit_prim(s.prims, p, q.o, q.d, q.t_best * 1.0000002f + 1e-30f, t, w) &&
+        (t < q.t_best || (t == q.t_best && p < q.best))) { q.t_best = t; q.best = p; }
+    vl = false;
+  }
+  if (vr && cr < 0) {
+    float t;
+    const int p = ~cr;
+    if (hit_prim(s.prims, p, q.o, q.d, q.t_best * 1.0000002f + 1e-30f, t, w) &&
+        (t < q.t_best || (t == q.t_best && p < q.best))) { q.t_best = t; q.best = p; }
+    vr = false;
+  }
+  if (vl && vr) {
+    const bool lfirst = tl <= tr;
+    if (q.sp < STACK) stack[q.sp++] = lfirst ? cr : cl;
+    q.node = lfirst ? cl : cr;
+  } else if (vl) {
+    q.node = cl;
+  } else if (vr) {
+    q.node = cr;
+  } else {
+    if (q.sp == 0) return false;
+    q.node = stack[--q.sp];
+  }
+  return ++q.visits < s.n_prims;
+}
+
+// Entry distances of the four child boxes of a 4-wide node against [0, tmax]
+// (NaN for a miss or an empty slot), by the same slab arithmetic as box_entry.
+__device__ __forceinline__ void box4_entry(const Bvh4Node& nd, f3 o, f3 inv, float tmax, float t[4]) {
+  const float lx[4] = {nd.lox.x, nd.lox.y, nd.lox.z, nd.lox.w}, ly[4] = {nd.loy.x, nd.loy.y, nd.loy.z, nd.loy.w};
+  const float lz[4] = {nd.loz.x, nd.loz.y, nd.loz.z, nd.loz.w}, hx[4] = {nd.hix.x, nd.hix.y, nd.hix.z, nd.hix.w};
+  const float hy[4] = {nd.hiy.x, nd.hiy.y, nd.hiy.z, nd.hiy.w}, hz[4] = {nd.hiz.x, nd.hiz.y, nd.hiz.z, nd.hiz.w};
+  const int ch[4] = {nd.child.x, nd.child.y, nd.child.z, nd.child.w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    float t0 = (lx[k] - o.x) * inv.x, t1 = (hx[k] - o.x) * inv.x;
+    float tn = fminf(t0, t1), tf = fmaxf(t0, t1);
+    t0 = (ly[k] - o.y) * inv.y; t1 = (hy[k] - o.y) * inv.y;
+    tn = fmaxf(tn, fminf(t0, t1)); tf = fminf(tf, fmaxf(t0, t1));
+    t0 = (lz[k] - o.z) * inv.z; t1 = (hz[k] - o.z) * inv.z;
+    tn = fmaxf(tn, fminf(t0, t1)); tf = fminf(tf, fmaxf(t0, t1));
+    tn = fmaxf(tn, 0.0f);
+    tf = fminf(tf, tmax);
+    t[k] = (ch[k] != BVH4_EMPTY && tn <= tf * 1.00000024f) ? tn : __int_as_float(0x7fffffff);
+  }
+}
+
+// Any hit with 0 < t < tmax over the 4-wide BVH.
+__device__ __forceinline__ bool trace_any4(const DevScene& s, f3 o, f3 d, float tmax, TraceWork& w) {
+  float th;
+  if (s.n_prims == 1) return hit_prim(s.prims, 0, o, d, tmax, th, w);
+  const f3 inv = mk3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
+  int stack[STACK];
+  int sp = 0;
+  int node = 0;
+  for (int visits = 0; visits < s.n_nodes4; ++visits) {
+    const Bvh4Node nd = s.nodes4[node];
+    w.nodes += 2;
+    float t[4];
+    box4_entry(nd, o, inv, tmax, t);
+    const int ch[4] = {nd.child.x, nd.child.y, nd.child.z, nd.child.w};
+    int next = -1;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (!(t[k] <= tmax)) continue;
+      if (ch[k] < 0) {
+        if (hit_prim(s.prims, ~ch[k], o, d, tmax, th, w)) return true;
+      } else if (next < 0) {
+        next = ch[k];
+      } else if (sp < STACK) {
+        stack[sp++] = ch[k];
+      }
+    }
+    if (next >= 0) {
+      node = next;
+    } else {
+      if (sp == 0) break;
+      node = stack[--sp];
+    }
+  }
+  return false;
+}
+
 // Any hit with 0 < t < tmax.
 __device__ __forceinline__ bool trace_any(const DevScene& s, f3 o, f3 d, float tmax, TraceWork& w) {
   float t;

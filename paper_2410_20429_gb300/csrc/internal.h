@@ -35,6 +35,16 @@ struct BvhNode {
   float4 a, b, c, d;
 };
 
+// 4-wide BVH node (collapsed from the binary LBVH on the host): the boxes of up
+// to four children as structure of arrays, one float4 per coordinate, and the
+// children: >= 0 internal node, < 0 primitive ~child, BVH4_EMPTY unused.
+constexpr int BVH4_EMPTY = 0x7fffffff;
+struct Bvh4Node {
+  float4 lox, loy, loz, hix, hiy, hiz;
+  int4 child;
+  float4 pad;
+};
+
 // Material: m0 = (type, alpha, reflective, emissive), m1 = (colour rgb, 0),
 // m2 = (emitted radiance rgb, 0).
 // Light: l0 = (p0 xyz, cdf), l1 = (e1 xyz, pmf), l2 = (e2 xyz, area),
@@ -42,6 +52,8 @@ struct BvhNode {
 struct DevScene {
   const float4* prims;
   const BvhNode* nodes;
+  const Bvh4Node* nodes4;
+  int n_nodes4;
   const float4* mats;
   const float4* lights;
   int n_prims, n_quads, n_lights, n_mats;
@@ -98,6 +110,7 @@ struct DevCounters {
   unsigned long long sbase[MAXD + 2];   // shadow rays of wave d
   unsigned long long scount[MAXD + 2];
   unsigned long long slcount[MAXD + 2];  // shadow rays of wave d that need tracing
+  unsigned long long fetch[MAXD + 2];    // rays of wave d handed out to the closest-hit kernel
   unsigned long long shadow_entries;     // shadow rays of committed tiles
   unsigned long long shadow_traced;      // listed (traced) shadow rays of committed tiles
   unsigned long long wave_total[MAXD + 2];  // rays per depth wave of committed tiles
@@ -153,7 +166,8 @@ struct WaveLaunch {
 
 // launch wrappers (render.cu)
 cudaError_t launch_tile(const DevScene& s, const DevCache& c, const Arena& a, const IterArgs& it,
-                        const WaveLaunch& L, cudaStream_t st, cudaEvent_t* ev);
+                        const WaveLaunch& L, cudaStream_t st, cudaStream_t side, const cudaEvent_t* sync,
+                        cudaEvent_t* ev);
 // resident blocks per SM of each wave kernel at the given block sizes and variants
 cudaError_t wave_occupancy(const int threads[WAVE_KERNELS], const int variant[WAVE_KERNELS],
                            int blocks_per_sm[WAVE_KERNELS]);

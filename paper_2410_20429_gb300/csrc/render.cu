@@ -138,6 +138,7 @@ __global__ void k_tile_init(DevCounters* ctr, unsigned long long n0) {
     ctr->sbase[t] = 0;
     ctr->scount[t] = 0;
     ctr->slcount[t] = 0;
+    ctr->fetch[t] = 0;
   }
   if (t == 0) {
     ctr->overflow = 0;
@@ -173,30 +174,77 @@ __global__ void k_tile_finish(DevCounters* ctr, unsigned int* tile_status, int s
 template <int MINB>
 __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_trace(const DevScene s, const DevCache c, const Arena a,
                                                          const IterArgs it, const int d) {
-  const DevCounters* ctr = c.ctr;
+  DevCounters* ctr = c.ctr;
   // after an overflow some slots of this wave were never written: stop, the
   // tile is re-rendered in smaller pieces
   if (ctr->overflow) return;
   const Wave w = wave_of(ctr, a, d);
   const Rng rng{it.seed, it.job, it.iteration};
+  const int lane = threadIdx.x & 31;
   TraceWork tw;
-  for (unsigned long long li = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; li < w.n;
-       li += gridDim.x * (unsigned long long)blockDim.x) {
-    const unsigned long long i = w.base + li;
-    f3 o, dir;
-    bool alive = true;
-    if (d == 1) {
-      camera_ray(s, rng, (uint32_t)(it.tile_begin + li), o, dir);
-    } else {
-      const float4 r0 = a.R[0][i], r1 = a.R[1][i];
-      o = xyz(r0);
-      dir = xyz(r1);
-      alive = r1.w > 0.0f;  // A = beta_t p_t is 0 for a drawn sample that is not traced
+  // Persistent traversal with lane refill: a lane whose ray has finished takes
+  // the next ray of the wave from a warp-private pool of FETCH rays (one
+  // atomic per pool), so the lanes of a warp stay busy while ray lengths
+  // differ, instead of idling until the warp's longest ray ends.
+  constexpr unsigned long long FETCH = 64;
+  unsigned long long pool = 0, pool_end = 0;
+  bool exhausted = false;
+  int stack[STACK];
+  ClosestState q;
+  bool busy = false;
+  unsigned long long ray = 0;
+  for (;;) {
+    unsigned idle = __ballot_sync(FULL, !busy);
+    while (idle && !exhausted) {
+      if (pool == pool_end) {
+        unsigned long long b = 0;
+        if (lane == 0) b = atomicAdd(&ctr->fetch[d], FETCH);
+        b = __shfl_sync(FULL, b, 0);
+        if (b >= w.n) {
+          exhausted = true;
+          break;
+        }
+        pool = b;
+        pool_end = b + FETCH < w.n ? b + FETCH : w.n;
+      }
+      const unsigned long long avail = pool_end - pool;
+      const int rank = __popc(idle & ((1u << lane) - 1u));
+      const bool take = !busy && (unsigned long long)rank < avail;
+      const unsigned taken = __ballot_sync(FULL, take);
+      if (take) {
+        ray = pool + (unsigned long long)rank;
+        const unsigned long long i = w.base + ray;
+        f3 o, dir;
+        bool alive = true;
+        if (d == 1) {
+          camera_ray(s, rng, (uint32_t)(it.tile_begin + ray), o, dir);
+        } else {
+          const float4 r0 = a.R[0][i], r1 = a.R[1][i];
+          o = xyz(r0);
+          dir = xyz(r1);
+          alive = r1.w > 0.0f;  // A = beta_t p_t is 0 for a drawn sample that is not traced
+        }
+        if (!alive) {
+          a.H[i] = make_float2(0.0f, __int_as_float(-2));  // -2: not traced
+        } else if (s.n_prims == 1) {
+          float t = __int_as_float(0x7f800000), th;
+          const bool h = hit_prim(s.prims, 0, o, dir, t, th, tw);
+          a.H[i] = make_float2(h ? th : t, __int_as_float(h ? 0 : -1));
+        } else {
+          closest_begin(q, o, dir);
+          busy = true;
+        }
+      }
+      pool += (unsigned long long)__popc(taken);
+      idle = __ballot_sync(FULL, !busy);
+      if (!__any_sync(FULL, take)) break;
     }
-    float t = 0.0f;
-    int prim = -2;  // -2: not traced, -1: traced and missed
-    if (alive) prim = trace_closest(s, o, dir, t, tw);
-    a.H[i] = make_float2(t, __int_as_float(prim));
+    if (!__any_sync(FULL, busy)) break;
+    if (busy && !closest_step(s, q, stack, tw)) {
+      // -1: traced and missed
+      a.H[w.base + ray] = make_float2(q.t_best, __int_as_float(q.best));
+      busy = false;
+    }
   }
   flush_work(tw, c.ctr->trace_work[0]);
 }
@@ -614,7 +662,7 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_shadow(const DevScen
     const float4 s0 = a.SH[0][j];
     if (!(s0.w > 0.0f)) continue;
     const float4 s1 = a.SH[1][j];
-    if (trace_any(s, xyz(s0), xyz(s1), s0.w, tw)) a.SH[2][j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (trace_any4(s, xyz(s0), xyz(s1), s0.w, tw)) a.SH[2][j] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   flush_work(tw, c.ctr->trace_work[1]);
 }
@@ -765,6 +813,9 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_reverse(const DevSce
         const uint32_t prev = __shfl_up_sync(FULL, key, 1);
         const bool head = lane == 0 || prev != key;
         const unsigned heads = __ballot_sync(FULL, head);
+        // a run of two or more lanes with statistics is the only case that needs
+        // the segmented scan (in deep waves neighbouring vertices rarely share a cell)
+        const bool pairs = __any_sync(FULL, !head && key != 0xffffffffu);
         const unsigned below = lane == 31 ? FULL : ((2u << lane) - 1u);
         const int start = 31 - __clz(heads & below);
         const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
@@ -773,7 +824,7 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_reverse(const DevSce
           if (!((c.techniques >> t) & 1)) continue;
           // skip a technique no lane drew, and the scan when every run is one lane
           if (!__any_sync(FULL, st[t][0] > 0.0f)) continue;
-          if (heads != FULL) {
+          if (pairs) {
 #pragma unroll
             for (int k = 0; k < NSTAT; ++k) st[t][k] = seg_scan(st[t][k], lane, start);
           }
@@ -860,27 +911,46 @@ cudaError_t wave_occupancy(const int threads[WAVE_KERNELS], const int variant[WA
 bool wave_threads_ok(int threads) { return threads >= 32 && threads <= MAX_WAVE_THREADS && threads % 32 == 0; }
 
 cudaError_t launch_tile(const DevScene& s, const DevCache& c, const Arena& a, const IterArgs& it, const WaveLaunch& L,
-                        cudaStream_t st, cudaEvent_t* ev) {
+                        cudaStream_t st, cudaStream_t side, const cudaEvent_t* sync, cudaEvent_t* ev) {
   const unsigned long long n0 = (unsigned long long)(it.tile_end - it.tile_begin);
   k_tile_init<<<1, 32, 0, st>>>(c.ctr, n0);
   const int D = c.max_depth;
   const int tT = L.threads[WK_TRACE], tS = L.threads[WK_SHADE], tH = L.threads[WK_SHADOW], tR = L.threads[WK_REVERSE];
   auto G = [&](int k, int d) { return L.wave_grid[k][d] > 0 ? L.wave_grid[k][d] : L.grid[k]; };
   const size_t smS = shade_smem(tS);
-  // ev (optional, 4 D + 1 events): ev[0] first; after wave d's trace, shade and
-  // shadow kernels ev[3(d-1) + 1..3]; after the k-th reverse kernel ev[3 D + k]
+  const bool nee = (c.techniques & MARS_TECH_NEE) != 0;
+  // The NEE shadow rays of wave d run on the side stream, overlapped with the
+  // forward kernels of the next waves (disjoint data); the reverse pass, their
+  // only consumer, waits for all of them.
+  // sync: D + 1 events without timing (after shade(d); after the last shadow
+  // kernel).  ev (optional, 5 D + 2 timing events): ev[0] start; ev[2(d-1)+1],
+  // ev[2(d-1)+2] after wave d's trace and shade; ev[2D + 2(d-1) + 1 .. 2] around
+  // its shadow kernel on the side stream; ev[5D + 1] when the reverse pass may
+  // start; ev[4D + k] after the k-th reverse kernel.
   if (ev) cudaEventRecord(ev[0], st);
+  bool any_shadow = false;
   for (int d = 1; d <= D; ++d) {
     trace_fn(L.variant[WK_TRACE])<<<G(WK_TRACE, d), tT, 0, st>>>(s, c, a, it, d);
-    if (ev) cudaEventRecord(ev[3 * (d - 1) + 1], st);
+    if (ev) cudaEventRecord(ev[2 * (d - 1) + 1], st);
     shade_fn(L.variant[WK_SHADE])<<<G(WK_SHADE, d), tS, smS, st>>>(s, c, a, it, d);
-    if (ev) cudaEventRecord(ev[3 * (d - 1) + 2], st);
-    if (d <= D - 1 && (c.techniques & MARS_TECH_NEE)) shadow_fn(L.variant[WK_SHADOW])<<<G(WK_SHADOW, d), tH, 0, st>>>(s, c, a, d);
-    if (ev) cudaEventRecord(ev[3 * (d - 1) + 3], st);
+    if (ev) cudaEventRecord(ev[2 * (d - 1) + 2], st);
+    if (d <= D - 1 && nee) {
+      cudaEventRecord(sync[d - 1], st);
+      cudaStreamWaitEvent(side, sync[d - 1], 0);
+      if (ev) cudaEventRecord(ev[2 * D + 2 * (d - 1) + 1], side);
+      shadow_fn(L.variant[WK_SHADOW])<<<G(WK_SHADOW, d), tH, 0, side>>>(s, c, a, d);
+      if (ev) cudaEventRecord(ev[2 * D + 2 * (d - 1) + 2], side);
+      any_shadow = true;
+    }
   }
+  if (any_shadow) {
+    cudaEventRecord(sync[D], side);
+    cudaStreamWaitEvent(st, sync[D], 0);
+  }
+  if (ev) cudaEventRecord(ev[5 * D + 1], st);
   for (int d = D; d >= 1; --d) {
     reverse_fn(L.variant[WK_REVERSE])<<<G(WK_REVERSE, d), tR, 0, st>>>(s, c, a, it, d);
-    if (ev) cudaEventRecord(ev[3 * D + (D - d + 1)], st);
+    if (ev) cudaEventRecord(ev[4 * D + (D - d + 1)], st);
   }
   k_tile_finish<<<1, 32, 0, st>>>(c.ctr, c.tile_status, it.tile_slot, D);
   return cudaGetLastError();
