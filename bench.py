@@ -336,6 +336,8 @@ def run_mars(args):
                    "autotuned": not (args.no_autotune or args.launch)},
     }
 
+    if rank == 0 and not args.no_large:
+        line["large_scene"] = large_scene(args, M, stream)
     if rank == 0 and args.serve_requests > 0:
         line["serving"] = serving(args)
     if rank == 0 and not args.no_precision:
@@ -351,6 +353,53 @@ def run_mars(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def large_scene(args, M, stream):
+    """The heightfield workload (256 x 256 quads = 131k triangles + 202 spheres,
+    1024 x 1024, D = 10, three techniques): LBVH build time, then 3 warm-up and
+    3 timed MARS iterations; throughput, kernel times and traversal work per
+    ray at this geometry size."""
+    import torch
+    cfg = W.config_heightfield(1024, 1024)
+    t0 = time.perf_counter()
+    scene = M.Scene(cfg.scene, stream=stream)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    cache = M.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, stream=stream)
+    img = torch.zeros(cfg.scene.n_pixels * 3, dtype=torch.float32, device="cuda")
+    it = 0
+    for k in range(3):
+        cache.render_iteration(img, seed=77, iteration=it, mode=M.MARS_MODE_WARMUP, update_estimate=True,
+                               stream=stream)
+        cache.update_counts(stream=stream)
+        it += 1
+    launch = cache.autotune(iteration=it, seed=77, mode=M.MARS_MODE_MARS, repeats=1, stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sts = []
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for k in range(3):
+        sts.append(cache.render_iteration(img, seed=77, iteration=it, mode=M.MARS_MODE_MARS, update_estimate=True,
+                                          profile=True, stream=stream))
+        cache.update_counts(stream=stream)
+        it += 1
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 3
+    verts = sum(s["vertices"] for s in sts) / 3
+    tw = [sum(s["trace_work"][0][q] for s in sts) for q in range(4)]
+    n = max(sum(s["wave_entries"] for s in sts), 1)
+    out = {"workload": cfg.name, "primitives": int(len(cfg.scene.tris) + len(cfg.scene.spheres) + len(cfg.scene.quads)),
+           "bvh_build_s": round(build_s, 3), "ms_per_step": round(ms, 3),
+           "mvertices_s": round(verts / (ms * 1e-3) / 1e6, 1), "vertices_per_step": int(verts),
+           "kernel_ms_per_step": {k: round(sum(s[k + "_ms"] for s in sts) / 3, 4)
+                                  for k in ("trace", "shade", "shadow", "reverse", "image")},
+           "closest_hit_per_ray": {"nodes": round(tw[0] / n, 2), "prim_tests": round(sum(tw[1:]) / n, 2)},
+           "mean_beta": [round(sum(s["mean_beta"][t] for s in sts) / 3, 4) for t in range(3)],
+           "launch": launch}
+    del cache, scene
+    return out
 
 
 def serving(args):
@@ -588,6 +637,7 @@ def main():
     ap.add_argument("--ref-pixels-per-step", type=int, default=1024)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--no-large", action="store_true", help="skip the heightfield (131k triangles) section")
     ap.add_argument("--serve-requests", type=int, default=256, help="serving-stream requests (0 = skip)")
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--serve-slots", type=int, default=8)

@@ -13,6 +13,8 @@ from .scenes import (  # noqa: F401
     area_light_plane_scene,
     config_box,
     config_guided,
+    config_heightfield,
+    heightfield_scene,
     random_count_fields,
     random_guide_cdf,
     random_pixel_estimate,

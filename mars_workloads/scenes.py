@@ -234,6 +234,73 @@ def guided_room_scene(seed: int = 0, width: int = 512, height: int = 512,
     return _mk(quads, quad_mat, spheres, sphere_mat, mats, cam, width, height, "guided_room")
 
 
+def heightfield_scene(seed: int = 0, n: int = 256, width: int = 1024, height: int = 1024,
+                      n_spheres: int = 200, size: float = 8.0) -> Scene:
+    """A seeded heightfield of n x n quads (2 n^2 triangles, heights from three
+    octaves of bilinearly interpolated value noise, Lambertian albedo 0.6) over a
+    size x size square, with ``n_spheres`` spheres resting above it (radius
+    U[0.05, 0.3], 60 % GGX with roughness U[0.05, 0.5], 40 % Lambertian), and one
+    small 0.2 x 0.2 emitter of radiance 200 facing down, hidden low between two
+    large occluding spheres so that little of the terrain sees it directly -- the
+    geometry of the bidirectional workloads, here lit for the unidirectional
+    tracer."""
+    rng = np.random.Generator(np.random.Philox(key=seed + 7))
+
+    def noise(cells):
+        g = rng.uniform(0.0, 1.0, size=(cells + 1, cells + 1))
+        x = np.linspace(0.0, cells, n + 1)
+        i = np.minimum(x.astype(int), cells - 1)
+        f = x - i
+        a = g[i][:, i] * (1 - f)[None, :] + g[i][:, i + 1] * f[None, :]
+        b = g[i + 1][:, i] * (1 - f)[None, :] + g[i + 1][:, i + 1] * f[None, :]
+        return a * (1 - f)[:, None] + b * f[:, None]
+
+    h = 0.8 * noise(4) + 0.3 * noise(16) + 0.08 * noise(64)
+    xs = np.linspace(0.0, size, n + 1)
+    P = np.stack(np.meshgrid(xs, xs, indexing="ij"), axis=-1)         # [n+1, n+1, (x, z)]
+    V = np.stack([P[..., 0], h, P[..., 1]], axis=-1)                   # vertices
+    a, b = V[:-1, :-1].reshape(-1, 3), V[1:, :-1].reshape(-1, 3)
+    c, d = V[1:, 1:].reshape(-1, 3), V[:-1, 1:].reshape(-1, 3)
+    # both triangles wound so that the normal points up (+y)
+    tris = np.concatenate([np.concatenate([a, d, c], 1), np.concatenate([a, c, b], 1)], 0)
+    mats = [_lambert(0.6, 0.6, 0.6)]
+    spheres, sphere_mat = [], []
+    for _ in range(n_spheres):
+        x, z = rng.uniform(0.2, size - 0.2, size=2)
+        r = rng.uniform(0.05, 0.3)
+        col = rng.uniform(0.2, 0.9, size=3)
+        if rng.uniform() < 0.6:
+            mats.append(_ggx(col[0], col[1], col[2], rng.uniform(0.05, 0.5)))
+        else:
+            mats.append(_lambert(col[0], col[1], col[2]))
+        spheres.append([x, 1.2 + r + rng.uniform(0.0, 0.4), z, r])
+        sphere_mat.append(len(mats) - 1)
+    # the hidden emitter: low above the middle, between two big spheres
+    mats.append(_lambert(0.0, 0.0, 0.0, (200.0, 200.0, 200.0)))
+    lx, lz, ly = 0.5 * size - 0.1, 0.5 * size - 0.1, 1.45
+    quads = [[lx, ly, lz, 0.2, 0, 0, 0, 0, 0.2]]                       # e1 x e2 = -y: faces down
+    quad_mat = [len(mats) - 1]
+    occ = len(mats)
+    mats.append(_lambert(0.5, 0.5, 0.5))
+    for dx in (-0.45, 0.65):
+        spheres.append([0.5 * size + dx, 1.45, 0.5 * size, 0.4])
+        sphere_mat.append(occ)
+    cam = [0.5 * size, 4.0, -2.5, 0.5 * size, 0.6, 0.5 * size, 0.0, 1.0, 0.0, 50.0]
+    sc = _mk(quads, quad_mat, spheres, sphere_mat, mats, cam, width, height, "heightfield")
+    sc.tris = _f32(tris)
+    sc.tri_mat = np.zeros(len(tris), dtype=np.int32)
+    return sc
+
+
+def config_heightfield(width: int = 1024, height: int = 1024, seed: int = 0) -> WorkloadConfig:
+    """Heightfield 256 x 256 quads (131k triangles) + 200 spheres, 1024^2, D = 10,
+    BSDF + NEE + guided, 32^3 grid (the geometry of the bidirectional workload,
+    rendered unidirectionally)."""
+    return WorkloadConfig(heightfield_scene(seed, 256, width, height), max_depth=10, grid_n=32,
+                          techniques=TECH_BSDF | TECH_NEE | TECH_GUIDED, iterations=16, warmup=3,
+                          name=f"heightfield_256q_{width}x{height}_D10_bsdf+nee+guided_grid32")
+
+
 def config_box(width: int = 64, height: int = 64) -> WorkloadConfig:
     """Box scene, 64 x 64, D = 5, BSDF + NEE, 8^3 grid, 4 iterations, 1 warm-up."""
     return WorkloadConfig(box_scene(width, height), max_depth=5, grid_n=8,

@@ -199,64 +199,6 @@ __device__ __forceinline__ int trace_closest(const DevScene& s, f3 o, f3 d, floa
   return best;
 }
 
-// Closest-hit traversal as a resumable state: one call of closest_step visits
-// one node, so a warp can refill lanes whose ray has finished with new rays
-// while the others keep traversing.  Same visiting rule, culling and tie-break
-// as trace_closest, hence the same result.
-struct ClosestState {
-  f3 o, d, inv;
-  float t_best;
-  int best, node, sp, visits;
-};
-
-__device__ __forceinline__ void closest_begin(ClosestState& q, f3 o, f3 d) {
-  q.o = o;
-  q.d = d;
-  q.inv = mk3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
-  q.t_best = __int_as_float(0x7f800000);
-  q.best = -1;
-  q.node = 0;
-  q.sp = 0;
-  q.visits = 0;
-}
-
-// returns false once the traversal has finished (result in t_best, best)
-__device__ __forceinline__ bool closest_step(const DevScene& s, ClosestState& q, int* stack, TraceWork& w) {
-  const BvhNode nd = s.nodes[q.node];
-  ++w.nodes;
-  const float tl = box_entry(nd.a, nd.b, q.o, q.inv, q.t_best);
-  const float tr = box_entry(nd.c, nd.d, q.o, q.inv, q.t_best);
-  const int cl = __float_as_int(nd.a.w), cr = __float_as_int(nd.b.w);
-  bool vl = tl <= q.t_best, vr = tr <= q.t_best;
-  if (vl && cl < 0) {
-    float t;
-    const int p = ~cl;
-    if (hit_prim(s.prims, p, q.o, q.d, q.t_best * 1.0000002f + 1e-30f, t, w) &&
-        (t < q.t_best || (t == q.t_best && p < q.best))) { q.t_best = t; q.best = p; }
-    vl = false;
-  }
-  if (vr && cr < 0) {
-    float t;
-    const int p = ~cr;
-    if (hit_prim(s.prims, p, q.o, q.d, q.t_best * 1.0000002f + 1e-30f, t, w) &&
-        (t < q.t_best || (t == q.t_best && p < q.best))) { q.t_best = t; q.best = p; }
-    vr = false;
-  }
-  if (vl && vr) {
-    const bool lfirst = tl <= tr;
-    if (q.sp < STACK) stack[q.sp++] = lfirst ? cr : cl;
-    q.node = lfirst ? cl : cr;
-  } else if (vl) {
-    q.node = cl;
-  } else if (vr) {
-    q.node = cr;
-  } else {
-    if (q.sp == 0) return false;
-    q.node = stack[--q.sp];
-  }
-  return ++q.visits < s.n_prims;
-}
-
 // Entry distances of the four child boxes of a 4-wide node against [0, tmax]
 // (NaN for a miss or an empty slot), by the same slab arithmetic as box_entry.
 __device__ __forceinline__ void box4_entry(const Bvh4Node& nd, f3 o, f3 inv, float tmax, float t[4]) {

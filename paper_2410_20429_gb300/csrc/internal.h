@@ -110,7 +110,6 @@ struct DevCounters {
   unsigned long long sbase[MAXD + 2];   // shadow rays of wave d
   unsigned long long scount[MAXD + 2];
   unsigned long long slcount[MAXD + 2];  // shadow rays of wave d that need tracing
-  unsigned long long fetch[MAXD + 2];    // rays of wave d handed out to the closest-hit kernel
   unsigned long long shadow_entries;     // shadow rays of committed tiles
   unsigned long long shadow_traced;      // listed (traced) shadow rays of committed tiles
   unsigned long long wave_total[MAXD + 2];  // rays per depth wave of committed tiles

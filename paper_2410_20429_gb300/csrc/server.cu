@@ -22,8 +22,9 @@ using Clock = std::chrono::steady_clock;
 // Served jobs bound the splitting along a path (mars_iter_params.max_multiplicity):
 // a dark pixel in a job's first MARS iterations, whose estimate comes from a
 // few warm-up samples, could otherwise split at the clamp (20) at every bounce
-// and hold up the GPU for every other job.
-constexpr float kServeMultiplicity = 100.0f;
+// and hold up the GPU for every other job.  A converged MARS run of the guided
+// room spawns about 4 vertices per depth per camera sample, well below the cap.
+constexpr float kServeMultiplicity = 16.0f;
 
 struct Job {
   uint64_t id = 0;

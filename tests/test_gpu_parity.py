@@ -127,6 +127,30 @@ def test_multiplicity_cap_parity(mars, orc):
     assert free.vertices > 2 * o.vertices   # the cap binds
 
 
+def test_heightfield_triangles_parity(mars, orc):
+    """Triangle geometry through the LBVH: a small seeded heightfield (12 x 12
+    quads, 288 triangles) with spheres and the hidden emitter, warm-up and a
+    teacher-forced MARS iteration with all three techniques."""
+    sc = W.heightfield_scene(5, n=12, width=40, height=32, n_spheres=20)
+    cfg = W.WorkloadConfig(sc, max_depth=5, grid_n=8, techniques=7, iterations=2, warmup=1, name="hf")
+    scene, cache = _make(mars, cfg)
+    g_img, g_st = _gpu_iteration(mars, cache, iteration=0, seed=8, mode=0)
+    g_state = cache.get_state()
+    o = orc.render(sc, grid_n=8, techniques=7, max_depth=5, iteration=0, seed=8)
+    _check(g_img, o.image, g_state, o, g_st, "heightfield warm-up")
+    assert o.image.mean() > 0
+    q_rr, q_s, valid = W.random_count_fields(cfg.n_cells, seed=121, lo=0.1, hi=3.0)
+    est = W.random_pixel_estimate(sc.n_pixels, seed=122, lo=0.01, hi=0.5)
+    cdf = W.random_guide_cdf(cfg.n_cells, seed=123)
+    cache.set_state(q_rr=q_rr, q_s=q_s, valid=valid, pixel_estimate=est, has_estimate=True, n_iterations=1,
+                    guide_cdf=cdf, stats=np.zeros((cfg.n_cells, 3, 8)))
+    g_img, g_st = _gpu_iteration(mars, cache, iteration=1, seed=8, mode=1)
+    g_state = cache.get_state()
+    o = orc.render(sc, grid_n=8, techniques=7, max_depth=5, iteration=1, seed=8, mode=orc.MODE_MARS, q_rr=q_rr,
+                   q_s=q_s, valid=valid, est=est, guide_cdf=cdf)
+    _check(g_img, o.image, g_state, o, g_st, "heightfield MARS")
+
+
 def test_guided_room_crop_parity(mars, orc):
     """Three techniques (BSDF, NEE, guided) on a 64 x 64 render of the guided room
     with 16 spheres, GGX and Lambert, random guide CDFs and random counts."""
