@@ -357,16 +357,18 @@ def run_mars(args):
 
 def large_scene(args, M, stream):
     """The heightfield workload (256 x 256 quads = 131k triangles + 202 spheres,
-    1024 x 1024, D = 10, three techniques): LBVH build time, then 3 warm-up and
-    3 timed MARS iterations; throughput, kernel times and traversal work per
-    ray at this geometry size."""
+    1024 x 1024, D = 10, three techniques) with the adaptive octree cache
+    (starting as the 32^3 grid, at most 64k leaves): LBVH build time, then 3
+    warm-up and 3 timed MARS iterations; throughput, kernel times, traversal
+    work per ray and the octree's size at this geometry size."""
     import torch
     cfg = W.config_heightfield(1024, 1024)
     t0 = time.perf_counter()
     scene = M.Scene(cfg.scene, stream=stream)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
-    cache = M.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, stream=stream)
+    cache = M.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, octree=True, max_leaves=65536,
+                    split_samples=4096.0, stream=stream)
     img = torch.zeros(cfg.scene.n_pixels * 3, dtype=torch.float32, device="cuda")
     it = 0
     for k in range(3):
@@ -397,7 +399,7 @@ def large_scene(args, M, stream):
                                   for k in ("trace", "shade", "shadow", "reverse", "image")},
            "closest_hit_per_ray": {"nodes": round(tw[0] / n, 2), "prim_tests": round(sum(tw[1:]) / n, 2)},
            "mean_beta": [round(sum(s["mean_beta"][t] for s in sts) / 3, 4) for t in range(3)],
-           "launch": launch}
+           "octree_leaves": int(cache.info()["oct_n_leaves"]), "launch": launch}
     del cache, scene
     return out
 

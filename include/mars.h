@@ -95,19 +95,31 @@ typedef struct {
  * techniques: MARS_TECH_* bits; BSDF is required.
  * max_depth: maximum number of path segments D (1..MARS_MAX_DEPTH); vertices
  *   x_1..x_{D-1} run the secondary estimator.
- * flags: 0, or MARS_CACHE_FP32_STATISTICS: accumulate the local statistics,
- *   run the count update and reduce V_I and C_I in float32 instead of float64
- *   (the float32-only variant of the precision study; default float64).
+ * flags: MARS_CACHE_FP32_STATISTICS: accumulate the local statistics, run the
+ *   count update and reduce V_I and C_I in float32 instead of float64 (the
+ *   float32-only variant of the precision study; default float64).
+ *   MARS_CACHE_OCTREE: an adaptive octree over the scene box instead of the
+ *   uniform grid (the EARS octree of Sec. 5.1): it starts as the grid (grid_n
+ *   a power of two, cells numbered as in the grid) and after every
+ *   mars_update_counts splits, in cell order, each leaf that received at least
+ *   split_samples samples (all techniques) in the iteration into 8 children,
+ *   down to 1024 cells per axis and while the leaves number at most
+ *   max_leaves; children inherit the counts and the guide distribution.
+ * max_leaves, split_samples: octree only (0: 65536 leaves, 4096 samples).
  * arena_capacity: rays held by the per-iteration queue arena summed over all
  *   depths (0 = 3 x pixels x max_depth, at least 2^20).  An iteration whose path
  *   trees do not fit is rendered in pixel tiles (results do not depend on it). */
 #define MARS_CACHE_FP32_STATISTICS 1
+#define MARS_CACHE_OCTREE 2
+#define MARS_OCTREE_MAX_LEVEL 10
 typedef struct {
   int32_t grid_n;
   int32_t techniques;
   int32_t max_depth;
   int32_t flags;
   uint64_t arena_capacity;
+  int32_t max_leaves;
+  float split_samples;
 } mars_cache_desc;
 
 /* Per-iteration parameters.
@@ -173,7 +185,11 @@ typedef struct {
  * stats [cells][3][8]: n, sum v (rgb), sum v^2 (rgb), sum cost (float64).
  * guide_hist [cells][256]: accumulated guide deposits.
  * guide_cdf [cells][256]: inclusive CDF of the guided technique per cell.
- * pixel_estimate [pixels][3], run_sum [pixels][3]: float32. */
+ * pixel_estimate [pixels][3], run_sum [pixels][3]: float32.
+ * Octree caches: cells = max_leaves (only the first oct_n_leaves are in use);
+ * oct_nodes [oct_n_nodes] int32: node >= 0 is the index of its first of 8
+ * children (octant = x | y << 1 | z << 2), < 0 a leaf ~cell; oct_leaf_level
+ * [oct_n_leaves] int32.  set_state takes a tree when oct_nodes is non-NULL. */
 typedef struct {
   float* q_rr;
   float* q_s;
@@ -186,6 +202,9 @@ typedef struct {
   int32_t n_iterations;   /* iterations summed in run_sum */
   int32_t has_estimate;   /* pixel_estimate is meaningful */
   double VI, CI;          /* inputs of the next mars_update_counts */
+  int32_t* oct_nodes;
+  int32_t* oct_leaf_level;
+  int32_t oct_n_nodes, oct_n_leaves;
 } mars_cache_state;
 
 typedef struct {
@@ -195,6 +214,8 @@ typedef struct {
   uint64_t device_bytes;
   int32_t device;
   int32_t n_lights;
+  int32_t oct_n_nodes, oct_n_leaves;  /* octree caches: current tree size (0 for a grid) */
+  int32_t oct_cap_nodes, reserved;    /* octree caches: node capacity (state buffers) */
 } mars_cache_info;
 
 /* ---- scene ------------------------------------------------------------

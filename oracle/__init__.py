@@ -70,7 +70,7 @@ class State(ct.Structure):
     _fields_ = [
         ("q_rr", ct.POINTER(ct.c_float)), ("q_s", ct.POINTER(ct.c_float)),
         ("valid", ct.POINTER(ct.c_uint8)), ("guide_cdf", ct.POINTER(ct.c_float)),
-        ("est", ct.POINTER(ct.c_float)),
+        ("est", ct.POINTER(ct.c_float)), ("oct_nodes", ct.POINTER(ct.c_int32)),
         ("image", ct.POINTER(ct.c_double)), ("stats", ct.POINTER(ct.c_double)),
         ("hist", ct.POINTER(ct.c_double)), ("counters", ct.POINTER(ct.c_double)),
     ]
@@ -118,6 +118,16 @@ def lib():
                                                 ct.c_double, ct.c_double, ct.POINTER(ct.c_double),
                                                 ct.POINTER(ct.c_double)]
             L.orc_bsdf_sample_local.restype = ct.c_int
+            I32 = ct.POINTER(ct.c_int32)
+            L.orc_octree_init.argtypes = [ct.c_int, I32, I32, I32]
+            L.orc_octree_init.restype = ct.c_int
+            L.orc_octree_refine.argtypes = [ct.c_int, ct.c_double, ct.POINTER(ct.c_double), I32, I32, I32, I32, I32,
+                                            ct.POINTER(ct.c_float), ct.POINTER(ct.c_float), ct.POINTER(ct.c_uint8),
+                                            ct.POINTER(ct.c_double), ct.POINTER(ct.c_float)]
+            L.orc_octree_refine.restype = ct.c_int
+            L.orc_octree_cell.argtypes = [ct.POINTER(ct.c_double), ct.POINTER(ct.c_double), I32,
+                                          ct.POINTER(ct.c_double)]
+            L.orc_octree_cell.restype = ct.c_int
             L.orc_guide_pdf.argtypes = [ct.POINTER(ct.c_float), ct.POINTER(ct.c_double)]
             L.orc_guide_pdf.restype = ct.c_double
             L.orc_guide_sample.argtypes = [ct.POINTER(ct.c_float), ct.c_double, ct.c_double, ct.c_double,
@@ -172,10 +182,13 @@ class RenderResult:
 def render(scene, *, grid_n, techniques, max_depth, mode=MODE_WARMUP, weights=WEIGHTS_AWARE,
            seed=0, job=0, iteration=0, clamp_lo=0.05, clamp_hi=20.0, outlier=50.0,
            q_rr=None, q_s=None, valid=None, guide_cdf=None, est=None, collect=True,
-           px_begin=0, px_end=None, max_mult=0.0) -> RenderResult:
-    """One iteration of the MARS path tracer over pixels [px_begin, px_end)."""
+           px_begin=0, px_end=None, max_mult=0.0, octree=None) -> RenderResult:
+    """One iteration of the MARS path tracer over pixels [px_begin, px_end).
+    ``octree``: (nodes int32 array, cells) to use an adaptive octree cache with
+    that many cells instead of the uniform grid_n^3 grid."""
     L = lib()
-    cells = grid_n ** 3
+    cells = grid_n ** 3 if octree is None else int(octree[1])
+    oct_nodes = None if octree is None else np.ascontiguousarray(octree[0], np.int32)
     npx = scene.width * scene.height
     if px_end is None:
         px_end = npx
@@ -205,7 +218,7 @@ def render(scene, *, grid_n, techniques, max_depth, mode=MODE_WARMUP, weights=WE
     P = Params(grid_n, techniques, max_depth, mode, weights, seed, job, iteration,
                clamp_lo, clamp_hi, outlier, int(has_est), int(bool(collect)), float(max_mult))
     S = State(_p(q_rr, ct.c_float), _p(q_s, ct.c_float), _p(valid, ct.c_uint8),
-              _p(guide_cdf, ct.c_float), _p(est, ct.c_float), _p(image, ct.c_double),
+              _p(guide_cdf, ct.c_float), _p(est, ct.c_float), _p(oct_nodes, ct.c_int32), _p(image, ct.c_double),
               _p(stats, ct.c_double), _p(hist, ct.c_double), _p(counters, ct.c_double))
     rc = L.orc_render(ct.byref(sh.desc), ct.byref(P), ct.byref(S), int(px_begin), int(px_end))
     if rc != 0:
@@ -235,6 +248,53 @@ def update_counts(stats, VI, CI, techniques, q_rr, q_s, valid):
     L.orc_update_counts(cells, int(techniques), _p(stats, ct.c_double), float(VI), float(CI),
                         _p(q_rr, ct.c_float), _p(q_s, ct.c_float), _p(valid, ct.c_uint8))
     return q_rr, q_s, valid
+
+
+OCT_LMAX = 10
+
+
+def octree_init(grid_n, max_leaves):
+    """The adaptive octree equal to the uniform grid: (nodes, n_nodes, n_leaves,
+    leaf_level, leaf_node) with arrays sized for max_leaves cells."""
+    L = lib()
+    cap_nodes = 2 * max_leaves + 8 ** 4
+    nodes = np.zeros(cap_nodes, np.int32)
+    level = np.zeros(max_leaves, np.int32)
+    lnode = np.zeros(max_leaves, np.int32)
+    n = L.orc_octree_init(int(grid_n), _p(nodes, ct.c_int32), _p(level, ct.c_int32), _p(lnode, ct.c_int32))
+    if n < 0:
+        raise ValueError("grid_n must be a power of two up to 2^10")
+    return nodes, n, grid_n ** 3, level, lnode
+
+
+def octree_refine(max_leaves, split_samples, stats, nodes, n_nodes, n_leaves, level, lnode, q_rr, q_s, valid,
+                  hist=None, cdf=None):
+    """One refinement step (in place on copies); returns the new
+    (nodes, n_nodes, n_leaves, level, lnode, q_rr, q_s, valid, hist, cdf, splits)."""
+    L = lib()
+    nodes, level, lnode = nodes.copy(), level.copy(), lnode.copy()
+    q_rr = np.array(q_rr, np.float32).copy()
+    q_s = np.array(q_s, np.float32).copy()
+    valid = np.array(valid, np.uint8).copy()
+    hist = None if hist is None else np.array(hist, np.float64).copy()
+    cdf = None if cdf is None else np.array(cdf, np.float32).copy()
+    nn, nl = ct.c_int32(n_nodes), ct.c_int32(n_leaves)
+    stats = np.ascontiguousarray(stats, np.float64)
+    sp = L.orc_octree_refine(int(max_leaves), float(split_samples), _p(stats, ct.c_double), _p(nodes, ct.c_int32),
+                             ct.byref(nn), ct.byref(nl), _p(level, ct.c_int32), _p(lnode, ct.c_int32),
+                             _p(q_rr, ct.c_float), _p(q_s, ct.c_float), _p(valid, ct.c_uint8),
+                             _p(hist, ct.c_double), _p(cdf, ct.c_float))
+    return nodes, nn.value, nl.value, level, lnode, q_rr, q_s, valid, hist, cdf, sp
+
+
+def octree_cell(lo, ext, nodes, p):
+    L = lib()
+    lo = np.ascontiguousarray(lo, np.float64)
+    ext = np.ascontiguousarray(ext, np.float64)
+    p = np.ascontiguousarray(p, np.float64)
+    nodes = np.ascontiguousarray(nodes, np.int32)
+    return int(L.orc_octree_cell(_p(lo, ct.c_double), _p(ext, ct.c_double), _p(nodes, ct.c_int32),
+                                 _p(p, ct.c_double)))
 
 
 def guide_update(hist):

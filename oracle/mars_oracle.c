@@ -469,10 +469,9 @@ typedef struct {
   int on[ORC_NT];  /* technique enabled */
 } rnd_t;
 
-static int cell_of(const ctx_t* C, int N, v3 p) {
-  /* the cell index is decided in float32 */
+static void cell_coords(const ctx_t* C, int N, v3 p, int idx[3]) {
+  /* the cell coordinates are decided in float32 */
   float pf[3] = {(float)p.x, (float)p.y, (float)p.z};
-  int idx[3];
   for (int a = 0; a < 3; ++a) {
     float f = (pf[a] - (float)C->lo[a]) / (float)C->ext[a] * (float)N;
     int i = (int)floorf(f);
@@ -480,7 +479,115 @@ static int cell_of(const ctx_t* C, int N, v3 p) {
     if (i > N - 1) i = N - 1;
     idx[a] = i;
   }
+}
+
+static int cell_of(const ctx_t* C, int N, v3 p) {
+  int idx[3];
+  cell_coords(C, N, p, idx);
   return (idx[2] * N + idx[1]) * N + idx[0];
+}
+
+/* leaf of the adaptive octree holding p: descend with the bits of the point's
+ * coordinates at the finest level, most significant first */
+static int octree_cell(const ctx_t* C, const int32_t* nodes, v3 p) {
+  int idx[3];
+  cell_coords(C, 1 << ORC_OCT_LMAX, p, idx);
+  int k = 0;
+  for (int level = 0; level < ORC_OCT_LMAX && nodes[k] >= 0; ++level) {
+    int sh = ORC_OCT_LMAX - 1 - level;
+    int oct = ((idx[0] >> sh) & 1) | (((idx[1] >> sh) & 1) << 1) | (((idx[2] >> sh) & 1) << 2);
+    k = nodes[k] + oct;
+  }
+  return ~nodes[k];
+}
+
+int orc_octree_cell(const double lo[3], const double ext[3], const int32_t* nodes, const double p[3]) {
+  ctx_t C;
+  memset(&C, 0, sizeof(C));
+  for (int a = 0; a < 3; ++a) {
+    C.lo[a] = lo[a];
+    C.ext[a] = ext[a];
+  }
+  v3 q = {p[0], p[1], p[2]};
+  return octree_cell(&C, nodes, q);
+}
+
+int orc_octree_init(int grid_n, int32_t* nodes, int32_t* leaf_level, int32_t* leaf_node) {
+  int L0 = 0;
+  while ((1 << L0) < grid_n) ++L0;
+  if ((1 << L0) != grid_n || L0 > ORC_OCT_LMAX) return -1;
+  /* breadth first: level l holds 8^l nodes; node (l, x, y, z) */
+  int first = 0, count = 1, next = 1;
+  int* cx = (int*)malloc(sizeof(int) * 3 * (size_t)grid_n * grid_n * grid_n + 3);
+  cx[0] = cx[1] = cx[2] = 0;
+  int* nx = (int*)malloc(sizeof(int) * 3 * (size_t)grid_n * grid_n * grid_n + 3);
+  for (int l = 0; l <= L0; ++l) {
+    for (int k = 0; k < count; ++k) {
+      int x = cx[3 * k], y = cx[3 * k + 1], z = cx[3 * k + 2];
+      if (l == L0) {
+        int cell = (z * grid_n + y) * grid_n + x;
+        nodes[first + k] = ~cell;
+        leaf_level[cell] = L0;
+        leaf_node[cell] = first + k;
+      } else {
+        nodes[first + k] = next + 8 * k;
+        for (int o = 0; o < 8; ++o) {
+          nx[3 * (8 * k + o)] = 2 * x + (o & 1);
+          nx[3 * (8 * k + o) + 1] = 2 * y + ((o >> 1) & 1);
+          nx[3 * (8 * k + o) + 2] = 2 * z + ((o >> 2) & 1);
+        }
+      }
+    }
+    if (l < L0) {
+      first = next;
+      next += 8 * count;
+      count *= 8;
+      int* t = cx;
+      cx = nx;
+      nx = t;
+    }
+  }
+  free(cx);
+  free(nx);
+  return next;
+}
+
+int orc_octree_refine(int max_leaves, double split_samples, const double* stats, int32_t* nodes,
+                      int32_t* n_nodes, int32_t* n_leaves, int32_t* leaf_level, int32_t* leaf_node,
+                      float* q_rr, float* q_s, uint8_t* valid, double* hist, float* cdf) {
+  const int L_count = *n_leaves, N0 = *n_nodes;
+  const int budget = (max_leaves - L_count) / 7;
+  int s = 0;
+  for (int L = 0; L < L_count && s < budget; ++L) {
+    double n = 0.0;
+    for (int t = 0; t < ORC_NT; ++t) n += stats[((size_t)L * ORC_NT + t) * ORC_NSTAT];
+    if (!(n >= split_samples) || leaf_level[L] >= ORC_OCT_LMAX) continue;
+    const int base = N0 + 8 * s;
+    nodes[leaf_node[L]] = base;
+    nodes[base] = ~L;
+    leaf_node[L] = base;
+    leaf_level[L] += 1;
+    for (int o = 1; o < 8; ++o) {
+      const int c = L_count + 7 * s + o - 1;
+      nodes[base + o] = ~c;
+      leaf_node[c] = base + o;
+      leaf_level[c] = leaf_level[L];
+      for (int k = 0; k < ORC_NT * 3; ++k) {
+        q_rr[(size_t)c * ORC_NT * 3 + k] = q_rr[(size_t)L * ORC_NT * 3 + k];
+        q_s[(size_t)c * ORC_NT * 3 + k] = q_s[(size_t)L * ORC_NT * 3 + k];
+      }
+      for (int t = 0; t < ORC_NT; ++t) valid[(size_t)c * ORC_NT + t] = valid[(size_t)L * ORC_NT + t];
+      if (hist && cdf)
+        for (int b = 0; b < ORC_GUIDE_BINS; ++b) {
+          hist[(size_t)c * ORC_GUIDE_BINS + b] = hist[(size_t)L * ORC_GUIDE_BINS + b];
+          cdf[(size_t)c * ORC_GUIDE_BINS + b] = cdf[(size_t)L * ORC_GUIDE_BINS + b];
+        }
+    }
+    ++s;
+  }
+  *n_nodes = N0 + 8 * s;
+  *n_leaves = L_count + 7 * s;
+  return s;
 }
 
 static double lum(const double* c) { return 0.2126 * c[0] + 0.7152 * c[1] + 0.0722 * c[2]; }
@@ -559,7 +666,7 @@ static void trace_sample(rnd_t* R, v3 o, v3 d, int depth, uint64_t lin, const ra
       x.wo = wo;
       x.ns = cosg >= 0.0 ? h.ng : scl(h.ng, -1.0);
       x.mat = h.mat;
-      x.cell = cell_of(C, P->grid_n, h.p);
+      x.cell = R->st->oct_nodes ? octree_cell(C, R->st->oct_nodes, h.p) : cell_of(C, P->grid_n, h.p);
       onb(x.ns, &x.b1, &x.b2);
       secondary_estimator(R, &x, depth, lin, ri->T_child, ri->mult_child, Lchild, &ccost);
     }

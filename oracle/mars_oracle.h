@@ -69,6 +69,8 @@ typedef struct {
   const uint8_t* valid;       /* [cells][3] */
   const float* guide_cdf;     /* [cells][256] inclusive CDF (guided only) */
   const float* est;           /* [pixels][3] pixel estimate */
+  const int32_t* oct_nodes;   /* adaptive octree over the scene box (NULL: the uniform grid_n^3 grid);
+                                 node >= 0: first of its 8 children, < 0: leaf ~cell */
   /* outputs (accumulated, caller zeroes) */
   double* image;              /* [pixels][3] one-sample pixel estimate (written) */
   double* stats;              /* [cells][3][8] */
@@ -97,6 +99,30 @@ void orc_update_counts(int n_cells, int techniques, const double* stats, double 
 /* Guide update: per cell, P_b = 0.9 h_b / H + 0.1 / 256 (uniform when H = 0),
  * cdf = inclusive prefix sum of P. */
 void orc_guide_update(int n_cells, const double* hist, float* cdf);
+
+/* Adaptive octree cache (the spatial structure of EARS, Sec. 5.1), refined
+ * between iterations.  Depth at most ORC_OCT_LMAX; a point's leaf is found by
+ * descending with the bits of its cell coordinates at the finest level,
+ * floor((p - lo) / ext * 2^LMAX) per axis decided in float32, octant =
+ * x | y << 1 | z << 2.
+ * orc_octree_init: the full tree down to the uniform grid (grid_n = 2^L0),
+ *   leaves numbered like the grid's cells, (z * N + y) * N + x; nodes in
+ *   breadth-first order.  Returns the node count.
+ * orc_octree_refine: leaves in id order whose samples this iteration (n summed
+ *   over the techniques, from stats) reach split_samples and whose level is
+ *   below ORC_OCT_LMAX split into 8 while the leaf count stays <= max_leaves.
+ *   Split s (0-based, in that order) turns node leaf_node[L] into an internal
+ *   node with children at n_nodes + 8 s .. + 7; octant 0 keeps cell L, octant
+ *   o > 0 gets the new cell n_leaves + 7 s + o - 1, which inherits L's counts
+ *   (q, valid) and guide histogram and CDF.  Updates the counts in place and
+ *   returns the number of splits. */
+#define ORC_OCT_LMAX 10
+/* leaf of the octree holding point p (scene box lo, ext) */
+int orc_octree_cell(const double lo[3], const double ext[3], const int32_t* nodes, const double p[3]);
+int orc_octree_init(int grid_n, int32_t* nodes, int32_t* leaf_level, int32_t* leaf_node);
+int orc_octree_refine(int max_leaves, double split_samples, const double* stats, int32_t* nodes,
+                      int32_t* n_nodes, int32_t* n_leaves, int32_t* leaf_level, int32_t* leaf_node,
+                      float* q_rr, float* q_s, uint8_t* valid, double* hist, float* cdf);
 
 /* Philox4x32-10 block for counter ctr[4] and key key[2]. */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

@@ -16,6 +16,7 @@ MARS_MODE_WARMUP, MARS_MODE_MARS, MARS_MODE_FIXED = 0, 1, 2
 MARS_WEIGHTS_AWARE, MARS_WEIGHTS_UNAWARE = 0, 1
 MARS_JOB_QUEUED, MARS_JOB_RUNNING, MARS_JOB_DONE, MARS_JOB_FAILED = range(4)
 MARS_CACHE_FP32_STATISTICS = 1
+MARS_CACHE_OCTREE = 2
 NUM_SLOTS, NUM_STATS, GUIDE_BINS, MAX_DEPTH = 3, 8, 256, 16
 
 
@@ -39,7 +40,8 @@ class mars_scene_desc(ct.Structure):
 
 class mars_cache_desc(ct.Structure):
     _fields_ = [("grid_n", ct.c_int32), ("techniques", ct.c_int32), ("max_depth", ct.c_int32),
-                ("flags", ct.c_int32), ("arena_capacity", ct.c_uint64)]
+                ("flags", ct.c_int32), ("arena_capacity", ct.c_uint64), ("max_leaves", ct.c_int32),
+                ("split_samples", ct.c_float)]
 
 
 class mars_iter_params(ct.Structure):
@@ -72,6 +74,8 @@ class mars_cache_state(ct.Structure):
         ("guide_cdf", ct.POINTER(ct.c_float)), ("pixel_estimate", ct.POINTER(ct.c_float)),
         ("run_sum", ct.POINTER(ct.c_float)), ("n_iterations", ct.c_int32), ("has_estimate", ct.c_int32),
         ("VI", ct.c_double), ("CI", ct.c_double),
+        ("oct_nodes", ct.POINTER(ct.c_int32)), ("oct_leaf_level", ct.POINTER(ct.c_int32)),
+        ("oct_n_nodes", ct.c_int32), ("oct_n_leaves", ct.c_int32),
     ]
 
 
@@ -80,6 +84,8 @@ class mars_cache_info(ct.Structure):
         ("n_cells", ct.c_int64), ("n_pixels", ct.c_int64), ("grid_n", ct.c_int32), ("techniques", ct.c_int32),
         ("max_depth", ct.c_int32), ("n_prims", ct.c_int32), ("arena_capacity", ct.c_uint64),
         ("device_bytes", ct.c_uint64), ("device", ct.c_int32), ("n_lights", ct.c_int32),
+        ("oct_n_nodes", ct.c_int32), ("oct_n_leaves", ct.c_int32), ("oct_cap_nodes", ct.c_int32),
+        ("reserved", ct.c_int32),
     ]
 
 

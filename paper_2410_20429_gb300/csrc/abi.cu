@@ -515,12 +515,27 @@ mars_status cache_create_impl(const mars_scene* s, const mars_cache_desc* d, cud
     return set_error(MARS_ERR_INVALID_ARG, "max_depth %d out of [1, %d]", d->max_depth, MAXD);
   if ((d->techniques & MARS_TECH_NEE) && s->n_lights == 0)
     return set_error(MARS_ERR_INVALID_ARG, "NEE requested but the scene has no emitting quad");
-  if (d->flags & ~MARS_CACHE_FP32_STATISTICS) return set_error(MARS_ERR_INVALID_ARG, "unknown cache flags %d", d->flags);
+  if (d->flags & ~(MARS_CACHE_FP32_STATISTICS | MARS_CACHE_OCTREE))
+    return set_error(MARS_ERR_INVALID_ARG, "unknown cache flags %d", d->flags);
   const bool fp32 = (d->flags & MARS_CACHE_FP32_STATISTICS) != 0;
+  const bool octree = (d->flags & MARS_CACHE_OCTREE) != 0;
   const int bits = (d->techniques & MARS_TECH_GUIDED) ? 6 : 5;
   if ((d->max_depth - 1) * bits > 64)
     return set_error(MARS_ERR_INVALID_ARG, "max_depth %d too deep for %d lineage bits per level", d->max_depth, bits);
-  const int64_t cells = (int64_t)d->grid_n * d->grid_n * d->grid_n;
+  const int64_t grid_cells = (int64_t)d->grid_n * d->grid_n * d->grid_n;
+  int64_t cells = grid_cells;
+  int oct_levels = 0;
+  if (octree) {
+    while ((1 << oct_levels) < d->grid_n) ++oct_levels;
+    if ((1 << oct_levels) != d->grid_n || oct_levels > OCT_LMAX)
+      return set_error(MARS_ERR_INVALID_ARG, "octree: grid_n %d is not a power of two up to %d", d->grid_n,
+                       1 << OCT_LMAX);
+    const int64_t ml = d->max_leaves ? d->max_leaves : 65536;
+    if (ml < grid_cells || ml > (1 << 24))
+      return set_error(MARS_ERR_INVALID_ARG, "octree: max_leaves %lld outside [grid_n^3, 2^24]", (long long)ml);
+    if (d->split_samples < 0.0f) return set_error(MARS_ERR_INVALID_ARG, "octree: split_samples < 0");
+    cells = ml;
+  }
   const int64_t pixels = (int64_t)s->width * s->height;
   uint64_t cap = d->arena_capacity ? d->arena_capacity : default_capacity(pixels, d->max_depth);
   if (cap < 64) cap = 64;
@@ -616,6 +631,66 @@ mars_status cache_create_impl(const mars_scene* s, const mars_cache_desc* d, cud
   c->dc.img = c->d_img;
   c->dc.ctr = c->d_ctr;
   c->dc.tile_status = c->d_tile_status;
+  if (octree) {
+    // the initial tree equals the grid: levels 0..L0 complete, breadth first,
+    // children of a node consecutive by octant, leaves numbered like the grid
+    const int N = d->grid_n;
+    std::vector<int> nodes, level((size_t)cells, 0), lnode((size_t)cells, 0);
+    std::vector<int> cur{0, 0, 0}, nxt;
+    nodes.push_back(0);
+    int first = 0, count = 1;
+    for (int l = 0; l <= oct_levels; ++l) {
+      nxt.clear();
+      const int next_first = first + count;
+      for (int k = 0; k < count; ++k) {
+        const int x = cur[3 * k], y = cur[3 * k + 1], z = cur[3 * k + 2];
+        if (l == oct_levels) {
+          const int cell = (z * N + y) * N + x;
+          nodes[first + k] = ~cell;
+          level[cell] = oct_levels;
+          lnode[cell] = first + k;
+        } else {
+          nodes[first + k] = next_first + 8 * k;
+          for (int o = 0; o < 8; ++o) {
+            nxt.push_back(2 * x + (o & 1));
+            nxt.push_back(2 * y + ((o >> 1) & 1));
+            nxt.push_back(2 * z + ((o >> 2) & 1));
+          }
+        }
+      }
+      if (l < oct_levels) {
+        nodes.resize((size_t)next_first + 8 * count);
+        first = next_first;
+        count *= 8;
+        cur.swap(nxt);
+      }
+    }
+    const int n_nodes = (int)nodes.size();
+    const int cap_nodes = n_nodes + 8 * (int)((cells - grid_cells) / 7 + 1);
+    const int meta[3] = {n_nodes, (int)grid_cells, 0};
+    if ((e = dev_alloc((void**)&c->d_oct_nodes, sizeof(int) * cap_nodes, st)) != cudaSuccess ||
+        (e = dev_alloc((void**)&c->d_oct_level, sizeof(int) * cells, st)) != cudaSuccess ||
+        (e = dev_alloc((void**)&c->d_oct_lnode, sizeof(int) * cells, st)) != cudaSuccess ||
+        (e = dev_alloc((void**)&c->d_oct_meta, sizeof(int) * 4, st)) != cudaSuccess ||
+        (e = dev_alloc((void**)&c->d_oct_split, sizeof(int) * (cells / 7 + 1), st)) != cudaSuccess ||
+        (e = dev_alloc((void**)&c->d_oct_leaf_n, sizeof(float) * cells, st)) != cudaSuccess)
+      return cleanup(e, "octree alloc");
+    if ((e = cudaMemcpyAsync(c->d_oct_nodes, nodes.data(), sizeof(int) * n_nodes, cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemcpyAsync(c->d_oct_level, level.data(), sizeof(int) * cells, cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemcpyAsync(c->d_oct_lnode, lnode.data(), sizeof(int) * cells, cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemcpyAsync(c->d_oct_meta, meta, sizeof(int) * 3, cudaMemcpyHostToDevice, st)) ||
+        (e = cudaStreamSynchronize(st)))
+      return cleanup(e, "octree init");
+    c->oct_cap_nodes = cap_nodes;
+    c->dc.oct_nodes = c->d_oct_nodes;
+    c->dc.oct_leaf_level = c->d_oct_level;
+    c->dc.oct_leaf_node = c->d_oct_lnode;
+    c->dc.oct_meta = c->d_oct_meta;
+    c->dc.oct_split = c->d_oct_split;
+    c->dc.oct_leaf_n = c->d_oct_leaf_n;
+    c->dc.oct_cap_nodes = cap_nodes;
+    c->dc.split_samples = d->split_samples > 0.0f ? d->split_samples : 4096.0f;
+  }
   c->device_bytes = cache_footprint(cells, pixels, d->max_depth, d->techniques, cap);
   if ((e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking)) != cudaSuccess)
     return cleanup(e, "side stream");
@@ -683,7 +758,9 @@ void cache_destroy_impl(mars_cache* c) {
   dev_free(c->arena.H, st);
   for (auto* p : c->arena.SH) dev_free(p, st);
   dev_free(c->arena.SL, st);
-  void* ptrs[] = {c->d_cnt, c->d_stats, c->d_stats32, c->d_hist, c->d_cdf, c->d_guide_dirty, c->d_est, c->d_run, c->d_img, c->d_ctr, c->d_tile_status};
+  void* ptrs[] = {c->d_cnt, c->d_stats, c->d_stats32, c->d_hist, c->d_cdf, c->d_guide_dirty, c->d_est, c->d_run,
+                  c->d_img, c->d_ctr, c->d_tile_status, c->d_oct_nodes, c->d_oct_level, c->d_oct_lnode,
+                  c->d_oct_meta, c->d_oct_split, c->d_oct_leaf_n};
   for (void* p : ptrs) dev_free(p, st);
   pinned_release(c->h_ctr, sizeof(DevCounters));
   pinned_release(c->h_tile_status, sizeof(unsigned int) * c->max_tiles);
@@ -929,8 +1006,11 @@ mars_status update_counts_impl(mars_cache* c, cudaStream_t st) {
   if (c->poisoned) return set_error(MARS_ERR_CUDA, "cache is poisoned by an earlier CUDA error");
   DeviceGuard g(c->device);
   c->last_stream = st;
-  cudaError_t e = launch_update(c->dc, c->scene->num_sms, st);
-  if (e != cudaSuccess) return poison(c, e, "update launch");
+  cudaError_t e = cudaSuccess;
+  if (c->dc.oct_nodes && (e = launch_leaf_samples(c->dc, st)) != cudaSuccess) return poison(c, e, "update launch");
+  if ((e = launch_update(c->dc, c->scene->num_sms, st)) != cudaSuccess) return poison(c, e, "update launch");
+  if (c->dc.oct_nodes && (e = launch_octree_refine(c->dc, c->scene->num_sms, st)) != cudaSuccess)
+    return poison(c, e, "octree refine launch");
   return MARS_OK;
 }
 
@@ -938,6 +1018,22 @@ mars_status get_state_impl(mars_cache* c, mars_cache_state* s, cudaStream_t st) 
   if (!c || !s) return set_error(MARS_ERR_INVALID_ARG, "null cache or state");
   if (c->poisoned) return set_error(MARS_ERR_CUDA, "cache is poisoned by an earlier CUDA error");
   DeviceGuard g(c->device);
+  if (c->dc.oct_nodes) {
+    int meta[3] = {0, 0, 0};
+    cudaError_t e0;
+    if ((e0 = cudaMemcpyAsync(meta, c->d_oct_meta, sizeof(int) * 3, cudaMemcpyDeviceToHost, st)) ||
+        (e0 = cudaStreamSynchronize(st)))
+      return poison(c, e0, "state copy");
+    s->oct_n_nodes = meta[0];
+    s->oct_n_leaves = meta[1];
+    if ((s->oct_nodes && (e0 = cudaMemcpyAsync(s->oct_nodes, c->d_oct_nodes, sizeof(int) * meta[0],
+                                                cudaMemcpyDeviceToHost, st))) ||
+        (s->oct_leaf_level && (e0 = cudaMemcpyAsync(s->oct_leaf_level, c->d_oct_level, sizeof(int) * meta[1],
+                                                     cudaMemcpyDeviceToHost, st))))
+      return poison(c, e0, "state copy");
+  } else {
+    s->oct_n_nodes = s->oct_n_leaves = 0;
+  }
   const int64_t cells = c->cells, px = c->pixels;
   const bool guided = c->techniques & MARS_TECH_GUIDED;
   cudaError_t e = cudaSuccess;
@@ -1006,6 +1102,44 @@ mars_status set_state_impl(mars_cache* c, const mars_cache_state* s, cudaStream_
   const int64_t cells = c->cells, px = c->pixels;
   const bool guided = c->techniques & MARS_TECH_GUIDED;
   cudaError_t e = cudaSuccess;
+  if (s->oct_nodes) {
+    if (!c->dc.oct_nodes) return set_error(MARS_ERR_INVALID_ARG, "octree state for a grid cache");
+    const int nn = s->oct_n_nodes, nl = s->oct_n_leaves;
+    if (nn < 1 || nn > c->oct_cap_nodes || nl < 1 || nl > cells || !s->oct_leaf_level)
+      return set_error(MARS_ERR_INVALID_ARG, "octree state: %d nodes, %d leaves out of range", nn, nl);
+    // check the tree before any kernel descends it: every node reached once
+    // from the root within the level limit, internal nodes' 8 children in
+    // range, every leaf cell in range exactly once, levels as given
+    std::vector<int> lnode((size_t)cells, -1), depth((size_t)nn, -1);
+    std::vector<std::pair<int, int>> stack{{0, 0}};
+    int leaves = 0;
+    bool ok = true;
+    while (!stack.empty() && ok) {
+      const auto [k, lev] = stack.back();
+      stack.pop_back();
+      if (depth[k] >= 0) { ok = false; break; }
+      depth[k] = lev;
+      const int v = s->oct_nodes[k];
+      if (v < 0) {
+        const int cell = ~v;
+        if (cell >= nl || lnode[cell] >= 0 || s->oct_leaf_level[cell] != lev) { ok = false; break; }
+        lnode[cell] = k;
+        ++leaves;
+      } else {
+        if (lev >= OCT_LMAX || v < 1 || v + 7 >= nn) { ok = false; break; }
+        for (int o = 0; o < 8; ++o) stack.push_back({v + o, lev + 1});
+      }
+    }
+    if (!ok || leaves != nl) return set_error(MARS_ERR_INVALID_ARG, "octree state: not a valid tree");
+    const int meta[3] = {nn, nl, 0};
+    for (auto& x : lnode) x = x < 0 ? 0 : x;
+    if ((e = cudaMemcpyAsync(c->d_oct_nodes, s->oct_nodes, sizeof(int) * nn, cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemcpyAsync(c->d_oct_level, s->oct_leaf_level, sizeof(int) * nl, cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemcpyAsync(c->d_oct_lnode, lnode.data(), sizeof(int) * nl, cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemcpyAsync(c->d_oct_meta, meta, sizeof(int) * 3, cudaMemcpyHostToDevice, st)) ||
+        (e = cudaStreamSynchronize(st)))
+      return poison(c, e, "state copy");
+  }
   if (s->q_rr || s->q_s || s->valid) {
     std::vector<float4> cnt(2 * NT * cells);
     if ((e = cudaMemcpy(cnt.data(), c->d_cnt, sizeof(float4) * cnt.size(), cudaMemcpyDeviceToHost)) != cudaSuccess)
@@ -1107,6 +1241,17 @@ mars_status mars_cache_info_get(const mars_cache* c, mars_cache_info* info) {
   info->device_bytes = c->device_bytes + c->scene->device_bytes;
   info->device = c->device;
   info->n_lights = c->scene->n_lights;
+  info->oct_cap_nodes = c->oct_cap_nodes;
+  info->oct_n_nodes = info->oct_n_leaves = 0;
+  info->reserved = 0;
+  if (c->dc.oct_nodes) {
+    DeviceGuard g(c->device);
+    int meta[3] = {0, 0, 0};
+    if (cudaMemcpy(meta, c->d_oct_meta, sizeof(int) * 3, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return set_error(MARS_ERR_CUDA, "octree size read failed");
+    info->oct_n_nodes = meta[0];
+    info->oct_n_leaves = meta[1];
+  }
   return MARS_OK;
 }
 

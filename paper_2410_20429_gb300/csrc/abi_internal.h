@@ -85,6 +85,13 @@ struct mars_cache {
   float* d_hist = nullptr;
   float* d_cdf = nullptr;
   uint8_t* d_guide_dirty = nullptr;
+  int* d_oct_nodes = nullptr;   // adaptive octree (MARS_CACHE_OCTREE)
+  int* d_oct_level = nullptr;
+  int* d_oct_lnode = nullptr;
+  int* d_oct_meta = nullptr;
+  int* d_oct_split = nullptr;
+  float* d_oct_leaf_n = nullptr;
+  int oct_cap_nodes = 0;
   float4* d_est = nullptr;
   float4* d_run = nullptr;
   float4* d_img = nullptr;

@@ -440,17 +440,38 @@ __device__ __forceinline__ f3 guide_dir(int b, float u1, float u2) {
 }
 
 // ----------------------------------------------------------------- cells
-// uniform grid cell of a point; decided in float32 like every integer choice
-__device__ __forceinline__ int cell_of(const DevScene& s, int N, f3 p) {
+// cell coordinates of a point on an N^3 grid over the scene box; decided in
+// float32 like every integer choice
+__device__ __forceinline__ void cell_coords(const DevScene& s, int N, f3 p, int idx[3]) {
   const float pa[3] = {p.x, p.y, p.z};
-  int idx[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const float f = (pa[a] - s.lo[a]) / s.ext[a] * (float)N;
     int i = (int)floorf(f);
     idx[a] = i < 0 ? 0 : (i > N - 1 ? N - 1 : i);
   }
+}
+
+// uniform grid cell of a point
+__device__ __forceinline__ int cell_of(const DevScene& s, int N, f3 p) {
+  int idx[3];
+  cell_coords(s, N, p, idx);
   return (idx[2] * N + idx[1]) * N + idx[0];
+}
+
+// adaptive octree leaf of a point: descend with the bits of its coordinates on
+// the finest (2^OCT_LMAX per axis) grid, most significant first.  Scaling by a
+// power of two is exact, so an unrefined octree gives the uniform grid's cell.
+__device__ __forceinline__ int octree_cell(const DevScene& s, const int* __restrict__ nodes, f3 p) {
+  int idx[3];
+  cell_coords(s, 1 << OCT_LMAX, p, idx);
+  int v = __ldg(nodes);
+  for (int level = 0; level < OCT_LMAX && v >= 0; ++level) {
+    const int sh = OCT_LMAX - 1 - level;
+    const int oct = ((idx[0] >> sh) & 1) | (((idx[1] >> sh) & 1) << 1) | (((idx[2] >> sh) & 1) << 2);
+    v = __ldg(nodes + v + oct);
+  }
+  return ~v;
 }
 
 }  // namespace mars

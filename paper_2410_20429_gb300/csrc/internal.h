@@ -142,7 +142,18 @@ struct DevCache {
   float4* img;          // [pixels] this iteration's image
   DevCounters* ctr;
   unsigned int* tile_status;  // [max tiles] overflow per tile of the current attempt
+  // adaptive octree over the scene box (oct_nodes null: the uniform grid).
+  // node >= 0: first of its 8 children (octant x | y << 1 | z << 2); < 0: leaf ~cell
+  int* oct_nodes;       // [oct_cap_nodes]
+  int* oct_leaf_level;  // [n_cells]
+  int* oct_leaf_node;   // [n_cells] node holding the leaf
+  int* oct_meta;        // [0] nodes, [1] leaves, [2] splits of the last refinement
+  int* oct_split;       // [n_cells / 7 + 1] parent cell of split s
+  float* oct_leaf_n;    // [n_cells] samples of the last iteration per leaf
+  int oct_cap_nodes;
+  float split_samples;
 };
+constexpr int OCT_LMAX = MARS_OCTREE_MAX_LEVEL;
 
 struct IterArgs {
   uint32_t seed, job, iteration;
@@ -179,6 +190,10 @@ cudaError_t launch_image_stats(const DevCache& c, int width, int height, int n_p
                                float* image_out_dev, cudaStream_t st);
 cudaError_t launch_image_copy(const DevCache& c, int npix, float* out, cudaStream_t st);
 cudaError_t launch_update(const DevCache& c, int num_sms, cudaStream_t st);
+// octree refinement after an update (stats.cu): leaf_samples must run before
+// launch_update (which zeroes the statistics), refine after it
+cudaError_t launch_leaf_samples(const DevCache& c, cudaStream_t st);
+cudaError_t launch_octree_refine(const DevCache& c, int num_sms, cudaStream_t st);
 // scene build (scene.cu)
 cudaError_t build_bvh(const float4* d_prims, int n, const float lo[3], const float ext[3], BvhNode* d_nodes,
                       cudaStream_t st, std::string* err);

@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_shade(const DevScene
         // ---- budgets and Alg. 1 at vertex x_d
         flags |= F_EST;
         ns = cosg >= 0.0f ? ng : ng * -1.0f;
-        cell = cell_of(s, c.grid_n, p);
+        cell = c.oct_nodes ? octree_cell(s, c.oct_nodes, p) : cell_of(s, c.grid_n, p);
         mat.type = (int)m0.x;
         mat.alpha = m0.y;
         mat.col = xyz(m1);

@@ -245,7 +245,123 @@ __global__ void k_guide_update(DevCache c) {
   cdf[1] = make_float4(o[4], o[5], o[6], o[7]);
 }
 
+// samples of the iteration per octree leaf, all techniques (exact in float32
+// below 2^24), read before the update zeroes the statistics
+__global__ void k_leaf_samples(DevCache c) {
+  const int L = blockIdx.x * blockDim.x + threadIdx.x;
+  if (L >= c.oct_meta[1]) return;
+  float n = 0.0f;
+  const size_t plane = (size_t)c.n_cells * NT;
+#pragma unroll
+  for (int t = 0; t < NT; ++t)
+    n += c.stats32 ? c.stats32[((size_t)L * NT + t) * NSTAT] : (float)c.stats[(size_t)L * NT + t + 0 * plane];
+  c.oct_leaf_n[L] = n;
+}
+
+// Octree refinement (one block): leaves in cell order whose samples reached
+// split_samples and whose level is below OCT_LMAX split into 8 while the leaf
+// count stays within n_cells.  Split s turns the leaf's node into an internal
+// node with children at nodes + 8 s; octant 0 keeps the cell, octant o > 0
+// gets the new cell leaves + 7 s + o - 1.  The order, and hence the numbering,
+// comes from a block-wide exclusive scan: deterministic.
+constexpr int REFINE_THREADS = 1024;
+__global__ void __launch_bounds__(REFINE_THREADS) k_octree_refine(DevCache c) {
+  __shared__ int wsum[REFINE_THREADS / 32];
+  __shared__ int s_base;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nn = c.oct_meta[0], nl = c.oct_meta[1];
+  int budget = (c.n_cells - nl) / 7;
+  const int bn = (c.oct_cap_nodes - nn) / 8;
+  if (bn < budget) budget = bn;
+  if (tid == 0) s_base = 0;
+  __syncthreads();
+  for (int L0 = 0; L0 < nl; L0 += REFINE_THREADS) {
+    const int L = L0 + tid;
+    const int flag = (L < nl && c.oct_leaf_n[L] >= c.split_samples && c.oct_leaf_level[L] < OCT_LMAX) ? 1 : 0;
+    int incl = flag;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += y;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      int v = wsum[lane];
+      int wi = v;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, wi, off);
+        if (lane >= off) wi += y;
+      }
+      wsum[lane] = wi - v;  // exclusive prefix of the warp totals
+    }
+    __syncthreads();
+    const int s = s_base + wsum[warp] + incl - flag;
+    if (flag && s < budget) {
+      const int base = nn + 8 * s;
+      c.oct_nodes[c.oct_leaf_node[L]] = base;
+      c.oct_nodes[base] = ~L;
+      c.oct_leaf_node[L] = base;
+      const int lev = c.oct_leaf_level[L] + 1;
+      c.oct_leaf_level[L] = lev;
+      for (int o = 1; o < 8; ++o) {
+        const int cn = nl + 7 * s + o - 1;
+        c.oct_nodes[base + o] = ~cn;
+        c.oct_leaf_node[cn] = base + o;
+        c.oct_leaf_level[cn] = lev;
+      }
+      c.oct_split[s] = L;
+    }
+    __syncthreads();
+    if (tid == REFINE_THREADS - 1) s_base += wsum[warp] + incl;  // the pass's total
+    __syncthreads();
+  }
+  if (tid == 0) {
+    const int splits = s_base < budget ? s_base : budget;
+    c.oct_meta[0] = nn + 8 * splits;
+    c.oct_meta[1] = nl + 7 * splits;
+    c.oct_meta[2] = splits;
+  }
+}
+
+// children of this refinement inherit their parent's counts and guide
+// histogram and CDF (one thread per child)
+__global__ void k_octree_inherit(DevCache c) {
+  const int splits = c.oct_meta[2];
+  const int nl0 = c.oct_meta[1] - 7 * splits;
+  const bool guided = c.techniques & MARS_TECH_GUIDED;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 7 * splits; k += gridDim.x * blockDim.x) {
+    const int s = k / 7, o = k % 7 + 1;
+    const int L = c.oct_split[s], cn = nl0 + 7 * s + o - 1;
+#pragma unroll
+    for (int q = 0; q < 2 * NT; ++q) c.cnt[(size_t)cn * 2 * NT + q] = c.cnt[(size_t)L * 2 * NT + q];
+    if (guided) {
+      const float4* hs = reinterpret_cast<const float4*>(c.guide_hist + (size_t)L * GUIDE_BINS);
+      const float4* cs = reinterpret_cast<const float4*>(c.guide_cdf + (size_t)L * GUIDE_BINS);
+      float4* hd = reinterpret_cast<float4*>(c.guide_hist + (size_t)cn * GUIDE_BINS);
+      float4* cd = reinterpret_cast<float4*>(c.guide_cdf + (size_t)cn * GUIDE_BINS);
+      for (int q = 0; q < GUIDE_BINS / 4; ++q) {
+        hd[q] = hs[q];
+        cd[q] = cs[q];
+      }
+      c.guide_dirty[cn] = 0;
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_leaf_samples(const DevCache& c, cudaStream_t st) {
+  k_leaf_samples<<<(c.n_cells + 255) / 256, 256, 0, st>>>(c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_octree_refine(const DevCache& c, int num_sms, cudaStream_t st) {
+  k_octree_refine<<<1, REFINE_THREADS, 0, st>>>(c);
+  k_octree_inherit<<<num_sms, 128, 0, st>>>(c);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_image_stats(const DevCache& c, int width, int height, int n_prev, float outlier,
                                float* image_out_dev, cudaStream_t st) {

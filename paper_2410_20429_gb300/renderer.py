@@ -78,17 +78,22 @@ class Cache:
     """Statistics cache, count fields, guide and image accumulators of one job."""
 
     def __init__(self, scene: Scene, grid_n: int, techniques: int, max_depth: int, arena_capacity: int = 0,
-                 fp32_statistics: bool = False, stream=None):
+                 fp32_statistics: bool = False, octree: bool = False, max_leaves: int = 0,
+                 split_samples: float = 0.0, stream=None):
         self._lib = A.load()
         self.scene = scene
-        flags = A.MARS_CACHE_FP32_STATISTICS if fp32_statistics else 0
-        d = A.mars_cache_desc(int(grid_n), int(techniques), int(max_depth), flags, int(arena_capacity))
+        flags = (A.MARS_CACHE_FP32_STATISTICS if fp32_statistics else 0) | (A.MARS_CACHE_OCTREE if octree else 0)
+        d = A.mars_cache_desc(int(grid_n), int(techniques), int(max_depth), flags, int(arena_capacity),
+                              int(max_leaves), float(split_samples))
         h = ct.c_void_p()
         A.check(self._lib.mars_cache_create(scene.handle, ct.byref(d), _stream_handle(stream), ct.byref(h)),
                 "mars_cache_create")
         self.handle = h
         self.grid_n, self.techniques, self.max_depth = int(grid_n), int(techniques), int(max_depth)
-        self.n_cells = self.grid_n ** 3
+        self.octree = bool(octree)
+        info = self.info()
+        self.n_cells = int(info["n_cells"])   # grid_n^3, or the octree's leaf capacity
+        self.oct_cap_nodes = int(info["oct_cap_nodes"])
         self.n_pixels = scene.width * scene.height
 
     def info(self) -> dict:
@@ -178,14 +183,21 @@ class Cache:
         s.pixel_estimate, s.run_sum = _dp(out["pixel_estimate"], ct.c_float), _dp(out["run_sum"], ct.c_float)
         if guided:
             s.guide_hist, s.guide_cdf = _dp(out["guide_hist"], ct.c_float), _dp(out["guide_cdf"], ct.c_float)
+        if self.octree:
+            nodes = np.zeros(self.oct_cap_nodes, np.int32)
+            levels = np.zeros(c, np.int32)
+            s.oct_nodes, s.oct_leaf_level = _dp(nodes, ct.c_int32), _dp(levels, ct.c_int32)
         A.check(self._lib.mars_cache_get_state(self.handle, ct.byref(s), _stream_handle(stream)),
                 "mars_cache_get_state")
         out.update(n_iterations=s.n_iterations, has_estimate=bool(s.has_estimate), VI=s.VI, CI=s.CI)
+        if self.octree:
+            out.update(oct_nodes=nodes[:s.oct_n_nodes].copy(), oct_leaf_level=levels[:s.oct_n_leaves].copy(),
+                       oct_n_nodes=s.oct_n_nodes, oct_n_leaves=s.oct_n_leaves)
         return out
 
     def set_state(self, *, q_rr=None, q_s=None, valid=None, stats=None, guide_hist=None, guide_cdf=None,
                   pixel_estimate=None, run_sum=None, n_iterations=0, has_estimate=False, VI=0.0, CI=0.0,
-                  stream=None) -> None:
+                  oct_nodes=None, oct_leaf_level=None, stream=None) -> None:
         c, px = self.n_cells, self.n_pixels
         keep = []
 
@@ -207,6 +219,12 @@ class Cache:
         s.run_sum = arr(run_sum, np.float32, (px, 3), ct.c_float)
         s.n_iterations, s.has_estimate = int(n_iterations), int(bool(has_estimate))
         s.VI, s.CI = float(VI), float(CI)
+        if oct_nodes is not None:
+            on = np.ascontiguousarray(oct_nodes, np.int32)
+            ol = np.ascontiguousarray(oct_leaf_level, np.int32)
+            keep += [on, ol]
+            s.oct_nodes, s.oct_leaf_level = _dp(on, ct.c_int32), _dp(ol, ct.c_int32)
+            s.oct_n_nodes, s.oct_n_leaves = len(on), len(ol)
         A.check(self._lib.mars_cache_set_state(self.handle, ct.byref(s), _stream_handle(stream)),
                 "mars_cache_set_state")
 
@@ -238,7 +256,7 @@ class Server:
         d, keep = scene_desc(desc)
         j = A.mars_job_desc()
         j.scene = ct.pointer(d)
-        j.cache = A.mars_cache_desc(int(grid_n), int(techniques), int(max_depth), 0, int(arena_capacity))
+        j.cache = A.mars_cache_desc(int(grid_n), int(techniques), int(max_depth), 0, int(arena_capacity), 0, 0.0)
         j.seed, j.iterations, j.warmup, j.key = int(seed), int(iterations), int(warmup), int(key)
         jid = ct.c_uint64()
         A.check(self._lib.mars_submit(self.handle, ct.byref(j), ct.byref(jid)), "mars_submit")

@@ -512,3 +512,93 @@ def test_statistics_bookkeeping(orc):
     assert np.all(r.stats[:, 0, 7] >= r.stats[:, 0, 0])
     # estimator vertices never exceed the traced vertices
     assert r.counters[2] <= r.counters[1]
+
+
+# --------------------------------------------------------- adaptive octree
+def _leaf_boxes(nodes, lmax=10):
+    """brute force: every leaf's integer box at the finest level, by walking the tree"""
+    boxes = {}
+    stack = [(0, 0, 0, 0, 0)]
+    while stack:
+        k, lvl, x, y, z = stack.pop()
+        v = int(nodes[k])
+        size = 1 << (lmax - lvl)
+        if v < 0:
+            boxes[~v] = (x, y, z, size)
+            continue
+        half = size // 2
+        for o in range(8):
+            stack.append((v + o, lvl + 1, x + (o & 1) * half, y + ((o >> 1) & 1) * half, z + ((o >> 2) & 1) * half))
+    return boxes
+
+
+def _random_refinement(orc, grid_n, max_leaves, rounds, seed):
+    rng = np.random.default_rng(seed)
+    nodes, nn, nl, lvl, lnode = orc.octree_init(grid_n, max_leaves)
+    q_rr = rng.uniform(0.1, 3, (max_leaves, 3, 3)).astype(np.float32)
+    q_s = (q_rr * 0.5).astype(np.float32)
+    valid = (rng.uniform(size=(max_leaves, 3)) < 0.7).astype(np.uint8)
+    hist = rng.exponential(size=(max_leaves, 256))
+    cdf = np.cumsum(hist, 1) / hist.sum(1, keepdims=True)
+    cdf = cdf.astype(np.float32)
+    for r in range(rounds):
+        stats = np.zeros((max_leaves, 3, 8))
+        stats[:nl, :, 0] = rng.integers(0, 60, size=(nl, 3))
+        (nodes, nn2, nl2, lvl, lnode, q_rr2, q_s2, valid2, hist2, cdf2, sp) = orc.octree_refine(
+            max_leaves, 100.0, stats, nodes, nn, nl, lvl, lnode, q_rr, q_s, valid, hist, cdf)
+        # the rule: leaves in id order with >= 100 samples split while the cap allows
+        want = [L for L in range(nl) if stats[L, :, 0].sum() >= 100 and lvl[L] < 10]
+        assert sp == min(len(want), (max_leaves - nl) // 7)
+        assert nl2 == nl + 7 * sp and nn2 == nn + 8 * sp
+        for s_, L in enumerate(want[:sp]):
+            for o in range(1, 8):
+                c = nl + 7 * s_ + o - 1
+                assert np.array_equal(q_rr2[c], q_rr2[L]) and np.array_equal(valid2[c], valid2[L])
+                assert np.array_equal(cdf2[c], cdf2[L])
+        nn, nl, q_rr, q_s, valid, hist, cdf = nn2, nl2, q_rr2, q_s2, valid2, hist2, cdf2
+    return nodes, nn, nl, lvl, q_rr, q_s, valid, cdf
+
+
+def test_octree_refinement_rule_and_partition(orc):
+    """Refinement follows the stated rule (leaves in id order with enough
+    samples, cap on the leaf count, children inherit counts and guide), and the
+    leaves always partition the scene box: the descent finds, for random
+    points, the unique leaf whose box contains them."""
+    nodes, nn, nl, lvl, *_ = _random_refinement(orc, 4, 640, 3, seed=7)
+    assert nl > 64
+    boxes = _leaf_boxes(nodes)
+    assert sorted(boxes) == list(range(nl))
+    vol = sum(b[3] ** 3 for b in boxes.values())
+    assert vol == 1024 ** 3                      # the leaves tile the box exactly
+    rng = np.random.default_rng(8)
+    lo, ext = np.array([-1.0, 0.5, 2.0]), np.array([3.0, 2.0, 5.0])
+    for _ in range(400):
+        p = lo + ext * rng.uniform(0, 1, 3)
+        leaf = orc.octree_cell(lo, ext, nodes, p)
+        x, y, z, size = boxes[leaf]
+        idx = np.clip(np.floor(((p - lo) / ext).astype(np.float32) * np.float32(1024)), 0, 1023)
+        assert x <= idx[0] < x + size and y <= idx[1] < y + size and z <= idx[2] < z + size
+        assert lvl[leaf] == 10 - int(np.log2(size))
+
+
+def test_octree_without_splits_is_the_grid_and_refined_tree_is_unbiased(orc):
+    """The initial octree numbers its leaves like the uniform grid, so an
+    unrefined octree renders exactly the grid's image and statistics; under a
+    refined tree with random counts the box's image mean is that of beta = 1
+    (any count field keeps the estimator unbiased)."""
+    cfg = W.config_box(24, 20)
+    kw = dict(grid_n=8, techniques=cfg.techniques, max_depth=cfg.max_depth, seed=1)
+    nodes, nn, nl, lvl, lnode = orc.octree_init(8, 2048)
+    a = orc.render(cfg.scene, iteration=0, **kw)
+    b = orc.render(cfg.scene, iteration=0, octree=(nodes, 2048), **kw)
+    assert np.array_equal(a.image, b.image) and np.array_equal(a.stats, b.stats[:512])
+    nodes, nn, nl, lvl, q_rr, q_s, valid, cdf = _random_refinement(orc, 8, 2048, 2, seed=9)
+    est = W.random_pixel_estimate(cfg.scene.n_pixels, seed=10, lo=0.05, hi=0.5)
+    ref, mars = [], []
+    for it in range(30):
+        ref.append(orc.render(cfg.scene, iteration=it, **kw).image.mean())
+        mars.append(orc.render(cfg.scene, iteration=it, mode=orc.MODE_MARS, q_rr=q_rr, q_s=q_s, valid=valid,
+                               est=est, octree=(nodes, 2048), **kw).image.mean())
+    m1, s1 = _mean_and_sem(ref)
+    m2, s2 = _mean_and_sem(mars)
+    assert abs(m1 - m2) < 3.5 * math.sqrt(s1 ** 2 + s2 ** 2)
