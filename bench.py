@@ -101,6 +101,39 @@ def sm_max_mhz():
 OPS_NODE, OPS_QUAD, OPS_SPHERE, OPS_TRI = 50, 67, 25, 45
 
 
+KERNEL_SOURCES = ["paper_2410_20429_gb300/csrc/render.cu", "paper_2410_20429_gb300/csrc/device.cuh",
+                  "paper_2410_20429_gb300/csrc/internal.h"]
+TRAFFIC_FILE = "profiles/dram_traffic_guided_room_512.txt"
+
+
+def kernel_sources_sha():
+    """sha256 of the wave kernels' sources: DRAM traffic measured on other
+    sources does not describe these kernels."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic():
+    """Per-launch DRAM bytes of each wave kernel from the committed ncu summary,
+    if it was taken on the current kernel sources; else {}."""
+    p = os.path.join(ROOT, TRAFFIC_FILE)
+    if not os.path.exists(p):
+        return {}
+    vals, sha = {}, None
+    for line in open(p):
+        parts = line.split()
+        if len(parts) == 2 and not line.startswith("#"):
+            if parts[0] == "sources_sha256":
+                sha = parts[1]
+            else:
+                vals[parts[0]] = float(parts[1])
+    return vals if sha == kernel_sources_sha() else {}
+
+
 def trace_ops(work):
     n, q, sp, t = work
     return OPS_NODE * n + OPS_QUAD * q + OPS_SPHERE * sp + OPS_TRI * t
@@ -220,8 +253,9 @@ def run_mars(args):
         cache.update_counts(stream=stream)
         return st
 
+    curve = []
     for _ in range(args.warmup):
-        step(it, M.MARS_MODE_WARMUP)
+        curve.append(step(it, M.MARS_MODE_WARMUP))
         it += 1
     # launch shape of the wave kernels picked by the library's autotuner on a
     # MARS iteration with the counts learned so far (no state change)
@@ -283,10 +317,17 @@ def run_mars(args):
                                         "prim_tests": round(sum(tw[0][1:]) / n_closest, 2)}
     per_kernel["k_shadow"]["per_ray"] = {"nodes": round(tw[1][0] / n_shadow, 2),
                                          "prim_tests": round(sum(tw[1][1:]) / n_shadow, 2)}
-    dom = max(kms, key=kms.get)
+    # dominant kernel: the longest of the kernels on the rendering stream (the
+    # shadow kernel overlaps the next waves on the side stream, so its event
+    # time is not time the iteration waits for)
+    dom = max(("k_trace", "k_shade", "k_reverse"), key=kms.get)
     d0 = per_kernel[dom]
+    traffic = measured_traffic().get(dom)
     roofline = {"kernel": dom, "bound": d0["bound"], "achieved": d0["achieved"], "peak": d0["peak"],
-                "unit": d0["unit"], "frac": d0["frac"], "traffic": None,
+                "unit": d0["unit"], "frac": d0["frac"],
+                "traffic": int(traffic) if traffic is not None else None,
+                "traffic_note": "DRAM read + write bytes per launch from one ncu pass (cold L2), " + TRAFFIC_FILE,
+                "overlapped": ["k_shadow"],
                 "peak_kind": peak_kind if d0["bound"] == "hbm" else
                 "derived: SMs x 128 FP32 lanes x 2 x max SM clock (measured)",
                 "per_launch": d0["per_launch"], "launch_ms": d0["launch_ms"],
@@ -332,6 +373,11 @@ def run_mars(args):
                      "mean_beta": [round(sum(s["mean_beta"][t] for s in sts) / args.steps, 4) for t in range(3)],
                      "tiles": sum(s["tiles"] for s in sts) / args.steps},
         "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+        # Fig. convergence (E8): average allocation per technique and the image
+        # efficiency estimate 1 / (V_I C_I) over the fixed-point iterations
+        "convergence": {"mean_beta": [[round(b, 4) for b in s["mean_beta"]] for s in curve + sts],
+                        "efficiency_estimate": [round(1.0 / max(s["VI"] * s["CI"], 1e-30), 4)
+                                                for s in curve + sts]},
         "launch": {"kernels": ["trace", "shade", "shadow", "reverse"], **launch,
                    "autotuned": not (args.no_autotune or args.launch)},
     }

@@ -348,3 +348,40 @@ def test_invalid_arguments_are_reported(mars):
         mars.Scene(bad)
     # the cache still works after rejected calls
     cache.render_iteration(img)
+
+
+@pytest.mark.parametrize("octree", [False, True])
+def test_checkpoint_resume_continues_the_run(mars, octree):
+    """Checkpoint / resume: the state of a run after a few fixed-point
+    iterations, copied into a fresh cache, continues exactly as the original:
+    the next iteration's image is bitwise equal (same counts, estimate, guide,
+    tree and random numbers); the one after agrees within the pixel bar (the
+    statistics of the resumed iteration are summed in another atomic order)."""
+    import torch
+    cfg = W.config_guided(48, 40)
+    scene = mars.Scene(cfg.scene)
+    kw = dict(octree=True, max_leaves=4096, split_samples=30.0) if octree else {}
+    a = mars.Cache(scene, 8, cfg.techniques, 6, **kw)
+    img = torch.zeros(a.n_pixels * 3, dtype=torch.float32, device="cuda")
+    for it in range(4):
+        a.render_iteration(img, seed=21, iteration=it, mode=0 if it < 2 else 1, update_estimate=True)
+        a.update_counts()
+    s = a.get_state()
+    if octree:
+        assert s["oct_n_leaves"] > 512
+    b = mars.Cache(scene, 8, cfg.techniques, 6, **kw)
+    extra = dict(oct_nodes=s["oct_nodes"], oct_leaf_level=s["oct_leaf_level"]) if octree else {}
+    b.set_state(q_rr=s["q_rr"], q_s=s["q_s"], valid=s["valid"], stats=s["stats"], guide_hist=s["guide_hist"],
+                guide_cdf=s["guide_cdf"], pixel_estimate=s["pixel_estimate"], run_sum=s["run_sum"],
+                n_iterations=s["n_iterations"], has_estimate=s["has_estimate"], VI=s["VI"], CI=s["CI"], **extra)
+    outs = []
+    for c in (a, b):
+        imgs = []
+        for it in (4, 5):
+            c.render_iteration(img, seed=21, iteration=it, mode=1, update_estimate=True)
+            c.update_counts()
+            torch.cuda.synchronize()
+            imgs.append(img.cpu().numpy().reshape(-1, 3).astype(np.float64))
+        outs.append(imgs)
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert _pixel_agreement(outs[1][1], outs[0][1]) >= 0.999
