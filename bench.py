@@ -391,6 +391,9 @@ def run_mars(args):
     if rank == 0 and not args.no_efficiency:
         line["efficiency"] = efficiency(args, M, cfg, scene, cache, seed, it, stream)
         line["efficiency_box"] = box_efficiency(args, M, stream)
+        # the same after 16 learning iterations: the counts of 3 one-sample MARS
+        # iterations on a 64 x 64 image are still noisy
+        line["efficiency_box_16"] = box_efficiency(args, M, stream, iterations=16)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg, args.cpu_seconds)
     if world > 1:
@@ -566,7 +569,7 @@ def efficiency(args, M, cfg, scene, cache, seed, it0, stream):
                         "other random numbers"}
 
 
-def box_efficiency(args, M, stream):
+def box_efficiency(args, M, stream, iterations=None):
     """The box workload (64 x 64, D = 5, BSDF + NEE, 8^3 grid; the paper's own
     failure case, where MARS's overhead can dominate): 1 warm-up and 3 MARS
     fixed-point iterations learn the counts, then the same equal-time comparison
@@ -574,11 +577,12 @@ def box_efficiency(args, M, stream):
     MARS iteration (launch-bound at this size)."""
     import torch
     cfg = W.config_box(64, 64)
+    n_iter = iterations or cfg.iterations
     scene = M.Scene(cfg.scene, stream=stream)
     cache = M.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, stream=stream)
     img = torch.zeros(cfg.scene.n_pixels * 3, dtype=torch.float32, device="cuda")
     it = 0
-    for k in range(cfg.iterations):
+    for k in range(n_iter):
         mode = M.MARS_MODE_WARMUP if k < cfg.warmup else M.MARS_MODE_MARS
         cache.render_iteration(img, seed=2024, iteration=it, mode=mode, update_estimate=True, stream=stream)
         cache.update_counts(stream=stream)
@@ -597,6 +601,7 @@ def box_efficiency(args, M, stream):
     ms = e0.elapsed_time(e1) / n
     eff = efficiency(args, M, cfg, scene, cache, 2024, it, stream)
     eff["workload"] = cfg.name
+    eff["learning_iterations"] = n_iter
     eff["iteration_ms"] = round(ms, 4)
     eff["mvertices_s"] = round(verts / n / (ms * 1e-3) / 1e6, 2)
     return eff

@@ -385,3 +385,44 @@ def test_checkpoint_resume_continues_the_run(mars, octree):
         outs.append(imgs)
     assert np.array_equal(outs[0][0], outs[1][0])
     assert _pixel_agreement(outs[1][1], outs[0][1]) >= 0.999
+
+
+def test_relmse_against_a_long_reference_matches_the_oracle(mars, orc):
+    """Third agreement criterion: the relMSE of the CUDA path's N-iteration
+    image and of the oracle's (same random numbers, same teacher-forced counts)
+    against a long reference render agree within 2 % of the oracle's.  The
+    reference is a 2048-iteration fixed-count render of the CUDA path with other
+    random numbers (the oracle's speed rules out a 64k-spp one here)."""
+    import torch
+    cfg = W.config_box(32, 32)
+    scene, cache = _make(mars, cfg)
+    ref_cache = mars.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth)
+    npx = cfg.scene.n_pixels
+    img = torch.zeros(npx * 3, dtype=torch.float32, device="cuda")
+    acc = torch.zeros(npx * 3, dtype=torch.float64, device="cuda")
+    for k in range(2048):
+        ref_cache.render_iteration(img, seed=999, iteration=k, mode=mars.MARS_MODE_FIXED, collect=False,
+                                   update_estimate=False)
+        acc += img.double()
+    ref = (acc / 2048).cpu().numpy().reshape(-1, 3)
+    q_rr, q_s, valid = W.random_count_fields(cfg.n_cells, seed=141, lo=0.1, hi=3.0)
+    est = W.random_pixel_estimate(npx, seed=142, lo=0.05, hi=0.5)
+    cache.set_state(q_rr=q_rr, q_s=q_s, valid=valid, pixel_estimate=est, has_estimate=True, n_iterations=1)
+    g_acc = np.zeros((npx, 3))
+    o_acc = np.zeros((npx, 3))
+    N = 16
+    for k in range(N):
+        g, _ = _gpu_iteration(mars, cache, iteration=10 + k, seed=5, mode=1, collect=False)
+        o = orc.render(cfg.scene, grid_n=cfg.grid_n, techniques=cfg.techniques, max_depth=cfg.max_depth,
+                       iteration=10 + k, seed=5, mode=orc.MODE_MARS, q_rr=q_rr, q_s=q_s, valid=valid, est=est,
+                       collect=False)
+        g_acc += g
+        o_acc += o.image
+
+    def rel_mse(x):
+        t = ((x - ref) ** 2 / (ref ** 2 + 1e-2)).mean(axis=1)
+        k = int(np.ceil(1e-4 * t.size))
+        return np.sort(t)[:-k].mean() if k else t.mean()
+
+    rg, ro = rel_mse(g_acc / N), rel_mse(o_acc / N)
+    assert ro > 0 and abs(rg - ro) <= 0.02 * ro, (rg, ro)
