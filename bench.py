@@ -449,6 +449,20 @@ def large_scene(args, M, stream):
            "closest_hit_per_ray": {"nodes": round(tw[0] / n, 2), "prim_tests": round(sum(tw[1:]) / n, 2)},
            "mean_beta": [round(sum(s["mean_beta"][t] for s in sts) / 3, 4) for t in range(3)],
            "octree_leaves": int(cache.info()["oct_n_leaves"]), "launch": launch}
+    if not args.no_precision:
+        # float32 versus float64 statistics at this size (the large bidirectional
+        # workload's precision comparison), on the learned state and tree
+        from paper_2410_20429_gb300 import precision
+        g = cache.get_state(stream=stream)
+        rep = precision.compare(cfg.scene, cfg.grid_n, cfg.techniques, cfg.max_depth, g["q_rr"], g["q_s"],
+                                g["valid"], g["pixel_estimate"], g["run_sum"], g["n_iterations"], iteration=it,
+                                seed=77, stream=stream,
+                                cache_kw=dict(octree=True, max_leaves=65536, split_samples=4096.0),
+                                tree=(g["oct_nodes"], g["oct_leaf_level"]), guide_cdf=g["guide_cdf"])
+        out["precision"] = {k: [float("%.3g" % rep[k]["max"]), float("%.3g" % rep[k]["median"])]
+                            for k in precision.STATISTICS}
+        out["precision"]["entries"] = rep["cells_compared"]
+        out["precision"]["images_equal"] = rep["images_equal"]
     del cache, scene
     return out
 
@@ -516,7 +530,7 @@ def precision_study(cfg, cache, seed, it, stream):
     g = cache.get_state(stream=stream)
     rep = precision.compare(cfg.scene, cfg.grid_n, cfg.techniques, cfg.max_depth, g["q_rr"], g["q_s"], g["valid"],
                             g["pixel_estimate"], g["run_sum"], g["n_iterations"], iteration=it, seed=seed,
-                            stream=stream)
+                            stream=stream, guide_cdf=g.get("guide_cdf"))
     out = {k: [float("%.3g" % rep[k]["max"]), float("%.3g" % rep[k]["median"])] for k in precision.STATISTICS}
     out["fields"] = "relative error of float32 vs float64 statistics: [max, median]"
     out["images_equal"] = rep["images_equal"]

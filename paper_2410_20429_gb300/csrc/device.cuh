@@ -328,6 +328,7 @@ __device__ __forceinline__ Frame make_frame(f3 n) {
 // reflection (Walter et al. 2007): D with roughness alpha, height-correlated
 // Smith masking, Schlick Fresnel with F0 = colour, sampling of D(h) cos(theta_h).
 constexpr float PI_F = 3.14159265358979323846f;
+constexpr float INV_PI_F = 0.318309886183790671538f;
 constexpr float TWO_PI_F = 6.28318530717958647692f;
 
 struct Mat {
@@ -348,8 +349,10 @@ __device__ __forceinline__ f3 bsdf_eval(const Mat& m, f3 wo, f3 wi, float& pdf) 
   pdf = 0.0f;
   if (wo.z <= 0.0f || wi.z <= 0.0f) return mk3(0.f, 0.f, 0.f);
   if (m.type == 0) {
-    pdf = wi.z / PI_F;
-    return mk3(m.col.x / PI_F * wi.z, m.col.y / PI_F * wi.z, m.col.z / PI_F * wi.z);
+    // cos / pi, with one multiplication by 1 / pi instead of divisions
+    const float cp = wi.z * INV_PI_F;
+    pdf = cp;
+    return mk3(m.col.x * cp, m.col.y * cp, m.col.z * cp);
   }
   const float a2 = m.alpha * m.alpha;
   const f3 h = normalize(wo + wi);
@@ -358,12 +361,13 @@ __device__ __forceinline__ f3 bsdf_eval(const Mat& m, f3 wo, f3 wi, float& pdf) 
   // 1 + cos^2(alpha^2 - 1) = sin^2 + alpha^2 cos^2 for a unit h: no cancellation
   // near the specular peak of a smooth surface
   const float k = (h.x * h.x + h.y * h.y) + a2 * (h.z * h.z);
-  const float D = a2 / (PI_F * k * k);
+  const float D = a2 * INV_PI_F / (k * k);
   const float G = 1.0f / (1.0f + ggx_lambda(a2, wo) + ggx_lambda(a2, wi));
   const float sf = 1.0f - woh;
   const float s5 = sf * sf * sf * sf * sf;
-  const float base = D * G / (4.0f * wo.z);
-  pdf = D * h.z / (4.0f * woh);
+  const float D4 = 0.25f * D;
+  const float base = D4 * G / wo.z;
+  pdf = D4 * h.z / woh;
   return mk3((m.col.x + (1.0f - m.col.x) * s5) * base, (m.col.y + (1.0f - m.col.y) * s5) * base,
              (m.col.z + (1.0f - m.col.z) * s5) * base);
 }

@@ -355,6 +355,9 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_shade(const DevScene
         // counts without learned statistics: one NEE sample and one
         // continuation sample split evenly over BSDF and guided sampling
         const float base_cont = (on_b && on_g) ? 0.5f : 1.0f;
+        // T / I_px per channel and the multiplicity cap, once per vertex
+        const f3 f = mk3(T.x / est.x, T.y / est.y, T.z / est.z);
+        const float cap = it.max_mult > 0.0f ? fmaxf(it.max_mult / mult, it.clamp_lo) : inf;
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
           const bool on = (c.techniques >> t) & 1;
@@ -363,15 +366,15 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_shade(const DevScene
             const float4 qr = __ldg(c.cnt + (2 * (NT * cell + t)));
             if (qr.w > 0.0f) {
               const float4 qs = __ldg(c.cnt + (2 * (NT * cell + t) + 1));
-              const f3 f = mk3(T.x / est.x, T.y / est.y, T.z / est.z);
               const f3 ar = mul(f, xyz(qr)), as = mul(f, xyz(qs));
-              const float brr = sqrtf(dot(ar, ar) / 3.0f), bs = sqrtf(dot(as, as) / 3.0f);
+              // root mean square over the channels
+              const float brr = sqrtf(dot(ar, ar) * (1.0f / 3.0f)), bs = sqrtf(dot(as, as) * (1.0f / 3.0f));
               b = brr < 1.0f ? brr : (bs > 1.0f ? bs : 1.0f);
               b = fminf(fmaxf(b, it.clamp_lo), it.clamp_hi);
             }
           }
           // path multiplicity cap: b <= max(clamp_lo, M / P)
-          if (on && it.max_mult > 0.0f) b = fminf(b, fmaxf(it.max_mult / mult, it.clamp_lo));
+          if (on) b = fminf(b, cap);
           beta[t] = b;
         }
         // Alg. 1: one uniform decides the rounding of every technique
@@ -512,9 +515,10 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_shade(const DevScene
           const float pg = on_g ? guide_pdf(c.guide_cdf + (size_t)__float_as_int(cx[C_CELL * 32 + L]) * GUIDE_BINS, wi)
                                 : 0.0f;
           if (nonzero(fc)) {
+            // f|cos| Le / p_N times the balance weight beta_N p_N / den: p_N cancels
             const float den = bwB * pb + bwG * pg + bwNv * pn;
-            const float wgt = bwNv * pn / den;
-            v = mk3(fc.x * l4.x / pn * wgt, fc.y * l4.y / pn * wgt, fc.z * l4.z / pn * wgt);
+            const float sc = bwNv / den;
+            v = mk3(fc.x * l4.x * sc, fc.y * l4.y * sc, fc.z * l4.z * sc);
           }
         }
         a.SH[2][j] = f4(v, 0.0f);
@@ -591,11 +595,13 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_shade(const DevScene
           const float pg = on_g ? guide_pdf(cdf, wi) : 0.0f;
           if (t == 0) pt = pb;
           if (pt > 0.0f && nonzero(fc)) {
-            cf = mk3(fc.x / pt, fc.y / pt, fc.z / pt);
+            const float ipt = 1.0f / pt;
+            cf = mk3(fc.x * ipt, fc.y * ipt, fc.z * ipt);
             cA = (t == 0 ? bwB : bwG) * pt;
             cS = bwB * pb + bwG * pg;
             const float w_ind = cA / cS;
-            cT = mk3(vT.x * cf.x * w_ind / bt, vT.y * cf.y * w_ind / bt, vT.z * cf.z * w_ind / bt);
+            const float wb = w_ind / bt;
+            cT = mk3(vT.x * cf.x * wb, vT.y * cf.y * wb, vT.z * cf.z * wb);
             const float sb = bB * pb + (on_g ? bG * pg : 0.0f);
             cinvSb = sb > 0.0f ? 1.0f / sb : 0.0f;
           }
@@ -734,11 +740,14 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_reverse(const DevSce
               st[1][4] += vc.x * vc.x; st[1][5] += vc.y * vc.y; st[1][6] += vc.z * vc.z;
             }
           }
-          Lr = mk3(sum.x / bt[1], sum.y / bt[1], sum.z / bt[1]);
+          const float ib1 = 1.0f / bt[1];
+          Lr = mk3(sum.x * ib1, sum.y * ib1, sum.z * ib1);
           csub += (uint32_t)gN;
           st[1][0] = (float)gN;
           st[1][7] = (float)gN;
         }
+        // 1 / beta once per technique, not one division per child value
+        const float ib0 = gB > 0 ? 1.0f / bt[0] : 0.0f, ib2 = gG > 0 ? 1.0f / bt[2] : 0.0f;
         for (int k = 0; k < ne; k += 4) {
           if (k > 0) {
 #pragma unroll
@@ -749,8 +758,8 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_reverse(const DevSce
             if (k + q >= ne) break;
             const float4 sv = pe[q];
             const int t = k + q < gB ? 0 : 2;
-            const float b = bt[t];
-            Lr = Lr + mk3(sv.x / b, sv.y / b, sv.z / b);
+            const float ib = t == 0 ? ib0 : ib2;
+            Lr = Lr + mk3(sv.x * ib, sv.y * ib, sv.z * ib);
             const uint32_t cc = __float_as_uint(sv.w);
             csub += cc;
             const f3 vc = fmin3(xyz(sv), climit);

@@ -35,18 +35,22 @@ def _summary(r):
 
 
 def compare(scene_desc, grid_n, techniques, max_depth, q_rr, q_s, valid, pixel_estimate, run_sum, n_prev,
-            iteration=1, seed=0, min_samples=2, stream=None):
+            iteration=1, seed=0, min_samples=2, stream=None, cache_kw=None, tree=None, guide_cdf=None):
     """Render one MARS iteration on a float64 and a float32-statistics cache
     from the same state; returns {statistic: {max, p99, median, count}} of the
     float32 run's relative error over the populated (cell, technique) entries
     with at least ``min_samples`` samples (per channel for the rgb sums), plus
-    the two images' agreement."""
+    the two images' agreement.  ``cache_kw`` (e.g. the octree settings) and
+    ``tree`` = (oct_nodes, oct_leaf_level) configure both caches alike."""
     scene = Scene(scene_desc, stream=stream)
     res = {}
     for fp32 in (False, True):
-        cache = Cache(scene, grid_n, techniques, max_depth, fp32_statistics=fp32, stream=stream)
+        cache = Cache(scene, grid_n, techniques, max_depth, fp32_statistics=fp32, stream=stream, **(cache_kw or {}))
+        extra = {} if tree is None else dict(oct_nodes=tree[0], oct_leaf_level=tree[1])
+        if guide_cdf is not None:
+            extra["guide_cdf"] = guide_cdf
         cache.set_state(q_rr=q_rr, q_s=q_s, valid=valid, pixel_estimate=pixel_estimate, run_sum=run_sum,
-                        n_iterations=n_prev, has_estimate=True, stream=stream)
+                        n_iterations=n_prev, has_estimate=True, stream=stream, **extra)
         img = np.zeros(3 * cache.n_pixels, np.float32)
         st = cache.render_iteration(img, seed=seed, iteration=iteration, mode=A.MARS_MODE_MARS,
                                     update_estimate=True, stream=stream)
