@@ -237,7 +237,7 @@ def run_mars(args):
     with torch.cuda.stream(stream):
         scene = M.Scene(sc, stream=stream)
         cache = M.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, arena_capacity=args.arena_capacity,
-                        stream=stream)
+                        graphs=not args.no_graphs, stream=stream)
     if args.launch:
         parts = args.launch.split(":")
         regs = [int(x) for x in parts[2].split(",")] if len(parts) > 2 else [0, 0, 0, 0]
@@ -268,25 +268,39 @@ def run_mars(args):
                           if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/mars_clocks_{rank}.csv")
     time.sleep(0.3)
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    sts = []
+    timed = []
     torch.cuda.synchronize()
     evs[0].record(stream)
     for k in range(args.steps):
-        sts.append(step(it, M.MARS_MODE_MARS, profile=True))
+        timed.append(step(it, M.MARS_MODE_MARS))
         it += 1
         evs[k + 1].record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
     per_step = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
     total_ms = sum(per_step)
-    verts = sum(s["vertices"] for s in sts)
+    verts = sum(s["vertices"] for s in timed)
     t_max, verts_all = reduce_over_ranks(total_ms, verts, world, "cuda")
     value = verts_all / (t_max * 1e-3) / 1e6
+    captures = cache.info()["graph_captures"]
+
+    # ---- as many MARS steps again with every launch between CUDA events
+    # (direct launches, no graph replay): the per-kernel device times
+    sts = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        sts.append(step(it, M.MARS_MODE_MARS, profile=True))
+        it += 1
+    e1.record(stream)
+    torch.cuda.synchronize()
+    profiled_ms = e0.elapsed_time(e1) / args.steps
+    verts_prof = sum(s["vertices"] for s in sts)
 
     # ---- dominant kernel roofline (live CUDA-event times of every launch)
     guided = bool(cfg.techniques & W.TECH_GUIDED)
     kb = kernel_bytes(sum(s["wave_entries"] for s in sts), npx * args.steps,
-                      sum(s["estimator_vertices"] for s in sts), verts, sum(s["shadow_entries"] for s in sts),
+                      sum(s["estimator_vertices"] for s in sts), verts_prof, sum(s["shadow_entries"] for s in sts),
                       sum(s["shadow_traced"] for s in sts), guided)
     kms = {k: sum(s[k[2:] + "_ms"] for s in sts) for k in kb}
     nlaunch = {k: sum(s["wave_launches"] for s in sts) for k in kb}
@@ -357,7 +371,7 @@ def run_mars(args):
     e2e = {"value": round(e2e_verts / e2e_s / 1e6, 3), "unit": UNIT, "h2d_bytes_per_step": 48,
            "d2h_bytes_per_step": npx * 3 * 4 + 512}
 
-    launches = sum(s["launches"] for s in sts) + args.steps * (2 if guided else 1)
+    launches = sum(s["launches"] for s in timed) + args.steps * (2 if guided else 1)
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 4), "higher_is_better": True,
@@ -369,15 +383,20 @@ def run_mars(args):
                    "parallelism": f"replicas x{world}"},
         "latency_ms": {"p50": round(float(np.percentile(per_step, 50)), 4),
                        "p99": round(float(np.percentile(per_step, 99)), 4)},
-        "per_step": {"vertices": verts / args.steps, "rays": sum(s["rays"] for s in sts) / args.steps,
-                     "mean_beta": [round(sum(s["mean_beta"][t] for s in sts) / args.steps, 4) for t in range(3)],
-                     "tiles": sum(s["tiles"] for s in sts) / args.steps},
+        "per_step": {"vertices": verts / args.steps, "rays": sum(s["rays"] for s in timed) / args.steps,
+                     "mean_beta": [round(sum(s["mean_beta"][t] for s in timed) / args.steps, 4) for t in range(3)],
+                     "tiles": sum(s["tiles"] for s in timed) / args.steps},
+        # the timed steps replay a recorded CUDA graph per iteration shape; the
+        # profiled steps (kernel times) launch every kernel directly
+        "graphs": {"enabled": not args.no_graphs, "captures_in_timed_steps": captures,
+                   "profiled_ms_per_step": round(profiled_ms, 4),
+                   "profiled_mvertices_s": round(verts_prof / (profiled_ms * args.steps * 1e-3) / 1e6, 3)},
         "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
         # Fig. convergence (E8): average allocation per technique and the image
         # efficiency estimate 1 / (V_I C_I) over the fixed-point iterations
-        "convergence": {"mean_beta": [[round(b, 4) for b in s["mean_beta"]] for s in curve + sts],
+        "convergence": {"mean_beta": [[round(b, 4) for b in s["mean_beta"]] for s in curve + timed + sts],
                         "efficiency_estimate": [round(1.0 / max(s["VI"] * s["CI"], 1e-30), 4)
-                                                for s in curve + sts]},
+                                                for s in curve + timed + sts]},
         "launch": {"kernels": ["trace", "shade", "shadow", "reverse"], **launch,
                    "autotuned": not (args.no_autotune or args.launch)},
     }
@@ -485,7 +504,7 @@ def serving(args):
             time.sleep(wait)
         ids.append(srv.submit(r["scene"], grid_n=r["grid_n"], techniques=r["techniques"],
                               max_depth=r["max_depth"], iterations=r["iterations"], warmup=r["warmup"],
-                              seed=r["seed"], key=r["key"]))
+                              seed=r["seed"], key=r["key"], graphs=not args.serve_no_graphs))
     done = {}
     while len(done) < len(ids):
         for j in ids:
@@ -509,6 +528,7 @@ def serving(args):
         peak = max(peak, cur)
     srv.close()
     return {"requests": len(ids), "rate_per_s": args.serve_rate, "slots": args.serve_slots,
+            "graphs": not args.serve_no_graphs,
             "budget_gb": 40, "failed": sum(s["state"] != M.MARS_JOB_DONE for s in sts),
             "iterations": int(lat.size), "iter_ms_p50": round(float(np.percentile(lat, 50)), 3),
             "iter_ms_p99": round(float(np.percentile(lat, 99)), 3),
@@ -703,11 +723,13 @@ def main():
     ap.add_argument("--eff-spp", type=int, default=32)
     ap.add_argument("--ref-pixels-per-step", type=int, default=1024)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-graphs", action="store_true", help="launch every kernel directly (no CUDA graph replay)")
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the heightfield (131k triangles) section")
     ap.add_argument("--serve-requests", type=int, default=256, help="serving-stream requests (0 = skip)")
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-no-graphs", action="store_true", help="served jobs launch every kernel directly")
     ap.add_argument("--launch", default="", help="fixed wave-kernel launch shape 't,t,t,t:b,b,b,b[:r,r,r,r]' (threads per "
                     "block, blocks per SM and register cap of trace, shade, shadow, reverse); skips the autotuner")
     ap.add_argument("--arena-capacity", type=int, default=0, help="queue arena slots (0 = library default)")

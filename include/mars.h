@@ -105,12 +105,19 @@ typedef struct {
  *   split_samples samples (all techniques) in the iteration into 8 children,
  *   down to 1024 cells per axis and while the leaves number at most
  *   max_leaves; children inherit the counts and the guide distribution.
+ *   MARS_CACHE_NO_GRAPHS: launch every kernel of an iteration directly.  By
+ *   default an iteration that fits the arena in one pixel tile, is not
+ *   profiled and runs on a stream other than the legacy default stream (which
+ *   cannot be captured) is recorded once as a CUDA graph and replayed; the
+ *   graph is recorded again when the output buffer, update_estimate, the
+ *   launch shape or the waves' sizes outgrow it.  Results are the same.
  * max_leaves, split_samples: octree only (0: 65536 leaves, 4096 samples).
  * arena_capacity: rays held by the per-iteration queue arena summed over all
  *   depths (0 = 3 x pixels x max_depth, at least 2^20).  An iteration whose path
  *   trees do not fit is rendered in pixel tiles (results do not depend on it). */
 #define MARS_CACHE_FP32_STATISTICS 1
 #define MARS_CACHE_OCTREE 2
+#define MARS_CACHE_NO_GRAPHS 4
 #define MARS_OCTREE_MAX_LEVEL 10
 typedef struct {
   int32_t grid_n;
@@ -215,7 +222,8 @@ typedef struct {
   int32_t device;
   int32_t n_lights;
   int32_t oct_n_nodes, oct_n_leaves;  /* octree caches: current tree size (0 for a grid) */
-  int32_t oct_cap_nodes, reserved;    /* octree caches: node capacity (state buffers) */
+  int32_t oct_cap_nodes;              /* octree caches: node capacity (state buffers) */
+  int32_t graph_captures;             /* iteration graphs recorded so far */
 } mars_cache_info;
 
 /* ---- scene ------------------------------------------------------------

@@ -17,6 +17,7 @@ MARS_WEIGHTS_AWARE, MARS_WEIGHTS_UNAWARE = 0, 1
 MARS_JOB_QUEUED, MARS_JOB_RUNNING, MARS_JOB_DONE, MARS_JOB_FAILED = range(4)
 MARS_CACHE_FP32_STATISTICS = 1
 MARS_CACHE_OCTREE = 2
+MARS_CACHE_NO_GRAPHS = 4
 NUM_SLOTS, NUM_STATS, GUIDE_BINS, MAX_DEPTH = 3, 8, 256, 16
 
 
@@ -85,7 +86,7 @@ class mars_cache_info(ct.Structure):
         ("max_depth", ct.c_int32), ("n_prims", ct.c_int32), ("arena_capacity", ct.c_uint64),
         ("device_bytes", ct.c_uint64), ("device", ct.c_int32), ("n_lights", ct.c_int32),
         ("oct_n_nodes", ct.c_int32), ("oct_n_leaves", ct.c_int32), ("oct_cap_nodes", ct.c_int32),
-        ("reserved", ct.c_int32),
+        ("graph_captures", ct.c_int32),
     ]
 
 

@@ -494,7 +494,7 @@ uint64_t cache_footprint(int64_t cells, int64_t pixels, int max_depth, int techn
   b += (uint64_t)cells * NT * (2 * sizeof(float4) + NSTAT * sizeof(double));
   if (techniques & MARS_TECH_GUIDED) b += (uint64_t)cells * GUIDE_BINS * 2 * sizeof(float);
   b += (uint64_t)pixels * 3 * sizeof(float4);
-  return b + sizeof(DevCounters) + 4096;
+  return b + sizeof(DevCounters) + 4096 * (sizeof(IterArgs) + sizeof(unsigned int)) + 4096;
 }
 
 uint64_t default_capacity(int64_t pixels, int max_depth) {
@@ -515,7 +515,7 @@ mars_status cache_create_impl(const mars_scene* s, const mars_cache_desc* d, cud
     return set_error(MARS_ERR_INVALID_ARG, "max_depth %d out of [1, %d]", d->max_depth, MAXD);
   if ((d->techniques & MARS_TECH_NEE) && s->n_lights == 0)
     return set_error(MARS_ERR_INVALID_ARG, "NEE requested but the scene has no emitting quad");
-  if (d->flags & ~(MARS_CACHE_FP32_STATISTICS | MARS_CACHE_OCTREE))
+  if (d->flags & ~(MARS_CACHE_FP32_STATISTICS | MARS_CACHE_OCTREE | MARS_CACHE_NO_GRAPHS))
     return set_error(MARS_ERR_INVALID_ARG, "unknown cache flags %d", d->flags);
   const bool fp32 = (d->flags & MARS_CACHE_FP32_STATISTICS) != 0;
   const bool octree = (d->flags & MARS_CACHE_OCTREE) != 0;
@@ -595,6 +595,11 @@ mars_status cache_create_impl(const mars_scene* s, const mars_cache_desc* d, cud
   if (!c->h_ctr) return cleanup(cudaErrorMemoryAllocation, "pinned alloc");
   c->h_tile_status = (unsigned int*)pinned_acquire(sizeof(unsigned int) * c->max_tiles);
   if (!c->h_tile_status) return cleanup(cudaErrorMemoryAllocation, "pinned alloc");
+  if ((e = dev_alloc((void**)&c->d_args, sizeof(IterArgs) * c->max_tiles, st)) != cudaSuccess)
+    return cleanup(e, "argument alloc");
+  c->h_args = (IterArgs*)pinned_acquire(sizeof(IterArgs) * c->max_tiles);
+  if (!c->h_args) return cleanup(cudaErrorMemoryAllocation, "pinned alloc");
+  c->use_graphs = (d->flags & MARS_CACHE_NO_GRAPHS) == 0;
   cudaMemsetAsync(c->d_cnt, 0, sizeof(float4) * 2 * NT * cells, st);
   if (c->d_stats) cudaMemsetAsync(c->d_stats, 0, sizeof(double) * NSTAT * NT * cells, st);
   if (c->d_stats32) cudaMemsetAsync(c->d_stats32, 0, sizeof(float) * NSTAT * NT * cells, st);
@@ -764,6 +769,9 @@ void cache_destroy_impl(mars_cache* c) {
   for (void* p : ptrs) dev_free(p, st);
   pinned_release(c->h_ctr, sizeof(DevCounters));
   pinned_release(c->h_tile_status, sizeof(unsigned int) * c->max_tiles);
+  dev_free(c->d_args, st);
+  pinned_release(c->h_args, sizeof(IterArgs) * c->max_tiles);
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   for (cudaEvent_t ev : c->events) cudaEventDestroy(ev);
   for (cudaEvent_t ev : c->sync_events) cudaEventDestroy(ev);
   if (c->side) {
@@ -835,6 +843,7 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
   it.clamp_hi = p->clamp_hi;
   it.outlier = p->outlier;
   it.max_mult = p->max_multiplicity;
+  it.n_prev = c->n_iterations;
 
   // reset the iteration counters (rays, vertices, beta sums, image sums)
   cudaError_t e = cudaMemsetAsync(c->d_ctr, 0, sizeof(DevCounters), st);
@@ -864,34 +873,90 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
         c->events.push_back(ev);
       }
     }
+    // the tiles' arguments: one pinned and one device slot per tile, copied
+    // ahead of the launches that read them (the previous attempt has finished)
     for (size_t t = 0; t < tiles.size(); ++t) {
-      it.tile_begin = (int)tiles[t].first;
-      it.tile_end = (int)tiles[t].second;
-      it.tile_slot = (int)t;
-      cudaEvent_t* ev = p->profile ? c->events.data() + t * per_tile : nullptr;
-      const WaveLaunch L = wave_grids(c, it.tile_end - it.tile_begin);
-      if ((e = launch_tile(s->ds, c->dc, c->arena, it, L, st, c->side, c->sync_events.data(), ev)) != cudaSuccess)
-        return poison(c, e, "render launch");
-      launches += (uint32_t)tile_launches(D, c->techniques);
-      wave_launches += (uint32_t)D;
+      IterArgs& a = c->h_args[t];
+      a = it;
+      a.tile_begin = (int)tiles[t].first;
+      a.tile_end = (int)tiles[t].second;
+      a.tile_slot = (int)t;
     }
+    if ((e = cudaMemcpyAsync(c->d_args, c->h_args, sizeof(IterArgs) * tiles.size(), cudaMemcpyHostToDevice, st)) !=
+        cudaSuccess)
+      return poison(c, e, "argument copy");
+    std::vector<WaveLaunch> Ls;
+    for (size_t t = 0; t < tiles.size(); ++t) Ls.push_back(wave_grids(c, tiles[t].second - tiles[t].first));
+    const bool profile = p->profile != 0;
+    // every launch of the attempt, in stream order on q
+    auto enqueue = [&](cudaStream_t q) -> cudaError_t {
+      cudaError_t r;
+      for (size_t t = 0; t < tiles.size(); ++t) {
+        cudaEvent_t* ev = profile ? c->events.data() + t * per_tile : nullptr;
+        if ((r = launch_tile(s->ds, c->dc, c->arena, c->d_args + t, Ls[t], q, c->side, c->sync_events.data(), ev)) !=
+            cudaSuccess)
+          return r;
+      }
+      cudaEvent_t* iev = profile ? c->events.data() + tiles.size() * per_tile : nullptr;
+      if (iev) cudaEventRecord(iev[0], q);
+      if (p->update_estimate) {
+        if ((r = launch_image_stats(c->dc, s->width, s->height, c->d_args, dev_out, q)) != cudaSuccess) return r;
+      } else if (dev_out) {
+        if ((r = launch_image_copy(c->dc, (int)npx, dev_out, q)) != cudaSuccess) return r;
+      }
+      if (iev) cudaEventRecord(iev[1], q);
+      if ((r = cudaMemcpyAsync(c->h_tile_status, c->d_tile_status, sizeof(unsigned int) * tiles.size(),
+                               cudaMemcpyDeviceToHost, q)) != cudaSuccess)
+        return r;
+      return cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, q);
+    };
+    // A single-tile first attempt is replayed from a recorded CUDA graph.  The
+    // legacy default stream cannot be captured, and a profiled iteration times
+    // every launch with stream events: both launch directly, as do the
+    // re-rendered tiles after an arena overflow.
+    const bool capturable = st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread;
+    if (c->use_graphs && capturable && !profile && retries == 0 && tiles.size() == 1) {
+      GraphKey key;
+      key.update_estimate = p->update_estimate != 0;
+      key.dev_out = dev_out;
+      key.L = Ls[0];
+      if (!c->graph_exec || !c->graph_key.covers(key)) {
+        // recorded with twice the grids asked for (at most the persistent
+        // grid), so that the graph outlives the waves' drift for a while
+        for (int k = 0; k < WAVE_KERNELS; ++k)
+          for (int d = 0; d < MAXD + 2; ++d)
+            key.L.wave_grid[k][d] = std::min(2 * key.L.wave_grid[k][d], key.L.grid[k]);
+        Ls[0] = key.L;
+        if (c->graph_exec) {
+          cudaGraphExecDestroy(c->graph_exec);
+          c->graph_exec = nullptr;
+        }
+        cudaGraph_t graph = nullptr;
+        if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+          return poison(c, e, "graph capture");
+        const cudaError_t ee = enqueue(st);
+        e = cudaStreamEndCapture(st, &graph);
+        if (ee != cudaSuccess || e != cudaSuccess) {
+          if (graph) cudaGraphDestroy(graph);
+          return poison(c, ee != cudaSuccess ? ee : e, "graph capture");
+        }
+        e = cudaGraphInstantiate(&c->graph_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+          c->graph_exec = nullptr;
+          return poison(c, e, "graph instantiate");
+        }
+        c->graph_key = key;
+        c->graph_captures += 1;
+      }
+      if ((e = cudaGraphLaunch(c->graph_exec, st)) != cudaSuccess) return poison(c, e, "graph launch");
+    } else if ((e = enqueue(st)) != cudaSuccess) {
+      return poison(c, e, "render launch");
+    }
+    launches += (uint32_t)(tiles.size() * tile_launches(D, c->techniques));
+    wave_launches += (uint32_t)(tiles.size() * D);
+    launches += p->update_estimate ? 3 : (dev_out ? 1 : 0);
     used += (uint32_t)tiles.size();
-    cudaEvent_t* iev = p->profile ? c->events.data() + tiles.size() * per_tile : nullptr;
-    if (iev) cudaEventRecord(iev[0], st);
-    if (p->update_estimate) {
-      if ((e = launch_image_stats(c->dc, s->width, s->height, c->n_iterations, p->outlier, dev_out, st)) !=
-          cudaSuccess)
-        return poison(c, e, "image stats launch");
-      launches += 3;
-    } else if (dev_out) {
-      if ((e = launch_image_copy(c->dc, (int)npx, dev_out, st)) != cudaSuccess) return poison(c, e, "image copy");
-      launches += 1;
-    }
-    if (iev) cudaEventRecord(iev[1], st);
-    if ((e = cudaMemcpyAsync(c->h_tile_status, c->d_tile_status, sizeof(unsigned int) * tiles.size(),
-                             cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
-      return poison(c, e, "status copy");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return poison(c, e, "render");
     if (p->profile) {
       for (size_t t = 0; t < tiles.size(); ++t) {
@@ -919,6 +984,7 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
         }
       }
       float ms = 0.f;
+      cudaEvent_t* iev = c->events.data() + tiles.size() * per_tile;
       cudaEventElapsedTime(&ms, iev[0], iev[1]);
       image_ms += ms;
     }
@@ -1243,7 +1309,7 @@ mars_status mars_cache_info_get(const mars_cache* c, mars_cache_info* info) {
   info->n_lights = c->scene->n_lights;
   info->oct_cap_nodes = c->oct_cap_nodes;
   info->oct_n_nodes = info->oct_n_leaves = 0;
-  info->reserved = 0;
+  info->graph_captures = c->graph_captures;
   if (c->dc.oct_nodes) {
     DeviceGuard g(c->device);
     int meta[3] = {0, 0, 0};

@@ -42,6 +42,32 @@ struct SceneDescCopy {
 
 mars_status set_error(mars_status s, const char* fmt, ...);
 
+// What a recorded iteration graph depends on besides the per-tile arguments,
+// which the kernels read from device memory.  The graph is replayed while the
+// flags, the output buffer and the launch shape are unchanged and every
+// per-wave grid it holds is at least the one the next iteration asks for and
+// at most eight times it: every wave kernel strides over its wave, so any grid
+// gives the same results and these bounds only keep it fast.  (The wave sizes
+// drift from one iteration to the next; an exact match would record a new
+// graph almost every time.)
+struct GraphKey {
+  bool update_estimate = false;
+  float* dev_out = nullptr;
+  WaveLaunch L{};
+  bool covers(const GraphKey& want) const {
+    if (update_estimate != want.update_estimate || dev_out != want.dev_out) return false;
+    for (int k = 0; k < WAVE_KERNELS; ++k) {
+      if (L.threads[k] != want.L.threads[k] || L.variant[k] != want.L.variant[k] || L.grid[k] != want.L.grid[k])
+        return false;
+      for (int d = 0; d < MAXD + 2; ++d) {
+        const int have = L.wave_grid[k][d], need = want.L.wave_grid[k][d];
+        if (have < need || have > 8 * need) return false;
+      }
+    }
+    return true;
+  }
+};
+
 // Device memory of scenes and caches comes from the device's stream-ordered
 // memory pool (cudaMallocAsync / cudaFreeAsync), which keeps released memory
 // for reuse: creating and destroying objects while other streams render
@@ -118,6 +144,15 @@ struct mars_cache {
   uint64_t last_count[mars::MAXD + 2] = {};
   uint64_t last_slcount[mars::MAXD + 2] = {};
   int64_t last_pixels = 0;
+  // per-tile iteration arguments: written to the pinned slots, copied to the
+  // device slots before the launches, read there by every kernel
+  mars::IterArgs* h_args = nullptr;
+  mars::IterArgs* d_args = nullptr;
+  // the recorded single-tile iteration graph (MARS_CACHE_NO_GRAPHS: none)
+  bool use_graphs = true;
+  cudaGraphExec_t graph_exec = nullptr;
+  mars::GraphKey graph_key{};
+  int graph_captures = 0;
 };
 
 namespace mars {

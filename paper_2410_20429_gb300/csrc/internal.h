@@ -155,12 +155,16 @@ struct DevCache {
 };
 constexpr int OCT_LMAX = MARS_OCTREE_MAX_LEVEL;
 
+// Arguments of one tile of one iteration.  They live in device memory (one
+// slot per tile) and every kernel reads them from there, so that a recorded
+// iteration graph is replayed with the next iteration's values.
 struct IterArgs {
   uint32_t seed, job, iteration;
   int mode, aware, collect, has_estimate;
   float clamp_lo, clamp_hi, outlier;
   float max_mult;  // path multiplicity cap (0: none)
   int tile_begin, tile_end, tile_slot;
+  int n_prev;      // iterations already summed into the running image
 };
 
 // Launch shape of the four per-wave kernels: threads per block (a multiple of
@@ -175,7 +179,8 @@ struct WaveLaunch {
 };
 
 // launch wrappers (render.cu)
-cudaError_t launch_tile(const DevScene& s, const DevCache& c, const Arena& a, const IterArgs& it,
+// it: device pointer to the tile's arguments
+cudaError_t launch_tile(const DevScene& s, const DevCache& c, const Arena& a, const IterArgs* it,
                         const WaveLaunch& L, cudaStream_t st, cudaStream_t side, const cudaEvent_t* sync,
                         cudaEvent_t* ev);
 // resident blocks per SM of each wave kernel at the given block sizes and variants
@@ -186,7 +191,8 @@ int wave_variant_registers(int kernel, int v);    // its register cap (0: the co
 bool wave_threads_ok(int threads);
 int tile_launches(int max_depth, int techniques);  // kernels launch_tile issues
 // image statistics (stats.cu)
-cudaError_t launch_image_stats(const DevCache& c, int width, int height, int n_prev, float outlier,
+// it: device pointer to the iteration's arguments (n_prev, outlier)
+cudaError_t launch_image_stats(const DevCache& c, int width, int height, const IterArgs* it,
                                float* image_out_dev, cudaStream_t st);
 cudaError_t launch_image_copy(const DevCache& c, int npix, float* out, cudaStream_t st);
 cudaError_t launch_update(const DevCache& c, int num_sms, cudaStream_t st);

@@ -133,7 +133,8 @@ __device__ __forceinline__ void flush_work(TraceWork w, unsigned long long* dst)
   }
 }
 
-__global__ void k_tile_init(DevCounters* ctr, unsigned long long n0) {
+__global__ void k_tile_init(DevCounters* ctr, const IterArgs* __restrict__ itp) {
+  const unsigned long long n0 = (unsigned long long)(itp->tile_end - itp->tile_begin);
   const int t = threadIdx.x;
   if (t < MAXD + 2) {
     ctr->base[t] = 0;
@@ -148,8 +149,9 @@ __global__ void k_tile_init(DevCounters* ctr, unsigned long long n0) {
   }
 }
 
-__global__ void k_tile_finish(DevCounters* ctr, unsigned int* tile_status, int slot, int D) {
+__global__ void k_tile_finish(DevCounters* ctr, unsigned int* tile_status, const IterArgs* __restrict__ itp, int D) {
   if (threadIdx.x != 0) return;
+  const int slot = itp->tile_slot;
   unsigned long long dem = 0;
   for (int d = 1; d <= D; ++d) {
     const unsigned long long e = ctr->base[d] + ctr->count[d];
@@ -175,7 +177,8 @@ __global__ void k_tile_finish(DevCounters* ctr, unsigned int* tile_status, int s
 // ------------------------------------------------------------------ trace
 template <int MINB>
 __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_trace(const DevScene s, const DevCache c, const Arena a,
-                                                         const IterArgs it, const int d) {
+                                                         const IterArgs* __restrict__ itp, const int d) {
+  const IterArgs it = *itp;
   const DevCounters* ctr = c.ctr;
   // after an overflow some slots of this wave were never written: stop, the
   // tile is re-rendered in smaller pieces
@@ -225,7 +228,8 @@ struct ShadeWarpCtx {
 
 template <int MINB>
 __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_shade(const DevScene s, const DevCache c, const Arena a,
-                                                         const IterArgs it, const int d) {
+                                                         const IterArgs* __restrict__ itp, const int d) {
+  const IterArgs it = *itp;
   DevCounters* ctr = c.ctr;
   // block-level allocation below synchronises the block: decide the early exit
   // once per block (other blocks may raise the overflow flag meanwhile)
@@ -656,7 +660,8 @@ __device__ __forceinline__ float seg_scan(float v, int lane, int start) {
 
 template <int MINB>
 __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_reverse(const DevScene s, const DevCache c, const Arena a,
-                                                             const IterArgs it, const int d) {
+                                                             const IterArgs* __restrict__ itp, const int d) {
+  const IterArgs it = *itp;
   DevCounters* ctr = c.ctr;
   if (ctr->overflow) return;  // the tile is re-rendered; commit nothing
   const Wave w = wave_of(ctr, a, d);
@@ -867,7 +872,7 @@ size_t shade_smem(int threads) { return (size_t)(threads / 32) * sizeof(ShadeWar
 // __launch_bounds__(256, MINB) for MINB = 1 (the compiler's choice), or a cap
 // that lets more blocks share an SM (shade and reverse: 80 and 64 registers;
 // trace and shadow: 64 and 40 registers), trading spills for occupancy.
-using TraceFn = void (*)(const DevScene, const DevCache, const Arena, const IterArgs, const int);
+using TraceFn = void (*)(const DevScene, const DevCache, const Arena, const IterArgs*, const int);
 using ShadowFn = void (*)(const DevScene, const DevCache, const Arena, const int);
 TraceFn trace_fn(int v) { return v == 2 ? k_trace<6> : (v == 1 ? k_trace<4> : k_trace<1>); }
 TraceFn shade_fn(int v) { return v == 2 ? k_shade<4> : (v == 1 ? k_shade<3> : k_shade<1>); }
@@ -902,10 +907,9 @@ cudaError_t wave_occupancy(const int threads[WAVE_KERNELS], const int variant[WA
 
 bool wave_threads_ok(int threads) { return threads >= 32 && threads <= MAX_WAVE_THREADS && threads % 32 == 0; }
 
-cudaError_t launch_tile(const DevScene& s, const DevCache& c, const Arena& a, const IterArgs& it, const WaveLaunch& L,
+cudaError_t launch_tile(const DevScene& s, const DevCache& c, const Arena& a, const IterArgs* it, const WaveLaunch& L,
                         cudaStream_t st, cudaStream_t side, const cudaEvent_t* sync, cudaEvent_t* ev) {
-  const unsigned long long n0 = (unsigned long long)(it.tile_end - it.tile_begin);
-  k_tile_init<<<1, 32, 0, st>>>(c.ctr, n0);
+  k_tile_init<<<1, 32, 0, st>>>(c.ctr, it);
   const int D = c.max_depth;
   const int tT = L.threads[WK_TRACE], tS = L.threads[WK_SHADE], tH = L.threads[WK_SHADOW], tR = L.threads[WK_REVERSE];
   auto G = [&](int k, int d) { return L.wave_grid[k][d] > 0 ? L.wave_grid[k][d] : L.grid[k]; };
@@ -944,7 +948,7 @@ cudaError_t launch_tile(const DevScene& s, const DevCache& c, const Arena& a, co
     reverse_fn(L.variant[WK_REVERSE])<<<G(WK_REVERSE, d), tR, 0, st>>>(s, c, a, it, d);
     if (ev) cudaEventRecord(ev[4 * D + (D - d + 1)], st);
   }
-  k_tile_finish<<<1, 32, 0, st>>>(c.ctr, c.tile_status, it.tile_slot, D);
+  k_tile_finish<<<1, 32, 0, st>>>(c.ctr, c.tile_status, it, D);
   return cudaGetLastError();
 }
 

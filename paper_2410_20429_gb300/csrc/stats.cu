@@ -44,9 +44,11 @@ template <>
 __device__ __forceinline__ void add_sum<float>(double*, float* d32, float v) { atomicAdd(d32, v); }
 
 template <typename T>
-__global__ void __launch_bounds__(IMG_THREADS) k_img_accum(DevCache c, int npix, int n_prev, float* out) {
+__global__ void __launch_bounds__(IMG_THREADS) k_img_accum(DevCache c, int npix, const IterArgs* __restrict__ itp,
+                                                            float* out) {
   __shared__ T sh[IMG_THREADS / 32];
   if (c.ctr->any_overflow) return;
+  const int n_prev = itp->n_prev;
   const float inv = 1.0f / (float)(n_prev + 1);
   T m0 = 0, m1 = 0, m2 = 0;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) {
@@ -74,9 +76,11 @@ __global__ void __launch_bounds__(IMG_THREADS) k_img_accum(DevCache c, int npix,
 }
 
 template <typename T>
-__global__ void __launch_bounds__(IMG_THREADS) k_img_est(DevCache c, int W, int H, int n_prev, float outlier) {
+__global__ void __launch_bounds__(IMG_THREADS) k_img_est(DevCache c, int W, int H, const IterArgs* __restrict__ itp) {
   __shared__ T sh[IMG_THREADS / 32];
   if (c.ctr->any_overflow) return;
+  const int n_prev = itp->n_prev;
+  const float outlier = itp->outlier;
   const int npix = W * H;
   const float inv = 1.0f / (float)(n_prev + 1);
   const bool f32 = c.stats32 != nullptr;
@@ -363,17 +367,17 @@ cudaError_t launch_octree_refine(const DevCache& c, int num_sms, cudaStream_t st
   return cudaGetLastError();
 }
 
-cudaError_t launch_image_stats(const DevCache& c, int width, int height, int n_prev, float outlier,
+cudaError_t launch_image_stats(const DevCache& c, int width, int height, const IterArgs* it,
                                float* image_out_dev, cudaStream_t st) {
   const int npix = width * height;
   int blocks = (npix + IMG_THREADS - 1) / IMG_THREADS;
   if (blocks > 4096) blocks = 4096;
   if (c.stats32) {
-    k_img_accum<float><<<blocks, IMG_THREADS, 0, st>>>(c, npix, n_prev, image_out_dev);
-    k_img_est<float><<<blocks, IMG_THREADS, 0, st>>>(c, width, height, n_prev, outlier);
+    k_img_accum<float><<<blocks, IMG_THREADS, 0, st>>>(c, npix, it, image_out_dev);
+    k_img_est<float><<<blocks, IMG_THREADS, 0, st>>>(c, width, height, it);
   } else {
-    k_img_accum<double><<<blocks, IMG_THREADS, 0, st>>>(c, npix, n_prev, image_out_dev);
-    k_img_est<double><<<blocks, IMG_THREADS, 0, st>>>(c, width, height, n_prev, outlier);
+    k_img_accum<double><<<blocks, IMG_THREADS, 0, st>>>(c, npix, it, image_out_dev);
+    k_img_est<double><<<blocks, IMG_THREADS, 0, st>>>(c, width, height, it);
   }
   k_img_final<<<1, 32, 0, st>>>(c, npix);
   return cudaGetLastError();

@@ -79,10 +79,11 @@ class Cache:
 
     def __init__(self, scene: Scene, grid_n: int, techniques: int, max_depth: int, arena_capacity: int = 0,
                  fp32_statistics: bool = False, octree: bool = False, max_leaves: int = 0,
-                 split_samples: float = 0.0, stream=None):
+                 split_samples: float = 0.0, graphs: bool = True, stream=None):
         self._lib = A.load()
         self.scene = scene
-        flags = (A.MARS_CACHE_FP32_STATISTICS if fp32_statistics else 0) | (A.MARS_CACHE_OCTREE if octree else 0)
+        flags = ((A.MARS_CACHE_FP32_STATISTICS if fp32_statistics else 0) | (A.MARS_CACHE_OCTREE if octree else 0)
+                 | (0 if graphs else A.MARS_CACHE_NO_GRAPHS))
         d = A.mars_cache_desc(int(grid_n), int(techniques), int(max_depth), flags, int(arena_capacity),
                               int(max_leaves), float(split_samples))
         h = ct.c_void_p()
@@ -252,11 +253,12 @@ class Server:
         self._descs = {}
 
     def submit(self, desc, *, grid_n, techniques, max_depth, iterations, warmup, seed=0, key=0,
-               arena_capacity=0) -> int:
+               arena_capacity=0, graphs=True) -> int:
         d, keep = scene_desc(desc)
         j = A.mars_job_desc()
         j.scene = ct.pointer(d)
-        j.cache = A.mars_cache_desc(int(grid_n), int(techniques), int(max_depth), 0, int(arena_capacity), 0, 0.0)
+        j.cache = A.mars_cache_desc(int(grid_n), int(techniques), int(max_depth),
+                                    0 if graphs else A.MARS_CACHE_NO_GRAPHS, int(arena_capacity), 0, 0.0)
         j.seed, j.iterations, j.warmup, j.key = int(seed), int(iterations), int(warmup), int(key)
         jid = ct.c_uint64()
         A.check(self._lib.mars_submit(self.handle, ct.byref(j), ct.byref(jid)), "mars_submit")

@@ -426,3 +426,77 @@ def test_relmse_against_a_long_reference_matches_the_oracle(mars, orc):
 
     rg, ro = rel_mse(g_acc / N), rel_mse(o_acc / N)
     assert ro > 0 and abs(rg - ro) <= 0.02 * ro, (rg, ro)
+
+
+def test_graph_replay_equals_direct_launches(mars):
+    """On a capturable stream an iteration that fits one pixel tile is recorded
+    once as a CUDA graph and replayed; its per-iteration arguments (seed,
+    iteration, mode, running-image count, ...) are read from device memory, so
+    a replay renders the next iteration, not the recorded one.  From the same
+    state, replayed and directly launched iterations give bitwise equal images
+    and counters and statistics equal up to the order of the float64 atomics,
+    across modes, seeds, a launch-shape change, a new output buffer, the
+    update_estimate flag and a profiled iteration; a graph is recorded again
+    only when one of those changes."""
+    import torch
+    cfg = W.config_guided(48, 40)
+    stream = torch.cuda.Stream()   # torch's streams can be captured; the legacy default stream cannot
+    scene = mars.Scene(cfg.scene, stream=stream)
+    caches = [mars.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, graphs=g, stream=stream)
+              for g in (True, False)]
+    bufs = [torch.zeros(caches[0].n_pixels * 3, dtype=torch.float32, device="cuda") for _ in range(2)]
+    q_rr, q_s, valid = W.random_count_fields(cfg.n_cells, seed=701, lo=0.3, hi=4.0)
+    est = W.random_pixel_estimate(cfg.scene.n_pixels, seed=702, lo=0.05, hi=0.5)
+    run = W.random_pixel_estimate(cfg.scene.n_pixels, seed=703, lo=0.05, hi=0.5)
+    for it in range(8):
+        res = []
+        for c in caches:
+            if it == 3:
+                c.set_launch([64, 128, 64, 128], [0, 0, 0, 0], [0, 64, 0, 80])
+            c.set_state(q_rr=q_rr, q_s=q_s, valid=valid, pixel_estimate=est, run_sum=run * (it + 1),
+                        has_estimate=True, n_iterations=it + 1, stats=np.zeros((cfg.n_cells, 3, 8)),
+                        stream=stream)
+            img = bufs[1 if it >= 5 else 0]
+            st = c.render_iteration(img, seed=31 + it, iteration=it, mode=0 if it < 2 else 1,
+                                    update_estimate=(it % 3 != 2), profile=(it == 6), stream=stream)
+            g = c.get_state(stream=stream)
+            torch.cuda.synchronize()
+            res.append((img.cpu().numpy().copy(), st, g))
+        (a, sa, ga), (b, sb, gb) = res
+        assert np.array_equal(a, b), f"iteration {it}: images differ"
+        assert sa["rays"] == sb["rays"] and sa["vertices"] == sb["vertices"], it
+        np.testing.assert_allclose(ga["stats"], gb["stats"], rtol=1e-6, atol=1e-9)
+        np.testing.assert_allclose(ga["run_sum"], gb["run_sum"], rtol=1e-6, atol=1e-9)
+        np.testing.assert_allclose(ga["pixel_estimate"], gb["pixel_estimate"], rtol=1e-6, atol=1e-9)
+        assert sa["VI"] == pytest.approx(sb["VI"], rel=1e-6) and sa["CI"] == pytest.approx(sb["CI"], rel=1e-9)
+    caps = caches[0].info()["graph_captures"]
+    # recorded at least for the first iteration, the new launch shape, the new
+    # buffer and the update_estimate changes; never for the profiled iteration
+    assert 3 <= caps <= 7, caps
+    assert caches[1].info()["graph_captures"] == 0
+
+
+def test_graph_replay_with_arena_overflow(mars):
+    """A recorded single-tile iteration whose path trees overflow the arena is
+    re-rendered in tiles by direct launches; the image equals that of a cache
+    whose arena holds the whole iteration."""
+    import torch
+    cfg = W.config_box(32, 32)
+    stream = torch.cuda.Stream()
+    q_rr, q_s, valid = W.random_count_fields(cfg.n_cells, seed=501, lo=0.5, hi=6.0)
+    est = W.random_pixel_estimate(cfg.scene.n_pixels, seed=502, lo=0.05, hi=0.5)
+    res = []
+    for cap in (0, 6000):
+        scene = mars.Scene(cfg.scene, stream=stream)
+        cache = mars.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, arena_capacity=cap, stream=stream)
+        cache.set_state(q_rr=q_rr, q_s=q_s, valid=valid, pixel_estimate=est, has_estimate=True, n_iterations=1,
+                        stream=stream)
+        img = torch.zeros(cache.n_pixels * 3, dtype=torch.float32, device="cuda")
+        st = cache.render_iteration(img, seed=2, iteration=1, mode=1, update_estimate=False, stream=stream)
+        stream.synchronize()
+        res.append((img.cpu().numpy().copy(), st, cache.info()["graph_captures"]))
+    (a, sa, ca), (b, sb, cb) = res
+    assert sa["retries"] == 0 and sb["retries"] > 0 and sb["tiles"] > 1
+    assert ca == 1 and cb == 1
+    assert np.array_equal(a, b)
+    assert sa["rays"] == sb["rays"] and sa["vertices"] == sb["vertices"]
