@@ -106,6 +106,9 @@ KERNEL_SOURCES = ["paper_2410_20429_gb300/csrc/render.cu", "paper_2410_20429_gb3
 TRAFFIC_FILE = "profiles/dram_traffic_guided_room_512.txt"
 
 
+BVH_KINDS = {"sah": 0, "lbvh": 1}   # MARS_BVH_SAH, MARS_BVH_LBVH
+
+
 def kernel_sources_sha():
     """sha256 of the wave kernels' sources: DRAM traffic measured on other
     sources does not describe these kernels."""
@@ -233,6 +236,7 @@ def run_mars(args):
     B.build()
     cfg = workload(args)
     sc = cfg.scene
+    sc.bvh = BVH_KINDS[args.bvh]
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         scene = M.Scene(sc, stream=stream)
@@ -377,7 +381,7 @@ def run_mars(args):
         "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": cfg.name, "pixels": npx, "max_depth": cfg.max_depth, "grid": cfg.grid_n,
-                   "techniques": "bsdf+nee+guided", "statistics_dtype": "f64",
+                   "techniques": "bsdf+nee+guided", "statistics_dtype": "f64", "bvh": args.bvh,
                    "l2": "working set > L2: queue arena %.0f MB per step" % (
                        entries / args.steps * SLOT_BYTES / 1e6),
                    "parallelism": f"replicas x{world}"},
@@ -431,6 +435,7 @@ def large_scene(args, M, stream):
     work per ray and the octree's size at this geometry size."""
     import torch
     cfg = W.config_heightfield(1024, 1024)
+    cfg.scene.bvh = BVH_KINDS[args.bvh]
     t0 = time.perf_counter()
     scene = M.Scene(cfg.scene, stream=stream)
     torch.cuda.synchronize()
@@ -723,6 +728,8 @@ def main():
     ap.add_argument("--eff-spp", type=int, default=32)
     ap.add_argument("--ref-pixels-per-step", type=int, default=1024)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--bvh", default="sah", choices=sorted(BVH_KINDS),
+                    help="hierarchy of the closest-hit and shadow queries (results do not depend on it)")
     ap.add_argument("--no-graphs", action="store_true", help="launch every kernel directly (no CUDA graph replay)")
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the heightfield (131k triangles) section")

@@ -75,7 +75,13 @@ typedef enum { MARS_WEIGHTS_AWARE = 0, MARS_WEIGHTS_UNAWARE = 1 } mars_weights;
  * materials [n_materials][8]: type (0 Lambert, 1 GGX), colour rgb (Lambertian
  *   albedo, or GGX Fresnel F0), GGX roughness alpha, emitted radiance rgb.
  * camera: pinhole origin, look-at point, up vector, vertical FOV in degrees;
- *   width x height pixels, one box-filtered sample per pixel per iteration. */
+ *   width x height pixels, one box-filtered sample per pixel per iteration.
+ * bvh: the hierarchy the closest-hit and shadow queries traverse (results do
+ *   not depend on it): MARS_BVH_SAH (0) a top-down build on the host with the
+ *   surface-area heuristic; MARS_BVH_LBVH a linear BVH built on the device
+ *   (Morton codes, Karras hierarchy).  reserved: 0. */
+#define MARS_BVH_SAH 0
+#define MARS_BVH_LBVH 1
 typedef struct {
   int32_t n_quads, n_spheres, n_tris, n_materials;
   const double* quads;
@@ -87,6 +93,7 @@ typedef struct {
   const double* materials;
   double camera[10];
   int32_t width, height;
+  int32_t bvh, reserved;
 } mars_scene_desc;
 
 /* Statistics cache and iteration state of one render job.

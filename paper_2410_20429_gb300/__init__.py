@@ -6,6 +6,9 @@ The compute lives in ``libmars.so`` (hand-written CUDA, C ABI in
 ``include/mars.h``); this package only marshals arguments.  Loading fails
 loudly when the library has not been built."""
 from ._abi import (  # noqa: F401
+    MARS_BVH_LBVH,
+    MARS_BVH_SAH,
+    MARS_CACHE_NO_GRAPHS,
     MARS_ERR_BUSY,
     MARS_ERR_CUDA,
     MARS_ERR_INVALID_ARG,

@@ -18,6 +18,8 @@ MARS_JOB_QUEUED, MARS_JOB_RUNNING, MARS_JOB_DONE, MARS_JOB_FAILED = range(4)
 MARS_CACHE_FP32_STATISTICS = 1
 MARS_CACHE_OCTREE = 2
 MARS_CACHE_NO_GRAPHS = 4
+MARS_BVH_SAH = 0
+MARS_BVH_LBVH = 1
 NUM_SLOTS, NUM_STATS, GUIDE_BINS, MAX_DEPTH = 3, 8, 256, 16
 
 
@@ -35,7 +37,7 @@ class mars_scene_desc(ct.Structure):
         ("tris", ct.POINTER(ct.c_double)), ("tri_mat", ct.POINTER(ct.c_int32)),
         ("materials", ct.POINTER(ct.c_double)),
         ("camera", ct.c_double * 10),
-        ("width", ct.c_int32), ("height", ct.c_int32),
+        ("width", ct.c_int32), ("height", ct.c_int32), ("bvh", ct.c_int32), ("reserved", ct.c_int32),
     ]
 
 

@@ -121,6 +121,8 @@ mars_status scene_create_impl(const mars_scene_desc* d, cudaStream_t st, mars_sc
   if (n <= 0) return set_error(MARS_ERR_INVALID_ARG, "scene has no primitives");
   if (d->width <= 0 || d->height <= 0 || (int64_t)d->width * d->height > (1ll << 31))
     return set_error(MARS_ERR_INVALID_ARG, "bad resolution %d x %d", d->width, d->height);
+  if (d->bvh != MARS_BVH_SAH && d->bvh != MARS_BVH_LBVH)
+    return set_error(MARS_ERR_INVALID_ARG, "unknown bvh kind %d", d->bvh);
   if ((d->n_quads && (!d->quads || !d->quad_mat)) || (d->n_spheres && (!d->spheres || !d->sphere_mat)) ||
       (d->n_tris && (!d->tris || !d->tri_mat)) || !d->materials)
     return set_error(MARS_ERR_INVALID_ARG, "null primitive array");
@@ -337,9 +339,21 @@ mars_status scene_create_impl(const mars_scene_desc* d, cudaStream_t st, mars_sc
       (e = cudaMemcpyAsync(s->d_mats, mats.data(), sizeof(float4) * mats.size(), cudaMemcpyHostToDevice, st)) ||
       (e = cudaMemcpyAsync(s->d_lights, lights.data(), sizeof(float4) * lights.size(), cudaMemcpyHostToDevice, st)))
     return cleanup(e, "scene upload");
-  std::string berr;
-  if ((e = build_bvh(s->d_boxes, n, s->ds.lo, s->ds.ext, s->d_nodes, st, &berr)) != cudaSuccess)
-    return cleanup(e, berr.c_str());
+  if (d->bvh == MARS_BVH_SAH && n >= 2) {
+    std::vector<BvhNode> sah;
+    if (!build_bvh_sah(boxes, n, sah)) {
+      set_error(MARS_ERR_CUDA, "SAH build produced an invalid hierarchy");
+      scene_destroy_impl(s);
+      return MARS_ERR_CUDA;
+    }
+    if ((e = cudaMemcpyAsync(s->d_nodes, sah.data(), sizeof(BvhNode) * (n - 1), cudaMemcpyHostToDevice, st)) !=
+        cudaSuccess)
+      return cleanup(e, "BVH upload");
+  } else {
+    std::string berr;
+    if ((e = build_bvh(s->d_boxes, n, s->ds.lo, s->ds.ext, s->d_nodes, st, &berr)) != cudaSuccess)
+      return cleanup(e, berr.c_str());
+  }
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cleanup(e, "scene create");
   if (n >= 2) {
     // check the hierarchy before any kernel traverses it: every internal node

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "mars.h"
 
@@ -201,6 +202,9 @@ cudaError_t launch_update(const DevCache& c, int num_sms, cudaStream_t st);
 cudaError_t launch_leaf_samples(const DevCache& c, cudaStream_t st);
 cudaError_t launch_octree_refine(const DevCache& c, int num_sms, cudaStream_t st);
 // scene build (scene.cu)
+// SAH build on the host from the primitive boxes (2 float4 per primitive):
+// n - 1 internal nodes, root 0; false if n < 2 (scene.cu)
+bool build_bvh_sah(const std::vector<float4>& boxes, int n, std::vector<BvhNode>& nodes);
 cudaError_t build_bvh(const float4* d_prims, int n, const float lo[3], const float ext[3], BvhNode* d_nodes,
                       cudaStream_t st, std::string* err);
 

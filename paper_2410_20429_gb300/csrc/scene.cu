@@ -4,7 +4,11 @@
 // the primitive index as a tie-breaking low word, a bitonic sort, one thread per internal node to find
 // its key range and split, and a bottom-up pass that fills the child bounds
 // (the second thread to reach a node computes it).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
 #include <string>
+#include <vector>
 
 #include "internal.h"
 
@@ -184,6 +188,183 @@ cudaError_t build_bvh(const float4* d_box, int n, const float lo[3], const float
   if (ibox) cudaFreeAsync(ibox, st);
   cudaStreamSynchronize(st);
   return e;
+}
+
+// ------------------------------------------------------------ SAH build
+// Top-down surface-area-heuristic build on the host (MacDonald and Booth's cost
+// model: a split of a node's primitives into L and R costs A(L) |L| + A(R) |R|,
+// A the surface area of the side's bounding box).  Ranges of at most 64
+// primitives try every split position in the centroid order along each axis;
+// larger ones 32 equal-width centroid bins per axis (Wald, "On fast
+// construction of SAH-based bounding volume hierarchies", 2007).  One
+// primitive per leaf, so the tree has n - 1 internal nodes, like the LBVH, in
+// the same node format; siblings get adjacent node numbers.  A range that
+// could otherwise end deeper than kMaxDepth levels is split at its centroid
+// median along the widest axis from there on, so no leaf lies deeper than
+// kMaxDepth and the traversal stacks (48 entries) never overflow.
+namespace {
+struct HBox {
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  void grow(const HBox& b) {
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = std::min(lo[a], b.lo[a]);
+      hi[a] = std::max(hi[a], b.hi[a]);
+    }
+  }
+  double area() const {
+    if (!(hi[0] >= lo[0])) return 0.0;
+    const double dx = hi[0] - lo[0], dy = hi[1] - lo[1], dz = hi[2] - lo[2];
+    return dx * dy + dy * dz + dz * dx;
+  }
+};
+}  // namespace
+
+bool build_bvh_sah(const std::vector<float4>& boxes, int n, std::vector<BvhNode>& nodes) {
+  if (n < 2) return false;
+  std::vector<HBox> pb(n);
+  std::vector<float> cen(3 * (size_t)n);
+  for (int i = 0; i < n; ++i) {
+    const float4 l = boxes[2 * i], h = boxes[2 * i + 1];
+    pb[i].lo[0] = l.x; pb[i].lo[1] = l.y; pb[i].lo[2] = l.z;
+    pb[i].hi[0] = h.x; pb[i].hi[1] = h.y; pb[i].hi[2] = h.z;
+    for (int a = 0; a < 3; ++a) cen[3 * (size_t)i + a] = 0.5f * (pb[i].lo[a] + pb[i].hi[a]);
+  }
+  std::vector<int> idx(n);
+  for (int i = 0; i < n; ++i) idx[i] = i;
+  nodes.assign(n - 1, BvhNode{});
+  struct Task {
+    int begin, end, node, depth;
+  };
+  std::vector<Task> todo{{0, n, 0, 1}};
+  int next = 1;
+  constexpr int BINS = 32, EXACT = 64, kMaxDepth = 44;
+  auto ceil_log2 = [](int v) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+  };
+  std::vector<double> left_area(std::max(EXACT, BINS));
+  while (!todo.empty()) {
+    const Task t = todo.back();
+    todo.pop_back();
+    const int cnt = t.end - t.begin;
+    int* r = idx.data() + t.begin;
+    int mid = -1;
+    if (t.depth + ceil_log2(cnt) >= kMaxDepth) {
+      float clo[3] = {INFINITY, INFINITY, INFINITY}, chi[3] = {-INFINITY, -INFINITY, -INFINITY};
+      for (int k = 0; k < cnt; ++k)
+        for (int a = 0; a < 3; ++a) {
+          clo[a] = std::min(clo[a], cen[3 * (size_t)r[k] + a]);
+          chi[a] = std::max(chi[a], cen[3 * (size_t)r[k] + a]);
+        }
+      int a = 0;
+      for (int b = 1; b < 3; ++b)
+        if (chi[b] - clo[b] > chi[a] - clo[a]) a = b;
+      mid = cnt / 2;
+      std::nth_element(r, r + mid, r + cnt, [&](int x, int y) {
+        const float cx = cen[3 * (size_t)x + a], cy = cen[3 * (size_t)y + a];
+        return cx < cy || (cx == cy && x < y);
+      });
+    } else if (cnt <= EXACT) {
+      // every split position of the centroid order along each axis
+      double best = INFINITY;
+      int best_axis = -1, best_k = 0;
+      for (int a = 0; a < 3; ++a) {
+        std::sort(r, r + cnt, [&](int x, int y) {
+          const float cx = cen[3 * (size_t)x + a], cy = cen[3 * (size_t)y + a];
+          return cx < cy || (cx == cy && x < y);
+        });
+        HBox acc;
+        for (int k = 0; k < cnt - 1; ++k) {
+          acc.grow(pb[r[k]]);
+          left_area[k] = acc.area() * (k + 1);
+        }
+        HBox racc;
+        for (int k = cnt - 1; k >= 1; --k) {
+          racc.grow(pb[r[k]]);
+          const double c = left_area[k - 1] + racc.area() * (cnt - k);
+          if (c < best) { best = c; best_axis = a; best_k = k; }
+        }
+      }
+      const int a = best_axis;
+      std::sort(r, r + cnt, [&](int x, int y) {
+        const float cx = cen[3 * (size_t)x + a], cy = cen[3 * (size_t)y + a];
+        return cx < cy || (cx == cy && x < y);
+      });
+      mid = best_k;
+    } else {
+      float clo[3] = {INFINITY, INFINITY, INFINITY}, chi[3] = {-INFINITY, -INFINITY, -INFINITY};
+      for (int k = 0; k < cnt; ++k)
+        for (int a = 0; a < 3; ++a) {
+          clo[a] = std::min(clo[a], cen[3 * (size_t)r[k] + a]);
+          chi[a] = std::max(chi[a], cen[3 * (size_t)r[k] + a]);
+        }
+      double best = INFINITY;
+      int best_axis = -1, best_bin = 0;
+      for (int a = 0; a < 3; ++a) {
+        const float ext = chi[a] - clo[a];
+        if (!(ext > 0.0f)) continue;
+        const float sc = (float)BINS / ext;
+        HBox bb[BINS];
+        int bc[BINS] = {};
+        for (int k = 0; k < cnt; ++k) {
+          const int b = std::min(BINS - 1, (int)((cen[3 * (size_t)r[k] + a] - clo[a]) * sc));
+          bb[b].grow(pb[r[k]]);
+          bc[b] += 1;
+        }
+        HBox acc;
+        int nl = 0;
+        for (int b = 0; b < BINS - 1; ++b) {
+          acc.grow(bb[b]);
+          nl += bc[b];
+          left_area[b] = acc.area() * nl;
+        }
+        HBox racc;
+        int nr = 0;
+        for (int b = BINS - 1; b >= 1; --b) {
+          racc.grow(bb[b]);
+          nr += bc[b];
+          if (nr == 0 || nr == cnt) continue;
+          const double c = left_area[b - 1] + racc.area() * nr;
+          if (c < best) { best = c; best_axis = a; best_bin = b; }
+        }
+      }
+      if (best_axis >= 0) {
+        const int a = best_axis;
+        const float sc = (float)BINS / (chi[a] - clo[a]);
+        int* m = std::partition(r, r + cnt, [&](int x) {
+          return std::min(BINS - 1, (int)((cen[3 * (size_t)x + a] - clo[a]) * sc)) < best_bin;
+        });
+        mid = (int)(m - r);
+      }
+      if (mid <= 0 || mid >= cnt) {
+        // all centroids in one bin: the median of the index order
+        std::sort(r, r + cnt);
+        mid = cnt / 2;
+      }
+    }
+    HBox side[2];
+    int child[2];
+    const int rng[2][2] = {{0, mid}, {mid, cnt}};
+    for (int sdx = 0; sdx < 2; ++sdx) {
+      for (int k = rng[sdx][0]; k < rng[sdx][1]; ++k) side[sdx].grow(pb[r[k]]);
+      if (rng[sdx][1] - rng[sdx][0] == 1) {
+        child[sdx] = ~r[rng[sdx][0]];
+      } else {
+        child[sdx] = next++;
+      }
+    }
+    for (int sdx = 1; sdx >= 0; --sdx)
+      if (child[sdx] >= 0) todo.push_back({t.begin + rng[sdx][0], t.begin + rng[sdx][1], child[sdx], t.depth + 1});
+    BvhNode& nd = nodes[t.node];
+    float cw[2];
+    std::memcpy(cw, child, sizeof(cw));
+    nd.a = make_float4(side[0].lo[0], side[0].lo[1], side[0].lo[2], cw[0]);
+    nd.b = make_float4(side[0].hi[0], side[0].hi[1], side[0].hi[2], cw[1]);
+    nd.c = make_float4(side[1].lo[0], side[1].lo[1], side[1].lo[2], 0.0f);
+    nd.d = make_float4(side[1].hi[0], side[1].hi[1], side[1].hi[2], 0.0f);
+  }
+  return next == n - 1;
 }
 
 }  // namespace mars

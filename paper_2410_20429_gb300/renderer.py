@@ -45,6 +45,7 @@ def scene_desc(desc):
     for i in range(10):
         d.camera[i] = float(desc.camera[i])
     d.width, d.height = int(desc.width), int(desc.height)
+    d.bvh = int(getattr(desc, "bvh", A.MARS_BVH_SAH))
     return d, keep
 
 

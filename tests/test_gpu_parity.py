@@ -500,3 +500,29 @@ def test_graph_replay_with_arena_overflow(mars):
     assert ca == 1 and cb == 1
     assert np.array_equal(a, b)
     assert sa["rays"] == sb["rays"] and sa["vertices"] == sb["vertices"]
+
+
+@pytest.mark.parametrize("which", ["guided", "heightfield"])
+def test_bvh_kind_does_not_change_results(mars, which):
+    """The SAH hierarchy (built on the host) and the linear BVH (built on the
+    device) hold the same primitives; closest hits break ties in t by the lower
+    primitive index, so the image is bitwise equal whichever is traversed and
+    only the traversal work differs."""
+    import dataclasses
+    cfg = W.config_guided(48, 40) if which == "guided" else W.config_heightfield(48, 40)
+    q_rr, q_s, valid = W.random_count_fields(cfg.n_cells, seed=801, lo=0.3, hi=4.0)
+    est = W.random_pixel_estimate(cfg.scene.n_pixels, seed=802, lo=0.05, hi=0.5)
+    res = []
+    for kind in (mars.MARS_BVH_SAH, mars.MARS_BVH_LBVH):
+        sc = dataclasses.replace(cfg.scene)
+        sc.bvh = kind
+        scene = mars.Scene(sc)
+        cache = mars.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth)
+        cache.set_state(q_rr=q_rr, q_s=q_s, valid=valid, pixel_estimate=est, has_estimate=True, n_iterations=1)
+        img, st = _gpu_iteration(mars, cache, iteration=1, seed=9, mode=1)
+        res.append((img, st, cache.get_state()["stats"]))
+    (a, sa, ta), (b, sb, tb) = res
+    assert np.array_equal(a, b)
+    assert sa["rays"] == sb["rays"] and sa["vertices"] == sb["vertices"]
+    np.testing.assert_allclose(ta, tb, rtol=1e-6, atol=1e-9)
+    assert sa["trace_work"][0][0] > 0 and sb["trace_work"][0][0] > 0
