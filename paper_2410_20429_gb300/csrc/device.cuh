@@ -129,17 +129,28 @@ __device__ __forceinline__ bool hit_prim(const float4* __restrict__ prims, int i
   return hit_tri(q, o, d, tmax, t);
 }
 
+// Three-input minimum and maximum: one instruction on sm_100 and later.  Like
+// fminf / fmaxf they return the extreme of the inputs that are not NaN, so a
+// chain of them gives the same value as the two-input chain.
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+
 // slab test of one box against [0, tmax]; returns the entry distance, or NaN
 // on a miss (so that every comparison with it is false)
 __device__ __forceinline__ float box_entry(float4 lo, float4 hi, f3 o, f3 inv, float tmax) {
-  float t0 = (lo.x - o.x) * inv.x, t1 = (hi.x - o.x) * inv.x;
-  float tn = fminf(t0, t1), tf = fmaxf(t0, t1);
-  t0 = (lo.y - o.y) * inv.y; t1 = (hi.y - o.y) * inv.y;
-  tn = fmaxf(tn, fminf(t0, t1)); tf = fminf(tf, fmaxf(t0, t1));
-  t0 = (lo.z - o.z) * inv.z; t1 = (hi.z - o.z) * inv.z;
-  tn = fmaxf(tn, fminf(t0, t1)); tf = fminf(tf, fmaxf(t0, t1));
-  tn = fmaxf(tn, 0.0f);
-  tf = fminf(tf, tmax);
+  const float x0 = (lo.x - o.x) * inv.x, x1 = (hi.x - o.x) * inv.x;
+  const float y0 = (lo.y - o.y) * inv.y, y1 = (hi.y - o.y) * inv.y;
+  const float z0 = (lo.z - o.z) * inv.z, z1 = (hi.z - o.z) * inv.z;
+  const float tn = fmax3(fminf(x0, x1), fminf(y0, y1), fmaxf(fminf(z0, z1), 0.0f));
+  const float tf = fmin3(fmaxf(x0, x1), fmaxf(y0, y1), fminf(fmaxf(z0, z1), tmax));
   return tn <= tf * 1.00000024f ? tn : __int_as_float(0x7fffffff);
 }
 
@@ -208,14 +219,11 @@ __device__ __forceinline__ void box4_entry(const Bvh4Node& nd, f3 o, f3 inv, flo
   const int ch[4] = {nd.child.x, nd.child.y, nd.child.z, nd.child.w};
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    float t0 = (lx[k] - o.x) * inv.x, t1 = (hx[k] - o.x) * inv.x;
-    float tn = fminf(t0, t1), tf = fmaxf(t0, t1);
-    t0 = (ly[k] - o.y) * inv.y; t1 = (hy[k] - o.y) * inv.y;
-    tn = fmaxf(tn, fminf(t0, t1)); tf = fminf(tf, fmaxf(t0, t1));
-    t0 = (lz[k] - o.z) * inv.z; t1 = (hz[k] - o.z) * inv.z;
-    tn = fmaxf(tn, fminf(t0, t1)); tf = fminf(tf, fmaxf(t0, t1));
-    tn = fmaxf(tn, 0.0f);
-    tf = fminf(tf, tmax);
+    const float x0 = (lx[k] - o.x) * inv.x, x1 = (hx[k] - o.x) * inv.x;
+    const float y0 = (ly[k] - o.y) * inv.y, y1 = (hy[k] - o.y) * inv.y;
+    const float z0 = (lz[k] - o.z) * inv.z, z1 = (hz[k] - o.z) * inv.z;
+    const float tn = fmax3(fminf(x0, x1), fminf(y0, y1), fmaxf(fminf(z0, z1), 0.0f));
+    const float tf = fmin3(fmaxf(x0, x1), fmaxf(y0, y1), fminf(fmaxf(z0, z1), tmax));
     t[k] = (ch[k] != BVH4_EMPTY && tn <= tf * 1.00000024f) ? tn : __int_as_float(0x7fffffff);
   }
 }
