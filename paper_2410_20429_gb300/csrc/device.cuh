@@ -179,19 +179,23 @@ __device__ __forceinline__ int trace_closest(const DevScene& s, f3 o, f3 d, floa
     const float tr = box_entry(nd.c, nd.d, o, inv, t_best);
     int cl = __float_as_int(nd.a.w), cr = __float_as_int(nd.b.w);
     bool vl = tl <= t_best, vr = tr <= t_best;
+    // the admitted leaf children (left first) go through one copy of the
+    // primitive test, so that lanes with a leaf on either side share it
+    int p0 = -1, p1 = -1;
     if (vl && cl < 0) {
-      float t;
-      const int p = ~cl;
-      if (hit_prim(s.prims, p, o, d, t_best * 1.0000002f + 1e-30f, t, w) &&
-          (t < t_best || (t == t_best && p < best))) { t_best = t; best = p; }
+      p0 = ~cl;
       vl = false;
     }
     if (vr && cr < 0) {
-      float t;
-      const int p = ~cr;
-      if (hit_prim(s.prims, p, o, d, t_best * 1.0000002f + 1e-30f, t, w) &&
-          (t < t_best || (t == t_best && p < best))) { t_best = t; best = p; }
+      if (p0 < 0) p0 = ~cr; else p1 = ~cr;
       vr = false;
+    }
+    while (p0 >= 0) {
+      float t;
+      if (hit_prim(s.prims, p0, o, d, t_best * 1.0000002f + 1e-30f, t, w) &&
+          (t < t_best || (t == t_best && p0 < best))) { t_best = t; best = p0; }
+      p0 = p1;
+      p1 = -1;
     }
     if (vl && vr) {
       const bool lfirst = tl <= tr;
@@ -243,16 +247,24 @@ __device__ __forceinline__ bool trace_any4(const DevScene& s, f3 o, f3 d, float 
     box4_entry(nd, o, inv, tmax, t);
     const int ch[4] = {nd.child.x, nd.child.y, nd.child.z, nd.child.w};
     int next = -1;
+    unsigned leaves = 0;  // admitted leaf children, tested below in child order
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       if (!(t[k] <= tmax)) continue;
       if (ch[k] < 0) {
-        if (hit_prim(s.prims, ~ch[k], o, d, tmax, th, w)) return true;
+        leaves |= 1u << k;
       } else if (next < 0) {
         next = ch[k];
       } else if (sp < STACK) {
         stack[sp++] = ch[k];
       }
+    }
+    // one copy of the primitive test for all of them (lanes share it)
+    while (leaves) {
+      const int k = __ffs(leaves) - 1;
+      leaves &= leaves - 1;
+      const int c = k == 0 ? ch[0] : (k == 1 ? ch[1] : (k == 2 ? ch[2] : ch[3]));
+      if (hit_prim(s.prims, ~c, o, d, tmax, th, w)) return true;
     }
     if (next >= 0) {
       node = next;
