@@ -784,6 +784,7 @@ void cache_destroy_impl(mars_cache* c) {
   pinned_release(c->h_ctr, sizeof(DevCounters));
   pinned_release(c->h_tile_status, sizeof(unsigned int) * c->max_tiles);
   dev_free(c->d_args, st);
+  dev_free(c->d_host_stage, st);
   pinned_release(c->h_args, sizeof(IterArgs) * c->max_tiles);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   for (cudaEvent_t ev : c->events) cudaEventDestroy(ev);
@@ -877,7 +878,13 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
   float wave_ms[WAVE_KERNELS][MAXD] = {};
   const int D = c->max_depth;
   const int per_tile = 5 * D + 2;
-  float* dev_out = p->image_on_host ? nullptr : image;
+  // a host image is packed on the device by the image pass into a staging
+  // buffer of the cache (allocated on first use) and read back in one copy
+  if (p->image_on_host && !c->d_host_stage &&
+      (e = dev_alloc((void**)&c->d_host_stage, sizeof(float) * 3 * (size_t)npx, st)) != cudaSuccess)
+    return set_error(e == cudaErrorMemoryAllocation ? MARS_ERR_OOM : MARS_ERR_CUDA, "staging alloc: %s",
+                     cudaGetErrorString(e));
+  float* dev_out = p->image_on_host ? c->d_host_stage : image;
   while (true) {
     if (p->profile) {
       const size_t need = tiles.size() * per_tile + 2;
@@ -1036,9 +1043,8 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
     c->has_estimate = true;
   }
   if (p->image_on_host) {
-    // gather the float4 image into the caller's packed rgb buffer
-    if ((e = cudaMemcpy2DAsync(image, 3 * sizeof(float), c->d_img, sizeof(float4), 3 * sizeof(float), (size_t)npx,
-                               cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    if ((e = cudaMemcpyAsync(image, c->d_host_stage, sizeof(float) * 3 * (size_t)npx, cudaMemcpyDeviceToHost, st)) !=
+        cudaSuccess)
       return poison(c, e, "image copy");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return poison(c, e, "image copy");
   }

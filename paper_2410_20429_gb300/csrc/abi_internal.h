@@ -148,6 +148,7 @@ struct mars_cache {
   // device slots before the launches, read there by every kernel
   mars::IterArgs* h_args = nullptr;
   mars::IterArgs* d_args = nullptr;
+  float* d_host_stage = nullptr;  // packed rgb image for image_on_host (first use)
   // the recorded single-tile iteration graph (MARS_CACHE_NO_GRAPHS: none)
   bool use_graphs = true;
   cudaGraphExec_t graph_exec = nullptr;

@@ -526,3 +526,31 @@ def test_bvh_kind_does_not_change_results(mars, which):
     assert sa["rays"] == sb["rays"] and sa["vertices"] == sb["vertices"]
     np.testing.assert_allclose(ta, tb, rtol=1e-6, atol=1e-9)
     assert sa["trace_work"][0][0] > 0 and sb["trace_work"][0][0] > 0
+
+
+@pytest.mark.parametrize("capturable", [False, True])
+def test_host_image_equals_device_image(mars, capturable):
+    """An image requested in host memory is packed on the device and copied
+    back once; it equals the image written to device memory from the same state,
+    with and without the image statistics pass, on the legacy default stream and
+    on a stream whose iterations replay a recorded graph."""
+    import torch
+    cfg = W.config_guided(40, 24)
+    q_rr, q_s, valid = W.random_count_fields(cfg.n_cells, seed=901, lo=0.3, hi=4.0)
+    est = W.random_pixel_estimate(cfg.scene.n_pixels, seed=902, lo=0.05, hi=0.5)
+    stream = torch.cuda.Stream() if capturable else None
+    scene = mars.Scene(cfg.scene, stream=stream)
+    cache = mars.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, stream=stream)
+    dev = torch.zeros(cache.n_pixels * 3, dtype=torch.float32, device="cuda")
+    host = np.zeros(cache.n_pixels * 3, np.float32)
+    for it, upd in ((1, True), (2, False), (3, True)):
+        outs = []
+        for target in (dev, host):
+            cache.set_state(q_rr=q_rr, q_s=q_s, valid=valid, pixel_estimate=est, has_estimate=True,
+                            n_iterations=1, stream=stream)
+            st = cache.render_iteration(target, seed=5, iteration=it, mode=1, update_estimate=upd, stream=stream)
+            torch.cuda.synchronize()
+            outs.append((dev.cpu().numpy().copy() if target is dev else host.copy(), st["vertices"]))
+        assert np.array_equal(outs[0][0], outs[1][0]), (it, upd)
+        assert outs[0][1] == outs[1][1]
+        assert np.isfinite(outs[1][0]).all() and outs[1][0].max() > 0
