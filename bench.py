@@ -430,9 +430,11 @@ def run_mars(args):
 def large_scene(args, M, stream):
     """The heightfield workload (256 x 256 quads = 131k triangles + 202 spheres,
     1024 x 1024, D = 10, three techniques) with the adaptive octree cache
-    (starting as the 32^3 grid, at most 64k leaves): LBVH build time, then 3
-    warm-up and 3 timed MARS iterations; throughput, kernel times, traversal
-    work per ray and the octree's size at this geometry size."""
+    (starting as the 32^3 grid, at most 64k leaves): hierarchy build time, then
+    3 warm-up and 3 timed MARS iterations with the bidirectional application's
+    image-level rules (Sec. 5.1: V_I without the 10 brightest pixels, the
+    iterations combined with weights 1 / V_I); throughput, kernel times,
+    traversal work per ray and the octree's size at this geometry size."""
     import torch
     cfg = W.config_heightfield(1024, 1024)
     cfg.scene.bvh = BVH_KINDS[args.bvh]
@@ -446,7 +448,7 @@ def large_scene(args, M, stream):
     it = 0
     for k in range(3):
         cache.render_iteration(img, seed=77, iteration=it, mode=M.MARS_MODE_WARMUP, update_estimate=True,
-                               stream=stream)
+                               vi_drop_brightest=10, stream=stream)
         cache.update_counts(stream=stream)
         it += 1
     launch = cache.autotune(iteration=it, seed=77, mode=M.MARS_MODE_MARS, repeats=1, stream=stream)
@@ -456,7 +458,8 @@ def large_scene(args, M, stream):
     e0.record(stream)
     for k in range(3):
         sts.append(cache.render_iteration(img, seed=77, iteration=it, mode=M.MARS_MODE_MARS, update_estimate=True,
-                                          profile=True, stream=stream))
+                                          profile=True, vi_drop_brightest=10, combine=2 if k == 0 else 1,
+                                          stream=stream))
         cache.update_counts(stream=stream)
         it += 1
     e1.record(stream)
@@ -472,7 +475,10 @@ def large_scene(args, M, stream):
                                   for k in ("trace", "shade", "shadow", "reverse", "image")},
            "closest_hit_per_ray": {"nodes": round(tw[0] / n, 2), "prim_tests": round(sum(tw[1:]) / n, 2)},
            "mean_beta": [round(sum(s["mean_beta"][t] for s in sts) / 3, 4) for t in range(3)],
-           "octree_leaves": int(cache.info()["oct_n_leaves"]), "launch": launch}
+           "octree_leaves": int(cache.info()["oct_n_leaves"]), "launch": launch,
+           "progressive": {"vi_drop_brightest": 10, "combined_iterations": 3,
+                           "combined_weight": round(cache.combined_image(stream=stream)[1], 4),
+                           "VI": [round(s["VI"], 5) for s in sts]}}
     if not args.no_precision:
         # float32 versus float64 statistics at this size (the large bidirectional
         # workload's precision comparison), on the learned state and tree
@@ -579,7 +585,7 @@ def efficiency(args, M, cfg, scene, cache, seed, it0, stream):
     ref = (acc / args.ref_spp).cpu().numpy().reshape(-1, 3)
     del ref_cache
 
-    def timed(c, mode, n, it_base):
+    def timed(c, mode, n, it_base, weights=M.MARS_WEIGHTS_AWARE):
         a = torch.zeros(npx * 3, dtype=torch.float64, device="cuda")
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
@@ -587,7 +593,7 @@ def efficiency(args, M, cfg, scene, cache, seed, it0, stream):
         rays = 0
         for k in range(n):
             st = c.render_iteration(img, seed=seed + 17, iteration=it_base + k, mode=mode, collect=False,
-                                    update_estimate=False, stream=stream)
+                                    weights=weights, update_estimate=False, stream=stream)
             rays += st["rays"]
             a += img.double()
         e1.record(stream)
@@ -601,7 +607,19 @@ def efficiency(args, M, cfg, scene, cache, seed, it0, stream):
     mars = timed(cache, M.MARS_MODE_MARS, args.eff_spp, 20000)
     fixed_cache = M.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, stream=stream)
     fixed = timed(fixed_cache, M.MARS_MODE_FIXED, args.eff_spp, 20000)
+    # the budget-unaware balance heuristic (weights from the sampling densities
+    # alone) learns its own counts over as many iterations, then renders alike
+    un_cache = M.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, stream=stream)
+    for k in range(it0):
+        un_cache.render_iteration(img, seed=seed, iteration=k, mode=M.MARS_MODE_WARMUP if k < args.warmup
+                                  else M.MARS_MODE_MARS, weights=M.MARS_WEIGHTS_UNAWARE, update_estimate=True,
+                                  stream=stream)
+        un_cache.update_counts(stream=stream)
+    unaware = timed(un_cache, M.MARS_MODE_MARS, args.eff_spp, 20000, weights=M.MARS_WEIGHTS_UNAWARE)
+    unaware["learning_iterations"] = it0
+    unaware["ratio_vs_aware"] = unaware["efficiency"] / mars["efficiency"]
     return {"mars": mars, "fixed_count_mis": fixed, "ratio": mars["efficiency"] / fixed["efficiency"],
+            "budget_unaware": unaware,
             "reference_spp": args.ref_spp,
             "protocol": "counts learned over warm-up + timed steps, then frozen; both estimators render "
                         f"{args.eff_spp} fresh iterations; reference = fixed-count MIS, {args.ref_spp} spp, "

@@ -150,7 +150,18 @@ typedef struct {
  * update_estimate: after rendering, add the image to the running mean and
  *   recompute the pixel estimate, V_I and C_I (needed before mars_update_counts).
  * profile: time every kernel launch with CUDA events on `stream`; the device
- *   time per stage is returned in mars_iter_stats. */
+ *   time per stage is returned in mars_iter_stats.
+ * vi_drop_brightest: K in 0..MARS_MAX_DROP_BRIGHTEST.  K > 0 replaces the
+ *   outlier clamp of V_I by the rejection of the bidirectional application
+ *   (Sec. 5.1 "Implementation"): the K pixels of highest luminance of the
+ *   iteration's image (0.2126 R + 0.7152 G + 0.0722 B in float32; ties to the
+ *   lower pixel index) leave the V_I mean, the others enter unclamped.
+ * combine: progressive combination of Sec. 5.1 (the inverse-variance weighted
+ *   combination of iterations): 1 adds this iteration's image with weight
+ *   1 / max(V_I, 1e-12) to the cache's combined image, 2 starts a new
+ *   combination with it; needs update_estimate.  Read it with
+ *   mars_cache_combined_image. */
+#define MARS_MAX_DROP_BRIGHTEST 16
 typedef struct {
   uint32_t seed, job, iteration;
   int32_t mode;
@@ -164,6 +175,8 @@ typedef struct {
                               further limited to max(clamp_lo, M / P), P = the product of the budgets
                               that drew the path so far, so one camera sample spawns at most M
                               vertices per depth in expectation; any budget field stays unbiased */
+  int32_t vi_drop_brightest;  /* K brightest pixels left out of V_I (0: the outlier clamp) */
+  int32_t combine;            /* 0 none, 1 add to, 2 restart the inverse-variance combination */
 } mars_iter_params;
 
 /* What one iteration did (host memory, filled by mars_render_iteration). */
@@ -277,6 +290,14 @@ mars_status mars_render_iteration(mars_cache* cache, const mars_iter_params* par
  * from the accumulated deposits (P_b = 0.9 h_b / H + 0.1 / 256).  Zeroes the
  * statistics.  Asynchronous on `stream`.  Errors: CUDA. */
 mars_status mars_update_counts(mars_cache* cache, void* stream);
+
+/* ---- progressive combination (Sec. 5.1 "Implementation") ----------------
+ * The combined image sum_i w_i I_i / sum_i w_i over the iterations rendered
+ * with params.combine (w_i = 1 / max(V_I of iteration i, 1e-12)), packed rgb
+ * float32 [height][width][3] into host memory image_rgb, and sum_i w_i into
+ * *weight_sum (either may be NULL).  Zeros while nothing was combined.
+ * Synchronises `stream`.  Errors: INVALID_ARG, OOM (staging buffer), CUDA. */
+mars_status mars_cache_combined_image(mars_cache* cache, float* image_rgb, double* weight_sum, void* stream);
 
 /* ---- state transfer (checkpoint / resume, teacher-forced checks) ----------
  * Synchronous copies of the fields whose pointers are non-NULL. */

@@ -91,6 +91,9 @@ def lib():
             L.orc_image_stats.argtypes = [ct.c_int, ct.c_int, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double),
                                           ct.c_int, ct.c_double, ct.POINTER(ct.c_double)]
             L.orc_image_stats.restype = ct.c_double
+            L.orc_image_stats_k.argtypes = [ct.c_int, ct.c_int, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double),
+                                            ct.c_int, ct.c_double, ct.c_int, ct.POINTER(ct.c_double)]
+            L.orc_image_stats_k.restype = ct.c_double
             L.orc_update_counts.argtypes = [ct.c_int, ct.c_int, ct.POINTER(ct.c_double), ct.c_double,
                                             ct.c_double, ct.POINTER(ct.c_float), ct.POINTER(ct.c_float),
                                             ct.POINTER(ct.c_uint8)]
@@ -226,15 +229,30 @@ def render(scene, *, grid_n, techniques, max_depth, mode=MODE_WARMUP, weights=WE
     return RenderResult(image, stats, hist, counters)
 
 
-def image_stats(width, height, img, run_sum, n_prev, outlier=50.0):
-    """Returns (V_I, new run_sum, pixel estimate)."""
+def image_stats(width, height, img, run_sum, n_prev, outlier=50.0, drop_k=0):
+    """Returns (V_I, new run_sum, pixel estimate).  drop_k > 0: the rejection of
+    the bidirectional application (Sec. 5.1) instead of the outlier clamp."""
     L = lib()
     img = np.ascontiguousarray(img, np.float64).reshape(-1, 3)
     rs = np.array(run_sum, dtype=np.float64).reshape(-1, 3).copy()
     est = np.zeros_like(rs)
-    vi = L.orc_image_stats(int(width), int(height), _p(img, ct.c_double), _p(rs, ct.c_double),
-                           int(n_prev), float(outlier), _p(est, ct.c_double))
+    vi = L.orc_image_stats_k(int(width), int(height), _p(img, ct.c_double), _p(rs, ct.c_double),
+                             int(n_prev), float(outlier), int(drop_k), _p(est, ct.c_double))
     return float(vi), rs, est
+
+
+def combine(images, vis):
+    """Progressive combination of Sec. 5.1 ("the inverse-variance weighted
+    combination of all iterations"): sum_i w_i I_i / sum_i w_i with
+    w_i = 1 / max(V_I of iteration i, 1e-12).  Returns (image, sum of weights)."""
+    acc = None
+    wsum = 0.0
+    for img, vi in zip(images, vis):
+        w = 1.0 / max(float(vi), 1e-12)
+        a = np.asarray(img, np.float64) * w
+        acc = a if acc is None else acc + a
+        wsum += w
+    return acc / wsum, wsum
 
 
 def update_counts(stats, VI, CI, techniques, q_rr, q_s, valid):

@@ -882,8 +882,26 @@ int orc_render(const orc_scene_desc* scene, const orc_params* P, orc_state* st, 
 }
 
 /* ------------------------------------------------------------ image / update */
+/* Brightness of a pixel for the rejection of the bidirectional application
+ * (Sec. 5.1 "Implementation": the brightest pixels of a pass leave its image
+ * variance estimate): luminance taken in float32, each product and sum rounded
+ * in turn, so that the order of pixels equals the kernel's. */
+static float bright_lum(const double* I) {
+  float r = (float)I[0], g = (float)I[1], b = (float)I[2];
+  float a = 0.2126f * r;
+  float c = 0.7152f * g;
+  float d = 0.0722f * b;
+  float l = (a + c) + d;
+  return l > 0.0f ? l : 0.0f;
+}
+
 double orc_image_stats(int W, int H, const double* img, double* run_sum, int n_prev,
                        double outlier, double* est_out) {
+  return orc_image_stats_k(W, H, img, run_sum, n_prev, outlier, 0, est_out);
+}
+
+double orc_image_stats_k(int W, int H, const double* img, double* run_sum, int n_prev,
+                         double outlier, int drop_k, double* est_out) {
   int n = W * H;
   double inv = 1.0 / (double)(n_prev + 1);
   double chmean[3] = {0, 0, 0};
@@ -915,16 +933,45 @@ double orc_image_stats(int W, int H, const double* img, double* run_sum, int n_p
       }
   /* image relative variance (Sec. 4.1 "Image estimates") with the sample
    * clamped at outlier x estimate ("Outlier clamping"); one sample per pixel */
+  if (drop_k <= 0) {
+    double vi = 0.0;
+    for (int p = 0; p < n; ++p)
+      for (int c = 0; c < 3; ++c) {
+        double e = est_out[3 * p + c];
+        double I = img[3 * p + c];
+        if (I > outlier * e) I = outlier * e;
+        double r = (I - e) / e;
+        vi += r * r;
+      }
+    return vi / (3.0 * (double)n);
+  }
+  /* the bidirectional application's rejection instead (Sec. 5.1
+   * "Implementation"): the drop_k brightest pixels (ties: lower index first)
+   * leave the mean, the others enter unclamped */
+  unsigned char* dropped = (unsigned char*)calloc((size_t)n, 1);
+  for (int k = 0; k < drop_k && k < n; ++k) {
+    int best = -1;
+    float bl = -1.0f;
+    for (int p = 0; p < n; ++p) {
+      if (dropped[p]) continue;
+      float l = bright_lum(img + 3 * p);
+      if (l > bl) { bl = l; best = p; }  /* strict: the lower index wins a tie */
+    }
+    dropped[best] = 1;
+  }
   double vi = 0.0;
-  for (int p = 0; p < n; ++p)
+  int kept = 0;
+  for (int p = 0; p < n; ++p) {
+    if (dropped[p]) continue;
+    ++kept;
     for (int c = 0; c < 3; ++c) {
       double e = est_out[3 * p + c];
-      double I = img[3 * p + c];
-      if (I > outlier * e) I = outlier * e;
-      double r = (I - e) / e;
+      double r = (img[3 * p + c] - e) / e;
       vi += r * r;
     }
-  return vi / (3.0 * (double)n);
+  }
+  free(dropped);
+  return vi / (3.0 * (double)kept);
 }
 
 /* Fixed-point step (Eq. optimalBeta in its spatial form, Sec. 3.1): the cache

@@ -89,6 +89,11 @@ int orc_render(const orc_scene_desc* scene, const orc_params* params, orc_state*
  * returns V_I = mean over pixels and channels of ((min(img, outlier*est) - est)/est)^2. */
 double orc_image_stats(int width, int height, const double* img, double* run_sum,
                        int n_prev, double outlier, double* est_out);
+/* The same with drop_k > 0: V_I instead leaves out the drop_k brightest pixels
+ * (float32 luminance, ties to the lower index) and clamps no sample (the
+ * rejection of the bidirectional application, Sec. 5.1).  drop_k = 0: as above. */
+double orc_image_stats_k(int width, int height, const double* img, double* run_sum,
+                         int n_prev, double outlier, int drop_k, double* est_out);
 
 /* One fixed-point step per (cell, technique): q^RR, q^S per channel from the
  * statistics, V_I and C_I.  Keeps previous values where n < 2, cost = 0 or

@@ -19,6 +19,7 @@ MARS_CACHE_FP32_STATISTICS = 1
 MARS_CACHE_OCTREE = 2
 MARS_CACHE_NO_GRAPHS = 4
 MARS_BVH_SAH = 0
+MARS_MAX_DROP_BRIGHTEST = 16
 MARS_BVH_LBVH = 1
 NUM_SLOTS, NUM_STATS, GUIDE_BINS, MAX_DEPTH = 3, 8, 256, 16
 
@@ -54,6 +55,7 @@ class mars_iter_params(ct.Structure):
         ("clamp_lo", ct.c_float), ("clamp_hi", ct.c_float), ("outlier", ct.c_float),
         ("collect", ct.c_int32), ("image_on_host", ct.c_int32), ("update_estimate", ct.c_int32),
         ("profile", ct.c_int32), ("max_multiplicity", ct.c_float),
+        ("vi_drop_brightest", ct.c_int32), ("combine", ct.c_int32),
     ]
 
 
@@ -118,6 +120,7 @@ SIGNATURES = {
     "mars_cache_info_get": ([_VP, ct.POINTER(mars_cache_info)], ct.c_int),
     "mars_render_iteration": ([_VP, ct.POINTER(mars_iter_params), _VP, ct.POINTER(mars_iter_stats), _VP], ct.c_int),
     "mars_update_counts": ([_VP, _VP], ct.c_int),
+    "mars_cache_combined_image": ([_VP, _VP, ct.POINTER(ct.c_double), _VP], ct.c_int),
     "mars_cache_get_state": ([_VP, ct.POINTER(mars_cache_state), _VP], ct.c_int),
     "mars_cache_set_state": ([_VP, ct.POINTER(mars_cache_state), _VP], ct.c_int),
     "mars_cache_get_launch": ([_VP, ct.POINTER(mars_launch_config)], ct.c_int),

@@ -507,7 +507,8 @@ uint64_t cache_footprint(int64_t cells, int64_t pixels, int max_depth, int techn
   uint64_t b = (uint64_t)cap * (SLOT_BYTES + SHADOW_BYTES);
   b += (uint64_t)cells * NT * (2 * sizeof(float4) + NSTAT * sizeof(double));
   if (techniques & MARS_TECH_GUIDED) b += (uint64_t)cells * GUIDE_BINS * 2 * sizeof(float);
-  b += (uint64_t)pixels * 3 * sizeof(float4);
+  b += (uint64_t)pixels * 4 * sizeof(float4);  // running sum, estimate, image, combination
+  b += (uint64_t)IMG_TOPK_BLOCKS * MAX_DROP * sizeof(unsigned long long);
   return b + sizeof(DevCounters) + 4096 * (sizeof(IterArgs) + sizeof(unsigned int)) + 4096;
 }
 
@@ -613,6 +614,13 @@ mars_status cache_create_impl(const mars_scene* s, const mars_cache_desc* d, cud
     return cleanup(e, "argument alloc");
   c->h_args = (IterArgs*)pinned_acquire(sizeof(IterArgs) * c->max_tiles);
   if (!c->h_args) return cleanup(cudaErrorMemoryAllocation, "pinned alloc");
+  if ((e = dev_alloc((void**)&c->d_comb, sizeof(float4) * pixels, st)) != cudaSuccess ||
+      (e = dev_alloc((void**)&c->d_comb_w, sizeof(double), st)) != cudaSuccess ||
+      (e = dev_alloc((void**)&c->d_topk, sizeof(unsigned long long) * IMG_TOPK_BLOCKS * MAX_DROP, st)) !=
+          cudaSuccess)
+    return cleanup(e, "image alloc");
+  cudaMemsetAsync(c->d_comb, 0, sizeof(float4) * pixels, st);
+  cudaMemsetAsync(c->d_comb_w, 0, sizeof(double), st);
   c->use_graphs = (d->flags & MARS_CACHE_NO_GRAPHS) == 0;
   cudaMemsetAsync(c->d_cnt, 0, sizeof(float4) * 2 * NT * cells, st);
   if (c->d_stats) cudaMemsetAsync(c->d_stats, 0, sizeof(double) * NSTAT * NT * cells, st);
@@ -650,6 +658,9 @@ mars_status cache_create_impl(const mars_scene* s, const mars_cache_desc* d, cud
   c->dc.img = c->d_img;
   c->dc.ctr = c->d_ctr;
   c->dc.tile_status = c->d_tile_status;
+  c->dc.comb = c->d_comb;
+  c->dc.comb_w = c->d_comb_w;
+  c->dc.topk = c->d_topk;
   if (octree) {
     // the initial tree equals the grid: levels 0..L0 complete, breadth first,
     // children of a node consecutive by octant, leaves numbered like the grid
@@ -779,7 +790,7 @@ void cache_destroy_impl(mars_cache* c) {
   dev_free(c->arena.SL, st);
   void* ptrs[] = {c->d_cnt, c->d_stats, c->d_stats32, c->d_hist, c->d_cdf, c->d_guide_dirty, c->d_est, c->d_run,
                   c->d_img, c->d_ctr, c->d_tile_status, c->d_oct_nodes, c->d_oct_level, c->d_oct_lnode,
-                  c->d_oct_meta, c->d_oct_split, c->d_oct_leaf_n};
+                  c->d_oct_meta, c->d_oct_split, c->d_oct_leaf_n, c->d_comb, c->d_comb_w, c->d_topk};
   for (void* p : ptrs) dev_free(p, st);
   pinned_release(c->h_ctr, sizeof(DevCounters));
   pinned_release(c->h_tile_status, sizeof(unsigned int) * c->max_tiles);
@@ -841,6 +852,13 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
   if (!(p->outlier > 0.0f)) return set_error(MARS_ERR_INVALID_ARG, "outlier multiple must be positive");
   if (!(p->max_multiplicity >= 0.0f)) return set_error(MARS_ERR_INVALID_ARG, "max_multiplicity must be >= 0");
   if (p->image_on_host && !image) return set_error(MARS_ERR_INVALID_ARG, "image_on_host without an image");
+  if (p->vi_drop_brightest < 0 || p->vi_drop_brightest > MARS_MAX_DROP_BRIGHTEST ||
+      (int64_t)p->vi_drop_brightest >= c->pixels)
+    return set_error(MARS_ERR_INVALID_ARG, "vi_drop_brightest %d outside 0..%d (and below the pixel count)",
+                     p->vi_drop_brightest, MARS_MAX_DROP_BRIGHTEST);
+  if (p->combine < 0 || p->combine > 2) return set_error(MARS_ERR_INVALID_ARG, "combine %d outside 0..2", p->combine);
+  if (p->combine && !p->update_estimate)
+    return set_error(MARS_ERR_INVALID_ARG, "combine needs update_estimate (the weight is 1 / V_I)");
   DeviceGuard g(c->device);
   if (!g.ok) return set_error(MARS_ERR_CUDA, "cannot select device %d", c->device);
   c->last_stream = st;
@@ -859,6 +877,8 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
   it.outlier = p->outlier;
   it.max_mult = p->max_multiplicity;
   it.n_prev = c->n_iterations;
+  it.drop_k = p->vi_drop_brightest;
+  it.combine = p->combine;
 
   // reset the iteration counters (rays, vertices, beta sums, image sums)
   cudaError_t e = cudaMemsetAsync(c->d_ctr, 0, sizeof(DevCounters), st);
@@ -921,7 +941,9 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
       cudaEvent_t* iev = profile ? c->events.data() + tiles.size() * per_tile : nullptr;
       if (iev) cudaEventRecord(iev[0], q);
       if (p->update_estimate) {
-        if ((r = launch_image_stats(c->dc, s->width, s->height, c->d_args, dev_out, q)) != cudaSuccess) return r;
+        if ((r = launch_image_stats(c->dc, s->width, s->height, c->d_args, dev_out, p->vi_drop_brightest > 0,
+                                    p->combine != 0, q)) != cudaSuccess)
+          return r;
       } else if (dev_out) {
         if ((r = launch_image_copy(c->dc, (int)npx, dev_out, q)) != cudaSuccess) return r;
       }
@@ -940,6 +962,8 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
       GraphKey key;
       key.update_estimate = p->update_estimate != 0;
       key.dev_out = dev_out;
+      key.drop = p->vi_drop_brightest > 0;
+      key.combine = p->combine != 0;
       key.L = Ls[0];
       if (!c->graph_exec || !c->graph_key.covers(key)) {
         // recorded with twice the grids asked for (at most the persistent
@@ -976,7 +1000,8 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
     }
     launches += (uint32_t)(tiles.size() * tile_launches(D, c->techniques));
     wave_launches += (uint32_t)(tiles.size() * D);
-    launches += p->update_estimate ? 3 : (dev_out ? 1 : 0);
+    launches += p->update_estimate ? 3 + (p->vi_drop_brightest > 0 ? 2 : 0) + (p->combine ? 1 : 0)
+                                   : (dev_out ? 1 : 0);
     used += (uint32_t)tiles.size();
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return poison(c, e, "render");
     if (p->profile) {
@@ -1354,6 +1379,33 @@ mars_status mars_cache_get_state(mars_cache* cache, mars_cache_state* state, voi
   return get_state_impl(cache, state, (cudaStream_t)stream);
 }
 
+mars_status mars_cache_combined_image(mars_cache* c, float* image_rgb, double* weight_sum, void* stream) {
+  if (!c) return set_error(MARS_ERR_INVALID_ARG, "null cache");
+  if (c->poisoned) return set_error(MARS_ERR_CUDA, "cache is poisoned by an earlier CUDA error");
+  DeviceGuard g(c->device);
+  if (!g.ok) return set_error(MARS_ERR_CUDA, "cannot select device %d", c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  c->last_stream = st;
+  const int64_t npx = c->pixels;
+  cudaError_t e;
+  if (image_rgb) {
+    if (!c->d_host_stage &&
+        (e = dev_alloc((void**)&c->d_host_stage, sizeof(float) * 3 * (size_t)npx, st)) != cudaSuccess)
+      return set_error(e == cudaErrorMemoryAllocation ? MARS_ERR_OOM : MARS_ERR_CUDA, "staging alloc: %s",
+                       cudaGetErrorString(e));
+    if ((e = launch_combined_out(c->dc, (int)npx, c->d_host_stage, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(image_rgb, c->d_host_stage, sizeof(float) * 3 * (size_t)npx, cudaMemcpyDeviceToHost,
+                             st)) != cudaSuccess)
+      return poison(c, e, "combined image");
+  }
+  double w = 0.0;
+  if ((e = cudaMemcpyAsync(&w, c->d_comb_w, sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(st)) != cudaSuccess)
+    return poison(c, e, "combined image");
+  if (weight_sum) *weight_sum = w;
+  return MARS_OK;
+}
+
 mars_status mars_cache_set_state(mars_cache* cache, const mars_cache_state* state, void* stream) {
   return set_state_impl(cache, state, (cudaStream_t)stream);
 }
@@ -1403,6 +1455,7 @@ mars_status mars_cache_autotune(mars_cache* c, const mars_iter_params* params, i
   p.collect = 0;
   p.update_estimate = 0;
   p.image_on_host = 0;
+  p.combine = 0;
   p.profile = 1;
   int threads[WAVE_KERNELS], bps[WAVE_KERNELS], var[WAVE_KERNELS];
   for (int k = 0; k < WAVE_KERNELS; ++k) {

@@ -51,11 +51,13 @@ mars_status set_error(mars_status s, const char* fmt, ...);
 // drift from one iteration to the next; an exact match would record a new
 // graph almost every time.)
 struct GraphKey {
-  bool update_estimate = false;
+  bool update_estimate = false, drop = false, combine = false;
   float* dev_out = nullptr;
   WaveLaunch L{};
   bool covers(const GraphKey& want) const {
-    if (update_estimate != want.update_estimate || dev_out != want.dev_out) return false;
+    if (update_estimate != want.update_estimate || dev_out != want.dev_out || drop != want.drop ||
+        combine != want.combine)
+      return false;
     for (int k = 0; k < WAVE_KERNELS; ++k) {
       if (L.threads[k] != want.L.threads[k] || L.variant[k] != want.L.variant[k] || L.grid[k] != want.L.grid[k])
         return false;
@@ -149,6 +151,9 @@ struct mars_cache {
   mars::IterArgs* h_args = nullptr;
   mars::IterArgs* d_args = nullptr;
   float* d_host_stage = nullptr;  // packed rgb image for image_on_host (first use)
+  float4* d_comb = nullptr;       // inverse-variance weighted image sum
+  double* d_comb_w = nullptr;     // its weight sum
+  unsigned long long* d_topk = nullptr;  // brightest-pixel candidates
   // the recorded single-tile iteration graph (MARS_CACHE_NO_GRAPHS: none)
   bool use_graphs = true;
   cudaGraphExec_t graph_exec = nullptr;

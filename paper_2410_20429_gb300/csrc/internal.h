@@ -127,6 +127,7 @@ struct DevCounters {
   double vi_sum;
   float chsum32[3], vi_sum32;  // the same sums in float32 (float32 statistics)
   double VI, CI;               // results of the last image-stats pass
+  int vi_dropped;              // pixels left out of the V_I mean
 };
 
 struct DevCache {
@@ -153,7 +154,12 @@ struct DevCache {
   float* oct_leaf_n;    // [n_cells] samples of the last iteration per leaf
   int oct_cap_nodes;
   float split_samples;
+  float4* comb;                 // [pixels] inverse-variance weighted image sum
+  double* comb_w;               // its weight sum
+  unsigned long long* topk;     // [IMG_TOPK_BLOCKS * MAX_DROP] brightness candidates
 };
+constexpr int MAX_DROP = MARS_MAX_DROP_BRIGHTEST;
+constexpr int IMG_TOPK_BLOCKS = 1024;
 constexpr int OCT_LMAX = MARS_OCTREE_MAX_LEVEL;
 
 // Arguments of one tile of one iteration.  They live in device memory (one
@@ -166,6 +172,8 @@ struct IterArgs {
   float max_mult;  // path multiplicity cap (0: none)
   int tile_begin, tile_end, tile_slot;
   int n_prev;      // iterations already summed into the running image
+  int drop_k;      // V_I leaves out the drop_k brightest pixels (0: outlier clamp)
+  int combine;     // 0 none, 1 add to, 2 restart the inverse-variance combination
 };
 
 // Launch shape of the four per-wave kernels: threads per block (a multiple of
@@ -192,9 +200,13 @@ int wave_variant_registers(int kernel, int v);    // its register cap (0: the co
 bool wave_threads_ok(int threads);
 int tile_launches(int max_depth, int techniques);  // kernels launch_tile issues
 // image statistics (stats.cu)
-// it: device pointer to the iteration's arguments (n_prev, outlier)
+// it: device pointer to the iteration's arguments (n_prev, outlier, drop_k,
+// combine); drop / combine: whether the brightest-pixel rejection and the
+// progressive combination kernels run
 cudaError_t launch_image_stats(const DevCache& c, int width, int height, const IterArgs* it,
-                               float* image_out_dev, cudaStream_t st);
+                               float* image_out_dev, bool drop, bool combine, cudaStream_t st);
+// the combined image divided by its weight sum, packed rgb, into out (device)
+cudaError_t launch_combined_out(const DevCache& c, int npix, float* out, cudaStream_t st);
 cudaError_t launch_image_copy(const DevCache& c, int npix, float* out, cudaStream_t st);
 cudaError_t launch_update(const DevCache& c, int num_sms, cudaStream_t st);
 // octree refinement after an update (stats.cu): leaf_samples must run before

@@ -13,6 +13,8 @@
 // with m2, var the per-sample moments of Sec. 4.1 "Local estimates" and C_t the
 // mean cost; cells with n < 2 or no cost keep their factors; statistics reset.
 // The guided technique's per-cell CDF is rebuilt from the accumulated deposits.
+#include <algorithm>
+
 #include "device.cuh"
 
 namespace mars {
@@ -75,12 +77,26 @@ __global__ void __launch_bounds__(IMG_THREADS) k_img_accum(DevCache c, int npix,
   }
 }
 
+// Squared relative errors of one pixel's three channels, each cast to T before
+// the sum; with `clamp` the sample is first bounded at outlier x estimate.
+template <typename T>
+__device__ __forceinline__ T pixel_err(float4 I, float e0, float e1, float e2, float outlier, bool clamp) {
+  const float i0 = clamp ? fminf(I.x, outlier * e0) : I.x;
+  const float i1 = clamp ? fminf(I.y, outlier * e1) : I.y;
+  const float i2 = clamp ? fminf(I.z, outlier * e2) : I.z;
+  const float r0 = (i0 - e0) / e0;
+  const float r1 = (i1 - e1) / e1;
+  const float r2 = (i2 - e2) / e2;
+  return (T)(r0 * r0) + (T)(r1 * r1) + (T)(r2 * r2);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(IMG_THREADS) k_img_est(DevCache c, int W, int H, const IterArgs* __restrict__ itp) {
   __shared__ T sh[IMG_THREADS / 32];
   if (c.ctr->any_overflow) return;
   const int n_prev = itp->n_prev;
   const float outlier = itp->outlier;
+  const bool clamp = itp->drop_k <= 0;  // the brightest-pixel rejection replaces the clamp
   const int npix = W * H;
   const float inv = 1.0f / (float)(n_prev + 1);
   const bool f32 = c.stats32 != nullptr;
@@ -106,11 +122,7 @@ __global__ void __launch_bounds__(IMG_THREADS) k_img_est(DevCache c, int W, int 
     float e1 = fmaxf(fmaxf(s1 / (float)k, fl1), 1e-8f);
     float e2 = fmaxf(fmaxf(s2 / (float)k, fl2), 1e-8f);
     c.est[p] = make_float4(e0, e1, e2, 0.0f);
-    const float4 I = c.img[p];
-    const float r0 = (fminf(I.x, outlier * e0) - e0) / e0;
-    const float r1 = (fminf(I.y, outlier * e1) - e1) / e1;
-    const float r2 = (fminf(I.z, outlier * e2) - e2) / e2;
-    vi += (T)(r0 * r0) + (T)(r1 * r1) + (T)(r2 * r2);
+    vi += pixel_err<T>(c.img[p], e0, e1, e2, outlier, clamp);
   }
   vi = block_sum<T>(vi, sh);
   if (threadIdx.x == 0) add_sum<T>(&c.ctr->vi_sum, &c.ctr->vi_sum32, vi);
@@ -126,13 +138,137 @@ __global__ void __launch_bounds__(IMG_THREADS) k_img_copy(DevCache c, int npix, 
   }
 }
 
+// ---- brightest-pixel rejection of V_I (Sec. 5.1 "Implementation")
+// Brightness order: float32 luminance (products and sums rounded one by one,
+// as the oracle does), descending, then pixel index ascending; the key is
+// unique per pixel and 0 never names one.
+__device__ __forceinline__ unsigned long long bright_key(float4 I, int p) {
+  float l = __fadd_rn(__fadd_rn(__fmul_rn(0.2126f, I.x), __fmul_rn(0.7152f, I.y)), __fmul_rn(0.0722f, I.z));
+  if (!(l > 0.0f)) l = 0.0f;
+  return ((unsigned long long)__float_as_uint(l) << 32) | (unsigned long long)(0xffffffffu - (unsigned)p);
+}
+
+// keeps L (descending, zero-filled) as the K largest keys seen
+__device__ __forceinline__ void topk_insert(unsigned long long (&L)[MAX_DROP], int K, unsigned long long x) {
+#pragma unroll
+  for (int q = 0; q < MAX_DROP; ++q)
+    if (q < K && x > L[q]) {
+      const unsigned long long t = L[q];
+      L[q] = x;
+      x = t;
+    }
+}
+
+// K rounds of "largest head of all threads' lists": the owner pops it; out[r]
+// (thread 0) receives the r-th largest key of the block (0 if none)
+__device__ __forceinline__ void topk_block(unsigned long long (&L)[MAX_DROP], int K, unsigned long long* out,
+                                           unsigned long long* sh, unsigned long long* best) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int r = 0; r < K; ++r) {
+    unsigned long long v = L[0];
+    for (int off = 16; off > 0; off >>= 1) {
+      const unsigned long long o = __shfl_xor_sync(0xffffffffu, v, off);
+      v = o > v ? o : v;
+    }
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long m = 0;
+      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) m = sh[k] > m ? sh[k] : m;
+      *best = m;
+      out[r] = m;
+    }
+    __syncthreads();
+    const unsigned long long m = *best;
+    if (m != 0 && L[0] == m) {
+#pragma unroll
+      for (int q = 0; q < MAX_DROP - 1; ++q) L[q] = L[q + 1];
+      L[MAX_DROP - 1] = 0;
+    }
+    __syncthreads();
+  }
+}
+
+// block b: the K brightest pixels of its contiguous pixel range
+__global__ void __launch_bounds__(IMG_THREADS) k_img_topk(DevCache c, int npix, const IterArgs* __restrict__ itp) {
+  __shared__ unsigned long long sh[IMG_THREADS / 32], best;
+  if (c.ctr->any_overflow) return;
+  const int K = itp->drop_k;
+  if (K <= 0) return;
+  const int per = (npix + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int lo = (int)blockIdx.x * per, hi = min(npix, lo + per);
+  unsigned long long L[MAX_DROP];
+#pragma unroll
+  for (int q = 0; q < MAX_DROP; ++q) L[q] = 0;
+  for (int p = lo + threadIdx.x; p < hi; p += blockDim.x) topk_insert(L, K, bright_key(c.img[p], p));
+  topk_block(L, K, c.topk + (size_t)blockIdx.x * K, sh, &best);
+}
+
+// one block: the K brightest of all candidates leave the V_I sum (their terms,
+// recomputed from the same image and estimate, are subtracted)
+template <typename T>
+__global__ void __launch_bounds__(1024) k_img_drop(DevCache c, int nblocks, const IterArgs* __restrict__ itp) {
+  __shared__ unsigned long long sh[32], best, sel[MAX_DROP];
+  if (c.ctr->any_overflow) return;
+  const int K = itp->drop_k;
+  if (K <= 0) return;
+  unsigned long long L[MAX_DROP];
+#pragma unroll
+  for (int q = 0; q < MAX_DROP; ++q) L[q] = 0;
+  const int ncand = nblocks * K;  // k_img_topk wrote K keys per block
+  for (int i = threadIdx.x; i < ncand; i += blockDim.x) topk_insert(L, K, c.topk[i]);
+  topk_block(L, K, sel, sh, &best);
+  if (threadIdx.x == 0) {
+    T sum = 0;
+    int n = 0;
+    for (int r = 0; r < K; ++r) {
+      if (sel[r] == 0) continue;
+      const int p = (int)(0xffffffffu - (unsigned)(sel[r] & 0xffffffffull));
+      const float4 e = c.est[p];
+      sum += pixel_err<T>(c.img[p], e.x, e.y, e.z, 0.0f, false);
+      ++n;
+    }
+    if (c.stats32) c.ctr->vi_sum32 -= (float)sum; else c.ctr->vi_sum -= (double)sum;
+    c.ctr->vi_dropped = n;
+  }
+}
+
+// ---- progressive combination (Sec. 5.1): weight 1 / V_I of this iteration
+__global__ void __launch_bounds__(IMG_THREADS) k_img_combine(DevCache c, int npix, const IterArgs* __restrict__ itp) {
+  if (c.ctr->any_overflow) return;
+  const int mode = itp->combine;
+  if (mode == 0) return;
+  const float w = (float)(1.0 / fmax(c.ctr->VI, 1e-12));
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) {
+    const float4 I = c.img[p];
+    float4 a = mode == 2 ? make_float4(0.f, 0.f, 0.f, 0.f) : c.comb[p];
+    a.x += w * I.x;
+    a.y += w * I.y;
+    a.z += w * I.z;
+    c.comb[p] = a;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *c.comb_w = (mode == 2 ? 0.0 : *c.comb_w) + (double)w;
+}
+
+__global__ void __launch_bounds__(IMG_THREADS) k_img_comb_out(DevCache c, int npix, float* out) {
+  const double w = *c.comb_w;
+  const float inv = w > 0.0 ? (float)(1.0 / w) : 0.0f;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) {
+    const float4 a = c.comb[p];
+    out[3 * p] = a.x * inv;
+    out[3 * p + 1] = a.y * inv;
+    out[3 * p + 2] = a.z * inv;
+  }
+}
+
 __global__ void k_img_final(DevCache c, int npix) {
   if (threadIdx.x != 0 || c.ctr->any_overflow) return;
+  const int kept = npix - c.ctr->vi_dropped;  // V_I: the mean over the pixels that were kept
   if (c.stats32) {
-    c.ctr->VI = (double)(c.ctr->vi_sum32 / (3.0f * (float)npix));
+    c.ctr->VI = (double)(c.ctr->vi_sum32 / (3.0f * (float)kept));
     c.ctr->CI = (double)((float)c.ctr->rays / (float)npix);
   } else {
-    c.ctr->VI = c.ctr->vi_sum / (3.0 * (double)npix);
+    c.ctr->VI = c.ctr->vi_sum / (3.0 * (double)kept);
     c.ctr->CI = (double)c.ctr->rays / (double)npix;
   }
 }
@@ -368,10 +504,11 @@ cudaError_t launch_octree_refine(const DevCache& c, int num_sms, cudaStream_t st
 }
 
 cudaError_t launch_image_stats(const DevCache& c, int width, int height, const IterArgs* it,
-                               float* image_out_dev, cudaStream_t st) {
+                               float* image_out_dev, bool drop, bool combine, cudaStream_t st) {
   const int npix = width * height;
   int blocks = (npix + IMG_THREADS - 1) / IMG_THREADS;
   if (blocks > 4096) blocks = 4096;
+  const int tblocks = std::min(blocks, IMG_TOPK_BLOCKS);
   if (c.stats32) {
     k_img_accum<float><<<blocks, IMG_THREADS, 0, st>>>(c, npix, it, image_out_dev);
     k_img_est<float><<<blocks, IMG_THREADS, 0, st>>>(c, width, height, it);
@@ -379,7 +516,24 @@ cudaError_t launch_image_stats(const DevCache& c, int width, int height, const I
     k_img_accum<double><<<blocks, IMG_THREADS, 0, st>>>(c, npix, it, image_out_dev);
     k_img_est<double><<<blocks, IMG_THREADS, 0, st>>>(c, width, height, it);
   }
+  if (drop) {
+    // candidates: tblocks x drop_k keys (drop_k <= MAX_DROP; the buffer holds
+    // IMG_TOPK_BLOCKS x MAX_DROP)
+    k_img_topk<<<tblocks, IMG_THREADS, 0, st>>>(c, npix, it);
+    if (c.stats32)
+      k_img_drop<float><<<1, 1024, 0, st>>>(c, tblocks, it);
+    else
+      k_img_drop<double><<<1, 1024, 0, st>>>(c, tblocks, it);
+  }
   k_img_final<<<1, 32, 0, st>>>(c, npix);
+  if (combine) k_img_combine<<<blocks, IMG_THREADS, 0, st>>>(c, npix, it);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_combined_out(const DevCache& c, int npix, float* out, cudaStream_t st) {
+  int blocks = (npix + IMG_THREADS - 1) / IMG_THREADS;
+  if (blocks > 4096) blocks = 4096;
+  k_img_comb_out<<<blocks, IMG_THREADS, 0, st>>>(c, npix, out);
   return cudaGetLastError();
 }
 

@@ -105,10 +105,13 @@ class Cache:
 
     def render_iteration(self, image, *, seed=0, job=0, iteration=0, mode=A.MARS_MODE_WARMUP,
                          weights=A.MARS_WEIGHTS_AWARE, clamp_lo=0.05, clamp_hi=20.0, outlier=50.0, collect=True,
-                         update_estimate=True, profile=False, max_multiplicity=0.0, stream=None) -> dict:
+                         update_estimate=True, profile=False, max_multiplicity=0.0, vi_drop_brightest=0,
+                         combine=0, stream=None) -> dict:
         """Render one iteration into ``image``: a CUDA float32 tensor with
         height*width*3 elements, or a host numpy float32 array of that size (the
-        library then copies the image back)."""
+        library then copies the image back).  ``vi_drop_brightest`` and
+        ``combine`` select the bidirectional application's image-variance
+        rejection and progressive combination (see mars.h)."""
         on_host = isinstance(image, np.ndarray)
         if on_host:
             if image.dtype != np.float32 or not image.flags.c_contiguous or image.size != 3 * self.n_pixels:
@@ -123,7 +126,8 @@ class Cache:
             ptr = image.data_ptr()
         p = A.mars_iter_params(int(seed), int(job), int(iteration), int(mode), int(weights), float(clamp_lo),
                                float(clamp_hi), float(outlier), int(bool(collect)), int(on_host),
-                               int(bool(update_estimate)), int(bool(profile)), float(max_multiplicity))
+                               int(bool(update_estimate)), int(bool(profile)), float(max_multiplicity),
+                               int(vi_drop_brightest), int(combine))
         st = A.mars_iter_stats()
         A.check(self._lib.mars_render_iteration(self.handle, ct.byref(p), ptr, ct.byref(st), _stream_handle(stream)),
                 "mars_render_iteration")
@@ -137,6 +141,15 @@ class Cache:
                 "wave_ms": [[st.wave_ms[k][d] for d in range(self.max_depth)] for k in range(4)],
                 "wave_rays": [st.wave_rays[d] for d in range(self.max_depth)],
                 "trace_work": [[st.trace_work[k][q] for q in range(4)] for k in range(2)]}
+
+    def combined_image(self, stream=None):
+        """(image [height][width][3] float32, weight sum) of the progressive
+        inverse-variance combination."""
+        img = np.zeros((self.scene.height, self.scene.width, 3), np.float32)
+        w = ct.c_double(0.0)
+        A.check(self._lib.mars_cache_combined_image(self.handle, img.ctypes.data, ct.byref(w), _stream_handle(stream)),
+                "mars_cache_combined_image")
+        return img, w.value
 
     def get_launch(self) -> dict:
         """Launch shape of the wave kernels (trace, shade, shadow, reverse)."""

@@ -554,3 +554,64 @@ def test_host_image_equals_device_image(mars, capturable):
         assert np.array_equal(outs[0][0], outs[1][0]), (it, upd)
         assert outs[0][1] == outs[1][1]
         assert np.isfinite(outs[1][0]).all() and outs[1][0].max() > 0
+
+
+@pytest.mark.parametrize("K", [1, 10, 16])
+def test_brightest_pixel_rejection_parity(mars, orc, K):
+    """V_I without its K brightest pixels (Sec. 5.1): the GPU's value against the
+    oracle's on the GPU's own image of the iteration (same running sum); the K
+    pixels are chosen by float32 luminance on both sides, so the choice is the
+    same, and the remaining sums agree to float32 rounding."""
+    cfg = W.config_guided(48, 40)
+    scene, cache = _make(mars, cfg)
+    q_rr, q_s, valid = W.random_count_fields(cfg.n_cells, seed=951, lo=0.3, hi=4.0)
+    est = W.random_pixel_estimate(cfg.scene.n_pixels, seed=952, lo=0.05, hi=0.5)
+    rs = W.random_pixel_estimate(cfg.scene.n_pixels, seed=953, lo=0.1, hi=3.0) * 2.0
+    res = {}
+    for k in (0, K):
+        cache.set_state(q_rr=q_rr, q_s=q_s, valid=valid, pixel_estimate=est, run_sum=rs, has_estimate=True,
+                        n_iterations=2, stats=np.zeros((cfg.n_cells, 3, 8)))
+        import torch
+        img = torch.zeros(cache.n_pixels * 3, dtype=torch.float32, device="cuda")
+        st = cache.render_iteration(img, seed=7, iteration=2, mode=1, update_estimate=True, vi_drop_brightest=k)
+        torch.cuda.synchronize()
+        res[k] = (img.cpu().numpy().reshape(-1, 3).astype(np.float64), st)
+    a, b = res[0], res[K]
+    assert np.array_equal(a[0], b[0])   # the rejection changes V_I only
+    vi0, _, _ = orc.image_stats(48, 40, a[0], rs.astype(np.float64), 2, outlier=50.0, drop_k=0)
+    viK, _, _ = orc.image_stats(48, 40, a[0], rs.astype(np.float64), 2, outlier=50.0, drop_k=K)
+    assert a[1]["VI"] == pytest.approx(vi0, rel=1e-4)
+    assert b[1]["VI"] == pytest.approx(viK, rel=1e-4)
+    assert b[1]["CI"] == a[1]["CI"]
+    with pytest.raises(mars.MarsError):
+        cache.render_iteration(None, iteration=3, update_estimate=True, vi_drop_brightest=17)
+
+
+def test_inverse_variance_combination_parity(mars, orc):
+    """Progressive combination (Sec. 5.1): after iterations rendered with
+    combine = 2 (restart) and then 1, the library's combined image and weight
+    sum equal the oracle's combination of the per-iteration images with weights
+    1 / V_I; an iteration with combine = 0 stays out; replayed graphs on a
+    capturable stream carry the flag."""
+    import torch
+    cfg = W.config_guided(40, 32)
+    stream = torch.cuda.Stream()
+    scene = mars.Scene(cfg.scene, stream=stream)
+    cache = mars.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, stream=stream)
+    img = torch.zeros(cache.n_pixels * 3, dtype=torch.float32, device="cuda")
+    imgs, vis = [], []
+    for it in range(7):
+        comb = 2 if it == 1 else (0 if it in (0, 4) else 1)
+        st = cache.render_iteration(img, seed=3, iteration=it, mode=0 if it < 2 else 1, update_estimate=True,
+                                    combine=comb, vi_drop_brightest=10 if it >= 3 else 0, stream=stream)
+        cache.update_counts(stream=stream)
+        stream.synchronize()
+        if comb:
+            imgs.append(img.cpu().numpy().reshape(-1, 3).astype(np.float64))
+            vis.append(st["VI"])
+    g_img, g_w = cache.combined_image(stream=stream)
+    o_img, o_w = orc.combine(imgs, vis)
+    assert g_w == pytest.approx(o_w, rel=1e-6)
+    np.testing.assert_allclose(g_img.reshape(-1, 3), o_img, rtol=1e-5, atol=1e-7)
+    with pytest.raises(mars.MarsError):
+        cache.render_iteration(img, iteration=9, update_estimate=False, combine=1, stream=stream)

@@ -602,3 +602,60 @@ def test_octree_without_splits_is_the_grid_and_refined_tree_is_unbiased(orc):
     m1, s1 = _mean_and_sem(ref)
     m2, s2 = _mean_and_sem(mars)
     assert abs(m1 - m2) < 3.5 * math.sqrt(s1 ** 2 + s2 ** 2)
+
+
+def _flat_mean_case(W, H, n_prev, m, bright):
+    """An image equal to the colour m everywhere except the pixels of `bright`
+    (index -> colour), with a running sum chosen so that the new running mean is
+    m at every pixel: the pixel estimate is then m exactly (a box filter of a
+    constant, above the 1e-3 floor), and a pixel's V_I term is
+    sum_ch ((I_ch - m_ch) / m_ch)^2."""
+    n = W * H
+    img = np.tile(np.asarray(m, np.float64), (n, 1))
+    for p, c in bright.items():
+        img[p] = c
+    run_sum = (n_prev + 1) * np.tile(np.asarray(m, np.float64), (n, 1)) - img
+    return img, run_sum
+
+
+def test_brightest_pixel_rejection_closed_form(orc):
+    """Sec. 5.1 "Implementation": the K brightest pixels of a pass leave its V_I.
+    On a flat image with K bright outliers V_I is 0 when all K are dropped; with
+    K - 1 dropped exactly the dimmest outlier remains, unclamped; brightness is
+    luminance, so a strongly blue pixel of low luminance stays in the mean while a
+    brighter green one is dropped; and K = 0 keeps the clamped estimate."""
+    W, H, n_prev = 8, 6, 3
+    n = W * H
+    m = np.array([0.5, 0.3, 0.2])
+    alphas = {5: 100.0, 17: 60.0, 30: 80.0}   # I = alpha * m
+    img, rs = _flat_mean_case(W, H, n_prev, m, {p: a * m for p, a in alphas.items()})
+    vi3, _, est = orc.image_stats(W, H, img, rs, n_prev, outlier=50.0, drop_k=3)
+    assert np.allclose(est, np.tile(m, (n, 1)), rtol=1e-12)
+    assert vi3 == pytest.approx(0.0, abs=1e-24)
+    vi2, _, _ = orc.image_stats(W, H, img, rs, n_prev, outlier=50.0, drop_k=2)
+    assert vi2 == pytest.approx(3 * (60.0 - 1) ** 2 / (3 * (n - 2)), rel=1e-12)
+    vi1, _, _ = orc.image_stats(W, H, img, rs, n_prev, outlier=50.0, drop_k=1)
+    assert vi1 == pytest.approx(3 * ((60.0 - 1) ** 2 + (80.0 - 1) ** 2) / (3 * (n - 1)), rel=1e-12)
+    # K = 0: the clamp at 50 x estimate bounds every outlier term at 3 * 49^2
+    vi0, _, _ = orc.image_stats(W, H, img, rs, n_prev, outlier=50.0, drop_k=0)
+    assert vi0 == pytest.approx(3 * (3 * 49.0 ** 2) / (3 * n), rel=1e-12)
+    # luminance decides: pixel 9 is blue (B = 40 m_B, luminance ~ 0.6), pixel 21
+    # green (G = 5 m_G, luminance ~ 1.3); K = 1 drops the green one
+    img2, rs2 = _flat_mean_case(W, H, n_prev, m, {9: m * np.array([1.0, 1.0, 40.0]),
+                                                  21: m * np.array([1.0, 5.0, 1.0])})
+    v, _, _ = orc.image_stats(W, H, img2, rs2, n_prev, drop_k=1)
+    assert v == pytest.approx(39.0 ** 2 / (3 * (n - 1)), rel=1e-12)
+
+
+def test_inverse_variance_combination_closed_form(orc):
+    """Sec. 5.1: iterations combine with weights 1 / V_I.  Constant images a_i
+    with variances V_i give sum(a_i / V_i) / sum(1 / V_i); equal variances give
+    the plain mean; an iteration with 100x the variance barely counts."""
+    imgs = [np.full((4, 3), a) for a in (1.0, 2.0, 4.0)]
+    out, w = orc.combine(imgs, [0.5, 0.25, 1.0])
+    assert w == pytest.approx(2 + 4 + 1)
+    assert np.allclose(out, (1 / 0.5 + 2 / 0.25 + 4 / 1.0) / 7.0)
+    out, _ = orc.combine(imgs, [0.3, 0.3, 0.3])
+    assert np.allclose(out, np.mean([1.0, 2.0, 4.0]))
+    out, _ = orc.combine([np.full(3, 1.0), np.full(3, 10.0)], [1.0, 100.0])
+    assert np.allclose(out, (1.0 + 0.1) / 1.01)
