@@ -808,32 +808,6 @@ void cache_destroy_impl(mars_cache* c) {
 }
 
 // ------------------------------------------------------------ iteration
-// Grid of every depth wave: the wave sizes of the last single-tile iteration,
-// scaled to this tile's pixels with 50 % headroom, in blocks, between one block
-// per SM and the persistent grid.  Only the speed depends on it: every kernel
-// strides over whatever its wave holds.
-static WaveLaunch wave_grids(const mars_cache* c, int64_t tile_pixels) {
-  WaveLaunch L = c->launch;
-  const int sms = c->scene->num_sms;
-  for (int k = 0; k < WAVE_KERNELS; ++k)
-    for (int d = 0; d < MAXD + 2; ++d) L.wave_grid[k][d] = 0;
-  if (c->last_pixels <= 0) return L;
-  const double scale = (double)tile_pixels / (double)c->last_pixels;
-  auto blocks = [&](int k, double items) {
-    const double est = items * scale * 1.5 + 2048.0;
-    int b = (int)std::ceil(est / L.threads[k]);
-    return std::max(std::min(b, L.grid[k]), std::min(sms, L.grid[k]));
-  };
-  for (int d = 1; d <= c->max_depth; ++d) {
-    const double n = d == 1 ? (double)c->last_pixels : (double)c->last_count[d];
-    L.wave_grid[WK_TRACE][d] = blocks(WK_TRACE, n);
-    L.wave_grid[WK_SHADE][d] = blocks(WK_SHADE, n);
-    L.wave_grid[WK_REVERSE][d] = blocks(WK_REVERSE, n);
-    L.wave_grid[WK_SHADOW][d] = blocks(WK_SHADOW, (double)c->last_slcount[d]);
-  }
-  return L;
-}
-
 static mars_status poison(mars_cache* c, cudaError_t e, const char* what) {
   c->poisoned = true;
   return set_error(MARS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
@@ -926,15 +900,13 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
     if ((e = cudaMemcpyAsync(c->d_args, c->h_args, sizeof(IterArgs) * tiles.size(), cudaMemcpyHostToDevice, st)) !=
         cudaSuccess)
       return poison(c, e, "argument copy");
-    std::vector<WaveLaunch> Ls;
-    for (size_t t = 0; t < tiles.size(); ++t) Ls.push_back(wave_grids(c, tiles[t].second - tiles[t].first));
     const bool profile = p->profile != 0;
     // every launch of the attempt, in stream order on q
     auto enqueue = [&](cudaStream_t q) -> cudaError_t {
       cudaError_t r;
       for (size_t t = 0; t < tiles.size(); ++t) {
         cudaEvent_t* ev = profile ? c->events.data() + t * per_tile : nullptr;
-        if ((r = launch_tile(s->ds, c->dc, c->arena, c->d_args + t, Ls[t], q, c->side, c->sync_events.data(), ev)) !=
+        if ((r = launch_tile(s->ds, c->dc, c->arena, c->d_args + t, c->launch, q, c->side, c->sync_events.data(), ev)) !=
             cudaSuccess)
           return r;
       }
@@ -964,14 +936,8 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
       key.dev_out = dev_out;
       key.drop = p->vi_drop_brightest > 0;
       key.combine = p->combine != 0;
-      key.L = Ls[0];
-      if (!c->graph_exec || !c->graph_key.covers(key)) {
-        // recorded with twice the grids asked for (at most the persistent
-        // grid), so that the graph outlives the waves' drift for a while
-        for (int k = 0; k < WAVE_KERNELS; ++k)
-          for (int d = 0; d < MAXD + 2; ++d)
-            key.L.wave_grid[k][d] = std::min(2 * key.L.wave_grid[k][d], key.L.grid[k]);
-        Ls[0] = key.L;
+      key.L = c->launch;
+      if (!c->graph_exec || !(c->graph_key == key)) {
         if (c->graph_exec) {
           cudaGraphExecDestroy(c->graph_exec);
           c->graph_exec = nullptr;
@@ -1035,6 +1001,19 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
       image_ms += ms;
     }
     demand = std::max<uint64_t>(demand, c->h_ctr->demand);
+    // Each overflowed tile is split into k pieces.  k comes from the last tile
+    // of the attempt: it had filled `demand` slots when its first dstar waves
+    // were allocated; with the remaining waves taken as large as those, it
+    // needed about demand x D / dstar slots (at least a halving, at most 16).
+    int k = 2;
+    {
+      const DevCounters& hc = *c->h_ctr;
+      int dstar = 1;
+      for (int d = 1; d <= D; ++d)
+        if (hc.count[d] > 0) dstar = d;
+      const double est = (double)hc.demand * (double)D / (double)dstar;
+      k = std::min(16, std::max(2, (int)std::ceil(1.3 * est / (double)c->arena.cap)));
+    }
     std::vector<std::pair<int64_t, int64_t>> again;
     for (size_t t = 0; t < tiles.size(); ++t) {
       if (!c->h_tile_status[t]) continue;
@@ -1042,9 +1021,8 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
       if (b - a <= 1)
         return set_error(MARS_ERR_OOM, "one pixel's path tree needs more than the arena's %llu rays",
                          (unsigned long long)c->arena.cap);
-      const int64_t m = (a + b) / 2;
-      again.emplace_back(a, m);
-      again.emplace_back(m, b);
+      const int64_t parts = std::min<int64_t>(k, b - a);
+      for (int64_t j = 0; j < parts; ++j) again.emplace_back(a + (b - a) * j / parts, a + (b - a) * (j + 1) / parts);
     }
     if (again.empty()) break;
     if ((int)again.size() > c->max_tiles) return set_error(MARS_ERR_OOM, "too many tiles after arena overflow");
@@ -1054,14 +1032,22 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
     if ((e = cudaMemsetAsync(&c->d_ctr->any_overflow, 0, sizeof(unsigned int), st)) != cudaSuccess)
       return poison(c, e, "overflow reset");
   }
-  // plan the next iteration's tiles: every failure split one tile in two; when
-  // the largest tile used less than half the arena, try fewer tiles again
+  // plan the next iteration's tiles from this one's committed arena use: a
+  // tile holds every depth wave of its pixels, about entries x (tile pixels /
+  // pixels) ray slots (and shadow slots likewise); 30 % headroom for the uneven
+  // spread of path trees over the image, times the growth over the previous
+  // iteration (up to 2x: the learned counts ramp up over the first MARS
+  // iterations); a tile that still overflows is split and re-rendered as above
   {
-    const int final_tiles = ntiles + (int)(retries / 2);
-    if (retries > 0)
-      c->next_tiles = std::min(c->max_tiles, (final_tiles * 5 + 3) / 4);
-    else if (c->next_tiles > 1 && demand < c->arena.cap / 2)
-      c->next_tiles = std::max(1, c->next_tiles / 2);
+    const DevCounters& h = *c->h_ctr;
+    const double need = std::max((double)h.entries / (double)c->arena.cap,
+                                 (double)h.shadow_entries / (double)c->arena.scap);
+    const double growth = c->last_entries > 0 ? std::min(2.0, std::max(1.0, (double)h.entries /
+                                                                             (double)c->last_entries))
+                                              : 1.0;
+    const int t = (int)std::ceil(need * 1.3 * growth);
+    c->next_tiles = std::min(c->max_tiles, std::max(1, t));
+    c->last_entries = h.entries;
   }
   if (p->update_estimate) {
     c->n_iterations += 1;
@@ -1102,13 +1088,6 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
   }
   c->last_VI = c->h_ctr->VI;
   c->last_CI = c->h_ctr->CI;
-  if (used == 1 && retries == 0) {
-    for (int d = 0; d < MAXD + 2; ++d) {
-      c->last_count[d] = c->h_ctr->count[d];
-      c->last_slcount[d] = c->h_ctr->slcount[d];
-    }
-    c->last_pixels = npx;
-  }
   return MARS_OK;
 }
 

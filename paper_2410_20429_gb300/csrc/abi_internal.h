@@ -5,6 +5,7 @@
 
 #include <condition_variable>
 #include <cstdint>
+#include <cstring>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -43,30 +44,15 @@ struct SceneDescCopy {
 mars_status set_error(mars_status s, const char* fmt, ...);
 
 // What a recorded iteration graph depends on besides the per-tile arguments,
-// which the kernels read from device memory.  The graph is replayed while the
-// flags, the output buffer and the launch shape are unchanged and every
-// per-wave grid it holds is at least the one the next iteration asks for and
-// at most eight times it: every wave kernel strides over its wave, so any grid
-// gives the same results and these bounds only keep it fast.  (The wave sizes
-// drift from one iteration to the next; an exact match would record a new
-// graph almost every time.)
+// which the kernels read from device memory: it is replayed while these are
+// unchanged and recorded again otherwise.
 struct GraphKey {
   bool update_estimate = false, drop = false, combine = false;
   float* dev_out = nullptr;
   WaveLaunch L{};
-  bool covers(const GraphKey& want) const {
-    if (update_estimate != want.update_estimate || dev_out != want.dev_out || drop != want.drop ||
-        combine != want.combine)
-      return false;
-    for (int k = 0; k < WAVE_KERNELS; ++k) {
-      if (L.threads[k] != want.L.threads[k] || L.variant[k] != want.L.variant[k] || L.grid[k] != want.L.grid[k])
-        return false;
-      for (int d = 0; d < MAXD + 2; ++d) {
-        const int have = L.wave_grid[k][d], need = want.L.wave_grid[k][d];
-        if (have < need || have > 8 * need) return false;
-      }
-    }
-    return true;
+  bool operator==(const GraphKey& o) const {
+    return update_estimate == o.update_estimate && drop == o.drop && combine == o.combine && dev_out == o.dev_out &&
+           std::memcmp(&L, &o.L, sizeof(WaveLaunch)) == 0;
   }
 };
 
@@ -140,12 +126,7 @@ struct mars_cache {
   std::vector<cudaEvent_t> sync_events;  // D + 1 cross-stream events (no timing)
   mars::WaveLaunch launch{};        // launch shape of the per-wave kernels
   int blocks_per_sm[mars::WAVE_KERNELS] = {0, 0, 0, 0};  // 0: occupancy maximum
-  // wave sizes of the last single-tile iteration (rays per depth wave, NEE
-  // shadow rays to trace per wave) and its pixel count: the next iteration sizes the
-  // grid of each small wave from them
-  uint64_t last_count[mars::MAXD + 2] = {};
-  uint64_t last_slcount[mars::MAXD + 2] = {};
-  int64_t last_pixels = 0;
+  uint64_t last_entries = 0;  // arena slots the last iteration used (tile planning)
   // per-tile iteration arguments: written to the pinned slots, copied to the
   // device slots before the launches, read there by every kernel
   mars::IterArgs* h_args = nullptr;

@@ -177,14 +177,16 @@ struct IterArgs {
 };
 
 // Launch shape of the four per-wave kernels: threads per block (a multiple of
-// 32, at most 256) and grid size in blocks.  Every kernel strides over its
-// wave in chunks of 32 slots, so results do not depend on the shape.
+// 32, at most 256) and grid size in blocks, the same for every depth wave (a
+// persistent grid; sizing each wave's grid from the previous iteration's wave
+// sizes measured no faster for small waves and starved the growing waves of
+// the first MARS iterations).  Every kernel strides over its wave in chunks
+// of 32 slots, so results do not depend on the shape.
 enum { WK_TRACE = 0, WK_SHADE = 1, WK_SHADOW = 2, WK_REVERSE = 3, WAVE_KERNELS = 4 };
 struct WaveLaunch {
   int threads[WAVE_KERNELS];
   int variant[WAVE_KERNELS];               // register-cap variant (wave_variant_registers)
   int grid[WAVE_KERNELS];                  // persistent grid: SMs x resident blocks
-  int wave_grid[WAVE_KERNELS][MAXD + 2];   // grid of wave d (<= grid; 0 = grid)
 };
 
 // launch wrappers (render.cu)

@@ -912,7 +912,7 @@ cudaError_t launch_tile(const DevScene& s, const DevCache& c, const Arena& a, co
   k_tile_init<<<1, 32, 0, st>>>(c.ctr, it);
   const int D = c.max_depth;
   const int tT = L.threads[WK_TRACE], tS = L.threads[WK_SHADE], tH = L.threads[WK_SHADOW], tR = L.threads[WK_REVERSE];
-  auto G = [&](int k, int d) { return L.wave_grid[k][d] > 0 ? L.wave_grid[k][d] : L.grid[k]; };
+  auto G = [&](int k, int) { return L.grid[k]; };
   const size_t smS = shade_smem(tS);
   const bool nee = (c.techniques & MARS_TECH_NEE) != 0;
   // The NEE shadow rays of wave d run on the side stream, overlapped with the
