@@ -407,6 +407,7 @@ def run_mars(args):
 
     if rank == 0 and not args.no_large:
         line["large_scene"] = large_scene(args, M, stream)
+        line["largest_scene"] = largest_scene(args, M, stream)
     if rank == 0 and args.serve_requests > 0:
         line["serving"] = serving(args)
     if rank == 0 and not args.no_precision:
@@ -494,6 +495,74 @@ def large_scene(args, M, stream):
         out["precision"]["entries"] = rep["cells_compared"]
         out["precision"]["images_equal"] = rep["images_equal"]
     del cache, scene
+    return out
+
+
+def largest_scene(args, M, stream):
+    """The largest single-GPU workload (the geometry of the large bidirectional
+    configuration, rendered unidirectionally): 512 x 512 quads = 524k triangles,
+    4096 GGX spheres, 8 area lights, 2048 x 2048, D = 12, BSDF + NEE, adaptive
+    octree <= 64k leaves, a 2 x pixels x D arena; 3 warm-up and 2 timed MARS iterations, then
+    the float32 versus float64 statistics comparison at this size."""
+    import torch
+    cfg = W.config_large(2048, 2048)
+    cfg.scene.bvh = BVH_KINDS[args.bvh]
+    t0 = time.perf_counter()
+    scene = M.Scene(cfg.scene, stream=stream)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    npx = cfg.scene.n_pixels
+    cap = 2 * npx * cfg.max_depth
+    kw = dict(octree=True, max_leaves=65536, split_samples=4096.0, arena_capacity=cap)
+    cache = M.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, stream=stream, **kw)
+    img = torch.zeros(npx * 3, dtype=torch.float32, device="cuda")
+    it = 0
+    for k in range(3):
+        cache.render_iteration(img, seed=91, iteration=it, mode=M.MARS_MODE_WARMUP, update_estimate=True,
+                               stream=stream)
+        cache.update_counts(stream=stream)
+        it += 1
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sts = []
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for k in range(2):
+        sts.append(cache.render_iteration(img, seed=91, iteration=it, mode=M.MARS_MODE_MARS, update_estimate=True,
+                                          profile=True, stream=stream))
+        cache.update_counts(stream=stream)
+        it += 1
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 2
+    verts = sum(s["vertices"] for s in sts) / 2
+    tw = [sum(s["trace_work"][0][q] for s in sts) for q in range(4)]
+    n = max(sum(s["wave_entries"] for s in sts), 1)
+    out = {"workload": cfg.name, "primitives": int(len(cfg.scene.tris) + len(cfg.scene.spheres) + len(cfg.scene.quads)),
+           "bvh_build_s": round(build_s, 3), "ms_per_step": round(ms, 3),
+           "mvertices_s": round(verts / (ms * 1e-3) / 1e6, 1), "vertices_per_step": int(verts),
+           "tiles": [s["tiles"] for s in sts], "arena_slots": cap,
+           "kernel_ms_per_step": {k: round(sum(s[k + "_ms"] for s in sts) / 2, 4)
+                                  for k in ("trace", "shade", "shadow", "reverse", "image")},
+           "closest_hit_per_ray": {"nodes": round(tw[0] / n, 2), "prim_tests": round(sum(tw[1:]) / n, 2)},
+           "mean_beta": [round(sum(s["mean_beta"][t] for s in sts) / 2, 4) for t in range(3)],
+           "octree_leaves": int(cache.info()["oct_n_leaves"]),
+           "device_gb": round(cache.info()["device_bytes"] / 1e9, 2)}
+    if not args.no_precision:
+        from paper_2410_20429_gb300 import precision
+        g = cache.get_state(stream=stream)
+        del cache
+        torch.cuda.synchronize()
+        rep = precision.compare(cfg.scene, cfg.grid_n, cfg.techniques, cfg.max_depth, g["q_rr"], g["q_s"],
+                                g["valid"], g["pixel_estimate"], g["run_sum"], g["n_iterations"], iteration=it,
+                                seed=91, stream=stream, cache_kw=kw,
+                                tree=(g["oct_nodes"], g["oct_leaf_level"]), guide_cdf=g.get("guide_cdf"))
+        out["precision"] = {k: [float("%.3g" % rep[k]["max"]), float("%.3g" % rep[k]["median"])]
+                            for k in precision.STATISTICS}
+        out["precision"]["entries"] = rep["cells_compared"]
+        out["precision"]["images_equal"] = rep["images_equal"]
+    else:
+        del cache
+    del scene
     return out
 
 

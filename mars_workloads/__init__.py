@@ -14,6 +14,7 @@ from .scenes import (  # noqa: F401
     config_box,
     config_guided,
     config_heightfield,
+    config_large,
     heightfield_scene,
     random_count_fields,
     random_guide_cdf,

@@ -235,15 +235,18 @@ def guided_room_scene(seed: int = 0, width: int = 512, height: int = 512,
 
 
 def heightfield_scene(seed: int = 0, n: int = 256, width: int = 1024, height: int = 1024,
-                      n_spheres: int = 200, size: float = 8.0) -> Scene:
+                      n_spheres: int = 200, size: float = 8.0, n_lights: int = 0,
+                      ggx_fraction: float = 0.6) -> Scene:
     """A seeded heightfield of n x n quads (2 n^2 triangles, heights from three
     octaves of bilinearly interpolated value noise, Lambertian albedo 0.6) over a
     size x size square, with ``n_spheres`` spheres resting above it (radius
-    U[0.05, 0.3], 60 % GGX with roughness U[0.05, 0.5], 40 % Lambertian), and one
-    small 0.2 x 0.2 emitter of radiance 200 facing down, hidden low between two
-    large occluding spheres so that little of the terrain sees it directly -- the
-    geometry of the bidirectional workloads, here lit for the unidirectional
-    tracer."""
+    U[0.05, 0.3], a fraction ``ggx_fraction`` GGX with roughness U[0.05, 0.5],
+    the rest Lambertian), and one small 0.2 x 0.2 emitter of radiance 200 facing
+    down, hidden low between two large occluding spheres so that little of the
+    terrain sees it directly -- the geometry of the bidirectional workloads, here
+    lit for the unidirectional tracer.  With ``n_lights`` > 0 the hidden emitter
+    is replaced by that many 0.3 x 0.3 emitters facing down at heights
+    U[2.5, 3.5] over the terrain, grey radiance log-uniform in [0.5, 500]."""
     rng = np.random.Generator(np.random.Philox(key=seed + 7))
 
     def noise(cells):
@@ -269,22 +272,32 @@ def heightfield_scene(seed: int = 0, n: int = 256, width: int = 1024, height: in
         x, z = rng.uniform(0.2, size - 0.2, size=2)
         r = rng.uniform(0.05, 0.3)
         col = rng.uniform(0.2, 0.9, size=3)
-        if rng.uniform() < 0.6:
+        if rng.uniform() < ggx_fraction:
             mats.append(_ggx(col[0], col[1], col[2], rng.uniform(0.05, 0.5)))
         else:
             mats.append(_lambert(col[0], col[1], col[2]))
         spheres.append([x, 1.2 + r + rng.uniform(0.0, 0.4), z, r])
         sphere_mat.append(len(mats) - 1)
-    # the hidden emitter: low above the middle, between two big spheres
-    mats.append(_lambert(0.0, 0.0, 0.0, (200.0, 200.0, 200.0)))
-    lx, lz, ly = 0.5 * size - 0.1, 0.5 * size - 0.1, 1.45
-    quads = [[lx, ly, lz, 0.2, 0, 0, 0, 0, 0.2]]                       # e1 x e2 = -y: faces down
-    quad_mat = [len(mats) - 1]
-    occ = len(mats)
-    mats.append(_lambert(0.5, 0.5, 0.5))
-    for dx in (-0.45, 0.65):
-        spheres.append([0.5 * size + dx, 1.45, 0.5 * size, 0.4])
-        sphere_mat.append(occ)
+    if n_lights > 0:
+        quads, quad_mat = [], []
+        for _ in range(n_lights):
+            lx, lz = rng.uniform(0.5, size - 0.8, size=2)
+            ly = rng.uniform(2.5, 3.5)
+            le = math.exp(rng.uniform(math.log(0.5), math.log(500.0)))
+            mats.append(_lambert(0.0, 0.0, 0.0, (le, le, le)))
+            quads.append([lx, ly, lz, 0.3, 0, 0, 0, 0, 0.3])            # e1 x e2 = -y: faces down
+            quad_mat.append(len(mats) - 1)
+    else:
+        # the hidden emitter: low above the middle, between two big spheres
+        mats.append(_lambert(0.0, 0.0, 0.0, (200.0, 200.0, 200.0)))
+        lx, lz, ly = 0.5 * size - 0.1, 0.5 * size - 0.1, 1.45
+        quads = [[lx, ly, lz, 0.2, 0, 0, 0, 0, 0.2]]                   # e1 x e2 = -y: faces down
+        quad_mat = [len(mats) - 1]
+        occ = len(mats)
+        mats.append(_lambert(0.5, 0.5, 0.5))
+        for dx in (-0.45, 0.65):
+            spheres.append([0.5 * size + dx, 1.45, 0.5 * size, 0.4])
+            sphere_mat.append(occ)
     cam = [0.5 * size, 4.0, -2.5, 0.5 * size, 0.6, 0.5 * size, 0.0, 1.0, 0.0, 50.0]
     sc = _mk(quads, quad_mat, spheres, sphere_mat, mats, cam, width, height, "heightfield")
     sc.tris = _f32(tris)
@@ -299,6 +312,16 @@ def config_heightfield(width: int = 1024, height: int = 1024, seed: int = 0) -> 
     return WorkloadConfig(heightfield_scene(seed, 256, width, height), max_depth=10, grid_n=32,
                           techniques=TECH_BSDF | TECH_NEE | TECH_GUIDED, iterations=16, warmup=3,
                           name=f"heightfield_256q_{width}x{height}_D10_bsdf+nee+guided_grid32")
+
+
+def config_large(width: int = 2048, height: int = 2048, seed: int = 0) -> WorkloadConfig:
+    """Heightfield 512 x 512 quads (524k triangles) + 4096 GGX spheres, 8 area
+    lights with radiance log-U[0.5, 500], 2048^2, D = 12, BSDF + NEE (the
+    bidirectional application has no guiding), 32^3 grid: the geometry of the
+    large bidirectional workload, rendered unidirectionally."""
+    return WorkloadConfig(heightfield_scene(seed, 512, width, height, n_spheres=4096, n_lights=8, ggx_fraction=1.0),
+                          max_depth=12, grid_n=32, techniques=TECH_BSDF | TECH_NEE, iterations=64,
+                          warmup=3, name=f"heightfield_512q_{width}x{height}_D12_bsdf+nee_grid32")
 
 
 def config_box(width: int = 64, height: int = 64) -> WorkloadConfig:
