@@ -241,7 +241,7 @@ def run_mars(args):
     with torch.cuda.stream(stream):
         scene = M.Scene(sc, stream=stream)
         cache = M.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, arena_capacity=args.arena_capacity,
-                        graphs=not args.no_graphs, stream=stream)
+                        graphs=not args.no_graphs, lanes=args.lanes, stream=stream)
     if args.launch:
         parts = args.launch.split(":")
         regs = [int(x) for x in parts[2].split(",")] if len(parts) > 2 else [0, 0, 0, 0]
@@ -381,7 +381,7 @@ def run_mars(args):
         "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": cfg.name, "pixels": npx, "max_depth": cfg.max_depth, "grid": cfg.grid_n,
-                   "techniques": "bsdf+nee+guided", "statistics_dtype": "f64", "bvh": args.bvh,
+                   "techniques": "bsdf+nee+guided", "statistics_dtype": "f64", "bvh": args.bvh, "lanes": args.lanes,
                    "l2": "working set > L2: queue arena %.0f MB per step" % (
                        entries / args.steps * SLOT_BYTES / 1e6),
                    "parallelism": f"replicas x{world}"},
@@ -818,6 +818,7 @@ def main():
     ap.add_argument("--bvh", default="sah", choices=sorted(BVH_KINDS),
                     help="hierarchy of the closest-hit and shadow queries (results do not depend on it)")
     ap.add_argument("--no-graphs", action="store_true", help="launch every kernel directly (no CUDA graph replay)")
+    ap.add_argument("--lanes", type=int, default=2, choices=[1, 2], help="concurrent pixel-tile lanes")
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the heightfield (131k triangles) section")
     ap.add_argument("--serve-requests", type=int, default=256, help="serving-stream requests (0 = skip)")

@@ -113,11 +113,16 @@ typedef struct {
  *   down to 1024 cells per axis and while the leaves number at most
  *   max_leaves; children inherit the counts and the guide distribution.
  *   MARS_CACHE_NO_GRAPHS: launch every kernel of an iteration directly.  By
- *   default an iteration that fits the arena in one pixel tile, is not
- *   profiled and runs on a stream other than the legacy default stream (which
- *   cannot be captured) is recorded once as a CUDA graph and replayed; the
- *   graph is recorded again when the output buffer, update_estimate, the
- *   launch shape or the waves' sizes outgrow it.  Results are the same.
+ *   default an iteration whose pixel tiles fit the arena at the first attempt,
+ *   is not profiled and runs on a stream other than the legacy default stream
+ *   (which cannot be captured) is recorded once as a CUDA graph and replayed;
+ *   the graph is recorded again when the output buffer, update_estimate, the
+ *   image-statistics options, the tile count or the launch shape change.
+ *   MARS_CACHE_ONE_LANE: one tile lane.  By default the pixels are split into
+ *   tiles dealt to two lanes, each with half the arena, its own streams and
+ *   counters, rendered concurrently (their wave kernels fill each other's idle
+ *   SMs).  Results are the same either way (statistics up to the order of
+ *   float64 atomics).
  * max_leaves, split_samples: octree only (0: 65536 leaves, 4096 samples).
  * arena_capacity: rays held by the per-iteration queue arena summed over all
  *   depths (0 = 3 x pixels x max_depth, at least 2^20).  An iteration whose path
@@ -125,6 +130,7 @@ typedef struct {
 #define MARS_CACHE_FP32_STATISTICS 1
 #define MARS_CACHE_OCTREE 2
 #define MARS_CACHE_NO_GRAPHS 4
+#define MARS_CACHE_ONE_LANE 8
 #define MARS_OCTREE_MAX_LEVEL 10
 typedef struct {
   int32_t grid_n;

@@ -18,6 +18,7 @@ MARS_JOB_QUEUED, MARS_JOB_RUNNING, MARS_JOB_DONE, MARS_JOB_FAILED = range(4)
 MARS_CACHE_FP32_STATISTICS = 1
 MARS_CACHE_OCTREE = 2
 MARS_CACHE_NO_GRAPHS = 4
+MARS_CACHE_ONE_LANE = 8
 MARS_BVH_SAH = 0
 MARS_MAX_DROP_BRIGHTEST = 16
 MARS_BVH_LBVH = 1

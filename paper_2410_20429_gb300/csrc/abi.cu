@@ -530,7 +530,7 @@ mars_status cache_create_impl(const mars_scene* s, const mars_cache_desc* d, cud
     return set_error(MARS_ERR_INVALID_ARG, "max_depth %d out of [1, %d]", d->max_depth, MAXD);
   if ((d->techniques & MARS_TECH_NEE) && s->n_lights == 0)
     return set_error(MARS_ERR_INVALID_ARG, "NEE requested but the scene has no emitting quad");
-  if (d->flags & ~(MARS_CACHE_FP32_STATISTICS | MARS_CACHE_OCTREE | MARS_CACHE_NO_GRAPHS))
+  if (d->flags & ~(MARS_CACHE_FP32_STATISTICS | MARS_CACHE_OCTREE | MARS_CACHE_NO_GRAPHS | MARS_CACHE_ONE_LANE))
     return set_error(MARS_ERR_INVALID_ARG, "unknown cache flags %d", d->flags);
   const bool fp32 = (d->flags & MARS_CACHE_FP32_STATISTICS) != 0;
   const bool octree = (d->flags & MARS_CACHE_OCTREE) != 0;
@@ -569,6 +569,9 @@ mars_status cache_create_impl(const mars_scene* s, const mars_cache_desc* d, cud
   c->arena.cap = cap;
   c->arena.scap = cap;  // NEE shadow rays: as many slots as rays
   c->max_tiles = 4096;
+  // two tile lanes (each with half the arena) unless asked for one or the
+  // image has a single pixel
+  c->lanes = ((d->flags & MARS_CACHE_ONE_LANE) || pixels < 2 || cap < 128) ? 1 : 2;
   auto cleanup = [&](cudaError_t e, const char* what) {
     const mars_status ms = e == cudaErrorMemoryAllocation ? MARS_ERR_OOM : MARS_ERR_CUDA;
     set_error(ms, "%s: %s", what, cudaGetErrorString(e));
@@ -603,7 +606,8 @@ mars_status cache_create_impl(const mars_scene* s, const mars_cache_desc* d, cud
   if ((e = dev_alloc((void**)&c->d_est, sizeof(float4) * pixels, st)) != cudaSuccess) return cleanup(e, "image alloc");
   if ((e = dev_alloc((void**)&c->d_run, sizeof(float4) * pixels, st)) != cudaSuccess) return cleanup(e, "image alloc");
   if ((e = dev_alloc((void**)&c->d_img, sizeof(float4) * pixels, st)) != cudaSuccess) return cleanup(e, "image alloc");
-  if ((e = dev_alloc((void**)&c->d_ctr, sizeof(DevCounters), st)) != cudaSuccess) return cleanup(e, "counter alloc");
+  if ((e = dev_alloc((void**)&c->d_ctr, sizeof(DevCounters) * mars_cache::kMaxLanes, st)) != cudaSuccess)
+    return cleanup(e, "counter alloc");
   if ((e = dev_alloc((void**)&c->d_tile_status, sizeof(unsigned int) * c->max_tiles, st)) != cudaSuccess)
     return cleanup(e, "counter alloc");
   c->h_ctr = (DevCounters*)pinned_acquire(sizeof(DevCounters));
@@ -629,7 +633,7 @@ mars_status cache_create_impl(const mars_scene* s, const mars_cache_desc* d, cud
   cudaMemsetAsync(c->d_guide_dirty, 0, (size_t)gcells, st);
   cudaMemsetAsync(c->d_run, 0, sizeof(float4) * pixels, st);
   cudaMemsetAsync(c->d_img, 0, sizeof(float4) * pixels, st);
-  cudaMemsetAsync(c->d_ctr, 0, sizeof(DevCounters), st);
+  cudaMemsetAsync(c->d_ctr, 0, sizeof(DevCounters) * mars_cache::kMaxLanes, st);
   cudaMemsetAsync(c->d_tile_status, 0, sizeof(unsigned int) * c->max_tiles, st);
   {
     std::vector<float> cdf((size_t)GUIDE_BINS * gcells);
@@ -729,6 +733,20 @@ mars_status cache_create_impl(const mars_scene* s, const mars_cache_desc* d, cud
     if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return cleanup(e, "event");
     c->sync_events.push_back(ev);
   }
+  if (c->lanes > 1) {
+    // the second lane's rendering and shadow streams, its D + 1 fork / join
+    // events and the two that fork it from and join it to the caller's stream
+    if ((e = cudaStreamCreateWithFlags(&c->lane_st, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&c->lane_side, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming)) != cudaSuccess)
+      return cleanup(e, "lane streams");
+    for (int k = 0; k <= d->max_depth; ++k) {
+      cudaEvent_t ev;
+      if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return cleanup(e, "event");
+      c->lane_sync.push_back(ev);
+    }
+  }
   {
     const int threads[WAVE_KERNELS] = {128, 128, 128, 128};
     const int bps[WAVE_KERNELS] = {0, 0, 0, 0};
@@ -800,14 +818,48 @@ void cache_destroy_impl(mars_cache* c) {
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   for (cudaEvent_t ev : c->events) cudaEventDestroy(ev);
   for (cudaEvent_t ev : c->sync_events) cudaEventDestroy(ev);
-  if (c->side) {
-    cudaStreamSynchronize(c->side);
-    cudaStreamDestroy(c->side);
-  }
+  for (cudaEvent_t ev : c->lane_sync) cudaEventDestroy(ev);
+  if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+  if (c->join_ev) cudaEventDestroy(c->join_ev);
+  for (cudaStream_t q : {c->side, c->lane_st, c->lane_side})
+    if (q) {
+      cudaStreamSynchronize(q);
+      cudaStreamDestroy(q);
+    }
   delete c;
 }
 
 // ------------------------------------------------------------ iteration
+// images below this size render in one lane (two half tiles measured 2 %
+// slower at 128 x 128 and 1.5 % at 256 x 256, 5 % faster at 512 x 512)
+constexpr int64_t kLaneMinPixels = 1 << 17;
+
+// lane l's view of the cache: the same cache fields, its own counters
+static DevCache lane_cache(const mars_cache* c, int l) {
+  DevCache d = c->dc;
+  d.ctr = c->d_ctr + l;
+  return d;
+}
+
+// lane l's share of the arena when nl lanes are in use: the l-th of nl equal
+// slices of every slot array
+static Arena lane_arena(const mars_cache* c, int l, int nl) {
+  Arena a = c->arena;
+  if (nl <= 1) return a;
+  const uint64_t rc = c->arena.cap / (uint64_t)nl, sc = c->arena.scap / (uint64_t)nl;
+  const uint64_t r0 = rc * (uint64_t)l, s0 = sc * (uint64_t)l;
+  for (auto& p : a.R) p += r0;
+  for (auto& p : a.V) p += r0;
+  a.S += r0;
+  a.M += r0;
+  a.H += r0;
+  for (auto& p : a.SH) p += s0;
+  a.SL += s0;
+  a.cap = rc;
+  a.scap = sc;
+  return a;
+}
+
 static mars_status poison(mars_cache* c, cudaError_t e, const char* what) {
   c->poisoned = true;
   return set_error(MARS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
@@ -855,12 +907,22 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
   it.combine = p->combine;
 
   // reset the iteration counters (rays, vertices, beta sums, image sums)
-  cudaError_t e = cudaMemsetAsync(c->d_ctr, 0, sizeof(DevCounters), st);
+  cudaError_t e = cudaMemsetAsync(c->d_ctr, 0, sizeof(DevCounters) * mars_cache::kMaxLanes, st);
   if (e != cudaSuccess) return poison(c, e, "counter reset");
 
   const int64_t npx = c->pixels;
   int ntiles = c->next_tiles > 0 ? c->next_tiles : 1;
   if (ntiles > c->max_tiles) ntiles = c->max_tiles;
+  // Two lanes when each half of the image is expected to fit half of the
+  // arena (the last iteration's use with the planner's headroom), the image is
+  // large enough for two tiles to keep the GPU busy, and the iteration is not
+  // profiled (a profiled iteration times each kernel alone on full-size
+  // waves).  Otherwise one lane with the whole arena per tile.
+  int iter_lanes = 1;
+  if (c->lanes > 1 && !p->profile && npx >= kLaneMinPixels && ntiles == 1 && 1.3 * c->last_need <= 1.0) {
+    iter_lanes = 2;
+    ntiles = 2;
+  }
   std::vector<std::pair<int64_t, int64_t>> tiles;
   for (int t = 0; t < ntiles; ++t) {
     const int64_t a = npx * t / ntiles, b = npx * (t + 1) / ntiles;
@@ -901,14 +963,36 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
         cudaSuccess)
       return poison(c, e, "argument copy");
     const bool profile = p->profile != 0;
-    // every launch of the attempt, in stream order on q
+    // Tiles go round-robin to the lanes; lane l has its own counters and its
+    // 1/lanes share of the arena.  Lane 1 runs on its own streams, forked from
+    // and joined to q, except in a profiled iteration, which times every
+    // kernel alone on q.  Its totals are merged into lane 0's before the image
+    // pass reads them.
+    const int nl = std::min<int>(iter_lanes, (int)tiles.size());
+    const bool concurrent = nl > 1 && !profile;
     auto enqueue = [&](cudaStream_t q) -> cudaError_t {
       cudaError_t r;
-      for (size_t t = 0; t < tiles.size(); ++t) {
-        cudaEvent_t* ev = profile ? c->events.data() + t * per_tile : nullptr;
-        if ((r = launch_tile(s->ds, c->dc, c->arena, c->d_args + t, c->launch, q, c->side, c->sync_events.data(), ev)) !=
-            cudaSuccess)
+      if (concurrent) {
+        if ((r = cudaEventRecord(c->fork_ev, q)) != cudaSuccess ||
+            (r = cudaStreamWaitEvent(c->lane_st, c->fork_ev, 0)) != cudaSuccess)
           return r;
+      }
+      for (size_t t = 0; t < tiles.size(); ++t) {
+        const int l = (int)(t % (size_t)nl);
+        cudaEvent_t* ev = profile ? c->events.data() + t * per_tile : nullptr;
+        const bool own = concurrent && l == 1;
+        if ((r = launch_tile(s->ds, lane_cache(c, l), lane_arena(c, l, nl), c->d_args + t, c->launch,
+                             own ? c->lane_st : q, own ? c->lane_side : c->side,
+                             own ? c->lane_sync.data() : c->sync_events.data(), ev)) != cudaSuccess)
+          return r;
+      }
+      if (nl > 1) {
+        if (concurrent) {
+          if ((r = cudaEventRecord(c->join_ev, c->lane_st)) != cudaSuccess ||
+              (r = cudaStreamWaitEvent(q, c->join_ev, 0)) != cudaSuccess)
+            return r;
+        }
+        if ((r = launch_merge_lanes(c->d_ctr, c->d_ctr + 1, q)) != cudaSuccess) return r;
       }
       cudaEvent_t* iev = profile ? c->events.data() + tiles.size() * per_tile : nullptr;
       if (iev) cudaEventRecord(iev[0], q);
@@ -925,13 +1009,14 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
         return r;
       return cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, q);
     };
-    // A single-tile first attempt is replayed from a recorded CUDA graph.  The
-    // legacy default stream cannot be captured, and a profiled iteration times
-    // every launch with stream events: both launch directly, as do the
-    // re-rendered tiles after an arena overflow.
+    // A first attempt with at most one tile per lane is replayed from a
+    // recorded CUDA graph.  The legacy default stream cannot be captured, and a
+    // profiled iteration times every launch with stream events: both launch
+    // directly, as do the re-rendered tiles after an arena overflow.
     const bool capturable = st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread;
-    if (c->use_graphs && capturable && !profile && retries == 0 && tiles.size() == 1) {
+    if (c->use_graphs && capturable && !profile && retries == 0 && (int)tiles.size() <= iter_lanes) {
       GraphKey key;
+      key.tiles = (int)tiles.size();
       key.update_estimate = p->update_estimate != 0;
       key.dev_out = dev_out;
       key.drop = p->vi_drop_brightest > 0;
@@ -964,7 +1049,7 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
     } else if ((e = enqueue(st)) != cudaSuccess) {
       return poison(c, e, "render launch");
     }
-    launches += (uint32_t)(tiles.size() * tile_launches(D, c->techniques));
+    launches += (uint32_t)(tiles.size() * tile_launches(D, c->techniques)) + (nl > 1 ? 1u : 0u);
     wave_launches += (uint32_t)(tiles.size() * D);
     launches += p->update_estimate ? 3 + (p->vi_drop_brightest > 0 ? 2 : 0) + (p->combine ? 1 : 0)
                                    : (dev_out ? 1 : 0);
@@ -1012,7 +1097,8 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
       for (int d = 1; d <= D; ++d)
         if (hc.count[d] > 0) dstar = d;
       const double est = (double)hc.demand * (double)D / (double)dstar;
-      k = std::min(16, std::max(2, (int)std::ceil(1.3 * est / (double)c->arena.cap)));
+      const double tcap = (double)(c->arena.cap / (uint64_t)std::max(1, nl));
+      k = std::min(16, std::max(2, (int)std::ceil(1.3 * est / tcap)));
     }
     std::vector<std::pair<int64_t, int64_t>> again;
     for (size_t t = 0; t < tiles.size(); ++t) {
@@ -1020,7 +1106,7 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
       const int64_t a = tiles[t].first, b = tiles[t].second;
       if (b - a <= 1)
         return set_error(MARS_ERR_OOM, "one pixel's path tree needs more than the arena's %llu rays",
-                         (unsigned long long)c->arena.cap);
+                         (unsigned long long)(c->arena.cap / (uint64_t)std::max(1, nl)));
       const int64_t parts = std::min<int64_t>(k, b - a);
       for (int64_t j = 0; j < parts; ++j) again.emplace_back(a + (b - a) * j / parts, a + (b - a) * (j + 1) / parts);
     }
@@ -1048,6 +1134,7 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
     const int t = (int)std::ceil(need * 1.3 * growth);
     c->next_tiles = std::min(c->max_tiles, std::max(1, t));
     c->last_entries = h.entries;
+    c->last_need = need;
   }
   if (p->update_estimate) {
     c->n_iterations += 1;

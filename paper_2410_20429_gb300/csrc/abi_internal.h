@@ -48,11 +48,12 @@ mars_status set_error(mars_status s, const char* fmt, ...);
 // unchanged and recorded again otherwise.
 struct GraphKey {
   bool update_estimate = false, drop = false, combine = false;
+  int tiles = 0;
   float* dev_out = nullptr;
   WaveLaunch L{};
   bool operator==(const GraphKey& o) const {
-    return update_estimate == o.update_estimate && drop == o.drop && combine == o.combine && dev_out == o.dev_out &&
-           std::memcmp(&L, &o.L, sizeof(WaveLaunch)) == 0;
+    return update_estimate == o.update_estimate && drop == o.drop && combine == o.combine && tiles == o.tiles &&
+           dev_out == o.dev_out && std::memcmp(&L, &o.L, sizeof(WaveLaunch)) == 0;
   }
 };
 
@@ -127,6 +128,17 @@ struct mars_cache {
   mars::WaveLaunch launch{};        // launch shape of the per-wave kernels
   int blocks_per_sm[mars::WAVE_KERNELS] = {0, 0, 0, 0};  // 0: occupancy maximum
   uint64_t last_entries = 0;  // arena slots the last iteration used (tile planning)
+  double last_need = 0.0;     // ... as a fraction of the arena (the larger of rays and shadow rays)
+  // Tile lanes: the pixel tiles of an iteration are dealt round-robin to
+  // `lanes` lanes; lane l renders on its own streams with its own counters
+  // (d_ctr[l]) in its own 1/lanes share of the arena, so the two lanes' wave
+  // kernels fill each other's idle SMs (the small deep waves leave most of the
+  // GPU idle); lane 1's totals are merged into lane 0's before the image pass.
+  static constexpr int kMaxLanes = 2;
+  int lanes = 1;
+  cudaStream_t lane_st = nullptr, lane_side = nullptr;
+  std::vector<cudaEvent_t> lane_sync;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   // per-tile iteration arguments: written to the pinned slots, copied to the
   // device slots before the launches, read there by every kernel
   mars::IterArgs* h_args = nullptr;

@@ -194,6 +194,8 @@ struct WaveLaunch {
 cudaError_t launch_tile(const DevScene& s, const DevCache& c, const Arena& a, const IterArgs* it,
                         const WaveLaunch& L, cudaStream_t st, cudaStream_t side, const cudaEvent_t* sync,
                         cudaEvent_t* ev);
+// adds a second tile lane's iteration totals into the first lane's counters
+cudaError_t launch_merge_lanes(DevCounters* dst, DevCounters* src, cudaStream_t st);
 // resident blocks per SM of each wave kernel at the given block sizes and variants
 cudaError_t wave_occupancy(const int threads[WAVE_KERNELS], const int variant[WAVE_KERNELS],
                            int blocks_per_sm[WAVE_KERNELS]);

@@ -174,6 +174,35 @@ __global__ void k_tile_finish(DevCounters* ctr, unsigned int* tile_status, const
   if (ctr->overflow) ctr->any_overflow = 1;
 }
 
+// Totals of a second tile lane's counters into the first's (added, then
+// cleared in the source, so that a later merge adds only what came after).
+__global__ void k_merge_lanes(DevCounters* dst, DevCounters* src) {
+  if (threadIdx.x != 0) return;
+  dst->shadow_entries += src->shadow_entries;
+  dst->shadow_traced += src->shadow_traced;
+  dst->rays += src->rays;
+  dst->vertices += src->vertices;
+  dst->est_vertices += src->est_vertices;
+  dst->entries += src->entries;
+  src->shadow_entries = src->shadow_traced = src->rays = src->vertices = src->est_vertices = src->entries = 0;
+  for (int d = 0; d < MAXD + 2; ++d) {
+    dst->wave_total[d] += src->wave_total[d];
+    src->wave_total[d] = 0;
+  }
+  for (int k = 0; k < 2; ++k)
+    for (int q = 0; q < 4; ++q) {
+      dst->trace_work[k][q] += src->trace_work[k][q];
+      src->trace_work[k][q] = 0;
+    }
+  for (int t = 0; t < NT; ++t) {
+    dst->sum_beta[t] += src->sum_beta[t];
+    src->sum_beta[t] = 0.0;
+  }
+  if (src->any_overflow) dst->any_overflow = 1;
+  src->any_overflow = 0;
+  if (src->demand > dst->demand) dst->demand = src->demand;
+}
+
 // ------------------------------------------------------------------ trace
 template <int MINB>
 __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_trace(const DevScene s, const DevCache c, const Arena a,
@@ -949,6 +978,11 @@ cudaError_t launch_tile(const DevScene& s, const DevCache& c, const Arena& a, co
     if (ev) cudaEventRecord(ev[4 * D + (D - d + 1)], st);
   }
   k_tile_finish<<<1, 32, 0, st>>>(c.ctr, c.tile_status, it, D);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_merge_lanes(DevCounters* dst, DevCounters* src, cudaStream_t st) {
+  k_merge_lanes<<<1, 32, 0, st>>>(dst, src);
   return cudaGetLastError();
 }
 

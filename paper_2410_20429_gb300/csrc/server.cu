@@ -86,7 +86,12 @@ struct mars_server {
       msg = "stream create failed";
     }
     if (rc == MARS_OK) rc = mars::scene_create_impl(&j->scene.desc, st, &sc);
-    if (rc == MARS_OK) rc = mars::cache_create_impl(sc, &j->cache, st, &ca);
+    // one tile lane per job: concurrent jobs already fill each other's idle
+    // SMs, and a job's first learned iterations, which grow fast, overflow
+    // half an arena more often than a whole one
+    mars_cache_desc cd = j->cache;
+    cd.flags |= MARS_CACHE_ONE_LANE;
+    if (rc == MARS_OK) rc = mars::cache_create_impl(sc, &cd, st, &ca);
     for (int it = 0; rc == MARS_OK && it < j->iterations; ++it) {
       mars_iter_params p{};
       p.seed = j->seed;

@@ -80,11 +80,11 @@ class Cache:
 
     def __init__(self, scene: Scene, grid_n: int, techniques: int, max_depth: int, arena_capacity: int = 0,
                  fp32_statistics: bool = False, octree: bool = False, max_leaves: int = 0,
-                 split_samples: float = 0.0, graphs: bool = True, stream=None):
+                 split_samples: float = 0.0, graphs: bool = True, lanes: int = 2, stream=None):
         self._lib = A.load()
         self.scene = scene
         flags = ((A.MARS_CACHE_FP32_STATISTICS if fp32_statistics else 0) | (A.MARS_CACHE_OCTREE if octree else 0)
-                 | (0 if graphs else A.MARS_CACHE_NO_GRAPHS))
+                 | (0 if graphs else A.MARS_CACHE_NO_GRAPHS) | (A.MARS_CACHE_ONE_LANE if lanes == 1 else 0))
         d = A.mars_cache_desc(int(grid_n), int(techniques), int(max_depth), flags, int(arena_capacity),
                               int(max_leaves), float(split_samples))
         h = ct.c_void_p()

@@ -615,3 +615,46 @@ def test_inverse_variance_combination_parity(mars, orc):
     np.testing.assert_allclose(g_img.reshape(-1, 3), o_img, rtol=1e-5, atol=1e-7)
     with pytest.raises(mars.MarsError):
         cache.render_iteration(img, iteration=9, update_estimate=False, combine=1, stream=stream)
+
+
+@pytest.mark.parametrize("capturable", [False, True])
+def test_two_lanes_equal_one_lane(mars, capturable):
+    """Pixel tiles dealt to two concurrent lanes (own streams, counters and half
+    of the arena each) give the image of one lane bitwise, the same counters and
+    the statistics up to the order of the float64 atomics; also when the half
+    arenas overflow and tiles are re-rendered."""
+    import torch
+    cfg = W.config_guided(384, 384)   # two lanes start at 2^17 pixels
+    q_rr, q_s, valid = W.random_count_fields(cfg.n_cells, seed=981, lo=0.3, hi=1.5)
+    est = W.random_pixel_estimate(cfg.scene.n_pixels, seed=982, lo=0.05, hi=0.5)
+    stream = torch.cuda.Stream() if capturable else None
+    scene = mars.Scene(cfg.scene, stream=stream)
+    for cap in (0, 400000):
+        res = []
+        for lanes in (1, 2):
+            cache = mars.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, arena_capacity=cap, lanes=lanes,
+                               stream=stream)
+            img = torch.zeros(cache.n_pixels * 3, dtype=torch.float32, device="cuda")
+            out = []
+            for it in (1, 2):
+                cache.set_state(q_rr=q_rr, q_s=q_s, valid=valid, pixel_estimate=est, has_estimate=True,
+                                n_iterations=1, stats=np.zeros((cfg.n_cells, 3, 8)), stream=stream)
+                st = cache.render_iteration(img, seed=13, iteration=it, mode=1, update_estimate=True, stream=stream)
+                g = cache.get_state(stream=stream)
+                torch.cuda.synchronize()
+                out.append((img.cpu().numpy().copy(), st, g))
+            res.append(out)
+            cache.close()
+        for (a, sa, ga), (b, sb, gb) in zip(res[0], res[1]):
+            assert np.array_equal(a, b), cap
+            for k in ("rays", "vertices", "estimator_vertices", "wave_entries", "shadow_entries", "shadow_traced"):
+                assert sa[k] == sb[k], (cap, k)
+            np.testing.assert_allclose(ga["stats"], gb["stats"], rtol=1e-6, atol=1e-9)
+            assert sa["VI"] == pytest.approx(sb["VI"], rel=1e-9)
+            assert sb["tiles"] >= 2
+        if cap:
+            assert any(s["retries"] > 0 for _, s, _ in res[1])
+        else:
+            # the first iteration (no history) of the two-lane cache renders
+            # one tile per lane; the one-lane cache one tile
+            assert res[0][0][1]["tiles"] == 1 and res[1][0][1]["tiles"] == 2 and res[1][0][1]["retries"] == 0
