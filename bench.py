@@ -432,9 +432,10 @@ def large_scene(args, M, stream):
     """The heightfield workload (256 x 256 quads = 131k triangles + 202 spheres,
     1024 x 1024, D = 10, three techniques) with the adaptive octree cache
     (starting as the 32^3 grid, at most 64k leaves): hierarchy build time, then
-    3 warm-up and 3 timed MARS iterations with the bidirectional application's
-    image-level rules (Sec. 5.1: V_I without the 10 brightest pixels, the
-    iterations combined with weights 1 / V_I); throughput, kernel times,
+    3 warm-up and 3 timed MARS iterations (then 3 more with every launch timed)
+    with the bidirectional application's image-level rules (Sec. 5.1: V_I
+    without the 10 brightest pixels, the iterations combined with weights
+    1 / V_I); throughput, kernel times,
     traversal work per ray and the octree's size at this geometry size."""
     import torch
     cfg = W.config_heightfield(1024, 1024)
@@ -459,14 +460,21 @@ def large_scene(args, M, stream):
     e0.record(stream)
     for k in range(3):
         sts.append(cache.render_iteration(img, seed=77, iteration=it, mode=M.MARS_MODE_MARS, update_estimate=True,
-                                          profile=True, vi_drop_brightest=10, combine=2 if k == 0 else 1,
-                                          stream=stream))
+                                          vi_drop_brightest=10, combine=2 if k == 0 else 1, stream=stream))
         cache.update_counts(stream=stream)
         it += 1
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / 3
     verts = sum(s["vertices"] for s in sts) / 3
+    timed = sts
+    # kernel times: the same iterations once more, every launch between events
+    sts = []
+    for k in range(3):
+        sts.append(cache.render_iteration(img, seed=77, iteration=it, mode=M.MARS_MODE_MARS, update_estimate=True,
+                                          profile=True, vi_drop_brightest=10, combine=1, stream=stream))
+        cache.update_counts(stream=stream)
+        it += 1
     tw = [sum(s["trace_work"][0][q] for s in sts) for q in range(4)]
     n = max(sum(s["wave_entries"] for s in sts), 1)
     out = {"workload": cfg.name, "primitives": int(len(cfg.scene.tris) + len(cfg.scene.spheres) + len(cfg.scene.quads)),
@@ -477,9 +485,10 @@ def large_scene(args, M, stream):
            "closest_hit_per_ray": {"nodes": round(tw[0] / n, 2), "prim_tests": round(sum(tw[1:]) / n, 2)},
            "mean_beta": [round(sum(s["mean_beta"][t] for s in sts) / 3, 4) for t in range(3)],
            "octree_leaves": int(cache.info()["oct_n_leaves"]), "launch": launch,
-           "progressive": {"vi_drop_brightest": 10, "combined_iterations": 3,
+           "tiles": [s["tiles"] for s in timed],
+           "progressive": {"vi_drop_brightest": 10, "combined_iterations": 6,
                            "combined_weight": round(cache.combined_image(stream=stream)[1], 4),
-                           "VI": [round(s["VI"], 5) for s in sts]}}
+                           "VI": [round(s["VI"], 5) for s in timed + sts]}}
     if not args.no_precision:
         # float32 versus float64 statistics at this size (the large bidirectional
         # workload's precision comparison), on the learned state and tree
@@ -502,8 +511,9 @@ def largest_scene(args, M, stream):
     """The largest single-GPU workload (the geometry of the large bidirectional
     configuration, rendered unidirectionally): 512 x 512 quads = 524k triangles,
     4096 GGX spheres, 8 area lights, 2048 x 2048, D = 12, BSDF + NEE, adaptive
-    octree <= 64k leaves, a 2 x pixels x D arena; 3 warm-up and 2 timed MARS iterations, then
-    the float32 versus float64 statistics comparison at this size."""
+    octree <= 64k leaves, a 2 x pixels x D arena; 3 warm-up and 2 timed MARS iterations (then
+    2 with every launch timed), then the float32 versus float64 statistics
+    comparison at this size."""
     import torch
     cfg = W.config_large(2048, 2048)
     cfg.scene.bvh = BVH_KINDS[args.bvh]
@@ -528,19 +538,26 @@ def largest_scene(args, M, stream):
     e0.record(stream)
     for k in range(2):
         sts.append(cache.render_iteration(img, seed=91, iteration=it, mode=M.MARS_MODE_MARS, update_estimate=True,
-                                          profile=True, stream=stream))
+                                          stream=stream))
         cache.update_counts(stream=stream)
         it += 1
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / 2
     verts = sum(s["vertices"] for s in sts) / 2
+    timed = sts
+    sts = []
+    for k in range(2):
+        sts.append(cache.render_iteration(img, seed=91, iteration=it, mode=M.MARS_MODE_MARS, update_estimate=True,
+                                          profile=True, stream=stream))
+        cache.update_counts(stream=stream)
+        it += 1
     tw = [sum(s["trace_work"][0][q] for s in sts) for q in range(4)]
     n = max(sum(s["wave_entries"] for s in sts), 1)
     out = {"workload": cfg.name, "primitives": int(len(cfg.scene.tris) + len(cfg.scene.spheres) + len(cfg.scene.quads)),
            "bvh_build_s": round(build_s, 3), "ms_per_step": round(ms, 3),
            "mvertices_s": round(verts / (ms * 1e-3) / 1e6, 1), "vertices_per_step": int(verts),
-           "tiles": [s["tiles"] for s in sts], "arena_slots": cap,
+           "tiles": [s["tiles"] for s in timed], "arena_slots": cap,
            "kernel_ms_per_step": {k: round(sum(s[k + "_ms"] for s in sts) / 2, 4)
                                   for k in ("trace", "shade", "shadow", "reverse", "image")},
            "closest_hit_per_ray": {"nodes": round(tw[0] / n, 2), "prim_tests": round(sum(tw[1:]) / n, 2)},
