@@ -502,6 +502,12 @@ void scene_destroy_impl(mars_scene* s) {
 }
 
 // ------------------------------------------------------------------ cache
+// images below this size render in one lane (two half tiles measured 2 %
+// slower at 128 x 128 and 1.5 % at 256 x 256, 5 % faster at 512 x 512); above
+// it, one lane per 2^16 pixels up to the cache's lanes
+constexpr int64_t kLaneMinPixels = 1 << 17;
+constexpr int kDefaultLanes = 2;
+
 uint64_t cache_footprint(int64_t cells, int64_t pixels, int max_depth, int techniques, uint64_t cap) {
   (void)max_depth;
   uint64_t b = (uint64_t)cap * (SLOT_BYTES + SHADOW_BYTES);
@@ -571,7 +577,7 @@ mars_status cache_create_impl(const mars_scene* s, const mars_cache_desc* d, cud
   c->max_tiles = 4096;
   // two tile lanes (each with half the arena) unless asked for one or the
   // image has a single pixel
-  c->lanes = ((d->flags & MARS_CACHE_ONE_LANE) || pixels < 2 || cap < 128) ? 1 : 2;
+  c->lanes = ((d->flags & MARS_CACHE_ONE_LANE) || pixels < 2 || cap < 128) ? 1 : kDefaultLanes;
   auto cleanup = [&](cudaError_t e, const char* what) {
     const mars_status ms = e == cudaErrorMemoryAllocation ? MARS_ERR_OOM : MARS_ERR_CUDA;
     set_error(ms, "%s: %s", what, cudaGetErrorString(e));
@@ -733,18 +739,22 @@ mars_status cache_create_impl(const mars_scene* s, const mars_cache_desc* d, cud
     if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return cleanup(e, "event");
     c->sync_events.push_back(ev);
   }
-  if (c->lanes > 1) {
-    // the second lane's rendering and shadow streams, its D + 1 fork / join
-    // events and the two that fork it from and join it to the caller's stream
-    if ((e = cudaStreamCreateWithFlags(&c->lane_st, cudaStreamNonBlocking)) != cudaSuccess ||
-        (e = cudaStreamCreateWithFlags(&c->lane_side, cudaStreamNonBlocking)) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming)) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming)) != cudaSuccess)
-      return cleanup(e, "lane streams");
+  if (c->lanes > 1 && (e = cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming)) != cudaSuccess)
+    return cleanup(e, "lane event");
+  for (int l = 1; l < c->lanes; ++l) {
+    cudaStream_t a = nullptr, b = nullptr;
+    cudaEvent_t j = nullptr;
+    if ((e = cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking)) == cudaSuccess) c->lane_st.push_back(a);
+    if (e == cudaSuccess && (e = cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking)) == cudaSuccess)
+      c->lane_side.push_back(b);
+    if (e == cudaSuccess && (e = cudaEventCreateWithFlags(&j, cudaEventDisableTiming)) == cudaSuccess)
+      c->join_ev.push_back(j);
+    if (e != cudaSuccess) return cleanup(e, "lane streams");
+    c->lane_sync.emplace_back();
     for (int k = 0; k <= d->max_depth; ++k) {
       cudaEvent_t ev;
       if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return cleanup(e, "event");
-      c->lane_sync.push_back(ev);
+      c->lane_sync.back().push_back(ev);
     }
   }
   {
@@ -818,10 +828,14 @@ void cache_destroy_impl(mars_cache* c) {
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   for (cudaEvent_t ev : c->events) cudaEventDestroy(ev);
   for (cudaEvent_t ev : c->sync_events) cudaEventDestroy(ev);
-  for (cudaEvent_t ev : c->lane_sync) cudaEventDestroy(ev);
+  for (auto& v : c->lane_sync)
+    for (cudaEvent_t ev : v) cudaEventDestroy(ev);
+  for (cudaEvent_t ev : c->join_ev) cudaEventDestroy(ev);
   if (c->fork_ev) cudaEventDestroy(c->fork_ev);
-  if (c->join_ev) cudaEventDestroy(c->join_ev);
-  for (cudaStream_t q : {c->side, c->lane_st, c->lane_side})
+  std::vector<cudaStream_t> qs{c->side};
+  qs.insert(qs.end(), c->lane_st.begin(), c->lane_st.end());
+  qs.insert(qs.end(), c->lane_side.begin(), c->lane_side.end());
+  for (cudaStream_t q : qs)
     if (q) {
       cudaStreamSynchronize(q);
       cudaStreamDestroy(q);
@@ -830,10 +844,6 @@ void cache_destroy_impl(mars_cache* c) {
 }
 
 // ------------------------------------------------------------ iteration
-// images below this size render in one lane (two half tiles measured 2 %
-// slower at 128 x 128 and 1.5 % at 256 x 256, 5 % faster at 512 x 512)
-constexpr int64_t kLaneMinPixels = 1 << 17;
-
 // lane l's view of the cache: the same cache fields, its own counters
 static DevCache lane_cache(const mars_cache* c, int l) {
   DevCache d = c->dc;
@@ -920,8 +930,8 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
   // waves).  Otherwise one lane with the whole arena per tile.
   int iter_lanes = 1;
   if (c->lanes > 1 && !p->profile && npx >= kLaneMinPixels && ntiles == 1 && 1.3 * c->last_need <= 1.0) {
-    iter_lanes = 2;
-    ntiles = 2;
+    iter_lanes = (int)std::min<int64_t>(c->lanes, npx / (kLaneMinPixels / 2));
+    ntiles = iter_lanes;
   }
   std::vector<std::pair<int64_t, int64_t>> tiles;
   for (int t = 0; t < ntiles; ++t) {
@@ -973,26 +983,27 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
     auto enqueue = [&](cudaStream_t q) -> cudaError_t {
       cudaError_t r;
       if (concurrent) {
-        if ((r = cudaEventRecord(c->fork_ev, q)) != cudaSuccess ||
-            (r = cudaStreamWaitEvent(c->lane_st, c->fork_ev, 0)) != cudaSuccess)
-          return r;
+        if ((r = cudaEventRecord(c->fork_ev, q)) != cudaSuccess) return r;
+        for (int l = 1; l < nl; ++l)
+          if ((r = cudaStreamWaitEvent(c->lane_st[l - 1], c->fork_ev, 0)) != cudaSuccess) return r;
       }
       for (size_t t = 0; t < tiles.size(); ++t) {
         const int l = (int)(t % (size_t)nl);
         cudaEvent_t* ev = profile ? c->events.data() + t * per_tile : nullptr;
-        const bool own = concurrent && l == 1;
+        const bool own = concurrent && l >= 1;
         if ((r = launch_tile(s->ds, lane_cache(c, l), lane_arena(c, l, nl), c->d_args + t, c->launch,
-                             own ? c->lane_st : q, own ? c->lane_side : c->side,
-                             own ? c->lane_sync.data() : c->sync_events.data(), ev)) != cudaSuccess)
+                             own ? c->lane_st[l - 1] : q, own ? c->lane_side[l - 1] : c->side,
+                             own ? c->lane_sync[l - 1].data() : c->sync_events.data(), ev)) != cudaSuccess)
           return r;
       }
       if (nl > 1) {
-        if (concurrent) {
-          if ((r = cudaEventRecord(c->join_ev, c->lane_st)) != cudaSuccess ||
-              (r = cudaStreamWaitEvent(q, c->join_ev, 0)) != cudaSuccess)
-            return r;
-        }
-        if ((r = launch_merge_lanes(c->d_ctr, c->d_ctr + 1, q)) != cudaSuccess) return r;
+        if (concurrent)
+          for (int l = 1; l < nl; ++l)
+            if ((r = cudaEventRecord(c->join_ev[l - 1], c->lane_st[l - 1])) != cudaSuccess ||
+                (r = cudaStreamWaitEvent(q, c->join_ev[l - 1], 0)) != cudaSuccess)
+              return r;
+        for (int l = 1; l < nl; ++l)
+          if ((r = launch_merge_lanes(c->d_ctr, c->d_ctr + l, q)) != cudaSuccess) return r;
       }
       cudaEvent_t* iev = profile ? c->events.data() + tiles.size() * per_tile : nullptr;
       if (iev) cudaEventRecord(iev[0], q);
@@ -1049,7 +1060,7 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
     } else if ((e = enqueue(st)) != cudaSuccess) {
       return poison(c, e, "render launch");
     }
-    launches += (uint32_t)(tiles.size() * tile_launches(D, c->techniques)) + (nl > 1 ? 1u : 0u);
+    launches += (uint32_t)(tiles.size() * tile_launches(D, c->techniques)) + (uint32_t)(nl - 1);
     wave_launches += (uint32_t)(tiles.size() * D);
     launches += p->update_estimate ? 3 + (p->vi_drop_brightest > 0 ? 2 : 0) + (p->combine ? 1 : 0)
                                    : (dev_out ? 1 : 0);

@@ -134,11 +134,15 @@ struct mars_cache {
   // (d_ctr[l]) in its own 1/lanes share of the arena, so the two lanes' wave
   // kernels fill each other's idle SMs (the small deep waves leave most of the
   // GPU idle); lane 1's totals are merged into lane 0's before the image pass.
-  static constexpr int kMaxLanes = 2;
+  static constexpr int kMaxLanes = 4;
   int lanes = 1;
-  cudaStream_t lane_st = nullptr, lane_side = nullptr;
-  std::vector<cudaEvent_t> lane_sync;
-  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+  // lanes 1..lanes-1: rendering stream, shadow stream, D + 1 fork / join
+  // events between them, and the event that joins the lane to the caller's
+  // stream; fork_ev forks all of them from it
+  std::vector<cudaStream_t> lane_st, lane_side;
+  std::vector<std::vector<cudaEvent_t>> lane_sync;
+  std::vector<cudaEvent_t> join_ev;
+  cudaEvent_t fork_ev = nullptr;
   // per-tile iteration arguments: written to the pinned slots, copied to the
   // device slots before the launches, read there by every kernel
   mars::IterArgs* h_args = nullptr;
