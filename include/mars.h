@@ -297,6 +297,18 @@ mars_status mars_render_iteration(mars_cache* cache, const mars_iter_params* par
  * statistics.  Asynchronous on `stream`.  Errors: CUDA. */
 mars_status mars_update_counts(mars_cache* cache, void* stream);
 
+/* ---- testing hook (host only; the paper has no counterpart) -------------
+ * Exercises the error paths without faulting a GPU.  kind MARS_INJECT_ALLOC:
+ * the n-th next device allocation of the library, in any call, fails as if the
+ * device were out of memory (the call returns MARS_ERR_OOM and releases what
+ * it had allocated).  kind MARS_INJECT_LAUNCH: the n-th next
+ * mars_render_iteration or mars_update_counts fails as if a kernel launch had
+ * failed (MARS_ERR_CUDA; that cache is poisoned, others are unaffected).
+ * n = 0 cancels.  Process-wide countdowns.  Errors: INVALID_ARG. */
+#define MARS_INJECT_ALLOC 0
+#define MARS_INJECT_LAUNCH 1
+mars_status mars_debug_inject_failure(int32_t kind, int32_t n);
+
 /* ---- progressive combination (Sec. 5.1 "Implementation") ----------------
  * The combined image sum_i w_i I_i / sum_i w_i over the iterations rendered
  * with params.combine (w_i = 1 / max(V_I of iteration i, 1e-12)), packed rgb
@@ -356,6 +368,9 @@ typedef struct {
   int32_t warmup;          /* leading iterations with beta = 1 */
   uint32_t key;            /* second Philox key word; a job's random numbers depend
                               on (seed, key) only, never on the server's job id */
+  double timeout_s;        /* wall-clock limit counted from the job's start (0: none):
+                              a job still running past it stops before its next
+                              iteration and fails with MARS_ERR_TIMEOUT */
 } mars_job_desc;
 
 typedef enum { MARS_JOB_QUEUED = 0, MARS_JOB_RUNNING = 1, MARS_JOB_DONE = 2, MARS_JOB_FAILED = 3 } mars_job_state;

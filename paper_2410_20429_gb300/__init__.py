@@ -9,6 +9,8 @@ from ._abi import (  # noqa: F401
     MARS_BVH_LBVH,
     MARS_BVH_SAH,
     MARS_CACHE_NO_GRAPHS,
+    MARS_INJECT_ALLOC,
+    MARS_INJECT_LAUNCH,
     MARS_ERR_BUSY,
     MARS_ERR_CUDA,
     MARS_ERR_INVALID_ARG,
@@ -30,4 +32,4 @@ from ._abi import (  # noqa: F401
     MarsError,
     load,
 )
-from .renderer import Cache, Scene, Server, scene_desc  # noqa: F401
+from .renderer import Cache, Scene, Server, inject_failure, scene_desc  # noqa: F401

@@ -21,6 +21,7 @@ MARS_CACHE_NO_GRAPHS = 4
 MARS_CACHE_ONE_LANE = 8
 MARS_BVH_SAH = 0
 MARS_MAX_DROP_BRIGHTEST = 16
+MARS_INJECT_ALLOC, MARS_INJECT_LAUNCH = 0, 1
 MARS_BVH_LBVH = 1
 NUM_SLOTS, NUM_STATS, GUIDE_BINS, MAX_DEPTH = 3, 8, 256, 16
 
@@ -101,7 +102,8 @@ class mars_launch_config(ct.Structure):
 
 class mars_job_desc(ct.Structure):
     _fields_ = [("scene", ct.POINTER(mars_scene_desc)), ("cache", mars_cache_desc), ("seed", ct.c_uint32),
-                ("iterations", ct.c_int32), ("warmup", ct.c_int32), ("key", ct.c_uint32)]
+                ("iterations", ct.c_int32), ("warmup", ct.c_int32), ("key", ct.c_uint32),
+                ("timeout_s", ct.c_double)]
 
 
 class mars_job_status(ct.Structure):
@@ -122,6 +124,7 @@ SIGNATURES = {
     "mars_render_iteration": ([_VP, ct.POINTER(mars_iter_params), _VP, ct.POINTER(mars_iter_stats), _VP], ct.c_int),
     "mars_update_counts": ([_VP, _VP], ct.c_int),
     "mars_cache_combined_image": ([_VP, _VP, ct.POINTER(ct.c_double), _VP], ct.c_int),
+    "mars_debug_inject_failure": ([ct.c_int32, ct.c_int32], ct.c_int),
     "mars_cache_get_state": ([_VP, ct.POINTER(mars_cache_state), _VP], ct.c_int),
     "mars_cache_set_state": ([_VP, ct.POINTER(mars_cache_state), _VP], ct.c_int),
     "mars_cache_get_launch": ([_VP, ct.POINTER(mars_launch_config)], ct.c_int),

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <cmath>
@@ -19,7 +20,22 @@ namespace mars {
 
 thread_local std::string g_last_error;
 
+// testing hook: countdowns of injected failures (see mars_debug_inject_failure)
+static std::atomic<int> g_inject_alloc{0}, g_inject_launch{0};
+
+// true when this call is the one the countdown was set to fail
+static bool inject_hit(std::atomic<int>& c) {
+  int v = c.load();
+  while (v > 0)
+    if (c.compare_exchange_weak(v, v - 1)) return v == 1;
+  return false;
+}
+
 cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t st) {
+  if (inject_hit(g_inject_alloc)) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
   static std::once_flag once[64];
   int dev = 0;
   cudaGetDevice(&dev);
@@ -113,6 +129,7 @@ int num_sms_of(int dev) {
 
 // ------------------------------------------------------------------ scene
 mars_status scene_create_impl(const mars_scene_desc* d, cudaStream_t st, mars_scene** out) {
+  NvtxRange nvtx("mars:scene_create");
   if (!d || !out) return set_error(MARS_ERR_INVALID_ARG, "null descriptor or output");
   *out = nullptr;
   if (d->n_quads < 0 || d->n_spheres < 0 || d->n_tris < 0 || d->n_materials <= 0)
@@ -339,6 +356,7 @@ mars_status scene_create_impl(const mars_scene_desc* d, cudaStream_t st, mars_sc
       (e = cudaMemcpyAsync(s->d_mats, mats.data(), sizeof(float4) * mats.size(), cudaMemcpyHostToDevice, st)) ||
       (e = cudaMemcpyAsync(s->d_lights, lights.data(), sizeof(float4) * lights.size(), cudaMemcpyHostToDevice, st)))
     return cleanup(e, "scene upload");
+  NvtxRange nvtx_bvh("mars:bvh_build");
   if (d->bvh == MARS_BVH_SAH && n >= 2) {
     std::vector<BvhNode> sah;
     if (!build_bvh_sah(boxes, n, sah)) {
@@ -527,6 +545,7 @@ uint64_t default_capacity(int64_t pixels, int max_depth) {
 }
 
 mars_status cache_create_impl(const mars_scene* s, const mars_cache_desc* d, cudaStream_t st, mars_cache** out) {
+  NvtxRange nvtx("mars:cache_create");
   if (!s || !d || !out) return set_error(MARS_ERR_INVALID_ARG, "null scene, descriptor or output");
   *out = nullptr;
   if (d->grid_n < 1 || d->grid_n > 256) return set_error(MARS_ERR_INVALID_ARG, "grid_n %d out of [1, 256]", d->grid_n);
@@ -877,6 +896,7 @@ static mars_status poison(mars_cache* c, cudaError_t e, const char* what) {
 
 mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, float* image, mars_iter_stats* out,
                                   cudaStream_t st) {
+  NvtxRange nvtx("mars:render_iteration");
   if (!c || !p) return set_error(MARS_ERR_INVALID_ARG, "null cache or params");
   if (c->poisoned) return set_error(MARS_ERR_CUDA, "cache is poisoned by an earlier CUDA error");
   if (p->iteration >= 65536u) return set_error(MARS_ERR_INVALID_ARG, "iteration %u >= 65536", p->iteration);
@@ -898,6 +918,7 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
   DeviceGuard g(c->device);
   if (!g.ok) return set_error(MARS_ERR_CUDA, "cannot select device %d", c->device);
   c->last_stream = st;
+  if (inject_hit(g_inject_launch)) return poison(c, cudaErrorLaunchFailure, "injected render failure");
   const mars_scene* s = c->scene;
 
   IterArgs it{};
@@ -1038,6 +1059,7 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
           cudaGraphExecDestroy(c->graph_exec);
           c->graph_exec = nullptr;
         }
+        NvtxRange nvtx_capture("mars:graph_capture");
         cudaGraph_t graph = nullptr;
         if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
           return poison(c, e, "graph capture");
@@ -1190,9 +1212,11 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
 }
 
 mars_status update_counts_impl(mars_cache* c, cudaStream_t st) {
+  NvtxRange nvtx("mars:update_counts");
   if (!c) return set_error(MARS_ERR_INVALID_ARG, "null cache");
   if (c->poisoned) return set_error(MARS_ERR_CUDA, "cache is poisoned by an earlier CUDA error");
   DeviceGuard g(c->device);
+  if (inject_hit(g_inject_launch)) return poison(c, cudaErrorLaunchFailure, "injected update failure");
   c->last_stream = st;
   cudaError_t e = cudaSuccess;
   if (c->dc.oct_nodes && (e = launch_leaf_samples(c->dc, st)) != cudaSuccess) return poison(c, e, "update launch");
@@ -1456,6 +1480,17 @@ mars_status mars_cache_get_state(mars_cache* cache, mars_cache_state* state, voi
   return get_state_impl(cache, state, (cudaStream_t)stream);
 }
 
+mars_status mars_debug_inject_failure(int32_t kind, int32_t n) {
+  if (n < 0) return set_error(MARS_ERR_INVALID_ARG, "negative countdown %d", n);
+  if (kind == MARS_INJECT_ALLOC)
+    g_inject_alloc.store(n);
+  else if (kind == MARS_INJECT_LAUNCH)
+    g_inject_launch.store(n);
+  else
+    return set_error(MARS_ERR_INVALID_ARG, "unknown injection kind %d", kind);
+  return MARS_OK;
+}
+
 mars_status mars_cache_combined_image(mars_cache* c, float* image_rgb, double* weight_sum, void* stream) {
   if (!c) return set_error(MARS_ERR_INVALID_ARG, "null cache");
   if (c->poisoned) return set_error(MARS_ERR_CUDA, "cache is poisoned by an earlier CUDA error");
@@ -1524,6 +1559,7 @@ mars_status mars_cache_set_launch(mars_cache* c, const mars_launch_config* cfg) 
 // as it was.
 mars_status mars_cache_autotune(mars_cache* c, const mars_iter_params* params, int32_t repeats,
                                 mars_launch_config* chosen, void* stream) {
+  NvtxRange nvtx("mars:autotune");
   if (!c || !params) return set_error(MARS_ERR_INVALID_ARG, "null cache or params");
   if (repeats < 1 || repeats > 100) return set_error(MARS_ERR_INVALID_ARG, "repeats %d outside 1..100", repeats);
   if (c->poisoned) return set_error(MARS_ERR_CUDA, "cache is poisoned by an earlier CUDA error");

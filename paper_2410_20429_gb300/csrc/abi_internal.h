@@ -13,6 +13,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.h"
 
 namespace mars {
@@ -42,6 +44,16 @@ struct SceneDescCopy {
 };
 
 mars_status set_error(mars_status s, const char* fmt, ...);
+
+// An NVTX range over a scope: the library's stages show up by name in
+// profilers (ncu --nvtx filters kernels by them); without a tool attached the
+// calls do nothing.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // What a recorded iteration graph depends on besides the per-tile arguments,
 // which the kernels read from device memory: it is replayed while these are

@@ -32,6 +32,7 @@ struct Job {
   mars_cache_desc cache{};
   uint32_t seed = 0, key = 0;
   int iterations = 0, warmup = 0;
+  double timeout_s = 0.0;
   uint64_t footprint = 0;
   mars_job_state state = MARS_JOB_QUEUED;
   int done_iters = 0;
@@ -64,6 +65,7 @@ struct mars_server {
   double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
 
   void run_job(Job* j) {
+    mars::NvtxRange nvtx("mars:served_job");
     cudaSetDevice(device);
     cudaStream_t st = nullptr;
     mars_scene* sc = nullptr;
@@ -93,6 +95,10 @@ struct mars_server {
     cd.flags |= MARS_CACHE_ONE_LANE;
     if (rc == MARS_OK) rc = mars::cache_create_impl(sc, &cd, st, &ca);
     for (int it = 0; rc == MARS_OK && it < j->iterations; ++it) {
+      if (j->timeout_s > 0.0 && now() - j->start_s > j->timeout_s) {
+        rc = mars::set_error(MARS_ERR_TIMEOUT, "job ran past its %.3f s timeout after %d iterations", j->timeout_s, it);
+        break;
+      }
       mars_iter_params p{};
       p.seed = j->seed;
       p.job = j->key;
@@ -205,6 +211,8 @@ mars_status mars_submit(mars_server* s, const mars_job_desc* jd, uint64_t* job_i
   j->key = jd->key;
   j->iterations = jd->iterations;
   j->warmup = jd->warmup;
+  if (!(jd->timeout_s >= 0.0)) return mars::set_error(MARS_ERR_INVALID_ARG, "negative timeout");
+  j->timeout_s = jd->timeout_s;
   const int64_t npx = (int64_t)d->width * d->height;
   const int64_t cells = (int64_t)jd->cache.grid_n * jd->cache.grid_n * jd->cache.grid_n;
   const uint64_t cap = jd->cache.arena_capacity ? jd->cache.arena_capacity

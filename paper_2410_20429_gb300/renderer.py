@@ -267,13 +267,14 @@ class Server:
         self._descs = {}
 
     def submit(self, desc, *, grid_n, techniques, max_depth, iterations, warmup, seed=0, key=0,
-               arena_capacity=0, graphs=True) -> int:
+               arena_capacity=0, graphs=True, timeout_s=0.0) -> int:
         d, keep = scene_desc(desc)
         j = A.mars_job_desc()
         j.scene = ct.pointer(d)
         j.cache = A.mars_cache_desc(int(grid_n), int(techniques), int(max_depth),
                                     0 if graphs else A.MARS_CACHE_NO_GRAPHS, int(arena_capacity), 0, 0.0)
         j.seed, j.iterations, j.warmup, j.key = int(seed), int(iterations), int(warmup), int(key)
+        j.timeout_s = float(timeout_s)
         jid = ct.c_uint64()
         A.check(self._lib.mars_submit(self.handle, ct.byref(j), ct.byref(jid)), "mars_submit")
         self._descs[jid.value] = (desc.width, desc.height)
@@ -314,3 +315,10 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def inject_failure(kind: int, n: int) -> None:
+    """Testing hook: the n-th next device allocation (kind MARS_INJECT_ALLOC) or
+    render / update call (kind MARS_INJECT_LAUNCH) of the library fails; n = 0
+    cancels (see mars_debug_inject_failure in mars.h)."""
+    A.check(A.load().mars_debug_inject_failure(int(kind), int(n)), "mars_debug_inject_failure")
