@@ -107,6 +107,7 @@ TRAFFIC_FILE = "profiles/dram_traffic_guided_room_512.txt"
 
 
 BVH_KINDS = {"sah": 0, "lbvh": 1}   # MARS_BVH_SAH, MARS_BVH_LBVH
+PATH_BYTES_PER_VERTEX = 330          # minimum DRAM traffic of one path vertex (ray, hit, vertex, shadow ray, ...)
 
 
 def kernel_sources_sha():
@@ -395,7 +396,14 @@ def run_mars(args):
         "graphs": {"enabled": not args.no_graphs, "captures_in_timed_steps": captures,
                    "profiled_ms_per_step": round(profiled_ms, 4),
                    "profiled_mvertices_s": round(verts_prof / (profiled_ms * args.steps * 1e-3) / 1e6, 3)},
-        "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+        "roofline": roofline, "e2e": e2e,
+        # the whole path against HBM: at the minimum traffic of ~330 B per path
+        # vertex (ray, hit, vertex record, shadow ray, count reads, statistics)
+        # the copy bandwidth allows hbm / 330 B vertices per second
+        "path_roofline": {"bytes_per_vertex": PATH_BYTES_PER_VERTEX,
+                          "ceiling_mvertices_s": round(peaks()[0] * 1e9 / PATH_BYTES_PER_VERTEX / 1e6, 1),
+                          "frac": round(value / (peaks()[0] * 1e9 / PATH_BYTES_PER_VERTEX / 1e6), 4)},
+        "gpu_launches": int(launches), "clocks": clk,
         # Fig. convergence (E8): average allocation per technique and the image
         # efficiency estimate 1 / (V_I C_I) over the fixed-point iterations
         "convergence": {"mean_beta": [[round(b, 4) for b in s["mean_beta"]] for s in curve + timed + sts],
@@ -750,22 +758,49 @@ def box_efficiency(args, M, stream, iterations=None):
     return eff
 
 
+def _oracle_chunks(job):
+    """Worker of the multi-core CPU baseline (a spawned process): render the
+    given pixel runs of one iteration with the oracle as it stands; returns
+    (path vertices, seconds)."""
+    scene, grid_n, techniques, max_depth, iteration, runs = job
+    import oracle
+    verts, t = 0, 0.0
+    for b, e in runs:
+        t0 = time.perf_counter()
+        r = oracle.render(scene, grid_n=grid_n, techniques=techniques, max_depth=max_depth, iteration=iteration,
+                          seed=3, px_begin=b, px_end=e)
+        t += time.perf_counter() - t0
+        verts += r.vertices
+    return verts, t
+
+
+def _cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part", "hardware")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def cpu_baseline(cfg, seconds, reference_arm=False):
-    """The CPU oracle (single thread, as it stands) on a bounded pixel sample of
-    the same workload: warm-up mode (beta = 1), pixels evenly strided over the
-    image, sized to roughly `seconds` of work."""
+    """The CPU oracle as it stands on the host cores, warm-up mode (beta = 1):
+    one thread on 4096-pixel runs spread evenly over the image (about `seconds`
+    of work; runs of that size keep the oracle's per-call set-up, a copy of the
+    cache fields and guide tables, from dominating), and the whole image split
+    into 4096-pixel runs over one spawned process per host core (started and
+    warmed before the clock starts)."""
     import oracle
     sc = cfg.scene
     oracle.build()
+    chunk = 4096
 
     def run(npx_sample, it):
         stride = max(1, sc.n_pixels // npx_sample)
         t = 0.0
         verts = 0.0
-        # render contiguous chunks at strided offsets to cover the image; a
-        # chunk of 4096 pixels amortises the oracle's per-call set-up (its copy
-        # of the cache fields and guide tables), which dominates small chunks
-        chunk = 4096
         starts = list(range(0, sc.n_pixels, stride * chunk))[: max(1, npx_sample // chunk)]
         for s0 in starts:
             t0 = time.perf_counter()
@@ -775,12 +810,35 @@ def cpu_baseline(cfg, seconds, reference_arm=False):
             verts += r.vertices
         return verts, t, len(starts) * chunk
 
-    v, t, n = run(4096, 0)
-    target = max(4096, int(4096 * seconds / max(t, 1e-3)))
+    v, t, n = run(chunk, 0)
+    target = max(chunk, int(chunk * seconds / max(t, 1e-3)))
     v, t, n = run(min(target, sc.n_pixels), 1)
-    return {"value": round(v / t / 1e6, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n} pixels of the {sc.width}x{sc.height} workload (4096-pixel runs evenly spread), "
-                      f"one warm-up iteration (beta = 1), {int(v)} path vertices in {t:.1f} s"}
+    single = round(v / t / 1e6, 5)
+    out = {"value": single, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{n} pixels of the {sc.width}x{sc.height} workload (4096-pixel runs evenly spread), "
+                     f"one warm-up iteration (beta = 1), {int(v)} path vertices in {t:.1f} s",
+           "cpu": _cpu_model(), "nproc": os.cpu_count()}
+    # all host cores: spawned workers (a process forked after CUDA was used hangs)
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    cores = max(1, os.cpu_count() or 1)
+    runs = [(b, min(sc.n_pixels, b + chunk)) for b in range(0, sc.n_pixels, chunk)]
+    jobs = [(sc, cfg.grid_n, cfg.techniques, cfg.max_depth, 1, runs[k::cores]) for k in range(cores)]
+    try:
+        with cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn")) as pool:
+            list(pool.map(_oracle_chunks, [(sc, cfg.grid_n, cfg.techniques, cfg.max_depth, 0, [(0, 64)])] * cores))
+            t0 = time.perf_counter()
+            res = list(pool.map(_oracle_chunks, jobs))
+            wall = time.perf_counter() - t0
+        verts = sum(r[0] for r in res)
+        out.update({"value": round(verts / wall / 1e6, 5), "cores": cores,
+                    "sample": f"the whole {sc.width}x{sc.height} image ({sc.n_pixels} pixels in 4096-pixel runs "
+                              f"over {cores} processes), one warm-up iteration (beta = 1), {int(verts)} path "
+                              f"vertices in {wall:.2f} s",
+                    "single_thread": {"value": single, "sample": out["sample"]}})
+    except Exception as exc:  # keep the single-thread figure if processes cannot be spawned
+        out["multi_core_error"] = repr(exc)[:200]
+    return out
 
 
 def run_reference(args):
@@ -789,21 +847,29 @@ def run_reference(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if rank != 0:
         return
+    import concurrent.futures as cf
+    import multiprocessing as mp
     import oracle
     oracle.build()
     cfg = workload(args)
     sc = cfg.scene
-    per_step = max(64, args.ref_pixels_per_step)
+    cores = max(1, os.cpu_count() or 1)
+    per_step = min(sc.n_pixels, max(64, args.ref_pixels_per_step))
+    chunk = max(64, per_step // cores)
     times, verts = [], []
-    for k in range(args.warmup + args.steps):
-        b = (k * 7919 * 64) % max(1, sc.n_pixels - per_step)
-        t0 = time.perf_counter()
-        r = oracle.render(sc, grid_n=cfg.grid_n, techniques=cfg.techniques, max_depth=cfg.max_depth, iteration=k,
-                          seed=3, px_begin=b, px_end=b + per_step)
-        dt = time.perf_counter() - t0
-        if k >= args.warmup:
-            times.append(dt)
-            verts.append(r.vertices)
+    # one spawned process per host core, started and warmed before the steps
+    with cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn")) as pool:
+        list(pool.map(_oracle_chunks, [(sc, cfg.grid_n, cfg.techniques, cfg.max_depth, 0, [(0, 64)])] * cores))
+        for k in range(args.warmup + args.steps):
+            b = (k * 7919 * 64) % max(1, sc.n_pixels - per_step + 1)
+            runs = [(b + q, min(b + per_step, b + q + chunk)) for q in range(0, per_step, chunk)]
+            jobs = [(sc, cfg.grid_n, cfg.techniques, cfg.max_depth, k, runs[w::cores]) for w in range(cores)]
+            t0 = time.perf_counter()
+            res = list(pool.map(_oracle_chunks, jobs))
+            dt = time.perf_counter() - t0
+            if k >= args.warmup:
+                times.append(dt)
+                verts.append(sum(r[0] for r in res))
     value = sum(verts) / sum(times) / 1e6
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * sum(times) / len(times), 3),
@@ -811,9 +877,10 @@ def run_reference(args):
             "data": "synthetic",
             "config": {"workload": cfg.name, "pixels": sc.n_pixels, "max_depth": cfg.max_depth,
                        "grid": cfg.grid_n, "techniques": "bsdf+nee+guided"},
-            "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{per_step} contiguous pixels per step of the {sc.width}x{sc.height} "
-                                       "workload, warm-up mode (beta = 1)"},
+                                       f"workload over {cores} processes, warm-up mode (beta = 1)",
+                             "cpu": _cpu_model()},
             "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -831,7 +898,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-spp", type=int, default=256)
     ap.add_argument("--eff-spp", type=int, default=32)
-    ap.add_argument("--ref-pixels-per-step", type=int, default=16384)
+    ap.add_argument("--ref-pixels-per-step", type=int, default=65536)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--bvh", default="sah", choices=sorted(BVH_KINDS),
                     help="hierarchy of the closest-hit and shadow queries (results do not depend on it)")
