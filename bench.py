@@ -762,10 +762,10 @@ def _oracle_chunks(job):
     """Worker of the multi-core CPU baseline (a spawned process): render the
     given pixel runs of one iteration with the oracle as it stands; returns
     (path vertices, seconds)."""
-    scene, grid_n, techniques, max_depth, iteration, runs = job
+    scene, grid_n, techniques, max_depth, runs = job
     import oracle
     verts, t = 0, 0.0
-    for b, e in runs:
+    for iteration, b, e in runs:
         t0 = time.perf_counter()
         r = oracle.render(scene, grid_n=grid_n, techniques=techniques, max_depth=max_depth, iteration=iteration,
                           seed=3, px_begin=b, px_end=e)
@@ -822,19 +822,23 @@ def cpu_baseline(cfg, seconds, reference_arm=False):
     import concurrent.futures as cf
     import multiprocessing as mp
     cores = max(1, os.cpu_count() or 1)
-    runs = [(b, min(sc.n_pixels, b + chunk)) for b in range(0, sc.n_pixels, chunk)]
-    jobs = [(sc, cfg.grid_n, cfg.techniques, cfg.max_depth, 1, runs[k::cores]) for k in range(cores)]
+    # the whole image, repeated (successive iterations) to about `seconds` of
+    # single-core work in all
+    images = max(1, int(round(seconds / max(t * sc.n_pixels / max(n, 1), 1e-3))))
+    runs = [(it, b, min(sc.n_pixels, b + chunk)) for it in range(1, images + 1)
+            for b in range(0, sc.n_pixels, chunk)]
+    jobs = [(sc, cfg.grid_n, cfg.techniques, cfg.max_depth, runs[k::cores]) for k in range(cores)]
     try:
         with cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn")) as pool:
-            list(pool.map(_oracle_chunks, [(sc, cfg.grid_n, cfg.techniques, cfg.max_depth, 0, [(0, 64)])] * cores))
+            list(pool.map(_oracle_chunks, [(sc, cfg.grid_n, cfg.techniques, cfg.max_depth, [(0, 0, 64)])] * cores))
             t0 = time.perf_counter()
             res = list(pool.map(_oracle_chunks, jobs))
             wall = time.perf_counter() - t0
         verts = sum(r[0] for r in res)
         out.update({"value": round(verts / wall / 1e6, 5), "cores": cores,
-                    "sample": f"the whole {sc.width}x{sc.height} image ({sc.n_pixels} pixels in 4096-pixel runs "
-                              f"over {cores} processes), one warm-up iteration (beta = 1), {int(verts)} path "
-                              f"vertices in {wall:.2f} s",
+                    "sample": f"the whole {sc.width}x{sc.height} image {images} times ({sc.n_pixels} pixels in "
+                              f"4096-pixel runs over {cores} processes), warm-up iterations (beta = 1), "
+                              f"{int(verts)} path vertices in {wall:.2f} s",
                     "single_thread": {"value": single, "sample": out["sample"]}})
     except Exception as exc:  # keep the single-thread figure if processes cannot be spawned
         out["multi_core_error"] = repr(exc)[:200]
@@ -859,11 +863,11 @@ def run_reference(args):
     times, verts = [], []
     # one spawned process per host core, started and warmed before the steps
     with cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn")) as pool:
-        list(pool.map(_oracle_chunks, [(sc, cfg.grid_n, cfg.techniques, cfg.max_depth, 0, [(0, 64)])] * cores))
+        list(pool.map(_oracle_chunks, [(sc, cfg.grid_n, cfg.techniques, cfg.max_depth, [(0, 0, 64)])] * cores))
         for k in range(args.warmup + args.steps):
             b = (k * 7919 * 64) % max(1, sc.n_pixels - per_step + 1)
-            runs = [(b + q, min(b + per_step, b + q + chunk)) for q in range(0, per_step, chunk)]
-            jobs = [(sc, cfg.grid_n, cfg.techniques, cfg.max_depth, k, runs[w::cores]) for w in range(cores)]
+            runs = [(k, b + q, min(b + per_step, b + q + chunk)) for q in range(0, per_step, chunk)]
+            jobs = [(sc, cfg.grid_n, cfg.techniques, cfg.max_depth, runs[w::cores]) for w in range(cores)]
             t0 = time.perf_counter()
             res = list(pool.map(_oracle_chunks, jobs))
             dt = time.perf_counter() - t0
