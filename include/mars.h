@@ -207,7 +207,25 @@ typedef struct {
   uint64_t wave_rays[16];     /* rays held by depth wave d (index d - 1), all tiles */
   uint64_t trace_work[2][4];  /* closest-hit [0] and shadow [1] traversal: BVH node visits
                                  (two box tests each), quad, sphere and triangle tests */
+  uint32_t check_flags;       /* MARS_CHECK_* bits of the index checks that failed (always 0
+                                 in the regular library; see below) */
+  uint32_t reserved;
 } mars_iter_stats;
+
+/* Index checks of the checked library (libmars_checked.so, the same sources
+ * built with MARS_CHECKED): kernels test every arena slot, cell, pixel, BVH node,
+ * primitive, material, light and guide-bin index they compute against the
+ * buffer it addresses, skip an access that fails, and report the kind here
+ * (compute-sanitizer is unavailable; no check traps or faults). */
+#define MARS_CHECK_ARENA 1u
+#define MARS_CHECK_SHADOW 2u
+#define MARS_CHECK_CELL 4u
+#define MARS_CHECK_PIXEL 8u
+#define MARS_CHECK_PRIM 16u
+#define MARS_CHECK_NODE 32u
+#define MARS_CHECK_LIGHT 64u
+#define MARS_CHECK_BIN 128u
+#define MARS_CHECK_MATERIAL 256u
 
 /* Host copy of a cache's state (checkpoint / teacher forcing).  Any pointer
  * may be NULL to skip that field.  Layouts:

@@ -70,7 +70,7 @@ class mars_iter_stats(ct.Structure):
         ("shadow_ms", ct.c_double), ("reverse_ms", ct.c_double), ("image_ms", ct.c_double),
         ("wave_entries", ct.c_uint64), ("shadow_entries", ct.c_uint64), ("shadow_traced", ct.c_uint64),
         ("wave_ms", (ct.c_float * 16) * 4), ("wave_rays", ct.c_uint64 * 16),
-        ("trace_work", (ct.c_uint64 * 4) * 2),
+        ("trace_work", (ct.c_uint64 * 4) * 2), ("check_flags", ct.c_uint32), ("reserved", ct.c_uint32),
     ]
 
 

@@ -1205,6 +1205,8 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
     for (int d = 0; d < MAXD; ++d) out->wave_rays[d] = h.wave_total[d + 1];
     for (int k = 0; k < 2; ++k)
       for (int q = 0; q < 4; ++q) out->trace_work[k][q] = h.trace_work[k][q];
+    out->check_flags = h.check_flags;
+    out->reserved = 0;
   }
   c->last_VI = c->h_ctr->VI;
   c->last_CI = c->h_ctr->CI;

@@ -115,7 +115,22 @@ __device__ __forceinline__ bool hit_tri(const float4* q, f3 o, f3 d, float tmax,
 // (two box tests each) and primitive tests by type.
 struct TraceWork {
   unsigned int nodes = 0, quads = 0, spheres = 0, tris = 0;
+  unsigned int bad = 0;  // checked builds: MARS_CHECK_NODE / MARS_CHECK_PRIM bits of failed checks
 };
+
+// checked builds: a node or primitive index the traversal read from the BVH is
+// inside the node or primitive array (else the bit is recorded and the
+// traversal stops)
+__device__ __forceinline__ bool trav_ok(bool ok, unsigned int bit, TraceWork& w) {
+#ifdef MARS_CHECKED
+  if (!ok) w.bad |= bit;
+  return ok;
+#else
+  (void)bit;
+  (void)w;
+  return true;
+#endif
+}
 
 __device__ __forceinline__ bool hit_prim(const float4* __restrict__ prims, int i, f3 o, f3 d, float tmax,
                                          float& t, TraceWork& w) {
@@ -172,6 +187,7 @@ __device__ __forceinline__ int trace_closest(const DevScene& s, f3 o, f3 d, floa
   int node = 0;
   // every internal node is visited at most once per ray
   for (int visits = 0; visits < s.n_prims; ++visits) {
+    if (!trav_ok(node >= 0 && node < s.n_prims - 1, MARS_CHECK_NODE, w)) break;
     const BvhNode nd = s.nodes[node];
     ++w.nodes;
     // admit boxes entered at t <= t_best (a tie may still win on index)
@@ -191,6 +207,7 @@ __device__ __forceinline__ int trace_closest(const DevScene& s, f3 o, f3 d, floa
       vr = false;
     }
     while (p0 >= 0) {
+      if (!trav_ok(p0 < s.n_prims, MARS_CHECK_PRIM, w)) break;
       float t;
       if (hit_prim(s.prims, p0, o, d, t_best * 1.0000002f + 1e-30f, t, w) &&
           (t < t_best || (t == t_best && p0 < best))) { t_best = t; best = p0; }
@@ -241,6 +258,7 @@ __device__ __forceinline__ bool trace_any4(const DevScene& s, f3 o, f3 d, float 
   int sp = 0;
   int node = 0;
   for (int visits = 0; visits < s.n_nodes4; ++visits) {
+    if (!trav_ok(node >= 0 && node < s.n_nodes4, MARS_CHECK_NODE, w)) break;
     const Bvh4Node nd = s.nodes4[node];
     w.nodes += 2;
     float t[4];
@@ -264,6 +282,7 @@ __device__ __forceinline__ bool trace_any4(const DevScene& s, f3 o, f3 d, float 
       const int k = __ffs(leaves) - 1;
       leaves &= leaves - 1;
       const int c = k == 0 ? ch[0] : (k == 1 ? ch[1] : (k == 2 ? ch[2] : ch[3]));
+      if (!trav_ok(~c < s.n_prims, MARS_CHECK_PRIM, w)) return false;
       if (hit_prim(s.prims, ~c, o, d, tmax, th, w)) return true;
     }
     if (next >= 0) {
@@ -285,6 +304,7 @@ __device__ __forceinline__ bool trace_any(const DevScene& s, f3 o, f3 d, float t
   int sp = 0;
   int node = 0;
   for (int visits = 0; visits < s.n_prims; ++visits) {
+    if (!trav_ok(node >= 0 && node < s.n_prims - 1, MARS_CHECK_NODE, w)) break;
     const BvhNode nd = s.nodes[node];
     ++w.nodes;
     const float tl = box_entry(nd.a, nd.b, o, inv, tmax);

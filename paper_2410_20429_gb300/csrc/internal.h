@@ -128,7 +128,23 @@ struct DevCounters {
   float chsum32[3], vi_sum32;  // the same sums in float32 (float32 statistics)
   double VI, CI;               // results of the last image-stats pass
   int vi_dropped;              // pixels left out of the V_I mean
+  unsigned int check_flags;    // MARS_CHECK_* bits of failed index checks (checked builds)
 };
+
+// Index checks of the checked build (-DMARS_CHECKED, libmars_checked.so): an
+// index a kernel computed is tested against the buffer it addresses; a failed
+// test sets its MARS_CHECK_* bit in the counters and the caller skips the
+// access.  Regular builds compile every check to `true`.
+__device__ __forceinline__ bool chk(bool ok, unsigned int bit, DevCounters* ctr) {
+#ifdef MARS_CHECKED
+  if (!ok) atomicOr(&ctr->check_flags, bit);
+  return ok;
+#else
+  (void)bit;
+  (void)ctr;
+  return true;
+#endif
+}
 
 struct DevCache {
   int grid_n, n_cells, techniques, max_depth, bits;

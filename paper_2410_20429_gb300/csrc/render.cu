@@ -119,7 +119,12 @@ __device__ __forceinline__ int owner_lane(const int* incl, int k) {
 }
 
 // warp sum of a thread's traversal counters, one atomic per counter and warp
-__device__ __forceinline__ void flush_work(TraceWork w, unsigned long long* dst) {
+__device__ __forceinline__ void flush_work(TraceWork w, unsigned long long* dst, DevCounters* ctr) {
+#ifdef MARS_CHECKED
+  if (w.bad) atomicOr(&ctr->check_flags, w.bad);
+#else
+  (void)ctr;
+#endif
   unsigned long long v[4] = {w.nodes, w.quads, w.spheres, w.tris};
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
@@ -200,6 +205,8 @@ __global__ void k_merge_lanes(DevCounters* dst, DevCounters* src) {
   }
   if (src->any_overflow) dst->any_overflow = 1;
   src->any_overflow = 0;
+  dst->check_flags |= src->check_flags;
+  src->check_flags = 0;
   if (src->demand > dst->demand) dst->demand = src->demand;
 }
 
@@ -221,6 +228,7 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_trace(const DevScene
   for (unsigned long long li = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; li < w.n;
        li += gridDim.x * (unsigned long long)blockDim.x) {
     const unsigned long long i = w.base + li;
+    if (!chk(i < a.cap, MARS_CHECK_ARENA, c.ctr)) break;
     f3 o, dir;
     bool alive = true;
     if (d == 1) {
@@ -239,7 +247,7 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_trace(const DevScene
     if (alive) prim = trace_closest(s, o, dir, t, tw);
     a.H[i] = make_float2(t, __int_as_float(prim));
   }
-  flush_work(tw, c.ctr->trace_work[0]);
+  flush_work(tw, c.ctr->trace_work[0], c.ctr);
 }
 
 // ------------------------------------------------------------------ shade
@@ -293,7 +301,7 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_shade(const DevScene
   for (unsigned long long b0 = blockIdx.x * (unsigned long long)blockDim.x; b0 < w.n;
        b0 += gridDim.x * (unsigned long long)blockDim.x) {
     const unsigned long long li = b0 + threadIdx.x;
-    const bool active = li < w.n;
+    const bool active = li < w.n && chk(w.base + li < a.cap, MARS_CHECK_ARENA, ctr);
     const unsigned long long i = w.base + li;
     if (d > 1) {
       // the ray record of this thread's next slot, fetched into L2 meanwhile
@@ -349,11 +357,12 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_shade(const DevScene
     mat.type = 0;
     mat.alpha = 1.0f;
     mat.col = mk3(0.f, 0.f, 0.f);
-    if (prim >= 0) {
+    if (prim >= 0 && chk(prim < s.n_prims, MARS_CHECK_PRIM, ctr)) {
       p = o + dir * th;
       const f3 ng = prim_normal(s.prims, prim, p);
       wo = dir * -1.0f;
-      const int m = prim_material(s.prims, prim);
+      int m = prim_material(s.prims, prim);
+      if (!chk(m >= 0 && m < s.n_mats, MARS_CHECK_MATERIAL, ctr)) m = 0;
       const float4 m0 = __ldg(s.mats + 3 * m), m1 = __ldg(s.mats + 3 * m + 1), m2 = __ldg(s.mats + 3 * m + 2);
       const float cosg = dot(ng, wo);
       if (cosg > 0.0f && m0.w > 0.0f) {
@@ -376,6 +385,8 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_shade(const DevScene
         flags |= F_EST;
         ns = cosg >= 0.0f ? ng : ng * -1.0f;
         cell = c.oct_nodes ? octree_cell(s, c.oct_nodes, p) : cell_of(s, c.grid_n, p);
+        if (!chk(cell >= 0 && cell < c.n_cells, MARS_CHECK_CELL, ctr)) cell = 0;
+        if (!chk(px < (uint32_t)c.n_pixels, MARS_CHECK_PIXEL, ctr)) px = 0;
         mat.type = (int)m0.x;
         mat.alpha = m0.y;
         mat.col = xyz(m1);
@@ -615,7 +626,8 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_shade(const DevScene
           ok = bsdf_sample(m, wol, u.x, u.y, wl);
           if (ok) wi = fr.to_world(wl);
         } else {
-          const int b = guide_pick(cdf, u.x);
+          int b = guide_pick(cdf, u.x);
+          if (!chk(b >= 0 && b < GUIDE_BINS, MARS_CHECK_BIN, ctr)) b = 0;
           wi = guide_dir(b, u.y, u.z);
           pt = guide_bin_prob(cdf, b) * (GUIDE_BINS / (4.0f * PI_F));
           ok = dot(wi, vns) > 0.0f;
@@ -668,12 +680,13 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_shadow(const DevScen
   for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < n;
        k += gridDim.x * (unsigned long long)blockDim.x) {
     const unsigned long long j = a.SL[sb + k];
+    if (!chk(j < a.scap, MARS_CHECK_SHADOW, c.ctr)) continue;
     const float4 s0 = a.SH[0][j];
     if (!(s0.w > 0.0f)) continue;
     const float4 s1 = a.SH[1][j];
     if (trace_any4(s, xyz(s0), xyz(s1), s0.w, tw)) a.SH[2][j] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
-  flush_work(tw, c.ctr->trace_work[1]);
+  flush_work(tw, c.ctr->trace_work[1], c.ctr);
 }
 
 // ---------------------------------------------------------------- reverse
@@ -707,7 +720,7 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_reverse(const DevSce
 
   for (unsigned long long c0 = gw * 32; c0 < w.n; c0 += nw * 32) {
     const unsigned long long li = c0 + lane;
-    const bool active = li < w.n;
+    const bool active = li < w.n && chk(w.base + li < a.cap, MARS_CHECK_ARENA, ctr);
     const unsigned long long i = w.base + li;
     {
       // the records of this thread's next slot, fetched into L2 while this one
@@ -743,9 +756,14 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_reverse(const DevSce
       float4 v4 = make_float4(0.f, 0.f, 0.f, 0.f);
       if (guide_dep) v4 = a.V[4][i];
       if (flags & F_EST) {
-        const int gB = flags & 0xff, gN = (flags >> 8) & 0xff, gG = (flags >> 16) & 0xff;
-        const int ne = gB + gG;
-        const unsigned long long first = __float_as_uint(fs.x), sf = __float_as_uint(fs.y);
+        int gB = flags & 0xff, gN = (flags >> 8) & 0xff, gG = (flags >> 16) & 0xff;
+        int ne = gB + gG;
+        unsigned long long first = __float_as_uint(fs.x), sf = __float_as_uint(fs.y);
+        // the children and NEE values lie inside the arena (else read none)
+        const bool in_a = chk(first + (unsigned long long)ne <= a.cap, MARS_CHECK_ARENA, ctr);
+        const bool in_s = chk(sf + (unsigned long long)gN <= a.scap, MARS_CHECK_SHADOW, ctr);
+        if (!in_a) { first = 0; ne = 0; gB = 0; gG = 0; }
+        if (!in_s) { sf = 0; gN = 0; }
         const float4 v1 = a.V[1][i], v2 = a.V[2][i], v3 = a.V[3][i];
         float4 pn[4], pe[4];
 #pragma unroll
@@ -756,6 +774,7 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_reverse(const DevSce
         bt[0] = v3.x; bt[1] = v3.y; bt[2] = v3.z;
         const f3 climit = xyz(v2);
         key = __float_as_uint(v2.w);
+        if (!chk(key < (uint32_t)c.n_cells, MARS_CHECK_CELL, ctr)) key = 0xffffffffu;
         if (gN > 0) {
           f3 sum = mk3(0.f, 0.f, 0.f);
           for (int k = 0; k < gN; k += 4) {
@@ -811,10 +830,12 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_reverse(const DevSce
       }
       const uint32_t cost = 1u + csub;
       a.S[i] = f4(E, __uint_as_float(cost));
-      if (d == 1) c.img[it.tile_begin + li] = f4(E, 0.0f);
+      if (d == 1 && chk(it.tile_begin + li < (unsigned long long)c.n_pixels, MARS_CHECK_PIXEL, ctr))
+        c.img[it.tile_begin + li] = f4(E, 0.0f);
       if (guide_dep) {
         const float wdep = (v4.x + lum(Lr)) * v4.y;
-        if (wdep > 0.0f) {
+        if (wdep > 0.0f && chk(__float_as_uint(v4.z) < (uint32_t)c.n_cells, MARS_CHECK_CELL, ctr) &&
+            chk(__float_as_int(v4.w) >= 0 && __float_as_int(v4.w) < GUIDE_BINS, MARS_CHECK_BIN, ctr)) {
           const uint32_t pc = __float_as_uint(v4.z);
           atomicAdd(c.guide_hist + (size_t)pc * GUIDE_BINS + __float_as_int(v4.w), wdep);
           c.guide_dirty[pc] = 1;

@@ -57,5 +57,5 @@ def test_struct_sizes_match_header(lib):
     from paper_2410_20429_gb300 import _abi
     assert ct.sizeof(_abi.mars_iter_params) == 60
     assert ct.sizeof(_abi.mars_cache_desc) == 32
-    assert ct.sizeof(_abi.mars_iter_stats) == 152 + 4 * 16 * 4 + 8 * 16 + 8 * 8
+    assert ct.sizeof(_abi.mars_iter_stats) == 152 + 4 * 16 * 4 + 8 * 16 + 8 * 8 + 8
     assert ct.sizeof(_abi.mars_scene_desc) == 16 + 7 * 8 + 80 + 16

@@ -1,0 +1,93 @@
+"""GPU test of the checked library (libmars_checked.so: the same sources with
+every kernel index check compiled in; compute-sanitizer is unavailable): over
+grid and octree caches, triangles, arena-overflow tiles, two tile lanes, the
+float32 statistics and the budget-unaware weights, no index check fails, and
+each image agrees with the regular library's to float rounding."""
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+import mars_workloads as W
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+# (name, config factory and size, cache keywords, render keywords)
+CASES = [
+    ("box", "config_box", (48, 40), {}, {"mode": 1}),
+    ("guided", "config_guided", (64, 48), {}, {"mode": 1}),
+    ("guided_unaware_fp32", "config_guided", (64, 48), {"fp32_statistics": True}, {"mode": 1, "weights": 1}),
+    ("guided_overflow", "config_guided", (64, 48), {"arena_capacity": 12000}, {"mode": 1}),
+    ("guided_octree", "config_guided", (64, 48), {"octree": True, "max_leaves": 40000, "split_samples": 16.0},
+     {"mode": 1}),
+    ("heightfield", "config_heightfield", (48, 40), {}, {"mode": 1}),
+    ("guided_lanes", "config_guided", (384, 384), {}, {"mode": 1}),
+]
+
+SCRIPT = r"""
+import json, sys, os
+import numpy as np
+sys.path.insert(0, ROOT)
+from paper_2410_20429_gb300 import build as B, _abi as A
+checked = sys.argv[1] == "1"
+A._lib = A.load(B.build(checked=checked))   # the library every binding call then uses
+import paper_2410_20429_gb300 as M
+import mars_workloads as W
+import torch
+out = {}
+for name, fac, size, ckw, rkw in CASES:
+    cfg = getattr(W, fac)(*size)
+    scene = M.Scene(cfg.scene)
+    cache = M.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, **ckw)
+    q_rr, q_s, valid = W.random_count_fields(cache.n_cells, seed=71, lo=0.3, hi=3.0)
+    est = W.random_pixel_estimate(cfg.scene.n_pixels, seed=72, lo=0.05, hi=0.5)
+    flags, imgs = [], []
+    img = torch.zeros(cache.n_pixels * 3, dtype=torch.float32, device="cuda")
+    for it in (1, 2):
+        cache.set_state(q_rr=q_rr, q_s=q_s, valid=valid, pixel_estimate=est, has_estimate=True, n_iterations=1)
+        st = cache.render_iteration(img, seed=5, iteration=it, update_estimate=True, **rkw)
+        cache.update_counts()
+        torch.cuda.synchronize()
+        flags.append(int(st["check_flags"]))
+        imgs.append(img.cpu().numpy().copy())
+    np.save(os.path.join(OUT, name + ("_checked" if checked else "_plain") + ".npy"), np.stack(imgs))
+    out[name] = flags
+    cache.close(); scene.close()
+print(json.dumps(out))
+"""
+
+
+def _run(tmp_path, checked):
+    code = f"ROOT = {ROOT!r}\nOUT = {str(tmp_path)!r}\nCASES = {CASES!r}\n" + SCRIPT
+    r = subprocess.run([sys.executable, "-c", code, "1" if checked else "0"], capture_output=True, text=True,
+                       timeout=900)
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-4000:]
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+
+
+def test_checked_library_finds_no_bad_index_and_renders_the_same_images(gpu, tmp_path):
+    checked = _run(tmp_path, True)
+    plain = _run(tmp_path, False)
+    for name, *_ in CASES:
+        assert checked[name] == [0, 0], (name, checked[name])
+        assert plain[name] == [0, 0], (name, plain[name])
+        a = np.load(tmp_path / f"{name}_checked.npy").reshape(2, -1, 3).astype(np.float64)
+        b = np.load(tmp_path / f"{name}_plain.npy").reshape(2, -1, 3).astype(np.float64)
+        # the added checks change the compiler's instruction selection (which
+        # products fuse into FMAs), so results agree to float rounding, and a
+        # rounding-level difference can flip a rare discrete decision
+        ok = (np.abs(a - b) <= 1e-4 * np.abs(b) + 1e-7).all(axis=2).mean()
+        assert ok >= 0.99, (name, ok)
+        assert np.allclose(a.mean(axis=1), b.mean(axis=1), rtol=2e-3), name
