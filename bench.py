@@ -360,6 +360,17 @@ def run_mars(args):
                                     for ki, k in enumerate(["k_trace", "k_shade", "k_shadow", "k_reverse"])}
     entries = sum(s["wave_entries"] for s in sts)
 
+    # ---- the same loop timed on the host clock with the image in device
+    # memory (the control for the end-to-end figure below)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctl_verts = 0
+    for k in range(args.steps):
+        ctl_verts += step(it, M.MARS_MODE_MARS)["vertices"]
+        it += 1
+    torch.cuda.synchronize()
+    ctl_s = time.perf_counter() - t0
+
     # ---- end to end through the C ABI with a pinned host image every step
     host_img = torch.empty(npx * 3, dtype=torch.float32, pin_memory=True).numpy()
     torch.cuda.synchronize()
@@ -374,7 +385,8 @@ def run_mars(args):
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e = {"value": round(e2e_verts / e2e_s / 1e6, 3), "unit": UNIT, "h2d_bytes_per_step": 48,
-           "d2h_bytes_per_step": npx * 3 * 4 + 512}
+           "d2h_bytes_per_step": npx * 3 * 4 + 512,
+           "host_clock_device_image": round(ctl_verts / ctl_s / 1e6, 3)}
 
     launches = sum(s["launches"] for s in timed) + args.steps * (2 if guided else 1)
     line = {

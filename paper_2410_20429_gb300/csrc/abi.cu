@@ -965,13 +965,26 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
   float wave_ms[WAVE_KERNELS][MAXD] = {};
   const int D = c->max_depth;
   const int per_tile = 5 * D + 2;
-  // a host image is packed on the device by the image pass into a staging
-  // buffer of the cache (allocated on first use) and read back in one copy
-  if (p->image_on_host && !c->d_host_stage &&
-      (e = dev_alloc((void**)&c->d_host_stage, sizeof(float) * 3 * (size_t)npx, st)) != cudaSuccess)
-    return set_error(e == cudaErrorMemoryAllocation ? MARS_ERR_OOM : MARS_ERR_CUDA, "staging alloc: %s",
-                     cudaGetErrorString(e));
-  float* dev_out = p->image_on_host ? c->d_host_stage : image;
+  // A host image in page-locked memory is written by the image pass itself,
+  // through its device address (no copy); any other host image is packed by
+  // the image pass into a staging buffer of the cache (allocated on first use)
+  // and read back in one copy.
+  float* dev_out = image;
+  bool staged = false;
+  if (p->image_on_host) {
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, image) == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer) {
+      dev_out = static_cast<float*>(pa.devicePointer);
+    } else {
+      cudaGetLastError();  // an unregistered pointer is not an error here
+      staged = true;
+      if (!c->d_host_stage &&
+          (e = dev_alloc((void**)&c->d_host_stage, sizeof(float) * 3 * (size_t)npx, st)) != cudaSuccess)
+        return set_error(e == cudaErrorMemoryAllocation ? MARS_ERR_OOM : MARS_ERR_CUDA, "staging alloc: %s",
+                         cudaGetErrorString(e));
+      dev_out = c->d_host_stage;
+    }
+  }
   while (true) {
     if (p->profile) {
       const size_t need = tiles.size() * per_tile + 2;
@@ -1173,7 +1186,7 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
     c->n_iterations += 1;
     c->has_estimate = true;
   }
-  if (p->image_on_host) {
+  if (staged) {
     if ((e = cudaMemcpyAsync(image, c->d_host_stage, sizeof(float) * 3 * (size_t)npx, cudaMemcpyDeviceToHost, st)) !=
         cudaSuccess)
       return poison(c, e, "image copy");

@@ -528,12 +528,13 @@ def test_bvh_kind_does_not_change_results(mars, which):
     assert sa["trace_work"][0][0] > 0 and sb["trace_work"][0][0] > 0
 
 
-@pytest.mark.parametrize("capturable", [False, True])
-def test_host_image_equals_device_image(mars, capturable):
-    """An image requested in host memory is packed on the device and copied
-    back once; it equals the image written to device memory from the same state,
-    with and without the image statistics pass, on the legacy default stream and
-    on a stream whose iterations replay a recorded graph."""
+@pytest.mark.parametrize("capturable,pinned", [(False, False), (True, False), (False, True), (True, True)])
+def test_host_image_equals_device_image(mars, capturable, pinned):
+    """An image requested in host memory (page-locked: written by the image pass
+    through its device address; pageable: packed on the device and copied back
+    once) equals the image written to device memory from the same state, with
+    and without the image statistics pass, on the legacy default stream and on a
+    stream whose iterations replay a recorded graph."""
     import torch
     cfg = W.config_guided(40, 24)
     q_rr, q_s, valid = W.random_count_fields(cfg.n_cells, seed=901, lo=0.3, hi=4.0)
@@ -542,7 +543,8 @@ def test_host_image_equals_device_image(mars, capturable):
     scene = mars.Scene(cfg.scene, stream=stream)
     cache = mars.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, stream=stream)
     dev = torch.zeros(cache.n_pixels * 3, dtype=torch.float32, device="cuda")
-    host = np.zeros(cache.n_pixels * 3, np.float32)
+    host = (torch.zeros(cache.n_pixels * 3, dtype=torch.float32, pin_memory=True).numpy() if pinned
+            else np.zeros(cache.n_pixels * 3, np.float32))
     for it, upd in ((1, True), (2, False), (3, True)):
         outs = []
         for target in (dev, host):
