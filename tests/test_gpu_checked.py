@@ -28,6 +28,8 @@ CASES = [
     ("heightfield", "config_heightfield", (48, 40), {}, {"mode": 1}),
     ("guided_lanes", "config_guided", (384, 384), {}, {"mode": 1}),
 ]
+# technique subsets and shallow depths: (name, techniques, max depth)
+SUBSETS = [("bsdf_d1", 1, 1), ("bsdf_d3", 1, 3), ("bsdf_guided_d3", 5, 3), ("bsdf_nee_d2", 3, 2)]
 
 SCRIPT = r"""
 import json, sys, os
@@ -58,12 +60,25 @@ for name, fac, size, ckw, rkw in CASES:
     np.save(os.path.join(OUT, name + ("_checked" if checked else "_plain") + ".npy"), np.stack(imgs))
     out[name] = flags
     cache.close(); scene.close()
+for name, tech, depth in SUBSETS:
+    sc = W.guided_room_scene(2, 48, 32, n_spheres=12)
+    scene = M.Scene(sc)
+    cache = M.Cache(scene, 8, tech, depth)
+    img = torch.zeros(cache.n_pixels * 3, dtype=torch.float32, device="cuda")
+    flags = []
+    for it in range(4):
+        st = cache.render_iteration(img, seed=5, iteration=it, mode=0 if it < 2 else 1, update_estimate=True)
+        cache.update_counts()
+        torch.cuda.synchronize()
+        flags.append(int(st["check_flags"]))
+    out[name] = flags
+    cache.close(); scene.close()
 print(json.dumps(out))
 """
 
 
 def _run(tmp_path, checked):
-    code = f"ROOT = {ROOT!r}\nOUT = {str(tmp_path)!r}\nCASES = {CASES!r}\n" + SCRIPT
+    code = f"ROOT = {ROOT!r}\nOUT = {str(tmp_path)!r}\nCASES = {CASES!r}\nSUBSETS = {SUBSETS!r}\n" + SCRIPT
     r = subprocess.run([sys.executable, "-c", code, "1" if checked else "0"], capture_output=True, text=True,
                        timeout=900)
     assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-4000:]
@@ -91,3 +106,5 @@ def test_checked_library_finds_no_bad_index_and_renders_the_same_images(gpu, tmp
         ok = (np.abs(a - b) <= 1e-4 * np.abs(b) + 1e-7).all(axis=2).mean()
         assert ok >= 0.99, (name, ok)
         assert np.allclose(a.mean(axis=1), b.mean(axis=1), rtol=2e-3), name
+    for name, *_ in SUBSETS:
+        assert checked[name] == [0, 0, 0, 0], (name, checked[name])

@@ -53,7 +53,7 @@ def _stat_agreement(gs, os_):
     pop = (n_g > 0) | (n_o > 0)
     close = np.abs(gs - os_) <= STAT_TOL * np.abs(os_) + 1e-9
     agree = close.all(axis=-1) & pop
-    return agree.sum() / max(pop.sum(), 1)
+    return agree.sum() / pop.sum() if pop.any() else 1.0   # no samples (D = 1): nothing to disagree
 
 
 def _check(g_img, o_img, g_state, o_res, g_st, what):
@@ -660,3 +660,26 @@ def test_two_lanes_equal_one_lane(mars, capturable):
             # the first iteration (no history) of the two-lane cache renders
             # one tile per lane; the one-lane cache one tile
             assert res[0][0][1]["tiles"] == 1 and res[1][0][1]["tiles"] == 2 and res[1][0][1]["retries"] == 0
+
+
+@pytest.mark.parametrize("techniques,D", [(1, 1), (1, 2), (1, 4), (5, 2), (5, 4), (3, 1), (3, 2), (7, 2)])
+def test_technique_sets_and_shallow_depths_parity(mars, orc, techniques, D):
+    """Technique subsets (BSDF alone, BSDF + guided without NEE) and the
+    shallowest depths (D = 1: camera rays only, no estimator vertex; D = 2: one
+    estimator level) against the oracle, on a 32 x 24 crop of the guided room
+    with random counts and guide distributions, warm-up and MARS iterations."""
+    sc = W.guided_room_scene(seed=2, width=32, height=24, n_spheres=12)
+    cfg = W.WorkloadConfig(sc, max_depth=D, grid_n=8, techniques=techniques, iterations=1, warmup=0, name="subset")
+    scene, cache = _make(mars, cfg)
+    q_rr, q_s, valid = W.random_count_fields(cfg.n_cells, seed=301 + D, lo=0.1, hi=3.0)
+    est = W.random_pixel_estimate(sc.n_pixels, seed=302, lo=0.05, hi=2.0)
+    cdf = W.random_guide_cdf(cfg.n_cells, seed=303)
+    for mode in (0, 1):
+        kw = dict(guide_cdf=cdf) if techniques & W.TECH_GUIDED else {}
+        cache.set_state(q_rr=q_rr, q_s=q_s, valid=valid, pixel_estimate=est, has_estimate=True, n_iterations=2,
+                        stats=np.zeros((cfg.n_cells, 3, 8)), **kw)
+        g_img, g_st = _gpu_iteration(mars, cache, iteration=2, seed=11, mode=mode)
+        g_state = cache.get_state()
+        o = orc.render(sc, grid_n=cfg.grid_n, techniques=techniques, max_depth=D, iteration=2, seed=11, mode=mode,
+                       q_rr=q_rr, q_s=q_s, valid=valid, est=est, **kw)
+        _check(g_img, o.image, g_state, o, g_st, f"techniques {techniques}, D {D}, mode {mode}")
