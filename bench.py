@@ -29,6 +29,7 @@ import math
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -269,8 +270,8 @@ def run_mars(args):
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    clocks = ClockSampler(local, os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
-                          if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/mars_clocks_{rank}.csv")
+    clocks = ClockSampler(local, args.clocks_csv.replace("{rank}", str(rank)) if args.clocks_csv
+                          else os.path.join(tempfile.gettempdir(), f"mars_clocks_{rank}.csv"))
     time.sleep(0.3)
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     timed = []
@@ -928,6 +929,8 @@ def main():
     ap.add_argument("--serve-no-graphs", action="store_true", help="served jobs launch every kernel directly")
     ap.add_argument("--launch", default="", help="fixed wave-kernel launch shape 't,t,t,t:b,b,b,b[:r,r,r,r]' (threads per "
                     "block, blocks per SM and register cap of trace, shade, shadow, reverse); skips the autotuner")
+    ap.add_argument("--clocks-csv", default="", help="where the nvidia-smi samples of the timed region go "
+                    "('{rank}' is replaced by the rank; default: the temp directory)")
     ap.add_argument("--arena-capacity", type=int, default=0, help="queue arena slots (0 = library default)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "mars":
