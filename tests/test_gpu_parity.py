@@ -683,3 +683,65 @@ def test_technique_sets_and_shallow_depths_parity(mars, orc, techniques, D):
         o = orc.render(sc, grid_n=cfg.grid_n, techniques=techniques, max_depth=D, iteration=2, seed=11, mode=mode,
                        q_rr=q_rr, q_s=q_s, valid=valid, est=est, **kw)
         _check(g_img, o.image, g_state, o, g_st, f"techniques {techniques}, D {D}, mode {mode}")
+
+
+def _single_quad_scene(width, height):
+    """One emitting Lambertian quad facing the camera, partly filling the view:
+    a one-primitive hierarchy, rays that miss, and NEE samples that can never
+    reach the only light (it lies in the plane of every vertex)."""
+    return W.scenes._mk([[0, 0, 1, 0, 1, 0, 1, 0, 0]], [0], [], [],
+                        [W.scenes._lambert(0.5, 0.4, 0.3, (2.0, 1.5, 1.0))],
+                        [0.5, 0.5, -1.4, 0.5, 0.5, 0.0, 0.0, 1.0, 0.0, 40.0], width, height, "single_quad")
+
+
+@pytest.mark.parametrize("case", ["one_pixel", "prime_size", "single_quad_sah", "single_quad_lbvh", "all_miss"])
+def test_degenerate_inputs_parity(mars, orc, case):
+    """Edge cases of the path against the oracle: a 1 x 1 image; a 37 x 29
+    image (1073 pixels: every wave ends in a partial warp and block); a scene of
+    one primitive under both hierarchy builders; a camera that sees nothing
+    (every wave after the first is empty).  A warm-up iteration and a
+    teacher-forced MARS iteration each, then the image statistics."""
+    import dataclasses
+    cfg = W.config_box(37, 29)
+    if case == "one_pixel":
+        cfg = W.config_box(1, 1)
+    elif case.startswith("single_quad"):
+        cfg = dataclasses.replace(cfg, scene=_single_quad_scene(37, 29), max_depth=3)
+        cfg.scene.bvh = mars.MARS_BVH_SAH if case.endswith("sah") else mars.MARS_BVH_LBVH
+    elif case == "all_miss":
+        sc = dataclasses.replace(cfg.scene)
+        sc.camera = np.array([0.5, 0.5, -1.4, 0.5, 0.5, -3.0, 0.0, 1.0, 0.0, 40.0], np.float32)
+        cfg = dataclasses.replace(cfg, scene=sc)
+    n = cfg.scene.n_pixels
+    kw = dict(grid_n=cfg.grid_n, techniques=cfg.techniques, max_depth=cfg.max_depth)
+    scene, cache = _make(mars, cfg)
+
+    g_img, g_st = _gpu_iteration(mars, cache, iteration=0, seed=2, mode=0)
+    o = orc.render(cfg.scene, iteration=0, seed=2, **kw)
+    _check(g_img, o.image, cache.get_state(), o, g_st, f"{case} warm-up")
+
+    q_rr, q_s, valid = W.random_count_fields(cfg.n_cells, seed=901, lo=0.05, hi=4.0)
+    est = W.random_pixel_estimate(n, seed=902, lo=0.05, hi=1.0)
+    # statistics accumulate until the count update: start the MARS iteration from none
+    zero = np.zeros_like(cache.get_state()["stats"])
+    cache.set_state(q_rr=q_rr, q_s=q_s, valid=valid, pixel_estimate=est, has_estimate=True, n_iterations=1,
+                    stats=zero)
+    g_img, g_st = _gpu_iteration(mars, cache, iteration=1, seed=2, mode=1)
+    o = orc.render(cfg.scene, iteration=1, seed=2, mode=orc.MODE_MARS, q_rr=q_rr, q_s=q_s, valid=valid, est=est, **kw)
+    _check(g_img, o.image, cache.get_state(), o, g_st, f"{case} MARS")
+    if case == "all_miss":
+        assert not g_img.any() and g_st["rays"] == n and g_st["estimator_vertices"] == 0
+
+    # image statistics of a fresh warm-up iteration from a seeded running sum
+    rs = W.random_pixel_estimate(n, seed=903, lo=0.1, hi=3.0) * 2.0
+    ones = np.ones((n, 3), np.float32)
+    cache.set_state(run_sum=rs, n_iterations=2, has_estimate=True, pixel_estimate=ones)
+    g_img, g_st = _gpu_iteration(mars, cache, iteration=2, seed=2, mode=0, update_estimate=True)
+    g = cache.get_state()
+    o = orc.render(cfg.scene, iteration=2, seed=2, est=ones, **kw)
+    vi, o_rs, o_est = orc.image_stats(cfg.scene.width, cfg.scene.height, o.image, rs.astype(np.float64), 2)
+    assert _pixel_agreement(g["run_sum"].astype(np.float64), o_rs) >= 0.999
+    est_ok = np.abs(g["pixel_estimate"] - o_est) <= 1e-4 * np.abs(o_est) + 1e-7
+    assert est_ok.all(axis=1).mean() >= 0.99
+    assert g_st["VI"] == pytest.approx(vi, rel=1e-2)
+    assert g_st["CI"] == pytest.approx(o.rays / n, rel=1e-3)
