@@ -274,6 +274,7 @@ def run_mars(args):
                           else os.path.join(tempfile.gettempdir(), f"mars_clocks_{rank}.csv"))
     time.sleep(0.3)
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    captures0 = cache.info()["graph_captures"]
     timed = []
     torch.cuda.synchronize()
     evs[0].record(stream)
@@ -288,7 +289,7 @@ def run_mars(args):
     verts = sum(s["vertices"] for s in timed)
     t_max, verts_all = reduce_over_ranks(total_ms, verts, world, "cuda")
     value = verts_all / (t_max * 1e-3) / 1e6
-    captures = cache.info()["graph_captures"]
+    captures = cache.info()["graph_captures"] - captures0
 
     # ---- as many MARS steps again with every launch between CUDA events
     # (direct launches, no graph replay): the per-kernel device times
