@@ -396,7 +396,7 @@ def run_mars(args):
         "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": cfg.name, "pixels": npx, "max_depth": cfg.max_depth, "grid": cfg.grid_n,
-                   "techniques": "bsdf+nee+guided", "statistics_dtype": "f64", "bvh": args.bvh, "lanes": args.lanes,
+                   "techniques": "bsdf+nee+guided", "statistics_dtype": "f64", "bvh": args.bvh, "lanes": launch.get("lanes", args.lanes),
                    "l2": "working set > L2: queue arena %.0f MB per step" % (
                        entries / args.steps * SLOT_BYTES / 1e6),
                    "parallelism": f"replicas x{world}"},
@@ -921,7 +921,8 @@ def main():
     ap.add_argument("--bvh", default="sah", choices=sorted(BVH_KINDS),
                     help="hierarchy of the closest-hit and shadow queries (results do not depend on it)")
     ap.add_argument("--no-graphs", action="store_true", help="launch every kernel directly (no CUDA graph replay)")
-    ap.add_argument("--lanes", type=int, default=2, choices=[1, 2], help="concurrent pixel-tile lanes")
+    ap.add_argument("--lanes", type=int, default=2, choices=[1, 2],
+                    help="concurrent pixel-tile lanes the cache is created with (the autotuner keeps one or all)")
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the heightfield (131k triangles) section")
     ap.add_argument("--serve-requests", type=int, default=256, help="serving-stream requests (0 = skip)")

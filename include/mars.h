@@ -351,14 +351,20 @@ mars_status mars_cache_set_state(mars_cache* cache, const mars_cache_state* stat
  *   (mars_cache_get_launch reports the resolved count).
  * max_registers[k]: selects a compiled variant of the kernel whose registers
  *   per thread are capped (more resident blocks, possibly some spilling).
- * Default: 128 threads, no cap, the occupancy maximum.  Each depth wave's grid
- * is further sized from the previous iteration's wave size (at least one block
- * per SM, at most the grid above).  Errors: INVALID_ARG, CUDA. */
+ * lanes: concurrent tile lanes an iteration may use, 1 up to the count the
+ *   cache was created with (two, or one with MARS_CACHE_ONE_LANE); 0 keeps the
+ *   current value in mars_cache_set_launch.
+ * lane_min_pixels: the smallest image split over the lanes (default 2^17;
+ *   at least 2); 0 keeps the current value.
+ * Default: 128 threads, no cap, the occupancy maximum, every depth wave on the
+ * same grid.  Errors: INVALID_ARG, CUDA. */
 typedef struct {
   int32_t threads[4];
   int32_t blocks_per_sm[4];
   int32_t max_registers[4];  /* register cap of the compiled variant: 0 = the compiler's
                                 choice; shade and reverse also 80 or 64, trace and shadow 64 or 40 */
+  int32_t lanes;
+  int32_t lane_min_pixels;
 } mars_launch_config;
 mars_status mars_cache_get_launch(const mars_cache* cache, mars_launch_config* out);
 mars_status mars_cache_set_launch(mars_cache* cache, const mars_launch_config* config);
@@ -367,9 +373,12 @@ mars_status mars_cache_set_launch(mars_cache* cache, const mars_launch_config* c
  * occupancy maximum)
  * by the kernel's device time over `repeats` (1..100) renders of `params`'s
  * iteration, rendered without statistics, guide deposits or image statistics
- * so that the cache's learned state is unchanged; keeps the fastest shape and
- * writes it to `chosen` (may be NULL).  Synchronises `stream` after every
- * render.  Errors: INVALID_ARG, and those of mars_render_iteration. */
+ * so that the cache's learned state is unchanged; keeps the fastest shape.
+ * Then, for a cache with more than one lane and an image of at least 2^14
+ * pixels, times whole iterations (as rendered outside profiling: graphs, lanes)
+ * with one lane and with all lanes for any image of that size, and keeps the
+ * faster.  Writes the result to `chosen` (may be NULL).  Synchronises `stream`
+ * after every render.  Errors: INVALID_ARG, and those of mars_render_iteration. */
 mars_status mars_cache_autotune(mars_cache* cache, const mars_iter_params* params, int32_t repeats,
                                 mars_launch_config* chosen, void* stream);
 

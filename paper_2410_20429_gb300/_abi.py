@@ -97,7 +97,8 @@ class mars_cache_info(ct.Structure):
 
 
 class mars_launch_config(ct.Structure):
-    _fields_ = [("threads", ct.c_int32 * 4), ("blocks_per_sm", ct.c_int32 * 4), ("max_registers", ct.c_int32 * 4)]
+    _fields_ = [("threads", ct.c_int32 * 4), ("blocks_per_sm", ct.c_int32 * 4), ("max_registers", ct.c_int32 * 4),
+                ("lanes", ct.c_int32), ("lane_min_pixels", ct.c_int32)]
 
 
 class mars_job_desc(ct.Structure):

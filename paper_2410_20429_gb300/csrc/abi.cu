@@ -525,6 +525,7 @@ void scene_destroy_impl(mars_scene* s) {
 // it, one lane per 2^16 pixels up to the cache's lanes
 constexpr int64_t kLaneMinPixels = 1 << 17;
 constexpr int kDefaultLanes = 2;
+constexpr int64_t kLaneFloorPixels = 1 << 14;  // the autotuner tries lanes on images from this size
 
 uint64_t cache_footprint(int64_t cells, int64_t pixels, int max_depth, int techniques, uint64_t cap) {
   (void)max_depth;
@@ -597,6 +598,8 @@ mars_status cache_create_impl(const mars_scene* s, const mars_cache_desc* d, cud
   // two tile lanes (each with half the arena) unless asked for one or the
   // image has a single pixel
   c->lanes = ((d->flags & MARS_CACHE_ONE_LANE) || pixels < 2 || cap < 128) ? 1 : kDefaultLanes;
+  c->use_lanes = c->lanes;
+  c->lane_min_pixels = kLaneMinPixels;
   auto cleanup = [&](cudaError_t e, const char* what) {
     const mars_status ms = e == cudaErrorMemoryAllocation ? MARS_ERR_OOM : MARS_ERR_CUDA;
     set_error(ms, "%s: %s", what, cudaGetErrorString(e));
@@ -950,8 +953,8 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
   // profiled (a profiled iteration times each kernel alone on full-size
   // waves).  Otherwise one lane with the whole arena per tile.
   int iter_lanes = 1;
-  if (c->lanes > 1 && !p->profile && npx >= kLaneMinPixels && ntiles == 1 && 1.3 * c->last_need <= 1.0) {
-    iter_lanes = (int)std::min<int64_t>(c->lanes, npx / (kLaneMinPixels / 2));
+  if (c->use_lanes > 1 && !p->profile && npx >= c->lane_min_pixels && ntiles == 1 && 1.3 * c->last_need <= 1.0) {
+    iter_lanes = (int)std::min<int64_t>(c->use_lanes, npx / std::max<int64_t>(1, c->lane_min_pixels / 2));
     ntiles = iter_lanes;
   }
   std::vector<std::pair<int64_t, int64_t>> tiles;
@@ -1544,6 +1547,8 @@ mars_status mars_cache_get_launch(const mars_cache* c, mars_launch_config* out) 
     out->blocks_per_sm[k] = c->blocks_per_sm[k];
     out->max_registers[k] = wave_variant_registers(k, c->launch.variant[k]);
   }
+  out->lanes = c->use_lanes;
+  out->lane_min_pixels = (int32_t)std::min<int64_t>(c->lane_min_pixels, INT32_MAX);
   return MARS_OK;
 }
 
@@ -1563,8 +1568,16 @@ mars_status mars_cache_set_launch(mars_cache* c, const mars_launch_config* cfg) 
     if (!variant_of(k, cfg->max_registers[k], &var[k]))
       return set_error(MARS_ERR_INVALID_ARG, "wave kernel %d: no variant capped at %d registers", k,
                        cfg->max_registers[k]);
+  if (cfg->lanes < 0 || cfg->lanes > c->lanes)
+    return set_error(MARS_ERR_INVALID_ARG, "lanes %d outside 1..%d (the cache's lanes)", cfg->lanes, c->lanes);
+  if (cfg->lane_min_pixels < 0 || cfg->lane_min_pixels == 1)
+    return set_error(MARS_ERR_INVALID_ARG, "lane_min_pixels %d below 2", cfg->lane_min_pixels);
   DeviceGuard g(c->device);
-  return apply_launch(c, cfg->threads, cfg->blocks_per_sm, var);
+  const mars_status rc = apply_launch(c, cfg->threads, cfg->blocks_per_sm, var);
+  if (rc != MARS_OK) return rc;
+  if (cfg->lanes > 0) c->use_lanes = cfg->lanes;
+  if (cfg->lane_min_pixels > 0) c->lane_min_pixels = cfg->lane_min_pixels;
+  return MARS_OK;
 }
 
 // Coordinate search over the launch shape of each wave kernel in turn (register
@@ -1641,8 +1654,48 @@ mars_status mars_cache_autotune(mars_cache* c, const mars_iter_params* params, i
     bps[k] = best_b;
     var[k] = best_v;
   }
-  const mars_status rc = apply_launch(c, threads, bps, var);
+  mars_status rc = apply_launch(c, threads, bps, var);
   if (rc != MARS_OK) return rc;
+  // Tile lanes: whole iterations as rendered outside profiling (graph replay,
+  // concurrent lanes), one lane against all of them, timed on the stream.
+  if (c->lanes > 1 && c->pixels >= kLaneFloorPixels) {
+    mars_iter_params q = p;
+    q.profile = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+      if (e0) cudaEventDestroy(e0);
+      return set_error(MARS_ERR_CUDA, "event create failed");
+    }
+    const int cand_lanes[2] = {1, c->lanes};
+    const int64_t cand_min[2] = {c->lane_min_pixels,
+                                 std::max<int64_t>(kLaneFloorPixels, std::min<int64_t>(kLaneMinPixels, c->pixels))};
+    double best = 1e300;
+    int best_k = 0;
+    for (int k = 0; k < 2 && rc == MARS_OK; ++k) {
+      c->use_lanes = cand_lanes[k];
+      c->lane_min_pixels = cand_min[k];
+      double tot = 0.0;
+      for (int r = 0; r <= repeats && rc == MARS_OK; ++r) {  // the first render warms up (and records the graph)
+        mars_iter_stats st{};
+        float ms = 0.f;
+        if (cudaEventRecord(e0, (cudaStream_t)stream) != cudaSuccess) rc = set_error(MARS_ERR_CUDA, "event record");
+        if (rc == MARS_OK) rc = render_iteration_impl(c, &q, nullptr, &st, (cudaStream_t)stream);
+        if (rc == MARS_OK && (cudaEventRecord(e1, (cudaStream_t)stream) != cudaSuccess ||
+                              cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+          rc = set_error(MARS_ERR_CUDA, "event timing");
+        if (r > 0) tot += ms;
+      }
+      if (rc == MARS_OK && tot < best) {
+        best = tot;
+        best_k = k;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != MARS_OK) return rc;
+    c->use_lanes = cand_lanes[best_k];
+    c->lane_min_pixels = cand_min[best_k];
+  }
   if (chosen) return mars_cache_get_launch(c, chosen);
   return MARS_OK;
 }

@@ -147,7 +147,9 @@ struct mars_cache {
   // kernels fill each other's idle SMs (the small deep waves leave most of the
   // GPU idle); lane 1's totals are merged into lane 0's before the image pass.
   static constexpr int kMaxLanes = 4;
-  int lanes = 1;
+  int lanes = 1;                    // lanes with streams and counters (as created)
+  int use_lanes = 1;                // lanes an iteration may use (<= lanes)
+  int64_t lane_min_pixels = 1 << 17;  // smallest image split over the lanes
   // lanes 1..lanes-1: rendering stream, shadow stream, D + 1 fork / join
   // events between them, and the event that joins the lane to the caller's
   // stream; fork_ev forks all of them from it

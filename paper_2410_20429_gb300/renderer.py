@@ -157,27 +157,33 @@ class Cache:
         cfg = A.mars_launch_config()
         A.check(self._lib.mars_cache_get_launch(self.handle, ct.byref(cfg)), "mars_cache_get_launch")
         return {"threads": list(cfg.threads), "blocks_per_sm": list(cfg.blocks_per_sm),
-                "max_registers": list(cfg.max_registers)}
+                "max_registers": list(cfg.max_registers), "lanes": cfg.lanes, "lane_min_pixels": cfg.lane_min_pixels}
 
-    def set_launch(self, threads, blocks_per_sm, max_registers=(0, 0, 0, 0)) -> None:
+    def set_launch(self, threads, blocks_per_sm, max_registers=(0, 0, 0, 0), lanes=0, lane_min_pixels=0) -> None:
+        """Launch shape of the wave kernels; ``lanes`` / ``lane_min_pixels`` (0:
+        unchanged) set how many concurrent tile lanes an iteration may use and
+        the smallest image split over them."""
         cfg = A.mars_launch_config()
         for k in range(4):
             cfg.threads[k] = int(threads[k])
             cfg.blocks_per_sm[k] = int(blocks_per_sm[k])
             cfg.max_registers[k] = int(max_registers[k])
+        cfg.lanes = int(lanes)
+        cfg.lane_min_pixels = int(lane_min_pixels)
         A.check(self._lib.mars_cache_set_launch(self.handle, ct.byref(cfg)), "mars_cache_set_launch")
 
     def autotune(self, *, seed=0, job=0, iteration=0, mode=A.MARS_MODE_WARMUP, weights=A.MARS_WEIGHTS_AWARE,
                  clamp_lo=0.05, clamp_hi=20.0, outlier=50.0, repeats=2, max_multiplicity=0.0, stream=None) -> dict:
-        """Pick the fastest launch shape of every wave kernel on this iteration
-        (rendered without statistics, so the learned state is unchanged)."""
+        """Pick the fastest launch shape of every wave kernel on this iteration,
+        then one or all tile lanes by whole-iteration time (rendered without
+        statistics, so the learned state is unchanged)."""
         p = A.mars_iter_params(int(seed), int(job), int(iteration), int(mode), int(weights), float(clamp_lo),
                                float(clamp_hi), float(outlier), 0, 0, 0, 1, float(max_multiplicity))
         cfg = A.mars_launch_config()
         A.check(self._lib.mars_cache_autotune(self.handle, ct.byref(p), int(repeats), ct.byref(cfg),
                                               _stream_handle(stream)), "mars_cache_autotune")
         return {"threads": list(cfg.threads), "blocks_per_sm": list(cfg.blocks_per_sm),
-                "max_registers": list(cfg.max_registers)}
+                "max_registers": list(cfg.max_registers), "lanes": cfg.lanes, "lane_min_pixels": cfg.lane_min_pixels}
 
     def update_counts(self, stream=None) -> None:
         A.check(self._lib.mars_update_counts(self.handle, _stream_handle(stream)), "mars_update_counts")

@@ -52,10 +52,39 @@ def test_error_string_and_version_without_gpu(lib):
     assert b"null" in L.mars_last_error_string()
 
 
-def test_struct_sizes_match_header(lib):
-    """Layouts of the descriptor structs as the C compiler sees them."""
+def test_struct_sizes_match_header(lib, tmp_path):
+    """Layouts of the descriptor structs as the C compiler sees them: a C
+    program built against include/mars.h prints every struct's size and every
+    field's offset, and the Python binding's ctypes structures must agree."""
+    import shutil
+    import subprocess
     from paper_2410_20429_gb300 import _abi
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [getattr(_abi, n) for n in dir(_abi)
+               if n.startswith("mars_") and isinstance(getattr(_abi, n), type)
+               and issubclass(getattr(_abi, n), ct.Structure)]
+    assert len(structs) >= 9
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "mars.h"', 'int main(void) {']
+    for S in structs:
+        lines.append(f'  printf("{S.__name__} size %zu\\n", sizeof({S.__name__}));')
+        for f, _ in S._fields_:
+            lines.append(f'  printf("{S.__name__} {f} %zu\\n", offsetof({S.__name__}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([cc, "-std=c11", "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        name, field, v = line.split()
+        got[(name, field)] = int(v)
+    for S in structs:
+        assert ct.sizeof(S) == got[(S.__name__, "size")], S.__name__
+        for f, _ in S._fields_:
+            assert getattr(S, f).offset == got[(S.__name__, f)], (S.__name__, f)
+    # the sizes the header documents
     assert ct.sizeof(_abi.mars_iter_params) == 60
-    assert ct.sizeof(_abi.mars_cache_desc) == 32
-    assert ct.sizeof(_abi.mars_iter_stats) == 152 + 4 * 16 * 4 + 8 * 16 + 8 * 8 + 8
-    assert ct.sizeof(_abi.mars_scene_desc) == 16 + 7 * 8 + 80 + 16
+    assert ct.sizeof(_abi.mars_launch_config) == 56

@@ -841,3 +841,48 @@ def test_full_size_sampled_parity(mars, orc, which):
     print(msg)
     assert n_off_well <= 0.001 * total + 1, msg
     assert n_off <= max(n_sens, 0.001 * total + 1), msg
+
+
+def test_lane_settings_and_autotuned_lanes(mars):
+    """Tile lanes as a launch setting: the lane count is checked against the
+    cache's, a small image (128 x 128, below the default 2^17-pixel floor) split
+    over two lanes once the floor is lowered renders the one-lane image bitwise,
+    and the autotuner keeps one or all lanes without touching the learned state."""
+    import torch
+    cfg = W.config_guided(128, 128)
+    q_rr, q_s, valid = W.random_count_fields(cfg.n_cells, seed=991, lo=0.3, hi=1.5)
+    est = W.random_pixel_estimate(cfg.scene.n_pixels, seed=992, lo=0.05, hi=0.5)
+    stream = torch.cuda.Stream()
+    scene = mars.Scene(cfg.scene, stream=stream)
+    cache = mars.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, lanes=2, stream=stream)
+    base = cache.get_launch()
+    assert base["lanes"] == 2 and base["lane_min_pixels"] == 1 << 17
+    with pytest.raises(mars.MarsError):
+        cache.set_launch(base["threads"], base["blocks_per_sm"], base["max_registers"], lanes=3)
+    with pytest.raises(mars.MarsError):
+        cache.set_launch(base["threads"], base["blocks_per_sm"], base["max_registers"], lane_min_pixels=1)
+    img = torch.zeros(cache.n_pixels * 3, dtype=torch.float32, device="cuda")
+    out = []
+    for lanes, floor in ((1, 1 << 17), (2, 1 << 14)):
+        cache.set_launch(base["threads"], base["blocks_per_sm"], base["max_registers"], lanes=lanes,
+                         lane_min_pixels=floor)
+        got = cache.get_launch()
+        assert got["lanes"] == lanes and got["lane_min_pixels"] == floor
+        cache.set_state(q_rr=q_rr, q_s=q_s, valid=valid, pixel_estimate=est, has_estimate=True, n_iterations=1,
+                        stats=np.zeros((cfg.n_cells, 3, 8)), stream=stream)
+        st = cache.render_iteration(img, seed=17, iteration=1, mode=1, stream=stream)
+        torch.cuda.synchronize()
+        out.append((img.cpu().numpy().copy(), st))
+    (a, sa), (b, sb) = out
+    assert sa["tiles"] == 1 and sb["tiles"] == 2
+    assert np.array_equal(a, b) and sa["rays"] == sb["rays"] and sa["vertices"] == sb["vertices"]
+    before = cache.get_state(stream=stream)
+    chosen = cache.autotune(iteration=2, seed=17, mode=1, repeats=1, stream=stream)
+    after = cache.get_state(stream=stream)
+    assert chosen["lanes"] in (1, 2) and chosen == cache.get_launch()
+    for k in ("q_rr", "q_s", "valid", "stats", "pixel_estimate", "guide_cdf"):
+        assert np.array_equal(before[k], after[k]), k
+    one = mars.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, lanes=1, stream=stream)
+    assert one.get_launch()["lanes"] == 1
+    with pytest.raises(mars.MarsError):
+        one.set_launch(base["threads"], base["blocks_per_sm"], base["max_registers"], lanes=2)
