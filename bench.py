@@ -10,7 +10,9 @@ Printed (one JSON line, rank 0):
   value      path vertices per second (closest-hit queries) over the K timed
              steps, device time from CUDA events on the rendering stream
   e2e        the same metric through the C ABI with the image returned to pinned
-             host memory every step (host copies inside the timed region)
+             host memory every step (host copies inside the timed region), on
+             the same iterations: the cache is put back to its state before the
+             timed steps (exact checkpoint / resume) and they are replayed
   roofline   the dominant kernel's algorithmic bytes per launch / its average
              launch time, against the measured HBM copy bandwidth
   efficiency equal-time efficiency 1 / (relMSE x seconds) of MARS (counts frozen
@@ -205,6 +207,17 @@ def rel_mse(img, ref):
     return float(t.mean())
 
 
+def restore_state(cache, snap, iteration, stream):
+    """Put a cache back to a checkpoint taken with get_state (exact resume)
+    and return the iteration index to continue from."""
+    extra = {k: snap[k] for k in ("oct_nodes", "oct_leaf_level") if snap.get(k) is not None}
+    cache.set_state(q_rr=snap["q_rr"], q_s=snap["q_s"], valid=snap["valid"], stats=snap["stats"],
+                    guide_hist=snap["guide_hist"], guide_cdf=snap["guide_cdf"], pixel_estimate=snap["pixel_estimate"],
+                    run_sum=snap["run_sum"], n_iterations=snap["n_iterations"], has_estimate=snap["has_estimate"],
+                    VI=snap["VI"], CI=snap["CI"], stream=stream, **extra)
+    return iteration
+
+
 def reduce_over_ranks(total_ms, units, world, device):
     """Whole-job aggregation across ranks: the slowest rank's time (MAX) and the
     units all ranks processed (SUM).  One rank: the inputs unchanged."""
@@ -273,6 +286,11 @@ def run_mars(args):
     clocks = ClockSampler(local, args.clocks_csv.replace("{rank}", str(rank)) if args.clocks_csv
                           else os.path.join(tempfile.gettempdir(), f"mars_clocks_{rank}.csv"))
     time.sleep(0.3)
+    # the state after warm-up (the library's exact checkpoint): the profiled,
+    # control and end-to-end loops below replay the timed iterations from it,
+    # so every figure of the line is taken on the same iterations (MARS
+    # converges over its iterations and later ones spawn fewer vertices)
+    snap, it_snap = cache.get_state(stream=stream), it
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     captures0 = cache.info()["graph_captures"]
     timed = []
@@ -294,6 +312,7 @@ def run_mars(args):
     # ---- as many MARS steps again with every launch between CUDA events
     # (direct launches, no graph replay): the per-kernel device times
     sts = []
+    it = restore_state(cache, snap, it_snap, stream)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for k in range(args.steps):
@@ -364,7 +383,9 @@ def run_mars(args):
 
     # ---- the same loop timed on the host clock with the image in device
     # memory (the control for the end-to-end figure below)
+    it = restore_state(cache, snap, it_snap, stream)
     torch.cuda.synchronize()
+    cap_ctl = cache.info()["graph_captures"]
     t0 = time.perf_counter()
     ctl_verts = 0
     for k in range(args.steps):
@@ -372,10 +393,13 @@ def run_mars(args):
         it += 1
     torch.cuda.synchronize()
     ctl_s = time.perf_counter() - t0
+    cap_ctl = cache.info()["graph_captures"] - cap_ctl
 
     # ---- end to end through the C ABI with a pinned host image every step
     host_img = torch.empty(npx * 3, dtype=torch.float32, pin_memory=True).numpy()
+    it = restore_state(cache, snap, it_snap, stream)
     torch.cuda.synchronize()
+    cap_e2e = cache.info()["graph_captures"]
     t0 = time.perf_counter()
     e2e_verts = 0
     for k in range(args.steps):
@@ -388,7 +412,10 @@ def run_mars(args):
     e2e_s = time.perf_counter() - t0
     e2e = {"value": round(e2e_verts / e2e_s / 1e6, 3), "unit": UNIT, "h2d_bytes_per_step": 48,
            "d2h_bytes_per_step": npx * 3 * 4 + 512,
-           "host_clock_device_image": round(ctl_verts / ctl_s / 1e6, 3)}
+           "host_clock_device_image": round(ctl_verts / ctl_s / 1e6, 3),
+           "iterations": "the timed ones, replayed from the checkpoint taken before them",
+           "graph_captures": {"device_image_loop": cap_ctl,
+                              "host_image_loop": cache.info()["graph_captures"] - cap_e2e}}
 
     launches = sum(s["launches"] for s in timed) + args.steps * (2 if guided else 1)
     line = {

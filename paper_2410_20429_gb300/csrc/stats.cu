@@ -37,6 +37,32 @@ __device__ __forceinline__ T block_sum(T v, T* sh) {
 }
 
 // image sums in the statistics' precision: float64, or float32 for the
+// The RGB of a warp's 32 consecutive pixels [b, b + 32) -- lane l holds pixel
+// b + l -- written to a packed float RGB image as 24 aligned 16-byte stores of
+// the 384 bytes instead of 96 scattered 4-byte stores.  A page-locked host
+// image is written by this pass across the chip-to-chip link, where partial
+// writes cost far more than whole ones.  A partial warp, or an output that is
+// not 16-byte aligned, stores per channel.  `stage`: this warp's 96 floats of
+// shared memory.  b, npix and out are uniform over the warp.
+__device__ __forceinline__ void store_rgb_warp(float* __restrict__ out, int b, int npix, float x, float y, float z,
+                                               float* stage) {
+  const int lane = threadIdx.x & 31;
+  if (b + 32 <= npix && (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
+    stage[3 * lane] = x;
+    stage[3 * lane + 1] = y;
+    stage[3 * lane + 2] = z;
+    __syncwarp();
+    if (lane < 24)
+      reinterpret_cast<float4*>(out + 3 * (size_t)b)[lane] = reinterpret_cast<const float4*>(stage)[lane];
+    __syncwarp();
+  } else if (b + lane < npix) {
+    const size_t q = 3 * (size_t)(b + lane);
+    out[q] = x;
+    out[q + 1] = y;
+    out[q + 2] = z;
+  }
+}
+
 // float32-statistics variant
 template <typename T>
 __device__ __forceinline__ void add_sum(double* d64, float* d32, T v);
@@ -49,23 +75,25 @@ template <typename T>
 __global__ void __launch_bounds__(IMG_THREADS) k_img_accum(DevCache c, int npix, const IterArgs* __restrict__ itp,
                                                             float* out) {
   __shared__ T sh[IMG_THREADS / 32];
+  __shared__ __align__(16) float stage[IMG_THREADS * 3];
   if (c.ctr->any_overflow) return;
   const int n_prev = itp->n_prev;
   const float inv = 1.0f / (float)(n_prev + 1);
   T m0 = 0, m1 = 0, m2 = 0;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) {
-    const float4 I = c.img[p];
-    float4 rs = c.run_sum[p];
-    rs.x += I.x; rs.y += I.y; rs.z += I.z;
-    c.run_sum[p] = rs;
-    if (out) {
-      out[3 * p] = I.x;
-      out[3 * p + 1] = I.y;
-      out[3 * p + 2] = I.z;
+  // warp-uniform trip count: the warp stores its pixels together
+  for (int b = blockIdx.x * blockDim.x + (threadIdx.x & ~31); b < npix; b += gridDim.x * blockDim.x) {
+    const int p = b + (threadIdx.x & 31);
+    float4 I = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (p < npix) {
+      I = c.img[p];
+      float4 rs = c.run_sum[p];
+      rs.x += I.x; rs.y += I.y; rs.z += I.z;
+      c.run_sum[p] = rs;
+      m0 += (T)(rs.x * inv);
+      m1 += (T)(rs.y * inv);
+      m2 += (T)(rs.z * inv);
     }
-    m0 += (T)(rs.x * inv);
-    m1 += (T)(rs.y * inv);
-    m2 += (T)(rs.z * inv);
+    if (out) store_rgb_warp(out, b, npix, I.x, I.y, I.z, stage + 96 * (threadIdx.x >> 5));
   }
   m0 = block_sum<T>(m0, sh);
   m1 = block_sum<T>(m1, sh);
@@ -129,12 +157,12 @@ __global__ void __launch_bounds__(IMG_THREADS) k_img_est(DevCache c, int W, int 
 }
 
 __global__ void __launch_bounds__(IMG_THREADS) k_img_copy(DevCache c, int npix, float* out) {
+  __shared__ __align__(16) float stage[IMG_THREADS * 3];
   if (c.ctr->any_overflow) return;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) {
-    const float4 I = c.img[p];
-    out[3 * p] = I.x;
-    out[3 * p + 1] = I.y;
-    out[3 * p + 2] = I.z;
+  for (int b = blockIdx.x * blockDim.x + (threadIdx.x & ~31); b < npix; b += gridDim.x * blockDim.x) {
+    const int p = b + (threadIdx.x & 31);
+    const float4 I = p < npix ? c.img[p] : make_float4(0.f, 0.f, 0.f, 0.f);
+    store_rgb_warp(out, b, npix, I.x, I.y, I.z, stage + 96 * (threadIdx.x >> 5));
   }
 }
 
@@ -251,13 +279,13 @@ __global__ void __launch_bounds__(IMG_THREADS) k_img_combine(DevCache c, int npi
 }
 
 __global__ void __launch_bounds__(IMG_THREADS) k_img_comb_out(DevCache c, int npix, float* out) {
+  __shared__ __align__(16) float stage[IMG_THREADS * 3];
   const double w = *c.comb_w;
   const float inv = w > 0.0 ? (float)(1.0 / w) : 0.0f;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) {
-    const float4 a = c.comb[p];
-    out[3 * p] = a.x * inv;
-    out[3 * p + 1] = a.y * inv;
-    out[3 * p + 2] = a.z * inv;
+  for (int b = blockIdx.x * blockDim.x + (threadIdx.x & ~31); b < npix; b += gridDim.x * blockDim.x) {
+    const int p = b + (threadIdx.x & 31);
+    const float4 a = p < npix ? c.comb[p] : make_float4(0.f, 0.f, 0.f, 0.f);
+    store_rgb_warp(out, b, npix, a.x * inv, a.y * inv, a.z * inv, stage + 96 * (threadIdx.x >> 5));
   }
 }
 
