@@ -152,23 +152,31 @@ def alu_peak_tflops(num_sms):
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle samples during the timed region."""
+    """nvidia-smi clock / throttle samples (every 20 ms, each with its
+    timestamp); only samples taken between begin() and stop() -- the GPU under
+    load -- enter the summary."""
 
-    def __init__(self, gpu_index: int, out_path: str):
+    def __init__(self, gpu_index: int, out_path: str, interval_ms: int = 20):
         self.proc = None
         self.path = out_path
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+        self.t0 = None
+        q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.f = open(out_path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(int(interval_ms))],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
-    def stop(self) -> dict:
+    def begin(self) -> None:
+        self.t0 = time.time()
+
+    def stop(self, window: str = "") -> dict:
+        import datetime
+        t1 = time.time()
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -177,24 +185,29 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.f.close()
-        sm, smax, reasons = [], [], set()
+        sm, smax, reasons, total = [], [], set(), 0
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
             parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
+            total += 1
             try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                clk, cmax = float(parts[2]), float(parts[3])
             except ValueError:
                 continue
+            if self.t0 is not None and not (self.t0 - 0.02 <= ts <= t1 + 0.02):
+                continue
+            sm.append(clk)
+            smax.append(cmax)
             for k, nm in enumerate(names):
-                if parts[5 + k].lower() in ("active", "1", "yes"):
+                if parts[6 + k].lower() in ("active", "1", "yes"):
                     reasons.add(nm)
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
-                "samples": len(sm)}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples under load"], "samples_total": total}
+        return {"sm_mhz": float(np.median(sm)), "sm_min_mhz": float(min(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm), "window": window}
 
 
 def rel_mse(img, ref):
@@ -281,11 +294,9 @@ def run_mars(args):
     launch = cache.autotune(iteration=it, seed=seed, mode=M.MARS_MODE_MARS, repeats=2, stream=stream) \
         if not (args.no_autotune or args.launch) else cache.get_launch()
     torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
     clocks = ClockSampler(local, args.clocks_csv.replace("{rank}", str(rank)) if args.clocks_csv
                           else os.path.join(tempfile.gettempdir(), f"mars_clocks_{rank}.csv"))
-    time.sleep(0.3)
+    time.sleep(0.3)  # nvidia-smi starts sampling
     # the state after warm-up (the library's exact checkpoint): the profiled,
     # control and end-to-end loops below replay the timed iterations from it,
     # so every figure of the line is taken on the same iterations (MARS
@@ -295,13 +306,18 @@ def run_mars(args):
     captures0 = cache.info()["graph_captures"]
     timed = []
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.begin()
     evs[0].record(stream)
     for k in range(args.steps):
         timed.append(step(it, M.MARS_MODE_MARS))
         it += 1
         evs[k + 1].record(stream)
     torch.cuda.synchronize()
-    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
     per_step = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
     total_ms = sum(per_step)
     verts = sum(s["vertices"] for s in timed)
@@ -410,6 +426,9 @@ def run_mars(args):
         it += 1
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
+    # clock samples under load: the timed steps and their three replays (the
+    # same iterations), so that a short timed region still has several
+    clk = clocks.stop("the timed steps and their three replays")
     e2e = {"value": round(e2e_verts / e2e_s / 1e6, 3), "unit": UNIT, "h2d_bytes_per_step": 48,
            "d2h_bytes_per_step": npx * 3 * 4 + 512,
            "host_clock_device_image": round(ctl_verts / ctl_s / 1e6, 3),
