@@ -1,0 +1,74 @@
+"""CPU checks of the benchmark's measurement helpers: the clock-sample summary
+(window filtering, throttle reasons), relMSE and the single-rank aggregation."""
+import datetime
+import time
+
+import numpy as np
+import pytest
+
+import bench
+
+
+class _DoneProc:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def _sampler(tmp_path, rows, t0):
+    path = tmp_path / "clocks.csv"
+    path.write_text("".join(rows))
+    s = bench.ClockSampler.__new__(bench.ClockSampler)
+    s.proc, s.path, s.t0 = _DoneProc(), str(path), t0
+    s.f = open(tmp_path / "sink", "w")
+    return s
+
+
+def _row(ts, clk, reasons=("Not Active",) * 4):
+    stamp = datetime.datetime.fromtimestamp(ts).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+    return f"{stamp}, 0, {clk}, 2070, 500.0, 0x0, " + ", ".join(reasons) + "\n"
+
+
+def test_clock_summary_keeps_only_samples_under_load(tmp_path):
+    now = time.time()
+    rows = [_row(now - 5.0, 1000),                      # before begin(): idle, dropped
+            _row(now - 0.50, 2070), _row(now - 0.48, 2060), _row(now - 0.46, 2070),
+            _row(now + 30.0, 900)]                      # after stop(): dropped
+    st = _sampler(tmp_path, rows, t0=now - 0.6).stop("test window")
+    assert st["samples"] == 3 and st["sm_mhz"] == 2070.0 and st["sm_min_mhz"] == 2060.0
+    assert st["sm_max_mhz"] == 2070.0 and st["reasons"] == [] and st["window"] == "test window"
+
+
+def test_clock_summary_reports_throttle_reasons(tmp_path):
+    now = time.time()
+    rows = [_row(now - 0.3, 1800, ("Not Active", "Not Active", "Not Active", "Active")),
+            _row(now - 0.2, 1500, ("Active", "Not Active", "Not Active", "Not Active")),
+            "garbage line\n"]
+    st = _sampler(tmp_path, rows, t0=now - 0.4).stop()
+    assert st["samples"] == 2 and st["reasons"] == ["hw_slowdown", "sw_power_cap"]
+
+
+def test_clock_summary_without_samples(tmp_path):
+    st = _sampler(tmp_path, [], t0=time.time()).stop()
+    assert st["sm_mhz"] is None and st["reasons"] == ["no samples under load"]
+
+
+def test_rel_mse_basics():
+    rng = np.random.default_rng(0)
+    ref = rng.uniform(0.1, 2.0, size=(64, 64, 3))
+    assert bench.rel_mse(ref, ref) == 0.0
+    # a uniform 10 % error on every pixel: (0.1 R)^2 / (R^2 + 0.01), no outliers to drop
+    v = bench.rel_mse(1.1 * ref, ref)
+    expect = ((0.1 * ref) ** 2 / (ref ** 2 + 1e-2)).reshape(-1, 3).mean(axis=1)
+    k = int(np.ceil(1e-4 * expect.size))
+    assert v == pytest.approx(np.sort(expect)[:-k].mean(), rel=1e-12)
+    # one wild pixel is dropped with the 0.01 % largest terms
+    bad = ref.copy()
+    bad[3, 5] = 1e6
+    assert bench.rel_mse(bad, ref) < 1e-12
+
+
+def test_single_rank_aggregation_is_identity():
+    assert bench.reduce_over_ranks(12.5, 3e6, 1, "cpu") == (12.5, 3e6)
