@@ -210,10 +210,16 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm), "window": window}
 
 
-def rel_mse(img, ref):
+def rel_mse(img, ref, ref_var=None):
     """relMSE: mean over pixels and channels of (I - R)^2 / (R^2 + 1e-2), after
-    dropping the 0.01 % largest per-pixel terms."""
-    t = ((img - ref) ** 2 / (ref ** 2 + 1e-2)).reshape(-1, 3).mean(axis=1)
+    dropping the 0.01 % largest per-pixel terms.  With ``ref_var`` (the variance
+    of the reference's mean, per pixel and channel) each squared difference is
+    reduced by it: E[(I - R)^2] = Var(I) + bias^2 + Var(R), so the estimate no
+    longer charges the reference's own noise to the image."""
+    d2 = (img - ref) ** 2
+    if ref_var is not None:
+        d2 = d2 - ref_var
+    t = (d2 / (ref ** 2 + 1e-2)).reshape(-1, 3).mean(axis=1)
     k = int(math.ceil(1e-4 * t.size))
     if k > 0:
         t = np.sort(t)[:-k]
@@ -732,11 +738,18 @@ def efficiency(args, M, cfg, scene, cache, seed, it0, stream):
     img = torch.zeros(npx * 3, dtype=torch.float32, device="cuda")
     ref_cache = M.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, stream=stream)
     acc = torch.zeros(npx * 3, dtype=torch.float64, device="cuda")
+    acc2 = torch.zeros(npx * 3, dtype=torch.float64, device="cuda")
     for k in range(args.ref_spp):
         ref_cache.render_iteration(img, seed=777, iteration=k, mode=M.MARS_MODE_FIXED, collect=False,
                                    update_estimate=False, stream=stream)
-        acc += img.double()
-    ref = (acc / args.ref_spp).cpu().numpy().reshape(-1, 3)
+        x = img.double()
+        acc += x
+        acc2 += x * x
+    n_ref = args.ref_spp
+    ref_t = acc / n_ref
+    # variance of the reference's mean, from the spread of its iterations
+    ref_var = ((acc2 / n_ref - ref_t * ref_t).clamp_min(0.0) / max(n_ref - 1, 1)).cpu().numpy().reshape(-1, 3)
+    ref = ref_t.cpu().numpy().reshape(-1, 3)
     del ref_cache
 
     def timed(c, mode, n, it_base, weights=M.MARS_WEIGHTS_AWARE):
@@ -754,9 +767,9 @@ def efficiency(args, M, cfg, scene, cache, seed, it0, stream):
         torch.cuda.synchronize()
         s = e0.elapsed_time(e1) * 1e-3
         mean = (a / n).cpu().numpy().reshape(-1, 3)
-        r = rel_mse(mean, ref)
-        return {"relmse": r, "seconds": s, "efficiency": 1.0 / (r * s), "rays_per_pixel": rays / n / npx,
-                "spp": n}
+        r = rel_mse(mean, ref, ref_var)
+        return {"relmse": r, "relmse_raw": rel_mse(mean, ref), "seconds": s, "efficiency": 1.0 / (r * s),
+                "rays_per_pixel": rays / n / npx, "spp": n}
 
     mars = timed(cache, M.MARS_MODE_MARS, args.eff_spp, 20000)
     fixed_cache = M.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, stream=stream)
@@ -777,7 +790,8 @@ def efficiency(args, M, cfg, scene, cache, seed, it0, stream):
             "reference_spp": args.ref_spp,
             "protocol": "counts learned over warm-up + timed steps, then frozen; both estimators render "
                         f"{args.eff_spp} fresh iterations; reference = fixed-count MIS, {args.ref_spp} spp, "
-                        "other random numbers"}
+                        "other random numbers; relMSE with the variance of the reference's mean subtracted "
+                        "(relmse_raw without)"}
 
 
 def box_efficiency(args, M, stream, iterations=None):
@@ -960,7 +974,7 @@ def main():
     ap.add_argument("--no-efficiency", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--ref-spp", type=int, default=256)
+    ap.add_argument("--ref-spp", type=int, default=2048)
     ap.add_argument("--eff-spp", type=int, default=32)
     ap.add_argument("--ref-pixels-per-step", type=int, default=65536)
     ap.add_argument("--no-autotune", action="store_true")

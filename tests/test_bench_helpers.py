@@ -72,3 +72,45 @@ def test_rel_mse_basics():
 
 def test_single_rank_aggregation_is_identity():
     assert bench.reduce_over_ranks(12.5, 3e6, 1, "cpu") == (12.5, 3e6)
+
+
+def test_rel_mse_subtracts_the_reference_variance():
+    """A noise-free image against a noisy reference of known variance: the raw
+    relMSE charges the reference's noise to the image, the corrected one does
+    not (E[(I - R)^2] = Var(I) + bias^2 + Var(R))."""
+    rng = np.random.default_rng(1)
+    truth = rng.uniform(0.2, 2.0, size=(256 * 256, 3))
+    var = (0.05 * truth) ** 2
+    ref = truth + rng.normal(size=truth.shape) * np.sqrt(var)
+    raw = bench.rel_mse(truth, ref)
+    fixed = bench.rel_mse(truth, ref, var)
+    assert raw > 1e-3
+    assert abs(fixed) < 0.05 * raw
+    # an image with its own error keeps it: Var(I) survives the correction
+    img = truth + rng.normal(size=truth.shape) * 0.1 * truth
+    own = ((0.1 * truth) ** 2 / (truth ** 2 + 1e-2)).mean()
+    assert bench.rel_mse(img, ref, var) == pytest.approx(own, rel=0.05)
+
+
+def test_every_called_name_is_defined():
+    """Every plain function name bench.py calls is defined in it, imported or a
+    builtin (the GPU-only code paths cannot run here)."""
+    import ast
+    import builtins
+    import os
+    src = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "bench.py")).read()
+    tree = ast.parse(src)
+    defined = set(dir(builtins))
+    for node in ast.walk(tree):
+        if isinstance(node, (ast.FunctionDef, ast.ClassDef)):
+            defined.add(node.name)
+            defined.update(a.arg for a in node.args.args + node.args.kwonlyargs) if isinstance(node, ast.FunctionDef) \
+                else None
+        elif isinstance(node, (ast.Import, ast.ImportFrom)):
+            defined.update((a.asname or a.name).split(".")[0] for a in node.names)
+        elif isinstance(node, ast.Name) and isinstance(node.ctx, ast.Store):
+            defined.add(node.id)
+        elif isinstance(node, ast.arg):
+            defined.add(node.arg)
+    called = {n.func.id for n in ast.walk(tree) if isinstance(n, ast.Call) and isinstance(n.func, ast.Name)}
+    assert not called - defined, sorted(called - defined)
