@@ -192,6 +192,30 @@ def area_light_plane_scene(width: int = 4, height: int = 4,
     return _mk(quads, [0, 1], [], [], mats, cam, width, height, "area_light_plane")
 
 
+def occluded_light_plane_scene(width: int = 1, height: int = 1, fov: float = 30.0,
+                               occluder_x1: float = 0.0) -> Scene:
+    """The floor of ``area_light_plane_scene`` (y = 0, [-1, 1]^2, albedo 0.5)
+    under a 0.5 x 0.5 light of radiance 2 at height 1, with a black occluder
+    quad at height 0.7 over x in [-0.5, occluder_x1], z in [-0.5, 0.5] that
+    hides part of the light from the floor below the camera, so that both NEE
+    (visibility) and BSDF sampling (hitting the light) have a large relative
+    variance.  The camera looks straight down from (0, 0.5, 0) with vertical
+    field of view ``fov``: one pixel covers a patch of floor whose irradiance
+    varies across it."""
+    mats = [
+        _lambert(0.5, 0.5, 0.5),
+        _lambert(0.0, 0.0, 0.0),
+        _lambert(0.0, 0.0, 0.0, (2.0, 2.0, 2.0)),
+    ]
+    quads = [
+        [-1.0, 0.0, -1.0, 0.0, 0.0, 2.0, 2.0, 0.0, 0.0],
+        [-0.5, 0.7, -0.5, 0.0, 0.0, 1.0, occluder_x1 + 0.5, 0.0, 0.0],
+        [-0.25, 1.0, -0.25, 0.5, 0.0, 0.0, 0.0, 0.0, 0.5],  # e1 x e2 = -y
+    ]
+    cam = [0.0, 0.5, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1.0, fov]
+    return _mk(quads, [0, 1, 2], [], [], mats, cam, width, height, "occluded_light_plane")
+
+
 def guided_room_scene(seed: int = 0, width: int = 512, height: int = 512,
                       n_spheres: int = 64, n_lights: int = 4) -> Scene:
     """Closed 4 x 4 x 4 room (albedo 0.7) with ``n_spheres`` seeded spheres

@@ -229,6 +229,44 @@ def render(scene, *, grid_n, techniques, max_depth, mode=MODE_WARMUP, weights=WE
     return RenderResult(image, stats, hist, counters)
 
 
+def render_samples(scene, n, *, grid_n, techniques, max_depth, mode=MODE_WARMUP, weights=WEIGHTS_AWARE,
+                   seed=0, px=0, clamp_lo=0.05, clamp_hi=20.0, outlier=50.0, q_rr=None, q_s=None, valid=None,
+                   est=None, collect=True):
+    """Pixel ``px`` rendered in n independent iterations (Philox iteration k,
+    k < 65536): one call of orc_render per iteration on reused buffers, so that
+    many samples of one pixel are cheap.  Returns (values [n, 3] float64, the
+    statistics summed over the n iterations [cells, 3, 8], the counters summed
+    over them)."""
+    L = lib()
+    if n > 65536:
+        raise ValueError("at most 65536 iterations per key")
+    cells = grid_n ** 3
+    npx = scene.width * scene.height
+    q_rr = np.ascontiguousarray(np.zeros((cells, NT, 3)) if q_rr is None else q_rr, np.float32).reshape(cells, NT, 3)
+    q_s = np.ascontiguousarray(np.zeros((cells, NT, 3)) if q_s is None else q_s, np.float32).reshape(cells, NT, 3)
+    valid = np.ascontiguousarray(np.zeros((cells, NT)) if valid is None else valid, np.uint8).reshape(cells, NT)
+    has_est = est is not None
+    est = np.ascontiguousarray(np.ones((npx, 3)) if est is None else est, np.float32).reshape(npx, 3)
+    image = np.zeros((npx, 3), np.float64)
+    stats = np.zeros((cells, NT, NSTAT), np.float64)
+    hist = np.zeros((cells, GUIDE_BINS), np.float64)
+    counters = np.zeros(8, np.float64)
+    sh = _SceneHolder(scene)
+    P = Params(grid_n, techniques, max_depth, mode, weights, seed, 0, 0, clamp_lo, clamp_hi, outlier,
+               int(has_est), int(bool(collect)), 0.0)
+    S = State(_p(q_rr, ct.c_float), _p(q_s, ct.c_float), _p(valid, ct.c_uint8), ct.POINTER(ct.c_float)(),
+              _p(est, ct.c_float), ct.POINTER(ct.c_int32)(), _p(image, ct.c_double), _p(stats, ct.c_double),
+              _p(hist, ct.c_double), _p(counters, ct.c_double))
+    out = np.zeros((n, 3), np.float64)
+    for k in range(n):
+        P.iteration = k
+        rc = L.orc_render(ct.byref(sh.desc), ct.byref(P), ct.byref(S), int(px), int(px) + 1)
+        if rc != 0:
+            raise ValueError(f"orc_render failed with {rc}")
+        out[k] = image[px]
+    return out, stats, counters
+
+
 def image_stats(width, height, img, run_sum, n_prev, outlier=50.0, drop_k=0):
     """Returns (V_I, new run_sum, pixel estimate).  drop_k > 0: the rejection of
     the bidirectional application (Sec. 5.1) instead of the outlier clamp."""

@@ -390,21 +390,15 @@ def test_checkpoint_resume_continues_the_run(mars, octree):
 def test_relmse_against_a_long_reference_matches_the_oracle(mars, orc):
     """Third agreement criterion: the relMSE of the CUDA path's N-iteration
     image and of the oracle's (same random numbers, same teacher-forced counts)
-    against a long reference render agree within 2 % of the oracle's.  The
-    reference is a 2048-iteration fixed-count render of the CUDA path with other
-    random numbers (the oracle's speed rules out a 64k-spp one here)."""
-    import torch
+    against a 65536-samples-per-pixel reference agree within 2 % of the
+    oracle's.  The reference is the oracle's own fixed-count render with other
+    random numbers, stored by tests/golden/make_box_reference.py."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "box_32x32_fixed_65536spp.txt")
+    ref = np.loadtxt(path)[:, :3]
     cfg = W.config_box(32, 32)
     scene, cache = _make(mars, cfg)
-    ref_cache = mars.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth)
     npx = cfg.scene.n_pixels
-    img = torch.zeros(npx * 3, dtype=torch.float32, device="cuda")
-    acc = torch.zeros(npx * 3, dtype=torch.float64, device="cuda")
-    for k in range(2048):
-        ref_cache.render_iteration(img, seed=999, iteration=k, mode=mars.MARS_MODE_FIXED, collect=False,
-                                   update_estimate=False)
-        acc += img.double()
-    ref = (acc / 2048).cpu().numpy().reshape(-1, 3)
     q_rr, q_s, valid = W.random_count_fields(cfg.n_cells, seed=141, lo=0.1, hi=3.0)
     est = W.random_pixel_estimate(npx, seed=142, lo=0.05, hi=0.5)
     cache.set_state(q_rr=q_rr, q_s=q_s, valid=valid, pixel_estimate=est, has_estimate=True, n_iterations=1)
