@@ -58,9 +58,38 @@ SHADOW_RAY_BYTES = 36   # SH0, SH1 and the work-list entry per traced shadow ray
 SLOT_BYTES = RAY_BYTES + HIT_BYTES + V0_BYTES + VERT_EST_BYTES + VERT_GUIDE_BYTES + SAMPLE_BYTES
 
 
+# Algorithmic bytes: the minimum traffic per unit of the path, whatever the
+# record layout -- a ray 64 B (origin, direction, throughput, pixel/lineage),
+# a hit 16 B, a vertex record 32 B, a shadow ray 32 B plus a 16 B result, a
+# sample value 16 B; count reads and statistics atomics stay in L2.
+ALG_RAY, ALG_RAY_TRACE, ALG_HIT, ALG_VERTEX, ALG_SHADOW, ALG_RESULT, ALG_VALUE = 64, 32, 16, 32, 32, 16, 16
+
+
+def algorithmic_bytes(entries, pixels, shadow_traced):
+    """Minimum HBM bytes each wave kernel must move for one step at the
+    per-unit minima above (each record written once by its producer and read
+    once by its consumer; camera rays are generated in registers, and an NEE
+    sample of value zero needs no shadow ray and no result): trace reads a
+    child ray's origin and direction and writes its hit; shade reads the ray
+    and the hit, writes the vertex record, every child ray and every shadow
+    ray; shadow reads the shadow rays and writes their results; reverse reads
+    the vertex record, every child's value and every NEE result, and writes the
+    slot's value."""
+    children = entries - pixels
+    return {
+        "k_trace": ALG_RAY_TRACE * children + ALG_HIT * entries,
+        "k_shade": (ALG_RAY * children + (ALG_HIT + ALG_VERTEX) * entries + ALG_RAY * children
+                    + ALG_SHADOW * shadow_traced),
+        "k_shadow": (ALG_SHADOW + ALG_RESULT) * shadow_traced,
+        "k_reverse": (ALG_VERTEX + ALG_VALUE) * entries + ALG_VALUE * children + ALG_RESULT * shadow_traced,
+    }
+
+
 def kernel_bytes(entries, pixels, est_v, traced, shadows, shadow_traced, guided):
-    """Minimum HBM bytes each wave kernel must move for one step (its inputs
-    read once, its outputs written once)."""
+    """HBM bytes each wave kernel moves for one step with this design's arena
+    records (csrc/internal.h: 80 B rays, 48 B estimator records, ...), inputs
+    read once and outputs written once: the layout bytes, reported beside the
+    algorithmic bytes."""
     children = entries - pixels
     guide = VERT_GUIDE_BYTES * (traced - pixels) if guided else 0
     return {
@@ -347,9 +376,11 @@ def run_mars(args):
 
     # ---- dominant kernel roofline (live CUDA-event times of every launch)
     guided = bool(cfg.techniques & W.TECH_GUIDED)
-    kb = kernel_bytes(sum(s["wave_entries"] for s in sts), npx * args.steps,
+    lb = kernel_bytes(sum(s["wave_entries"] for s in sts), npx * args.steps,
                       sum(s["estimator_vertices"] for s in sts), verts_prof, sum(s["shadow_entries"] for s in sts),
                       sum(s["shadow_traced"] for s in sts), guided)
+    kb = algorithmic_bytes(sum(s["wave_entries"] for s in sts), npx * args.steps,
+                           sum(s["shadow_traced"] for s in sts))
     kms = {k: sum(s[k[2:] + "_ms"] for s in sts) for k in kb}
     nlaunch = {k: sum(s["wave_launches"] for s in sts) for k in kb}
     nlaunch["k_shadow"] = sum(max(s["wave_launches"] - s["tiles"], 0) for s in sts)  # no shadow launch at d = D
@@ -369,9 +400,12 @@ def run_mars(args):
                              "launch_ms": round(ms_launch, 4)}
         else:
             a = kb[k] / max(nlaunch[k], 1) / (ms_launch * 1e-3) / 1e9
+            al = lb[k] / max(nlaunch[k], 1) / (ms_launch * 1e-3) / 1e9
             per_kernel[k] = {"bound": "hbm", "achieved": round(a, 1), "peak": hbm, "unit": "GB/s",
                              "frac": round(a / hbm, 4), "per_launch": int(kb[k] / max(nlaunch[k], 1)),
-                             "launch_ms": round(ms_launch, 4)}
+                             "launch_ms": round(ms_launch, 4),
+                             "layout_bytes": {"per_launch": int(lb[k] / max(nlaunch[k], 1)),
+                                              "achieved": round(al, 1), "frac": round(al / hbm, 4)}}
     tw = [[sum(s["trace_work"][k][q] for s in sts) for q in range(4)] for k in range(2)]
     n_closest = max(sum(s["wave_entries"] for s in sts), 1)
     n_shadow = max(sum(s["shadow_traced"] for s in sts), 1)
@@ -393,6 +427,9 @@ def run_mars(args):
                 "peak_kind": peak_kind if d0["bound"] == "hbm" else
                 "derived: SMs x 128 FP32 lanes x 2 x max SM clock (measured)",
                 "per_launch": d0["per_launch"], "launch_ms": d0["launch_ms"],
+                "bytes_model": "algorithmic: per-unit minima (ray 64 B, hit 16, vertex record 32, shadow ray 32 "
+                               "+ 16 result, sample value 16) x units; layout_bytes: this design's records",
+                "layout_bytes": d0.get("layout_bytes"),
                 "kernels": per_kernel,
                 "kernel_ms_per_step": {k: round(v / args.steps, 4) for k, v in kms.items()}}
     roofline["kernel_ms_per_step"]["image"] = round(sum(s["image_ms"] for s in sts) / args.steps, 4)
@@ -493,7 +530,8 @@ def run_mars(args):
         # iterations on a 64 x 64 image are still noisy
         line["efficiency_box_16"] = box_efficiency(args, M, stream, iterations=16)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(cfg, args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(cfg, args.cpu_seconds, learn_iterations=args.warmup, warmup=args.warmup,
+                                            iteration=it_snap)
     if world > 1:
         dist.barrier()
     if rank == 0:
@@ -563,6 +601,10 @@ def large_scene(args, M, stream):
            "progressive": {"vi_drop_brightest": 10, "combined_iterations": 6,
                            "combined_weight": round(cache.combined_image(stream=stream)[1], 4),
                            "VI": [round(s["VI"], 5) for s in timed + sts]}}
+    if not args.no_efficiency:
+        out["efficiency"] = efficiency(args, M, cfg, scene, cache, 77, it, stream, ref_spp=args.large_ref_spp,
+                                       cache_kw=dict(octree=True, max_leaves=65536, split_samples=4096.0),
+                                       unaware=False)
     if not args.no_precision:
         # float32 versus float64 statistics at this size (the large bidirectional
         # workload's precision comparison), on the learned state and tree
@@ -638,6 +680,9 @@ def largest_scene(args, M, stream):
            "mean_beta": [round(sum(s["mean_beta"][t] for s in sts) / 2, 4) for t in range(3)],
            "octree_leaves": int(cache.info()["oct_n_leaves"]),
            "device_gb": round(cache.info()["device_bytes"] / 1e9, 2)}
+    if not args.no_efficiency:
+        out["efficiency"] = efficiency(args, M, cfg, scene, cache, 91, it, stream, ref_spp=args.large_ref_spp,
+                                       cache_kw=kw, unaware=False)
     if not args.no_precision:
         from paper_2410_20429_gb300 import precision
         g = cache.get_state(stream=stream)
@@ -729,28 +774,34 @@ def precision_study(cfg, cache, seed, it, stream):
     return out
 
 
-def efficiency(args, M, cfg, scene, cache, seed, it0, stream):
+def efficiency(args, M, cfg, scene, cache, seed, it0, stream, ref_spp=None, cache_kw=None, unaware=True):
     """Equal-time efficiency 1/(relMSE * s): MARS with the counts learned so far
     (frozen: no statistics, no update) vs fixed-count MIS (beta = 1), both
-    timed with CUDA events, against a long fixed-count reference."""
+    timed with CUDA events, against a long fixed-count reference.  Like for
+    like: the fixed-count arm samples the guided technique from the MARS
+    cache's learned guide (same cells: an octree cache's tree is copied too),
+    so the two arms differ in their counts alone; the guided workloads also
+    report fixed-count MIS with a guide it learned itself over as many
+    iterations, and with the uniform guide of a fresh cache."""
     import torch
     npx = cfg.scene.n_pixels
+    n_ref = ref_spp or args.ref_spp
+    cache_kw = cache_kw or {}
     img = torch.zeros(npx * 3, dtype=torch.float32, device="cuda")
-    ref_cache = M.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, stream=stream)
+    ref_cache = M.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, stream=stream, **cache_kw)
     acc = torch.zeros(npx * 3, dtype=torch.float64, device="cuda")
     acc2 = torch.zeros(npx * 3, dtype=torch.float64, device="cuda")
-    for k in range(args.ref_spp):
+    for k in range(n_ref):
         ref_cache.render_iteration(img, seed=777, iteration=k, mode=M.MARS_MODE_FIXED, collect=False,
                                    update_estimate=False, stream=stream)
         x = img.double()
         acc += x
         acc2 += x * x
-    n_ref = args.ref_spp
     ref_t = acc / n_ref
     # variance of the reference's mean, from the spread of its iterations
     ref_var = ((acc2 / n_ref - ref_t * ref_t).clamp_min(0.0) / max(n_ref - 1, 1)).cpu().numpy().reshape(-1, 3)
     ref = ref_t.cpu().numpy().reshape(-1, 3)
-    del ref_cache
+    del ref_cache, acc, acc2
 
     def timed(c, mode, n, it_base, weights=M.MARS_WEIGHTS_AWARE):
         a = torch.zeros(npx * 3, dtype=torch.float64, device="cuda")
@@ -771,27 +822,54 @@ def efficiency(args, M, cfg, scene, cache, seed, it0, stream):
         return {"relmse": r, "relmse_raw": rel_mse(mean, ref), "seconds": s, "efficiency": 1.0 / (r * s),
                 "rays_per_pixel": rays / n / npx, "spp": n}
 
+    guided = bool(cfg.techniques & W.TECH_GUIDED)
     mars = timed(cache, M.MARS_MODE_MARS, args.eff_spp, 20000)
-    fixed_cache = M.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, stream=stream)
+    learned = cache.get_state(stream=stream)
+    fixed_cache = M.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, stream=stream, **cache_kw)
+    if guided:
+        tree = {"oct_nodes": learned["oct_nodes"], "oct_leaf_level": learned["oct_leaf_level"]} \
+            if "oct_nodes" in learned else {}
+        fixed_cache.set_state(guide_cdf=learned["guide_cdf"], stream=stream, **tree)
     fixed = timed(fixed_cache, M.MARS_MODE_FIXED, args.eff_spp, 20000)
-    # the budget-unaware balance heuristic (weights from the sampling densities
-    # alone) learns its own counts over as many iterations, then renders alike
-    un_cache = M.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, stream=stream)
-    for k in range(it0):
-        un_cache.render_iteration(img, seed=seed, iteration=k, mode=M.MARS_MODE_WARMUP if k < args.warmup
-                                  else M.MARS_MODE_MARS, weights=M.MARS_WEIGHTS_UNAWARE, update_estimate=True,
-                                  stream=stream)
-        un_cache.update_counts(stream=stream)
-    unaware = timed(un_cache, M.MARS_MODE_MARS, args.eff_spp, 20000, weights=M.MARS_WEIGHTS_UNAWARE)
-    unaware["learning_iterations"] = it0
-    unaware["ratio_vs_aware"] = unaware["efficiency"] / mars["efficiency"]
-    return {"mars": mars, "fixed_count_mis": fixed, "ratio": mars["efficiency"] / fixed["efficiency"],
-            "budget_unaware": unaware,
-            "reference_spp": args.ref_spp,
-            "protocol": "counts learned over warm-up + timed steps, then frozen; both estimators render "
-                        f"{args.eff_spp} fresh iterations; reference = fixed-count MIS, {args.ref_spp} spp, "
-                        "other random numbers; relMSE with the variance of the reference's mean subtracted "
-                        "(relmse_raw without)"}
+    del fixed_cache
+    out = {"mars": mars, "fixed_count_mis": fixed, "ratio": mars["efficiency"] / fixed["efficiency"],
+           "reference_spp": n_ref, "learning_iterations": it0,
+           "protocol": "counts learned over the warm-up and timed iterations, then frozen; both arms render "
+                       f"{args.eff_spp} fresh iterations with the same learned guide (fixed-count MIS: beta = 1); "
+                       f"reference = fixed-count MIS, {n_ref} spp, other random numbers; relMSE with the variance "
+                       "of the reference's mean subtracted (relmse_raw without)"}
+    if guided:
+        # fixed-count MIS that learns its own guide from its own deposits over as
+        # many iterations, and with the uniform guide of a fresh cache
+        own = M.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, stream=stream, **cache_kw)
+        for k in range(it0):
+            own.render_iteration(img, seed=seed, iteration=k, mode=M.MARS_MODE_FIXED, update_estimate=True,
+                                 stream=stream)
+            own.update_counts(stream=stream)
+        f_own = timed(own, M.MARS_MODE_FIXED, args.eff_spp, 20000)
+        del own
+        uni = M.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, stream=stream, **cache_kw)
+        f_uni = timed(uni, M.MARS_MODE_FIXED, args.eff_spp, 20000)
+        del uni
+        out["fixed_count_mis_own_guide"] = f_own
+        out["ratio_vs_own_guide"] = mars["efficiency"] / f_own["efficiency"]
+        out["fixed_count_mis_uniform_guide"] = f_uni
+        out["ratio_vs_uniform_guide"] = mars["efficiency"] / f_uni["efficiency"]
+    if unaware:
+        # the budget-unaware balance heuristic (weights from the sampling densities
+        # alone) learns its own counts over as many iterations, then renders alike
+        un_cache = M.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, stream=stream, **cache_kw)
+        for k in range(it0):
+            un_cache.render_iteration(img, seed=seed, iteration=k, mode=M.MARS_MODE_WARMUP if k < args.warmup
+                                      else M.MARS_MODE_MARS, weights=M.MARS_WEIGHTS_UNAWARE, update_estimate=True,
+                                      stream=stream)
+            un_cache.update_counts(stream=stream)
+        un = timed(un_cache, M.MARS_MODE_MARS, args.eff_spp, 20000, weights=M.MARS_WEIGHTS_UNAWARE)
+        del un_cache
+        un["learning_iterations"] = it0
+        un["ratio_vs_aware"] = un["efficiency"] / mars["efficiency"]
+        out["budget_unaware"] = un
+    return out
 
 
 def box_efficiency(args, M, stream, iterations=None):
@@ -832,17 +910,33 @@ def box_efficiency(args, M, stream, iterations=None):
     return eff
 
 
+_STATE_CACHE = {}
+
+
+def _mars_inputs(state_path):
+    """The teacher-forced MARS inputs (count fields, pixel estimate, guide CDF)
+    saved by the GPU run, loaded once per worker process."""
+    if state_path not in _STATE_CACHE:
+        z = np.load(state_path)
+        _STATE_CACHE[state_path] = {k: z[k] for k in z.files}
+    d = _STATE_CACHE[state_path]
+    return dict(mode=1, q_rr=d["q_rr"], q_s=d["q_s"], valid=d["valid"], est=d["pixel_estimate"],
+                guide_cdf=d.get("guide_cdf"))
+
+
 def _oracle_chunks(job):
     """Worker of the multi-core CPU baseline (a spawned process): render the
-    given pixel runs of one iteration with the oracle as it stands; returns
-    (path vertices, seconds)."""
-    scene, grid_n, techniques, max_depth, runs = job
+    given pixel runs of one iteration with the oracle as it stands -- in MARS
+    mode from the GPU run's state when `state_path` is given, else with
+    beta = 1; returns (path vertices, seconds)."""
+    scene, grid_n, techniques, max_depth, runs, state_path = job
     import oracle
+    kw = _mars_inputs(state_path) if state_path else {}
     verts, t = 0, 0.0
     for iteration, b, e in runs:
         t0 = time.perf_counter()
         r = oracle.render(scene, grid_n=grid_n, techniques=techniques, max_depth=max_depth, iteration=iteration,
-                          seed=3, px_begin=b, px_end=e)
+                          seed=3, px_begin=b, px_end=e, **kw)
         t += time.perf_counter() - t0
         verts += r.vertices
     return verts, t
@@ -859,17 +953,109 @@ def _cpu_model():
     return platform.processor() or platform.machine()
 
 
-def cpu_baseline(cfg, seconds, reference_arm=False):
-    """The CPU oracle as it stands on the host cores, warm-up mode (beta = 1):
-    one thread on 4096-pixel runs spread evenly over the image (about `seconds`
-    of work; runs of that size keep the oracle's per-call set-up, a copy of the
+def _oracle_learn_chunk(job):
+    """Worker (a spawned process) of the oracle's own fixed-point learning: one
+    iteration over a share of the pixels with statistics and guide deposits;
+    returns (pixel runs, statistics, guide deposits, counters)."""
+    scene, grid_n, techniques, max_depth, runs, iteration, state_path = job
+    import oracle
+    kw = _mars_inputs(state_path) if state_path else {}
+    stats = hist = None
+    ctr = np.zeros(8)
+    imgs = []
+    for b, e in runs:
+        r = oracle.render(scene, grid_n=grid_n, techniques=techniques, max_depth=max_depth, iteration=iteration,
+                          seed=3, px_begin=b, px_end=e, **kw)
+        imgs.append((b, e, r.image[b:e].copy()))
+        stats = r.stats if stats is None else stats + r.stats
+        hist = r.hist if hist is None else hist + r.hist
+        ctr += r.counters
+    return imgs, stats, hist, ctr
+
+
+def oracle_learned_state(cfg, pool, cores, iterations, warmup):
+    """The oracle's own MARS state after `iterations` fixed-point iterations of
+    the whole image (the first `warmup` with beta = 1), in spawned processes:
+    each iteration renders every pixel with statistics, then the image
+    statistics, the count update and the guide update run on the sums -- the
+    same protocol that produces the GPU's state before its timed steps, with
+    every input from the oracle itself.  Returns the path of an .npz with the
+    count fields, pixel estimate and guide CDF."""
+    import oracle
+    sc = cfg.scene
+    npx = sc.n_pixels
+    cells = cfg.n_cells
+    chunk = 4096
+    runs = [(b, min(npx, b + chunk)) for b in range(0, npx, chunk)]
+    q_rr = np.zeros((cells, 3, 3), np.float32)
+    q_s = np.zeros((cells, 3, 3), np.float32)
+    valid = np.zeros((cells, 3), np.uint8)
+    hist_acc = np.zeros((cells, oracle.GUIDE_BINS))
+    cdf = np.tile((np.arange(1, oracle.GUIDE_BINS + 1) / oracle.GUIDE_BINS).astype(np.float32), (cells, 1))
+    run_sum = np.zeros((npx, 3))
+    est = np.ones((npx, 3), np.float32)
+    path = os.path.join(tempfile.gettempdir(), f"mars_oracle_state_{os.getpid()}.npz")
+    for it in range(iterations):
+        state_path = None
+        if it >= warmup:
+            np.savez(path, q_rr=q_rr, q_s=q_s, valid=valid, pixel_estimate=est, guide_cdf=cdf)
+            state_path = path
+            _STATE_CACHE.pop(path, None)
+        jobs = [(sc, cfg.grid_n, cfg.techniques, cfg.max_depth, runs[k::cores], it, state_path)
+                for k in range(cores)]
+        res = list(pool.map(_oracle_learn_chunk, jobs))
+        img = np.zeros((npx, 3))
+        stats = np.zeros((cells, 3, 8))
+        ctr = np.zeros(8)
+        for imgs, st, h, c in res:
+            for b, e, rows in imgs:
+                img[b:e] = rows
+            if st is not None:
+                stats += st
+                hist_acc += h
+            ctr += c
+        vi, run_sum, est64 = oracle.image_stats(sc.width, sc.height, img, run_sum, it)
+        est = est64.astype(np.float32)
+        q_rr, q_s, valid = oracle.update_counts(stats, vi, ctr[0] / npx, cfg.techniques, q_rr, q_s, valid)
+        if cfg.techniques & W.TECH_GUIDED:
+            cdf = oracle.guide_update(hist_acc)
+    np.savez(path, q_rr=q_rr, q_s=q_s, valid=valid, pixel_estimate=est, guide_cdf=cdf)
+    return path
+
+
+def cpu_baseline(cfg, seconds, learn_iterations=3, warmup=3, iteration=3):
+    """The CPU oracle as it stands on the host cores, on the work of the GPU's
+    timed steps: MARS iterations (index `iteration` on) from the state the
+    oracle itself learned over `learn_iterations` iterations of the whole image
+    (the first `warmup` with beta = 1; count fields, pixel estimate and guide),
+    as the GPU's timed steps start from the state of its own warm-up.  One
+    thread on 4096-pixel runs spread evenly over the image (about `seconds` of
+    work; runs of that size keep the oracle's per-call set-up, a copy of the
     cache fields and guide tables, from dominating), and the whole image split
-    into 4096-pixel runs over one spawned process per host core (started and
-    warmed before the clock starts)."""
+    into 4096-pixel runs over one spawned process per host core (started before
+    the clock starts)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
     import oracle
     sc = cfg.scene
     oracle.build()
     chunk = 4096
+    cores = max(1, os.cpu_count() or 1)
+    out = {"unit": UNIT, "kind": "oracle", "cpu": _cpu_model(), "nproc": os.cpu_count()}
+    # all host cores: spawned workers (a process forked after CUDA was used hangs)
+    pool = cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn"))
+    try:
+        t0 = time.perf_counter()
+        state_path = oracle_learned_state(cfg, pool, cores, learn_iterations, min(warmup, learn_iterations))
+        learn_s = time.perf_counter() - t0
+    except Exception as exc:  # no spawned processes: learn nothing, time warm-up iterations
+        pool.shutdown()
+        pool, state_path, learn_s = None, None, 0.0
+        out["multi_core_error"] = repr(exc)[:200]
+    kw = _mars_inputs(state_path) if state_path else {}
+    what = (f"MARS iterations from the oracle's own state after {learn_iterations} whole-image iterations "
+            f"({min(warmup, learn_iterations)} with beta = 1; learned in {learn_s:.1f} s)") if state_path \
+        else "warm-up iterations (beta = 1)"
 
     def run(npx_sample, it):
         stride = max(1, sc.n_pixels // npx_sample)
@@ -879,43 +1065,45 @@ def cpu_baseline(cfg, seconds, reference_arm=False):
         for s0 in starts:
             t0 = time.perf_counter()
             r = oracle.render(sc, grid_n=cfg.grid_n, techniques=cfg.techniques, max_depth=cfg.max_depth,
-                              iteration=it, seed=3, px_begin=s0, px_end=min(sc.n_pixels, s0 + chunk))
+                              iteration=it, seed=3, px_begin=s0, px_end=min(sc.n_pixels, s0 + chunk), **kw)
             t += time.perf_counter() - t0
             verts += r.vertices
         return verts, t, len(starts) * chunk
 
-    v, t, n = run(chunk, 0)
+    v, t, n = run(chunk, iteration)
     target = max(chunk, int(chunk * seconds / max(t, 1e-3)))
-    v, t, n = run(min(target, sc.n_pixels), 1)
+    v, t, n = run(min(target, sc.n_pixels), iteration + 1)
     single = round(v / t / 1e6, 5)
-    out = {"value": single, "unit": UNIT, "cores": 1, "kind": "oracle",
-           "sample": f"{n} pixels of the {sc.width}x{sc.height} workload (4096-pixel runs evenly spread), "
-                     f"one warm-up iteration (beta = 1), {int(v)} path vertices in {t:.1f} s",
-           "cpu": _cpu_model(), "nproc": os.cpu_count()}
-    # all host cores: spawned workers (a process forked after CUDA was used hangs)
-    import concurrent.futures as cf
-    import multiprocessing as mp
-    cores = max(1, os.cpu_count() or 1)
-    # the whole image, repeated (successive iterations) to about `seconds` of
-    # single-core work in all
-    images = max(1, int(round(seconds / max(t * sc.n_pixels / max(n, 1), 1e-3))))
-    runs = [(it, b, min(sc.n_pixels, b + chunk)) for it in range(1, images + 1)
-            for b in range(0, sc.n_pixels, chunk)]
-    jobs = [(sc, cfg.grid_n, cfg.techniques, cfg.max_depth, runs[k::cores]) for k in range(cores)]
-    try:
-        with cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn")) as pool:
-            list(pool.map(_oracle_chunks, [(sc, cfg.grid_n, cfg.techniques, cfg.max_depth, [(0, 0, 64)])] * cores))
+    out.update({"value": single, "cores": 1,
+                "sample": f"{n} pixels of the {sc.width}x{sc.height} workload (4096-pixel runs evenly spread), "
+                          f"one iteration: {what}, {int(v)} path vertices in {t:.1f} s"})
+    if pool is not None:
+        # the whole image, repeated (successive iterations) to about `seconds` of
+        # single-core work in all
+        images = max(1, int(round(seconds / max(t * sc.n_pixels / max(n, 1), 1e-3))))
+        runs = [(iteration + it, b, min(sc.n_pixels, b + chunk)) for it in range(1, images + 1)
+                for b in range(0, sc.n_pixels, chunk)]
+        jobs = [(sc, cfg.grid_n, cfg.techniques, cfg.max_depth, runs[k::cores], state_path) for k in range(cores)]
+        try:
+            list(pool.map(_oracle_chunks, [(sc, cfg.grid_n, cfg.techniques, cfg.max_depth, [(0, 0, 64)],
+                                            state_path)] * cores))
             t0 = time.perf_counter()
             res = list(pool.map(_oracle_chunks, jobs))
             wall = time.perf_counter() - t0
-        verts = sum(r[0] for r in res)
-        out.update({"value": round(verts / wall / 1e6, 5), "cores": cores,
-                    "sample": f"the whole {sc.width}x{sc.height} image {images} times ({sc.n_pixels} pixels in "
-                              f"4096-pixel runs over {cores} processes), warm-up iterations (beta = 1), "
-                              f"{int(verts)} path vertices in {wall:.2f} s",
-                    "single_thread": {"value": single, "sample": out["sample"]}})
-    except Exception as exc:  # keep the single-thread figure if processes cannot be spawned
-        out["multi_core_error"] = repr(exc)[:200]
+            verts = sum(r[0] for r in res)
+            out.update({"value": round(verts / wall / 1e6, 5), "cores": cores,
+                        "sample": f"the whole {sc.width}x{sc.height} image {images} times ({sc.n_pixels} pixels in "
+                                  f"4096-pixel runs over {cores} processes), {what}, "
+                                  f"{int(verts)} path vertices in {wall:.2f} s",
+                        "single_thread": {"value": single, "sample": out["sample"]}})
+        except Exception as exc:
+            out["multi_core_error"] = repr(exc)[:200]
+        pool.shutdown()
+    if state_path:
+        try:
+            os.remove(state_path)
+        except OSError:
+            pass
     return out
 
 
@@ -937,11 +1125,11 @@ def run_reference(args):
     times, verts = [], []
     # one spawned process per host core, started and warmed before the steps
     with cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn")) as pool:
-        list(pool.map(_oracle_chunks, [(sc, cfg.grid_n, cfg.techniques, cfg.max_depth, [(0, 0, 64)])] * cores))
+        list(pool.map(_oracle_chunks, [(sc, cfg.grid_n, cfg.techniques, cfg.max_depth, [(0, 0, 64)], None)] * cores))
         for k in range(args.warmup + args.steps):
             b = (k * 7919 * 64) % max(1, sc.n_pixels - per_step + 1)
             runs = [(k, b + q, min(b + per_step, b + q + chunk)) for q in range(0, per_step, chunk)]
-            jobs = [(sc, cfg.grid_n, cfg.techniques, cfg.max_depth, runs[w::cores]) for w in range(cores)]
+            jobs = [(sc, cfg.grid_n, cfg.techniques, cfg.max_depth, runs[w::cores], None) for w in range(cores)]
             t0 = time.perf_counter()
             res = list(pool.map(_oracle_chunks, jobs))
             dt = time.perf_counter() - t0
@@ -975,6 +1163,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-spp", type=int, default=2048)
+    ap.add_argument("--large-ref-spp", type=int, default=256,
+                    help="reference iterations of the efficiency comparison on the heightfield workloads")
     ap.add_argument("--eff-spp", type=int, default=32)
     ap.add_argument("--ref-pixels-per-step", type=int, default=65536)
     ap.add_argument("--no-autotune", action="store_true")

@@ -166,7 +166,19 @@ typedef struct {
  *   combination of iterations): 1 adds this iteration's image with weight
  *   1 / max(V_I, 1e-12) to the cache's combined image, 2 starts a new
  *   combination with it; needs update_estimate.  Read it with
- *   mars_cache_combined_image. */
+ *   mars_cache_combined_image.
+ * Pixel ranges (px_begin < px_end <= pixels): only the camera paths of those
+ *   pixels are traced.  Every camera path is independent within an iteration
+ *   (Sec. 3.1 "Random walks"), and its random numbers depend on its pixel index
+ *   only, so a frame split into ranges rendered by several caches (one per GPU)
+ *   gives, range by range, the pixels of the whole-frame render, and the
+ *   statistics, rays, vertices and beta sums of the ranges add up to the whole
+ *   frame's (up to the order of the float64 sums).  This is the partitioning of
+ *   a multi-GPU job: each rank renders its range, the float64 statistics and
+ *   the counters are summed across ranks, and the update runs on the sum.  A
+ *   range needs update_estimate = 0 and combine = 0 (the image statistics
+ *   filter across the whole image); image_rgb still spans the whole frame and
+ *   only the range's pixels are written. */
 #define MARS_MAX_DROP_BRIGHTEST 16
 typedef struct {
   uint32_t seed, job, iteration;
@@ -183,6 +195,8 @@ typedef struct {
                               vertices per depth in expectation; any budget field stays unbiased */
   int32_t vi_drop_brightest;  /* K brightest pixels left out of V_I (0: the outlier clamp) */
   int32_t combine;            /* 0 none, 1 add to, 2 restart the inverse-variance combination */
+  int32_t px_begin, px_end;   /* pixel range [px_begin, px_end) in row-major order (both 0: every
+                                 pixel); see "Pixel ranges" below */
 } mars_iter_params;
 
 /* What one iteration did (host memory, filled by mars_render_iteration). */
@@ -271,10 +285,15 @@ typedef struct {
 } mars_cache_info;
 
 /* ---- scene ------------------------------------------------------------
- * Copies the description to the device, builds a linear BVH (Morton codes,
- * radix sort, Karras hierarchy, bottom-up bounds) and the light-selection
- * table (probability proportional to area x mean radiance).  Synchronises
- * `stream` before returning.  Errors: INVALID_ARG (no primitives, bad sizes,
+ * Copies the description to the device, builds the closest-hit hierarchy
+ * selected by desc->bvh -- by default (MARS_BVH_SAH) a top-down surface-area
+ * heuristic build on the host CPU (binned above 64 primitives, exact sweeps
+ * below; about 0.1 s for 131k triangles, 0.4 s for 524k), with MARS_BVH_LBVH a
+ * linear BVH built on the device (Morton codes, sort, Karras hierarchy,
+ * bottom-up bounds); either is validated on the host and collapsed into the
+ * 4-wide hierarchy of the shadow rays -- and the light-selection table
+ * (probability proportional to area x mean radiance).  Results do not depend
+ * on the hierarchy.  Synchronises `stream` before returning.  Errors: INVALID_ARG (no primitives, bad sizes,
  * material index out of range, emitting sphere/triangle), OOM, CUDA. */
 mars_status mars_scene_create(const mars_scene_desc* desc, void* stream, mars_scene** out);
 mars_status mars_scene_destroy(mars_scene* scene);
@@ -432,7 +451,10 @@ mars_status mars_job_latencies(mars_server* server, uint64_t job_id, double* ms,
  * being captured, allocator-less embedded hosts, or a serving process whose
  * device memory is fully reserved up front.  For them this call computes the
  * same per-iteration image statistics as mars_render_iteration with
- * update_estimate = 1 (running sum, pixel estimate, V_I and C_I) directly on
+ * update_estimate = 1 (running sum, pixel estimate, V_I and C_I) -- for a cache
+ * with float64 statistics and vi_drop_brightest = 0: its V_I clamps every
+ * sample at `outlier` x the pixel estimate and averages over all pixels, and it
+ * has no float32 variant and no brightest-pixel rejection -- directly on
  * caller buffers and allocates nothing: its only scratch is a static device
  * array of the library (256 KB, held by every GPU that loads the library until
  * the process exits), with room for images of at most 8192 rows.
@@ -443,7 +465,10 @@ mars_status mars_job_latencies(mars_server* server, uint64_t job_id, double* ms,
  *   vi_ci        2 float64, device, out: V_I and C_I = rays / pixels.
  * Asynchronous on `stream`.  The first call on a device looks up the scratch
  * array's device address (cudaGetSymbolAddress) and must therefore come before
- * any stream capture on that device.  All calls share the scratch array: calls
+ * any stream capture on that device.  The address is cached for the life of
+ * the process: after cudaDeviceReset (or anything else that destroys the
+ * device's primary context) this entry point must not be called again on that
+ * device.  All calls share the scratch array: calls
  * whose work overlaps on the GPU race and give wrong results; serialise them.
  * Errors: INVALID_ARG (null pointer, height above 8192 rows, bad sizes), CUDA. */
 mars_status mars_image_stats_static(const float* image_rgb, float* run_sum_rgb, float* estimate_rgb, int32_t width,

@@ -58,6 +58,7 @@ class mars_iter_params(ct.Structure):
         ("collect", ct.c_int32), ("image_on_host", ct.c_int32), ("update_estimate", ct.c_int32),
         ("profile", ct.c_int32), ("max_multiplicity", ct.c_float),
         ("vi_drop_brightest", ct.c_int32), ("combine", ct.c_int32),
+        ("px_begin", ct.c_int32), ("px_end", ct.c_int32),
     ]
 
 

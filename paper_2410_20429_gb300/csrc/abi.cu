@@ -918,6 +918,16 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
   if (p->combine < 0 || p->combine > 2) return set_error(MARS_ERR_INVALID_ARG, "combine %d outside 0..2", p->combine);
   if (p->combine && !p->update_estimate)
     return set_error(MARS_ERR_INVALID_ARG, "combine needs update_estimate (the weight is 1 / V_I)");
+  // the pixel range of a shard (both 0: the whole frame)
+  const bool ranged = p->px_begin != 0 || p->px_end != 0;
+  if (ranged) {
+    if (p->px_begin < 0 || (int64_t)p->px_end > c->pixels || p->px_begin >= p->px_end)
+      return set_error(MARS_ERR_INVALID_ARG, "pixel range [%d, %d) outside [0, %lld)", p->px_begin, p->px_end,
+                       (long long)c->pixels);
+    if (p->update_estimate || p->combine)
+      return set_error(MARS_ERR_INVALID_ARG, "a pixel range renders without update_estimate and combine (the "
+                                             "image statistics need the whole frame)");
+  }
   DeviceGuard g(c->device);
   if (!g.ok) return set_error(MARS_ERR_CUDA, "cannot select device %d", c->device);
   c->last_stream = st;
@@ -945,6 +955,7 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
   if (e != cudaSuccess) return poison(c, e, "counter reset");
 
   const int64_t npx = c->pixels;
+  const int64_t r0 = ranged ? p->px_begin : 0, r1 = ranged ? p->px_end : npx, nr = r1 - r0;
   int ntiles = c->next_tiles > 0 ? c->next_tiles : 1;
   if (ntiles > c->max_tiles) ntiles = c->max_tiles;
   // Two lanes when each half of the image is expected to fit half of the
@@ -953,13 +964,13 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
   // profiled (a profiled iteration times each kernel alone on full-size
   // waves).  Otherwise one lane with the whole arena per tile.
   int iter_lanes = 1;
-  if (c->use_lanes > 1 && !p->profile && npx >= c->lane_min_pixels && ntiles == 1 && 1.3 * c->last_need <= 1.0) {
-    iter_lanes = (int)std::min<int64_t>(c->use_lanes, npx / std::max<int64_t>(1, c->lane_min_pixels / 2));
+  if (c->use_lanes > 1 && !p->profile && nr >= c->lane_min_pixels && ntiles == 1 && 1.3 * c->last_need <= 1.0) {
+    iter_lanes = (int)std::min<int64_t>(c->use_lanes, nr / std::max<int64_t>(1, c->lane_min_pixels / 2));
     ntiles = iter_lanes;
   }
   std::vector<std::pair<int64_t, int64_t>> tiles;
   for (int t = 0; t < ntiles; ++t) {
-    const int64_t a = npx * t / ntiles, b = npx * (t + 1) / ntiles;
+    const int64_t a = r0 + nr * t / ntiles, b = r0 + nr * (t + 1) / ntiles;
     if (b > a) tiles.emplace_back(a, b);
   }
   uint32_t retries = 0, used = 0, launches = 0, wave_launches = 0;
@@ -1048,6 +1059,8 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
         if ((r = launch_image_stats(c->dc, s->width, s->height, c->d_args, dev_out, p->vi_drop_brightest > 0,
                                     p->combine != 0, q)) != cudaSuccess)
           return r;
+      } else if (dev_out && ranged) {
+        if ((r = launch_image_copy_range(c->dc, (int)r0, (int)r1, dev_out, q)) != cudaSuccess) return r;
       } else if (dev_out) {
         if ((r = launch_image_copy(c->dc, (int)npx, dev_out, q)) != cudaSuccess) return r;
       }
@@ -1069,6 +1082,8 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
       key.dev_out = dev_out;
       key.drop = p->vi_drop_brightest > 0;
       key.combine = p->combine != 0;
+      key.r0 = ranged ? r0 : 0;
+      key.r1 = ranged ? r1 : 0;
       key.L = c->launch;
       if (!c->graph_exec || !(c->graph_key == key)) {
         if (c->graph_exec) {
@@ -1190,8 +1205,8 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
     c->has_estimate = true;
   }
   if (staged) {
-    if ((e = cudaMemcpyAsync(image, c->d_host_stage, sizeof(float) * 3 * (size_t)npx, cudaMemcpyDeviceToHost, st)) !=
-        cudaSuccess)
+    if ((e = cudaMemcpyAsync(image + 3 * (size_t)r0, c->d_host_stage + 3 * (size_t)r0, sizeof(float) * 3 * (size_t)nr,
+                             cudaMemcpyDeviceToHost, st)) != cudaSuccess)
       return poison(c, e, "image copy");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return poison(c, e, "image copy");
   }

@@ -62,10 +62,11 @@ struct GraphKey {
   bool update_estimate = false, drop = false, combine = false;
   int tiles = 0;
   float* dev_out = nullptr;
+  int64_t r0 = 0, r1 = 0;  // pixel range (the image copy of a range is recorded with its bounds)
   WaveLaunch L{};
   bool operator==(const GraphKey& o) const {
     return update_estimate == o.update_estimate && drop == o.drop && combine == o.combine && tiles == o.tiles &&
-           dev_out == o.dev_out && std::memcmp(&L, &o.L, sizeof(WaveLaunch)) == 0;
+           dev_out == o.dev_out && r0 == o.r0 && r1 == o.r1 && std::memcmp(&L, &o.L, sizeof(WaveLaunch)) == 0;
   }
 };
 

@@ -228,6 +228,8 @@ cudaError_t launch_image_stats(const DevCache& c, int width, int height, const I
 // the combined image divided by its weight sum, packed rgb, into out (device)
 cudaError_t launch_combined_out(const DevCache& c, int npix, float* out, cudaStream_t st);
 cudaError_t launch_image_copy(const DevCache& c, int npix, float* out, cudaStream_t st);
+// the iteration image of pixels [p0, p1) only, packed rgb, into out (device; the whole frame's layout)
+cudaError_t launch_image_copy_range(const DevCache& c, int p0, int p1, float* out, cudaStream_t st);
 cudaError_t launch_update(const DevCache& c, int num_sms, cudaStream_t st);
 // octree refinement after an update (stats.cu): leaf_samples must run before
 // launch_update (which zeroes the statistics), refine after it

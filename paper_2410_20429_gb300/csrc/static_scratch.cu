@@ -30,7 +30,10 @@ double* g_scratch_of_device[kMaxDevices] = {};
 
 // Device address of g_row_sums on the current device.  Host code must not use
 // the symbol itself (it names a host-side stand-in), so the address is looked
-// up once per device with that device current and cached.
+// up once per device with that device current and cached for the life of the
+// process.  A cudaDeviceReset (or a host that tears down the device's primary
+// context) invalidates the cached address; the entry point must not be used on
+// that device afterwards.
 mars_status scratch_address(double** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return mars::set_error(MARS_ERR_CUDA, "no current CUDA device");

@@ -166,6 +166,19 @@ __global__ void __launch_bounds__(IMG_THREADS) k_img_copy(DevCache c, int npix, 
   }
 }
 
+// the pixels of one range of the frame (a shard of a multi-GPU job), one
+// thread per pixel: three scalar stores, since a range need not start on a
+// warp-aligned pixel
+__global__ void __launch_bounds__(IMG_THREADS) k_img_copy_range(DevCache c, int p0, int p1, float* out) {
+  if (c.ctr->any_overflow) return;
+  for (int p = p0 + blockIdx.x * blockDim.x + threadIdx.x; p < p1; p += gridDim.x * blockDim.x) {
+    const float4 I = c.img[p];
+    out[3 * (size_t)p] = I.x;
+    out[3 * (size_t)p + 1] = I.y;
+    out[3 * (size_t)p + 2] = I.z;
+  }
+}
+
 // ---- brightest-pixel rejection of V_I (Sec. 5.1 "Implementation")
 // Brightness order: float32 luminance (products and sums rounded one by one,
 // as the oracle does), descending, then pixel index ascending; the key is
@@ -569,6 +582,14 @@ cudaError_t launch_image_copy(const DevCache& c, int npix, float* out, cudaStrea
   int blocks = (npix + IMG_THREADS - 1) / IMG_THREADS;
   if (blocks > 4096) blocks = 4096;
   k_img_copy<<<blocks, IMG_THREADS, 0, st>>>(c, npix, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_image_copy_range(const DevCache& c, int p0, int p1, float* out, cudaStream_t st) {
+  int blocks = (p1 - p0 + IMG_THREADS - 1) / IMG_THREADS;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  k_img_copy_range<<<blocks, IMG_THREADS, 0, st>>>(c, p0, p1, out);
   return cudaGetLastError();
 }
 

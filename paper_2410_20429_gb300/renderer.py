@@ -106,12 +106,13 @@ class Cache:
     def render_iteration(self, image, *, seed=0, job=0, iteration=0, mode=A.MARS_MODE_WARMUP,
                          weights=A.MARS_WEIGHTS_AWARE, clamp_lo=0.05, clamp_hi=20.0, outlier=50.0, collect=True,
                          update_estimate=True, profile=False, max_multiplicity=0.0, vi_drop_brightest=0,
-                         combine=0, stream=None) -> dict:
+                         combine=0, px_range=None, stream=None) -> dict:
         """Render one iteration into ``image``: a CUDA float32 tensor with
         height*width*3 elements, or a host numpy float32 array of that size (the
         library then copies the image back).  ``vi_drop_brightest`` and
         ``combine`` select the bidirectional application's image-variance
-        rejection and progressive combination (see mars.h)."""
+        rejection and progressive combination (see mars.h).  ``px_range``
+        (begin, end) renders only those pixels (a shard of a multi-GPU job)."""
         on_host = isinstance(image, np.ndarray)
         if on_host:
             if image.dtype != np.float32 or not image.flags.c_contiguous or image.size != 3 * self.n_pixels:
@@ -127,7 +128,8 @@ class Cache:
         p = A.mars_iter_params(int(seed), int(job), int(iteration), int(mode), int(weights), float(clamp_lo),
                                float(clamp_hi), float(outlier), int(bool(collect)), int(on_host),
                                int(bool(update_estimate)), int(bool(profile)), float(max_multiplicity),
-                               int(vi_drop_brightest), int(combine))
+                               int(vi_drop_brightest), int(combine),
+                               *((0, 0) if px_range is None else (int(px_range[0]), int(px_range[1]))))
         st = A.mars_iter_stats()
         A.check(self._lib.mars_render_iteration(self.handle, ct.byref(p), ptr, ct.byref(st), _stream_handle(stream)),
                 "mars_render_iteration")

@@ -86,5 +86,5 @@ def test_struct_sizes_match_header(lib, tmp_path):
         for f, _ in S._fields_:
             assert getattr(S, f).offset == got[(S.__name__, f)], (S.__name__, f)
     # the sizes the header documents
-    assert ct.sizeof(_abi.mars_iter_params) == 60
+    assert ct.sizeof(_abi.mars_iter_params) == 68
     assert ct.sizeof(_abi.mars_launch_config) == 56

@@ -5,8 +5,11 @@ Bars (floating point; the oracle is float64, the CUDA path float32):
 * images: at least 99.9 % of pixels agree within 1e-4 relative in every channel
   (a rare pixel may take a different discrete branch -- a rounding decision of
   Alg. 1 or a grazing hit -- because float32 and float64 differ in the last bits);
-* per-cell statistics: 99 % of (cell, technique) entries within 1e-3 relative,
-  and the sums over all cells within 1e-3 relative;
+* per-cell statistics: every (cell, technique) entry that no disagreeing
+  pixel's path reaches agrees within 1e-3 relative in all 8 sums (the cells a
+  disagreeing pixel reaches are found by rendering that pixel alone, on both
+  sides, from the same state); the fraction of all populated entries that
+  agree is printed; the sums over all cells agree within 1e-3 relative;
 * integer counters (rays, traced vertices) within 0.1 %.
 """
 import math
@@ -56,11 +59,58 @@ def _stat_agreement(gs, os_):
     return agree.sum() / pop.sum() if pop.any() else 1.0   # no samples (D = 1): nothing to disagree
 
 
-def _check(g_img, o_img, g_state, o_res, g_st, what):
+def _touched_cells(M, orc, cache, sc, gpu_kw, orc_kw, pixels):
+    """Cells in which any of `pixels`' path trees recorded a sample, on the CUDA
+    path (the pixel rendered alone through a pixel range, from the cache's
+    state) or in the oracle (the pixel alone): where a pixel took a different
+    discrete branch on the two sides, its samples land in different cells."""
+    import torch
+    touched = np.zeros(cache.n_cells, bool)
+    if len(pixels) == 0:
+        return touched
+    saved = cache.get_state()["stats"]
+    img = torch.zeros(cache.n_pixels * 3, dtype=torch.float32, device="cuda")
+    for px in pixels:
+        px = int(px)
+        cache.set_state(stats=np.zeros_like(saved))
+        cache.render_iteration(img, update_estimate=False, px_range=(px, px + 1), **gpu_kw)
+        torch.cuda.synchronize()
+        touched |= cache.get_state()["stats"][..., 0].sum(-1) > 0
+        o = orc.render(sc, px_begin=px, px_end=px + 1, **orc_kw)
+        touched[: o.stats.shape[0]] |= o.stats[..., 0].sum(-1) > 0
+    cache.set_state(stats=saved)
+    return touched
+
+
+def _strict_stats(g_stats, o_stats, touched, what):
+    """Every populated (cell, technique) entry outside the cells reached by a
+    disagreeing pixel agrees within STAT_TOL in all 8 sums; returns the
+    fraction of all populated entries that agree."""
+    g_stats = g_stats[: o_stats.shape[0]]
+    pop = (g_stats[..., 0] > 0) | (o_stats[..., 0] > 0)
+    close = (np.abs(g_stats - o_stats) <= STAT_TOL * np.abs(o_stats) + 1e-9).all(axis=-1)
+    keep = pop & ~touched[: o_stats.shape[0], None]
+    bad = np.argwhere(keep & ~close)
+    assert bad.size == 0, f"{what}: {len(bad)} (cell, technique) entries outside the disagreeing pixels' " \
+                          f"cells differ, e.g. {bad[:3].tolist()}"
+    frac = (close & pop).sum() / max(pop.sum(), 1)
+    print(f"{what}: {frac:.5f} of {int(pop.sum())} populated entries agree; "
+          f"{int(touched.sum())} cells reached by disagreeing pixels")
+    return frac
+
+
+def _check(g_img, o_img, g_state, o_res, g_st, what, touch=None):
+    """Image, statistics and counter bars.  touch(pixels) -> the cells those
+    pixels reach (see _touched_cells); without it the per-cell bar is 99 % of
+    the populated entries."""
     frac = _pixel_agreement(g_img, o_img)
     assert frac >= 0.999, f"{what}: only {frac:.5f} of pixels agree"
-    sa = _stat_agreement(g_state["stats"], o_res.stats)
-    assert sa >= 0.99, f"{what}: only {sa:.4f} of cell statistics agree"
+    if touch is not None:
+        off = ~(np.abs(g_img - o_img) <= PIX_TOL * np.abs(o_img) + 1e-7).all(axis=1)
+        _strict_stats(g_state["stats"], o_res.stats, touch(np.flatnonzero(off)), what)
+    else:
+        sa = _stat_agreement(g_state["stats"], o_res.stats)
+        assert sa >= 0.99, f"{what}: only {sa:.4f} of cell statistics agree"
     tot_g = g_state["stats"].sum(axis=0)
     tot_o = o_res.stats.sum(axis=0)
     assert np.allclose(tot_g, tot_o, rtol=STAT_TOL, atol=1e-6), f"{what}: total statistics differ"
@@ -79,8 +129,10 @@ def test_box_warmup_iteration_parity(mars, orc):
     scene, cache = _make(mars, cfg)
     g_img, g_st = _gpu_iteration(mars, cache, iteration=0, seed=0, mode=0)
     g_state = cache.get_state()
-    o = orc.render(cfg.scene, grid_n=cfg.grid_n, techniques=cfg.techniques, max_depth=cfg.max_depth, iteration=0)
-    _check(g_img, o.image, g_state, o, g_st, "box warm-up")
+    okw = dict(grid_n=cfg.grid_n, techniques=cfg.techniques, max_depth=cfg.max_depth, iteration=0)
+    o = orc.render(cfg.scene, **okw)
+    touch = lambda px: _touched_cells(mars, orc, cache, cfg.scene, dict(iteration=0, seed=0, mode=0), okw, px)
+    _check(g_img, o.image, g_state, o, g_st, "box warm-up", touch)
     assert g_st["estimator_vertices"] == pytest.approx(o.counters[2], rel=1e-3)
 
 
@@ -95,9 +147,12 @@ def test_box_mars_iteration_parity(mars, orc, weights):
     cache.set_state(q_rr=q_rr, q_s=q_s, valid=valid, pixel_estimate=est, has_estimate=True, n_iterations=1)
     g_img, g_st = _gpu_iteration(mars, cache, iteration=3, seed=5, mode=1, weights=weights)
     g_state = cache.get_state()
-    o = orc.render(cfg.scene, grid_n=cfg.grid_n, techniques=cfg.techniques, max_depth=cfg.max_depth, iteration=3,
-                   seed=5, mode=orc.MODE_MARS, weights=weights, q_rr=q_rr, q_s=q_s, valid=valid, est=est)
-    _check(g_img, o.image, g_state, o, g_st, "box MARS")
+    okw = dict(grid_n=cfg.grid_n, techniques=cfg.techniques, max_depth=cfg.max_depth, iteration=3, seed=5,
+               mode=orc.MODE_MARS, weights=weights, q_rr=q_rr, q_s=q_s, valid=valid, est=est)
+    o = orc.render(cfg.scene, **okw)
+    touch = lambda px: _touched_cells(mars, orc, cache, cfg.scene,
+                                      dict(iteration=3, seed=5, mode=1, weights=weights), okw, px)
+    _check(g_img, o.image, g_state, o, g_st, "box MARS", touch)
     # splitting and roulette really happened
     assert o.counters[3] / o.counters[2] != pytest.approx(1.0, abs=0.05)
     for t in range(2):
@@ -119,9 +174,12 @@ def test_multiplicity_cap_parity(mars, orc):
     torch.cuda.synchronize()
     g_img = img.cpu().numpy().reshape(-1, 3).astype(np.float64)
     g_state = cache.get_state()
-    o = orc.render(cfg.scene, grid_n=cfg.grid_n, techniques=cfg.techniques, max_depth=cfg.max_depth, iteration=2,
-                   seed=6, mode=orc.MODE_MARS, q_rr=q_rr, q_s=q_s, valid=valid, est=est, max_mult=6.0)
-    _check(g_img, o.image, g_state, o, g_st, "box MARS, multiplicity cap")
+    okw = dict(grid_n=cfg.grid_n, techniques=cfg.techniques, max_depth=cfg.max_depth, iteration=2, seed=6,
+               mode=orc.MODE_MARS, q_rr=q_rr, q_s=q_s, valid=valid, est=est, max_mult=6.0)
+    o = orc.render(cfg.scene, **okw)
+    touch = lambda px: _touched_cells(mars, orc, cache, cfg.scene,
+                                      dict(iteration=2, seed=6, mode=1, max_multiplicity=6.0), okw, px)
+    _check(g_img, o.image, g_state, o, g_st, "box MARS, multiplicity cap", touch)
     free = orc.render(cfg.scene, grid_n=cfg.grid_n, techniques=cfg.techniques, max_depth=cfg.max_depth,
                       iteration=2, seed=6, mode=orc.MODE_MARS, q_rr=q_rr, q_s=q_s, valid=valid, est=est)
     assert free.vertices > 2 * o.vertices   # the cap binds
@@ -136,8 +194,10 @@ def test_heightfield_triangles_parity(mars, orc):
     scene, cache = _make(mars, cfg)
     g_img, g_st = _gpu_iteration(mars, cache, iteration=0, seed=8, mode=0)
     g_state = cache.get_state()
-    o = orc.render(sc, grid_n=8, techniques=7, max_depth=5, iteration=0, seed=8)
-    _check(g_img, o.image, g_state, o, g_st, "heightfield warm-up")
+    okw = dict(grid_n=8, techniques=7, max_depth=5, iteration=0, seed=8, collect=True)
+    o = orc.render(sc, **okw)
+    touch = lambda px: _touched_cells(mars, orc, cache, sc, dict(iteration=0, seed=8, mode=0), okw, px)
+    _check(g_img, o.image, g_state, o, g_st, "heightfield warm-up", touch)
     assert o.image.mean() > 0
     q_rr, q_s, valid = W.random_count_fields(cfg.n_cells, seed=121, lo=0.1, hi=3.0)
     est = W.random_pixel_estimate(sc.n_pixels, seed=122, lo=0.01, hi=0.5)
@@ -146,9 +206,11 @@ def test_heightfield_triangles_parity(mars, orc):
                     guide_cdf=cdf, stats=np.zeros((cfg.n_cells, 3, 8)))
     g_img, g_st = _gpu_iteration(mars, cache, iteration=1, seed=8, mode=1)
     g_state = cache.get_state()
-    o = orc.render(sc, grid_n=8, techniques=7, max_depth=5, iteration=1, seed=8, mode=orc.MODE_MARS, q_rr=q_rr,
-                   q_s=q_s, valid=valid, est=est, guide_cdf=cdf)
-    _check(g_img, o.image, g_state, o, g_st, "heightfield MARS")
+    okw = dict(grid_n=8, techniques=7, max_depth=5, iteration=1, seed=8, mode=orc.MODE_MARS, q_rr=q_rr, q_s=q_s,
+               valid=valid, est=est, guide_cdf=cdf)
+    o = orc.render(sc, **okw)
+    touch = lambda px: _touched_cells(mars, orc, cache, sc, dict(iteration=1, seed=8, mode=1), okw, px)
+    _check(g_img, o.image, g_state, o, g_st, "heightfield MARS", touch)
 
 
 def test_guided_room_crop_parity(mars, orc):
@@ -164,9 +226,11 @@ def test_guided_room_crop_parity(mars, orc):
                     n_iterations=2)
     g_img, g_st = _gpu_iteration(mars, cache, iteration=2, seed=9, mode=1)
     g_state = cache.get_state()
-    o = orc.render(sc, grid_n=cfg.grid_n, techniques=7, max_depth=cfg.max_depth, iteration=2, seed=9,
-                   mode=orc.MODE_MARS, q_rr=q_rr, q_s=q_s, valid=valid, est=est, guide_cdf=cdf)
-    _check(g_img, o.image, g_state, o, g_st, "guided room")
+    okw = dict(grid_n=cfg.grid_n, techniques=7, max_depth=cfg.max_depth, iteration=2, seed=9, mode=orc.MODE_MARS,
+               q_rr=q_rr, q_s=q_s, valid=valid, est=est, guide_cdf=cdf)
+    o = orc.render(sc, **okw)
+    touch = lambda px: _touched_cells(mars, orc, cache, sc, dict(iteration=2, seed=9, mode=1), okw, px)
+    _check(g_img, o.image, g_state, o, g_st, "guided room", touch)
     gh, oh = g_state["guide_hist"].astype(np.float64), o.hist
     pop = (gh > 0) | (oh > 0)
     close = np.abs(gh - oh) <= STAT_TOL * np.abs(oh) + 1e-9
@@ -225,6 +289,93 @@ def test_image_statistics_parity(mars, orc):
     assert g_st["VI"] == pytest.approx(vi, rel=1e-2)
     assert g_st["CI"] == pytest.approx(o.rays / cfg.scene.n_pixels, rel=1e-3)
     assert g["n_iterations"] == 3
+
+
+def test_pixel_ranges_shard_the_frame(mars, orc):
+    """The partitioning of a multi-GPU job (one pixel range per rank): two
+    caches from the same state render the two halves of the frame (split at a
+    pixel that is not warp-aligned); their pixels are bitwise those of the
+    whole-frame render, their statistics, rays, vertices and budget sums add up
+    to the whole frame's (up to the order of float64 sums), the image
+    statistics of the assembled frame (the library's allocation-free image pass
+    on caller buffers, with the summed rays) equal the whole-frame cache's, and
+    the fixed-point update on the summed statistics equals the update on the
+    whole.  Argument errors: an empty or out-of-frame range, or a range with
+    update_estimate."""
+    import torch
+    cfg = W.WorkloadConfig(W.guided_room_scene(seed=2, width=64, height=48, n_spheres=24), max_depth=6, grid_n=8,
+                           techniques=7, iterations=1, warmup=0, name="guided 64x48")
+    npx = cfg.scene.n_pixels
+    q_rr, q_s, valid = W.random_count_fields(cfg.n_cells, seed=501, lo=0.1, hi=3.0)
+    est = W.random_pixel_estimate(npx, seed=502, lo=0.05, hi=2.0)
+    cdf = W.random_guide_cdf(cfg.n_cells, seed=503)
+    rs = W.random_pixel_estimate(npx, seed=504, lo=0.1, hi=3.0) * 2.0
+    state = dict(q_rr=q_rr, q_s=q_s, valid=valid, pixel_estimate=est, guide_cdf=cdf, run_sum=rs,
+                 has_estimate=True, n_iterations=2)
+    scene = mars.Scene(cfg.scene)
+    caches = [mars.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth) for _ in range(3)]
+    for c in caches:
+        c.set_state(**state)
+    kw = dict(seed=13, iteration=4, mode=mars.MARS_MODE_MARS)
+    full = torch.zeros(npx * 3, dtype=torch.float32, device="cuda")
+    st_full = caches[0].render_iteration(full, update_estimate=True, **kw)
+    split = 1337
+    part = torch.full((npx * 3,), -1.0, dtype=torch.float32, device="cuda")
+    st_a = caches[1].render_iteration(part, update_estimate=False, px_range=(0, split), **kw)
+    st_b = caches[2].render_iteration(part, update_estimate=False, px_range=(split, npx), **kw)
+    torch.cuda.synchronize()
+    assert torch.equal(part, full)
+    g_full, g_a, g_b = (c.get_state() for c in caches)
+    assert st_a["rays"] + st_b["rays"] == st_full["rays"]
+    assert st_a["vertices"] + st_b["vertices"] == st_full["vertices"]
+    assert st_a["estimator_vertices"] + st_b["estimator_vertices"] == st_full["estimator_vertices"]
+    for t in range(3):
+        sb = st_a["mean_beta"][t] * st_a["estimator_vertices"] + st_b["mean_beta"][t] * st_b["estimator_vertices"]
+        assert sb == pytest.approx(st_full["mean_beta"][t] * st_full["estimator_vertices"], rel=1e-9)
+    summed = g_a["stats"] + g_b["stats"]
+    np.testing.assert_allclose(summed, g_full["stats"], rtol=1e-6, atol=1e-9)
+    assert np.array_equal(summed[..., 0], g_full["stats"][..., 0])
+    assert np.array_equal(summed[..., 7], g_full["stats"][..., 7])
+    np.testing.assert_allclose(g_a["guide_hist"].astype(np.float64) + g_b["guide_hist"],
+                               g_full["guide_hist"], rtol=1e-4, atol=1e-6)
+    # the oracle over the same two ranges agrees with the shards' sum
+    okw = dict(grid_n=cfg.grid_n, techniques=7, max_depth=cfg.max_depth, iteration=4, seed=13, mode=orc.MODE_MARS,
+               q_rr=q_rr, q_s=q_s, valid=valid, est=est, guide_cdf=cdf)
+    o = [orc.render(cfg.scene, px_begin=b, px_end=e, **okw) for b, e in ((0, split), (split, npx))]
+    assert np.allclose(summed.sum(0), (o[0].stats + o[1].stats).sum(0), rtol=STAT_TOL, atol=1e-6)
+    # image statistics of the assembled frame on caller buffers, rays summed over the shards
+    L = mars.load()
+    run_sum = torch.tensor(rs.reshape(-1), dtype=torch.float32, device="cuda")
+    est_out = torch.zeros(npx * 3, dtype=torch.float32, device="cuda")
+    vi_ci = torch.zeros(2, dtype=torch.float64, device="cuda")
+    rc = L.mars_image_stats_static(part.data_ptr(), run_sum.data_ptr(), est_out.data_ptr(), 64, 48, 2, 50.0,
+                                   float(st_a["rays"] + st_b["rays"]), vi_ci.data_ptr(),
+                                   torch.cuda.current_stream().cuda_stream)
+    assert rc == 0
+    torch.cuda.synchronize()
+    VI, CI = vi_ci.cpu().tolist()
+    assert VI == pytest.approx(st_full["VI"], rel=1e-6) and CI == pytest.approx(st_full["CI"], rel=1e-12)
+    np.testing.assert_allclose(est_out.cpu().numpy().reshape(-1, 3), g_full["pixel_estimate"], rtol=1e-6)
+    # the update on the summed statistics equals the update on the whole
+    caches[1].set_state(stats=summed, VI=VI, CI=CI, has_estimate=True, n_iterations=3)
+    caches[0].update_counts()
+    caches[1].update_counts()
+    u_full, u_sum = caches[0].get_state(), caches[1].get_state()
+    assert np.array_equal(u_full["valid"], u_sum["valid"])
+    np.testing.assert_allclose(u_sum["q_rr"], u_full["q_rr"], rtol=1e-5)
+    # q^S = sqrt(var) amplifies the regrouped float32 partial sums by m2 / var
+    # where the variance is small against the second moment
+    close = np.abs(u_sum["q_s"] - u_full["q_s"]) <= 1e-4 * np.abs(u_full["q_s"]) + 1e-12
+    assert close.mean() >= 0.999
+    np.testing.assert_allclose(u_sum["q_s"], u_full["q_s"], rtol=1e-2, atol=1e-9)
+    # argument errors
+    for bad in ((0, 0 - 1), (5, 5), (0, npx + 1), (-3, 10)):
+        with pytest.raises(mars.MarsError) as e:
+            caches[2].render_iteration(part, update_estimate=False, px_range=bad, **kw)
+        assert e.value.status == mars.MARS_ERR_INVALID_ARG
+    with pytest.raises(mars.MarsError) as e:
+        caches[2].render_iteration(part, update_estimate=True, px_range=(0, 10), **kw)
+    assert e.value.status == mars.MARS_ERR_INVALID_ARG
 
 
 def test_arena_overflow_tiles_reproduce_the_image(mars):
@@ -753,88 +904,162 @@ def _nudged(scene, direction):
     return out
 
 
+FULL_RUNS, FULL_RUN_LEN = 64, 64   # 4096 sampled pixels per workload
+
+
+def _full_size_inputs(which):
+    """Seeded inputs of the full-size parity case, built the same way in the
+    test process and in the oracle's worker processes: the workload, its
+    teacher-forced counts, pixel estimate and guide, and for the heightfields an
+    adaptive octree refined by the oracle's own rule from seeded per-leaf sample
+    counts (three rounds, split at 100 samples, at most 64k leaves)."""
+    import oracle
+    if which == "guided_512":
+        cfg = W.config_guided(512, 512)
+        cells, tree = cfg.n_cells, None
+    else:
+        cfg = W.config_heightfield(1024, 1024) if which == "heightfield_1024" else W.config_large(2048, 2048)
+        cells = 65536
+        nodes, nn, nl, lvl, lnode = oracle.octree_init(cfg.grid_n, cells)
+        rng = np.random.default_rng(1004)
+        z = np.zeros((cells, 3, 3), np.float32)
+        zv = np.zeros((cells, 3), np.uint8)
+        for _ in range(3):
+            st = np.zeros((cells, 3, 8))
+            st[:nl, 0, 0] = rng.integers(0, 160, size=nl)
+            nodes, nn, nl, lvl, lnode, *_ = oracle.octree_refine(cells, 100.0, st, nodes, nn, nl, lvl, lnode,
+                                                                 z, z, zv)
+        tree = (nodes[:nn].copy(), lvl[:nl].copy(), nl)
+    q_rr, q_s, valid = W.random_count_fields(cells, seed=1001, lo=0.1, hi=2.0)
+    est = W.random_pixel_estimate(cfg.scene.n_pixels, seed=1002, lo=0.2, hi=2.0)
+    cdf = W.random_guide_cdf(cells, seed=1003) if cfg.techniques & 4 else None
+    return cfg, cells, tree, q_rr, q_s, valid, est, cdf
+
+
+def _full_size_runs(npx):
+    stride = npx // FULL_RUNS
+    return [r * stride + (r * 7919) % max(1, stride - FULL_RUN_LEN) for r in range(FULL_RUNS)]
+
+
+def _full_size_oracle(job):
+    """Worker (a spawned process): the oracle over some runs of pixels of the
+    full-size case, on the scene nudged by `nudge` float32 ulps; returns the
+    runs' pixels and, unnudged, their summed statistics and counters."""
+    which, nudge, starts = job
+    import oracle
+    cfg, cells, tree, q_rr, q_s, valid, est, cdf = _full_size_inputs(which)
+    sc = cfg.scene if nudge == 0 else _nudged(cfg.scene, nudge)
+    kw = dict(grid_n=cfg.grid_n, techniques=cfg.techniques, max_depth=cfg.max_depth, iteration=7, seed=11,
+              mode=oracle.MODE_MARS, q_rr=q_rr, q_s=q_s, valid=valid, est=est, guide_cdf=cdf, collect=nudge == 0)
+    if tree is not None:
+        kw["octree"] = (tree[0], cells)
+    pix, stats, ctr = {}, None, np.zeros(8)
+    for b in starts:
+        r = oracle.render(sc, px_begin=b, px_end=b + FULL_RUN_LEN, **kw)
+        pix[b] = r.image[b:b + FULL_RUN_LEN].copy()
+        if nudge == 0:
+            stats = r.stats if stats is None else stats + r.stats
+            ctr += r.counters
+    return pix, stats, ctr
+
+
 @pytest.mark.parametrize("which", ["guided_512", "heightfield_1024", "large_2048"])
 def test_full_size_sampled_parity(mars, orc, which):
     """The workloads at their full sizes, in the launch configuration the
     benchmark times (iteration graphs, two tile lanes, the autotuner's launch
-    shape; the octree caches of the two heightfield workloads, unrefined, whose
-    first grid_n^3 leaves are the grid's cells), one teacher-forced MARS
-    iteration of the whole frame, compared with the oracle on evenly spread
-    runs of pixels: every pixel's random streams are keyed by its index, so a
-    run of pixels is rendered identically inside the frame and alone.
+    shape; adaptive octree caches for the two heightfield workloads, refined by
+    the oracle's rule), one teacher-forced MARS iteration of the whole frame
+    without a multiplicity cap, compared with the oracle on 4096 pixels in 64
+    evenly spread runs: every pixel's random streams are keyed by its index, so
+    a run of pixels is rendered identically inside the frame and alone.  The
+    statistics of the sampled runs (the CUDA path renders them again as pixel
+    ranges into empty statistics) are compared in total within 1e-3 and per
+    (cell, technique) entry wherever no disagreeing pixel reaches.
 
-    Bar: these frames hold pixels whose value a float32 evaluation cannot pin
-    down -- small GGX spheres (alpha down to 0.05) that reflect a light, where
-    a normal's rounding error is amplified by ~1 / alpha^2.  The oracle finds
-    them itself: moving every geometry value of the float32 scene by one ulp
-    (both ways) moves those pixels by more than 1e-4 in float64.  Outside that
-    set, at least 99.9 % of the sampled pixels agree within 1e-4 (the bar of the
-    small parity cases); and the float32 path disagrees on no more pixels than
-    one ulp of input moves the oracle by."""
+    Pixel bar: these frames hold pixels whose value a float32 evaluation cannot
+    pin down -- small GGX spheres (alpha down to 0.05) that reflect a light,
+    where a normal's rounding error is amplified by ~1 / alpha^2.  The oracle
+    finds them itself: moving every geometry value of the float32 scene by one
+    ulp (both ways) moves those pixels by more than 1e-4 in float64.  Outside
+    that set, at least 99.9 % of the sampled pixels agree within 1e-4 (the bar
+    of the small parity cases); and the float32 path disagrees on no more
+    pixels than one ulp of input moves the oracle by."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import os
     import torch
-    if which == "guided_512":
-        cfg, kw, runs, run_len, cells = W.config_guided(512, 512), {}, 16, 256, None
-    else:
-        cfg = W.config_heightfield(1024, 1024) if which == "heightfield_1024" else W.config_large(2048, 2048)
-        npx = cfg.scene.n_pixels
-        kw = dict(octree=True, max_leaves=65536, split_samples=1e30, arena_capacity=2 * npx * cfg.max_depth)
-        runs, run_len = (32, 4) if which == "heightfield_1024" else (16, 2)
-        cells = 65536
+    cfg, cells, tree, q_rr, q_s, valid, est, cdf = _full_size_inputs(which)
     sc = cfg.scene
     npx = sc.n_pixels
+    starts = _full_size_runs(npx)
+    # the oracle's share starts first, in spawned processes (fork after CUDA hangs)
+    procs = max(1, min(32, os.cpu_count() or 1))
+    pool = cf.ProcessPoolExecutor(max_workers=procs, mp_context=mp.get_context("spawn"))
+    futs = {nudge: [pool.submit(_full_size_oracle, (which, nudge, starts[k::procs])) for k in range(procs)]
+            for nudge in (0, 1, -1)}
+    kw = {} if tree is None else dict(octree=True, max_leaves=cells, split_samples=1e30,
+                                      arena_capacity=2 * npx * cfg.max_depth)
     scene = mars.Scene(sc)
     cache = mars.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, **kw)
-    n = cfg.n_cells
-    q_rr, q_s, valid = W.random_count_fields(n, seed=1001, lo=0.1, hi=2.0)
-    est = W.random_pixel_estimate(npx, seed=1002, lo=0.2, hi=2.0)
-    cdf = W.random_guide_cdf(n, seed=1003) if cfg.techniques & 4 else None
-    M = 8.0   # the multiplicity cap bounds the vertices of a depth per camera sample
-
-    def pad(a):
-        if cells is None:
-            return a
-        out = np.zeros((cells,) + a.shape[1:], a.dtype)
-        out[:n] = a
-        return out
-
-    st = dict(q_rr=pad(q_rr), q_s=pad(q_s), valid=pad(valid), pixel_estimate=est, has_estimate=True,
-              n_iterations=1)
+    st = dict(q_rr=q_rr, q_s=q_s, valid=valid, pixel_estimate=est, has_estimate=True, n_iterations=1)
     if cdf is not None:
-        st["guide_cdf"] = pad(cdf)
+        st["guide_cdf"] = cdf
+    if tree is not None:
+        st.update(oct_nodes=tree[0], oct_leaf_level=tree[1])
     cache.set_state(**st)
-    launch = cache.autotune(iteration=7, seed=11, mode=mars.MARS_MODE_MARS, repeats=1, max_multiplicity=M)
+    if tree is not None:
+        assert cache.info()["oct_n_leaves"] == tree[2] > cfg.n_cells
+    gkw = dict(iteration=7, seed=11, mode=mars.MARS_MODE_MARS)
+    launch = cache.autotune(repeats=1, **gkw)
     assert all(t > 0 for t in launch["threads"])
     img = torch.zeros(npx * 3, dtype=torch.float32, device="cuda")
-    g_st = cache.render_iteration(img, seed=11, iteration=7, mode=mars.MARS_MODE_MARS, max_multiplicity=M)
+    g_st = cache.render_iteration(img, update_estimate=False, **gkw)
     torch.cuda.synchronize()
     g = img.cpu().numpy().reshape(-1, 3).astype(np.float64)
     assert g_st["tiles"] >= 1 and np.isfinite(g).all()
-
-    def oracle_run(scene_desc, b):
-        return orc.render(scene_desc, grid_n=cfg.grid_n, techniques=cfg.techniques, max_depth=cfg.max_depth,
-                          iteration=7, seed=11, mode=orc.MODE_MARS, q_rr=q_rr, q_s=q_s, valid=valid, est=est,
-                          guide_cdf=cdf, max_mult=M, px_begin=b, px_end=b + run_len).image[b:b + run_len]
+    # the sampled runs again, as pixel ranges, into empty statistics
+    cache.set_state(stats=np.zeros((cells, 3, 8)))
+    rays = verts = 0
+    for b in starts:
+        s_ = cache.render_iteration(img, update_estimate=False, px_range=(b, b + FULL_RUN_LEN), **gkw)
+        rays += s_["rays"]
+        verts += s_["vertices"]
+    torch.cuda.synchronize()
+    g_stats = cache.get_state()["stats"]
+    res = {n: [f.result() for f in fl] for n, fl in futs.items()}
+    pool.shutdown()
+    o_pix = {n: {b: p for r in rl for b, p in r[0].items()} for n, rl in res.items()}
+    o_stats = sum(r[1] for r in res[0] if r[1] is not None)
+    o_ctr = sum(r[2] for r in res[0])
 
     def off(x, y):
         return (np.abs(x - y) > PIX_TOL * np.abs(y) + 1e-7).any(axis=1)
 
-    up, down = _nudged(sc, +1), _nudged(sc, -1)
-    stride = npx // runs
-    n_off, n_sens, n_off_well, total = 0, 0, 0, 0
-    for r in range(runs):
-        b = r * stride + (r * 7919) % max(1, stride - run_len)
-        o = oracle_run(sc, b)
-        f = off(g[b:b + run_len], o)
-        sens = off(oracle_run(up, b), o) | off(oracle_run(down, b), o)
+    n_off = n_sens = n_off_well = 0
+    bad = []
+    for b in starts:
+        o = o_pix[0][b]
+        f = off(g[b:b + FULL_RUN_LEN], o)
+        sens = off(o_pix[1][b], o) | off(o_pix[-1][b], o)
         n_off += int(f.sum())
         n_sens += int(sens.sum())
         n_off_well += int((f & ~sens).sum())
-        total += run_len
+        bad += [b + k for k in np.flatnonzero(f)]
+    total = FULL_RUNS * FULL_RUN_LEN
     msg = f"{which}: {n_off} of {total} pixels off by > 1e-4 ({n_off_well} of them well conditioned); " \
           f"one ulp of input moves {n_sens}"
     print(msg)
     assert n_off_well <= 0.001 * total + 1, msg
     assert n_off <= max(n_sens, 0.001 * total + 1), msg
+    # statistics of the sampled runs
+    assert abs(rays - o_ctr[0]) <= 1e-3 * o_ctr[0] + 1 and abs(verts - o_ctr[1]) <= 1e-3 * o_ctr[1] + 1
+    assert np.allclose(g_stats.sum(0), o_stats.sum(0), rtol=STAT_TOL, atol=1e-6), which
+    okw = dict(grid_n=cfg.grid_n, techniques=cfg.techniques, max_depth=cfg.max_depth, iteration=7, seed=11,
+               mode=orc.MODE_MARS, q_rr=q_rr, q_s=q_s, valid=valid, est=est, guide_cdf=cdf)
+    if tree is not None:
+        okw["octree"] = (tree[0], cells)
+    touched = _touched_cells(mars, orc, cache, sc, gkw, okw, bad)
+    _strict_stats(g_stats, o_stats, touched, which)
 
 
 def test_lane_settings_and_autotuned_lanes(mars):

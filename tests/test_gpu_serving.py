@@ -24,8 +24,8 @@ def mars():
     return M
 
 
-def _submit(srv, scene, *, seed, key, iterations=5, warmup=2, grid_n=16, max_depth=6):
-    return srv.submit(scene, grid_n=grid_n, techniques=TECH, max_depth=max_depth, iterations=iterations,
+def _submit(srv, scene, *, seed, key, iterations=5, warmup=2, grid_n=16, max_depth=6, techniques=TECH):
+    return srv.submit(scene, grid_n=grid_n, techniques=techniques, max_depth=max_depth, iterations=iterations,
                       warmup=warmup, seed=seed, key=key)
 
 
@@ -79,6 +79,40 @@ def test_job_result_is_the_same_alone_and_in_the_mix(mars):
     assert ok >= 0.99, f"only {ok:.4f} of pixels agree"
     assert abs(mix.mean() - alone.mean()) <= 1e-3 * alone.mean()
     assert np.isfinite(mix).all() and alone.mean() > 0
+    srv.close()
+
+
+def test_first_mars_iteration_agrees_alone_and_in_the_mix_at_the_parity_bar(mars):
+    """A job of two warm-up iterations and one MARS iteration (BSDF + NEE, so no
+    float32 guide deposit feeds the counts), alone and beside three other jobs
+    on their own streams.  Its warm-up images are bitwise reproducible, but its
+    counts are not bitwise: the order in which thread blocks allocate queue
+    slots, and with it the grouping of the float32 partial sums of the local
+    statistics, varies from run to run, so the float64 sums (and the float32 q
+    fields) differ in their last bits.  The one MARS iteration -- the job's
+    returned image -- therefore meets the oracle parity bar: at least 99.9 % of
+    the pixels within 1e-4 relative, and the image mean within 1e-5."""
+    A = W.guided_room_scene(12, 64, 64, n_spheres=24)
+    kw = dict(seed=9, key=31, iterations=3, warmup=2, techniques=W.TECH_BSDF | W.TECH_NEE)
+    srv = mars.Server(8 << 30, 1)
+    ja = _submit(srv, A, **kw)
+    st, imgs = _wait(mars, srv, [ja])
+    assert st[ja]["state"] == mars.MARS_JOB_DONE and st[ja]["iterations_done"] == 3
+    alone = imgs[ja]
+    srv.close()
+    srv = mars.Server(8 << 30, 4)
+    others = [W.guided_room_scene(40 + k, r, r, n_spheres=n) for k, (r, n) in
+              enumerate([(128, 200), (96, 16), (160, 1000)])]
+    ids = [_submit(srv, others[0], seed=6, key=1, iterations=6)]
+    ids.append(_submit(srv, A, **kw))
+    ids += [_submit(srv, o, seed=7 + k, key=2 + k, iterations=5) for k, o in enumerate(others[1:])]
+    st, imgs = _wait(mars, srv, ids)
+    assert all(s["state"] == mars.MARS_JOB_DONE for s in st.values())
+    mix = imgs[ids[1]]
+    ok = (np.abs(mix - alone) <= 1e-4 * np.abs(alone) + 1e-7).all(axis=-1).mean()
+    print(f"first MARS iteration: {ok:.5f} of pixels within 1e-4, {np.mean(mix == alone):.5f} bitwise")
+    assert ok >= 0.999, f"only {ok:.5f} of pixels agree"
+    assert abs(mix.mean() - alone.mean()) <= 1e-5 * alone.mean() and alone.mean() > 0
     srv.close()
 
 
