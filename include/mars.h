@@ -270,6 +270,8 @@ typedef struct {
   int32_t* oct_nodes;
   int32_t* oct_leaf_level;
   int32_t oct_n_nodes, oct_n_leaves;
+  float* pixel_rays;      /* get_state only: [pixels] rays of each pixel's path tree in the last
+                             rendered iteration (its camera ray and every sample drawn below it) */
 } mars_cache_state;
 
 typedef struct {

@@ -73,6 +73,7 @@ class State(ct.Structure):
         ("est", ct.POINTER(ct.c_float)), ("oct_nodes", ct.POINTER(ct.c_int32)),
         ("image", ct.POINTER(ct.c_double)), ("stats", ct.POINTER(ct.c_double)),
         ("hist", ct.POINTER(ct.c_double)), ("counters", ct.POINTER(ct.c_double)),
+        ("px_rays", ct.POINTER(ct.c_double)),
     ]
 
 
@@ -167,11 +168,12 @@ class _SceneHolder:
 
 
 class RenderResult:
-    def __init__(self, image, stats, hist, counters):
+    def __init__(self, image, stats, hist, counters, px_rays=None):
         self.image = image          # [pixels, 3] float64
         self.stats = stats          # [cells, 3, 8] float64
         self.hist = hist            # [cells, 256] float64
         self.counters = counters    # rays, traced vertices, estimator vertices, sum beta x3
+        self.px_rays = px_rays      # [pixels] rays of each pixel's path tree (rendered pixels)
 
     @property
     def rays(self) -> float:
@@ -217,16 +219,17 @@ def render(scene, *, grid_n, techniques, max_depth, mode=MODE_WARMUP, weights=WE
     stats = np.zeros((cells, NT, NSTAT), np.float64)
     hist = np.zeros((cells, GUIDE_BINS), np.float64)
     counters = np.zeros(8, np.float64)
+    px_rays = np.zeros(npx, np.float64)
     sh = _SceneHolder(scene)
     P = Params(grid_n, techniques, max_depth, mode, weights, seed, job, iteration,
                clamp_lo, clamp_hi, outlier, int(has_est), int(bool(collect)), float(max_mult))
     S = State(_p(q_rr, ct.c_float), _p(q_s, ct.c_float), _p(valid, ct.c_uint8),
               _p(guide_cdf, ct.c_float), _p(est, ct.c_float), _p(oct_nodes, ct.c_int32), _p(image, ct.c_double),
-              _p(stats, ct.c_double), _p(hist, ct.c_double), _p(counters, ct.c_double))
+              _p(stats, ct.c_double), _p(hist, ct.c_double), _p(counters, ct.c_double), _p(px_rays, ct.c_double))
     rc = L.orc_render(ct.byref(sh.desc), ct.byref(P), ct.byref(S), int(px_begin), int(px_end))
     if rc != 0:
         raise ValueError(f"orc_render failed with {rc}")
-    return RenderResult(image, stats, hist, counters)
+    return RenderResult(image, stats, hist, counters, px_rays)
 
 
 def render_samples(scene, n, *, grid_n, techniques, max_depth, mode=MODE_WARMUP, weights=WEIGHTS_AWARE,
@@ -256,7 +259,7 @@ def render_samples(scene, n, *, grid_n, techniques, max_depth, mode=MODE_WARMUP,
                int(has_est), int(bool(collect)), 0.0)
     S = State(_p(q_rr, ct.c_float), _p(q_s, ct.c_float), _p(valid, ct.c_uint8), ct.POINTER(ct.c_float)(),
               _p(est, ct.c_float), ct.POINTER(ct.c_int32)(), _p(image, ct.c_double), _p(stats, ct.c_double),
-              _p(hist, ct.c_double), _p(counters, ct.c_double))
+              _p(hist, ct.c_double), _p(counters, ct.c_double), ct.POINTER(ct.c_double)())
     out = np.zeros((n, 3), np.float64)
     for k in range(n):
         P.iteration = k

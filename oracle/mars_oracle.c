@@ -876,6 +876,7 @@ int orc_render(const orc_scene_desc* scene, const orc_params* P, orc_state* st, 
     trace_sample(&R, C.cam_o, d, 1, 0, &ri, v, &cost, NULL);
     for (int c = 0; c < 3; ++c) st->image[3 * px + c] = v[c];
     st->counters[0] += cost;
+    if (st->px_rays) st->px_rays[px] = cost;
   }
   ctx_free(&C);
   return 0;

@@ -77,6 +77,7 @@ typedef struct {
   double* hist;               /* [cells][256] guide deposits */
   double* counters;           /* [0] rays (cost units) [1] traced path vertices
                                  [2] estimator vertices [3..5] sum of beta per technique */
+  double* px_rays;            /* [pixels] rays of each pixel's path tree (written; may be NULL) */
 } orc_state;
 
 /* Render pixels [px_begin, px_end) of one iteration depth-first.  Returns 0 on

@@ -84,6 +84,7 @@ class mars_cache_state(ct.Structure):
         ("VI", ct.c_double), ("CI", ct.c_double),
         ("oct_nodes", ct.POINTER(ct.c_int32)), ("oct_leaf_level", ct.POINTER(ct.c_int32)),
         ("oct_n_nodes", ct.c_int32), ("oct_n_leaves", ct.c_int32),
+        ("pixel_rays", ct.POINTER(ct.c_float)),
     ]
 
 

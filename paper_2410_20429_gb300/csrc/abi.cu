@@ -1319,6 +1319,11 @@ mars_status get_state_impl(mars_cache* c, mars_cache_state* s, cudaStream_t st) 
       (e = cudaMemcpy2DAsync(s->run_sum, 3 * sizeof(float), c->d_run, sizeof(float4), 3 * sizeof(float), (size_t)px,
                              cudaMemcpyDeviceToHost, st)) != cudaSuccess)
     return poison(c, e, "state copy");
+  // the fourth channel of the iteration image holds each pixel's ray count
+  if (s->pixel_rays &&
+      (e = cudaMemcpy2DAsync(s->pixel_rays, sizeof(float), reinterpret_cast<const float*>(c->d_img) + 3,
+                             sizeof(float4), sizeof(float), (size_t)px, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return poison(c, e, "state copy");
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return poison(c, e, "state copy");
   for (size_t k = 0; k < s32.size(); ++k) s->stats[k] = (double)s32[k];
   if (!s64.empty()) {

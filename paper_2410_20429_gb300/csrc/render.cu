@@ -831,7 +831,7 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_reverse(const DevSce
       const uint32_t cost = 1u + csub;
       a.S[i] = f4(E, __uint_as_float(cost));
       if (d == 1 && chk(it.tile_begin + li < (unsigned long long)c.n_pixels, MARS_CHECK_PIXEL, ctr))
-        c.img[it.tile_begin + li] = f4(E, 0.0f);
+        c.img[it.tile_begin + li] = f4(E, (float)cost);  // w: rays of the pixel's path tree
       if (guide_dep) {
         const float wdep = (v4.x + lum(Lr)) * v4.y;
         if (wdep > 0.0f && chk(__float_as_uint(v4.z) < (uint32_t)c.n_cells, MARS_CHECK_CELL, ctr) &&

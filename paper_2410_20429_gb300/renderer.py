@@ -196,6 +196,7 @@ class Cache:
             "q_rr": np.zeros((c, 3, 3), np.float32), "q_s": np.zeros((c, 3, 3), np.float32),
             "valid": np.zeros((c, 3), np.uint8), "stats": np.zeros((c, 3, 8), np.float64),
             "pixel_estimate": np.zeros((px, 3), np.float32), "run_sum": np.zeros((px, 3), np.float32),
+            "pixel_rays": np.zeros(px, np.float32),
         }
         guided = bool(self.techniques & A.MARS_TECH_GUIDED)
         if guided:
@@ -205,6 +206,7 @@ class Cache:
         s.q_rr, s.q_s = _dp(out["q_rr"], ct.c_float), _dp(out["q_s"], ct.c_float)
         s.valid, s.stats = _dp(out["valid"], ct.c_uint8), _dp(out["stats"], ct.c_double)
         s.pixel_estimate, s.run_sum = _dp(out["pixel_estimate"], ct.c_float), _dp(out["run_sum"], ct.c_float)
+        s.pixel_rays = _dp(out["pixel_rays"], ct.c_float)
         if guided:
             s.guide_hist, s.guide_cdf = _dp(out["guide_hist"], ct.c_float), _dp(out["guide_cdf"], ct.c_float)
         if self.octree:
