@@ -71,8 +71,11 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
  * key = (seed, job); counter = (pixel, iteration << 16 | dimension,
  * lineage low word, lineage high word).  Dimension: technique slot * 32 +
  * sample index for technique samples, 96 for the Alg. 1 draw, 97 for the
- * camera jitter.  Each uniform takes the top 24 bits of one output word. */
-enum { DIM_ROUND = 96, DIM_CAMERA = 97 };
+ * camera jitter, 128 + 8 s + k for step k of the light subpath of light
+ * connection sample s (k = 0: light and point, 1: emission direction, k >= 2:
+ * the bounce at the subpath's (k - 1)-th surface vertex and its Russian
+ * roulette).  Each uniform takes the top 24 bits of one output word. */
+enum { DIM_ROUND = 96, DIM_CAMERA = 97, DIM_LIGHT = 128 };
 static void rng4(const orc_params* P, uint32_t px, uint32_t dim, uint64_t lin, double u[4]) {
   uint32_t ctr[4] = {px, (P->iteration << 16) | dim, (uint32_t)lin, (uint32_t)(lin >> 32)};
   uint32_t key[2] = {P->seed, P->job};
@@ -461,12 +464,27 @@ double orc_vertex_count(const float* q_rr, const float* q_s, const double* T, co
 }
 
 /* ----------------------------------------------------------------- renderer */
+/* A vertex of a full path in camera order (bidirectional application): its
+ * position, unit geometric normal and material, the unit directions towards
+ * the previous vertex (dp, towards the camera) and the next one (dn, towards
+ * the light), and the distance tn to the next vertex. */
+typedef struct {
+  v3 p, ng, dp, dn;
+  int mat;
+  double tn;
+} pathv_t;
+#define ORC_MAXP 32
+
 typedef struct {
   const ctx_t* C;
   const orc_params* P;
   orc_state* st;
   int px;
   int on[ORC_NT];  /* technique enabled */
+  int bd;          /* bidirectional application: slot 2 is the light connection */
+  /* the camera vertices x_1..x_k of the path being traced, index = depth; dn and
+   * tn of x_j are those of the segment towards x_{j+1} (set before it is traced) */
+  pathv_t cam[ORC_MAXP];
 } rnd_t;
 
 static void cell_coords(const ctx_t* C, int N, v3 p, int idx[3]) {
@@ -617,6 +635,297 @@ static double nee_pdf_at(const ctx_t* C, int quad, v3 x, v3 y, v3 wi) {
   return 0.0;
 }
 
+/* ------------------------------------------- bidirectional application
+ * Sec. 5 combines three techniques at every camera vertex, each with its own
+ * budget: path tracing (the BSDF continuation), NEE, and connections to the
+ * vertices of light subpaths ("light connection", slot 2).  Readings (the
+ * paper gives no formulas for them):
+ *  - one light connection sample at x_i traces one light subpath of its own:
+ *    a light chosen as for NEE (area x radiance) with a uniform point y_0,
+ *    a cosine-distributed emission direction, BSDF sampling at every surface
+ *    vertex, throughput-based Russian roulette after each bounce (continue
+ *    with probability q = min(1, max_ch f cos / p) and divide by it; Sec. 5:
+ *    light paths are never split), at most ORC_LIGHT_MAX surface vertices and
+ *    at most D - 1 - i (the full path keeps at most D segments); the sample
+ *    connects x_i to every surface vertex y_1..y_m of it (y_0 is NEE's), and
+ *    its value is the sum of the weighted connections;
+ *  - a light connection sample is drawn only at vertices with i <= D - 2 (a
+ *    connection from x_{D-1} would exceed D segments); its base budget is 1,
+ *    as NEE's;
+ *  - the weights are the balance heuristic over every strategy that samples
+ *    the same full path z_1..z_n (z_n on a light): the camera path alone
+ *    (BSDF sampling to z_n), NEE at z_{n-1}, and light connection at z_i for
+ *    i = 1..n-2 with n - 1 - i <= ORC_LIGHT_MAX light surface vertices; each
+ *    strategy's density is multiplied by its expected sample count, the
+ *    product of the budgets of the camera vertices it passes through (BSDF
+ *    budgets, then the budget of its last technique) -- budget-aware
+ *    multi-sample MIS over whole paths (budget-unaware: every count 1); the
+ *    budgets at vertices that a strategy would have reached as camera vertices
+ *    are evaluated by the count rule there, with the throughput T of a camera
+ *    path through them;
+ *  - the BSDF continuation carries no MIS weight (w_ind = 1): every
+ *    contribution is weighted once, where its full path ends;
+ *  - the local outlier clamp is off (Sec. 5.1: local outlier rejection
+ *    lowered efficiency in this application). */
+
+/* light index of quad primitive q, -1 if it does not emit */
+static int light_of_quad(const ctx_t* C, int q) {
+  for (int l = 0; l < C->n_lights; ++l)
+    if (C->light_quad[l] == q) return l;
+  return -1;
+}
+
+/* end point of a full path: a point on light l */
+typedef struct {
+  int l;
+  v3 p, n;     /* point, unit emitting normal */
+  double pN;   /* area density of NEE's light point (pmf / area) */
+} light_end;
+
+static light_end light_end_at(const ctx_t* C, int l, v3 y) {
+  light_end e;
+  const double* q = C->d->quads + 9 * C->light_quad[l];
+  v3 n = cross(ld3(q + 3), ld3(q + 6));
+  double area = len(n);
+  e.l = l;
+  e.p = y;
+  e.n = scl(n, 1.0 / area);
+  e.pN = C->light_pmf[l] / area;
+  return e;
+}
+
+/* f |cos wi| and the BSDF-sampling density of wi given wo at a path vertex,
+ * the shading normal facing wo */
+static void bsdf_at(const ctx_t* C, const pathv_t* z, v3 wo, v3 wi, double fc[3], double* pdf) {
+  v3 ns = dot(z->ng, wo) >= 0.0 ? z->ng : scl(z->ng, -1.0);
+  v3 b1, b2;
+  onb(ns, &b1, &b2);
+  bsdf_eval(mat_of(C->d, z->mat), to_local(wo, b1, b2, ns), to_local(wi, b1, b2, ns), fc, pdf);
+}
+
+static double max3(const double* a) { return fmax(a[0], fmax(a[1], a[2])); }
+
+/* technique t drawn at a camera vertex of this depth */
+static int tech_at(const rnd_t* R, int t, int depth) {
+  if (!R->on[t]) return 0;
+  if (R->bd && t == ORC_T_LIGHT && depth > R->P->max_depth - 2) return 0;
+  return 1;
+}
+
+static int cell_at(const rnd_t* R, v3 p) {
+  return R->st->oct_nodes ? octree_cell(R->C, R->st->oct_nodes, p) : cell_of(R->C, R->P->grid_n, p);
+}
+
+/* Budgets beta_t at a vertex of depth `depth` in `cell` with throughput T and
+ * path multiplicity mult.  Without learned counts (warm-up, fixed-count mode,
+ * cells without statistics) every vertex draws one NEE sample (and one light
+ * connection sample) and one continuation sample split evenly over the
+ * continuation techniques (BSDF, guided): Sec. 4.1 "Fixed-point iteration"
+ * warms up without splitting; with two continuation techniques beta = 1 each
+ * would double every path at every bounce.  Alg. 1 turns (1/2, 1/2) into
+ * exactly one continuation.  With a multiplicity cap M > 0 every budget is
+ * further limited to max(clamp_lo, M / mult) (in float32).  The budgets are
+ * carried in float32. */
+static void budgets_at(const rnd_t* R, int cell, int depth, const double T[3], float mult, float betaf[ORC_NT]) {
+  const orc_params* P = R->P;
+  const orc_state* st = R->st;
+  const int guided = R->on[ORC_T_GUIDED] && !R->bd;
+  const double base_cont = 1.0 / (double)(R->on[ORC_T_BSDF] + guided);
+  for (int t = 0; t < ORC_NT; ++t) {
+    betaf[t] = 0.0f;
+    if (!tech_at(R, t, depth)) continue;
+    double b = (t == ORC_T_NEE || (R->bd && t == ORC_T_LIGHT)) ? 1.0 : base_cont;
+    if (P->mode == ORC_MODE_MARS && st->valid[cell * ORC_NT + t]) {
+      size_t o = ((size_t)cell * ORC_NT + t) * 3;
+      b = orc_vertex_count(st->q_rr + o, st->q_s + o, T, st->est + 3 * R->px, P->clamp_lo, P->clamp_hi);
+    }
+    betaf[t] = (float)b;
+    if (P->max_mult > 0.0f) {
+      float cap = P->max_mult / mult;
+      if (cap < (float)P->clamp_lo) cap = (float)P->clamp_lo;
+      if (betaf[t] > cap) betaf[t] = cap;
+    }
+  }
+}
+
+enum { STRAT_CAMERA = 0, STRAT_NEE = 1, STRAT_LIGHT = 2 };
+
+/* Balance-heuristic weight, over every strategy that samples it, of the full
+ * path z[1..n-1], e (camera order; z[0] unused), for the strategy `kind`
+ * (STRAT_LIGHT: connection at camera vertex z[si]).  Evaluated from the
+ * definitions, strategy by strategy:
+ *   C_1 = 1, C_{j+1} = C_j bw_B(z_j) P->_j     (camera prefix: BSDF counts x densities)
+ *   camera path: C_n;  NEE at z_{n-1}: C_{n-1} bw_N(z_{n-1}) pN;
+ *   light connection at z_i: C_i bw_L(z_i) pN prod_{j=i+1}^{n-1} P<-_j,
+ * with P->_j the area density of z_{j+1} by BSDF sampling at z_j, P<-_j the
+ * area density of z_j on a light subpath (cosine emission from z_n, or BSDF
+ * sampling at z_{j+1} towards z_j times its survival probability), pN the
+ * area density of the light point, and bw = beta (budget-aware) or 1. */
+static double path_weight(const rnd_t* R, int n, const pathv_t* z, const light_end* e, int kind, int si) {
+  const ctx_t* C = R->C;
+  const orc_params* P = R->P;
+  const int aware = P->weights == ORC_WEIGHTS_AWARE;
+  double CP[ORC_MAXP], LP[ORC_MAXP], bwN[ORC_MAXP], bwL[ORC_MAXP];
+  double T[3] = {1.0, 1.0, 1.0};
+  float mult = 1.0f;
+  for (int j = 1; j <= n - 1; ++j) {
+    float bf[ORC_NT];
+    budgets_at(R, cell_at(R, z[j].p), j, T, mult, bf);
+    double fc[3], pB;
+    bsdf_at(C, &z[j], z[j].dp, z[j].dn, fc, &pB);
+    double cos_next = j + 1 < n ? fabs(dot(z[j + 1].ng, z[j].dn)) : -dot(e->n, z[j].dn);
+    if (cos_next < 0.0) cos_next = 0.0;
+    CP[j] = (aware ? (double)bf[ORC_T_BSDF] : 1.0) * pB * cos_next / (z[j].tn * z[j].tn);
+    bwN[j] = tech_at(R, ORC_T_NEE, j) ? (aware ? (double)bf[ORC_T_NEE] : 1.0) : 0.0;
+    bwL[j] = tech_at(R, ORC_T_LIGHT, j) ? (aware ? (double)bf[ORC_T_LIGHT] : 1.0) : 0.0;
+    for (int ch = 0; ch < 3; ++ch) T[ch] = pB > 0.0 ? T[ch] * fc[ch] / pB / (double)bf[ORC_T_BSDF] : 0.0;
+    mult = mult * bf[ORC_T_BSDF];
+  }
+  for (int j = 1; j <= n - 1; ++j) {
+    double cos_j = fabs(dot(z[j].ng, z[j].dn)), g = cos_j / (z[j].tn * z[j].tn);
+    if (j == n - 1) {
+      double cl = -dot(e->n, z[j].dn);
+      LP[j] = cl > 0.0 ? cl / PI * g : 0.0;
+    } else {
+      double fc[3], pB;
+      bsdf_at(C, &z[j + 1], z[j + 1].dn, z[j + 1].dp, fc, &pB);
+      double q = pB > 0.0 ? fmin(1.0, max3(fc) / pB) : 0.0;
+      LP[j] = pB * q * g;
+    }
+  }
+  double sum = 0.0, chosen = 0.0, Cj = 1.0;
+  for (int j = 1; j <= n - 1; ++j) {
+    /* light connection at z_j to z_{j+1} (n - 1 - j light surface vertices) */
+    int k = n - 1 - j;
+    if (R->bd && k >= 1 && k <= ORC_LIGHT_MAX && bwL[j] > 0.0) {
+      double t = Cj * bwL[j] * e->pN;
+      for (int m = j + 1; m <= n - 1; ++m) t *= LP[m];
+      sum += t;
+      if (kind == STRAT_LIGHT && si == j) chosen = t;
+    }
+    if (j == n - 1 && bwN[j] > 0.0) {
+      double t = Cj * bwN[j] * e->pN;
+      sum += t;
+      if (kind == STRAT_NEE) chosen = t;
+    }
+    Cj *= CP[j];
+  }
+  sum += Cj;
+  if (kind == STRAT_CAMERA) chosen = Cj;
+  return sum > 0.0 ? chosen / sum : 0.0;
+}
+
+/* one light connection sample at camera vertex x (depth i): its light subpath
+ * and the weighted connections to it; returns the sample value and its cost
+ * (the rays its subpath traced plus one per connection) */
+static void light_connection(rnd_t* R, const vtx_t* x, int depth_i, uint64_t lin, int s, double v[3],
+                             double* cost) {
+  const ctx_t* C = R->C;
+  const orc_params* P = R->P;
+  orc_state* st = R->st;
+  v[0] = v[1] = v[2] = 0.0;
+  *cost = 0.0;
+  int kmax = P->max_depth - 1 - depth_i;
+  if (kmax > ORC_LIGHT_MAX) kmax = ORC_LIGHT_MAX;
+  if (kmax < 1 || C->n_lights == 0) return;
+  double u[4];
+  /* y_0: light by area x radiance (decided in float32), uniform point */
+  rng4(P, (uint32_t)R->px, (uint32_t)(DIM_LIGHT + 8 * s), lin, u);
+  int l = C->n_lights - 1;
+  for (int k = 0; k < C->n_lights; ++k)
+    if ((float)u[0] < C->light_cdf[k]) { l = k; break; }
+  const double* q = C->d->quads + 9 * C->light_quad[l];
+  v3 y0 = add(ld3(q), add(scl(ld3(q + 3), u[1]), scl(ld3(q + 6), u[2])));
+  light_end e = light_end_at(C, l, y0);
+  const double* Le = mat_of(C->d, C->d->quad_mat[C->light_quad[l]]) + 5;
+  /* cosine-distributed emission direction about the light's normal */
+  rng4(P, (uint32_t)R->px, (uint32_t)(DIM_LIGHT + 8 * s + 1), lin, u);
+  v3 b1, b2;
+  onb(e.n, &b1, &b2);
+  double r = sqrt(u[0]), phi = 2.0 * PI * u[1], zc = 1.0 - u[0];
+  v3 dir = to_world(mk(r * cos(phi), r * sin(phi), sqrt(zc > 0.0 ? zc : 0.0)), b1, b2, e.n);
+  v3 org = add(y0, scl(e.n, C->eps));
+  /* alpha_1 = Le cos / (pN p_omega) = Le pi / pN */
+  double alpha[3];
+  for (int c = 0; c < 3; ++c) alpha[c] = Le[c] * PI / e.pN;
+  pathv_t y[ORC_LIGHT_MAX + 1];
+  double ya[ORC_LIGHT_MAX + 1][3];
+  int m = 0, rays = 0;
+  for (int k = 1; k <= kmax; ++k) {
+    hit_t h;
+    rays += 1;
+    st->counters[1] += 1.0;
+    st->counters[6] += 1.0;
+    if (!closest_hit(C, org, dir, &h)) break;
+    const double* mat = mat_of(C->d, h.mat);
+    if (!(mat[1] > 0.0 || mat[2] > 0.0 || mat[3] > 0.0)) break;
+    pathv_t* yk = &y[k];
+    yk->p = h.p;
+    yk->ng = h.ng;
+    yk->mat = h.mat;
+    yk->dn = scl(dir, -1.0);   /* camera order: towards y_{k-1} */
+    yk->tn = h.t;
+    for (int c = 0; c < 3; ++c) ya[k][c] = alpha[c];
+    yk->dp = mk(0, 0, 0);      /* towards the camera side: set by the connection */
+    m = k;
+    if (k == kmax) break;
+    /* continue: BSDF sampling at y_k with the light arriving from y_{k-1} */
+    rng4(P, (uint32_t)R->px, (uint32_t)(DIM_LIGHT + 8 * s + k + 1), lin, u);
+    v3 l_in = yk->dn;
+    v3 ns = dot(h.ng, l_in) >= 0.0 ? h.ng : scl(h.ng, -1.0);
+    v3 c1, c2;
+    onb(ns, &c1, &c2);
+    v3 wl;
+    if (!bsdf_sample(mat, to_local(l_in, c1, c2, ns), u[0], u[1], &wl)) break;
+    v3 o = to_world(wl, c1, c2, ns);
+    double fc[3], pB;
+    bsdf_eval(mat, to_local(l_in, c1, c2, ns), wl, fc, &pB);
+    if (!(pB > 0.0) || !(fc[0] > 0.0 || fc[1] > 0.0 || fc[2] > 0.0)) break;
+    double qk = fmin(1.0, max3(fc) / pB);
+    if (!((float)u[2] < (float)qk)) break;   /* Russian roulette, decided in float32 */
+    for (int c = 0; c < 3; ++c) alpha[c] *= fc[c] / pB / qk;
+    org = add(h.p, scl(ns, C->eps));
+    dir = o;
+  }
+  *cost = (double)(rays + m);
+  /* connections x_i -- y_k */
+  v3 xo = add(x->p, scl(x->ns, C->eps));
+  for (int k = 1; k <= m; ++k) {
+    v3 nsy = dot(y[k].ng, y[k].dn) >= 0.0 ? y[k].ng : scl(y[k].ng, -1.0);
+    v3 yo = add(y[k].p, scl(nsy, C->eps));
+    v3 dv = sub(yo, xo);
+    double dist = len(dv);
+    v3 w = scl(dv, 1.0 / dist);
+    double fx[3], px_, fy[3], py;
+    bsdf_eval(mat_of(C->d, x->mat), to_local(x->wo, x->b1, x->b2, x->ns), to_local(w, x->b1, x->b2, x->ns), fx,
+              &px_);
+    pathv_t yv = y[k];
+    yv.dp = scl(w, -1.0);
+    bsdf_at(C, &yv, y[k].dn, scl(w, -1.0), fy, &py);
+    double cval[3];
+    int nz = 0;
+    for (int c = 0; c < 3; ++c) {
+      cval[c] = ya[k][c] * fy[c] * fx[c] / (dist * dist);
+      nz |= cval[c] > 0.0;
+    }
+    if (!nz) continue;
+    /* the full path: x_1..x_i, y_k..y_1, y_0 */
+    pathv_t z[ORC_MAXP];
+    for (int j = 1; j <= depth_i; ++j) z[j] = R->cam[j];
+    z[depth_i].dn = w;
+    z[depth_i].tn = dist;
+    for (int a = 1; a <= k; ++a) {
+      z[depth_i + a] = y[k - a + 1];
+      z[depth_i + a].dp = a == 1 ? scl(w, -1.0) : scl(y[k - a + 2].dn, -1.0);
+    }
+    int n = depth_i + 1 + k;
+    double wgt = path_weight(R, n, z, &e, STRAT_LIGHT, depth_i);
+    st->counters[7] += 1.0;
+    if (occluded(C, xo, w, dist - C->eps)) continue;
+    for (int c = 0; c < 3; ++c) v[c] += wgt * cval[c];
+  }
+}
+
 /* Trace a ray drawn at the parent (or the camera) and return its sample value
  * fcp * (Le * w_dir + w_ind * <L_r(child)>), its cost in rays, and the
  * luminance of the incident radiance estimate (for guide learning). */
@@ -643,10 +952,22 @@ static void trace_sample(rnd_t* R, v3 o, v3 d, int depth, uint64_t lin, const ra
     v3 wo = scl(d, -1.0);
     const double* m = mat_of(C->d, h.mat);
     double cosg = dot(h.ng, wo);
+    if (!ri->camera && R->bd) {
+      /* the parent's segment towards this hit */
+      R->cam[depth - 1].dn = d;
+      R->cam[depth - 1].tn = h.t;
+    }
     if (cosg > 0.0 && mean3(m + 5) > 0.0) {
-      /* emission reached by a technique sample: weight against NEE's density */
+      /* emission reached by a technique sample: weight against NEE's density
+       * (and, bidirectionally, against every strategy of the full path) */
       double w_dir = 1.0;
-      if (!ri->camera) {
+      if (!ri->camera && R->bd) {
+        int l = h.prim < C->d->n_quads ? light_of_quad(C, h.prim) : -1;
+        if (l >= 0) {
+          light_end e = light_end_at(C, l, h.p);
+          w_dir = path_weight(R, depth, R->cam, &e, STRAT_CAMERA, 0);
+        }
+      } else if (!ri->camera) {
         double pn = 0.0;
         if (ri->betaN_pN0 > 0.0 && h.prim < C->d->n_quads)
           pn = nee_pdf_at(C, h.prim, o, h.p, d);
@@ -666,7 +987,7 @@ static void trace_sample(rnd_t* R, v3 o, v3 d, int depth, uint64_t lin, const ra
       x.wo = wo;
       x.ns = cosg >= 0.0 ? h.ng : scl(h.ng, -1.0);
       x.mat = h.mat;
-      x.cell = R->st->oct_nodes ? octree_cell(C, R->st->oct_nodes, h.p) : cell_of(C, P->grid_n, h.p);
+      x.cell = cell_at(R, h.p);
       onb(x.ns, &x.b1, &x.b2);
       secondary_estimator(R, &x, depth, lin, ri->T_child, ri->mult_child, Lchild, &ccost);
     }
@@ -686,8 +1007,9 @@ static void stat_add(rnd_t* R, int cell, int t, const double v[3], double cost, 
   for (int c = 0; c < 3; ++c) {
     double x = v[c];
     /* local outlier clamp (Sec. 4.1): the sample's image contribution is kept
-     * below outlier x pixel estimate, i.e. v <= outlier * I_px / T */
-    if (R->P->has_estimate && T[c] > 0.0) {
+     * below outlier x pixel estimate, i.e. v <= outlier * I_px / T (not in the
+     * bidirectional application, Sec. 5.1) */
+    if (R->P->has_estimate && T[c] > 0.0 && !R->bd) {
       double lim = R->P->outlier * (double)R->st->est[3 * R->px + c] / T[c];
       if (x > lim) x = lim;
     }
@@ -700,10 +1022,8 @@ static void stat_add(rnd_t* R, int cell, int t, const double v[3], double cost, 
 /* Secondary estimator at vertex x (Sec. 3.1): sum over techniques t of
  * 1/beta_t times the sum of gamma_t primary estimates, gamma from Alg. 1.
  * mult is the path multiplicity at x: the product of the budgets of the
- * techniques that drew the path's earlier vertices (1 at the first vertex).
- * With a cap M > 0 every budget is further limited to max(clamp_lo, M / mult)
- * (in float32), which bounds the expected number of vertices per depth that one
- * camera sample spawns by M; any budget field keeps the estimator unbiased. */
+ * techniques that drew the path's earlier vertices (1 at the first vertex),
+ * see budgets_at. */
 static void secondary_estimator(rnd_t* R, const vtx_t* x, int depth, uint64_t lin, const double T[3],
                                 float mult, double Lr[3], double* cost) {
   const ctx_t* C = R->C;
@@ -713,41 +1033,29 @@ static void secondary_estimator(rnd_t* R, const vtx_t* x, int depth, uint64_t li
   Lr[0] = Lr[1] = Lr[2] = 0.0;
   *cost = 0.0;
   st->counters[2] += 1.0;
+  if (R->bd) {
+    R->cam[depth].p = x->p;
+    R->cam[depth].ng = x->ng;
+    R->cam[depth].dp = x->wo;
+    R->cam[depth].mat = x->mat;
+  }
 
-  /* budgets beta_t(x).  Without learned counts (warm-up, fixed-count mode,
-   * cells without statistics) every vertex draws one NEE sample and one
-   * continuation sample split evenly over the continuation techniques (BSDF,
-   * guided): Sec. 4.1 "Fixed-point iteration" warms up without splitting; with
-   * two continuation techniques beta = 1 each would double every path at every
-   * bounce.  Alg. 1 turns beta = (1/2, 1/2) into exactly one continuation. */
-  float betaf[ORC_NT] = {0, 0, 0};
-  double beta[ORC_NT] = {0, 0, 0};
-  const double base_cont = 1.0 / (double)(R->on[ORC_T_BSDF] + R->on[ORC_T_GUIDED]);
+  float betaf[ORC_NT];
+  double beta[ORC_NT];
+  budgets_at(R, x->cell, depth, T, mult, betaf);
   for (int t = 0; t < ORC_NT; ++t) {
-    if (!R->on[t]) continue;
-    double b = t == ORC_T_NEE ? 1.0 : base_cont;
-    if (P->mode == ORC_MODE_MARS && st->valid[x->cell * ORC_NT + t]) {
-      size_t o = ((size_t)x->cell * ORC_NT + t) * 3;
-      b = orc_vertex_count(st->q_rr + o, st->q_s + o, T, st->est + 3 * R->px, P->clamp_lo, P->clamp_hi);
-    }
-    betaf[t] = (float)b;       /* the budget is carried in float32 */
-    if (P->max_mult > 0.0f) {
-      float cap = P->max_mult / mult;
-      if (cap < (float)P->clamp_lo) cap = (float)P->clamp_lo;
-      if (betaf[t] > cap) betaf[t] = cap;
-    }
     beta[t] = (double)betaf[t];
     st->counters[3 + t] += beta[t];
   }
 
-  /* Alg. 1 */
+  /* Alg. 1 over the techniques drawn at this vertex */
   double u[4];
   rng4(P, (uint32_t)R->px, DIM_ROUND, lin, u);
   float rb[ORC_NT];
   int32_t gam[ORC_NT];
   int n_on = 0, idx[ORC_NT];
   for (int t = 0; t < ORC_NT; ++t)
-    if (R->on[t]) { rb[n_on] = betaf[t]; idx[n_on++] = t; }
+    if (tech_at(R, t, depth)) { rb[n_on] = betaf[t]; idx[n_on++] = t; }
   int32_t gtmp[ORC_NT];
   orc_stochastic_round(n_on, rb, (float)u[0], gtmp);
   for (int t = 0; t < ORC_NT; ++t) gam[t] = 0;
@@ -757,11 +1065,19 @@ static void secondary_estimator(rnd_t* R, const vtx_t* x, int depth, uint64_t li
   int aware = P->weights == ORC_WEIGHTS_AWARE;
   double bw[ORC_NT];
   for (int t = 0; t < ORC_NT; ++t) bw[t] = R->on[t] ? (aware ? beta[t] : 1.0) : 0.0;
-  const float* cdf = (R->on[ORC_T_GUIDED]) ? st->guide_cdf + (size_t)x->cell * ORC_GUIDE_BINS : NULL;
+  if (R->bd) bw[ORC_T_LIGHT] = 0.0;   /* not a direction-sampling technique */
+  const float* cdf = (R->on[ORC_T_GUIDED] && !R->bd) ? st->guide_cdf + (size_t)x->cell * ORC_GUIDE_BINS : NULL;
 
   for (int t = 0; t < ORC_NT; ++t) {
     for (int s = 0; s < gam[t]; ++s) {
       double v[3] = {0, 0, 0}, c_s = 1.0;
+      if (R->bd && t == ORC_T_LIGHT) {
+        light_connection(R, x, depth, lin, s, v, &c_s);
+        for (int c = 0; c < 3; ++c) Lr[c] += v[c] / beta[t];
+        *cost += c_s;
+        stat_add(R, x->cell, t, v, c_s, T);
+        continue;
+      }
       rng4(P, (uint32_t)R->px, (uint32_t)(t * 32 + s), lin, u);
       if (t == ORC_T_NEE) {
         /* primary estimator of NEE: light by area x radiance, uniform point */
@@ -782,8 +1098,17 @@ static void secondary_estimator(rnd_t* R, const vtx_t* x, int depth, uint64_t li
           bsdf_eval(m, to_local(x->wo, x->b1, x->b2, x->ns), to_local(wi, x->b1, x->b2, x->ns), fc, &pb);
           if (cdf) pg = orc_guide_pdf(cdf, (double[]){wi.x, wi.y, wi.z});
           if ((fc[0] > 0.0 || fc[1] > 0.0 || fc[2] > 0.0) && !occluded(C, xo, wi, dist - C->eps)) {
-            double den = bw[ORC_T_BSDF] * pb + bw[ORC_T_GUIDED] * pg + bw[ORC_T_NEE] * pn;
-            double w = bw[ORC_T_NEE] * pn / den;
+            double w;
+            if (R->bd) {
+              /* the full path x_1..x_depth, y: weight over every strategy */
+              R->cam[depth].dn = wi;
+              R->cam[depth].tn = dist;
+              light_end e = light_end_at(C, l, y);
+              w = path_weight(R, depth + 1, R->cam, &e, STRAT_NEE, 0);
+            } else {
+              double den = bw[ORC_T_BSDF] * pb + bw[ORC_T_GUIDED] * pg + bw[ORC_T_NEE] * pn;
+              w = bw[ORC_T_NEE] * pn / den;
+            }
             const double* Le = mat_of(C->d, C->d->quad_mat[qi]) + 5;
             for (int c = 0; c < 3; ++c) v[c] = fc[c] * Le[c] / pn * w;
           }
@@ -847,6 +1172,8 @@ int orc_render(const orc_scene_desc* scene, const orc_params* P, orc_state* st, 
   if (P->clamp_hi > 30.0 || P->clamp_lo < 0.0) return -1;
   if (P->mode == ORC_MODE_MARS && !P->has_estimate) return -2;
   if ((P->techniques & 4) && !st->guide_cdf) return -1;
+  if ((P->techniques & 4) && (P->techniques & ORC_TECH_LIGHT)) return -1;
+  if (P->max_depth + ORC_LIGHT_MAX + 2 > ORC_MAXP) return -1;
   ctx_t C;
   if (ctx_init(&C, scene, P) != 0) { ctx_free(&C); return -3; }
   if ((P->max_depth - 1) * C.bits > 64) { ctx_free(&C); return -1; }
@@ -857,6 +1184,8 @@ int orc_render(const orc_scene_desc* scene, const orc_params* P, orc_state* st, 
   R.P = P;
   R.st = st;
   for (int t = 0; t < ORC_NT; ++t) R.on[t] = (P->techniques >> t) & 1;
+  R.bd = (P->techniques & ORC_TECH_LIGHT) != 0;
+  if (R.bd) R.on[ORC_T_LIGHT] = 1;
   for (int px = px_begin; px < px_end; ++px) {
     R.px = px;
     double u[4];

@@ -22,11 +22,19 @@
 extern "C" {
 #endif
 
-/* technique slots (fixed order BSDF, NEE, guided; Alg. 1 rounds in this order) */
+/* technique slots (fixed order BSDF, NEE, guided or light connection; Alg. 1
+ * rounds in this order).  Technique bits: 1 BSDF, 2 NEE, 4 guided, 8 light
+ * connection (the bidirectional application, Sec. 5); guided and light
+ * connection share slot 2 and exclude each other. */
 #define ORC_T_BSDF 0
 #define ORC_T_NEE 1
 #define ORC_T_GUIDED 2
+#define ORC_T_LIGHT 2
 #define ORC_NT 3
+#define ORC_TECH_LIGHT 8
+/* surface vertices of a light subpath at most (the light vertex y_0 plus 5:
+ * light subpaths of at most 6 vertices) */
+#define ORC_LIGHT_MAX 5
 /* per (cell, technique) statistics: n, sum v[3], sum v^2[3], sum cost */
 #define ORC_NSTAT 8
 #define ORC_GUIDE_BINS 256
@@ -75,8 +83,9 @@ typedef struct {
   double* image;              /* [pixels][3] one-sample pixel estimate (written) */
   double* stats;              /* [cells][3][8] */
   double* hist;               /* [cells][256] guide deposits */
-  double* counters;           /* [0] rays (cost units) [1] traced path vertices
-                                 [2] estimator vertices [3..5] sum of beta per technique */
+  double* counters;           /* [0] rays (cost units) [1] closest-hit queries (camera and light
+                                 paths) [2] estimator vertices [3..5] sum of beta per technique
+                                 [6] light-path closest-hit queries [7] connection rays traced */
   double* px_rays;            /* [pixels] rays of each pixel's path tree (written; may be NULL) */
 } orc_state;
 

@@ -875,3 +875,109 @@ def test_long_box_reference_agrees_with_a_fresh_oracle_render(orc):
     z2 = (m[ok] - ref[ok]) ** 2 / var_d[ok]
     assert 0.85 < z2.mean() < 1.2, z2.mean()
     assert np.all(np.abs(m.sum(0) - ref.sum(0)) < 4 * np.sqrt(var_d.sum(0)))
+
+
+# ----------------------------------------- bidirectional application (Sec. 5)
+TECH_BDPT = W.TECH_BSDF | W.TECH_NEE | 8   # BSDF, NEE, light connection
+
+
+@pytest.mark.parametrize("weights", [0, 1])
+@pytest.mark.parametrize("counts", ["beta1", "random"])
+def test_bidirectional_furnace_closed_form(orc, weights, counts):
+    """Sec. 5: path tracing, NEE and connections to light subpaths combined
+    with budget-aware (or -unaware) balance weights over every strategy of a
+    full path.  The closed furnace keeps its closed form Le (1 - a^D)/(1 - a)
+    under any count field: the weights of the strategies that sample a path
+    sum to one and every technique divides by its real-valued budget."""
+    albedo, D = 0.6, 5
+    sc = W.furnace_scene(albedo=albedo, radiance=1.5, width=10, height=10)
+    cells = 4 ** 3
+    q_rr, q_s, valid = W.random_count_fields(cells, seed=111, lo=0.1, hi=3.0)
+    est = W.random_pixel_estimate(sc.n_pixels, seed=112, lo=0.5, hi=4.0)
+    vals = []
+    for it in range(60):
+        kw = dict(grid_n=4, techniques=TECH_BDPT, max_depth=D, iteration=it, weights=weights)
+        if counts == "random":
+            kw.update(mode=orc.MODE_MARS, q_rr=q_rr, q_s=q_s, valid=valid, est=est)
+        r = orc.render(sc, **kw)
+        vals.append(r.image.mean())
+    assert r.stats[:, 2, 0].sum() > 0     # light connection samples were drawn
+    m, se = _mean_and_sem(vals)
+    expected = 1.5 * (1 - albedo ** D) / (1 - albedo)
+    assert abs(m - expected) < 3.5 * se + 1e-9
+
+
+def test_bidirectional_unbiased_where_light_paths_matter(orc):
+    """A heightfield lit by one small emitter hidden between two spheres (the
+    bidirectional workload's geometry, small): with random count fields for
+    all three techniques the image mean equals BSDF + NEE with budgets 1
+    within 3.5 sigma (App. A.1's unbiasedness, now over whole-path weights),
+    and the light connections carry a share of it."""
+    sc = W.heightfield_scene(3, n=6, width=32, height=24, n_spheres=6)
+    cells = 4 ** 3
+    q_rr, q_s, valid = W.random_count_fields(cells, seed=121, lo=0.1, hi=3.0)
+    est = W.random_pixel_estimate(sc.n_pixels, seed=122, lo=0.05, hi=2.0)
+    a, b, lc = [], [], []
+    for it in range(100):
+        kw = dict(grid_n=4, max_depth=5, iteration=it)
+        a.append(orc.render(sc, techniques=3, **kw).image.mean())
+        r = orc.render(sc, techniques=TECH_BDPT, mode=orc.MODE_MARS, q_rr=q_rr, q_s=q_s, valid=valid, est=est,
+                       seed=9, **kw)
+        b.append(r.image.mean())
+        lc.append(r.stats[:, 2, 1:4].sum())
+    ma, sa = _mean_and_sem(a)
+    mb, sb = _mean_and_sem(b)
+    assert abs(ma - mb) < 3.5 * math.hypot(sa, sb)
+    assert np.mean(lc) > 0
+
+
+def test_light_connection_cost_and_roulette(orc):
+    """A light connection sample costs the rays its light subpath traced plus
+    one per connection.  In the closed furnace every light ray finds a wall, so
+    each light vertex costs one ray and one connection (cost = 2 x light rays);
+    with D = 3 only first vertices draw the technique (a connection from x_2
+    would exceed D segments) and each subpath holds one vertex (cost 2 per
+    sample); with D = 4 the subpath of a first-vertex sample continues past
+    y_1 with the throughput-based survival probability, which for a grey
+    Lambertian surface is its albedo a."""
+    a = 0.625
+    sc = W.furnace_scene(albedo=a, radiance=1.0, width=12, height=12)
+    P = sc.n_pixels
+    r = orc.render(sc, grid_n=2, techniques=TECH_BDPT, max_depth=3)
+    s = r.stats[:, 2, :].sum(0)
+    assert s[0] == P and s[7] == 2 * P and r.counters[6] == P
+    n_light, rays = 0.0, []
+    for it in range(40):
+        r = orc.render(sc, grid_n=2, techniques=TECH_BDPT, max_depth=4, iteration=it)
+        s = r.stats[:, 2, :].sum(0)
+        assert s[0] == 2 * P and s[7] == 2 * r.counters[6]
+        rays.append(r.counters[6] / P)
+    # per pixel: the depth-1 sample traces 1 + Bernoulli(a) rays, the depth-2 one 1
+    m, se = _mean_and_sem(rays)
+    assert abs(m - (2 + a)) < 4 * se + 1e-9
+
+
+def test_whole_path_weights_reduce_to_the_vertex_weights_without_light_connections(orc):
+    """With the light connection's budget 0 everywhere (clamp_lo = 0 and q = 0:
+    no sample is drawn and, budget-aware, the strategy's count is 0), the
+    whole-path balance weights of the bidirectional renderer reduce to the
+    per-vertex balance heuristic of BSDF sampling and NEE (App. A.1): camera
+    path and NEE are the only strategies, and the whole-path density ratio of
+    the two is the ratio of their solid-angle densities at the last vertex.
+    The images agree to rounding at every depth.  (Budget-unaware weights
+    count every technique once whatever its budget, so they need budgets
+    above 0 -- the paper's clamp [0.05, 20] -- to stay unbiased.)"""
+    weights = 0
+    cfg = W.config_box(20, 16)
+    cells = cfg.n_cells
+    q_rr, q_s, valid = W.random_count_fields(cells, seed=131, lo=0.1, hi=3.0, p_valid=1.0)
+    q_rr[:, 2] = 0.0
+    q_s[:, 2] = 0.0
+    est = W.random_pixel_estimate(cfg.scene.n_pixels, seed=132, lo=0.05, hi=1.0)
+    kw = dict(grid_n=cfg.grid_n, max_depth=cfg.max_depth, iteration=4, seed=3, mode=orc.MODE_MARS, q_rr=q_rr,
+              q_s=q_s, valid=valid, est=est, clamp_lo=0.0, weights=weights, outlier=1e30)
+    a = orc.render(cfg.scene, techniques=3, **kw)
+    b = orc.render(cfg.scene, techniques=TECH_BDPT, **kw)
+    assert b.stats[:, 2, 0].sum() == 0 and a.rays == b.rays
+    np.testing.assert_allclose(b.image, a.image, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(b.stats[:, :2], a.stats[:, :2], rtol=1e-12, atol=1e-15)
