@@ -52,14 +52,28 @@ typedef struct mars_scene mars_scene;
 typedef struct mars_cache mars_cache;
 typedef struct mars_server mars_server;
 
-/* technique bits and slots; slots are the order Alg. 1 rounds in */
+/* technique bits and slots; slots are the order Alg. 1 rounds in.
+ * MARS_TECH_LIGHT: connections to light subpaths, the third technique of the
+ * bidirectional application (Sec. 5); it takes slot 2 and excludes
+ * MARS_TECH_GUIDED.  A light connection sample at camera vertex x_i traces one
+ * light subpath of its own (light and point chosen as for NEE, cosine
+ * emission, BSDF sampling and throughput-based Russian roulette at every
+ * surface vertex, at most MARS_LIGHT_MAX surface vertices and D - 1 - i) and
+ * connects x_i to each of its surface vertices; it is drawn at vertices of
+ * depth <= D - 2.  With it, every contribution is weighted by the
+ * budget-aware balance heuristic over all strategies of its full path (camera
+ * path, NEE at the last vertex, light connection at any earlier one), and the
+ * local outlier clamp is off (Sec. 5.1). */
 #define MARS_TECH_BSDF 1
 #define MARS_TECH_NEE 2
 #define MARS_TECH_GUIDED 4
+#define MARS_TECH_LIGHT 8
 #define MARS_SLOT_BSDF 0
 #define MARS_SLOT_NEE 1
 #define MARS_SLOT_GUIDED 2
+#define MARS_SLOT_LIGHT 2
 #define MARS_NUM_SLOTS 3
+#define MARS_LIGHT_MAX 5      /* surface vertices of a light subpath (6 vertices with the light's) */
 #define MARS_NUM_STATS 8      /* n, sum v (rgb), sum v^2 (rgb), sum cost */
 #define MARS_GUIDE_BINS 256   /* 16 (cos theta) x 16 (phi) equal-area bins */
 #define MARS_MAX_DEPTH 16
@@ -224,6 +238,11 @@ typedef struct {
   uint32_t check_flags;       /* MARS_CHECK_* bits of the index checks that failed (always 0
                                  in the regular library; see below) */
   uint32_t reserved;
+  /* light connections (MARS_TECH_LIGHT): light-subpath closest-hit queries
+     (included in `vertices`), connection shadow rays traced, light connection
+     samples drawn, and (profile = 1) the device time of their kernel */
+  uint64_t light_rays, connection_rays, light_samples;
+  double light_ms;
 } mars_iter_stats;
 
 /* Index checks of the checked library (libmars_checked.so, the same sources

@@ -16,6 +16,8 @@ from .scenes import (  # noqa: F401
     config_guided,
     config_heightfield,
     config_large,
+    config_bdpt_heightfield,
+    config_bdpt_large,
     heightfield_scene,
     random_count_fields,
     random_guide_cdf,
@@ -24,6 +26,7 @@ from .scenes import (  # noqa: F401
     TECH_BSDF,
     TECH_NEE,
     TECH_GUIDED,
+    TECH_LIGHT,
     MAT_LAMBERT,
     MAT_GGX,
 )

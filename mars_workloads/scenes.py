@@ -42,6 +42,7 @@ MAT_GGX = 1
 TECH_BSDF = 1
 TECH_NEE = 2
 TECH_GUIDED = 4
+TECH_LIGHT = 8   # connections to light subpaths (the bidirectional application)
 
 GUIDE_BINS = 256  # 16 (cos theta) x 16 (phi) cylindrical bins per cell
 
@@ -346,6 +347,27 @@ def config_large(width: int = 2048, height: int = 2048, seed: int = 0) -> Worklo
     return WorkloadConfig(heightfield_scene(seed, 512, width, height, n_spheres=4096, n_lights=8, ggx_fraction=1.0),
                           max_depth=12, grid_n=32, techniques=TECH_BSDF | TECH_NEE, iterations=64,
                           warmup=3, name=f"heightfield_512q_{width}x{height}_D12_bsdf+nee_grid32")
+
+
+def config_bdpt_heightfield(width: int = 1024, height: int = 1024, seed: int = 0) -> WorkloadConfig:
+    """The bidirectional workload: the heightfield of 256 x 256 quads (131k
+    triangles) with 200 spheres and one small emitter hidden between two
+    occluding spheres, 1024^2, D = 10, BSDF + NEE + light connections (light
+    subpaths of at most 6 vertices), 32^3 grid refined as an adaptive octree of
+    at most 64k leaves, 32 iterations, 3 warm-up."""
+    return WorkloadConfig(heightfield_scene(seed, 256, width, height), max_depth=10, grid_n=32,
+                          techniques=TECH_BSDF | TECH_NEE | TECH_LIGHT, iterations=32, warmup=3,
+                          name=f"bdpt_heightfield_256q_{width}x{height}_D10_bsdf+nee+light_octree64k")
+
+
+def config_bdpt_large(width: int = 2048, height: int = 2048, seed: int = 0) -> WorkloadConfig:
+    """The large bidirectional workload: 512 x 512 quads (524k triangles) + 4096
+    GGX spheres, 8 area lights with radiance log-U[0.5, 500], 2048^2, D = 12,
+    BSDF + NEE + light connections, adaptive octree of at most 64k leaves, 64
+    iterations at 1 spp, 3 warm-up."""
+    return WorkloadConfig(heightfield_scene(seed, 512, width, height, n_spheres=4096, n_lights=8, ggx_fraction=1.0),
+                          max_depth=12, grid_n=32, techniques=TECH_BSDF | TECH_NEE | TECH_LIGHT, iterations=64,
+                          warmup=3, name=f"bdpt_heightfield_512q_{width}x{height}_D12_bsdf+nee+light_octree64k")
 
 
 def config_box(width: int = 64, height: int = 64) -> WorkloadConfig:

@@ -1313,7 +1313,9 @@ void orc_update_counts(int n_cells, int techniques, const double* stats, double 
   if (!(VI > 1e-12)) return;
   for (int c = 0; c < n_cells; ++c)
     for (int t = 0; t < ORC_NT; ++t) {
-      if (!((techniques >> t) & 1)) continue;
+      /* slot 2 holds the guided technique or the light connection */
+      int on = t == 2 ? (techniques & (4 | ORC_TECH_LIGHT)) != 0 : (techniques >> t) & 1;
+      if (!on) continue;
       const double* s = stats + ((size_t)c * ORC_NT + t) * ORC_NSTAT;
       double n = s[0];
       if (n < 2.0 || !(s[7] > 0.0)) continue;

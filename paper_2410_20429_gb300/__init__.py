@@ -26,6 +26,7 @@ from ._abi import (  # noqa: F401
     MARS_MODE_WARMUP,
     MARS_TECH_BSDF,
     MARS_TECH_GUIDED,
+    MARS_TECH_LIGHT,
     MARS_TECH_NEE,
     MARS_WEIGHTS_AWARE,
     MARS_WEIGHTS_UNAWARE,

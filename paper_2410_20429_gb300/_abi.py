@@ -11,7 +11,8 @@ LIB_PATH = os.path.join(_PKG, "libmars.so")
 
 MARS_OK, MARS_ERR_INVALID_ARG, MARS_ERR_OOM, MARS_ERR_CUDA, MARS_ERR_TIMEOUT, MARS_ERR_BUSY, MARS_ERR_NOT_FOUND = range(7)
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "BUSY", 6: "NOT_FOUND"}
-MARS_TECH_BSDF, MARS_TECH_NEE, MARS_TECH_GUIDED = 1, 2, 4
+MARS_TECH_BSDF, MARS_TECH_NEE, MARS_TECH_GUIDED, MARS_TECH_LIGHT = 1, 2, 4, 8
+MARS_LIGHT_MAX = 5
 MARS_MODE_WARMUP, MARS_MODE_MARS, MARS_MODE_FIXED = 0, 1, 2
 MARS_WEIGHTS_AWARE, MARS_WEIGHTS_UNAWARE = 0, 1
 MARS_JOB_QUEUED, MARS_JOB_RUNNING, MARS_JOB_DONE, MARS_JOB_FAILED = range(4)
@@ -72,6 +73,8 @@ class mars_iter_stats(ct.Structure):
         ("wave_entries", ct.c_uint64), ("shadow_entries", ct.c_uint64), ("shadow_traced", ct.c_uint64),
         ("wave_ms", (ct.c_float * 16) * 4), ("wave_rays", ct.c_uint64 * 16),
         ("trace_work", (ct.c_uint64 * 4) * 2), ("check_flags", ct.c_uint32), ("reserved", ct.c_uint32),
+        ("light_rays", ct.c_uint64), ("connection_rays", ct.c_uint64), ("light_samples", ct.c_uint64),
+        ("light_ms", ct.c_double),
     ]
 
 

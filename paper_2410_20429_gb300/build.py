@@ -17,7 +17,7 @@ LIB = os.path.join(PKG, "libmars.so")
 # the checked variant: the same sources with the kernels' index checks compiled in
 BUILD_CHECKED = os.path.join(PKG, "_build_checked")
 LIB_CHECKED = os.path.join(PKG, "libmars_checked.so")
-SOURCES = ["abi.cu", "render.cu", "stats.cu", "scene.cu", "server.cu", "static_scratch.cu"]
+SOURCES = ["abi.cu", "render.cu", "bdpt.cu", "stats.cu", "scene.cu", "server.cu", "static_scratch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

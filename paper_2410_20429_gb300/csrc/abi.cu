@@ -530,6 +530,7 @@ constexpr int64_t kLaneFloorPixels = 1 << 14;  // the autotuner tries lanes on i
 uint64_t cache_footprint(int64_t cells, int64_t pixels, int max_depth, int techniques, uint64_t cap) {
   (void)max_depth;
   uint64_t b = (uint64_t)cap * (SLOT_BYTES + SHADOW_BYTES);
+  if (techniques & MARS_TECH_LIGHT) b += (uint64_t)cap * LIGHT_SLOT_BYTES;
   b += (uint64_t)cells * NT * (2 * sizeof(float4) + NSTAT * sizeof(double));
   if (techniques & MARS_TECH_GUIDED) b += (uint64_t)cells * GUIDE_BINS * 2 * sizeof(float);
   b += (uint64_t)pixels * 4 * sizeof(float4);  // running sum, estimate, image, combination
@@ -550,8 +551,12 @@ mars_status cache_create_impl(const mars_scene* s, const mars_cache_desc* d, cud
   if (!s || !d || !out) return set_error(MARS_ERR_INVALID_ARG, "null scene, descriptor or output");
   *out = nullptr;
   if (d->grid_n < 1 || d->grid_n > 256) return set_error(MARS_ERR_INVALID_ARG, "grid_n %d out of [1, 256]", d->grid_n);
-  if (!(d->techniques & MARS_TECH_BSDF) || (d->techniques & ~7))
-    return set_error(MARS_ERR_INVALID_ARG, "techniques must include BSDF and only use bits 0..2");
+  if (!(d->techniques & MARS_TECH_BSDF) || (d->techniques & ~15))
+    return set_error(MARS_ERR_INVALID_ARG, "techniques must include BSDF and only use bits 0..3");
+  if ((d->techniques & MARS_TECH_GUIDED) && (d->techniques & MARS_TECH_LIGHT))
+    return set_error(MARS_ERR_INVALID_ARG, "the guided technique and light connections share slot 2");
+  if ((d->techniques & MARS_TECH_LIGHT) && s->n_lights == 0)
+    return set_error(MARS_ERR_INVALID_ARG, "light connections requested but the scene has no emitting quad");
   if (d->max_depth < 1 || d->max_depth > MAXD)
     return set_error(MARS_ERR_INVALID_ARG, "max_depth %d out of [1, %d]", d->max_depth, MAXD);
   if ((d->techniques & MARS_TECH_NEE) && s->n_lights == 0)
@@ -594,6 +599,7 @@ mars_status cache_create_impl(const mars_scene* s, const mars_cache_desc* d, cud
   c->pixels = pixels;
   c->arena.cap = cap;
   c->arena.scap = cap;  // NEE shadow rays: as many slots as rays
+  c->arena.lcap = (d->techniques & MARS_TECH_LIGHT) ? cap : 0;  // light connection samples: likewise
   c->max_tiles = 4096;
   // two tile lanes (each with half the arena) unless asked for one or the
   // image has a single pixel
@@ -619,6 +625,14 @@ mars_status cache_create_impl(const mars_scene* s, const mars_cache_desc* d, cud
       return cleanup(e, "arena alloc");
   if ((e = dev_alloc((void**)&c->arena.SL, sizeof(unsigned int) * c->arena.scap, st)) != cudaSuccess)
     return cleanup(e, "arena alloc");
+  if (c->arena.lcap) {
+    if ((e = dev_alloc((void**)&c->arena.R5, sizeof(float4) * cap, st)) != cudaSuccess) return cleanup(e, "arena alloc");
+    for (int k = 0; k < NLJ; ++k)
+      if ((e = dev_alloc((void**)&c->arena.LJ[k], sizeof(float4) * c->arena.lcap, st)) != cudaSuccess)
+        return cleanup(e, "arena alloc");
+    if ((e = dev_alloc((void**)&c->arena.LR, sizeof(float4) * c->arena.lcap, st)) != cudaSuccess)
+      return cleanup(e, "arena alloc");
+  }
   if ((e = dev_alloc((void**)&c->d_cnt, sizeof(float4) * 2 * NT * cells, st)) != cudaSuccess) return cleanup(e, "cache alloc");
   c->fp32_stats = fp32;
   if (fp32) {
@@ -838,6 +852,9 @@ void cache_destroy_impl(mars_cache* c) {
   dev_free(c->arena.H, st);
   for (auto* p : c->arena.SH) dev_free(p, st);
   dev_free(c->arena.SL, st);
+  dev_free(c->arena.R5, st);
+  for (auto* p : c->arena.LJ) dev_free(p, st);
+  dev_free(c->arena.LR, st);
   void* ptrs[] = {c->d_cnt, c->d_stats, c->d_stats32, c->d_hist, c->d_cdf, c->d_guide_dirty, c->d_est, c->d_run,
                   c->d_img, c->d_ctr, c->d_tile_status, c->d_oct_nodes, c->d_oct_level, c->d_oct_lnode,
                   c->d_oct_meta, c->d_oct_split, c->d_oct_leaf_n, c->d_comb, c->d_comb_w, c->d_topk};
@@ -879,7 +896,8 @@ static Arena lane_arena(const mars_cache* c, int l, int nl) {
   Arena a = c->arena;
   if (nl <= 1) return a;
   const uint64_t rc = c->arena.cap / (uint64_t)nl, sc = c->arena.scap / (uint64_t)nl;
-  const uint64_t r0 = rc * (uint64_t)l, s0 = sc * (uint64_t)l;
+  const uint64_t lc = c->arena.lcap / (uint64_t)nl;
+  const uint64_t r0 = rc * (uint64_t)l, s0 = sc * (uint64_t)l, l0 = lc * (uint64_t)l;
   for (auto& p : a.R) p += r0;
   for (auto& p : a.V) p += r0;
   a.S += r0;
@@ -887,8 +905,14 @@ static Arena lane_arena(const mars_cache* c, int l, int nl) {
   a.H += r0;
   for (auto& p : a.SH) p += s0;
   a.SL += s0;
+  if (a.lcap) {
+    a.R5 += r0;
+    for (auto& p : a.LJ) p += l0;
+    a.LR += l0;
+  }
   a.cap = rc;
   a.scap = sc;
+  a.lcap = lc;
   return a;
 }
 
@@ -975,10 +999,10 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
   }
   uint32_t retries = 0, used = 0, launches = 0, wave_launches = 0;
   uint64_t demand = 0;
-  double trace_ms = 0.0, shade_ms = 0.0, shadow_ms = 0.0, reverse_ms = 0.0, image_ms = 0.0;
+  double trace_ms = 0.0, shade_ms = 0.0, shadow_ms = 0.0, reverse_ms = 0.0, image_ms = 0.0, light_ms = 0.0;
   float wave_ms[WAVE_KERNELS][MAXD] = {};
   const int D = c->max_depth;
-  const int per_tile = 5 * D + 2;
+  const int per_tile = 7 * D + 2;
   // A host image in page-locked memory is written by the image pass itself,
   // through its device address (no copy); any other host image is packed by
   // the image pass into a staging buffer of the cache (allocated on first use)
@@ -1136,6 +1160,10 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
             shadow_ms += ms;
             wave_ms[WK_SHADOW][d - 1] += ms;
           }
+          if (d <= D - 2 && (c->techniques & MARS_TECH_LIGHT)) {
+            cudaEventElapsedTime(&ms, ev[5 * D + 2 + 2 * (d - 1)], ev[5 * D + 2 + 2 * (d - 1) + 1]);
+            light_ms += ms;
+          }
         }
         // the k-th reverse launch (k = 1..D) handles wave D - k + 1
         for (int k = 1; k <= D; ++k) {
@@ -1190,8 +1218,9 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
   // iterations); a tile that still overflows is split and re-rendered as above
   {
     const DevCounters& h = *c->h_ctr;
-    const double need = std::max((double)h.entries / (double)c->arena.cap,
-                                 (double)h.shadow_entries / (double)c->arena.scap);
+    double need = std::max((double)h.entries / (double)c->arena.cap,
+                           (double)h.shadow_entries / (double)c->arena.scap);
+    if (c->arena.lcap) need = std::max(need, (double)h.light_entries / (double)c->arena.lcap);
     const double growth = c->last_entries > 0 ? std::min(2.0, std::max(1.0, (double)h.entries /
                                                                              (double)c->last_entries))
                                               : 1.0;
@@ -1215,7 +1244,7 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
     out->VI = h.VI;
     out->CI = h.CI;
     out->rays = h.rays;
-    out->vertices = h.vertices;
+    out->vertices = h.vertices + h.light_rays;  // closest-hit queries of camera and light paths
     out->estimator_vertices = h.est_vertices;
     for (int t = 0; t < NT; ++t) out->mean_beta[t] = h.est_vertices ? h.sum_beta[t] / (double)h.est_vertices : 0.0;
     out->tiles = used;
@@ -1238,6 +1267,10 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
       for (int q = 0; q < 4; ++q) out->trace_work[k][q] = h.trace_work[k][q];
     out->check_flags = h.check_flags;
     out->reserved = 0;
+    out->light_rays = h.light_rays;
+    out->connection_rays = h.conn_rays;
+    out->light_samples = h.light_entries;
+    out->light_ms = light_ms;
   }
   c->last_VI = c->h_ctr->VI;
   c->last_CI = c->h_ctr->CI;

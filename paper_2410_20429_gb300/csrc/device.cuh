@@ -483,6 +483,47 @@ __device__ __forceinline__ f3 guide_dir(int b, float u1, float u2) {
   return mk3(s * cp, s * sp, z);
 }
 
+// ----------------------------------------------------------------- counts
+// Budgets beta_t of the techniques at a vertex (Sec. 3.1 "Optimization", in the
+// spatial form of Sec. 4.1): per channel T_ch / I_ch x q_ch for the RR and the
+// splitting factor, their root mean square over the channels ("Handling
+// colors"), the three cases (RR below 1, else splitting above 1, else 1) and
+// the clamp.  A technique without learned statistics draws its base count:
+// NEE 1, the light connection (slot 2 with MARS_TECH_LIGHT) 1, and one
+// continuation sample split over the continuation techniques (base_cont: 1
+// for BSDF alone, 1/2 each for BSDF and guided).  Then the path multiplicity
+// cap b <= max(clamp_lo, M / mult).  on_mask: bit t set if technique t is
+// drawn at this vertex.
+__device__ __forceinline__ void vertex_budgets(const DevCache& c, const IterArgs& it, int cell, f3 T, float4 est,
+                                               float mult, unsigned on_mask, float base_cont, float base2,
+                                               float beta[NT]) {
+  const float inf = __int_as_float(0x7f800000);
+  const f3 f = mk3(T.x / est.x, T.y / est.y, T.z / est.z);
+  const float cap = it.max_mult > 0.0f ? fmaxf(it.max_mult / mult, it.clamp_lo) : inf;
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    const bool on = (on_mask >> t) & 1u;
+    float b = on ? (t == 1 ? 1.0f : (t == 2 ? base2 : base_cont)) : 0.0f;
+    if (on && it.mode == MARS_MODE_MARS) {
+      const float4 qr = __ldg(c.cnt + (2 * (NT * cell + t)));
+      if (qr.w > 0.0f) {
+        const float4 qs = __ldg(c.cnt + (2 * (NT * cell + t) + 1));
+        const f3 ar = mul(f, xyz(qr)), as = mul(f, xyz(qs));
+        // root mean square over the channels
+        const float brr = sqrtf(dot(ar, ar) * (1.0f / 3.0f)), bs = sqrtf(dot(as, as) * (1.0f / 3.0f));
+        b = brr < 1.0f ? brr : (bs > 1.0f ? bs : 1.0f);
+        b = fminf(fmaxf(b, it.clamp_lo), it.clamp_hi);
+      }
+    }
+    // path multiplicity cap: b <= max(clamp_lo, M / P)
+    if (on) b = fminf(b, cap);
+    beta[t] = b;
+  }
+}
+
+// the largest of the three channels
+__device__ __forceinline__ float max_channel(f3 a) { return fmaxf(a.x, fmaxf(a.y, a.z)); }
+
 // ----------------------------------------------------------------- cells
 // cell coordinates of a point on an N^3 grid over the scene box; decided in
 // float32 like every integer choice

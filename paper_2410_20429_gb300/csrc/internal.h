@@ -18,6 +18,11 @@ constexpr int GUIDE_BINS = MARS_GUIDE_BINS;
 constexpr int MAXD = MARS_MAX_DEPTH;
 constexpr uint32_t DIM_ROUND = 96;   // Philox dimension of the Alg. 1 draw
 constexpr uint32_t DIM_CAMERA = 97;  // Philox dimension of the pixel jitter
+// Philox dimension of step k of the light subpath of light connection sample
+// s: DIM_LIGHT + 8 s + k (k = 0 light and point, 1 emission direction, k >= 2
+// the bounce at surface vertex k - 1 and its Russian roulette)
+constexpr uint32_t DIM_LIGHT = 128;
+constexpr int LIGHT_MAX = MARS_LIGHT_MAX;
 
 // ---------------------------------------------------------------- scene
 // Primitive record: four float4 per primitive.
@@ -85,9 +90,21 @@ struct DevScene {
 // Only samples with a nonzero value need a ray: their slots are listed in
 // SL[sbase[d], sbase[d] + slcount[d]) (a compacted work list), and SH0/SH1 are
 // written for them alone.
-constexpr int NR = 5, NV = 5, NSH = 3;
+//
+// With light connections (MARS_TECH_LIGHT) a ray carries the running sums of
+// the whole-path weights instead of the guided technique's fields:
+//   R2.w = |cos| at the parent of the ray's direction (instead of S_ind),
+//   R4.zw, R5 = Z[1..6]: Z[1] = the parent's light connection count, Z[l] the
+//   term of a light connection l vertices back, relative to the camera prefix
+//   up to the parent (divided by the last step's density at the hit),
+// V3.w holds the first light connection slot of the vertex, and the light
+// connection samples of wave d occupy [lbase[d], lbase[d] + lcount[d]) of a
+// third region: LJ0..LJ7 the camera vertex's context (written by the shade
+// kernel), LR = (sample value rgb, cost) written by the light kernel.
+constexpr int NR = 5, NV = 5, NSH = 3, NLJ = 8;
 constexpr int SLOT_BYTES = (NR + NV + 1) * 16 + 8 + 4;  // per ray slot
 constexpr int SHADOW_BYTES = NSH * 16 + 4;          // per shadow-ray slot
+constexpr int LIGHT_SLOT_BYTES = 16 + (NLJ + 1) * 16;  // R5 per ray slot, LJ and LR per connection slot
 struct Arena {
   float4* R[NR];
   float2* H;
@@ -96,8 +113,12 @@ struct Arena {
   float* M;   // path multiplicity of the ray (product of the budgets that drew its path)
   float4* SH[NSH];
   unsigned int* SL;
+  float4* R5;        // light connections only
+  float4* LJ[NLJ];
+  float4* LR;
   uint64_t cap;   // ray slots
   uint64_t scap;  // shadow-ray slots
+  uint64_t lcap;  // light connection slots (0 without light connections)
 };
 
 // V0.w flag bits
@@ -111,6 +132,10 @@ struct DevCounters {
   unsigned long long sbase[MAXD + 2];   // shadow rays of wave d
   unsigned long long scount[MAXD + 2];
   unsigned long long slcount[MAXD + 2];  // shadow rays of wave d that need tracing
+  unsigned long long lbase[MAXD + 2];    // light connection samples of wave d
+  unsigned long long lcount[MAXD + 2];
+  unsigned long long light_rays, conn_rays;  // light-subpath closest hits, connection rays (every launch)
+  unsigned long long light_entries;          // light connection samples of committed tiles
   unsigned long long shadow_entries;     // shadow rays of committed tiles
   unsigned long long shadow_traced;      // listed (traced) shadow rays of committed tiles
   unsigned long long wave_total[MAXD + 2];  // rays per depth wave of committed tiles
@@ -130,6 +155,12 @@ struct DevCounters {
   int vi_dropped;              // pixels left out of the V_I mean
   unsigned int check_flags;    // MARS_CHECK_* bits of failed index checks (checked builds)
 };
+
+// technique t's slot is in use: slot 2 holds the guided technique or the light
+// connection (they exclude each other)
+__host__ __device__ __forceinline__ bool slot_on(int techniques, int t) {
+  return t == 2 ? (techniques & (MARS_TECH_GUIDED | MARS_TECH_LIGHT)) != 0 : ((techniques >> t) & 1) != 0;
+}
 
 // Index checks of the checked build (-DMARS_CHECKED, libmars_checked.so): an
 // index a kernel computed is tested against the buffer it addresses; a failed
@@ -198,12 +229,18 @@ struct IterArgs {
 // sizes measured no faster for small waves and starved the growing waves of
 // the first MARS iterations).  Every kernel strides over its wave in chunks
 // of 32 slots, so results do not depend on the shape.
+// (the light connection kernel runs with the shadow kernel's shape)
 enum { WK_TRACE = 0, WK_SHADE = 1, WK_SHADOW = 2, WK_REVERSE = 3, WAVE_KERNELS = 4 };
 struct WaveLaunch {
   int threads[WAVE_KERNELS];
   int variant[WAVE_KERNELS];               // register-cap variant (wave_variant_registers)
   int grid[WAVE_KERNELS];                  // persistent grid: SMs x resident blocks
 };
+
+// the light connection kernel of wave d (bdpt.cu)
+cudaError_t launch_light(const DevScene& s, const DevCache& c, const Arena& a, const IterArgs* it, int variant,
+                         int grid, int threads, int d, cudaStream_t st);
+int light_variants();
 
 // launch wrappers (render.cu)
 // it: device pointer to the tile's arguments

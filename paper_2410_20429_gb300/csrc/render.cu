@@ -147,6 +147,8 @@ __global__ void k_tile_init(DevCounters* ctr, const IterArgs* __restrict__ itp) 
     ctr->sbase[t] = 0;
     ctr->scount[t] = 0;
     ctr->slcount[t] = 0;
+    ctr->lbase[t] = 0;
+    ctr->lcount[t] = 0;
   }
   if (t == 0) {
     ctr->overflow = 0;
@@ -164,16 +166,18 @@ __global__ void k_tile_finish(DevCounters* ctr, unsigned int* tile_status, const
   }
   ctr->demand = dem;
   if (!ctr->overflow) {
-    unsigned long long tot = 0, sh = 0, sl = 0;
+    unsigned long long tot = 0, sh = 0, sl = 0, lc = 0;
     for (int d = 1; d <= D; ++d) {
       tot += ctr->count[d];
       sh += ctr->scount[d];
       sl += ctr->slcount[d];
+      lc += ctr->lcount[d];
       ctr->wave_total[d] += ctr->count[d];
     }
     ctr->entries += tot;
     ctr->shadow_entries += sh;
     ctr->shadow_traced += sl;
+    ctr->light_entries += lc;
   }
   tile_status[slot] = ctr->overflow;
   if (ctr->overflow) ctr->any_overflow = 1;
@@ -189,7 +193,11 @@ __global__ void k_merge_lanes(DevCounters* dst, DevCounters* src) {
   dst->vertices += src->vertices;
   dst->est_vertices += src->est_vertices;
   dst->entries += src->entries;
+  dst->light_entries += src->light_entries;
+  dst->light_rays += src->light_rays;
+  dst->conn_rays += src->conn_rays;
   src->shadow_entries = src->shadow_traced = src->rays = src->vertices = src->est_vertices = src->entries = 0;
+  src->light_entries = src->light_rays = src->conn_rays = 0;
   for (int d = 0; d < MAXD + 2; ++d) {
     dst->wave_total[d] += src->wave_total[d];
     src->wave_total[d] = 0;
@@ -253,17 +261,37 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_trace(const DevScene
 // ------------------------------------------------------------------ shade
 // Per-warp staging area of k_shade: the context of the 32 vertices of a chunk,
 // structure of arrays [field][lane], read by the lanes that draw their samples.
+// C_Y and C_GP are used with light connections only (see k_shade<., true>).
 enum {
   C_XO = 0, C_NS = 3, C_WO = 6, C_MTYPE = 9, C_ALPHA = 10, C_COL = 11, C_CELL = 14, C_PX = 15, C_LIN = 16,
-  C_T = 18, C_B0 = 21, C_B1 = 22, C_B2 = 23, C_G0 = 24, C_MULT = 25, C_FIELDS = 26
+  C_T = 18, C_B0 = 21, C_B1 = 22, C_B2 = 23, C_G0 = 24, C_MULT = 25, C_Y = 26, C_GP = 31, C_FIELDS = 32
 };
 struct ShadeWarpCtx {
   float f[C_FIELDS][32];
   int incl_ext[32];
   int incl_sh[32];
+  int incl_lc[32];
 };
 
-template <int MINB>
+// Whole-path weights with light connections (the bidirectional application,
+// Sec. 5): the balance heuristic over every strategy of a full path z_1..z_n
+// (z_n on a light) -- the camera path, NEE at z_{n-1}, light connection at
+// z_i (i <= n - 2, n - 1 - i <= LIGHT_MAX light vertices) -- each strategy's
+// density times its expected sample count.  Relative to the camera prefix
+// C_k = prod_{j<k} bw_B(x_j) P->_j (P->_j: area density of x_{j+1} by BSDF
+// sampling at x_j) the strategies that split the path before x_k add up to the
+// window Y_k[l] = bw_L(x_{k-l}) prod_{m=k-l+1}^{k-2} P<-_m / prod_{m=k-l}^{k-1}
+// bw_B P->_m (P<-_m: area density of x_m on a light subpath), which a ray
+// carries forward as Z (Y of its parent times the parent's P<- towards the
+// grandparent, Z[1] = the parent's light connection count) and the hit divides
+// by the last step's bw_B P->.  The term of a light connection l vertices back
+// at x_k is W_k[l] = Y_k[1] for l = 1 and Y_k[l] P<-_{k-1} for l >= 2 (P<-_{k-1}
+// depends on the direction x_k continues in); a child carries Z[l] = W[l - 1].
+// Emission hit at x_n from x_{n-1}:
+//   w = bw_B P->_{n-1} / (bw_B P->_{n-1} + bw_N(x_{n-1}) pN + pN P<-_{n-1} sum_{l>=2} Z[l]);
+// NEE at x_k towards y: w = bw_N pN / (bw_N pN + bw_B P->_k + pN P<-_k sum_l W_k[l]);
+// light connections: the light kernel (bdpt.cu).
+template <int MINB, bool BD>
 __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_shade(const DevScene s, const DevCache c, const Arena a,
                                                          const IterArgs* __restrict__ itp, const int d) {
   const IterArgs it = *itp;
@@ -271,8 +299,8 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_shade(const DevScene
   // block-level allocation below synchronises the block: decide the early exit
   // once per block (other blocks may raise the overflow flag meanwhile)
   __shared__ unsigned int blk_exit;
-  __shared__ int blk_n[2][MAX_WAVE_THREADS / 32];
-  __shared__ unsigned long long blk_base[2][MAX_WAVE_THREADS / 32];
+  __shared__ int blk_n[3][MAX_WAVE_THREADS / 32];
+  __shared__ unsigned long long blk_base[3][MAX_WAVE_THREADS / 32];
   if (threadIdx.x == 0) blk_exit = ctr->overflow;
   __syncthreads();
   if (blk_exit) return;
@@ -280,9 +308,11 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_shade(const DevScene
   const unsigned long long cnt = ctr->count[d];
   const unsigned long long base_next = w.base + cnt < a.cap ? w.base + cnt : a.cap;
   const unsigned long long sbase = d == 1 ? 0ull : ctr->sbase[d - 1] + ctr->scount[d - 1];
+  const unsigned long long lbase = d == 1 ? 0ull : ctr->lbase[d - 1] + ctr->lcount[d - 1];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     ctr->base[d + 1] = base_next;
     ctr->sbase[d] = sbase;
+    if (BD) ctr->lbase[d] = lbase;
   }
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -290,7 +320,9 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_shade(const DevScene
   const bool est_depth = d <= D - 1;
   const bool camera = d == 1;
   const bool on_b = c.techniques & MARS_TECH_BSDF, on_n = c.techniques & MARS_TECH_NEE,
-             on_g = c.techniques & MARS_TECH_GUIDED;
+             on_g = !BD && (c.techniques & MARS_TECH_GUIDED);
+  // light connections are drawn at vertices of depth <= D - 2
+  const bool on_l = BD && d <= D - 2;
   const Rng rng{it.seed, it.job, it.iteration};
   const float inf = __int_as_float(0x7f800000);
   extern __shared__ ShadeWarpCtx shade_ctx[];
@@ -320,6 +352,7 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_shade(const DevScene
     uint32_t px = 0, parent_cell = 0;
     float th = 0.0f, mult = 1.0f;
     int prim = -2;
+    float Z[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // light connections: whole-path weight window
     if (active) {
       if (camera) {
         px = (uint32_t)(it.tile_begin + li);
@@ -332,12 +365,17 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_shade(const DevScene
         dir = xyz(r1);
         A = r1.w;
         T = xyz(r2);
-        S_ind = r2.w;
+        S_ind = r2.w;   // light connections: |cos| at the parent
         fcp = xyz(r3);
         bwN = r3.w;
         lin = (uint64_t)__float_as_uint(r4.x) | ((uint64_t)__float_as_uint(r4.y) << 32);
-        parent_cell = __float_as_uint(r4.z);
-        invSb = r4.w;
+        if (BD) {
+          const float4 r5 = a.R5[i];
+          Z[0] = r4.z; Z[1] = r4.w; Z[2] = r5.x; Z[3] = r5.y; Z[4] = r5.z; Z[5] = r5.w;
+        } else {
+          parent_cell = __float_as_uint(r4.z);
+          invSb = r4.w;
+        }
       }
       const float2 h = a.H[i];
       th = h.x;
@@ -346,10 +384,13 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_shade(const DevScene
 
     f3 E = mk3(0.f, 0.f, 0.f);
     float Le_lum = 0.0f;
-    const f3 G = camera ? mk3(1.f, 1.f, 1.f) : (S_ind > 0.0f ? fcp * (A / S_ind) : mk3(0.f, 0.f, 0.f));
+    const f3 G = camera ? mk3(1.f, 1.f, 1.f)
+                        : (BD ? fcp : (S_ind > 0.0f ? fcp * (A / S_ind) : mk3(0.f, 0.f, 0.f)));
     uint32_t flags = prim >= -1 ? F_TRACED : 0u;
     int gam[NT] = {0, 0, 0};
     float beta[NT] = {0.f, 0.f, 0.f};
+    float Y[5] = {0.f, 0.f, 0.f, 0.f, 0.f};   // light connections: Y_k[1..5]
+    float gprev = 0.0f;                        // |cos| at the parent / t^2
     int cell = 0;
     f3 p = mk3(0.f, 0.f, 0.f), ns = mk3(0.f, 0.f, 1.f), wo = mk3(0.f, 0.f, 1.f);
     f3 climit = mk3(inf, inf, inf);
@@ -365,9 +406,23 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_shade(const DevScene
       if (!chk(m >= 0 && m < s.n_mats, MARS_CHECK_MATERIAL, ctr)) m = 0;
       const float4 m0 = __ldg(s.mats + 3 * m), m1 = __ldg(s.mats + 3 * m + 1), m2 = __ldg(s.mats + 3 * m + 2);
       const float cosg = dot(ng, wo);
+      // the last step's bw_B P-> (area density of this hit from the parent)
+      const float inv_t2 = 1.0f / (th * th);
+      const float cp_prev = BD && !camera ? A * fabsf(cosg) * inv_t2 : 0.0f;
       if (cosg > 0.0f && m0.w > 0.0f) {
         float w_dir = 1.0f;
-        if (!camera) {
+        if (!camera && BD) {
+          float sz = Z[1] + Z[2] + Z[3] + Z[4] + Z[5];
+          float pN = 0.0f;
+          if (prim < s.n_quads) {
+            const int l = __float_as_int(__ldg(&s.prims[4 * prim + 3].w));
+            if (l >= 0 && chk(l < s.n_lights, MARS_CHECK_LIGHT, ctr))
+              pN = __ldg(&s.lights[5 * l + 1].w) / __ldg(&s.lights[5 * l + 2].w);
+          }
+          const float lpe = cosg * INV_PI_F * S_ind * inv_t2;   // P<-_{n-1}: cosine emission towards the parent
+          const float den = cp_prev + bwN * pN + pN * lpe * sz;
+          w_dir = den > 0.0f ? cp_prev / den : 0.0f;
+        } else if (!camera) {
           float pn = 0.0f;
           if (bwN > 0.0f && prim < s.n_quads) {
             const int l = __float_as_int(__ldg(&s.prims[4 * prim + 3].w));
@@ -391,41 +446,28 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_shade(const DevScene
         mat.alpha = m0.y;
         mat.col = xyz(m1);
         const float4 est = it.has_estimate ? c.est[px] : make_float4(1.f, 1.f, 1.f, 0.f);
-        if (it.collect && it.has_estimate) {
+        if (!BD && it.collect && it.has_estimate) {
           climit.x = T.x > 0.0f ? it.outlier * est.x / T.x : inf;
           climit.y = T.y > 0.0f ? it.outlier * est.y / T.y : inf;
           climit.z = T.z > 0.0f ? it.outlier * est.z / T.z : inf;
         }
-        // counts without learned statistics: one NEE sample and one
-        // continuation sample split evenly over BSDF and guided sampling
+        // counts without learned statistics: one NEE (and light connection)
+        // sample and one continuation sample split evenly over BSDF and guided
+        // sampling
         const float base_cont = (on_b && on_g) ? 0.5f : 1.0f;
-        // T / I_px per channel and the multiplicity cap, once per vertex
-        const f3 f = mk3(T.x / est.x, T.y / est.y, T.z / est.z);
-        const float cap = it.max_mult > 0.0f ? fmaxf(it.max_mult / mult, it.clamp_lo) : inf;
+        const unsigned on_mask = (on_b ? 1u : 0u) | (on_n ? 2u : 0u) | ((on_g || on_l) ? 4u : 0u);
+        vertex_budgets(c, it, cell, T, est, mult, on_mask, base_cont, BD ? 1.0f : base_cont, beta);
+        if (BD && !camera) {
+          const float icp = cp_prev > 0.0f ? 1.0f / cp_prev : 0.0f;
 #pragma unroll
-        for (int t = 0; t < NT; ++t) {
-          const bool on = (c.techniques >> t) & 1;
-          float b = on ? (t == 1 ? 1.0f : base_cont) : 0.0f;
-          if (on && it.mode == MARS_MODE_MARS) {
-            const float4 qr = __ldg(c.cnt + (2 * (NT * cell + t)));
-            if (qr.w > 0.0f) {
-              const float4 qs = __ldg(c.cnt + (2 * (NT * cell + t) + 1));
-              const f3 ar = mul(f, xyz(qr)), as = mul(f, xyz(qs));
-              // root mean square over the channels
-              const float brr = sqrtf(dot(ar, ar) * (1.0f / 3.0f)), bs = sqrtf(dot(as, as) * (1.0f / 3.0f));
-              b = brr < 1.0f ? brr : (bs > 1.0f ? bs : 1.0f);
-              b = fminf(fmaxf(b, it.clamp_lo), it.clamp_hi);
-            }
-          }
-          // path multiplicity cap: b <= max(clamp_lo, M / P)
-          if (on) b = fminf(b, cap);
-          beta[t] = b;
+          for (int l = 0; l < 5; ++l) Y[l] = Z[l] * icp;
+          gprev = S_ind * inv_t2;
         }
         // Alg. 1: one uniform decides the rounding of every technique
         float r = rng.u4(px, DIM_ROUND, lin).x;
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
-          if (!((c.techniques >> t) & 1)) continue;
+          if (!((on_mask >> t) & 1u)) continue;
           const float sm = beta[t] + r;
           const int g = (int)floorf(sm);
           gam[t] = g;
@@ -434,39 +476,48 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_shade(const DevScene
       }
     }
 
-    // ---- slots for the children (wave d+1) and the NEE shadow rays: warp
-    // scans, then one atomic per counter and block (every block of the grid
-    // allocates from the same two counters)
-    const int n_ext = gam[0] + gam[2], n_sh = gam[1];
+    // ---- slots for the children (wave d+1), the NEE shadow rays and the light
+    // connection samples: warp scans, then one atomic per counter and block
+    // (every block of the grid allocates from the same counters)
+    const int n_ext = BD ? gam[0] : gam[0] + gam[2], n_sh = gam[1], n_lc = BD ? gam[2] : 0;
     const int2 se = warp_scan(n_ext, lane), ss = warp_scan(n_sh, lane);
+    const int2 sl = BD ? warp_scan(n_lc, lane) : make_int2(0, 0);
     if (lane == 31) {
       blk_n[0][warp] = se.y;
       blk_n[1][warp] = ss.y;
+      blk_n[2][warp] = sl.y;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      int te = 0, ts = 0;
+      int te = 0, ts = 0, tl = 0;
       for (int k = 0; k < nwarps; ++k) {
-        const int e = blk_n[0][k], h = blk_n[1][k];
+        const int e = blk_n[0][k], h = blk_n[1][k], q = blk_n[2][k];
         blk_n[0][k] = te;
         blk_n[1][k] = ts;
+        blk_n[2][k] = tl;
         te += e;
         ts += h;
+        tl += q;
       }
       const unsigned long long be = te > 0 ? atomicAdd(&ctr->count[d + 1], (unsigned long long)te) : 0ull;
       const unsigned long long bs = ts > 0 ? atomicAdd(&ctr->scount[d], (unsigned long long)ts) : 0ull;
+      const unsigned long long bl = (BD && tl > 0) ? atomicAdd(&ctr->lcount[d], (unsigned long long)tl) : 0ull;
       for (int k = 0; k < nwarps; ++k) {
         blk_base[0][k] = be + (unsigned long long)blk_n[0][k];
         blk_base[1][k] = bs + (unsigned long long)blk_n[1][k];
+        blk_base[2][k] = bl + (unsigned long long)blk_n[2][k];
       }
     }
     __syncthreads();
     const WarpAlloc ae{blk_base[0][warp], se.x, se.y};
     const WarpAlloc as{blk_base[1][warp], ss.x, ss.y};
+    const WarpAlloc al{blk_base[2][warp], sl.x, sl.y};
     const unsigned long long first = base_next + ae.base + (unsigned long long)(ae.incl - n_ext);
     const unsigned long long sfirst = sbase + as.base + (unsigned long long)(as.incl - n_sh);
-    const bool fits = first + (unsigned long long)n_ext <= a.cap && sfirst + (unsigned long long)n_sh <= a.scap;
-    if ((n_ext > 0 || n_sh > 0) && !fits) atomicOr(&ctr->overflow, 1u);
+    const unsigned long long lfirst = lbase + al.base + (unsigned long long)(al.incl - n_lc);
+    const bool fits = first + (unsigned long long)n_ext <= a.cap && sfirst + (unsigned long long)n_sh <= a.scap &&
+                      (!BD || lfirst + (unsigned long long)n_lc <= a.lcap);
+    if ((n_ext > 0 || n_sh > 0 || n_lc > 0) && !fits) atomicOr(&ctr->overflow, 1u);
 
     // ---- vertex record of this slot
     if (active) {
@@ -475,7 +526,7 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_shade(const DevScene
       if (flags & F_EST) {
         a.V[1][i] = f4(G, 0.0f);
         a.V[2][i] = f4(climit, __uint_as_float((uint32_t)cell));
-        a.V[3][i] = make_float4(beta[0], beta[1], beta[2], 0.0f);
+        a.V[3][i] = make_float4(beta[0], beta[1], beta[2], __uint_as_float((uint32_t)(fits && BD ? lfirst : 0ull)));
         // the hit record is dead from here on: keep the first child and first
         // shadow-ray slots in it for the reverse pass
         a.H[i] = make_float2(__uint_as_float((uint32_t)(fits ? first : 0ull)),
@@ -484,7 +535,7 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_shade(const DevScene
       if (on_g && it.collect && !camera && (flags & F_TRACED))
         a.V[4][i] = make_float4(Le_lum, invSb, __uint_as_float(parent_cell), __int_as_float(guide_bin(dir)));
     }
-    if (ae.total == 0 && as.total == 0) continue;  // warp-uniform; no block barrier follows
+    if (ae.total == 0 && as.total == 0 && al.total == 0) continue;  // warp-uniform; no block barrier follows
 
     // ---- stage the vertex context of every lane for the cooperative loops
     {
@@ -508,8 +559,14 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_shade(const DevScene
       cx[C_B2 * 32 + lane] = beta[2];
       cx[C_G0 * 32 + lane] = __int_as_float(gam[0]);
       cx[C_MULT * 32 + lane] = mult;
+      if (BD) {
+#pragma unroll
+        for (int l = 0; l < 5; ++l) cx[(C_Y + l) * 32 + lane] = Y[l];
+        cx[C_GP * 32 + lane] = gprev;
+      }
       ctx->incl_ext[lane] = ae.incl;
       ctx->incl_sh[lane] = as.incl;
+      ctx->incl_lc[lane] = al.incl;
     }
     __syncwarp();
     const float* cx = ctx->f[0];
@@ -555,14 +612,44 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_shade(const DevScene
         if (pn > 0.0f && ci > 0.0f) {
           const Frame fr = make_frame(vns);
           float pb;
-          const f3 fc = bsdf_eval(m, wol, fr.to_local(wi), pb);
+          const f3 wil = fr.to_local(wi);
+          const f3 fc = bsdf_eval(m, wol, wil, pb);
           const float pg = on_g ? guide_pdf(c.guide_cdf + (size_t)__float_as_int(cx[C_CELL * 32 + L]) * GUIDE_BINS, wi)
                                 : 0.0f;
           if (nonzero(fc)) {
-            // f|cos| Le / p_N times the balance weight beta_N p_N / den: p_N cancels
-            const float den = bwB * pb + bwG * pg + bwNv * pn;
-            const float sc = bwNv / den;
-            v = mk3(fc.x * l4.x * sc, fc.y * l4.y * sc, fc.z * l4.z * sc);
+            if (BD) {
+              // the full path x_1..x_d, y: weight over every strategy
+              const float4 l3 = __ldg(s.lights + 5 * l + 3);
+              const float pN = l1.w / l2.w;
+              const float cosl = -dot(xyz(l3), wi);
+              const float id2 = 1.0f / (dist * dist);
+              const float t_nee = bwNv * pN;
+              const float t_cam = bwB * pb * cosl * id2;
+              // light connections l vertices back: W[1] = Y[1], W[l] = Y[l] P<-_{d-1} (l >= 2)
+              const float y1 = cx[C_Y * 32 + L];
+              float sy = 0.0f;
+#pragma unroll
+              for (int q = 1; q < 5; ++q) sy += cx[(C_Y + q) * 32 + L];
+              float t_lc = 0.0f;
+              if (y1 > 0.0f || sy > 0.0f) {
+                float lp = 0.0f;
+                if (sy > 0.0f) {
+                  float prev;
+                  const f3 frev = bsdf_eval(m, wil, wol, prev);   // at x_d, light arriving along wi
+                  const float qx = prev > 0.0f ? fminf(1.0f, max_channel(frev) / prev) : 0.0f;
+                  lp = prev * qx * cx[C_GP * 32 + L];
+                }
+                t_lc = pN * (cosl * INV_PI_F * ci * id2) * (y1 + lp * sy);
+              }
+              const float den = t_nee + t_cam + t_lc;
+              const float sc = den > 0.0f ? t_nee / (den * pn) : 0.0f;
+              v = mk3(fc.x * l4.x * sc, fc.y * l4.y * sc, fc.z * l4.z * sc);
+            } else {
+              // f|cos| Le / p_N times the balance weight beta_N p_N / den: p_N cancels
+              const float den = bwB * pb + bwG * pg + bwNv * pn;
+              const float sc = bwNv / den;
+              v = mk3(fc.x * l4.x * sc, fc.y * l4.y * sc, fc.z * l4.z * sc);
+            }
           }
         }
         a.SH[2][j] = f4(v, 0.0f);
@@ -634,21 +721,45 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_shade(const DevScene
         }
         float cA = 0.0f, cS = 0.0f, cinvSb = 0.0f;
         f3 cf = mk3(0.f, 0.f, 0.f), cT = mk3(0.f, 0.f, 0.f);
+        float cz[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (ok) {
           float pb;
-          const f3 fc = bsdf_eval(m, wol, fr.to_local(wi), pb);
+          const f3 wil = fr.to_local(wi);
+          const f3 fc = bsdf_eval(m, wol, wil, pb);
           const float pg = on_g ? guide_pdf(cdf, wi) : 0.0f;
           if (t == 0) pt = pb;
           if (pt > 0.0f && nonzero(fc)) {
             const float ipt = 1.0f / pt;
             cf = mk3(fc.x * ipt, fc.y * ipt, fc.z * ipt);
             cA = (t == 0 ? bwB : bwG) * pt;
-            cS = bwB * pb + bwG * pg;
-            const float w_ind = cA / cS;
-            const float wb = w_ind / bt;
-            cT = mk3(vT.x * cf.x * wb, vT.y * cf.y * wb, vT.z * cf.z * wb);
-            const float sb = bB * pb + (on_g ? bG * pg : 0.0f);
-            cinvSb = sb > 0.0f ? 1.0f / sb : 0.0f;
+            if (BD) {
+              // no MIS weight on the continuation; the ray carries |cos| here and
+              // the whole-path window
+              const float wb = 1.0f / bt;
+              cT = mk3(vT.x * cf.x * wb, vT.y * cf.y * wb, vT.z * cf.z * wb);
+              cS = dot(vns, wi);
+              // Z of the child: Z[1] = bw_L here, Z[l] = W[l - 1] (W[1] = Y[1], W[l] = Y[l] P<-_{d-1})
+              cz[0] = on_l ? (it.aware ? bG : 1.0f) : 0.0f;
+              cz[1] = cx[C_Y * 32 + L];
+              float sy = 0.0f;
+#pragma unroll
+              for (int q = 1; q < 5; ++q) sy += cx[(C_Y + q) * 32 + L];
+              if (sy > 0.0f) {
+                float prev;
+                const f3 frev = bsdf_eval(m, wil, wol, prev);   // P<- of the parent towards its parent
+                const float qx = prev > 0.0f ? fminf(1.0f, max_channel(frev) / prev) : 0.0f;
+                const float lp = prev * qx * cx[C_GP * 32 + L];
+#pragma unroll
+                for (int q = 1; q < 5; ++q) cz[q + 1] = cx[(C_Y + q) * 32 + L] * lp;
+              }
+            } else {
+              cS = bwB * pb + bwG * pg;
+              const float w_ind = cA / cS;
+              const float wb = w_ind / bt;
+              cT = mk3(vT.x * cf.x * wb, vT.y * cf.y * wb, vT.z * cf.z * wb);
+              const float sb = bB * pb + (on_g ? bG * pg : 0.0f);
+              cinvSb = sb > 0.0f ? 1.0f / sb : 0.0f;
+            }
           }
         }
         const uint64_t digit = (uint64_t)(t == 0 ? sidx + 1 : 32 + sidx + 1);
@@ -657,9 +768,43 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_shade(const DevScene
         a.R[1][j] = f4(wi, cA);
         a.R[2][j] = f4(cT, cS);
         a.R[3][j] = f4(cf, bwNv);
-        a.R[4][j] = make_float4(__uint_as_float((uint32_t)clin), __uint_as_float((uint32_t)(clin >> 32)),
-                                __uint_as_float((uint32_t)vcell), cinvSb);
+        if (BD) {
+          a.R[4][j] = make_float4(__uint_as_float((uint32_t)clin), __uint_as_float((uint32_t)(clin >> 32)), cz[0], cz[1]);
+          a.R5[j] = make_float4(cz[2], cz[3], cz[4], cz[5]);
+        } else {
+          a.R[4][j] = make_float4(__uint_as_float((uint32_t)clin), __uint_as_float((uint32_t)(clin >> 32)),
+                                  __uint_as_float((uint32_t)vcell), cinvSb);
+        }
         a.M[j] = cx[C_MULT * 32 + L] * bt;
+      }
+    }
+
+    // light connection samples: the camera vertex's context for the light kernel
+    if (BD) {
+      for (int k0 = 0; k0 < al.total; k0 += 32) {
+        const int k = k0 + lane;
+        const unsigned long long j = lbase + al.base + (unsigned long long)k;
+        if (k < al.total && j < a.lcap) {
+          const int L = owner_lane(ctx->incl_lc, k);
+          const int sidx = k - (L > 0 ? ctx->incl_lc[L - 1] : 0);
+          const f3 vns = mk3(cx[C_NS * 32 + L], cx[(C_NS + 1) * 32 + L], cx[(C_NS + 2) * 32 + L]);
+          const f3 wow = make_frame(vns).to_world(mk3(cx[C_WO * 32 + L], cx[(C_WO + 1) * 32 + L],
+                                                      cx[(C_WO + 2) * 32 + L]));
+          const float bB = cx[C_B0 * 32 + L], bN = cx[C_B1 * 32 + L], bL = cx[C_B2 * 32 + L];
+          a.LJ[0][j] = make_float4(cx[C_XO * 32 + L], cx[(C_XO + 1) * 32 + L], cx[(C_XO + 2) * 32 + L],
+                                   cx[C_PX * 32 + L]);
+          a.LJ[1][j] = f4(vns, __uint_as_float((uint32_t)__float_as_int(cx[C_MTYPE * 32 + L]) |
+                                               ((uint32_t)sidx << 8) | ((uint32_t)d << 16)));
+          a.LJ[2][j] = make_float4(cx[C_COL * 32 + L], cx[(C_COL + 1) * 32 + L], cx[(C_COL + 2) * 32 + L],
+                                   cx[C_ALPHA * 32 + L]);
+          a.LJ[3][j] = f4(wow, cx[C_MULT * 32 + L]);
+          a.LJ[4][j] = make_float4(cx[C_T * 32 + L], cx[(C_T + 1) * 32 + L], cx[(C_T + 2) * 32 + L], bB);
+          a.LJ[5][j] = make_float4(it.aware ? bB : 1.0f, on_n ? (it.aware ? bN : 1.0f) : 0.0f,
+                                   it.aware ? bL : 1.0f, cx[C_GP * 32 + L]);
+          a.LJ[6][j] = make_float4(cx[C_Y * 32 + L], cx[(C_Y + 1) * 32 + L], cx[(C_Y + 2) * 32 + L],
+                                   cx[(C_Y + 3) * 32 + L]);
+          a.LJ[7][j] = make_float4(cx[C_LIN * 32 + L], cx[(C_LIN + 1) * 32 + L], 0.0f, 0.0f);
+        }
       }
     }
     __syncwarp();  // the context is overwritten by the next chunk
@@ -700,7 +845,7 @@ __device__ __forceinline__ float seg_scan(float v, int lane, int start) {
   return v;
 }
 
-template <int MINB>
+template <int MINB, bool BD>
 __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_reverse(const DevScene s, const DevCache c, const Arena a,
                                                              const IterArgs* __restrict__ itp, const int d) {
   const IterArgs it = *itp;
@@ -710,7 +855,7 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_reverse(const DevSce
   const int lane = threadIdx.x & 31;
   const unsigned long long gw = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
   const unsigned long long nw = (gridDim.x * (unsigned long long)blockDim.x) >> 5;
-  const bool on_n = c.techniques & MARS_TECH_NEE, on_g = c.techniques & MARS_TECH_GUIDED;
+  const bool on_n = c.techniques & MARS_TECH_NEE, on_g = !BD && (c.techniques & MARS_TECH_GUIDED);
   const bool collect = it.collect != 0;
   // iteration counters of this thread's slots: one warp reduction and one
   // atomic per counter and warp at the end, not per chunk (every warp of the
@@ -757,6 +902,10 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_reverse(const DevSce
       if (guide_dep) v4 = a.V[4][i];
       if (flags & F_EST) {
         int gB = flags & 0xff, gN = (flags >> 8) & 0xff, gG = (flags >> 16) & 0xff;
+        // with light connections slot 2 holds the light connection samples,
+        // which are not children
+        int gL = BD ? gG : 0;
+        if (BD) gG = 0;
         int ne = gB + gG;
         unsigned long long first = __float_as_uint(fs.x), sf = __float_as_uint(fs.y);
         // the children and NEE values lie inside the arena (else read none)
@@ -825,6 +974,21 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_reverse(const DevSce
             }
           }
         }
+        if (BD && gL > 0) {
+          // light connection samples: value and cost from the light kernel
+          unsigned long long lf = __float_as_uint(v3.w);
+          if (!chk(lf + (unsigned long long)gL <= a.lcap, MARS_CHECK_ARENA, ctr)) gL = 0;
+          const float ib = 1.0f / bt[2];
+          for (int q = 0; q < gL; ++q) {
+            const float4 lv = a.LR[lf + q];
+            const f3 v = xyz(lv);
+            const uint32_t cc = (uint32_t)lv.w;
+            Lr = Lr + mk3(v.x * ib, v.y * ib, v.z * ib);
+            csub += cc;
+            st[2][0] += 1.0f; st[2][1] += v.x; st[2][2] += v.y; st[2][3] += v.z;
+            st[2][4] += v.x * v.x; st[2][5] += v.y * v.y; st[2][6] += v.z * v.z; st[2][7] += (float)cc;
+          }
+        }
         const f3 G = xyz(v1);
         E = E + mul(G, Lr);
       }
@@ -868,7 +1032,7 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_reverse(const DevSce
         const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
-          if (!((c.techniques >> t) & 1)) continue;
+          if (!slot_on(c.techniques, t)) continue;
           // skip a technique no lane drew, and the scan when every run is one lane
           if (!__any_sync(FULL, st[t][0] > 0.0f)) continue;
           if (pairs) {
@@ -910,7 +1074,7 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_reverse(const DevSce
       atomicAdd(&ctr->est_vertices, n_est);
       atomicAdd(&ctr->sum_beta[0], sb0);
       if (on_n) atomicAdd(&ctr->sum_beta[1], sb1);
-      if (on_g) atomicAdd(&ctr->sum_beta[2], sb2);
+      if (on_g || BD) atomicAdd(&ctr->sum_beta[2], sb2);
     }
     if (n_rays) atomicAdd(&ctr->rays, n_rays);
   }
@@ -925,9 +1089,15 @@ size_t shade_smem(int threads) { return (size_t)(threads / 32) * sizeof(ShadeWar
 using TraceFn = void (*)(const DevScene, const DevCache, const Arena, const IterArgs*, const int);
 using ShadowFn = void (*)(const DevScene, const DevCache, const Arena, const int);
 TraceFn trace_fn(int v) { return v == 2 ? k_trace<6> : (v == 1 ? k_trace<4> : k_trace<1>); }
-TraceFn shade_fn(int v) { return v == 2 ? k_shade<4> : (v == 1 ? k_shade<3> : k_shade<1>); }
+TraceFn shade_fn(int v, bool bd = false) {
+  if (bd) return v == 2 ? k_shade<4, true> : (v == 1 ? k_shade<3, true> : k_shade<1, true>);
+  return v == 2 ? k_shade<4, false> : (v == 1 ? k_shade<3, false> : k_shade<1, false>);
+}
 ShadowFn shadow_fn(int v) { return v == 2 ? k_shadow<6> : (v == 1 ? k_shadow<4> : k_shadow<1>); }
-TraceFn reverse_fn(int v) { return v == 2 ? k_reverse<4> : (v == 1 ? k_reverse<3> : k_reverse<1>); }
+TraceFn reverse_fn(int v, bool bd = false) {
+  if (bd) return v == 2 ? k_reverse<4, true> : (v == 1 ? k_reverse<3, true> : k_reverse<1, true>);
+  return v == 2 ? k_reverse<4, false> : (v == 1 ? k_reverse<3, false> : k_reverse<1, false>);
+}
 
 }  // namespace
 
@@ -965,37 +1135,49 @@ cudaError_t launch_tile(const DevScene& s, const DevCache& c, const Arena& a, co
   auto G = [&](int k, int) { return L.grid[k]; };
   const size_t smS = shade_smem(tS);
   const bool nee = (c.techniques & MARS_TECH_NEE) != 0;
-  // The NEE shadow rays of wave d run on the side stream, overlapped with the
-  // forward kernels of the next waves (disjoint data); the reverse pass, their
-  // only consumer, waits for all of them.
-  // sync: D + 1 events without timing (after shade(d); after the last shadow
-  // kernel).  ev (optional, 5 D + 2 timing events): ev[0] start; ev[2(d-1)+1],
+  const bool bd = (c.techniques & MARS_TECH_LIGHT) != 0;
+  // The NEE shadow rays and the light connection samples of wave d run on the
+  // side stream, overlapped with the forward kernels of the next waves
+  // (disjoint data); the reverse pass, their only consumer, waits for all of
+  // them.
+  // sync: D + 1 events without timing (after shade(d); after the last side
+  // kernel).  ev (optional, 7 D + 2 timing events): ev[0] start; ev[2(d-1)+1],
   // ev[2(d-1)+2] after wave d's trace and shade; ev[2D + 2(d-1) + 1 .. 2] around
   // its shadow kernel on the side stream; ev[5D + 1] when the reverse pass may
-  // start; ev[4D + k] after the k-th reverse kernel.
+  // start; ev[4D + k] after the k-th reverse kernel; ev[5D + 2 + 2(d-1) .. + 1]
+  // around its light connection kernel on the side stream.
   if (ev) cudaEventRecord(ev[0], st);
-  bool any_shadow = false;
+  bool any_side = false;
   for (int d = 1; d <= D; ++d) {
     trace_fn(L.variant[WK_TRACE])<<<G(WK_TRACE, d), tT, 0, st>>>(s, c, a, it, d);
     if (ev) cudaEventRecord(ev[2 * (d - 1) + 1], st);
-    shade_fn(L.variant[WK_SHADE])<<<G(WK_SHADE, d), tS, smS, st>>>(s, c, a, it, d);
+    shade_fn(L.variant[WK_SHADE], bd)<<<G(WK_SHADE, d), tS, smS, st>>>(s, c, a, it, d);
     if (ev) cudaEventRecord(ev[2 * (d - 1) + 2], st);
-    if (d <= D - 1 && nee) {
+    const bool shadow = d <= D - 1 && nee, light = bd && d <= D - 2;
+    if (shadow || light) {
       cudaEventRecord(sync[d - 1], st);
       cudaStreamWaitEvent(side, sync[d - 1], 0);
+      any_side = true;
+    }
+    if (shadow) {
       if (ev) cudaEventRecord(ev[2 * D + 2 * (d - 1) + 1], side);
       shadow_fn(L.variant[WK_SHADOW])<<<G(WK_SHADOW, d), tH, 0, side>>>(s, c, a, d);
       if (ev) cudaEventRecord(ev[2 * D + 2 * (d - 1) + 2], side);
-      any_shadow = true;
+    }
+    if (light) {
+      if (ev) cudaEventRecord(ev[5 * D + 2 + 2 * (d - 1)], side);
+      cudaError_t e = launch_light(s, c, a, it, L.variant[WK_SHADOW], G(WK_SHADOW, d), tH, d, side);
+      if (e != cudaSuccess) return e;
+      if (ev) cudaEventRecord(ev[5 * D + 2 + 2 * (d - 1) + 1], side);
     }
   }
-  if (any_shadow) {
+  if (any_side) {
     cudaEventRecord(sync[D], side);
     cudaStreamWaitEvent(st, sync[D], 0);
   }
   if (ev) cudaEventRecord(ev[5 * D + 1], st);
   for (int d = D; d >= 1; --d) {
-    reverse_fn(L.variant[WK_REVERSE])<<<G(WK_REVERSE, d), tR, 0, st>>>(s, c, a, it, d);
+    reverse_fn(L.variant[WK_REVERSE], bd)<<<G(WK_REVERSE, d), tR, 0, st>>>(s, c, a, it, d);
     if (ev) cudaEventRecord(ev[4 * D + (D - d + 1)], st);
   }
   k_tile_finish<<<1, 32, 0, st>>>(c.ctr, c.tile_status, it, D);
@@ -1008,7 +1190,8 @@ cudaError_t launch_merge_lanes(DevCounters* dst, DevCounters* src, cudaStream_t 
 }
 
 int tile_launches(int max_depth, int techniques) {
-  return 2 + 2 * max_depth + max_depth + ((techniques & MARS_TECH_NEE) ? max_depth - 1 : 0);
+  return 2 + 2 * max_depth + max_depth + ((techniques & MARS_TECH_NEE) ? max_depth - 1 : 0) +
+         ((techniques & MARS_TECH_LIGHT) && max_depth > 2 ? max_depth - 2 : 0);
 }
 
 }  // namespace mars

@@ -329,7 +329,7 @@ __global__ void k_update_counts(DevCache c) {
   for (int k = 1; k < NSTAT; ++k) v[k] = sp[k * plane];
   const double VI = c.ctr->VI, CI = c.ctr->CI;
   const double cost = v[7];
-  if (((c.techniques >> t) & 1) && VI > 1e-12 && n >= 2.0 && cost > 0.0) {
+  if (slot_on(c.techniques, t) && VI > 1e-12 && n >= 2.0 && cost > 0.0) {
     // C_I / C_t / V_I with C_t = cost / n, and 1 / n, formed once in float64
     const double inv_n = 1.0 / n;
     const double r = CI * n / (cost * VI);
@@ -361,7 +361,7 @@ __global__ void k_update_counts32(DevCache c) {
   const float4 b = s4[1];
   const float VI = (float)c.ctr->VI, CI = (float)c.ctr->CI;
   const float n = a.x, cost = b.w;
-  if (((c.techniques >> t) & 1) && VI > 1e-12f && n >= 2.0f && cost > 0.0f) {
+  if (slot_on(c.techniques, t) && VI > 1e-12f && n >= 2.0f && cost > 0.0f) {
     const float inv_n = 1.0f / n;
     const float r = CI * n / (cost * VI);
     const float s1[3] = {a.y, a.z, a.w}, s2v[3] = {b.x, b.y, b.z};

@@ -143,7 +143,9 @@ class Cache:
                 "wave_ms": [[st.wave_ms[k][d] for d in range(self.max_depth)] for k in range(4)],
                 "wave_rays": [st.wave_rays[d] for d in range(self.max_depth)],
                 "trace_work": [[st.trace_work[k][q] for q in range(4)] for k in range(2)],
-                "check_flags": st.check_flags}
+                "check_flags": st.check_flags, "light_rays": st.light_rays,
+                "connection_rays": st.connection_rays, "light_samples": st.light_samples,
+                "light_ms": st.light_ms}
 
     def combined_image(self, stream=None):
         """(image [height][width][3] float32, weight sum) of the progressive

@@ -1174,3 +1174,127 @@ def test_lane_settings_and_autotuned_lanes(mars):
     assert one.get_launch()["lanes"] == 1
     with pytest.raises(mars.MarsError):
         one.set_launch(base["threads"], base["blocks_per_sm"], base["max_registers"], lanes=2)
+
+
+# ------------------------------------------- bidirectional application (Sec. 5)
+TECH_BD = W.TECH_BSDF | W.TECH_NEE | W.TECH_LIGHT
+
+
+@pytest.mark.parametrize("mode,weights", [(0, 0), (1, 0), (1, 1)])
+def test_bidirectional_box_parity(mars, orc, mode, weights):
+    """Light connections in the box: warm-up (budgets 1) and a teacher-forced
+    MARS iteration with random count fields for all three techniques
+    (budget-aware and -unaware whole-path weights): image, per-cell statistics
+    (the light connection's value, second moment and cost included) and
+    counters against the oracle."""
+    cfg = W.WorkloadConfig(W.box_scene(48, 40), max_depth=5, grid_n=8, techniques=TECH_BD, iterations=2, warmup=1,
+                           name="box bidirectional")
+    scene, cache = _make(mars, cfg)
+    q_rr, q_s, valid = W.random_count_fields(cfg.n_cells, seed=601, lo=0.1, hi=3.0)
+    est = W.random_pixel_estimate(cfg.scene.n_pixels, seed=602, lo=0.05, hi=1.0)
+    okw = dict(grid_n=cfg.grid_n, techniques=TECH_BD, max_depth=cfg.max_depth, iteration=3, seed=5, weights=weights)
+    if mode == 1:
+        cache.set_state(q_rr=q_rr, q_s=q_s, valid=valid, pixel_estimate=est, has_estimate=True, n_iterations=1)
+        okw.update(mode=orc.MODE_MARS, q_rr=q_rr, q_s=q_s, valid=valid, est=est)
+    g_img, g_st = _gpu_iteration(mars, cache, iteration=3, seed=5, mode=mode, weights=weights)
+    g_state = cache.get_state()
+    o = orc.render(cfg.scene, **okw)
+    touch = lambda px: _touched_cells(mars, orc, cache, cfg.scene,
+                                      dict(iteration=3, seed=5, mode=mode, weights=weights), okw, px)
+    _check(g_img, o.image, g_state, o, g_st, f"box bidirectional mode {mode} weights {weights}", touch)
+    assert o.stats[:, 2, 0].sum() > 0 and o.stats[:, 2, 1:4].sum() > 0
+    assert g_st["light_samples"] == pytest.approx(o.stats[:, 2, 0].sum(), rel=1e-3)
+    assert g_st["light_rays"] == pytest.approx(o.counters[6], rel=1e-3)
+    assert g_st["vertices"] == pytest.approx(o.counters[1], rel=1e-3)
+
+
+def test_bidirectional_heightfield_parity(mars, orc):
+    """The bidirectional workload's geometry, small: a heightfield whose emitter
+    hides between two spheres (most of the terrain is lit only through light
+    paths), triangles and spheres, with an adaptive octree refined by the
+    oracle's rule and random counts."""
+    sc = W.heightfield_scene(3, n=12, width=40, height=32, n_spheres=20)
+    cfg = W.WorkloadConfig(sc, max_depth=6, grid_n=4, techniques=TECH_BD, iterations=2, warmup=1, name="hf bd")
+    cells = 1024
+    nodes, nn, nl, lvl, lnode = orc.octree_init(4, cells)
+    rng = np.random.default_rng(611)
+    z = np.zeros((cells, 3, 3), np.float32)
+    zv = np.zeros((cells, 3), np.uint8)
+    stt = np.zeros((cells, 3, 8))
+    stt[:nl, 0, 0] = rng.integers(0, 200, size=nl)
+    nodes, nn, nl, lvl, lnode, *_ = orc.octree_refine(cells, 100.0, stt, nodes, nn, nl, lvl, lnode, z, z, zv)
+    scene = mars.Scene(sc)
+    cache = mars.Cache(scene, 4, TECH_BD, 6, octree=True, max_leaves=cells, split_samples=1e30)
+    q_rr, q_s, valid = W.random_count_fields(cells, seed=612, lo=0.1, hi=3.0)
+    est = W.random_pixel_estimate(sc.n_pixels, seed=613, lo=0.01, hi=0.5)
+    cache.set_state(q_rr=q_rr, q_s=q_s, valid=valid, pixel_estimate=est, has_estimate=True, n_iterations=1,
+                    oct_nodes=nodes[:nn], oct_leaf_level=lvl[:nl])
+    g_img, g_st = _gpu_iteration(mars, cache, iteration=2, seed=8, mode=1)
+    g_state = cache.get_state()
+    okw = dict(grid_n=4, techniques=TECH_BD, max_depth=6, iteration=2, seed=8, mode=orc.MODE_MARS, q_rr=q_rr,
+               q_s=q_s, valid=valid, est=est, octree=(nodes, cells))
+    o = orc.render(sc, **okw)
+    touch = lambda px: _touched_cells(mars, orc, cache, sc, dict(iteration=2, seed=8, mode=1), okw, px)
+    _check(g_img, o.image, g_state, o, g_st, "heightfield bidirectional", touch)
+    assert o.stats[:, 2, 1:4].sum() > 0
+
+
+@pytest.mark.parametrize("albedo,D", [(0.5, 4), (0.7, 6)])
+def test_gpu_bidirectional_furnace_closed_form(mars, albedo, D):
+    """The closed furnace through the CUDA path with light connections and
+    random counts: the image mean is Le (1 - a^D)/(1 - a) within 3.5 sigma."""
+    import torch
+    sc = W.furnace_scene(albedo=albedo, radiance=1.5, width=32, height=32)
+    scene = mars.Scene(sc)
+    cache = mars.Cache(scene, 4, TECH_BD, D)
+    q_rr, q_s, valid = W.random_count_fields(64, seed=621, lo=0.1, hi=3.0)
+    est = W.random_pixel_estimate(sc.n_pixels, seed=622, lo=0.5, hi=4.0)
+    cache.set_state(q_rr=q_rr, q_s=q_s, valid=valid, pixel_estimate=est, has_estimate=True, n_iterations=1)
+    img = torch.zeros(sc.n_pixels * 3, dtype=torch.float32, device="cuda")
+    vals = []
+    for it in range(40):
+        cache.render_iteration(img, iteration=it, mode=1, collect=False, update_estimate=False)
+        vals.append(float(img.double().mean()))
+    m, se = np.mean(vals), np.std(vals, ddof=1) / math.sqrt(len(vals))
+    expected = 1.5 * (1 - albedo ** D) / (1 - albedo)
+    assert abs(m - expected) < 3.5 * se + 1e-6, (m, expected, se)
+
+
+def test_bidirectional_tiles_lanes_and_graphs_do_not_change_the_image(mars):
+    """A queue arena too small for the frame (pixel tiles, re-rendered after an
+    overflow), two tile lanes and CUDA-graph replay give the image of one
+    directly launched tile bit for bit, with light connections."""
+    import torch
+    cfg = W.WorkloadConfig(W.box_scene(64, 48), max_depth=6, grid_n=8, techniques=TECH_BD, iterations=1, warmup=0,
+                           name="box bd")
+    scene = mars.Scene(cfg.scene)
+    q_rr, q_s, valid = W.random_count_fields(cfg.n_cells, seed=631, lo=0.3, hi=4.0)
+    est = W.random_pixel_estimate(cfg.scene.n_pixels, seed=632, lo=0.05, hi=0.5)
+    out = []
+    for kw in (dict(graphs=False, lanes=1), dict(arena_capacity=20000, graphs=False, lanes=1),
+               dict(graphs=True, lanes=2)):
+        cache = mars.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, **kw)
+        cache.set_state(q_rr=q_rr, q_s=q_s, valid=valid, pixel_estimate=est, has_estimate=True, n_iterations=1)
+        if kw.get("lanes") == 2:
+            cache.set_launch([128] * 4, [0] * 4, lanes=2, lane_min_pixels=2)
+        s = torch.cuda.Stream()
+        img = torch.zeros(cfg.scene.n_pixels * 3, dtype=torch.float32, device="cuda")
+        for rep in range(2):
+            st = cache.render_iteration(img, iteration=4, seed=2, mode=1, update_estimate=False, stream=s)
+        torch.cuda.synchronize()
+        out.append((img.cpu().numpy().copy(), st))
+    assert out[1][1]["tiles"] > 1
+    for img, st in out[1:]:
+        assert np.array_equal(img, out[0][0])
+        assert st["light_samples"] == out[0][1]["light_samples"] and st["rays"] == out[0][1]["rays"]
+
+
+def test_bidirectional_argument_errors(mars):
+    sc = W.box_scene(8, 8)
+    scene = mars.Scene(sc)
+    with pytest.raises(mars.MarsError) as e:
+        mars.Cache(scene, 4, W.TECH_BSDF | W.TECH_GUIDED | W.TECH_LIGHT, 4)
+    assert e.value.status == mars.MARS_ERR_INVALID_ARG
+    with pytest.raises(mars.MarsError) as e:
+        mars.Cache(scene, 4, W.TECH_BSDF | 16, 4)
+    assert e.value.status == mars.MARS_ERR_INVALID_ARG
