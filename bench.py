@@ -540,98 +540,17 @@ def run_mars(args):
         dist.destroy_process_group()
 
 
-def large_scene(args, M, stream):
-    """The heightfield workload (256 x 256 quads = 131k triangles + 202 spheres,
-    1024 x 1024, D = 10, three techniques) with the adaptive octree cache
-    (starting as the 32^3 grid, at most 64k leaves): hierarchy build time, then
-    3 warm-up and 3 timed MARS iterations (then 3 more with every launch timed)
-    with the bidirectional application's image-level rules (Sec. 5.1: V_I
-    without the 10 brightest pixels, the iterations combined with weights
-    1 / V_I); throughput, kernel times,
-    traversal work per ray and the octree's size at this geometry size."""
+def bidirectional_scene(args, M, stream, cfg, seed, timed_iters, precision_study_too, unaware=False):
+    """A bidirectional workload (Sec. 5: BSDF sampling, NEE and connections to
+    light subpaths, each with its own budget; whole-path budget-aware balance
+    weights) with the adaptive octree cache (starting as the 32^3 grid, at most
+    64k leaves) and the application's image-level rules (Sec. 5.1: V_I without
+    the 10 brightest pixels, iterations combined with weights 1 / V_I):
+    hierarchy build time, 3 warm-up and `timed_iters` timed MARS iterations
+    (then as many with every launch timed), the equal-time efficiency against
+    fixed-count MIS on the same GPU, and optionally the float32 versus float64
+    statistics comparison at this size."""
     import torch
-    cfg = W.config_heightfield(1024, 1024)
-    cfg.scene.bvh = BVH_KINDS[args.bvh]
-    t0 = time.perf_counter()
-    scene = M.Scene(cfg.scene, stream=stream)
-    torch.cuda.synchronize()
-    build_s = time.perf_counter() - t0
-    cache = M.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, octree=True, max_leaves=65536,
-                    split_samples=4096.0, stream=stream)
-    img = torch.zeros(cfg.scene.n_pixels * 3, dtype=torch.float32, device="cuda")
-    it = 0
-    for k in range(3):
-        cache.render_iteration(img, seed=77, iteration=it, mode=M.MARS_MODE_WARMUP, update_estimate=True,
-                               vi_drop_brightest=10, stream=stream)
-        cache.update_counts(stream=stream)
-        it += 1
-    launch = cache.autotune(iteration=it, seed=77, mode=M.MARS_MODE_MARS, repeats=1, stream=stream)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    sts = []
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for k in range(3):
-        sts.append(cache.render_iteration(img, seed=77, iteration=it, mode=M.MARS_MODE_MARS, update_estimate=True,
-                                          vi_drop_brightest=10, combine=2 if k == 0 else 1, stream=stream))
-        cache.update_counts(stream=stream)
-        it += 1
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / 3
-    verts = sum(s["vertices"] for s in sts) / 3
-    timed = sts
-    # kernel times: the same iterations once more, every launch between events
-    sts = []
-    for k in range(3):
-        sts.append(cache.render_iteration(img, seed=77, iteration=it, mode=M.MARS_MODE_MARS, update_estimate=True,
-                                          profile=True, vi_drop_brightest=10, combine=1, stream=stream))
-        cache.update_counts(stream=stream)
-        it += 1
-    tw = [sum(s["trace_work"][0][q] for s in sts) for q in range(4)]
-    n = max(sum(s["wave_entries"] for s in sts), 1)
-    out = {"workload": cfg.name, "primitives": int(len(cfg.scene.tris) + len(cfg.scene.spheres) + len(cfg.scene.quads)),
-           "bvh_build_s": round(build_s, 3), "ms_per_step": round(ms, 3),
-           "mvertices_s": round(verts / (ms * 1e-3) / 1e6, 1), "vertices_per_step": int(verts),
-           "kernel_ms_per_step": {k: round(sum(s[k + "_ms"] for s in sts) / 3, 4)
-                                  for k in ("trace", "shade", "shadow", "reverse", "image")},
-           "closest_hit_per_ray": {"nodes": round(tw[0] / n, 2), "prim_tests": round(sum(tw[1:]) / n, 2)},
-           "mean_beta": [round(sum(s["mean_beta"][t] for s in sts) / 3, 4) for t in range(3)],
-           "octree_leaves": int(cache.info()["oct_n_leaves"]), "launch": launch,
-           "tiles": [s["tiles"] for s in timed],
-           "progressive": {"vi_drop_brightest": 10, "combined_iterations": 6,
-                           "combined_weight": round(cache.combined_image(stream=stream)[1], 4),
-                           "VI": [round(s["VI"], 5) for s in timed + sts]}}
-    if not args.no_efficiency:
-        out["efficiency"] = efficiency(args, M, cfg, scene, cache, 77, it, stream, ref_spp=args.large_ref_spp,
-                                       cache_kw=dict(octree=True, max_leaves=65536, split_samples=4096.0),
-                                       unaware=False)
-    if not args.no_precision:
-        # float32 versus float64 statistics at this size (the large bidirectional
-        # workload's precision comparison), on the learned state and tree
-        from paper_2410_20429_gb300 import precision
-        g = cache.get_state(stream=stream)
-        rep = precision.compare(cfg.scene, cfg.grid_n, cfg.techniques, cfg.max_depth, g["q_rr"], g["q_s"],
-                                g["valid"], g["pixel_estimate"], g["run_sum"], g["n_iterations"], iteration=it,
-                                seed=77, stream=stream,
-                                cache_kw=dict(octree=True, max_leaves=65536, split_samples=4096.0),
-                                tree=(g["oct_nodes"], g["oct_leaf_level"]), guide_cdf=g["guide_cdf"])
-        out["precision"] = {k: [float("%.3g" % rep[k]["max"]), float("%.3g" % rep[k]["median"])]
-                            for k in precision.STATISTICS}
-        out["precision"]["entries"] = rep["cells_compared"]
-        out["precision"]["images_equal"] = rep["images_equal"]
-    del cache, scene
-    return out
-
-
-def largest_scene(args, M, stream):
-    """The largest single-GPU workload (the geometry of the large bidirectional
-    configuration, rendered unidirectionally): 512 x 512 quads = 524k triangles,
-    4096 GGX spheres, 8 area lights, 2048 x 2048, D = 12, BSDF + NEE, adaptive
-    octree <= 64k leaves, a 2 x pixels x D arena; 3 warm-up and 2 timed MARS iterations (then
-    2 with every launch timed), then the float32 versus float64 statistics
-    comparison at this size."""
-    import torch
-    cfg = W.config_large(2048, 2048)
     cfg.scene.bvh = BVH_KINDS[args.bvh]
     t0 = time.perf_counter()
     scene = M.Scene(cfg.scene, stream=stream)
@@ -643,54 +562,68 @@ def largest_scene(args, M, stream):
     cache = M.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, stream=stream, **kw)
     img = torch.zeros(npx * 3, dtype=torch.float32, device="cuda")
     it = 0
-    for k in range(3):
-        cache.render_iteration(img, seed=91, iteration=it, mode=M.MARS_MODE_WARMUP, update_estimate=True,
-                               stream=stream)
+    for k in range(cfg.warmup):
+        cache.render_iteration(img, seed=seed, iteration=it, mode=M.MARS_MODE_WARMUP, update_estimate=True,
+                               vi_drop_brightest=10, stream=stream)
         cache.update_counts(stream=stream)
         it += 1
+    launch = cache.autotune(iteration=it, seed=seed, mode=M.MARS_MODE_MARS, repeats=1, stream=stream)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     sts = []
     torch.cuda.synchronize()
     e0.record(stream)
-    for k in range(2):
-        sts.append(cache.render_iteration(img, seed=91, iteration=it, mode=M.MARS_MODE_MARS, update_estimate=True,
-                                          stream=stream))
+    for k in range(timed_iters):
+        sts.append(cache.render_iteration(img, seed=seed, iteration=it, mode=M.MARS_MODE_MARS, update_estimate=True,
+                                          vi_drop_brightest=10, combine=2 if k == 0 else 1, stream=stream))
         cache.update_counts(stream=stream)
         it += 1
     e1.record(stream)
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / 2
-    verts = sum(s["vertices"] for s in sts) / 2
+    ms = e0.elapsed_time(e1) / timed_iters
+    verts = sum(s["vertices"] for s in sts) / timed_iters
     timed = sts
+    # kernel times: as many iterations again, every launch between events
     sts = []
-    for k in range(2):
-        sts.append(cache.render_iteration(img, seed=91, iteration=it, mode=M.MARS_MODE_MARS, update_estimate=True,
-                                          profile=True, stream=stream))
+    for k in range(timed_iters):
+        sts.append(cache.render_iteration(img, seed=seed, iteration=it, mode=M.MARS_MODE_MARS, update_estimate=True,
+                                          profile=True, vi_drop_brightest=10, combine=1, stream=stream))
         cache.update_counts(stream=stream)
         it += 1
     tw = [sum(s["trace_work"][0][q] for s in sts) for q in range(4)]
     n = max(sum(s["wave_entries"] for s in sts), 1)
+    k_n = len(sts)
     out = {"workload": cfg.name, "primitives": int(len(cfg.scene.tris) + len(cfg.scene.spheres) + len(cfg.scene.quads)),
-           "bvh_build_s": round(build_s, 3), "ms_per_step": round(ms, 3),
+           "techniques": "bsdf+nee+light_connection", "bvh_build_s": round(build_s, 3), "ms_per_step": round(ms, 3),
            "mvertices_s": round(verts / (ms * 1e-3) / 1e6, 1), "vertices_per_step": int(verts),
-           "tiles": [s["tiles"] for s in timed], "arena_slots": cap,
-           "kernel_ms_per_step": {k: round(sum(s[k + "_ms"] for s in sts) / 2, 4)
-                                  for k in ("trace", "shade", "shadow", "reverse", "image")},
+           "vertices_note": "closest-hit queries of camera paths and light subpaths",
+           "light_subpath_rays_per_step": int(sum(s["light_rays"] for s in timed) / timed_iters),
+           "connection_rays_per_step": int(sum(s["connection_rays"] for s in timed) / timed_iters),
+           "light_samples_per_step": int(sum(s["light_samples"] for s in timed) / timed_iters),
+           "kernel_ms_per_step": {k: round(sum(s[k + "_ms"] for s in sts) / k_n, 4)
+                                  for k in ("trace", "shade", "shadow", "light", "reverse", "image")},
            "closest_hit_per_ray": {"nodes": round(tw[0] / n, 2), "prim_tests": round(sum(tw[1:]) / n, 2)},
-           "mean_beta": [round(sum(s["mean_beta"][t] for s in sts) / 2, 4) for t in range(3)],
-           "octree_leaves": int(cache.info()["oct_n_leaves"]),
-           "device_gb": round(cache.info()["device_bytes"] / 1e9, 2)}
+           "mean_beta": {"bsdf": round(sum(s["mean_beta"][0] for s in sts) / k_n, 4),
+                         "nee": round(sum(s["mean_beta"][1] for s in sts) / k_n, 4),
+                         "light_connection": round(sum(s["mean_beta"][2] for s in sts) / k_n, 4)},
+           "octree_leaves": int(cache.info()["oct_n_leaves"]), "launch": launch,
+           "tiles": [s["tiles"] for s in timed], "arena_slots": cap,
+           "device_gb": round(cache.info()["device_bytes"] / 1e9, 2),
+           "progressive": {"vi_drop_brightest": 10, "combined_iterations": 2 * timed_iters,
+                           "combined_weight": round(cache.combined_image(stream=stream)[1], 4),
+                           "VI": [round(s["VI"], 5) for s in timed + sts]}}
     if not args.no_efficiency:
-        out["efficiency"] = efficiency(args, M, cfg, scene, cache, 91, it, stream, ref_spp=args.large_ref_spp,
-                                       cache_kw=kw, unaware=False)
-    if not args.no_precision:
+        out["efficiency"] = efficiency(args, M, cfg, scene, cache, seed, it, stream, ref_spp=args.large_ref_spp,
+                                       cache_kw=kw, unaware=unaware, vi_drop=10)
+    if precision_study_too and not args.no_precision:
+        # float32 versus float64 statistics at this size (the large bidirectional
+        # workload's precision comparison), on the learned state and tree
         from paper_2410_20429_gb300 import precision
         g = cache.get_state(stream=stream)
         del cache
         torch.cuda.synchronize()
         rep = precision.compare(cfg.scene, cfg.grid_n, cfg.techniques, cfg.max_depth, g["q_rr"], g["q_s"],
                                 g["valid"], g["pixel_estimate"], g["run_sum"], g["n_iterations"], iteration=it,
-                                seed=91, stream=stream, cache_kw=kw,
+                                seed=seed, stream=stream, cache_kw=kw,
                                 tree=(g["oct_nodes"], g["oct_leaf_level"]), guide_cdf=g.get("guide_cdf"))
         out["precision"] = {k: [float("%.3g" % rep[k]["max"]), float("%.3g" % rep[k]["median"])]
                             for k in precision.STATISTICS}
@@ -700,6 +633,20 @@ def largest_scene(args, M, stream):
         del cache
     del scene
     return out
+
+
+def large_scene(args, M, stream):
+    """The bidirectional workload: heightfield of 256 x 256 quads (131k
+    triangles) + 200 spheres with one small emitter hidden between two
+    spheres, 1024 x 1024, D = 10, light subpaths of at most 6 vertices."""
+    return bidirectional_scene(args, M, stream, W.config_bdpt_heightfield(1024, 1024), 77, 3, False, unaware=True)
+
+
+def largest_scene(args, M, stream):
+    """The large bidirectional workload: 512 x 512 quads = 524k triangles, 4096
+    GGX spheres, 8 area lights, 2048 x 2048, D = 12, with the float32 versus
+    float64 statistics comparison at this size."""
+    return bidirectional_scene(args, M, stream, W.config_bdpt_large(2048, 2048), 91, 2, True)
 
 
 def serving(args):
@@ -774,7 +721,7 @@ def precision_study(cfg, cache, seed, it, stream):
     return out
 
 
-def efficiency(args, M, cfg, scene, cache, seed, it0, stream, ref_spp=None, cache_kw=None, unaware=True):
+def efficiency(args, M, cfg, scene, cache, seed, it0, stream, ref_spp=None, cache_kw=None, unaware=True, vi_drop=0):
     """Equal-time efficiency 1/(relMSE * s): MARS with the counts learned so far
     (frozen: no statistics, no update) vs fixed-count MIS (beta = 1), both
     timed with CUDA events, against a long fixed-count reference.  Like for
@@ -844,7 +791,7 @@ def efficiency(args, M, cfg, scene, cache, seed, it0, stream, ref_spp=None, cach
         own = M.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, stream=stream, **cache_kw)
         for k in range(it0):
             own.render_iteration(img, seed=seed, iteration=k, mode=M.MARS_MODE_FIXED, update_estimate=True,
-                                 stream=stream)
+                                 vi_drop_brightest=vi_drop, stream=stream)
             own.update_counts(stream=stream)
         f_own = timed(own, M.MARS_MODE_FIXED, args.eff_spp, 20000)
         del own
@@ -862,7 +809,7 @@ def efficiency(args, M, cfg, scene, cache, seed, it0, stream, ref_spp=None, cach
         for k in range(it0):
             un_cache.render_iteration(img, seed=seed, iteration=k, mode=M.MARS_MODE_WARMUP if k < args.warmup
                                       else M.MARS_MODE_MARS, weights=M.MARS_WEIGHTS_UNAWARE, update_estimate=True,
-                                      stream=stream)
+                                      vi_drop_brightest=vi_drop, stream=stream)
             un_cache.update_counts(stream=stream)
         un = timed(un_cache, M.MARS_MODE_MARS, args.eff_spp, 20000, weights=M.MARS_WEIGHTS_UNAWARE)
         del un_cache
