@@ -104,14 +104,17 @@ def _stat_tolerance(o_stats):
     return tol
 
 
-def _strict_stats(g_stats, o_stats, touched, what):
+def _strict_stats(g_stats, o_stats, touched, what, sensitive=None):
     """Every populated (cell, technique) entry outside the cells reached by a
-    disagreeing pixel agrees in all 8 sums (see _stat_tolerance); returns the
-    fraction of all populated entries that agree."""
+    disagreeing pixel (and outside the `sensitive` entries, if given) agrees in
+    all 8 sums (see _stat_tolerance); returns the fraction of all populated
+    entries that agree."""
     g_stats = g_stats[: o_stats.shape[0]]
     pop = (g_stats[..., 0] > 0) | (o_stats[..., 0] > 0)
     close = (np.abs(g_stats - o_stats) <= _stat_tolerance(o_stats) + 1e-12).all(axis=-1)
     keep = pop & ~touched[: o_stats.shape[0], None]
+    if sensitive is not None:
+        keep &= ~sensitive
     bad = np.argwhere(keep & ~close)
     assert bad.size == 0, f"{what}: {len(bad)} (cell, technique) entries outside the disagreeing pixels' " \
                           f"cells differ, e.g. {bad[:3].tolist()}: " + \
@@ -990,7 +993,7 @@ def _full_size_runs(npx):
 def _full_size_oracle(job):
     """Worker (a spawned process): the oracle over some runs of pixels of the
     full-size case, on the scene nudged by `nudge` float32 ulps; returns the
-    runs' pixels and, unnudged, their summed statistics and counters."""
+    runs' pixels and statistics and, unnudged, their summed counters."""
     which, nudge, starts = job
     import oracle
     cfg, cells, tree, q_rr, q_s, valid, est, cdf = _full_size_inputs(which)
@@ -998,17 +1001,17 @@ def _full_size_oracle(job):
     if nudge != 0:
         est = _nudge32(est, nudge)
     kw = dict(grid_n=cfg.grid_n, techniques=cfg.techniques, max_depth=cfg.max_depth, iteration=7, seed=11,
-              mode=oracle.MODE_MARS, q_rr=q_rr, q_s=q_s, valid=valid, est=est, guide_cdf=cdf, collect=nudge == 0)
+              mode=oracle.MODE_MARS, q_rr=q_rr, q_s=q_s, valid=valid, est=est, guide_cdf=cdf, collect=True)
     if tree is not None:
         kw["octree"] = (tree[0], cells)
     pix, runs, ctr = {}, {}, np.zeros(8)
     for b in starts:
         r = oracle.render(sc, px_begin=b, px_end=b + FULL_RUN_LEN, **kw)
         pix[b] = (r.image[b:b + FULL_RUN_LEN].copy(), r.px_rays[b:b + FULL_RUN_LEN].copy())
+        flat = r.stats.reshape(-1, 8)
+        idx = np.flatnonzero(flat[:, 0] > 0)
+        runs[b] = (idx, flat[idx].copy())   # the run's populated (cell, technique) entries
         if nudge == 0:
-            flat = r.stats.reshape(-1, 8)
-            idx = np.flatnonzero(flat[:, 0] > 0)
-            runs[b] = (idx, flat[idx].copy())   # the run's populated (cell, technique) entries
             ctr += r.counters
     return pix, runs, ctr
 
@@ -1026,7 +1029,10 @@ def test_full_size_sampled_parity(mars, orc, which):
     a run of pixels is rendered identically inside the frame and alone.  The
     statistics of the sampled runs (the CUDA path renders them again as pixel
     ranges into empty statistics) are compared in total within 1e-3 and per
-    (cell, technique) entry wherever no disagreeing pixel reaches.
+    (cell, technique) entry wherever no disagreeing pixel reaches and 4 ulps of
+    input do not move the oracle's entry beyond the bar (a single light
+    connection over a short distance carries the float32 error of its end
+    points amplified by 1 / d^2, as a glossy pixel does its normal's).
 
     Pixel bar: these frames hold pixels whose value a float32 evaluation cannot
     pin down -- small GGX spheres (alpha down to 0.05) that reflect a light,
@@ -1086,12 +1092,22 @@ def test_full_size_sampled_parity(mars, orc, which):
     res = {n: [f.result() for f in fl] for n, fl in futs.items()}
     pool.shutdown()
     o_pix = {n: {b: p for r in rl for b, p in r[0].items()} for n, rl in res.items()}
-    o_runs = {b: v for r in res[0] for b, v in r[1].items()}
+    o_runs_n = {n: {b: v for r in rl for b, v in r[1].items()} for n, rl in res.items()}
+    o_runs = o_runs_n[0]
     o_ctr = sum(r[2] for r in res[0])
     g_stats = sum(g_runs.values())
-    o_stats = np.zeros((cells, 3, 8))
-    for idx, vals in o_runs.values():
-        o_stats.reshape(-1, 8)[idx] += vals
+    o_stats_n = {}
+    for n, runs_ in o_runs_n.items():
+        o_stats_n[n] = np.zeros((cells, 3, 8))
+        for idx, vals in runs_.values():
+            o_stats_n[n].reshape(-1, 8)[idx] += vals
+    o_stats = o_stats_n[0]
+    # (cell, technique) entries whose sums NUDGE_ULPS ulps of input move beyond the bar
+    tol = _stat_tolerance(o_stats) + 1e-12
+    sensitive = np.zeros((cells, 3), bool)
+    for n in (1, -1):
+        sensitive |= (np.abs(o_stats_n[n] - o_stats) > tol).any(axis=-1)
+    del o_stats_n, o_runs_n
 
     def off(x, y):
         return (np.abs(x - y) > PIX_TOL * np.abs(y) + 1e-7).any(axis=1)
@@ -1140,7 +1156,11 @@ def test_full_size_sampled_parity(mars, orc, which):
     assert abs(rays - o_ctr[0]) <= 1e-3 * o_ctr[0] + 1 and abs(verts - o_ctr[1]) <= 1e-3 * o_ctr[1] + 1
     assert n_flagged < FULL_RUNS // 2, msg
     assert np.allclose(g_ok.sum(0), o_ok.sum(0), rtol=STAT_TOL, atol=1e-6), which
-    _strict_stats(g_stats, o_stats, touched, which)
+    pop = (g_stats[..., 0] > 0) | (o_stats[..., 0] > 0)
+    e_off = pop & ~(np.abs(g_stats - o_stats) <= tol).all(axis=-1)
+    print(f"{which}: {NUDGE_ULPS} ulps of input move {int((sensitive & pop).sum())} of {int(pop.sum())} "
+          f"populated entries; {int(e_off.sum())} entries off, {int((e_off & sensitive).sum())} of them sensitive")
+    _strict_stats(g_stats, o_stats, touched, which, sensitive=sensitive)
 
 
 def test_lane_settings_and_autotuned_lanes(mars):
