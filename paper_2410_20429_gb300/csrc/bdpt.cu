@@ -39,8 +39,15 @@ constexpr int MAX_LIGHT_THREADS = 256;
 
 struct LightVertex {
   f3 p, l, alpha;  // position, unit direction towards the previous light vertex, throughput
+  f3 ng;           // geometric normal
   float t, lam;    // distance to the previous light vertex, area density on the subpath
-  int prim;
+  int prim, cell;  // primitive; statistics cell (for the budgets of a camera path through it)
+  Mat mat;
+  // the BSDF towards the previous light vertex with the next one as the outgoing
+  // direction (f cos and density, as a camera path y_{k+1} -> y_k -> y_{k-1}
+  // samples it), and |cos| at the previous vertex towards this one
+  f3 frev;
+  float prev, cos_prev;
 };
 
 __device__ __forceinline__ Mat material_at(const DevScene& s, int prim, DevCounters* ctr, float4* m0_out) {
@@ -131,9 +138,11 @@ __global__ void __launch_bounds__(MAX_LIGHT_THREADS, MINB) k_light(const DevScen
       y[kk - 1].p = p;
       y[kk - 1].l = lin_dir;
       y[kk - 1].alpha = alpha;
+      y[kk - 1].ng = ng;
       y[kk - 1].t = t;
       y[kk - 1].lam = lam;
       y[kk - 1].prim = prim;
+      y[kk - 1].mat = mt;
       m = kk;
       if (kk == kmax) break;
       // continue: BSDF sampling with the light arriving from y_{k-1}, then the roulette
@@ -156,13 +165,33 @@ __global__ void __launch_bounds__(MAX_LIGHT_THREADS, MINB) k_light(const DevScen
     }
     n_rays += (unsigned long long)rays;
 
+    // ---- what the connections' weights need of each light vertex, once per
+    // vertex rather than once per connection that passes it: its cell, the
+    // reverse BSDF towards the previous vertex (the next vertex as the outgoing
+    // direction; the last vertex's depends on the connection), the cosine there
+    for (int kk = 1; kk <= m; ++kk) {
+      LightVertex& v = y[kk - 1];
+      int cell = c.oct_nodes ? octree_cell(s, c.oct_nodes, v.p) : cell_of(s, c.grid_n, v.p);
+      if (!chk(cell >= 0 && cell < c.n_cells, MARS_CHECK_CELL, ctr)) cell = 0;
+      v.cell = cell;
+      v.cos_prev = kk == 1 ? cos0 : fabsf(dot(y[kk - 2].ng, v.l));
+      v.frev = mk3(0.f, 0.f, 0.f);
+      v.prev = 0.0f;
+      if (kk < m) {
+        const f3 wo_u = y[kk].l * -1.0f;
+        const f3 nsu = dot(v.ng, wo_u) >= 0.0f ? v.ng : v.ng * -1.0f;
+        const Frame fu = make_frame(nsu);
+        v.frev = bsdf_eval(v.mat, fu.to_local(wo_u), fu.to_local(v.l), v.prev);
+      }
+    }
+
     // ---- connections x_i -- y_k
     f3 val = mk3(0.f, 0.f, 0.f);
     const Frame fx = make_frame(nsx);
     const f3 wox = fx.to_local(wo_x);
     for (int kk = 1; kk <= m; ++kk) {
       const LightVertex& yk = y[kk - 1];
-      const f3 ngk = prim_normal(s.prims, yk.prim, yk.p);
+      const f3 ngk = yk.ng;
       const f3 nsy = dot(ngk, yk.l) >= 0.0f ? ngk : ngk * -1.0f;
       const f3 yo = yk.p + nsy * s.eps;
       const f3 dv = yo - xo;
@@ -172,7 +201,7 @@ __global__ void __launch_bounds__(MAX_LIGHT_THREADS, MINB) k_light(const DevScen
       const f3 wx = fx.to_local(w);
       float pxv;
       const f3 fxv = bsdf_eval(mx, wox, wx, pxv);
-      const Mat my = material_at(s, yk.prim, ctr, nullptr);
+      const Mat my = yk.mat;
       const Frame fy = make_frame(nsy);
       const f3 ly = fy.to_local(yk.l), wy = fy.to_local(w * -1.0f);
       float pyv;
@@ -212,29 +241,27 @@ __global__ void __launch_bounds__(MAX_LIGHT_THREADS, MINB) k_light(const DevScen
       for (int a_ = 1; a_ <= kk; ++a_) {
         const LightVertex& uv = y[kk - a_];
         const int depth_u = depth_i + a_;
-        const f3 ngu = prim_normal(s.prims, uv.prim, uv.p);
-        int cell = c.oct_nodes ? octree_cell(s, c.oct_nodes, uv.p) : cell_of(s, c.grid_n, uv.p);
-        if (!chk(cell >= 0 && cell < c.n_cells, MARS_CHECK_CELL, ctr)) cell = 0;
         const bool lc_here = depth_u <= D - 2;
         const unsigned on_mask = 1u | (on_n ? 2u : 0u) | (lc_here ? 4u : 0u);
         float bu[NT];
-        vertex_budgets(c, it, cell, Tu, est, mu, on_mask, 1.0f, 1.0f, bu);
+        vertex_budgets(c, it, uv.cell, Tu, est, mu, on_mask, 1.0f, 1.0f, bu);
         const float bwBu = aware ? bu[0] : 1.0f;
         const float bwNu = on_n ? (aware ? bu[1] : 1.0f) : 0.0f;
         const float bwLu = lc_here ? (aware ? bu[2] : 1.0f) : 0.0f;
-        const f3 nsu = dot(ngu, wo_u) >= 0.0f ? ngu : ngu * -1.0f;
-        const Frame fu = make_frame(nsu);
-        const Mat mu_ = material_at(s, uv.prim, ctr, nullptr);
         float pBu;
-        const f3 fcu = bsdf_eval(mu_, fu.to_local(wo_u), fu.to_local(uv.l), pBu);
+        f3 fcu;
+        if (a_ == 1) {
+          // the connected vertex: the camera side arrives along the connection
+          const f3 nsu = dot(uv.ng, wo_u) >= 0.0f ? uv.ng : uv.ng * -1.0f;
+          const Frame fu = make_frame(nsu);
+          fcu = bsdf_eval(uv.mat, fu.to_local(wo_u), fu.to_local(uv.l), pBu);
+        } else {
+          fcu = uv.frev;
+          pBu = uv.prev;
+        }
         if (a_ <= kk - 1) tc += G * bwLu * y[kk - a_ - 1].lam;
         if (a_ == kk) tc += G * bwNu * pN;
-        float cos_next = cos0;
-        if (a_ < kk) {
-          const LightVertex& nx = y[kk - a_ - 1];
-          cos_next = fabsf(dot(prim_normal(s.prims, nx.prim, nx.p), uv.l));
-        }
-        G *= bwBu * pBu * cos_next / (uv.t * uv.t);
+        G *= bwBu * pBu * uv.cos_prev / (uv.t * uv.t);
         Tu = pBu > 0.0f ? mul(Tu, fcu) * (1.0f / (pBu * bu[0])) : mk3(0.f, 0.f, 0.f);
         mu *= bu[0];
         wo_u = uv.l * -1.0f;
