@@ -18,6 +18,11 @@ LIB = os.path.join(PKG, "libmars.so")
 BUILD_CHECKED = os.path.join(PKG, "_build_checked")
 LIB_CHECKED = os.path.join(PKG, "libmars_checked.so")
 SOURCES = ["abi.cu", "render.cu", "bdpt.cu", "stats.cu", "scene.cu", "server.cu", "static_scratch.cu"]
+# the wave kernels (traversal, shading, light subpaths, reverse pass) take
+# float32 division and square root to within 2 ulp instead of correctly
+# rounded (the cell of a point keeps the IEEE operations); the hierarchy
+# build, image statistics and count update keep IEEE float32 arithmetic
+APPROX_DIV_SQRT = {"render.cu", "bdpt.cu"}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -58,6 +63,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, 
             extra = ["-Xptxas", "-v"] if ptxas_info else []
             if checked:
                 extra.append("-DMARS_CHECKED")
+            if src in APPROX_DIV_SQRT:
+                extra += ["-prec-div=false", "-prec-sqrt=false"]
             jobs.append([nv, *_flags(extra), "-c", s, "-o", o])
 
     def run(cmd):

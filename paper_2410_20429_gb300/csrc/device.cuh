@@ -526,12 +526,13 @@ __device__ __forceinline__ float max_channel(f3 a) { return fmaxf(a.x, fmaxf(a.y
 
 // ----------------------------------------------------------------- cells
 // cell coordinates of a point on an N^3 grid over the scene box; decided in
-// float32 like every integer choice
+// float32 like every integer choice, with IEEE round-to-nearest division and
+// product whatever the translation unit's division flags
 __device__ __forceinline__ void cell_coords(const DevScene& s, int N, f3 p, int idx[3]) {
   const float pa[3] = {p.x, p.y, p.z};
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const float f = (pa[a] - s.lo[a]) / s.ext[a] * (float)N;
+    const float f = __fmul_rn(__fdiv_rn(__fsub_rn(pa[a], s.lo[a]), s.ext[a]), (float)N);
     int i = (int)floorf(f);
     idx[a] = i < 0 ? 0 : (i > N - 1 ? N - 1 : i);
   }
