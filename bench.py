@@ -134,7 +134,7 @@ OPS_NODE, OPS_QUAD, OPS_SPHERE, OPS_TRI = 50, 67, 25, 45
 
 
 KERNEL_SOURCES = ["paper_2410_20429_gb300/csrc/render.cu", "paper_2410_20429_gb300/csrc/device.cuh",
-                  "paper_2410_20429_gb300/csrc/internal.h"]
+                  "paper_2410_20429_gb300/csrc/internal.h", "paper_2410_20429_gb300/build.py"]
 TRAFFIC_FILE = "profiles/dram_traffic_guided_room_512.txt"
 
 
@@ -239,16 +239,17 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm), "window": window}
 
 
-def rel_mse(img, ref, ref_var=None):
-    """relMSE: mean over pixels and channels of (I - R)^2 / (R^2 + 1e-2), after
-    dropping the 0.01 % largest per-pixel terms.  With ``ref_var`` (the variance
-    of the reference's mean, per pixel and channel) each squared difference is
-    reduced by it: E[(I - R)^2] = Var(I) + bias^2 + Var(R), so the estimate no
-    longer charges the reference's own noise to the image."""
+def rel_mse(img, ref, ref_var=None, eps=1e-2):
+    """relMSE: mean over pixels and channels of (I - R)^2 / (R^2 + eps), eps =
+    1e-2 by default, after dropping the 0.01 % largest per-pixel terms.  With
+    ``ref_var`` (the variance of the reference's mean, per pixel and channel)
+    each squared difference is reduced by it: E[(I - R)^2] = Var(I) + bias^2 +
+    Var(R), so the estimate no longer charges the reference's own noise to the
+    image."""
     d2 = (img - ref) ** 2
     if ref_var is not None:
         d2 = d2 - ref_var
-    t = (d2 / (ref ** 2 + 1e-2)).reshape(-1, 3).mean(axis=1)
+    t = (d2 / (ref ** 2 + eps)).reshape(-1, 3).mean(axis=1)
     k = int(math.ceil(1e-4 * t.size))
     if k > 0:
         t = np.sort(t)[:-k]
@@ -521,6 +522,8 @@ def run_mars(args):
         line["largest_scene"] = largest_scene(args, M, stream)
     if rank == 0 and args.serve_requests > 0:
         line["serving"] = serving(args)
+        if not args.no_efficiency:
+            line["serving"]["efficiency"] = serving_efficiency(args, M, stream)
     if rank == 0 and not args.no_precision:
         line["precision"] = precision_study(cfg, cache, seed, it, stream)
     if rank == 0 and not args.no_efficiency:
@@ -540,16 +543,17 @@ def run_mars(args):
         dist.destroy_process_group()
 
 
-def bidirectional_scene(args, M, stream, cfg, seed, timed_iters, precision_study_too, unaware=False):
+def bidirectional_scene(args, M, stream, cfg, seed, precision_study_too, unaware=False):
     """A bidirectional workload (Sec. 5: BSDF sampling, NEE and connections to
     light subpaths, each with its own budget; whole-path budget-aware balance
     weights) with the adaptive octree cache (starting as the 32^3 grid, at most
     64k leaves) and the application's image-level rules (Sec. 5.1: V_I without
     the 10 brightest pixels, iterations combined with weights 1 / V_I):
-    hierarchy build time, 3 warm-up and `timed_iters` timed MARS iterations
-    (then as many with every launch timed), the equal-time efficiency against
-    fixed-count MIS on the same GPU, and optionally the float32 versus float64
-    statistics comparison at this size."""
+    hierarchy build time, the workload's warm-up iterations, then its MARS
+    iterations timed (the whole job: `cfg.iterations` in all), then 3 with
+    every launch timed, the equal-time efficiency against fixed-count MIS on the
+    same GPU, and optionally the float32 versus float64 statistics comparison
+    at this size."""
     import torch
     cfg.scene.bvh = BVH_KINDS[args.bvh]
     t0 = time.perf_counter()
@@ -568,23 +572,30 @@ def bidirectional_scene(args, M, stream, cfg, seed, timed_iters, precision_study
         cache.update_counts(stream=stream)
         it += 1
     launch = cache.autotune(iteration=it, seed=seed, mode=M.MARS_MODE_MARS, repeats=1, stream=stream)
+    timed_iters = cfg.iterations - cfg.warmup
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     sts = []
     torch.cuda.synchronize()
     e0.record(stream)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(timed_iters + 1)]
+    evs[0] = e0
     for k in range(timed_iters):
         sts.append(cache.render_iteration(img, seed=seed, iteration=it, mode=M.MARS_MODE_MARS, update_estimate=True,
                                           vi_drop_brightest=10, combine=2 if k == 0 else 1, stream=stream))
         cache.update_counts(stream=stream)
         it += 1
+        if k + 1 < timed_iters:
+            evs[k + 1].record(stream)
     e1.record(stream)
+    evs[timed_iters] = e1
     torch.cuda.synchronize()
+    sts_ms = [evs[k].elapsed_time(evs[k + 1]) for k in range(timed_iters)]
     ms = e0.elapsed_time(e1) / timed_iters
     verts = sum(s["vertices"] for s in sts) / timed_iters
     timed = sts
-    # kernel times: as many iterations again, every launch between events
+    # kernel times: 3 iterations more, every launch between events
     sts = []
-    for k in range(timed_iters):
+    for k in range(3):
         sts.append(cache.render_iteration(img, seed=seed, iteration=it, mode=M.MARS_MODE_MARS, update_estimate=True,
                                           profile=True, vi_drop_brightest=10, combine=1, stream=stream))
         cache.update_counts(stream=stream)
@@ -595,6 +606,8 @@ def bidirectional_scene(args, M, stream, cfg, seed, timed_iters, precision_study
     out = {"workload": cfg.name, "primitives": int(len(cfg.scene.tris) + len(cfg.scene.spheres) + len(cfg.scene.quads)),
            "techniques": "bsdf+nee+light_connection", "bvh_build_s": round(build_s, 3), "ms_per_step": round(ms, 3),
            "mvertices_s": round(verts / (ms * 1e-3) / 1e6, 1), "vertices_per_step": int(verts),
+           "timed_iterations": timed_iters, "warmup_iterations": cfg.warmup,
+           "ms_per_step_first_last": [round(sts_ms[0], 3), round(sts_ms[-1], 3)],
            "vertices_note": "closest-hit queries of camera paths and light subpaths",
            "light_subpath_rays_per_step": int(sum(s["light_rays"] for s in timed) / timed_iters),
            "connection_rays_per_step": int(sum(s["connection_rays"] for s in timed) / timed_iters),
@@ -608,7 +621,7 @@ def bidirectional_scene(args, M, stream, cfg, seed, timed_iters, precision_study
            "octree_leaves": int(cache.info()["oct_n_leaves"]), "launch": launch,
            "tiles": [s["tiles"] for s in timed], "arena_slots": cap,
            "device_gb": round(cache.info()["device_bytes"] / 1e9, 2),
-           "progressive": {"vi_drop_brightest": 10, "combined_iterations": 2 * timed_iters,
+           "progressive": {"vi_drop_brightest": 10, "combined_iterations": timed_iters + 3,
                            "combined_weight": round(cache.combined_image(stream=stream)[1], 4),
                            "VI": [round(s["VI"], 5) for s in timed + sts]}}
     if not args.no_efficiency:
@@ -638,15 +651,18 @@ def bidirectional_scene(args, M, stream, cfg, seed, timed_iters, precision_study
 def large_scene(args, M, stream):
     """The bidirectional workload: heightfield of 256 x 256 quads (131k
     triangles) + 200 spheres with one small emitter hidden between two
-    spheres, 1024 x 1024, D = 10, light subpaths of at most 6 vertices."""
-    return bidirectional_scene(args, M, stream, W.config_bdpt_heightfield(1024, 1024), 77, 3, False, unaware=True)
+    spheres, 1024 x 1024, D = 10, light subpaths of at most 6 vertices, 32
+    iterations."""
+    n = args.large_size or 1024
+    return bidirectional_scene(args, M, stream, W.config_bdpt_heightfield(n, n), 77, False, unaware=True)
 
 
 def largest_scene(args, M, stream):
     """The large bidirectional workload: 512 x 512 quads = 524k triangles, 4096
-    GGX spheres, 8 area lights, 2048 x 2048, D = 12, with the float32 versus
-    float64 statistics comparison at this size."""
-    return bidirectional_scene(args, M, stream, W.config_bdpt_large(2048, 2048), 91, 2, True)
+    GGX spheres, 8 area lights, 2048 x 2048, D = 12, 64 iterations, with the
+    float32 versus float64 statistics comparison at this size."""
+    n = args.large_size or 2048
+    return bidirectional_scene(args, M, stream, W.config_bdpt_large(n, n), 91, True)
 
 
 def serving(args):
@@ -704,6 +720,43 @@ def serving(args):
             "failures": sorted(set(s.get("message", "")[:120] for s in sts if s["state"] != M.MARS_JOB_DONE))[:3]}
 
 
+def serving_efficiency(args, M, stream):
+    """Equal-time efficiency of the served workload (config 4): the first
+    request of each resolution of the serving stream, learned over its own
+    iterations (its warm-up, then MARS) as the server renders it, then the same
+    comparison with fixed-count MIS as for the main workload (512-spp reference)."""
+    import torch
+    reqs = W.serving_requests(args.serve_requests, rate=args.serve_rate, seed=11)
+    picked, seen = [], set()
+    for r in reqs:
+        if r["scene"].width not in seen:
+            seen.add(r["scene"].width)
+            picked.append(r)
+    out = []
+    for r in sorted(picked, key=lambda q: q["scene"].width):
+        cfg = W.WorkloadConfig(r["scene"], r["max_depth"], r["grid_n"], r["techniques"], r["iterations"], r["warmup"],
+                               r["scene"].name)
+        scene = M.Scene(cfg.scene, stream=stream)
+        cache = M.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, stream=stream)
+        img = torch.zeros(cfg.scene.n_pixels * 3, dtype=torch.float32, device="cuda")
+        for k in range(cfg.iterations):
+            cache.render_iteration(img, seed=r["seed"], iteration=k,
+                                   mode=M.MARS_MODE_WARMUP if k < cfg.warmup else M.MARS_MODE_MARS,
+                                   update_estimate=True, stream=stream)
+            cache.update_counts(stream=stream)
+        e = efficiency(args, M, cfg, scene, cache, r["seed"], cfg.iterations, stream, ref_spp=512, unaware=False)
+        out.append({"scene": cfg.name, "iterations": cfg.iterations, "ratio": round(e["ratio"], 4),
+                    "ratio_scaled": round(e["ratio_scaled"], 4),
+                    "ratio_vs_own_guide": round(e["ratio_vs_own_guide"], 4),
+                    "relmse": [e["mars"]["relmse"], e["fixed_count_mis"]["relmse"]],
+                    "seconds": [e["mars"]["seconds"], e["fixed_count_mis"]["seconds"]]})
+        del cache, scene
+    geo = float(np.exp(np.mean([np.log(max(q["ratio"], 1e-30)) for q in out])))
+    return {"requests": out, "ratio_geomean": round(geo, 4),
+            "protocol": "the first request of each resolution of the serving stream; efficiency() after its own "
+                        "iterations; fixed-count MIS with the learned guide; 512-spp fixed-count reference"}
+
+
 def precision_study(cfg, cache, seed, it, stream):
     """Float32 versus float64 statistics on the full workload: the next MARS
     iteration rendered from the bench cache's learned state on one cache of
@@ -749,6 +802,11 @@ def efficiency(args, M, cfg, scene, cache, seed, it0, stream, ref_spp=None, cach
     ref_var = ((acc2 / n_ref - ref_t * ref_t).clamp_min(0.0) / max(n_ref - 1, 1)).cpu().numpy().reshape(-1, 3)
     ref = ref_t.cpu().numpy().reshape(-1, 3)
     del ref_cache, acc, acc2
+    # relMSE's eps = 1e-2 assumes pixel values of order one (an image exposed
+    # for display); the same relMSE at this image's own scale takes eps = 1e-2
+    # times its squared mean (what scaling the emitters to a mean of one does)
+    ref_mean = float(ref.mean())
+    eps_scaled = 1e-2 * max(ref_mean, 1e-30) ** 2
 
     def timed(c, mode, n, it_base, weights=M.MARS_WEIGHTS_AWARE):
         a = torch.zeros(npx * 3, dtype=torch.float64, device="cuda")
@@ -765,8 +823,12 @@ def efficiency(args, M, cfg, scene, cache, seed, it0, stream, ref_spp=None, cach
         torch.cuda.synchronize()
         s = e0.elapsed_time(e1) * 1e-3
         mean = (a / n).cpu().numpy().reshape(-1, 3)
-        r = rel_mse(mean, ref, ref_var)
+        # a relMSE at or below zero (the reference's own variance exceeds the
+        # error) is floored: the comparison then resolves nothing
+        r = max(rel_mse(mean, ref, ref_var), 1e-30)
+        rs = max(rel_mse(mean, ref, ref_var, eps=eps_scaled), 1e-30)
         return {"relmse": r, "relmse_raw": rel_mse(mean, ref), "seconds": s, "efficiency": 1.0 / (r * s),
+                "relmse_scaled": rs, "efficiency_scaled": 1.0 / (rs * s),
                 "rays_per_pixel": rays / n / npx, "spp": n}
 
     guided = bool(cfg.techniques & W.TECH_GUIDED)
@@ -780,11 +842,14 @@ def efficiency(args, M, cfg, scene, cache, seed, it0, stream, ref_spp=None, cach
     fixed = timed(fixed_cache, M.MARS_MODE_FIXED, args.eff_spp, 20000)
     del fixed_cache
     out = {"mars": mars, "fixed_count_mis": fixed, "ratio": mars["efficiency"] / fixed["efficiency"],
+           "ratio_scaled": mars["efficiency_scaled"] / fixed["efficiency_scaled"],
+           "reference_mean": ref_mean, "eps_scaled": eps_scaled,
            "reference_spp": n_ref, "learning_iterations": it0,
            "protocol": "counts learned over the warm-up and timed iterations, then frozen; both arms render "
                        f"{args.eff_spp} fresh iterations with the same learned guide (fixed-count MIS: beta = 1); "
                        f"reference = fixed-count MIS, {n_ref} spp, other random numbers; relMSE with the variance "
-                       "of the reference's mean subtracted (relmse_raw without)"}
+                       "of the reference's mean subtracted (relmse_raw without); ratio_scaled: the same with "
+                       "relMSE's eps = 1e-2 x the reference's squared mean (the image at its own scale)"}
     if guided:
         # fixed-count MIS that learns its own guide from its own deposits over as
         # many iterations, and with the uniform guide of a fresh cache
@@ -1121,7 +1186,10 @@ def main():
     ap.add_argument("--lanes", type=int, default=2, choices=[1, 2],
                     help="concurrent pixel-tile lanes the cache is created with (the autotuner keeps one or all)")
     ap.add_argument("--no-precision", action="store_true")
-    ap.add_argument("--no-large", action="store_true", help="skip the heightfield (131k triangles) section")
+    ap.add_argument("--no-large", action="store_true", help="skip the bidirectional heightfield sections")
+    ap.add_argument("--large-size", type=int, default=0,
+                    help="image side of both bidirectional sections (0: 1024 and 2048, their workloads' sizes; "
+                         "smaller for profiling captures)")
     ap.add_argument("--serve-requests", type=int, default=256, help="serving-stream requests (0 = skip)")
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--serve-slots", type=int, default=8)

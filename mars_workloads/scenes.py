@@ -220,11 +220,16 @@ def occluded_light_plane_scene(width: int = 1, height: int = 1, fov: float = 30.
 def guided_room_scene(seed: int = 0, width: int = 512, height: int = 512,
                       n_spheres: int = 64, n_lights: int = 4) -> Scene:
     """Closed 4 x 4 x 4 room (albedo 0.7) with ``n_spheres`` seeded spheres
-    (centres uniform in the room, radius U[0.05, 0.5]); 70 % GGX with roughness
-    U[0.05, 0.5] and 30 % Lambertian, colour U[0.2, 0.9] per channel; and
-    ``n_lights`` 0.3 x 0.3 ceiling lights with radiance log-uniform in [1, 100]."""
+    (centres uniform in the room, radius U[0.05, 0.5], scaled by (64 /
+    n_spheres)^(1/3) beyond 64 spheres so that they fill the room no more than
+    64 do; a sphere that would hold the camera shrinks to 0.9 of its distance
+    from it); 70 % GGX with roughness U[0.05, 0.5] and 30 % Lambertian, colour
+    U[0.2, 0.9] per channel; and ``n_lights`` 0.3 x 0.3 ceiling lights with
+    radiance log-uniform in [1, 100]."""
     rng = np.random.Generator(np.random.Philox(key=seed))
     L = 4.0
+    cam = [2.0, 2.0, 0.05, 2.0, 1.6, 4.0, 0.0, 1.0, 0.0, 65.0]
+    rscale = (64.0 / n_spheres) ** (1.0 / 3.0) if n_spheres > 64 else 1.0
     mats = [_lambert(0.7, 0.7, 0.7)]
     quads = [
         [0, 0, 0, 0, 0, L, L, 0, 0],   # floor
@@ -239,7 +244,10 @@ def guided_room_scene(seed: int = 0, width: int = 512, height: int = 512,
     sphere_mat = []
     for _ in range(n_spheres):
         c = rng.uniform(0.0, L, size=3)
-        r = rng.uniform(0.05, 0.5)
+        r = rng.uniform(0.05, 0.5) * rscale
+        dcam = math.sqrt(sum((c[k] - cam[k]) ** 2 for k in range(3)))
+        if dcam <= r:
+            r = 0.9 * dcam
         col = rng.uniform(0.2, 0.9, size=3)
         if rng.uniform() < 0.7:
             mats.append(_ggx(col[0], col[1], col[2], rng.uniform(0.05, 0.5)))
@@ -255,7 +263,6 @@ def guided_room_scene(seed: int = 0, width: int = 512, height: int = 512,
         mats.append(_lambert(0.0, 0.0, 0.0, (le, le, le)))
         quads.append([x, y_light, z, s, 0, 0, 0, 0, s])  # e1 x e2 = -y
         quad_mat.append(len(mats) - 1)
-    cam = [2.0, 2.0, 0.05, 2.0, 1.6, 4.0, 0.0, 1.0, 0.0, 65.0]
     return _mk(quads, quad_mat, spheres, sphere_mat, mats, cam, width, height, "guided_room")
 
 
