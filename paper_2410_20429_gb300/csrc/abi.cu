@@ -600,6 +600,7 @@ mars_status cache_create_impl(const mars_scene* s, const mars_cache_desc* d, cud
   c->arena.cap = cap;
   c->arena.scap = cap;  // NEE shadow rays: as many slots as rays
   c->arena.lcap = (d->techniques & MARS_TECH_LIGHT) ? cap : 0;  // light connection samples: likewise
+  c->arena.vcap = c->arena.lcap;                                  // and light subpath vertices
   c->max_tiles = 4096;
   // two tile lanes (each with half the arena) unless asked for one or the
   // image has a single pixel
@@ -631,6 +632,11 @@ mars_status cache_create_impl(const mars_scene* s, const mars_cache_desc* d, cud
       if ((e = dev_alloc((void**)&c->arena.LJ[k], sizeof(float4) * c->arena.lcap, st)) != cudaSuccess)
         return cleanup(e, "arena alloc");
     if ((e = dev_alloc((void**)&c->arena.LR, sizeof(float4) * c->arena.lcap, st)) != cudaSuccess)
+      return cleanup(e, "arena alloc");
+    for (int k = 0; k < NLV; ++k)
+      if ((e = dev_alloc((void**)&c->arena.LV[k], sizeof(float4) * c->arena.vcap, st)) != cudaSuccess)
+        return cleanup(e, "arena alloc");
+    if ((e = dev_alloc((void**)&c->arena.LC, sizeof(float4) * c->arena.vcap, st)) != cudaSuccess)
       return cleanup(e, "arena alloc");
   }
   if ((e = dev_alloc((void**)&c->d_cnt, sizeof(float4) * 2 * NT * cells, st)) != cudaSuccess) return cleanup(e, "cache alloc");
@@ -855,6 +861,8 @@ void cache_destroy_impl(mars_cache* c) {
   dev_free(c->arena.R5, st);
   for (auto* p : c->arena.LJ) dev_free(p, st);
   dev_free(c->arena.LR, st);
+  for (auto* p : c->arena.LV) dev_free(p, st);
+  dev_free(c->arena.LC, st);
   void* ptrs[] = {c->d_cnt, c->d_stats, c->d_stats32, c->d_hist, c->d_cdf, c->d_guide_dirty, c->d_est, c->d_run,
                   c->d_img, c->d_ctr, c->d_tile_status, c->d_oct_nodes, c->d_oct_level, c->d_oct_lnode,
                   c->d_oct_meta, c->d_oct_split, c->d_oct_leaf_n, c->d_comb, c->d_comb_w, c->d_topk};
@@ -896,8 +904,8 @@ static Arena lane_arena(const mars_cache* c, int l, int nl) {
   Arena a = c->arena;
   if (nl <= 1) return a;
   const uint64_t rc = c->arena.cap / (uint64_t)nl, sc = c->arena.scap / (uint64_t)nl;
-  const uint64_t lc = c->arena.lcap / (uint64_t)nl;
-  const uint64_t r0 = rc * (uint64_t)l, s0 = sc * (uint64_t)l, l0 = lc * (uint64_t)l;
+  const uint64_t lc = c->arena.lcap / (uint64_t)nl, vc = c->arena.vcap / (uint64_t)nl;
+  const uint64_t r0 = rc * (uint64_t)l, s0 = sc * (uint64_t)l, l0 = lc * (uint64_t)l, v0 = vc * (uint64_t)l;
   for (auto& p : a.R) p += r0;
   for (auto& p : a.V) p += r0;
   a.S += r0;
@@ -909,10 +917,13 @@ static Arena lane_arena(const mars_cache* c, int l, int nl) {
     a.R5 += r0;
     for (auto& p : a.LJ) p += l0;
     a.LR += l0;
+    for (auto& p : a.LV) p += v0;
+    a.LC += v0;
   }
   a.cap = rc;
   a.scap = sc;
   a.lcap = lc;
+  a.vcap = vc;
   return a;
 }
 
@@ -1221,6 +1232,7 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
     double need = std::max((double)h.entries / (double)c->arena.cap,
                            (double)h.shadow_entries / (double)c->arena.scap);
     if (c->arena.lcap) need = std::max(need, (double)h.light_entries / (double)c->arena.lcap);
+    if (c->arena.vcap) need = std::max(need, (double)h.light_vertex_entries / (double)c->arena.vcap);
     const double growth = c->last_entries > 0 ? std::min(2.0, std::max(1.0, (double)h.entries /
                                                                              (double)c->last_entries))
                                               : 1.0;

@@ -100,11 +100,23 @@ struct DevScene {
 // V3.w holds the first light connection slot of the vertex, and the light
 // connection samples of wave d occupy [lbase[d], lbase[d] + lcount[d]) of a
 // third region: LJ0..LJ7 the camera vertex's context (written by the shade
-// kernel), LR = (sample value rgb, cost) written by the light kernel.
-constexpr int NR = 5, NV = 5, NSH = 3, NLJ = 8;
+// kernel), LR = (first light vertex slot, light vertex count m, pN, cost)
+// written by the light-subpath kernel.  The light vertices of wave d's samples
+// occupy [vbase(d), vbase(d) + vcount[d]) of a fourth region, vbase(d) the sum
+// of the earlier waves' vcount, each sample's m vertices in order:
+//   LV0 = (position, primitive), LV1 = (unit direction to the previous light
+//   vertex, distance to it), LV2 = (throughput alpha, area density lambda),
+//   LV3 = (geometric normal, cell), LV4 = (reverse f cos towards the previous
+//   vertex with the next one outgoing, its density), LV5 = (|cos| at the
+//   previous vertex towards this one, sample slot, index in the subpath, -),
+// and LC = (weighted contribution of the connection to it if visible, -),
+// written by the connection kernel.
+constexpr int NR = 5, NV = 5, NSH = 3, NLJ = 8, NLV = 6;
 constexpr int SLOT_BYTES = (NR + NV + 1) * 16 + 8 + 4;  // per ray slot
 constexpr int SHADOW_BYTES = NSH * 16 + 4;          // per shadow-ray slot
-constexpr int LIGHT_SLOT_BYTES = 16 + (NLJ + 1) * 16;  // R5 per ray slot, LJ and LR per connection slot
+// R5 per ray slot, LJ and LR per connection slot, LV and LC per light vertex
+// slot (as many of each as ray slots)
+constexpr int LIGHT_SLOT_BYTES = 16 + (NLJ + 1) * 16 + (NLV + 1) * 16;
 struct Arena {
   float4* R[NR];
   float2* H;
@@ -116,9 +128,12 @@ struct Arena {
   float4* R5;        // light connections only
   float4* LJ[NLJ];
   float4* LR;
+  float4* LV[NLV];
+  float4* LC;
   uint64_t cap;   // ray slots
   uint64_t scap;  // shadow-ray slots
   uint64_t lcap;  // light connection slots (0 without light connections)
+  uint64_t vcap;  // light vertex slots (0 without light connections)
 };
 
 // V0.w flag bits
@@ -134,8 +149,10 @@ struct DevCounters {
   unsigned long long slcount[MAXD + 2];  // shadow rays of wave d that need tracing
   unsigned long long lbase[MAXD + 2];    // light connection samples of wave d
   unsigned long long lcount[MAXD + 2];
+  unsigned long long vcount[MAXD + 2];   // light subpath vertices of wave d's samples
   unsigned long long light_rays, conn_rays;  // light-subpath closest hits, connection rays (every launch)
   unsigned long long light_entries;          // light connection samples of committed tiles
+  unsigned long long light_vertex_entries;   // light subpath vertices of committed tiles
   unsigned long long shadow_entries;     // shadow rays of committed tiles
   unsigned long long shadow_traced;      // listed (traced) shadow rays of committed tiles
   unsigned long long wave_total[MAXD + 2];  // rays per depth wave of committed tiles

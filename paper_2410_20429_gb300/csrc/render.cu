@@ -149,6 +149,7 @@ __global__ void k_tile_init(DevCounters* ctr, const IterArgs* __restrict__ itp) 
     ctr->slcount[t] = 0;
     ctr->lbase[t] = 0;
     ctr->lcount[t] = 0;
+    ctr->vcount[t] = 0;
   }
   if (t == 0) {
     ctr->overflow = 0;
@@ -166,18 +167,20 @@ __global__ void k_tile_finish(DevCounters* ctr, unsigned int* tile_status, const
   }
   ctr->demand = dem;
   if (!ctr->overflow) {
-    unsigned long long tot = 0, sh = 0, sl = 0, lc = 0;
+    unsigned long long tot = 0, sh = 0, sl = 0, lc = 0, lv = 0;
     for (int d = 1; d <= D; ++d) {
       tot += ctr->count[d];
       sh += ctr->scount[d];
       sl += ctr->slcount[d];
       lc += ctr->lcount[d];
+      lv += ctr->vcount[d];
       ctr->wave_total[d] += ctr->count[d];
     }
     ctr->entries += tot;
     ctr->shadow_entries += sh;
     ctr->shadow_traced += sl;
     ctr->light_entries += lc;
+    ctr->light_vertex_entries += lv;
   }
   tile_status[slot] = ctr->overflow;
   if (ctr->overflow) ctr->any_overflow = 1;
@@ -194,10 +197,11 @@ __global__ void k_merge_lanes(DevCounters* dst, DevCounters* src) {
   dst->est_vertices += src->est_vertices;
   dst->entries += src->entries;
   dst->light_entries += src->light_entries;
+  dst->light_vertex_entries += src->light_vertex_entries;
   dst->light_rays += src->light_rays;
   dst->conn_rays += src->conn_rays;
   src->shadow_entries = src->shadow_traced = src->rays = src->vertices = src->est_vertices = src->entries = 0;
-  src->light_entries = src->light_rays = src->conn_rays = 0;
+  src->light_entries = src->light_vertex_entries = src->light_rays = src->conn_rays = 0;
   for (int d = 0; d < MAXD + 2; ++d) {
     dst->wave_total[d] += src->wave_total[d];
     src->wave_total[d] = 0;
@@ -975,14 +979,19 @@ __global__ void __launch_bounds__(MAX_WAVE_THREADS, MINB) k_reverse(const DevSce
           }
         }
         if (BD && gL > 0) {
-          // light connection samples: value and cost from the light kernel
+          // light connection samples: the sum of the sample's connections (in
+          // the order of its light vertices) and its cost from the light kernels
           unsigned long long lf = __float_as_uint(v3.w);
           if (!chk(lf + (unsigned long long)gL <= a.lcap, MARS_CHECK_ARENA, ctr)) gL = 0;
           const float ib = 1.0f / bt[2];
           for (int q = 0; q < gL; ++q) {
-            const float4 lv = a.LR[lf + q];
-            const f3 v = xyz(lv);
-            const uint32_t cc = (uint32_t)lv.w;
+            const float4 lr = a.LR[lf + q];
+            const unsigned long long vf = __float_as_uint(lr.x);
+            int m = (int)__float_as_uint(lr.y);
+            if (!chk(m <= LIGHT_MAX && vf + (unsigned long long)m <= a.vcap, MARS_CHECK_ARENA, ctr)) m = 0;
+            f3 v = mk3(0.f, 0.f, 0.f);
+            for (int k = 0; k < m; ++k) v = v + xyz(a.LC[vf + k]);
+            const uint32_t cc = (uint32_t)lr.w;
             Lr = Lr + mk3(v.x * ib, v.y * ib, v.z * ib);
             csub += cc;
             st[2][0] += 1.0f; st[2][1] += v.x; st[2][2] += v.y; st[2][3] += v.z;
@@ -1190,8 +1199,9 @@ cudaError_t launch_merge_lanes(DevCounters* dst, DevCounters* src, cudaStream_t 
 }
 
 int tile_launches(int max_depth, int techniques) {
+  // light connections: a light-subpath and a connection kernel per wave of depth <= D - 2
   return 2 + 2 * max_depth + max_depth + ((techniques & MARS_TECH_NEE) ? max_depth - 1 : 0) +
-         ((techniques & MARS_TECH_LIGHT) && max_depth > 2 ? max_depth - 2 : 0);
+         ((techniques & MARS_TECH_LIGHT) && max_depth > 2 ? 2 * (max_depth - 2) : 0);
 }
 
 }  // namespace mars
