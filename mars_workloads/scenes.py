@@ -426,7 +426,11 @@ def serving_requests(n: int = 256, rate: float = 20.0, seed: int = 0,
     ``resolutions`` (log-uniform over 64^2 .. 512^2), a room with a log-uniform
     number of spheres in ``spheres`` and 4 ceiling lights, and a uniform number
     of fixed-point iterations in ``iterations`` (at least warmup + 1).  Every
-    request carries its own scene seed and Philox key."""
+    request carries its own scene seed and Philox key.  The statistics grid is
+    as fine as the job's camera samples allow: about 64 of them per cell over
+    the job (N^3 cells, N = round((pixels x iterations / 64)^(1/3)) between 8
+    and 32) -- a 32^3 grid for a 128^2 job of 16 iterations would hold about
+    eight samples per cell, too few for any count to be learned."""
     rng = np.random.default_rng(seed)
     t = 0.0
     out = []
@@ -438,8 +442,10 @@ def serving_requests(n: int = 256, rate: float = 20.0, seed: int = 0,
         scene_seed = int(rng.integers(1, 2 ** 31))
         sc = guided_room_scene(scene_seed, res, res, n_spheres=ns)
         sc.name = f"room{ns}_{res}x{res}"
-        out.append({"arrival_s": t, "scene": sc, "iterations": max(iters, warmup + 1), "warmup": warmup,
-                    "seed": scene_seed & 0xFFFFFFFF, "key": k + 1, "grid_n": 32, "max_depth": 10,
+        iters = max(iters, warmup + 1)
+        grid_n = int(min(32, max(8, round((res * res * iters / 64.0) ** (1.0 / 3.0)))))
+        out.append({"arrival_s": t, "scene": sc, "iterations": iters, "warmup": warmup,
+                    "seed": scene_seed & 0xFFFFFFFF, "key": k + 1, "grid_n": grid_n, "max_depth": 10,
                     "techniques": TECH_BSDF | TECH_NEE | TECH_GUIDED})
     return out
 
