@@ -154,19 +154,21 @@ def kernel_sources_sha():
 
 
 def measured_traffic():
-    """Per-launch DRAM bytes of each wave kernel from the committed ncu summary,
-    if it was taken on the current kernel sources; else {}."""
+    """DRAM bytes per unit of work (ray slot; traced shadow ray for k_shadow) of
+    each wave kernel from the committed ncu summary, if it was taken on the
+    current kernel sources and build flags; else {}."""
     p = os.path.join(ROOT, TRAFFIC_FILE)
     if not os.path.exists(p):
         return {}
     vals, sha = {}, None
     for line in open(p):
         parts = line.split()
-        if len(parts) == 2 and not line.startswith("#"):
-            if parts[0] == "sources_sha256":
-                sha = parts[1]
-            else:
-                vals[parts[0]] = float(parts[1])
+        if line.startswith("#") or len(parts) < 2:
+            continue
+        if parts[0] == "sources_sha256":
+            sha = parts[1]
+        elif parts[0].startswith("k_"):
+            vals[parts[0]] = float(parts[1])
     return vals if sha == kernel_sources_sha() else {}
 
 
@@ -419,11 +421,17 @@ def run_mars(args):
     # time is not time the iteration waits for)
     dom = max(("k_trace", "k_shade", "k_reverse"), key=kms.get)
     d0 = per_kernel[dom]
-    traffic = measured_traffic().get(dom)
+    # DRAM bytes per launch: the measured bytes per unit x this run's units per launch
+    units = {"k_trace": sum(s["wave_entries"] for s in sts), "k_shade": sum(s["wave_entries"] for s in sts),
+             "k_reverse": sum(s["wave_entries"] for s in sts), "k_shadow": sum(s["shadow_traced"] for s in sts)}
+    per_unit = measured_traffic().get(dom)
+    traffic = per_unit * units[dom] / max(nlaunch[dom], 1) if per_unit is not None else None
     roofline = {"kernel": dom, "bound": d0["bound"], "achieved": d0["achieved"], "peak": d0["peak"],
                 "unit": d0["unit"], "frac": d0["frac"],
                 "traffic": int(traffic) if traffic is not None else None,
-                "traffic_note": "DRAM read + write bytes per launch from one ncu pass (cold L2), " + TRAFFIC_FILE,
+                "traffic_note": "DRAM read + write bytes per launch: bytes per unit from one ncu pass over every "
+                                "launch of one 256^2 iteration (cold L2), " + TRAFFIC_FILE + ", x this run's units "
+                                "per launch",
                 "overlapped": ["k_shadow"],
                 "peak_kind": peak_kind if d0["bound"] == "hbm" else
                 "derived: SMs x 128 FP32 lanes x 2 x max SM clock (measured)",
@@ -436,6 +444,8 @@ def run_mars(args):
     roofline["kernel_ms_per_step"]["image"] = round(sum(s["image_ms"] for s in sts) / args.steps, 4)
     roofline["wave_rays_per_step"] = [int(sum(s["wave_rays"][d] for s in sts) / args.steps)
                                       for d in range(cfg.max_depth)]
+    roofline["units_per_step"] = {"ray_slots": units["k_shade"] / args.steps,
+                                  "shadow_traced": units["k_shadow"] / args.steps}
     roofline["wave_ms_per_step"] = {k: [round(sum(s["wave_ms"][ki][d] for s in sts) / args.steps, 4)
                                         for d in range(cfg.max_depth)]
                                     for ki, k in enumerate(["k_trace", "k_shade", "k_shadow", "k_reverse"])}
