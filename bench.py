@@ -135,7 +135,7 @@ OPS_NODE, OPS_QUAD, OPS_SPHERE, OPS_TRI = 50, 67, 25, 45
 
 KERNEL_SOURCES = ["paper_2410_20429_gb300/csrc/render.cu", "paper_2410_20429_gb300/csrc/device.cuh",
                   "paper_2410_20429_gb300/csrc/internal.h", "paper_2410_20429_gb300/build.py"]
-TRAFFIC_FILE = "profiles/dram_traffic_guided_room_512.txt"
+TRAFFIC_FILE = "profiles/dram_traffic_wave_kernels_guided_room_256.txt"
 
 
 BVH_KINDS = {"sah": 0, "lbvh": 1}   # MARS_BVH_SAH, MARS_BVH_LBVH
