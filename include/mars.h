@@ -139,8 +139,10 @@ typedef struct {
  *   float64 atomics).
  * max_leaves, split_samples: octree only (0: 65536 leaves, 4096 samples).
  * arena_capacity: rays held by the per-iteration queue arena summed over all
- *   depths (0 = 3 x pixels x max_depth, at least 2^20).  An iteration whose path
- *   trees do not fit is rendered in pixel tiles (results do not depend on it). */
+ *   depths (0 = 3 x pixels x max_depth, at least 2^20); as many NEE shadow-ray
+ *   slots, and with light connections as many connection-sample and light-vertex
+ *   slots.  An iteration whose path trees do not fit is rendered in pixel tiles
+ *   (results do not depend on it). */
 #define MARS_CACHE_FP32_STATISTICS 1
 #define MARS_CACHE_OCTREE 2
 #define MARS_CACHE_NO_GRAPHS 4
@@ -240,7 +242,8 @@ typedef struct {
   uint32_t reserved;
   /* light connections (MARS_TECH_LIGHT): light-subpath closest-hit queries
      (included in `vertices`), connection shadow rays traced, light connection
-     samples drawn, and (profile = 1) the device time of their kernel */
+     samples drawn, and (profile = 1) the device time of their kernels (the
+     light-subpath and connection kernels of every wave) */
   uint64_t light_rays, connection_rays, light_samples;
   double light_ms;
 } mars_iter_stats;
