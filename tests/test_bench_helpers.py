@@ -114,3 +114,29 @@ def test_every_called_name_is_defined():
             defined.add(node.arg)
     called = {n.func.id for n in ast.walk(tree) if isinstance(n, ast.Call) and isinstance(n.func, ast.Name)}
     assert not called - defined, sorted(called - defined)
+
+
+def test_rel_mse_at_the_images_scale_is_scale_free():
+    """relMSE with eps = 1e-2 x the reference's squared mean does not change
+    when the image and the reference are scaled together (what the bench's
+    `ratio_scaled` relies on), while the fixed eps = 1e-2 does."""
+    rng = np.random.default_rng(2)
+    ref = rng.uniform(0.0, 0.05, size=(128 * 128, 3))
+    img = ref * (1.0 + 0.2 * rng.normal(size=ref.shape))
+    for k in (1.0, 37.0):
+        eps = 1e-2 * float((k * ref).mean()) ** 2
+        r = bench.rel_mse(k * img, k * ref, eps=eps)
+        if k == 1.0:
+            r1 = r
+    assert r == pytest.approx(r1, rel=1e-9)
+    assert bench.rel_mse(37.0 * img, 37.0 * ref) > 5 * bench.rel_mse(img, ref)
+
+
+def test_measured_traffic_is_per_unit_and_keyed_by_the_sources(tmp_path, monkeypatch):
+    """The committed traffic summary gives bytes per unit for every wave kernel,
+    and is ignored once the kernel sources or build flags hash differently."""
+    vals = bench.measured_traffic()
+    assert set(vals) == {"k_trace", "k_shade", "k_shadow", "k_reverse"}
+    assert all(10.0 < v < 1000.0 for v in vals.values())
+    monkeypatch.setattr(bench, "kernel_sources_sha", lambda: "0" * 64)
+    assert bench.measured_traffic() == {}
