@@ -1145,13 +1145,20 @@ def run_reference(args):
     per_step = min(sc.n_pixels, max(64, args.ref_pixels_per_step))
     chunk = max(64, per_step // cores)
     times, verts = [], []
-    # one spawned process per host core, started and warmed before the steps
+    learn = max(1, args.warmup)
+    # one spawned process per host core, started and warmed before the steps;
+    # the MARS state comes from the oracle itself: `learn` whole-image
+    # iterations with beta = 1 (the GPU arm's warm-up), untimed, as the GPU
+    # arm's timed MARS iterations start from the state of its own warm-up
     with cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn")) as pool:
         list(pool.map(_oracle_chunks, [(sc, cfg.grid_n, cfg.techniques, cfg.max_depth, [(0, 0, 64)], None)] * cores))
+        t0 = time.perf_counter()
+        state_path = oracle_learned_state(cfg, pool, cores, learn, learn)
+        learn_s = time.perf_counter() - t0
         for k in range(args.warmup + args.steps):
             b = (k * 7919 * 64) % max(1, sc.n_pixels - per_step + 1)
-            runs = [(k, b + q, min(b + per_step, b + q + chunk)) for q in range(0, per_step, chunk)]
-            jobs = [(sc, cfg.grid_n, cfg.techniques, cfg.max_depth, runs[w::cores], None) for w in range(cores)]
+            runs = [(learn + k, b + q, min(b + per_step, b + q + chunk)) for q in range(0, per_step, chunk)]
+            jobs = [(sc, cfg.grid_n, cfg.techniques, cfg.max_depth, runs[w::cores], state_path) for w in range(cores)]
             t0 = time.perf_counter()
             res = list(pool.map(_oracle_chunks, jobs))
             dt = time.perf_counter() - t0
@@ -1167,7 +1174,9 @@ def run_reference(args):
                        "grid": cfg.grid_n, "techniques": "bsdf+nee+guided"},
             "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{per_step} contiguous pixels per step of the {sc.width}x{sc.height} "
-                                       f"workload over {cores} processes, warm-up mode (beta = 1)",
+                                       f"workload over {cores} processes, MARS iterations from the oracle's own "
+                                       f"state after {learn} whole-image iterations with beta = 1 (learned in "
+                                       f"{learn_s:.1f} s, untimed)",
                              "cpu": _cpu_model()},
             "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
