@@ -505,9 +505,10 @@ __device__ __forceinline__ void vertex_budgets(const DevCache& c, const IterArgs
     const bool on = (on_mask >> t) & 1u;
     float b = on ? (t == 1 ? 1.0f : (t == 2 ? base2 : base_cont)) : 0.0f;
     if (on && it.mode == MARS_MODE_MARS) {
+      // both records in one round trip (the second is not worth a dependent load)
       const float4 qr = __ldg(c.cnt + (2 * (NT * cell + t)));
+      const float4 qs = __ldg(c.cnt + (2 * (NT * cell + t) + 1));
       if (qr.w > 0.0f) {
-        const float4 qs = __ldg(c.cnt + (2 * (NT * cell + t) + 1));
         const f3 ar = mul(f, xyz(qr)), as = mul(f, xyz(qs));
         // root mean square over the channels
         const float brr = sqrtf(dot(ar, ar) * (1.0f / 3.0f)), bs = sqrtf(dot(as, as) * (1.0f / 3.0f));
