@@ -136,6 +136,7 @@ OPS_NODE, OPS_QUAD, OPS_SPHERE, OPS_TRI = 50, 67, 25, 45
 KERNEL_SOURCES = ["paper_2410_20429_gb300/csrc/render.cu", "paper_2410_20429_gb300/csrc/device.cuh",
                   "paper_2410_20429_gb300/csrc/internal.h", "paper_2410_20429_gb300/build.py"]
 TRAFFIC_FILE = "profiles/dram_traffic_wave_kernels_guided_room_256.txt"
+SERVE_MULTIPLICITY = 16.0   # the server's path multiplicity cap for served jobs (csrc/server.cu)
 
 
 BVH_KINDS = {"sah": 0, "lbvh": 1}   # MARS_BVH_SAH, MARS_BVH_LBVH
@@ -733,8 +734,10 @@ def serving(args):
 def serving_efficiency(args, M, stream):
     """Equal-time efficiency of the served workload (config 4): the first
     request of each resolution of the serving stream, learned over its own
-    iterations (its warm-up, then MARS) as the server renders it, then the same
-    comparison with fixed-count MIS as for the main workload (512-spp reference)."""
+    iterations (its warm-up, then MARS) as the server renders it -- with the
+    server's path multiplicity cap -- then the same comparison with fixed-count
+    MIS as for the main workload (512-spp reference), MARS rendering with the
+    cap too."""
     import torch
     reqs = W.serving_requests(args.serve_requests, rate=args.serve_rate, seed=11)
     picked, seen = [], set()
@@ -752,9 +755,10 @@ def serving_efficiency(args, M, stream):
         for k in range(cfg.iterations):
             cache.render_iteration(img, seed=r["seed"], iteration=k,
                                    mode=M.MARS_MODE_WARMUP if k < cfg.warmup else M.MARS_MODE_MARS,
-                                   update_estimate=True, stream=stream)
+                                   update_estimate=True, max_multiplicity=SERVE_MULTIPLICITY, stream=stream)
             cache.update_counts(stream=stream)
-        e = efficiency(args, M, cfg, scene, cache, r["seed"], cfg.iterations, stream, ref_spp=512, unaware=False)
+        e = efficiency(args, M, cfg, scene, cache, r["seed"], cfg.iterations, stream, ref_spp=512, unaware=False,
+                       max_mult=SERVE_MULTIPLICITY)
         out.append({"scene": cfg.name, "iterations": cfg.iterations, "ratio": round(e["ratio"], 4),
                     "ratio_scaled": round(e["ratio_scaled"], 4),
                     "ratio_vs_own_guide": round(e["ratio_vs_own_guide"], 4),
@@ -764,7 +768,9 @@ def serving_efficiency(args, M, stream):
     geo = float(np.exp(np.mean([np.log(max(q["ratio"], 1e-30)) for q in out])))
     return {"requests": out, "ratio_geomean": round(geo, 4),
             "protocol": "the first request of each resolution of the serving stream; efficiency() after its own "
-                        "iterations; fixed-count MIS with the learned guide; 512-spp fixed-count reference"}
+                        "iterations, learned and rendered with the server's path multiplicity cap "
+                        f"({SERVE_MULTIPLICITY:g}); fixed-count MIS with the learned guide; 512-spp fixed-count "
+                        "reference"}
 
 
 def precision_study(cfg, cache, seed, it, stream):
@@ -784,7 +790,8 @@ def precision_study(cfg, cache, seed, it, stream):
     return out
 
 
-def efficiency(args, M, cfg, scene, cache, seed, it0, stream, ref_spp=None, cache_kw=None, unaware=True, vi_drop=0):
+def efficiency(args, M, cfg, scene, cache, seed, it0, stream, ref_spp=None, cache_kw=None, unaware=True, vi_drop=0,
+               max_mult=0.0):
     """Equal-time efficiency 1/(relMSE * s): MARS with the counts learned so far
     (frozen: no statistics, no update) vs fixed-count MIS (beta = 1), both
     timed with CUDA events, against a long fixed-count reference.  Like for
@@ -826,7 +833,8 @@ def efficiency(args, M, cfg, scene, cache, seed, it0, stream, ref_spp=None, cach
         rays = 0
         for k in range(n):
             st = c.render_iteration(img, seed=seed + 17, iteration=it_base + k, mode=mode, collect=False,
-                                    weights=weights, update_estimate=False, stream=stream)
+                                    weights=weights, update_estimate=False, max_multiplicity=max_mult,
+                                    stream=stream)
             rays += st["rays"]
             a += img.double()
         e1.record(stream)
