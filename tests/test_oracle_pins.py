@@ -981,3 +981,31 @@ def test_whole_path_weights_reduce_to_the_vertex_weights_without_light_connectio
     assert b.stats[:, 2, 0].sum() == 0 and a.rays == b.rays
     np.testing.assert_allclose(b.image, a.image, rtol=1e-12, atol=1e-15)
     np.testing.assert_allclose(b.stats[:, :2], a.stats[:, :2], rtol=1e-12, atol=1e-15)
+
+
+@pytest.mark.parametrize("D,counts", [(2, "beta1"), (2, "random"), (3, "beta1")])
+def test_guide_deposits_closed_form_in_the_furnace(orc, D, counts):
+    """Guide learning records, per continuation sample, the incident radiance
+    over the multi-sample density of the indirect techniques (real budgets):
+    sum_t beta_t E_t[L_i / (beta_B p_B + beta_G p_G)] = the integral of L_i over
+    the hemisphere, whatever the budgets.  In the closed furnace (radiance Le,
+    albedo a, uniform guide, no NEE) every camera vertex therefore deposits
+    2 pi Le in expectation when D = 2; when D = 3 it deposits 2 pi (1 + a) Le (the
+    incident radiance includes the next vertex's reflected estimate) and each
+    of its 0.75 children on average (the BSDF child, and the guided child when it
+    lands above the surface: half of the uniform guide) deposits 2 pi Le."""
+    a, le = 0.5, 1.5
+    sc = W.furnace_scene(albedo=a, radiance=le, width=16, height=16)
+    cells = 2 ** 3
+    cdf = np.tile((np.arange(1, orc.GUIDE_BINS + 1) / orc.GUIDE_BINS).astype(np.float32), (cells, 1))
+    q_rr, q_s, valid = W.random_count_fields(cells, seed=21, lo=0.2, hi=3.0)
+    est = W.random_pixel_estimate(sc.n_pixels, seed=22, lo=0.5, hi=4.0)
+    tot = []
+    for it in range(30):
+        kw = dict(grid_n=2, techniques=W.TECH_BSDF | W.TECH_GUIDED, max_depth=D, iteration=it, guide_cdf=cdf)
+        if counts == "random":
+            kw.update(mode=orc.MODE_MARS, q_rr=q_rr, q_s=q_s, valid=valid, est=est)
+        tot.append(orc.render(sc, **kw).hist.sum() / sc.n_pixels)
+    m, se = _mean_and_sem(tot)
+    expected = 2 * math.pi * le * (1.0 if D == 2 else (1 + a) + 0.75)
+    assert abs(m - expected) < 3.5 * se, (m, se, expected)
