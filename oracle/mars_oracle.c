@@ -21,6 +21,12 @@
  *     outlier and count clamping (Sec. 4.1 "Outlier clamping"), channel
  *     handling ("Handling colors").
  * Readings of passages the paper leaves open are stated where they are used.
+ *
+ * Parity unpinned: the Philox bit values (pinned statistically only; no
+ * published known-answer vectors are available here) and, in the whole-path
+ * weights of the bidirectional application, the light-side densities of the
+ * connection strategies (only their partition of unity, hence unbiasedness,
+ * is pinned).
  */
 #include "mars_oracle.h"
 
