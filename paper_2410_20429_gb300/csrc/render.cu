@@ -72,29 +72,13 @@ __device__ __forceinline__ Wave wave_of(const DevCounters* ctr, const Arena& a, 
   return {base, cnt < a.cap - base ? cnt : a.cap - base};
 }
 
-// Warp-aggregated allocation: inclusive warp scan of a per-lane count and one
-// atomicAdd per warp on *counter.  The warp's slots are contiguous, in lane
+// A warp's allocation from a shared counter: its slots are contiguous, in lane
 // order: lane l owns [base + incl - n, base + incl).
 struct WarpAlloc {
   unsigned long long base;  // first slot of the warp (relative to the counter's origin)
   int incl;                 // inclusive prefix of the counts up to this lane
   int total;                // slots of the whole warp
 };
-__device__ __forceinline__ WarpAlloc warp_alloc(int n, int lane, unsigned long long* counter) {
-  int incl = n;
-#pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    const int y = __shfl_up_sync(FULL, incl, off);
-    if (lane >= off) incl += y;
-  }
-  const int total = __shfl_sync(FULL, incl, 31);
-  unsigned long long wbase = 0;
-  if (total > 0) {
-    if (lane == 31) wbase = atomicAdd(counter, (unsigned long long)total);
-    wbase = __shfl_sync(FULL, wbase, 31);
-  }
-  return {wbase, incl, total};
-}
 
 // inclusive warp scan of a per-lane count; returns (inclusive prefix, warp total)
 __device__ __forceinline__ int2 warp_scan(int n, int lane) {
