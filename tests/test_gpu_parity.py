@@ -569,21 +569,28 @@ def test_checkpoint_resume_continues_the_run(mars, octree):
     assert _pixel_agreement(outs[1][1], outs[0][1]) >= 0.999
 
 
-def test_relmse_against_a_long_reference_matches_the_oracle(mars, orc):
+@pytest.mark.parametrize("which", ["box", "guided_room"])
+def test_relmse_against_a_long_reference_matches_the_oracle(mars, orc, which):
     """Third agreement criterion: the relMSE of the CUDA path's N-iteration
-    image and of the oracle's (same random numbers, same teacher-forced counts)
-    against a 65536-samples-per-pixel reference agree within 2 % of the
-    oracle's.  The reference is the oracle's own fixed-count render with other
-    random numbers, stored by tests/golden/make_box_reference.py."""
+    image and of the oracle's (same random numbers, same teacher-forced counts
+    and, for the guided room, guide) against a 65536-samples-per-pixel reference
+    agree within 2 % of the oracle's.  The references are the oracle's own
+    fixed-count renders at 32 x 32 with other random numbers, stored by
+    tests/golden/make_box_reference.py: the box, and the guided room's geometry
+    with all three techniques."""
     import os
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "box_32x32_fixed_65536spp.txt")
+    name = "box_32x32_fixed_65536spp.txt" if which == "box" else "guided_room_32x32_fixed_65536spp.txt"
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
     ref = np.loadtxt(path)[:, :3]
-    cfg = W.config_box(32, 32)
+    cfg = W.config_box(32, 32) if which == "box" else W.config_guided(32, 32)
     scene, cache = _make(mars, cfg)
     npx = cfg.scene.n_pixels
     q_rr, q_s, valid = W.random_count_fields(cfg.n_cells, seed=141, lo=0.1, hi=3.0)
     est = W.random_pixel_estimate(npx, seed=142, lo=0.05, hi=0.5)
-    cache.set_state(q_rr=q_rr, q_s=q_s, valid=valid, pixel_estimate=est, has_estimate=True, n_iterations=1)
+    cdf = W.random_guide_cdf(cfg.n_cells, seed=143) if cfg.techniques & W.TECH_GUIDED else None
+    extra = {} if cdf is None else {"guide_cdf": cdf}
+    cache.set_state(q_rr=q_rr, q_s=q_s, valid=valid, pixel_estimate=est, has_estimate=True, n_iterations=1,
+                    **extra)
     g_acc = np.zeros((npx, 3))
     o_acc = np.zeros((npx, 3))
     N = 16
@@ -591,7 +598,7 @@ def test_relmse_against_a_long_reference_matches_the_oracle(mars, orc):
         g, _ = _gpu_iteration(mars, cache, iteration=10 + k, seed=5, mode=1, collect=False)
         o = orc.render(cfg.scene, grid_n=cfg.grid_n, techniques=cfg.techniques, max_depth=cfg.max_depth,
                        iteration=10 + k, seed=5, mode=orc.MODE_MARS, q_rr=q_rr, q_s=q_s, valid=valid, est=est,
-                       collect=False)
+                       collect=False, guide_cdf=cdf)
         g_acc += g
         o_acc += o.image
 

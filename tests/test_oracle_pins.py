@@ -877,6 +877,33 @@ def test_long_box_reference_agrees_with_a_fresh_oracle_render(orc):
     assert np.all(np.abs(m.sum(0) - ref.sum(0)) < 4 * np.sqrt(var_d.sum(0)))
 
 
+def test_long_guided_room_reference_agrees_with_a_fresh_oracle_render(orc):
+    """The stored 65536-iteration reference of the guided room's geometry at 32 x
+    32 (tests/golden/make_box_reference.py --scene guided, written by the oracle
+    alone) agrees with a fresh 512-iteration oracle render under other random
+    numbers: the image mean within 4 sigma per channel, and most pixels within 2
+    sigma (their values are heavy-tailed -- small glossy lobes and lights -- so
+    the squared deviations do not average to one at this sample count)."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "guided_room_32x32_fixed_65536spp.txt")
+    a = np.loadtxt(path)
+    ref, ref_var = a[:, :3], a[:, 3:]
+    cfg = W.config_guided(32, 32)
+    cdf = np.tile((np.arange(1, orc.GUIDE_BINS + 1) / orc.GUIDE_BINS).astype(np.float32), (cfg.n_cells, 1))
+    n, n_ref = 512, 65536
+    s1 = np.zeros_like(ref)
+    for it in range(n):
+        r = orc.render(cfg.scene, grid_n=cfg.grid_n, techniques=cfg.techniques, max_depth=cfg.max_depth,
+                       mode=orc.MODE_FIXED, seed=4321, iteration=it, collect=False, guide_cdf=cdf)
+        s1 += r.image
+    m = s1 / n
+    var_d = ref_var * n_ref / n + ref_var
+    assert (var_d > 0).all()
+    assert np.all(np.abs(m.sum(0) - ref.sum(0)) < 4 * np.sqrt(var_d.sum(0)))
+    z = (m - ref) / np.sqrt(var_d)
+    assert (np.abs(z) < 2).mean() > 0.9
+
+
 # ----------------------------------------- bidirectional application (Sec. 5)
 TECH_BDPT = W.TECH_BSDF | W.TECH_NEE | 8   # BSDF, NEE, light connection
 
