@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(MAX_LIGHT_THREADS, MINB) k_light_path(const De
       u = rng.u4(px, DIM_LIGHT + 8u * (uint32_t)sidx + 1u, lin);
       const Frame fl = make_frame(nl);
       float sp, cp;
-      sincosf(TWO_PI_F * u.y, &sp, &cp);
+      sincospif(2.0f * u.y, &sp, &cp);   // sin, cos of 2 pi u.y (2 u.y is exact)
       const float r = sqrtf(u.x), zc = 1.0f - u.x;
       const f3 dir0 = fl.to_world(mk3(r * cp, r * sp, sqrtf(zc > 0.0f ? zc : 0.0f)));
       cos0 = dot(nl, dir0);

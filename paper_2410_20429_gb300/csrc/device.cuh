@@ -416,7 +416,7 @@ __device__ __forceinline__ bool bsdf_sample(const Mat& m, f3 wo, float u0, float
   if (m.type == 0) {
     const float r = sqrtf(u0);
     float sp, cp;
-    sincosf(TWO_PI_F * u1, &sp, &cp);
+    sincospif(2.0f * u1, &sp, &cp);   // sin, cos of 2 pi u1 (2 u1 is exact)
     const float z = 1.0f - u0;
     wi = mk3(r * cp, r * sp, sqrtf(z > 0.0f ? z : 0.0f));
     return wi.z > 0.0f;
@@ -426,7 +426,7 @@ __device__ __forceinline__ bool bsdf_sample(const Mat& m, f3 wo, float u0, float
   const float ct = 1.0f / sqrtf(1.0f + t2);
   const float st = sqrtf(t2) * ct;
   float sp, cp;
-  sincosf(TWO_PI_F * u1, &sp, &cp);
+  sincospif(2.0f * u1, &sp, &cp);   // sin, cos of 2 pi u1 (2 u1 is exact)
   const f3 h = mk3(st * cp, st * sp, ct);
   const float woh = dot(wo, h);
   if (woh <= 0.0f) return false;
@@ -475,11 +475,10 @@ __device__ __forceinline__ int guide_pick(const float* __restrict__ cdf, float u
 __device__ __forceinline__ f3 guide_dir(int b, float u1, float u2) {
   const int iz = b >> 4, ip = b & 15;
   const float z = -1.0f + 2.0f * ((float)iz + u1) / 16.0f;
-  const float phi = TWO_PI_F * ((float)ip + u2) / 16.0f;
   float s = (1.0f - z) * (1.0f + z);  // 1 - z^2 without cancellation near the poles
   s = sqrtf(s > 0.0f ? s : 0.0f);
   float sp, cp;
-  sincosf(phi, &sp, &cp);
+  sincospif(((float)ip + u2) * 0.125f, &sp, &cp);   // phi = 2 pi (ip + u2) / 16
   return mk3(s * cp, s * sp, z);
 }
 
