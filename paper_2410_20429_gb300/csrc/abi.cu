@@ -774,9 +774,12 @@ mars_status cache_create_impl(const mars_scene* s, const mars_cache_desc* d, cud
     c->dc.split_samples = d->split_samples > 0.0f ? d->split_samples : 4096.0f;
   }
   c->device_bytes = cache_footprint(cells, pixels, d->max_depth, d->techniques, cap);
+  const bool light = (d->techniques & MARS_TECH_LIGHT) != 0;
   if ((e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking)) != cudaSuccess)
     return cleanup(e, "side stream");
-  for (int k = 0; k <= d->max_depth; ++k) {
+  if (light && (e = cudaStreamCreateWithFlags(&c->side2, cudaStreamNonBlocking)) != cudaSuccess)
+    return cleanup(e, "side stream");
+  for (int k = 0; k <= d->max_depth + 1; ++k) {
     cudaEvent_t ev;
     if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return cleanup(e, "event");
     c->sync_events.push_back(ev);
@@ -789,11 +792,15 @@ mars_status cache_create_impl(const mars_scene* s, const mars_cache_desc* d, cud
     if ((e = cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking)) == cudaSuccess) c->lane_st.push_back(a);
     if (e == cudaSuccess && (e = cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking)) == cudaSuccess)
       c->lane_side.push_back(b);
+    if (e == cudaSuccess && light) {
+      cudaStream_t b2 = nullptr;
+      if ((e = cudaStreamCreateWithFlags(&b2, cudaStreamNonBlocking)) == cudaSuccess) c->lane_side2.push_back(b2);
+    }
     if (e == cudaSuccess && (e = cudaEventCreateWithFlags(&j, cudaEventDisableTiming)) == cudaSuccess)
       c->join_ev.push_back(j);
     if (e != cudaSuccess) return cleanup(e, "lane streams");
     c->lane_sync.emplace_back();
-    for (int k = 0; k <= d->max_depth; ++k) {
+    for (int k = 0; k <= d->max_depth + 1; ++k) {
       cudaEvent_t ev;
       if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return cleanup(e, "event");
       c->lane_sync.back().push_back(ev);
@@ -879,9 +886,10 @@ void cache_destroy_impl(mars_cache* c) {
     for (cudaEvent_t ev : v) cudaEventDestroy(ev);
   for (cudaEvent_t ev : c->join_ev) cudaEventDestroy(ev);
   if (c->fork_ev) cudaEventDestroy(c->fork_ev);
-  std::vector<cudaStream_t> qs{c->side};
+  std::vector<cudaStream_t> qs{c->side, c->side2};
   qs.insert(qs.end(), c->lane_st.begin(), c->lane_st.end());
   qs.insert(qs.end(), c->lane_side.begin(), c->lane_side.end());
+  qs.insert(qs.end(), c->lane_side2.begin(), c->lane_side2.end());
   for (cudaStream_t q : qs)
     if (q) {
       cudaStreamSynchronize(q);
@@ -1074,8 +1082,9 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
         const int l = (int)(t % (size_t)nl);
         cudaEvent_t* ev = profile ? c->events.data() + t * per_tile : nullptr;
         const bool own = concurrent && l >= 1;
+        cudaStream_t side2 = own ? (c->lane_side2.empty() ? nullptr : c->lane_side2[l - 1]) : c->side2;
         if ((r = launch_tile(s->ds, lane_cache(c, l), lane_arena(c, l, nl), c->d_args + t, c->launch,
-                             own ? c->lane_st[l - 1] : q, own ? c->lane_side[l - 1] : c->side,
+                             own ? c->lane_st[l - 1] : q, own ? c->lane_side[l - 1] : c->side, side2,
                              own ? c->lane_sync[l - 1].data() : c->sync_events.data(), ev)) != cudaSuccess)
           return r;
       }

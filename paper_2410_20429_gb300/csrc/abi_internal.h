@@ -137,7 +137,8 @@ struct mars_cache {
   std::vector<cudaEvent_t> events;  // profiling events, grown on demand
   cudaStream_t last_stream = nullptr;  // the stream of the last call that used the cache
   cudaStream_t side = nullptr;         // second stream: NEE shadow rays overlap the next waves
-  std::vector<cudaEvent_t> sync_events;  // D + 1 cross-stream events (no timing)
+  cudaStream_t side2 = nullptr;        // third stream: light connection kernels (light connections only)
+  std::vector<cudaEvent_t> sync_events;  // D + 2 cross-stream events (no timing)
   mars::WaveLaunch launch{};        // launch shape of the per-wave kernels
   int blocks_per_sm[mars::WAVE_KERNELS] = {0, 0, 0, 0};  // 0: occupancy maximum
   uint64_t last_entries = 0;  // arena slots the last iteration used (tile planning)
@@ -154,7 +155,7 @@ struct mars_cache {
   // lanes 1..lanes-1: rendering stream, shadow stream, D + 1 fork / join
   // events between them, and the event that joins the lane to the caller's
   // stream; fork_ev forks all of them from it
-  std::vector<cudaStream_t> lane_st, lane_side;
+  std::vector<cudaStream_t> lane_st, lane_side, lane_side2;
   std::vector<std::vector<cudaEvent_t>> lane_sync;
   std::vector<cudaEvent_t> join_ev;
   cudaEvent_t fork_ev = nullptr;

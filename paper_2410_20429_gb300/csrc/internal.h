@@ -261,9 +261,11 @@ int light_variants();
 
 // launch wrappers (render.cu)
 // it: device pointer to the tile's arguments
+// side2: the light connection kernels' stream (light connections only; null:
+// they run on side); sync: D + 2 events
 cudaError_t launch_tile(const DevScene& s, const DevCache& c, const Arena& a, const IterArgs* it,
-                        const WaveLaunch& L, cudaStream_t st, cudaStream_t side, const cudaEvent_t* sync,
-                        cudaEvent_t* ev);
+                        const WaveLaunch& L, cudaStream_t st, cudaStream_t side, cudaStream_t side2,
+                        const cudaEvent_t* sync, cudaEvent_t* ev);
 // adds a second tile lane's iteration totals into the first lane's counters
 cudaError_t launch_merge_lanes(DevCounters* dst, DevCounters* src, cudaStream_t st);
 // resident blocks per SM of each wave kernel at the given block sizes and variants

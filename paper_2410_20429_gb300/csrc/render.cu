@@ -1121,7 +1121,8 @@ cudaError_t wave_occupancy(const int threads[WAVE_KERNELS], const int variant[WA
 bool wave_threads_ok(int threads) { return threads >= 32 && threads <= MAX_WAVE_THREADS && threads % 32 == 0; }
 
 cudaError_t launch_tile(const DevScene& s, const DevCache& c, const Arena& a, const IterArgs* it, const WaveLaunch& L,
-                        cudaStream_t st, cudaStream_t side, const cudaEvent_t* sync, cudaEvent_t* ev) {
+                        cudaStream_t st, cudaStream_t side, cudaStream_t side2, const cudaEvent_t* sync,
+                        cudaEvent_t* ev) {
   k_tile_init<<<1, 32, 0, st>>>(c.ctr, it);
   const int D = c.max_depth;
   const int tT = L.threads[WK_TRACE], tS = L.threads[WK_SHADE], tH = L.threads[WK_SHADOW], tR = L.threads[WK_REVERSE];
@@ -1129,42 +1130,52 @@ cudaError_t launch_tile(const DevScene& s, const DevCache& c, const Arena& a, co
   const size_t smS = shade_smem(tS);
   const bool nee = (c.techniques & MARS_TECH_NEE) != 0;
   const bool bd = (c.techniques & MARS_TECH_LIGHT) != 0;
-  // The NEE shadow rays and the light connection samples of wave d run on the
-  // side stream, overlapped with the forward kernels of the next waves
+  // The NEE shadow rays of wave d run on the side stream and its light
+  // connection samples on a second one (side2, else the side stream too),
+  // overlapped with the forward kernels of the next waves and with each other
   // (disjoint data); the reverse pass, their only consumer, waits for all of
   // them.
-  // sync: D + 1 events without timing (after shade(d); after the last side
-  // kernel).  ev (optional, 7 D + 2 timing events): ev[0] start; ev[2(d-1)+1],
+  // sync: D + 2 events without timing (after shade(d); after the last shadow
+  // kernel; after the last light kernel).  ev (optional, 7 D + 2 timing
+  // events): ev[0] start; ev[2(d-1)+1],
   // ev[2(d-1)+2] after wave d's trace and shade; ev[2D + 2(d-1) + 1 .. 2] around
   // its shadow kernel on the side stream; ev[5D + 1] when the reverse pass may
   // start; ev[4D + k] after the k-th reverse kernel; ev[5D + 2 + 2(d-1) .. + 1]
   // around its light connection kernel on the side stream.
   if (ev) cudaEventRecord(ev[0], st);
-  bool any_side = false;
+  cudaStream_t lside = side2 ? side2 : side;
+  bool any_shadow = false, any_light = false;
   for (int d = 1; d <= D; ++d) {
     trace_fn(L.variant[WK_TRACE])<<<G(WK_TRACE, d), tT, 0, st>>>(s, c, a, it, d);
     if (ev) cudaEventRecord(ev[2 * (d - 1) + 1], st);
     shade_fn(L.variant[WK_SHADE], bd)<<<G(WK_SHADE, d), tS, smS, st>>>(s, c, a, it, d);
     if (ev) cudaEventRecord(ev[2 * (d - 1) + 2], st);
     const bool shadow = d <= D - 1 && nee, light = bd && d <= D - 2;
-    if (shadow || light) {
-      cudaEventRecord(sync[d - 1], st);
-      cudaStreamWaitEvent(side, sync[d - 1], 0);
-      any_side = true;
-    }
+    if (shadow || light) cudaEventRecord(sync[d - 1], st);
     if (shadow) {
+      cudaStreamWaitEvent(side, sync[d - 1], 0);
+      any_shadow = true;
       if (ev) cudaEventRecord(ev[2 * D + 2 * (d - 1) + 1], side);
       shadow_fn(L.variant[WK_SHADOW])<<<G(WK_SHADOW, d), tH, 0, side>>>(s, c, a, d);
       if (ev) cudaEventRecord(ev[2 * D + 2 * (d - 1) + 2], side);
     }
     if (light) {
-      if (ev) cudaEventRecord(ev[5 * D + 2 + 2 * (d - 1)], side);
-      cudaError_t e = launch_light(s, c, a, it, L.variant[WK_SHADOW], G(WK_SHADOW, d), tH, d, side);
+      if (lside != side || !shadow) cudaStreamWaitEvent(lside, sync[d - 1], 0);
+      any_light = true;
+      if (ev) cudaEventRecord(ev[5 * D + 2 + 2 * (d - 1)], lside);
+      cudaError_t e = launch_light(s, c, a, it, L.variant[WK_SHADOW], G(WK_SHADOW, d), tH, d, lside);
       if (e != cudaSuccess) return e;
-      if (ev) cudaEventRecord(ev[5 * D + 2 + 2 * (d - 1) + 1], side);
+      if (ev) cudaEventRecord(ev[5 * D + 2 + 2 * (d - 1) + 1], lside);
     }
   }
-  if (any_side) {
+  if (any_shadow) {
+    cudaEventRecord(sync[D], side);
+    cudaStreamWaitEvent(st, sync[D], 0);
+  }
+  if (any_light && lside != side) {
+    cudaEventRecord(sync[D + 1], lside);
+    cudaStreamWaitEvent(st, sync[D + 1], 0);
+  } else if (any_light && !any_shadow) {
     cudaEventRecord(sync[D], side);
     cudaStreamWaitEvent(st, sync[D], 0);
   }
