@@ -1,7 +1,8 @@
 """GPU test of the checked library (libmars_checked.so: the same sources with
 every kernel index check compiled in; compute-sanitizer is unavailable): over
 grid and octree caches, triangles, arena-overflow tiles, two tile lanes, the
-float32 statistics and the budget-unaware weights, no index check fails, and
+float32 statistics, the budget-unaware weights and light connections (with an
+octree, and with tiles split after an overflow), no index check fails, and
 each image agrees with the regular library's to float rounding."""
 import json
 import os
@@ -27,6 +28,9 @@ CASES = [
      {"mode": 1}),
     ("heightfield", "config_heightfield", (48, 40), {}, {"mode": 1}),
     ("guided_lanes", "config_guided", (384, 384), {}, {"mode": 1}),
+    ("bdpt_octree", "config_bdpt_heightfield", (48, 40), {"octree": True, "max_leaves": 40000,
+                                                          "split_samples": 16.0}, {"mode": 1}),
+    ("bdpt_overflow", "config_bdpt_heightfield", (48, 40), {"arena_capacity": 15000}, {"mode": 1}),
 ]
 # technique subsets and shallow depths: (name, techniques, max depth)
 SUBSETS = [("bsdf_d1", 1, 1), ("bsdf_d3", 1, 3), ("bsdf_guided_d3", 5, 3), ("bsdf_nee_d2", 3, 2)]
