@@ -673,7 +673,7 @@ def largest_scene(args, M, stream):
     GGX spheres, 8 area lights, 2048 x 2048, D = 12, 64 iterations, with the
     float32 versus float64 statistics comparison at this size."""
     n = args.large_size or 2048
-    return bidirectional_scene(args, M, stream, W.config_bdpt_large(n, n), 91, True)
+    return bidirectional_scene(args, M, stream, W.config_bdpt_large(n, n), 91, True, unaware=True)
 
 
 def serving(args):
