@@ -1101,7 +1101,7 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
       if (iev) cudaEventRecord(iev[0], q);
       if (p->update_estimate) {
         if ((r = launch_image_stats(c->dc, s->width, s->height, c->d_args, dev_out, p->vi_drop_brightest > 0,
-                                    p->combine != 0, q)) != cudaSuccess)
+                                    p->combine != 0, c->scene->num_sms, q)) != cudaSuccess)
           return r;
       } else if (dev_out && ranged) {
         if ((r = launch_image_copy_range(c->dc, (int)r0, (int)r1, dev_out, q)) != cudaSuccess) return r;

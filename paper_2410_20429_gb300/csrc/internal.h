@@ -140,6 +140,11 @@ struct Arena {
 constexpr uint32_t F_TRACED = 1u << 24;
 constexpr uint32_t F_EST = 1u << 25;
 
+// the image pass's block sums go to IMG_SLOTS addresses (block b adds to slot
+// b mod IMG_SLOTS) instead of one: same-address float64 atomics from every block
+// of the grid serialise
+constexpr int IMG_SLOTS = 32;
+
 // Device-resident per-iteration counters.
 struct DevCounters {
   unsigned long long base[MAXD + 2];
@@ -165,9 +170,12 @@ struct DevCounters {
   unsigned long long rays, vertices, est_vertices;
   unsigned long long entries;  // arena slots processed by committed tiles (all waves)
   double sum_beta[NT];
-  double chsum[3];             // sum over pixels of the running mean (image stats)
-  double vi_sum;
-  float chsum32[3], vi_sum32;  // the same sums in float32 (float32 statistics)
+  // image statistics: per slot, the sums over pixels of the running mean's
+  // channels (0..2) and of the pixels' squared relative errors (3)
+  double img_part[IMG_SLOTS][4];
+  float img_part32[IMG_SLOTS][4];  // the same sums in float32 (float32 statistics)
+  double vi_sum;                   // the V_I sum: the slots' total less the rejected pixels' terms
+  float vi_sum32;
   double VI, CI;               // results of the last image-stats pass
   int vi_dropped;              // pixels left out of the V_I mean
   unsigned int check_flags;    // MARS_CHECK_* bits of failed index checks (checked builds)
@@ -280,7 +288,7 @@ int tile_launches(int max_depth, int techniques);  // kernels launch_tile issues
 // combine); drop / combine: whether the brightest-pixel rejection and the
 // progressive combination kernels run
 cudaError_t launch_image_stats(const DevCache& c, int width, int height, const IterArgs* it,
-                               float* image_out_dev, bool drop, bool combine, cudaStream_t st);
+                               float* image_out_dev, bool drop, bool combine, int num_sms, cudaStream_t st);
 // the combined image divided by its weight sum, packed rgb, into out (device)
 cudaError_t launch_combined_out(const DevCache& c, int npix, float* out, cudaStream_t st);
 cudaError_t launch_image_copy(const DevCache& c, int npix, float* out, cudaStream_t st);

@@ -36,7 +36,6 @@ __device__ __forceinline__ T block_sum(T v, T* sh) {
   return r;  // valid in thread 0
 }
 
-// image sums in the statistics' precision: float64, or float32 for the
 // The RGB of a warp's 32 consecutive pixels [b, b + 32) -- lane l holds pixel
 // b + l -- written to a packed float RGB image as 24 aligned 16-byte stores of
 // the 384 bytes instead of 96 scattered 4-byte stores.  A page-locked host
@@ -63,6 +62,13 @@ __device__ __forceinline__ void store_rgb_warp(float* __restrict__ out, int b, i
   }
 }
 
+// sum of a float over the warp (every lane receives it)
+__device__ __forceinline__ float warp_sum(float v) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// image sums in the statistics' precision: float64, or float32 for the
 // float32-statistics variant
 template <typename T>
 __device__ __forceinline__ void add_sum(double* d64, float* d32, T v);
@@ -71,15 +77,18 @@ __device__ __forceinline__ void add_sum<double>(double* d64, float*, double v) {
 template <>
 __device__ __forceinline__ void add_sum<float>(double*, float* d32, float v) { atomicAdd(d32, v); }
 
+// The channel sums only set the estimate's floor: each warp sums its pixels in
+// float32, the block adds its warps' sums in T (a float64 operation per warp
+// instead of per pixel: float64 runs at 1/64 of the float32 rate here).
 template <typename T>
 __global__ void __launch_bounds__(IMG_THREADS) k_img_accum(DevCache c, int npix, const IterArgs* __restrict__ itp,
                                                             float* out) {
-  __shared__ T sh[IMG_THREADS / 32];
+  __shared__ T sh[3][IMG_THREADS / 32];
   __shared__ __align__(16) float stage[IMG_THREADS * 3];
   if (c.ctr->any_overflow) return;
   const int n_prev = itp->n_prev;
   const float inv = 1.0f / (float)(n_prev + 1);
-  T m0 = 0, m1 = 0, m2 = 0;
+  float m0 = 0.f, m1 = 0.f, m2 = 0.f;
   // warp-uniform trip count: the warp stores its pixels together
   for (int b = blockIdx.x * blockDim.x + (threadIdx.x & ~31); b < npix; b += gridDim.x * blockDim.x) {
     const int p = b + (threadIdx.x & 31);
@@ -89,33 +98,48 @@ __global__ void __launch_bounds__(IMG_THREADS) k_img_accum(DevCache c, int npix,
       float4 rs = c.run_sum[p];
       rs.x += I.x; rs.y += I.y; rs.z += I.z;
       c.run_sum[p] = rs;
-      m0 += (T)(rs.x * inv);
-      m1 += (T)(rs.y * inv);
-      m2 += (T)(rs.z * inv);
+      m0 += rs.x * inv;
+      m1 += rs.y * inv;
+      m2 += rs.z * inv;
     }
     if (out) store_rgb_warp(out, b, npix, I.x, I.y, I.z, stage + 96 * (threadIdx.x >> 5));
   }
-  m0 = block_sum<T>(m0, sh);
-  m1 = block_sum<T>(m1, sh);
-  m2 = block_sum<T>(m2, sh);
+  m0 = warp_sum(m0);
+  m1 = warp_sum(m1);
+  m2 = warp_sum(m2);
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    sh[0][w] = (T)m0;
+    sh[1][w] = (T)m1;
+    sh[2][w] = (T)m2;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    add_sum<T>(&c.ctr->chsum[0], &c.ctr->chsum32[0], m0);
-    add_sum<T>(&c.ctr->chsum[1], &c.ctr->chsum32[1], m1);
-    add_sum<T>(&c.ctr->chsum[2], &c.ctr->chsum32[2], m2);
+    T s0 = 0, s1 = 0, s2 = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      s0 += sh[0][k];
+      s1 += sh[1][k];
+      s2 += sh[2][k];
+    }
+    const int slot = blockIdx.x % IMG_SLOTS;
+    add_sum<T>(&c.ctr->img_part[slot][0], &c.ctr->img_part32[slot][0], s0);
+    add_sum<T>(&c.ctr->img_part[slot][1], &c.ctr->img_part32[slot][1], s1);
+    add_sum<T>(&c.ctr->img_part[slot][2], &c.ctr->img_part32[slot][2], s2);
   }
 }
 
-// Squared relative errors of one pixel's three channels, each cast to T before
-// the sum; with `clamp` the sample is first bounded at outlier x estimate.
-template <typename T>
-__device__ __forceinline__ T pixel_err(float4 I, float e0, float e1, float e2, float outlier, bool clamp) {
+// Sum of the squared relative errors of one pixel's three channels, in
+// float32 with every operation rounded on its own (no contraction), so that the
+// brightest-pixel rejection subtracts exactly the term that was added; with
+// `clamp` the sample is first bounded at outlier x estimate.
+__device__ __forceinline__ float pixel_err(float4 I, float e0, float e1, float e2, float outlier, bool clamp) {
   const float i0 = clamp ? fminf(I.x, outlier * e0) : I.x;
   const float i1 = clamp ? fminf(I.y, outlier * e1) : I.y;
   const float i2 = clamp ? fminf(I.z, outlier * e2) : I.z;
-  const float r0 = (i0 - e0) / e0;
-  const float r1 = (i1 - e1) / e1;
-  const float r2 = (i2 - e2) / e2;
-  return (T)(r0 * r0) + (T)(r1 * r1) + (T)(r2 * r2);
+  const float r0 = __fdiv_rn(__fsub_rn(i0, e0), e0);
+  const float r1 = __fdiv_rn(__fsub_rn(i1, e1), e1);
+  const float r2 = __fdiv_rn(__fsub_rn(i2, e2), e2);
+  return __fadd_rn(__fadd_rn(__fmul_rn(r0, r0), __fmul_rn(r1, r1)), __fmul_rn(r2, r2));
 }
 
 template <typename T>
@@ -128,9 +152,23 @@ __global__ void __launch_bounds__(IMG_THREADS) k_img_est(DevCache c, int W, int 
   const int npix = W * H;
   const float inv = 1.0f / (float)(n_prev + 1);
   const bool f32 = c.stats32 != nullptr;
-  const float fl0 = 1e-3f * (f32 ? c.ctr->chsum32[0] / (float)npix : (float)(c.ctr->chsum[0] / npix));
-  const float fl1 = 1e-3f * (f32 ? c.ctr->chsum32[1] / (float)npix : (float)(c.ctr->chsum[1] / npix));
-  const float fl2 = 1e-3f * (f32 ? c.ctr->chsum32[2] / (float)npix : (float)(c.ctr->chsum[2] / npix));
+  // the floor: 1e-3 x each channel's mean, its sum added over the slots in the
+  // statistics' precision by the first warp
+  __shared__ float fl_sh[3];
+  if (threadIdx.x < 32) {
+    static_assert(IMG_SLOTS == 32, "one slot per lane");
+    T ch[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      T v = f32 ? (T)c.ctr->img_part32[threadIdx.x][q] : (T)c.ctr->img_part[threadIdx.x][q];
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      ch[q] = v;
+    }
+    if (threadIdx.x == 0)
+      for (int q = 0; q < 3; ++q) fl_sh[q] = 1e-3f * (float)(ch[q] / (T)npix);
+  }
+  __syncthreads();
+  const float fl0 = fl_sh[0], fl1 = fl_sh[1], fl2 = fl_sh[2];
   T vi = 0;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) {
     const int x = p % W, y = p / W;
@@ -150,10 +188,11 @@ __global__ void __launch_bounds__(IMG_THREADS) k_img_est(DevCache c, int W, int 
     float e1 = fmaxf(fmaxf(s1 / (float)k, fl1), 1e-8f);
     float e2 = fmaxf(fmaxf(s2 / (float)k, fl2), 1e-8f);
     c.est[p] = make_float4(e0, e1, e2, 0.0f);
-    vi += pixel_err<T>(c.img[p], e0, e1, e2, outlier, clamp);
+    vi += (T)pixel_err(c.img[p], e0, e1, e2, outlier, clamp);
   }
   vi = block_sum<T>(vi, sh);
-  if (threadIdx.x == 0) add_sum<T>(&c.ctr->vi_sum, &c.ctr->vi_sum32, vi);
+  const int slot = blockIdx.x % IMG_SLOTS;
+  if (threadIdx.x == 0) add_sum<T>(&c.ctr->img_part[slot][3], &c.ctr->img_part32[slot][3], vi);
 }
 
 __global__ void __launch_bounds__(IMG_THREADS) k_img_copy(DevCache c, int npix, float* out) {
@@ -189,44 +228,70 @@ __device__ __forceinline__ unsigned long long bright_key(float4 I, int p) {
   return ((unsigned long long)__float_as_uint(l) << 32) | (unsigned long long)(0xffffffffu - (unsigned)p);
 }
 
-// keeps L (descending, zero-filled) as the K largest keys seen
-__device__ __forceinline__ void topk_insert(unsigned long long (&L)[MAX_DROP], int K, unsigned long long x) {
+// The K largest keys seen: L descending and zero-filled (entries from K on stay
+// 0), kth = L[K - 1], so that a key that cannot enter is rejected by one
+// comparison.
+struct TopK {
+  unsigned long long L[MAX_DROP];
+  unsigned long long kth;
+};
+
+__device__ __forceinline__ void topk_clear(TopK& t) {
 #pragma unroll
-  for (int q = 0; q < MAX_DROP; ++q)
-    if (q < K && x > L[q]) {
-      const unsigned long long t = L[q];
-      L[q] = x;
-      x = t;
+  for (int q = 0; q < MAX_DROP; ++q) t.L[q] = 0;
+  t.kth = 0;
+}
+
+__device__ __forceinline__ void topk_insert(TopK& t, int K, unsigned long long x) {
+  if (x <= t.kth) return;
+  unsigned long long kth = 0;
+#pragma unroll
+  for (int q = 0; q < MAX_DROP; ++q) {
+    if (q < K && x > t.L[q]) {
+      const unsigned long long v = t.L[q];
+      t.L[q] = x;
+      x = v;
     }
+    if (q == K - 1) kth = t.L[q];
+  }
+  t.kth = kth;
+}
+
+// largest of a key over the warp (every lane receives it)
+__device__ __forceinline__ unsigned long long warp_max_key(unsigned long long v) {
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(0xffffffffu, v, off);
+    v = o > v ? o : v;
+  }
+  return v;
 }
 
 // K rounds of "largest head of all threads' lists": the owner pops it; out[r]
-// (thread 0) receives the r-th largest key of the block (0 if none)
-__device__ __forceinline__ void topk_block(unsigned long long (&L)[MAX_DROP], int K, unsigned long long* out,
-                                           unsigned long long* sh, unsigned long long* best) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+// (thread 0) receives the r-th largest key of the block (0 if none).  sh holds
+// one key per warp (at most 32 warps).
+__device__ __forceinline__ void topk_block(TopK& t, int K, unsigned long long* out, unsigned long long* sh,
+                                           unsigned long long* best) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
   for (int r = 0; r < K; ++r) {
-    unsigned long long v = L[0];
-    for (int off = 16; off > 0; off >>= 1) {
-      const unsigned long long o = __shfl_xor_sync(0xffffffffu, v, off);
-      v = o > v ? o : v;
-    }
+    const unsigned long long v = warp_max_key(t.L[0]);
     if (lane == 0) sh[w] = v;
     __syncthreads();
-    if (threadIdx.x == 0) {
-      unsigned long long m = 0;
-      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) m = sh[k] > m ? sh[k] : m;
-      *best = m;
-      out[r] = m;
+    if (w == 0) {
+      const unsigned long long m = warp_max_key(lane < nw ? sh[lane] : 0ull);
+      if (lane == 0) {
+        *best = m;
+        out[r] = m;
+      }
     }
+    // sh is rewritten, and *best written, only after the next round's first
+    // barrier, which every thread reaches after reading *best here
     __syncthreads();
     const unsigned long long m = *best;
-    if (m != 0 && L[0] == m) {
+    if (m != 0 && t.L[0] == m) {
 #pragma unroll
-      for (int q = 0; q < MAX_DROP - 1; ++q) L[q] = L[q + 1];
-      L[MAX_DROP - 1] = 0;
+      for (int q = 0; q < MAX_DROP - 1; ++q) t.L[q] = t.L[q + 1];
+      t.L[MAX_DROP - 1] = 0;
     }
-    __syncthreads();
   }
 }
 
@@ -238,11 +303,10 @@ __global__ void __launch_bounds__(IMG_THREADS) k_img_topk(DevCache c, int npix, 
   if (K <= 0) return;
   const int per = (npix + (int)gridDim.x - 1) / (int)gridDim.x;
   const int lo = (int)blockIdx.x * per, hi = min(npix, lo + per);
-  unsigned long long L[MAX_DROP];
-#pragma unroll
-  for (int q = 0; q < MAX_DROP; ++q) L[q] = 0;
-  for (int p = lo + threadIdx.x; p < hi; p += blockDim.x) topk_insert(L, K, bright_key(c.img[p], p));
-  topk_block(L, K, c.topk + (size_t)blockIdx.x * K, sh, &best);
+  TopK t;
+  topk_clear(t);
+  for (int p = lo + threadIdx.x; p < hi; p += blockDim.x) topk_insert(t, K, bright_key(c.img[p], p));
+  topk_block(t, K, c.topk + (size_t)blockIdx.x * K, sh, &best);
 }
 
 // one block: the K brightest of all candidates leave the V_I sum (their terms,
@@ -253,12 +317,11 @@ __global__ void __launch_bounds__(1024) k_img_drop(DevCache c, int nblocks, cons
   if (c.ctr->any_overflow) return;
   const int K = itp->drop_k;
   if (K <= 0) return;
-  unsigned long long L[MAX_DROP];
-#pragma unroll
-  for (int q = 0; q < MAX_DROP; ++q) L[q] = 0;
+  TopK t;
+  topk_clear(t);
   const int ncand = nblocks * K;  // k_img_topk wrote K keys per block
-  for (int i = threadIdx.x; i < ncand; i += blockDim.x) topk_insert(L, K, c.topk[i]);
-  topk_block(L, K, sel, sh, &best);
+  for (int i = threadIdx.x; i < ncand; i += blockDim.x) topk_insert(t, K, c.topk[i]);
+  topk_block(t, K, sel, sh, &best);
   if (threadIdx.x == 0) {
     T sum = 0;
     int n = 0;
@@ -266,7 +329,7 @@ __global__ void __launch_bounds__(1024) k_img_drop(DevCache c, int nblocks, cons
       if (sel[r] == 0) continue;
       const int p = (int)(0xffffffffu - (unsigned)(sel[r] & 0xffffffffull));
       const float4 e = c.est[p];
-      sum += pixel_err<T>(c.img[p], e.x, e.y, e.z, 0.0f, false);
+      sum += (T)pixel_err(c.img[p], e.x, e.y, e.z, 0.0f, false);
       ++n;
     }
     if (c.stats32) c.ctr->vi_sum32 -= (float)sum; else c.ctr->vi_sum -= (double)sum;
@@ -302,8 +365,18 @@ __global__ void __launch_bounds__(IMG_THREADS) k_img_comb_out(DevCache c, int np
   }
 }
 
+// one warp: V_I and C_I from the slots' sums (and the rejection's subtraction)
 __global__ void k_img_final(DevCache c, int npix) {
-  if (threadIdx.x != 0 || c.ctr->any_overflow) return;
+  if (c.ctr->any_overflow) return;
+  double v64 = c.ctr->img_part[threadIdx.x][3];
+  float v32 = c.ctr->img_part32[threadIdx.x][3];
+  for (int off = 16; off > 0; off >>= 1) {
+    v64 += __shfl_xor_sync(0xffffffffu, v64, off);
+    v32 += __shfl_xor_sync(0xffffffffu, v32, off);
+  }
+  if (threadIdx.x != 0) return;
+  c.ctr->vi_sum += v64;
+  c.ctr->vi_sum32 += v32;
   const int kept = npix - c.ctr->vi_dropped;  // V_I: the mean over the pixels that were kept
   if (c.stats32) {
     c.ctr->VI = (double)(c.ctr->vi_sum32 / (3.0f * (float)kept));
@@ -545,10 +618,13 @@ cudaError_t launch_octree_refine(const DevCache& c, int num_sms, cudaStream_t st
 }
 
 cudaError_t launch_image_stats(const DevCache& c, int width, int height, const IterArgs* it,
-                               float* image_out_dev, bool drop, bool combine, cudaStream_t st) {
+                               float* image_out_dev, bool drop, bool combine, int num_sms, cudaStream_t st) {
   const int npix = width * height;
   int blocks = (npix + IMG_THREADS - 1) / IMG_THREADS;
-  if (blocks > 4096) blocks = 4096;
+  // four blocks per SM, grid-stride beyond: fewer blocks, fewer float64 atomics
+  // (measured: 1024^2 image pass 0.19 -> 0.10 ms against one block per 256 pixels)
+  const int cap = 4 * std::max(num_sms, 1);
+  if (blocks > cap) blocks = cap;
   const int tblocks = std::min(blocks, IMG_TOPK_BLOCKS);
   if (c.stats32) {
     k_img_accum<float><<<blocks, IMG_THREADS, 0, st>>>(c, npix, it, image_out_dev);
@@ -566,7 +642,7 @@ cudaError_t launch_image_stats(const DevCache& c, int width, int height, const I
     else
       k_img_drop<double><<<1, 1024, 0, st>>>(c, tblocks, it);
   }
-  k_img_final<<<1, 32, 0, st>>>(c, npix);
+  k_img_final<<<1, IMG_SLOTS, 0, st>>>(c, npix);
   if (combine) k_img_combine<<<blocks, IMG_THREADS, 0, st>>>(c, npix, it);
   return cudaGetLastError();
 }
