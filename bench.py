@@ -266,7 +266,7 @@ def restore_state(cache, snap, iteration, stream):
     cache.set_state(q_rr=snap["q_rr"], q_s=snap["q_s"], valid=snap["valid"], stats=snap["stats"],
                     guide_hist=snap["guide_hist"], guide_cdf=snap["guide_cdf"], pixel_estimate=snap["pixel_estimate"],
                     run_sum=snap["run_sum"], n_iterations=snap["n_iterations"], has_estimate=snap["has_estimate"],
-                    VI=snap["VI"], CI=snap["CI"], stream=stream, **extra)
+                    VI=snap["VI"], CI=snap["CI"], image_iterations=snap["image_iterations"], stream=stream, **extra)
     return iteration
 
 
@@ -538,7 +538,13 @@ def run_mars(args):
     if rank == 0 and not args.no_precision:
         line["precision"] = precision_study(cfg, cache, seed, it, stream)
     if rank == 0 and not args.no_efficiency:
-        line["efficiency"] = efficiency(args, M, cfg, scene, cache, seed, it, stream)
+        # the comparison's MARS arm learns as a job does: as many renders as the
+        # bench cache saw, with the count update closing each training iteration
+        eff_cache = M.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, arena_capacity=args.arena_capacity,
+                            lanes=args.lanes, stream=stream)
+        learn(M, eff_cache, img, seed, it, args.warmup, stream)
+        line["efficiency"] = efficiency(args, M, cfg, scene, eff_cache, seed, it, stream)
+        del eff_cache
         line["efficiency_box"] = box_efficiency(args, M, stream)
         # the same after 16 learning iterations: the counts of 3 one-sample MARS
         # iterations on a 64 x 64 image are still noisy
@@ -561,8 +567,9 @@ def bidirectional_scene(args, M, stream, cfg, seed, precision_study_too, unaware
     64k leaves) and the application's image-level rules (Sec. 5.1: V_I without
     the 10 brightest pixels, iterations combined with weights 1 / V_I):
     hierarchy build time, the workload's warm-up iterations, then its MARS
-    iterations timed (the whole job: `cfg.iterations` in all), then 3 with
-    every launch timed, the equal-time efficiency against fixed-count MIS on the
+    iterations timed (the whole job: `cfg.iterations` renders in all, the count
+    update closing each training iteration of the library's schedule), then 3
+    more renders with every launch timed, the equal-time efficiency against fixed-count MIS on the
     same GPU, and optionally the float32 versus float64 statistics comparison
     at this size."""
     import torch
@@ -593,7 +600,8 @@ def bidirectional_scene(args, M, stream, cfg, seed, precision_study_too, unaware
     for k in range(timed_iters):
         sts.append(cache.render_iteration(img, seed=seed, iteration=it, mode=M.MARS_MODE_MARS, update_estimate=True,
                                           vi_drop_brightest=10, combine=2 if k == 0 else 1, stream=stream))
-        cache.update_counts(stream=stream)
+        if M.training_step_ends(it, cfg.warmup, cfg.iterations):
+            cache.update_counts(stream=stream)
         it += 1
         if k + 1 < timed_iters:
             evs[k + 1].record(stream)
@@ -604,12 +612,12 @@ def bidirectional_scene(args, M, stream, cfg, seed, precision_study_too, unaware
     ms = e0.elapsed_time(e1) / timed_iters
     verts = sum(s["vertices"] for s in sts) / timed_iters
     timed = sts
-    # kernel times: 3 iterations more, every launch between events
+    # kernel times: 3 renders more with the job's final counts (no update), every
+    # launch between events
     sts = []
     for k in range(3):
         sts.append(cache.render_iteration(img, seed=seed, iteration=it, mode=M.MARS_MODE_MARS, update_estimate=True,
                                           profile=True, vi_drop_brightest=10, combine=1, stream=stream))
-        cache.update_counts(stream=stream)
         it += 1
     tw = [sum(s["trace_work"][0][q] for s in sts) for q in range(4)]
     n = max(sum(s["wave_entries"] for s in sts), 1)
@@ -618,6 +626,7 @@ def bidirectional_scene(args, M, stream, cfg, seed, precision_study_too, unaware
            "techniques": "bsdf+nee+light_connection", "bvh_build_s": round(build_s, 3), "ms_per_step": round(ms, 3),
            "mvertices_s": round(verts / (ms * 1e-3) / 1e6, 1), "vertices_per_step": int(verts),
            "timed_iterations": timed_iters, "warmup_iterations": cfg.warmup,
+           "training_schedule": M.training_schedule(cfg.iterations, cfg.warmup),
            "ms_per_step_first_last": [round(sts_ms[0], 3), round(sts_ms[-1], 3)],
            "vertices_note": "closest-hit queries of camera paths and light subpaths",
            "light_subpath_rays_per_step": int(sum(s["light_rays"] for s in timed) / timed_iters),
@@ -636,7 +645,8 @@ def bidirectional_scene(args, M, stream, cfg, seed, precision_study_too, unaware
                            "combined_weight": round(cache.combined_image(stream=stream)[1], 4),
                            "VI": [round(s["VI"], 5) for s in timed + sts]}}
     if not args.no_efficiency:
-        out["efficiency"] = efficiency(args, M, cfg, scene, cache, seed, it, stream, ref_spp=args.large_ref_spp,
+        out["efficiency"] = efficiency(args, M, cfg, scene, cache, seed, cfg.iterations, stream,
+                                       ref_spp=args.large_ref_spp,
                                        cache_kw=kw, unaware=unaware, vi_drop=10)
     if precision_study_too and not args.no_precision:
         # float32 versus float64 statistics at this size (the large bidirectional
@@ -752,11 +762,7 @@ def serving_efficiency(args, M, stream):
         scene = M.Scene(cfg.scene, stream=stream)
         cache = M.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, stream=stream)
         img = torch.zeros(cfg.scene.n_pixels * 3, dtype=torch.float32, device="cuda")
-        for k in range(cfg.iterations):
-            cache.render_iteration(img, seed=r["seed"], iteration=k,
-                                   mode=M.MARS_MODE_WARMUP if k < cfg.warmup else M.MARS_MODE_MARS,
-                                   update_estimate=True, max_multiplicity=SERVE_MULTIPLICITY, stream=stream)
-            cache.update_counts(stream=stream)
+        learn(M, cache, img, r["seed"], cfg.iterations, cfg.warmup, stream, max_mult=SERVE_MULTIPLICITY)
         e = efficiency(args, M, cfg, scene, cache, r["seed"], cfg.iterations, stream, ref_spp=512, unaware=False,
                        max_mult=SERVE_MULTIPLICITY)
         out.append({"scene": cfg.name, "iterations": cfg.iterations, "ratio": round(e["ratio"], 4),
@@ -790,6 +796,23 @@ def precision_study(cfg, cache, seed, it, stream):
     return out
 
 
+def learn(M, cache, img, seed, n, warmup, stream, mode=None, weights=None, drop=0, max_mult=0.0, combine=False):
+    """A job of n one-sample renders on `cache` (the first `warmup` of them
+    warm-up renders, or all in `mode`), with the count update closing each
+    training iteration of the library's schedule (1, 2, 4, ... renders after the
+    warm-up ones; Sec. 4.1 "Fixed-point iteration", Sec. 5.1)."""
+    weights = M.MARS_WEIGHTS_AWARE if weights is None else weights
+    sts = []
+    for k in range(n):
+        m = mode if mode is not None else (M.MARS_MODE_WARMUP if k < warmup else M.MARS_MODE_MARS)
+        sts.append(cache.render_iteration(img, seed=seed, iteration=k, mode=m, weights=weights, update_estimate=True,
+                                          vi_drop_brightest=drop, max_multiplicity=max_mult,
+                                          combine=(2 if k == 0 else 1) if combine else 0, stream=stream))
+        if M.training_step_ends(k, warmup, n):
+            cache.update_counts(stream=stream)
+    return sts
+
+
 def efficiency(args, M, cfg, scene, cache, seed, it0, stream, ref_spp=None, cache_kw=None, unaware=True, vi_drop=0,
                max_mult=0.0):
     """Equal-time efficiency 1/(relMSE * s): MARS with the counts learned so far
@@ -799,7 +822,9 @@ def efficiency(args, M, cfg, scene, cache, seed, it0, stream, ref_spp=None, cach
     cache's learned guide (same cells: an octree cache's tree is copied too),
     so the two arms differ in their counts alone; the guided workloads also
     report fixed-count MIS with a guide it learned itself over as many
-    iterations, and with the uniform guide of a fresh cache."""
+    iterations, and with the uniform guide of a fresh cache.  Every arm that
+    learns follows the library's training schedule, and every arm renders with
+    the launch shape the library's autotuner picks for its own iterations."""
     import torch
     npx = cfg.scene.n_pixels
     n_ref = ref_spp or args.ref_spp
@@ -849,7 +874,13 @@ def efficiency(args, M, cfg, scene, cache, seed, it0, stream, ref_spp=None, cach
                 "relmse_scaled": rs, "efficiency_scaled": 1.0 / (rs * s),
                 "rays_per_pixel": rays / n / npx, "spp": n}
 
+    def tune(c, mode, weights=M.MARS_WEIGHTS_AWARE):
+        # renders without statistics: the learned state is unchanged
+        c.autotune(seed=seed + 17, iteration=20000, mode=mode, weights=weights, repeats=1,
+                   max_multiplicity=max_mult, stream=stream)
+
     guided = bool(cfg.techniques & W.TECH_GUIDED)
+    tune(cache, M.MARS_MODE_MARS)
     mars = timed(cache, M.MARS_MODE_MARS, args.eff_spp, 20000)
     learned = cache.get_state(stream=stream)
     fixed_cache = M.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, stream=stream, **cache_kw)
@@ -857,13 +888,17 @@ def efficiency(args, M, cfg, scene, cache, seed, it0, stream, ref_spp=None, cach
         tree = {"oct_nodes": learned["oct_nodes"], "oct_leaf_level": learned["oct_leaf_level"]} \
             if "oct_nodes" in learned else {}
         fixed_cache.set_state(guide_cdf=learned["guide_cdf"], stream=stream, **tree)
+    tune(fixed_cache, M.MARS_MODE_FIXED)
     fixed = timed(fixed_cache, M.MARS_MODE_FIXED, args.eff_spp, 20000)
     del fixed_cache
     out = {"mars": mars, "fixed_count_mis": fixed, "ratio": mars["efficiency"] / fixed["efficiency"],
            "ratio_scaled": mars["efficiency_scaled"] / fixed["efficiency_scaled"],
            "reference_mean": ref_mean, "eps_scaled": eps_scaled,
            "reference_spp": n_ref, "learning_iterations": it0,
-           "protocol": "counts learned over the warm-up and timed iterations, then frozen; both arms render "
+           "training_schedule": M.training_schedule(it0, cfg.warmup),
+           "protocol": f"counts learned over {it0} one-sample renders in training iterations of the library's "
+                       "schedule (training_schedule: renders per iteration, one update after each), then frozen; "
+                       "every arm autotuned for its own iterations; both arms render "
                        f"{args.eff_spp} fresh iterations with the same learned guide (fixed-count MIS: beta = 1); "
                        f"reference = fixed-count MIS, {n_ref} spp, other random numbers; relMSE with the variance "
                        "of the reference's mean subtracted (relmse_raw without); ratio_scaled: the same with "
@@ -872,13 +907,12 @@ def efficiency(args, M, cfg, scene, cache, seed, it0, stream, ref_spp=None, cach
         # fixed-count MIS that learns its own guide from its own deposits over as
         # many iterations, and with the uniform guide of a fresh cache
         own = M.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, stream=stream, **cache_kw)
-        for k in range(it0):
-            own.render_iteration(img, seed=seed, iteration=k, mode=M.MARS_MODE_FIXED, update_estimate=True,
-                                 vi_drop_brightest=vi_drop, stream=stream)
-            own.update_counts(stream=stream)
+        learn(M, own, img, seed, it0, cfg.warmup, stream, mode=M.MARS_MODE_FIXED, drop=vi_drop, max_mult=max_mult)
+        tune(own, M.MARS_MODE_FIXED)
         f_own = timed(own, M.MARS_MODE_FIXED, args.eff_spp, 20000)
         del own
         uni = M.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, stream=stream, **cache_kw)
+        tune(uni, M.MARS_MODE_FIXED)
         f_uni = timed(uni, M.MARS_MODE_FIXED, args.eff_spp, 20000)
         del uni
         out["fixed_count_mis_own_guide"] = f_own
@@ -889,11 +923,9 @@ def efficiency(args, M, cfg, scene, cache, seed, it0, stream, ref_spp=None, cach
         # the budget-unaware balance heuristic (weights from the sampling densities
         # alone) learns its own counts over as many iterations, then renders alike
         un_cache = M.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, stream=stream, **cache_kw)
-        for k in range(it0):
-            un_cache.render_iteration(img, seed=seed, iteration=k, mode=M.MARS_MODE_WARMUP if k < args.warmup
-                                      else M.MARS_MODE_MARS, weights=M.MARS_WEIGHTS_UNAWARE, update_estimate=True,
-                                      vi_drop_brightest=vi_drop, stream=stream)
-            un_cache.update_counts(stream=stream)
+        learn(M, un_cache, img, seed, it0, cfg.warmup, stream, weights=M.MARS_WEIGHTS_UNAWARE, drop=vi_drop,
+              max_mult=max_mult)
+        tune(un_cache, M.MARS_MODE_MARS, M.MARS_WEIGHTS_UNAWARE)
         un = timed(un_cache, M.MARS_MODE_MARS, args.eff_spp, 20000, weights=M.MARS_WEIGHTS_UNAWARE)
         del un_cache
         un["learning_iterations"] = it0
@@ -904,8 +936,8 @@ def efficiency(args, M, cfg, scene, cache, seed, it0, stream, ref_spp=None, cach
 
 def box_efficiency(args, M, stream, iterations=None):
     """The box workload (64 x 64, D = 5, BSDF + NEE, 8^3 grid; the paper's own
-    failure case, where MARS's overhead can dominate): 1 warm-up and 3 MARS
-    fixed-point iterations learn the counts, then the same equal-time comparison
+    failure case, where MARS's overhead can dominate): 1 warm-up render and
+    training iterations of 1 and 2 renders learn the counts, then the same equal-time comparison
     with fixed-count MIS as for the main workload, plus the device time of one
     MARS iteration (launch-bound at this size)."""
     import torch
@@ -914,12 +946,8 @@ def box_efficiency(args, M, stream, iterations=None):
     scene = M.Scene(cfg.scene, stream=stream)
     cache = M.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth, stream=stream)
     img = torch.zeros(cfg.scene.n_pixels * 3, dtype=torch.float32, device="cuda")
-    it = 0
-    for k in range(n_iter):
-        mode = M.MARS_MODE_WARMUP if k < cfg.warmup else M.MARS_MODE_MARS
-        cache.render_iteration(img, seed=2024, iteration=it, mode=mode, update_estimate=True, stream=stream)
-        cache.update_counts(stream=stream)
-        it += 1
+    learn(M, cache, img, 2024, n_iter, cfg.warmup, stream)
+    it = n_iter
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)

@@ -288,12 +288,16 @@ typedef struct {
   float* run_sum;
   int32_t n_iterations;   /* iterations summed in run_sum */
   int32_t has_estimate;   /* pixel_estimate is meaningful */
-  double VI, CI;          /* inputs of the next mars_update_counts */
+  double VI, CI;          /* inputs of the next mars_update_counts: the means over the
+                             image_iterations iterations rendered with update_estimate
+                             since the last update (0 when there were none) */
   int32_t* oct_nodes;
   int32_t* oct_leaf_level;
   int32_t oct_n_nodes, oct_n_leaves;
   float* pixel_rays;      /* get_state only: [pixels] rays of each pixel's path tree in the last
                              rendered iteration (its camera ray and every sample drawn below it) */
+  int32_t image_iterations; /* iterations averaged into VI and CI; set_state takes 0 as one
+                               when VI or CI is non-zero */
 } mars_cache_state;
 
 typedef struct {
@@ -350,13 +354,32 @@ mars_status mars_render_iteration(mars_cache* cache, const mars_iter_params* par
                                   mars_iter_stats* stats_host, void* stream);
 
 /* ---- fixed-point update (Sec. 3.1 "Optimization"; App. A.3) -----------------
- * One step per (cell, technique): q^RR and q^S per channel from the collected
- * statistics and the V_I, C_I of the last mars_render_iteration with
- * update_estimate; keeps the previous factors where n < 2 or the cost is 0, and
- * everything when V_I <= 1e-12.  Rebuilds the guided technique's per-cell CDF
+ * Closes one training iteration: every mars_render_iteration since the last
+ * update (one or several samples per pixel; the paper's training iterations
+ * grow in duration, Sec. 4.1 "Fixed-point iteration" and Sec. 5.1) added its
+ * statistics, and each one with update_estimate its V_I and C_I.  One step per
+ * (cell, technique): q^RR and q^S per channel from the collected statistics and
+ * the means of those V_I and C_I (the paper's V_I averages the squared relative
+ * errors over every sample of the iteration, Sec. 4.1 "Image estimates");
+ * keeps the previous factors where n < 2 or the cost is 0, and everything when
+ * V_I <= 1e-12 (no image statistics ran).  Rebuilds the guided technique's per-cell CDF
  * from the accumulated deposits (P_b = 0.9 h_b / H + 0.1 / 256).  Zeroes the
  * statistics.  Asynchronous on `stream`.  Errors: CUDA. */
 mars_status mars_update_counts(mars_cache* cache, void* stream);
+
+/* ---- training schedule (Sec. 4.1 "Fixed-point iteration"; Sec. 5.1) ---------
+ * The paper's training iterations grow in duration (the guided application
+ * follows the guiding scheme it builds on, whose iterations double; the
+ * bidirectional one renders "short iterations that grow in duration").  A job
+ * of `iterations` one-sample renders whose first `warmup` are warm-up renders
+ * is split into training iterations: each warm-up render is one, then 1, 2, 4,
+ * ... renders, the last one taking what is left; an iteration after which
+ * fewer renders than its own would remain takes them too (no short last
+ * iteration replaces counts learned from a long one).  Returns 1 when render
+ * `iteration` (0-based) closes a training iteration, i.e. mars_update_counts
+ * follows it, else 0 (also for iteration < 0, iteration >= iterations or
+ * warmup < 0).  Host only; no device work. */
+int32_t mars_training_step_ends(int32_t iteration, int32_t warmup, int32_t iterations);
 
 /* ---- testing hook (host only; the paper has no counterpart) -------------
  * Exercises the error paths without faulting a GPU.  kind MARS_INJECT_ALLOC:
@@ -434,8 +457,9 @@ typedef struct {
   const mars_scene_desc* scene;
   mars_cache_desc cache;
   uint32_t seed;           /* Philox key of the job: (seed, key) */
-  int32_t iterations;      /* fixed-point iterations of the job */
-  int32_t warmup;          /* leading iterations with beta = 1 */
+  int32_t iterations;      /* one-sample renders of the job; the count update follows
+                              the renders that mars_training_step_ends names */
+  int32_t warmup;          /* leading renders with beta = 1 */
   uint32_t key;            /* second Philox key word; a job's random numbers depend
                               on (seed, key) only, never on the server's job id */
   double timeout_s;        /* wall-clock limit counted from the job's start (0: none):

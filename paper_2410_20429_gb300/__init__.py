@@ -33,4 +33,12 @@ from ._abi import (  # noqa: F401
     MarsError,
     load,
 )
-from .renderer import Cache, Scene, Server, inject_failure, scene_desc  # noqa: F401
+from .renderer import (  # noqa: F401
+    Cache,
+    Scene,
+    Server,
+    inject_failure,
+    scene_desc,
+    training_schedule,
+    training_step_ends,
+)

@@ -87,7 +87,7 @@ class mars_cache_state(ct.Structure):
         ("VI", ct.c_double), ("CI", ct.c_double),
         ("oct_nodes", ct.POINTER(ct.c_int32)), ("oct_leaf_level", ct.POINTER(ct.c_int32)),
         ("oct_n_nodes", ct.c_int32), ("oct_n_leaves", ct.c_int32),
-        ("pixel_rays", ct.POINTER(ct.c_float)),
+        ("pixel_rays", ct.POINTER(ct.c_float)), ("image_iterations", ct.c_int32),
     ]
 
 
@@ -146,6 +146,7 @@ SIGNATURES = {
                                  _VP], ct.c_int),
     "mars_last_error_string": ([], ct.c_char_p),
     "mars_version": ([], ct.c_char_p),
+    "mars_training_step_ends": ([ct.c_int32, ct.c_int32, ct.c_int32], ct.c_int32),
 }
 
 _lib = None

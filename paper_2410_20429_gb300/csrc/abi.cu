@@ -668,11 +668,13 @@ mars_status cache_create_impl(const mars_scene* s, const mars_cache_desc* d, cud
   if (!c->h_args) return cleanup(cudaErrorMemoryAllocation, "pinned alloc");
   if ((e = dev_alloc((void**)&c->d_comb, sizeof(float4) * pixels, st)) != cudaSuccess ||
       (e = dev_alloc((void**)&c->d_comb_w, sizeof(double), st)) != cudaSuccess ||
+      (e = dev_alloc((void**)&c->d_img_acc, 3 * sizeof(double), st)) != cudaSuccess ||
       (e = dev_alloc((void**)&c->d_topk, sizeof(unsigned long long) * IMG_TOPK_BLOCKS * MAX_DROP, st)) !=
           cudaSuccess)
     return cleanup(e, "image alloc");
   cudaMemsetAsync(c->d_comb, 0, sizeof(float4) * pixels, st);
   cudaMemsetAsync(c->d_comb_w, 0, sizeof(double), st);
+  cudaMemsetAsync(c->d_img_acc, 0, 3 * sizeof(double), st);
   c->use_graphs = (d->flags & MARS_CACHE_NO_GRAPHS) == 0;
   cudaMemsetAsync(c->d_cnt, 0, sizeof(float4) * 2 * NT * cells, st);
   if (c->d_stats) cudaMemsetAsync(c->d_stats, 0, sizeof(double) * NSTAT * NT * cells, st);
@@ -712,6 +714,7 @@ mars_status cache_create_impl(const mars_scene* s, const mars_cache_desc* d, cud
   c->dc.tile_status = c->d_tile_status;
   c->dc.comb = c->d_comb;
   c->dc.comb_w = c->d_comb_w;
+  c->dc.img_acc = c->d_img_acc;
   c->dc.topk = c->d_topk;
   if (octree) {
     // the initial tree equals the grid: levels 0..L0 complete, breadth first,
@@ -872,7 +875,7 @@ void cache_destroy_impl(mars_cache* c) {
   dev_free(c->arena.LC, st);
   void* ptrs[] = {c->d_cnt, c->d_stats, c->d_stats32, c->d_hist, c->d_cdf, c->d_guide_dirty, c->d_est, c->d_run,
                   c->d_img, c->d_ctr, c->d_tile_status, c->d_oct_nodes, c->d_oct_level, c->d_oct_lnode,
-                  c->d_oct_meta, c->d_oct_split, c->d_oct_leaf_n, c->d_comb, c->d_comb_w, c->d_topk};
+                  c->d_oct_meta, c->d_oct_split, c->d_oct_leaf_n, c->d_comb, c->d_comb_w, c->d_img_acc, c->d_topk};
   for (void* p : ptrs) dev_free(p, st);
   pinned_release(c->h_ctr, sizeof(DevCounters));
   pinned_release(c->h_tile_status, sizeof(unsigned int) * c->max_tiles);
@@ -1293,8 +1296,6 @@ mars_status render_iteration_impl(mars_cache* c, const mars_iter_params* p, floa
     out->light_samples = h.light_entries;
     out->light_ms = light_ms;
   }
-  c->last_VI = c->h_ctr->VI;
-  c->last_CI = c->h_ctr->CI;
   return MARS_OK;
 }
 
@@ -1310,6 +1311,9 @@ mars_status update_counts_impl(mars_cache* c, cudaStream_t st) {
   if ((e = launch_update(c->dc, c->scene->num_sms, st)) != cudaSuccess) return poison(c, e, "update launch");
   if (c->dc.oct_nodes && (e = launch_octree_refine(c->dc, c->scene->num_sms, st)) != cudaSuccess)
     return poison(c, e, "octree refine launch");
+  // the next training iteration averages its own V_I and C_I
+  if ((e = cudaMemsetAsync(c->d_img_acc, 0, 3 * sizeof(double), st)) != cudaSuccess)
+    return poison(c, e, "image statistics reset");
   return MARS_OK;
 }
 
@@ -1393,8 +1397,13 @@ mars_status get_state_impl(mars_cache* c, mars_cache_state* s, cudaStream_t st) 
   }
   s->n_iterations = c->n_iterations;
   s->has_estimate = c->has_estimate ? 1 : 0;
-  s->VI = c->last_VI;
-  s->CI = c->last_CI;
+  double acc[3] = {0.0, 0.0, 0.0};
+  if ((e = cudaMemcpyAsync(acc, c->d_img_acc, sizeof(acc), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(st)) != cudaSuccess)
+    return poison(c, e, "state copy");
+  s->image_iterations = (int32_t)acc[2];
+  s->VI = acc[2] > 0.0 ? acc[0] / acc[2] : 0.0;
+  s->CI = acc[2] > 0.0 ? acc[1] / acc[2] : 0.0;
   return MARS_OK;
 }
 
@@ -1496,15 +1505,15 @@ mars_status set_state_impl(mars_cache* c, const mars_cache_state* s, cudaStream_
       (e = cudaMemcpy2DAsync(c->d_run, sizeof(float4), s->run_sum, 3 * sizeof(float), 3 * sizeof(float), (size_t)px,
                              cudaMemcpyHostToDevice, st)) != cudaSuccess)
     return poison(c, e, "state copy");
-  // V_I and C_I feed the next update
-  if ((e = cudaMemcpyAsync(&c->d_ctr->VI, &s->VI, sizeof(double), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(&c->d_ctr->CI, &s->CI, sizeof(double), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+  // V_I and C_I feed the next update: the means of image_iterations iterations
+  // (one when it is 0 and either is set)
+  const int32_t ni = s->image_iterations > 0 ? s->image_iterations : (s->VI != 0.0 || s->CI != 0.0 ? 1 : 0);
+  const double acc[3] = {s->VI * ni, s->CI * ni, (double)ni};
+  if ((e = cudaMemcpyAsync(c->d_img_acc, acc, sizeof(acc), cudaMemcpyHostToDevice, st)) != cudaSuccess)
     return poison(c, e, "state copy");
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return poison(c, e, "state copy");
   c->n_iterations = s->n_iterations;
   c->has_estimate = s->has_estimate != 0;
-  c->last_VI = s->VI;
-  c->last_CI = s->CI;
   return MARS_OK;
 }
 
@@ -1777,5 +1786,16 @@ mars_status mars_cache_autotune(mars_cache* c, const mars_iter_params* params, i
 const char* mars_last_error_string(void) { return g_last_error.c_str(); }
 
 const char* mars_version(void) { return "mars-gb300 0.1 (sm_103a)"; }
+
+int32_t mars_training_step_ends(int32_t iteration, int32_t warmup, int32_t iterations) {
+  if (iteration < 0 || iteration >= iterations || warmup < 0) return 0;
+  if (iteration < warmup || iteration == iterations - 1) return 1;
+  // after warm-up: training iterations of 1, 2, 4, ... renders end where the
+  // renders so far, k + 1, are 2^m - 1, unless fewer renders than the ending
+  // iteration's 2^(m-1) would remain (they join it)
+  const int64_t k2 = (int64_t)(iteration - warmup) + 2;
+  const int64_t left = (int64_t)iterations - 1 - iteration;
+  return (k2 & (k2 - 1)) == 0 && left >= k2 / 2 ? 1 : 0;
+}
 
 }  // extern "C"

@@ -132,7 +132,6 @@ struct mars_cache {
   int n_iterations = 0;
   bool has_estimate = false;
   bool poisoned = false;
-  double last_VI = 0.0, last_CI = 0.0;
   uint64_t device_bytes = 0;
   std::vector<cudaEvent_t> events;  // profiling events, grown on demand
   cudaStream_t last_stream = nullptr;  // the stream of the last call that used the cache
@@ -166,6 +165,7 @@ struct mars_cache {
   float* d_host_stage = nullptr;  // packed rgb image for image_on_host (first use)
   float4* d_comb = nullptr;       // inverse-variance weighted image sum
   double* d_comb_w = nullptr;     // its weight sum
+  double* d_img_acc = nullptr;    // V_I and C_I sums since the last update, and their count
   unsigned long long* d_topk = nullptr;  // brightest-pixel candidates
   // the recorded single-tile iteration graph (MARS_CACHE_NO_GRAPHS: none)
   bool use_graphs = true;

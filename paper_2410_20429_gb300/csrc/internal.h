@@ -228,6 +228,9 @@ struct DevCache {
   float split_samples;
   float4* comb;                 // [pixels] inverse-variance weighted image sum
   double* comb_w;               // its weight sum
+  // [3] sums of V_I and C_I over the iterations whose image statistics ran since
+  // the last update, and their count: the update takes the means
+  double* img_acc;
   unsigned long long* topk;     // [IMG_TOPK_BLOCKS * MAX_DROP] brightness candidates
 };
 constexpr int MAX_DROP = MARS_MAX_DROP_BRIGHTEST;

@@ -5,7 +5,9 @@
 // is free.  Every admitted job gets a worker thread with its own CUDA stream,
 // so the iterations of resident jobs overlap on the device; a job's scene,
 // cache, queues and image stay resident on the device across its fixed-point
-// iterations and are freed when it finishes, which admits the next job.
+// iterations and are freed when it finishes, which admits the next job.  A job
+// of n renders follows the training schedule of mars_training_step_ends: one
+// update after each warm-up render, then after 1, 2, 4, ... renders.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -115,7 +117,10 @@ struct mars_server {
       const auto a = Clock::now();
       mars_iter_stats ist{};
       rc = mars::render_iteration_impl(ca, &p, nullptr, &ist, st);
-      if (rc == MARS_OK) rc = mars::update_counts_impl(ca, st);
+      // the fixed-point step closes each training iteration (1, 2, 4, ...
+      // renders after the warm-up ones)
+      if (rc == MARS_OK && mars_training_step_ends(it, j->warmup, j->iterations))
+        rc = mars::update_counts_impl(ca, st);
       if (rc == MARS_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = MARS_ERR_CUDA;
       const double ms = std::chrono::duration<double, std::milli>(Clock::now() - a).count();
       if (rc != MARS_OK) break;

@@ -365,6 +365,16 @@ __global__ void __launch_bounds__(IMG_THREADS) k_img_comb_out(DevCache c, int np
   }
 }
 
+// V_I and C_I of the training iteration the update closes: the means over its
+// iterations (Sec. 4.1 "Image estimates" averages the squared relative errors
+// over every sample of the iteration); 0 when no image statistics ran, which
+// keeps every factor
+__device__ __forceinline__ void image_means(const DevCache& c, double& VI, double& CI) {
+  const double n = c.img_acc[2];
+  VI = n > 0.0 ? c.img_acc[0] / n : 0.0;
+  CI = n > 0.0 ? c.img_acc[1] / n : 0.0;
+}
+
 // one warp: V_I and C_I from the slots' sums (and the rejection's subtraction)
 __global__ void k_img_final(DevCache c, int npix) {
   if (c.ctr->any_overflow) return;
@@ -385,6 +395,10 @@ __global__ void k_img_final(DevCache c, int npix) {
     c.ctr->VI = c.ctr->vi_sum / (3.0 * (double)kept);
     c.ctr->CI = (double)c.ctr->rays / (double)npix;
   }
+  // a training iteration of several such iterations: the update averages them
+  c.img_acc[0] += c.ctr->VI;
+  c.img_acc[1] += c.ctr->CI;
+  c.img_acc[2] += 1.0;
 }
 
 __global__ void k_update_counts(DevCache c) {
@@ -400,7 +414,8 @@ __global__ void k_update_counts(DevCache c) {
   double v[NSTAT];
 #pragma unroll
   for (int k = 1; k < NSTAT; ++k) v[k] = sp[k * plane];
-  const double VI = c.ctr->VI, CI = c.ctr->CI;
+  double VI, CI;
+  image_means(c, VI, CI);
   const double cost = v[7];
   if (slot_on(c.techniques, t) && VI > 1e-12 && n >= 2.0 && cost > 0.0) {
     // C_I / C_t / V_I with C_t = cost / n, and 1 / n, formed once in float64
@@ -432,7 +447,9 @@ __global__ void k_update_counts32(DevCache c) {
   const float4 a = s4[0];
   if (a.x == 0.0f) return;
   const float4 b = s4[1];
-  const float VI = (float)c.ctr->VI, CI = (float)c.ctr->CI;
+  double VI64, CI64;
+  image_means(c, VI64, CI64);
+  const float VI = (float)VI64, CI = (float)CI64;
   const float n = a.x, cost = b.w;
   if (slot_on(c.techniques, t) && VI > 1e-12f && n >= 2.0f && cost > 0.0f) {
     const float inv_n = 1.0f / n;

@@ -217,7 +217,8 @@ class Cache:
             s.oct_nodes, s.oct_leaf_level = _dp(nodes, ct.c_int32), _dp(levels, ct.c_int32)
         A.check(self._lib.mars_cache_get_state(self.handle, ct.byref(s), _stream_handle(stream)),
                 "mars_cache_get_state")
-        out.update(n_iterations=s.n_iterations, has_estimate=bool(s.has_estimate), VI=s.VI, CI=s.CI)
+        out.update(n_iterations=s.n_iterations, has_estimate=bool(s.has_estimate), VI=s.VI, CI=s.CI,
+                   image_iterations=s.image_iterations)
         if self.octree:
             out.update(oct_nodes=nodes[:s.oct_n_nodes].copy(), oct_leaf_level=levels[:s.oct_n_leaves].copy(),
                        oct_n_nodes=s.oct_n_nodes, oct_n_leaves=s.oct_n_leaves)
@@ -225,7 +226,7 @@ class Cache:
 
     def set_state(self, *, q_rr=None, q_s=None, valid=None, stats=None, guide_hist=None, guide_cdf=None,
                   pixel_estimate=None, run_sum=None, n_iterations=0, has_estimate=False, VI=0.0, CI=0.0,
-                  oct_nodes=None, oct_leaf_level=None, stream=None) -> None:
+                  image_iterations=0, oct_nodes=None, oct_leaf_level=None, stream=None) -> None:
         c, px = self.n_cells, self.n_pixels
         keep = []
 
@@ -247,6 +248,7 @@ class Cache:
         s.run_sum = arr(run_sum, np.float32, (px, 3), ct.c_float)
         s.n_iterations, s.has_estimate = int(n_iterations), int(bool(has_estimate))
         s.VI, s.CI = float(VI), float(CI)
+        s.image_iterations = int(image_iterations)
         if oct_nodes is not None:
             on = np.ascontiguousarray(oct_nodes, np.int32)
             ol = np.ascontiguousarray(oct_leaf_level, np.int32)
@@ -328,6 +330,25 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def training_step_ends(iteration: int, warmup: int, iterations: int) -> bool:
+    """Whether render `iteration` of a job of `iterations` one-sample renders
+    (the first `warmup` warm-up renders) closes a training iteration, so that
+    update_counts follows it (mars_training_step_ends in mars.h)."""
+    return bool(A.load().mars_training_step_ends(int(iteration), int(warmup), int(iterations)))
+
+
+def training_schedule(iterations: int, warmup: int) -> list:
+    """Renders per training iteration of such a job, e.g. 3 warm-up renders and
+    32 in all: [1, 1, 1, 1, 2, 4, 8, 14]; 35 in all: [1, 1, 1, 1, 2, 4, 8, 17]."""
+    out, n = [], 0
+    for k in range(iterations):
+        n += 1
+        if training_step_ends(k, warmup, iterations):
+            out.append(n)
+            n = 0
+    return out
 
 
 def inject_failure(kind: int, n: int) -> None:

@@ -301,6 +301,42 @@ def test_update_and_guide_parity(mars, orc):
     np.testing.assert_allclose(g["guide_cdf"], cdf, atol=2e-7)
 
 
+def test_training_iteration_update_takes_the_mean_image_statistics(mars, orc):
+    """A training iteration of three renders (Sec. 4.1 "Fixed-point iteration":
+    the iterations grow in duration): the statistics of all three accumulate,
+    the state reports the mean of their V_I and C_I over three image
+    iterations, and the update equals the oracle's update of the accumulated
+    statistics with those means; the next training iteration starts afresh."""
+    cfg = W.config_box(32, 24)
+    scene, cache = _make(mars, cfg)
+    sts = [_gpu_iteration(mars, cache, iteration=k, seed=5, mode=0, update_estimate=True)[1] for k in range(3)]
+    g = cache.get_state()
+    vi = np.mean([s["VI"] for s in sts])
+    ci = np.mean([s["CI"] for s in sts])
+    assert g["image_iterations"] == 3
+    assert g["VI"] == pytest.approx(vi, rel=1e-12) and g["CI"] == pytest.approx(ci, rel=1e-12)
+    assert g["stats"][..., 0].sum() > 0
+    cache.update_counts()
+    u = cache.get_state()
+    q_rr, q_s, valid = orc.update_counts(g["stats"], g["VI"], g["CI"], cfg.techniques, g["q_rr"], g["q_s"],
+                                         g["valid"])
+    assert np.array_equal(u["valid"], valid)
+    np.testing.assert_allclose(u["q_rr"], q_rr, rtol=1e-6)
+    np.testing.assert_allclose(u["q_s"], q_s, rtol=1e-6, atol=1e-30)
+    assert u["image_iterations"] == 0 and u["VI"] == 0.0 and u["CI"] == 0.0
+    # a checkpoint in the middle of a training iteration resumes it exactly
+    st = _gpu_iteration(mars, cache, iteration=3, seed=5, mode=1, update_estimate=True)[1]
+    _gpu_iteration(mars, cache, iteration=4, seed=5, mode=1, update_estimate=True)
+    s = cache.get_state()
+    assert s["image_iterations"] == 2
+    other = mars.Cache(scene, cfg.grid_n, cfg.techniques, cfg.max_depth)
+    other.set_state(VI=st["VI"], CI=st["CI"], image_iterations=1)
+    assert other.get_state()["image_iterations"] == 1
+    other.set_state(VI=s["VI"], CI=s["CI"], image_iterations=2)
+    o = other.get_state()
+    assert o["image_iterations"] == 2 and o["VI"] == pytest.approx(s["VI"], rel=1e-15)
+
+
 def test_image_statistics_parity(mars, orc):
     """Running mean, pixel estimate and V_I after one rendered iteration, from a
     seeded running sum; the oracle uses its own image of the same iteration."""
