@@ -22,11 +22,10 @@
  *     handling ("Handling colors").
  * Readings of passages the paper leaves open are stated where they are used.
  *
- * Parity unpinned: the Philox bit values (pinned statistically only; no
- * published known-answer vectors are available here) and, in the whole-path
- * weights of the bidirectional application, the light-side densities of the
- * connection strategies (only their partition of unity, hence unbiasedness,
- * is pinned).
+ * The Philox bits are pinned by the generator's published known-answer
+ * vectors.  Parity unpinned: in the whole-path weights of the bidirectional
+ * application, the light-side densities of the connection strategies (only
+ * their partition of unity, hence unbiasedness, is pinned).
  */
 #include "mars_oracle.h"
 
