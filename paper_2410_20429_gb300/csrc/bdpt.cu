@@ -143,6 +143,11 @@ __global__ void __launch_bounds__(MAX_LIGHT_THREADS, MINB) k_light_path(const De
       f3 alpha = xyz(l4) * (PI_F / pN);
       f3 org = y0 + nl * s.eps, dir = dir0;
       float pdens = cos0 * INV_PI_F;   // solid-angle density of the next vertex's direction
+      // the loops stay rolled: unrolled, the compiler keeps every vertex of y in
+      // registers (235 per thread, 8 warps per SM); rolled, y lives in the
+      // thread's local frame (L1) and the kernel takes 112 (config 3 at 1024^2:
+      // light kernels 3.27 -> 2.74 ms alone, iteration 7.7 -> 6.7 ms)
+#pragma unroll 1
       for (int kk = 1; kk <= kmax; ++kk) {
         ++rays;
         float t = 0.0f;
@@ -201,6 +206,7 @@ __global__ void __launch_bounds__(MAX_LIGHT_THREADS, MINB) k_light_path(const De
       // reverse BSDF towards the previous vertex with the next one as the
       // outgoing direction (the last vertex's depends on the connection), and
       // the cosine at the previous vertex towards it
+#pragma unroll 1
       for (int kk = 1; kk <= m; ++kk) {
         const LightVertex& v = y[kk - 1];
         int cell = c.oct_nodes ? octree_cell(s, c.oct_nodes, v.p) : cell_of(s, c.grid_n, v.p);
