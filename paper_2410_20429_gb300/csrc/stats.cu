@@ -428,8 +428,11 @@ __global__ void k_update_counts(DevCache c) {
       const double m1 = s1[ch] * inv_n, m2 = s2v[ch] * inv_n;
       double var = m2 - m1 * m1;
       if (var < 0.0) var = 0.0;
-      qr[ch] = (float)sqrt(r * m2);
-      qs[ch] = (float)sqrt(r * var);
+      // square roots in float32 of the float64 products (the factors are stored
+      // in float32; a float64 square root costs tens of operations at 1/64 of
+      // the float32 rate on this part): within 1e-7 of the float64 root
+      qr[ch] = sqrtf((float)(r * m2));
+      qs[ch] = sqrtf((float)(r * var));
     }
     c.cnt[2 * idx] = make_float4(qr[0], qr[1], qr[2], 1.0f);
     c.cnt[2 * idx + 1] = make_float4(qs[0], qs[1], qs[2], 0.0f);
@@ -471,11 +474,62 @@ __global__ void k_update_counts32(DevCache c) {
   s4[1] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
+// ---- float-float arithmetic: a value held as an unevaluated sum hi + lo of two
+// floats, about 48 significant bits, from float32 operations only (float64 runs
+// at 1/64 of the float32 rate on this part).  TwoSum (Knuth), FastTwoSum
+// (Dekker, |a| >= |b|) and TwoProduct through a fused multiply-add (Ogita, Rump
+// and Oishi 2005); addition, product and quotient as in the double-double
+// arithmetic of Hida, Li and Bailey (2001).
+struct FF {
+  float hi, lo;
+};
+__device__ __forceinline__ FF two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ FF fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  FF s = two_sum(a.hi, b.hi);
+  const FF t = two_sum(a.lo, b.lo);
+  s = fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
+}
+__device__ __forceinline__ FF ff_neg(FF a) { return {-a.hi, -a.lo}; }
+// a x b for a float b
+__device__ __forceinline__ FF ff_mul_f(FF a, float b) {
+  const float p = __fmul_rn(a.hi, b);
+  const float e = __fmaf_rn(a.hi, b, -p);
+  return fast_two_sum(p, __fmaf_rn(a.lo, b, e));
+}
+// a / b, b > 0: the float quotient of the leading parts, corrected twice by the
+// remainder
+__device__ __forceinline__ FF ff_div(FF a, FF b) {
+  const float q1 = __fdiv_rn(a.hi, b.hi);
+  FF r = ff_add(a, ff_neg(ff_mul_f(b, q1)));
+  const float q2 = __fdiv_rn(r.hi, b.hi);
+  r = ff_add(r, ff_neg(ff_mul_f(b, q2)));
+  const float q3 = __fdiv_rn(r.hi, b.hi);
+  const FF q = fast_two_sum(q1, q2);
+  return ff_add(q, FF{q3, 0.0f});
+}
+__device__ __forceinline__ FF ff_shfl_xor(FF a, int off) {
+  return {__shfl_xor_sync(0xffffffffu, a.hi, off), __shfl_xor_sync(0xffffffffu, a.lo, off)};
+}
+__device__ __forceinline__ FF ff_shfl_up(FF a, int off) {
+  return {__shfl_up_sync(0xffffffffu, a.hi, off), __shfl_up_sync(0xffffffffu, a.lo, off)};
+}
+// a float-float constant from a double one (folded at compile time)
+#define FF_CONST(x) FF{(float)(x), (float)((x) - (double)(float)(x))}
+
 // one warp per cell: P_b = 0.9 h_b / H + 0.1 / 256 (uniform when H = 0), then an
-// inclusive prefix sum in float64.  Lane l holds bins 8 l .. 8 l + 7 (two float4
-// loads and stores); one float64 reciprocal per cell.  Only cells that received
-// deposits since their last rebuild are rebuilt: the others' CDF already is
-// the one their histogram gives.
+// inclusive prefix sum, in float-float arithmetic (every step of the float64
+// formulation, at about 48 bits; each CDF value is rounded once to float32).
+// Lane l holds bins 8 l .. 8 l + 7 (two float4 loads and stores).  Only cells
+// that received deposits since their last rebuild are rebuilt: the others' CDF
+// already is the one their histogram gives.
 __global__ void k_guide_update(DevCache c) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -485,31 +539,34 @@ __global__ void k_guide_update(DevCache c) {
   const float4* h = reinterpret_cast<const float4*>(c.guide_hist + (size_t)warp * GUIDE_BINS) + 2 * lane;
   float4* cdf = reinterpret_cast<float4*>(c.guide_cdf + (size_t)warp * GUIDE_BINS) + 2 * lane;
   const float4 h0 = h[0], h1 = h[1];
-  double v[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
-  double loc = 0.0;
+  const float hv[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+  FF H{hv[0], 0.0f};
 #pragma unroll
-  for (int k = 0; k < 8; ++k) loc += v[k];
-  double H = loc;
-  for (int off = 16; off > 0; off >>= 1) H += __shfl_xor_sync(0xffffffffu, H, off);
-  const double sc = H > 0.0 ? 0.9 / H : 0.0;
-  const double base = H > 0.0 ? 0.1 / GUIDE_BINS : 1.0 / GUIDE_BINS;
-  double run = 0.0;
+  for (int k = 1; k < 8; ++k) H = ff_add(H, FF{hv[k], 0.0f});
+  for (int off = 16; off > 0; off >>= 1) H = ff_add(H, ff_shfl_xor(H, off));
+  // every lane takes lane 0's total (the butterfly's lanes add in other orders)
+  H = FF{__shfl_sync(0xffffffffu, H.hi, 0), __shfl_sync(0xffffffffu, H.lo, 0)};
+  const bool pos = H.hi > 0.0f;
+  const FF sc = pos ? ff_div(FF_CONST(0.9), H) : FF{0.0f, 0.0f};
+  const FF base = pos ? FF_CONST(0.1 / GUIDE_BINS) : FF_CONST(1.0 / GUIDE_BINS);
+  FF v[8];
+  FF run{0.0f, 0.0f};
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
-    v[k] = v[k] * sc + base;
-    run += v[k];
+    v[k] = ff_add(ff_mul_f(sc, hv[k]), base);
+    run = ff_add(run, v[k]);
   }
-  double incl = run;
+  FF incl = run;
   for (int off = 1; off < 32; off <<= 1) {
-    const double y = __shfl_up_sync(0xffffffffu, incl, off);
-    if (lane >= off) incl += y;
+    const FF y = ff_shfl_up(incl, off);
+    if (lane >= off) incl = ff_add(incl, y);
   }
-  double acc = incl - run;
+  FF acc = ff_add(incl, ff_neg(run));
   float o[8];
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
-    acc += v[k];
-    o[k] = (float)acc;
+    acc = ff_add(acc, v[k]);
+    o[k] = __fadd_rn(acc.hi, acc.lo);
   }
   if (lane == 31) o[7] = 1.0f;
   cdf[0] = make_float4(o[0], o[1], o[2], o[3]);
