@@ -8,7 +8,8 @@
 // C_I is rays per pixel.
 //
 // Update (Eq. "optimalBeta", spatial form of Sec. 3.1 "Optimization"): per
-// cell, technique and channel, in float64,
+// cell, technique and channel, the moments and the ratio in float64 (the square
+// roots in float32),
 //   q^RR = sqrt(C_I / C_t * m2 / V_I),   q^S = sqrt(C_I / C_t * var / V_I),
 // with m2, var the per-sample moments of Sec. 4.1 "Local estimates" and C_t the
 // mean cost; cells with n < 2 or no cost keep their factors; statistics reset.
