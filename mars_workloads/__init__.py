@@ -11,6 +11,7 @@ from .scenes import (  # noqa: F401
     furnace_scene,
     guided_room_scene,
     area_light_plane_scene,
+    light_step_scene,
     occluded_light_plane_scene,
     config_box,
     config_guided,

@@ -217,6 +217,23 @@ def occluded_light_plane_scene(width: int = 1, height: int = 1, fov: float = 30.
     return _mk(quads, [0, 1, 2], [], [], mats, cam, width, height, "occluded_light_plane")
 
 
+def light_step_scene(floor_ggx_alpha: float = 0.0) -> Scene:
+    """A floor (y = 0, [-1, 1]^2; Lambertian of albedo 0.5, or GGX of roughness
+    ``floor_ggx_alpha`` > 0 and colour 0.5), a Lambertian wall at x = 1 (y in
+    [0, 2], z in [-1, 1], albedo 0.5) and a 0.5 x 0.5 light of radiance 2 at
+    height 1 facing down (light 0): the geometry of the checks of light subpath
+    steps (emission from the light, one bounce on the floor towards the wall)."""
+    floor = _ggx(0.5, 0.5, 0.5, floor_ggx_alpha) if floor_ggx_alpha > 0.0 else _lambert(0.5, 0.5, 0.5)
+    mats = [floor, _lambert(0.5, 0.5, 0.5), _lambert(0.0, 0.0, 0.0, (2.0, 2.0, 2.0))]
+    quads = [
+        [-1.0, 0.0, -1.0, 0.0, 0.0, 2.0, 2.0, 0.0, 0.0],
+        [1.0, 0.0, -1.0, 0.0, 0.0, 2.0, 0.0, 2.0, 0.0],
+        [-0.25, 1.0, -0.25, 0.5, 0.0, 0.0, 0.0, 0.0, 0.5],  # e1 x e2 = -y
+    ]
+    cam = [0.0, 0.5, -2.0, 0.0, 0.5, 0.0, 0.0, 1.0, 0.0, 40.0]
+    return _mk(quads, [0, 1, 2], [], [], mats, cam, 1, 1, "light_step")
+
+
 def guided_room_scene(seed: int = 0, width: int = 512, height: int = 512,
                       n_spheres: int = 64, n_lights: int = 4) -> Scene:
     """Closed 4 x 4 x 4 room (albedo 0.7) with ``n_spheres`` seeded spheres

@@ -123,6 +123,15 @@ def lib():
                                                 ct.POINTER(ct.c_double)]
             L.orc_bsdf_sample_local.restype = ct.c_int
             I32 = ct.POINTER(ct.c_int32)
+            D = ct.POINTER(ct.c_double)
+            L.orc_debug_light_emit.argtypes = [ct.POINTER(SceneDesc), ct.POINTER(Params), ct.c_int, D, ct.c_int, D,
+                                               D, I32]
+            L.orc_debug_light_emit.restype = ct.c_int
+            L.orc_debug_light_bounce.argtypes = [ct.POINTER(SceneDesc), ct.POINTER(Params), ct.c_int, D, D,
+                                                 ct.c_int, D, D, I32]
+            L.orc_debug_light_bounce.restype = ct.c_int
+            L.orc_debug_light_density.argtypes = [ct.POINTER(SceneDesc), ct.POINTER(Params), ct.c_int, D, D, D, D]
+            L.orc_debug_light_density.restype = ct.c_int
             L.orc_octree_init.argtypes = [ct.c_int, I32, I32, I32]
             L.orc_octree_init.restype = ct.c_int
             L.orc_octree_refine.argtypes = [ct.c_int, ct.c_double, ct.POINTER(ct.c_double), I32, I32, I32, I32, I32,
@@ -398,6 +407,66 @@ def balance_weight(beta, pdf, participates, t, aware=True):
     q = np.ascontiguousarray(participates, np.int32)
     return L.orc_balance_weight(len(b), _p(b, ct.c_double), _p(p, ct.c_double), _p(q, ct.c_int), int(t),
                                 int(bool(aware)))
+
+
+def _debug_params(techniques=7, max_depth=6):
+    return Params(4, techniques, max_depth, MODE_WARMUP, WEIGHTS_AWARE, 0, 0, 0, 0.05, 20.0, 50.0, 0, 0, 0.0)
+
+
+def light_emit(scene, light, y0, u):
+    """Test hook: the first hits of cosine emission directions from point y0 of
+    light ``light`` drawn by u[i] = (u0, u1); returns (hits [n, 3], prims [n],
+    -1 on a miss)."""
+    L = lib()
+    sh = _SceneHolder(scene)
+    P = _debug_params()
+    y = np.ascontiguousarray(y0, np.float64)
+    uu = np.ascontiguousarray(u, np.float64).reshape(-1, 2)
+    hit = np.zeros((len(uu), 3), np.float64)
+    prim = np.zeros(len(uu), np.int32)
+    rc = L.orc_debug_light_emit(ct.byref(sh.desc), ct.byref(P), int(light), _p(y, ct.c_double), len(uu),
+                                _p(uu, ct.c_double), _p(hit, ct.c_double), _p(prim, ct.c_int32))
+    if rc != 0:
+        raise ValueError(f"orc_debug_light_emit failed with {rc}")
+    return hit, prim
+
+
+def light_bounce(scene, light, y0, d1, u):
+    """Test hook: the light subpath vertex y_1 hit from y0 along d1, and the next
+    vertex of bounces there drawn by u[i] = (u0, u1, u2) (BSDF sampling and the
+    roulette); returns (hits [n, 3], prims [n], -1 when the subpath ended)."""
+    L = lib()
+    sh = _SceneHolder(scene)
+    P = _debug_params()
+    y = np.ascontiguousarray(y0, np.float64)
+    d = np.ascontiguousarray(d1, np.float64)
+    uu = np.ascontiguousarray(u, np.float64).reshape(-1, 3)
+    hit = np.zeros((len(uu), 3), np.float64)
+    prim = np.zeros(len(uu), np.int32)
+    rc = L.orc_debug_light_bounce(ct.byref(sh.desc), ct.byref(P), int(light), _p(y, ct.c_double),
+                                  _p(d, ct.c_double), len(uu), _p(uu, ct.c_double), _p(hit, ct.c_double),
+                                  _p(prim, ct.c_int32))
+    if rc != 0:
+        raise ValueError(f"orc_debug_light_bounce failed with {rc}")
+    return hit, prim
+
+
+def light_density(scene, light, y0, d1, x):
+    """Test hook: (P<- of y_1, the first hit from y0 along d1; P<- of the first
+    hit from y_1 towards x, the light arriving from y0), the light-side area
+    densities of the whole-path weights."""
+    L = lib()
+    sh = _SceneHolder(scene)
+    P = _debug_params()
+    y = np.ascontiguousarray(y0, np.float64)
+    d = np.ascontiguousarray(d1, np.float64)
+    xx = np.ascontiguousarray(x, np.float64)
+    out = np.zeros(2, np.float64)
+    rc = L.orc_debug_light_density(ct.byref(sh.desc), ct.byref(P), int(light), _p(y, ct.c_double),
+                                   _p(d, ct.c_double), _p(xx, ct.c_double), _p(out, ct.c_double))
+    if rc != 0:
+        raise ValueError(f"orc_debug_light_density failed with {rc}")
+    return float(out[0]), float(out[1])
 
 
 def bsdf_eval_local(scene, mat, wo, wi):

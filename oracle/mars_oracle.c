@@ -23,9 +23,9 @@
  * Readings of passages the paper leaves open are stated where they are used.
  *
  * The Philox bits are pinned by the generator's published known-answer
- * vectors.  Parity unpinned: in the whole-path weights of the bidirectional
- * application, the light-side densities of the connection strategies (only
- * their partition of unity, hence unbiasedness, is pinned).
+ * vectors; the light-side densities of the whole-path weights by brute force
+ * (the landing frequencies of light subpath steps drawn by this renderer's own
+ * routines, through the test hooks at the end of the file).
  */
 #include "mars_oracle.h"
 
@@ -755,6 +755,24 @@ static void budgets_at(const rnd_t* R, int cell, int depth, const double T[3], f
 
 enum { STRAT_CAMERA = 0, STRAT_NEE = 1, STRAT_LIGHT = 2 };
 
+/* P<-_j: the area density of path vertex z_j on a light subpath.  With z_{j+1}
+ * (zj1): BSDF sampling at z_{j+1} with the light arriving from z_{j+2} (its dn)
+ * towards z_j (its dp), times that bounce's survival probability q =
+ * min(1, max_ch f cos / p); without (zj1 = NULL): cosine emission from the light
+ * point of e.  The solid-angle density becomes an area density by |cos| at z_j
+ * over the squared distance. */
+static double light_side_density(const ctx_t* C, const pathv_t* zj, const pathv_t* zj1, const light_end* e) {
+  double cos_j = fabs(dot(zj->ng, zj->dn)), g = cos_j / (zj->tn * zj->tn);
+  if (!zj1) {
+    double cl = -dot(e->n, zj->dn);
+    return cl > 0.0 ? cl / PI * g : 0.0;
+  }
+  double fc[3], pB;
+  bsdf_at(C, zj1, zj1->dn, zj1->dp, fc, &pB);
+  double q = pB > 0.0 ? fmin(1.0, max3(fc) / pB) : 0.0;
+  return pB * q * g;
+}
+
 /* Balance-heuristic weight, over every strategy that samples it, of the full
  * path z[1..n-1], e (camera order; z[0] unused), for the strategy `kind`
  * (STRAT_LIGHT: connection at camera vertex z[si]).  Evaluated from the
@@ -786,18 +804,7 @@ static double path_weight(const rnd_t* R, int n, const pathv_t* z, const light_e
     for (int ch = 0; ch < 3; ++ch) T[ch] = pB > 0.0 ? T[ch] * fc[ch] / pB / (double)bf[ORC_T_BSDF] : 0.0;
     mult = mult * bf[ORC_T_BSDF];
   }
-  for (int j = 1; j <= n - 1; ++j) {
-    double cos_j = fabs(dot(z[j].ng, z[j].dn)), g = cos_j / (z[j].tn * z[j].tn);
-    if (j == n - 1) {
-      double cl = -dot(e->n, z[j].dn);
-      LP[j] = cl > 0.0 ? cl / PI * g : 0.0;
-    } else {
-      double fc[3], pB;
-      bsdf_at(C, &z[j + 1], z[j + 1].dn, z[j + 1].dp, fc, &pB);
-      double q = pB > 0.0 ? fmin(1.0, max3(fc) / pB) : 0.0;
-      LP[j] = pB * q * g;
-    }
-  }
+  for (int j = 1; j <= n - 1; ++j) LP[j] = light_side_density(C, &z[j], j == n - 1 ? NULL : &z[j + 1], e);
   double sum = 0.0, chosen = 0.0, Cj = 1.0;
   for (int j = 1; j <= n - 1; ++j) {
     /* light connection at z_j to z_{j+1} (n - 1 - j light surface vertices) */
@@ -818,6 +825,40 @@ static double path_weight(const rnd_t* R, int n, const pathv_t* z, const light_e
   sum += Cj;
   if (kind == STRAT_CAMERA) chosen = Cj;
   return sum > 0.0 ? chosen / sum : 0.0;
+}
+
+/* cosine-distributed direction about the unit normal n, drawn by (u0, u1) */
+static v3 emit_dir(v3 n, double u0, double u1) {
+  v3 b1, b2;
+  onb(n, &b1, &b2);
+  double r = sqrt(u0), phi = 2.0 * PI * u1, zc = 1.0 - u0;
+  return to_world(mk(r * cos(phi), r * sin(phi), sqrt(zc > 0.0 ? zc : 0.0)), b1, b2, n);
+}
+
+/* One bounce of a light subpath at the hit h, the light arriving along l_in
+ * (the unit direction towards the previous light vertex): BSDF sampling with
+ * u[0], u[1], then throughput-based Russian roulette with u[2] (survival
+ * q = min(1, max_ch f cos / p), decided in float32).  Returns 0 if the subpath
+ * ends there; else the offset origin and direction of the next ray and the
+ * throughput factor f cos / (p q). */
+static int light_bounce(const ctx_t* C, const hit_t* h, v3 l_in, const double u[4], v3* org, v3* dir,
+                        double wb[3]) {
+  const double* mat = mat_of(C->d, h->mat);
+  v3 ns = dot(h->ng, l_in) >= 0.0 ? h->ng : scl(h->ng, -1.0);
+  v3 c1, c2;
+  onb(ns, &c1, &c2);
+  v3 wl;
+  if (!bsdf_sample(mat, to_local(l_in, c1, c2, ns), u[0], u[1], &wl)) return 0;
+  v3 o = to_world(wl, c1, c2, ns);
+  double fc[3], pB;
+  bsdf_eval(mat, to_local(l_in, c1, c2, ns), wl, fc, &pB);
+  if (!(pB > 0.0) || !(fc[0] > 0.0 || fc[1] > 0.0 || fc[2] > 0.0)) return 0;
+  double qk = fmin(1.0, max3(fc) / pB);
+  if (!((float)u[2] < (float)qk)) return 0;
+  for (int c = 0; c < 3; ++c) wb[c] = fc[c] / pB / qk;
+  *org = add(h->p, scl(ns, C->eps));
+  *dir = o;
+  return 1;
 }
 
 /* one light connection sample at camera vertex x (depth i): its light subpath
@@ -845,10 +886,7 @@ static void light_connection(rnd_t* R, const vtx_t* x, int depth_i, uint64_t lin
   const double* Le = mat_of(C->d, C->d->quad_mat[C->light_quad[l]]) + 5;
   /* cosine-distributed emission direction about the light's normal */
   rng4(P, (uint32_t)R->px, (uint32_t)(DIM_LIGHT + 8 * s + 1), lin, u);
-  v3 b1, b2;
-  onb(e.n, &b1, &b2);
-  double r = sqrt(u[0]), phi = 2.0 * PI * u[1], zc = 1.0 - u[0];
-  v3 dir = to_world(mk(r * cos(phi), r * sin(phi), sqrt(zc > 0.0 ? zc : 0.0)), b1, b2, e.n);
+  v3 dir = emit_dir(e.n, u[0], u[1]);
   v3 org = add(y0, scl(e.n, C->eps));
   /* alpha_1 = Le cos / (pN p_omega) = Le pi / pN */
   double alpha[3];
@@ -876,21 +914,9 @@ static void light_connection(rnd_t* R, const vtx_t* x, int depth_i, uint64_t lin
     if (k == kmax) break;
     /* continue: BSDF sampling at y_k with the light arriving from y_{k-1} */
     rng4(P, (uint32_t)R->px, (uint32_t)(DIM_LIGHT + 8 * s + k + 1), lin, u);
-    v3 l_in = yk->dn;
-    v3 ns = dot(h.ng, l_in) >= 0.0 ? h.ng : scl(h.ng, -1.0);
-    v3 c1, c2;
-    onb(ns, &c1, &c2);
-    v3 wl;
-    if (!bsdf_sample(mat, to_local(l_in, c1, c2, ns), u[0], u[1], &wl)) break;
-    v3 o = to_world(wl, c1, c2, ns);
-    double fc[3], pB;
-    bsdf_eval(mat, to_local(l_in, c1, c2, ns), wl, fc, &pB);
-    if (!(pB > 0.0) || !(fc[0] > 0.0 || fc[1] > 0.0 || fc[2] > 0.0)) break;
-    double qk = fmin(1.0, max3(fc) / pB);
-    if (!((float)u[2] < (float)qk)) break;   /* Russian roulette, decided in float32 */
-    for (int c = 0; c < 3; ++c) alpha[c] *= fc[c] / pB / qk;
-    org = add(h.p, scl(ns, C->eps));
-    dir = o;
+    double wb[3];
+    if (!light_bounce(C, &h, yk->dn, u, &org, &dir, wb)) break;
+    for (int c = 0; c < 3; ++c) alpha[c] *= wb[c];
   }
   *cost = (double)(rays + m);
   /* connections x_i -- y_k */
@@ -1211,6 +1237,104 @@ int orc_render(const orc_scene_desc* scene, const orc_params* P, orc_state* st, 
     for (int c = 0; c < 3; ++c) st->image[3 * px + c] = v[c];
     st->counters[0] += cost;
     if (st->px_rays) st->px_rays[px] = cost;
+  }
+  ctx_free(&C);
+  return 0;
+}
+
+/* ------------------------------------------------------------ test hooks
+ * Brute-force checks of the light-side densities of the whole-path weights.
+ * The renderer does not call these: they draw light subpath steps with the
+ * renderer's own routines (emit_dir, light_bounce, closest_hit) and return the
+ * density that the weights give the same steps (light_side_density), so that
+ * a test can compare the frequency of the drawn landing points with it. */
+static int debug_setup(ctx_t* C, const orc_scene_desc* scene, const orc_params* P, int l) {
+  if (!scene || !P) return -1;
+  if (ctx_init(C, scene, P) != 0) return -3;
+  if (l < 0 || l >= C->n_lights) return -1;
+  return 0;
+}
+
+int orc_debug_light_emit(const orc_scene_desc* scene, const orc_params* P, int l, const double* y0, int n,
+                         const double* u, double* hit, int32_t* prim) {
+  ctx_t C;
+  int rc = debug_setup(&C, scene, P, l);
+  if (rc != 0) { ctx_free(&C); return rc; }
+  light_end e = light_end_at(&C, l, ld3(y0));
+  v3 org = add(e.p, scl(e.n, C.eps));
+  for (int i = 0; i < n; ++i) {
+    hit_t h;
+    v3 dir = emit_dir(e.n, u[2 * i], u[2 * i + 1]);
+    prim[i] = closest_hit(&C, org, dir, &h) ? h.prim : -1;
+    if (prim[i] >= 0) { hit[3 * i] = h.p.x; hit[3 * i + 1] = h.p.y; hit[3 * i + 2] = h.p.z; }
+  }
+  ctx_free(&C);
+  return 0;
+}
+
+/* y_1: the first hit of the ray leaving light l's point y0 along d1 */
+static int debug_first_vertex(const ctx_t* C, const light_end* e, const double* d1, hit_t* h1, v3* dir1) {
+  *dir1 = nrm(ld3(d1));
+  return closest_hit(C, add(e->p, scl(e->n, C->eps)), *dir1, h1);
+}
+
+int orc_debug_light_bounce(const orc_scene_desc* scene, const orc_params* P, int l, const double* y0,
+                           const double* d1, int n, const double* u, double* hit, int32_t* prim) {
+  ctx_t C;
+  int rc = debug_setup(&C, scene, P, l);
+  if (rc != 0) { ctx_free(&C); return rc; }
+  light_end e = light_end_at(&C, l, ld3(y0));
+  hit_t h1;
+  v3 dir1;
+  if (!debug_first_vertex(&C, &e, d1, &h1, &dir1)) { ctx_free(&C); return -4; }
+  for (int i = 0; i < n; ++i) {
+    double uu[4] = {u[3 * i], u[3 * i + 1], u[3 * i + 2], 0.0};
+    v3 org, dir;
+    double wb[3];
+    hit_t h;
+    prim[i] = -1;
+    if (light_bounce(&C, &h1, scl(dir1, -1.0), uu, &org, &dir, wb) && closest_hit(&C, org, dir, &h)) {
+      prim[i] = h.prim;
+      hit[3 * i] = h.p.x; hit[3 * i + 1] = h.p.y; hit[3 * i + 2] = h.p.z;
+    }
+  }
+  ctx_free(&C);
+  return 0;
+}
+
+int orc_debug_light_density(const orc_scene_desc* scene, const orc_params* P, int l, const double* y0,
+                            const double* d1, const double* x, double* out) {
+  ctx_t C;
+  int rc = debug_setup(&C, scene, P, l);
+  if (rc != 0) { ctx_free(&C); return rc; }
+  light_end e = light_end_at(&C, l, ld3(y0));
+  hit_t h1, hx;
+  v3 dir1;
+  if (!debug_first_vertex(&C, &e, d1, &h1, &dir1)) { ctx_free(&C); return -4; }
+  /* y_1 as a path vertex (camera order: dn towards the light point) */
+  pathv_t z1;
+  z1.p = h1.p;
+  z1.ng = h1.ng;
+  z1.mat = h1.mat;
+  z1.dn = scl(dir1, -1.0);
+  z1.tn = h1.t;
+  z1.dp = mk(0, 0, 0);
+  out[0] = light_side_density(&C, &z1, NULL, &e);
+  /* x: the first hit of the ray from y_1 (offset as a bounce offsets it) towards x */
+  v3 ns = dot(h1.ng, z1.dn) >= 0.0 ? h1.ng : scl(h1.ng, -1.0);
+  v3 org = add(h1.p, scl(ns, C.eps));
+  v3 dx = nrm(sub(ld3(x), org));
+  out[1] = 0.0;
+  if (closest_hit(&C, org, dx, &hx)) {
+    pathv_t zx;
+    zx.p = hx.p;
+    zx.ng = hx.ng;
+    zx.mat = hx.mat;
+    zx.dn = scl(dx, -1.0);
+    zx.tn = hx.t;
+    zx.dp = mk(0, 0, 0);
+    z1.dp = dx;
+    out[1] = light_side_density(&C, &zx, &z1, &e);
   }
   ctx_free(&C);
   return 0;

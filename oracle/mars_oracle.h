@@ -115,6 +115,26 @@ void orc_update_counts(int n_cells, int techniques, const double* stats, double 
  * cdf = inclusive prefix sum of P. */
 void orc_guide_update(int n_cells, const double* hist, float* cdf);
 
+/* Test hooks (the renderer does not call them): light subpath steps drawn by
+ * the renderer's routines, and the light-side densities the whole-path weights
+ * give them.  l: light index; y0: a point on it.
+ * orc_debug_light_emit: n cosine emission directions from y0, drawn by
+ *   u[2i], u[2i+1]; hit[3i..3i+2] = the first hit, prim[i] its primitive (-1:
+ *   miss).
+ * orc_debug_light_bounce: y_1 = the first hit of the ray from y0 along d1; n
+ *   bounces at y_1 (BSDF sampling and the roulette) drawn by u[3i..3i+2];
+ *   hit / prim of the next vertex (-1: the subpath ended or missed).
+ * orc_debug_light_density: out[0] = P<- of y_1 (emission density, area measure),
+ *   out[1] = P<- of the first hit x' of the ray from y_1 towards x (the bounce
+ *   density with the light arriving from y0, times the survival probability).
+ * Return 0, or a negative value on invalid input (-4: the ray along d1 misses). */
+int orc_debug_light_emit(const orc_scene_desc* scene, const orc_params* P, int l, const double* y0, int n,
+                         const double* u, double* hit, int32_t* prim);
+int orc_debug_light_bounce(const orc_scene_desc* scene, const orc_params* P, int l, const double* y0,
+                           const double* d1, int n, const double* u, double* hit, int32_t* prim);
+int orc_debug_light_density(const orc_scene_desc* scene, const orc_params* P, int l, const double* y0,
+                            const double* d1, const double* x, double* out);
+
 /* Adaptive octree cache (the spatial structure of EARS, Sec. 5.1), refined
  * between iterations.  Depth at most ORC_OCT_LMAX; a point's leaf is found by
  * descending with the bits of its cell coordinates at the finest level,

@@ -1029,6 +1029,76 @@ def test_whole_path_weights_reduce_to_the_vertex_weights_without_light_connectio
     np.testing.assert_allclose(b.stats[:, :2], a.stats[:, :2], rtol=1e-12, atol=1e-15)
 
 
+def _patch_counts_and_expectation(hits, prims, prim, axes, lo, hi, density, n, grid=8):
+    """Landings of n drawn steps on primitive `prim` inside the rectangle
+    [lo, hi] of the coordinates `axes`, and their expected number: n times the
+    integral of `density` (a function of a point) over the rectangle, by the
+    midpoint rule on a grid x grid lattice."""
+    sel = prims == prim
+    for a, l0, h0 in zip(axes, lo, hi):
+        sel &= (hits[:, a] >= l0) & (hits[:, a] < h0)
+    count = int(sel.sum())
+    plane = hits[prims == prim][0].copy()
+    total = 0.0
+    for i in range(grid):
+        for j in range(grid):
+            x = plane.copy()
+            x[axes[0]] = lo[0] + (i + 0.5) * (hi[0] - lo[0]) / grid
+            x[axes[1]] = lo[1] + (j + 0.5) * (hi[1] - lo[1]) / grid
+            total += density(x)
+    area = (hi[0] - lo[0]) * (hi[1] - lo[1])
+    return count, n * total / grid ** 2 * area
+
+
+def _assert_frequency_matches(count, expected):
+    # Poisson scatter of the count, plus 2 % for the midpoint rule
+    assert expected > 400
+    assert abs(count - expected) < 5.0 * math.sqrt(expected) + 0.02 * expected, (count, expected)
+
+
+def test_light_side_densities_match_the_drawn_light_steps(orc):
+    """Brute force on the light-side densities P<- of the whole-path weights:
+    light subpath steps drawn by the renderer's own routines land on a patch as
+    often as the density the weights give those steps says.  Emission: cosine
+    directions from a point of the light, landings on a floor patch and on a
+    wall patch (the cosines at the light and at the landing point differ, and
+    no 1/pi or 1/d^2 may be missing).  Bounce: BSDF sampling with the light
+    arriving from the light point, then the roulette, at a floor vertex, landings
+    on two wall patches: the density is that of the sampled direction towards
+    the landing point given the direction the light came from, times the
+    survival probability, converted by the cosine at the landing point --
+    Lambertian floor (survival 0.5) and a GGX floor whose lobe the landings
+    follow."""
+    n = 400_000
+    rng = np.random.default_rng(2024)
+    scene = W.light_step_scene()
+    y0 = np.array([0.0, 1.0, 0.0])
+    org = y0 + np.array([0.0, -1.0, 0.0]) * 1e-4   # the emission origin is offset along the light normal
+    hits, prims = orc.light_emit(scene, 0, y0, rng.uniform(size=(n, 2)))
+
+    def emit_density(x):
+        return orc.light_density(scene, 0, y0, x - org, x)[0]
+
+    for prim, axes, lo, hi in ((0, (0, 2), (0.3, -0.5), (0.5, -0.3)), (1, (1, 2), (0.3, 0.0), (0.5, 0.2))):
+        _assert_frequency_matches(*_patch_counts_and_expectation(hits, prims, prim, axes, lo, hi, emit_density, n))
+
+    for alpha, y0, y1, patches in (
+            (0.0, np.array([0.0, 1.0, 0.0]), np.array([-0.3, 0.0, 0.2]),
+             (((1, 2), (0.2, -0.2), (0.5, 0.1)), ((1, 2), (0.6, 0.3), (0.9, 0.6)))),
+            (0.3, np.array([-0.2, 1.0, 0.0]), np.array([0.5, 0.0, 0.0]),
+             (((1, 2), (0.66, -0.05), (0.76, 0.05)), ((1, 2), (0.4, 0.1), (0.5, 0.2))))):
+        scene = W.light_step_scene(alpha)
+        d1 = y1 - (y0 + np.array([0.0, -1.0, 0.0]) * 1e-4)
+        hits, prims = orc.light_bounce(scene, 0, y0, d1, rng.uniform(size=(n, 3)))
+
+        def bounce_density(x, scene=scene, y0=y0, d1=d1):
+            return orc.light_density(scene, 0, y0, d1, x)[1]
+
+        for axes, lo, hi in patches:
+            _assert_frequency_matches(*_patch_counts_and_expectation(hits, prims, 1, axes, lo, hi, bounce_density,
+                                                                     n))
+
+
 @pytest.mark.parametrize("D,counts", [(2, "beta1"), (2, "random"), (3, "beta1")])
 def test_guide_deposits_closed_form_in_the_furnace(orc, D, counts):
     """Guide learning records, per continuation sample, the incident radiance
