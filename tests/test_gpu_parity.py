@@ -301,6 +301,38 @@ def test_update_and_guide_parity(mars, orc):
     np.testing.assert_allclose(g["guide_cdf"], cdf, atol=2e-7)
 
 
+def test_guide_update_edge_cases(mars, orc):
+    """The guide CDF rebuild (float-float arithmetic on the GPU, float64 in the
+    oracle) on histograms at the edges: empty, one bin, two bins 40 orders of
+    magnitude apart, uniform, every bin tiny or huge, a geometric ramp over 256
+    bins, and seeded random rows; every CDF value within 2e-7 of the oracle's,
+    the last exactly 1."""
+    cfg = W.config_guided(16, 16)
+    scene, cache = _make(mars, cfg)
+    cells = cfg.n_cells
+    rng = np.random.default_rng(311)
+    hist = rng.exponential(1.0, size=(cells, 256)).astype(np.float32)
+    hist[rng.uniform(size=hist.shape) < 0.3] = 0.0
+    hist[0] = 0.0
+    hist[1] = 0.0
+    hist[1, 17] = 3.0
+    hist[2] = 0.0
+    hist[2, 0], hist[2, 255] = 1e20, 1e-20
+    hist[3] = 1.0
+    hist[4] = 1e-20
+    hist[5] = 1e20
+    hist[6] = (1.07 ** np.arange(256)).astype(np.float32)
+    hist[7] = 0.0
+    hist[7, 255] = 5.0
+    cache.set_state(guide_hist=hist, has_estimate=True, n_iterations=1)
+    cache.update_counts()
+    g = cache.get_state()
+    cdf = orc.guide_update(hist.astype(np.float64))
+    np.testing.assert_allclose(g["guide_cdf"], cdf, atol=2e-7, rtol=0)
+    assert np.all(g["guide_cdf"][:, -1] == 1.0)
+    assert np.all(np.diff(g["guide_cdf"], axis=1) >= 0.0)
+
+
 def test_training_iteration_update_takes_the_mean_image_statistics(mars, orc):
     """A training iteration of three renders (Sec. 4.1 "Fixed-point iteration":
     the iterations grow in duration): the statistics of all three accumulate,
