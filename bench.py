@@ -796,7 +796,7 @@ def precision_study(cfg, cache, seed, it, stream):
     return out
 
 
-def learn(M, cache, img, seed, n, warmup, stream, mode=None, weights=None, drop=0, max_mult=0.0, combine=False):
+def learn(M, cache, img, seed, n, warmup, stream, mode=None, weights=None, drop=0, max_mult=0.0):
     """A job of n one-sample renders on `cache` (the first `warmup` of them
     warm-up renders, or all in `mode`), with the count update closing each
     training iteration of the library's schedule (1, 2, 4, ... renders after the
@@ -806,8 +806,7 @@ def learn(M, cache, img, seed, n, warmup, stream, mode=None, weights=None, drop=
     for k in range(n):
         m = mode if mode is not None else (M.MARS_MODE_WARMUP if k < warmup else M.MARS_MODE_MARS)
         sts.append(cache.render_iteration(img, seed=seed, iteration=k, mode=m, weights=weights, update_estimate=True,
-                                          vi_drop_brightest=drop, max_multiplicity=max_mult,
-                                          combine=(2 if k == 0 else 1) if combine else 0, stream=stream))
+                                          vi_drop_brightest=drop, max_multiplicity=max_mult, stream=stream))
         if M.training_step_ends(k, warmup, n):
             cache.update_counts(stream=stream)
     return sts

@@ -573,6 +573,7 @@ __global__ void k_guide_update(DevCache c) {
   cdf[0] = make_float4(o[0], o[1], o[2], o[3]);
   cdf[1] = make_float4(o[4], o[5], o[6], o[7]);
 }
+#undef FF_CONST
 
 // samples of the iteration per octree leaf, all techniques (exact in float32
 // below 2^24), read before the update zeroes the statistics
