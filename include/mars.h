@@ -338,7 +338,7 @@ mars_status mars_cache_create(const mars_scene* scene, const mars_cache_desc* de
 mars_status mars_cache_destroy(mars_cache* cache);
 mars_status mars_cache_info_get(const mars_cache* cache, mars_cache_info* info);
 
-/* ---- one fixed-point iteration (Sec. 4.1, "Fixed-point iteration") ---------
+/* ---- one render of a training iteration (Sec. 4.1, "Fixed-point iteration") -
  * Renders one sample per pixel with the wavefront MARS path tracer: camera
  * rays, then per depth wave closest hit, count lookup (T(x)/I_px x q, three
  * cases, clamp), Alg. 1, NEE shadow rays, BSDF/guided child rays compacted
